@@ -1,0 +1,211 @@
+"""FP64 CPU oracle for abstract rendering (test infrastructure only).
+
+The arithmetic lives in oracle.c (plain C, double precision, straight loops in
+the order of the paper's Algorithms 1-4).  This module compiles it with gcc and
+marshals numpy arrays through ctypes.  Only the test-suite, the smoke check
+and the benchmark's CPU-baseline leg may import it; the CUDA library never
+does.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIB = os.path.join(_LIBDIR, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into oracle/_lib/liboracle.so (OpenMP if available)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", _SRC, "-o", _LIB + ".tmp", "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        I64 = ctypes.c_int64
+        I = ctypes.c_int
+        D = ctypes.c_double
+        lib.orc_render_concrete.argtypes = [P, P, P, P, P, I64, P, P, P, P, I, P]
+        lib.orc_render_concrete.restype = I
+        lib.orc_render_abstract.argtypes = [P, P, P, P, P, I64, P, P, P, P, P, I, I, I, I, P, P, P]
+        lib.orc_render_abstract.restype = I
+        lib.orc_records.argtypes = [P, P, P, P, P, I64, P, P, P, P, P, P]
+        lib.orc_records.restype = I
+        lib.orc_matrixinv_interval.argtypes = [P, P, I, I, P, P, P]
+        lib.orc_matrixinv_interval.restype = I
+        lib.orc_relax_mul.argtypes = [P, P, P]
+        lib.orc_relax_sq.argtypes = [P, P]
+        lib.orc_rot_forms.argtypes = [P, P, P]
+        lib.orc_concrete_alpha.argtypes = [P, P, P, D, P, P, P, P, D, D]
+        lib.orc_concrete_alpha.restype = D
+        lib.orc_check_samples.argtypes = [P, P, P, P, P, I64, P, P, P, P, I64, P, P, D, P]
+        lib.orc_check_samples.restype = D
+        lib.orc_empirical_bounds.argtypes = [P, P, P, P, P, I64, P, P, P, P, I64, P, P]
+        lib.orc_set_threads.argtypes = [I]
+        lib.orc_set_threads.restype = I
+        _lib = lib
+    return _lib
+
+
+def _d(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def set_threads(n: int = 0) -> int:
+    """Set (n > 0) and return the oracle's OpenMP thread count."""
+    return int(_load().orc_set_threads(int(n)))
+
+
+def _scene_args(scene):
+    arrs = [_d(scene.uw), _d(scene.logscale), _d(scene.quat), _d(scene.opacity), _d(scene.rgb)]
+    return arrs
+
+
+def _cam_args(cam):
+    intr = _d([cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, cam.near])
+    return intr, _d(cam.R_wc).reshape(9), _d(cam.t)
+
+
+def render_concrete(scene, cam, delta, blend: str = "ind") -> np.ndarray:
+    """GSplat (Algorithm 1) at one pose; blend 'sort' (Algorithm 2) or 'ind' (Algorithm 4)."""
+    lib = _load()
+    s = _scene_args(scene)
+    intr, R0, t0 = _cam_args(cam)
+    dl = _d(delta).reshape(6)
+    out = np.zeros((cam.height, cam.width, 3), dtype=np.float64)
+    st = lib.orc_render_concrete(*[_p(a) for a in s], scene.n, _p(intr), _p(R0), _p(t0), _p(dl),
+                                 0 if blend == "sort" else 1, _p(out))
+    if st:
+        raise RuntimeError("oracle concrete render failed")
+    return out
+
+
+def render_abstract(scene, cam, cell_lo, cell_hi, window=None):
+    """AbstractSplat bounds of one pose cell.
+
+    Returns (lo, hi, fragile): lo/hi are [H, W, 3] float64 (only `window`
+    = (px0, px1, py0, py1), inclusive, is filled; the rest stays NaN) and
+    fragile [H, W] uint8 marks pixels where a threshold decision that the
+    single-precision path takes lies within its rounding band."""
+    lib = _load()
+    s = _scene_args(scene)
+    intr, R0, t0 = _cam_args(cam)
+    lo = np.full((cam.height, cam.width, 3), np.nan)
+    hi = np.full((cam.height, cam.width, 3), np.nan)
+    frag = np.zeros((cam.height, cam.width), dtype=np.uint8)
+    if window is None:
+        window = (0, cam.width - 1, 0, cam.height - 1)
+    px0, px1, py0, py1 = (int(v) for v in window)
+    st = lib.orc_render_abstract(*[_p(a) for a in s], scene.n, _p(intr), _p(R0), _p(t0),
+                                 _p(_d(cell_lo).reshape(6)), _p(_d(cell_hi).reshape(6)),
+                                 px0, px1, py0, py1, _p(lo), _p(hi), _p(frag))
+    if st:
+        raise RuntimeError("oracle abstract render failed")
+    return lo, hi, frag
+
+
+def records(scene, cam, cell_lo, cell_hi) -> dict:
+    """Per-Gaussian summary of the abstract pipeline for one cell."""
+    lib = _load()
+    s = _scene_args(scene)
+    intr, R0, t0 = _cam_args(cam)
+    out = np.zeros((scene.n, 10), dtype=np.float64)
+    lib.orc_records(*[_p(a) for a in s], scene.n, _p(intr), _p(R0), _p(t0),
+                    _p(_d(cell_lo).reshape(6)), _p(_d(cell_hi).reshape(6)), _p(out))
+    keys = ["valid", "straddle", "fallback", "klo", "khi", "px0", "px1", "py0", "py1", "rho"]
+    return {k: out[:, i] for i, k in enumerate(keys)}
+
+
+def concrete_alpha(uw, logscale, quat, opacity, cam, delta, ux, uy) -> float:
+    lib = _load()
+    intr, R0, t0 = _cam_args(cam)
+    return float(lib.orc_concrete_alpha(_p(_d(uw)), _p(_d(logscale)), _p(_d(quat)), float(opacity),
+                                        _p(intr), _p(R0), _p(t0), _p(_d(delta)), float(ux), float(uy)))
+
+
+def matrixinv_interval(Xl, Xu, k: int = 8, symmetric: bool = False):
+    """MatrixInv (Algorithm 3) on an interval 2x2 matrix whose entries are
+    independent (symmetric=True: the off-diagonal entries are one variable).
+    Returns (lower, upper, rho) as 2x2 arrays, or None if the assertion fails."""
+    lib = _load()
+    xl = _d(Xl).reshape(4)
+    xu = _d(Xu).reshape(4)
+    ol = np.zeros(4)
+    ou = np.zeros(4)
+    rho = np.zeros(1)
+    st = lib.orc_matrixinv_interval(_p(xl), _p(xu), int(k), 1 if symmetric else 0, _p(ol), _p(ou), _p(rho))
+    if st:
+        return None
+    return ol.reshape(2, 2), ou.reshape(2, 2), float(rho[0])
+
+
+def relax_mul(x, y) -> np.ndarray:
+    """Mul relaxation on bounded scalars given as 14-vectors (lo form, hi form)."""
+    lib = _load()
+    out = np.zeros(14)
+    lib.orc_relax_mul(_p(_d(x)), _p(_d(y)), _p(out))
+    return out
+
+
+def relax_sq(x) -> np.ndarray:
+    lib = _load()
+    out = np.zeros(14)
+    lib.orc_relax_sq(_p(_d(x)), _p(out))
+    return out
+
+
+def rot_forms(lo, hi) -> np.ndarray:
+    """Forms of the nine entries of R_delta over the cell: (9, 14)."""
+    lib = _load()
+    out = np.zeros((9, 14))
+    lib.orc_rot_forms(_p(_d(lo)), _p(_d(hi)), _p(out))
+    return out
+
+
+def check_samples(scene, cam, poses, lo, hi, tol: float = 0.0):
+    """Render at each pose (BlendSort) and compare with [lo, hi].
+    Returns (largest violation, number of violating values)."""
+    lib = _load()
+    s = _scene_args(scene)
+    intr, R0, t0 = _cam_args(cam)
+    P = _d(poses).reshape(-1, 6)
+    nv = np.zeros(1, dtype=np.int64)
+    worst = lib.orc_check_samples(*[_p(a) for a in s], scene.n, _p(intr), _p(R0), _p(t0), _p(P), P.shape[0],
+                                  _p(_d(lo)), _p(_d(hi)), float(tol), _p(nv))
+    return float(worst), int(nv[0])
+
+
+def empirical_bounds(scene, cam, poses):
+    """Per-pixel min/max of the concrete renders over the given poses."""
+    lib = _load()
+    s = _scene_args(scene)
+    intr, R0, t0 = _cam_args(cam)
+    P = _d(poses).reshape(-1, 6)
+    lo = np.zeros((cam.height, cam.width, 3))
+    hi = np.zeros((cam.height, cam.width, 3))
+    lib.orc_empirical_bounds(*[_p(a) for a in s], scene.n, _p(intr), _p(R0), _p(t0), _p(P), P.shape[0],
+                             _p(lo), _p(hi))
+    return lo, hi

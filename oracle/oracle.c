@@ -1,0 +1,846 @@
+/*
+ * FP64 CPU oracle for abstract rendering of Gaussian-splat scenes
+ * (Li, Ji, Zhong, Zhang, Mitra, "Abstract Rendering: Computing All that is Seen
+ * in Gaussian Splat Scenes", arXiv 2503.00308).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, double-precision
+ * statement of what the CUDA path computes.  Only the test-suite, the smoke
+ * check and the benchmark's CPU-baseline leg load it.  It shares no code,
+ * header or table with the CUDA library; the two meet only through the seeded
+ * input generator.
+ *
+ * Everything is straight loops in the order of the paper's algorithms:
+ *   - GSplat, Algorithm 1 (Sec. 2.2), with either blend:
+ *       BlendSort, Algorithm 2 (depth sort + cumulative product), and
+ *       BlendInd,  Algorithm 4 (pairwise Ind, O(N^2)).
+ *   - AbstractSplat (Sec. 3.3): Algorithm 1 with every variable replaced by a
+ *     pair of linear bounds over the pose cell, Conic replaced by MatrixInv
+ *     (Algorithm 3, Sec. 3.1) and BlendSort by BlendInd (Sec. 3.2).
+ *
+ * Linear bounds.  A pose cell is a box over delta = (tx,ty,tz,rx,ry,rz); each
+ * coordinate is written delta_k = ctr_k + h_k * p_k with p in [-1,1]^6.  A
+ * "bounded scalar" is a pair of affine forms lo(p) <= v <= hi(p), the
+ * piecewise-linear relation of Sec. 2.1 with a single piece.  Concretising a
+ * form over the box gives  k - sum|c|  (lower) or  k + sum|c|  (upper).
+ *
+ * Relaxations the paper delegates to CROWN and does not print are fixed here
+ * (each is a sound choice; all collapse to the exact value on a point cell):
+ *   Mul x*y    : average of the two McCormick planes of each side.
+ *   Square x^2 : tangent at the interval midpoint (lower), secant (upper).
+ *   Exp        : Table 2 -- tangent at the lower end, secant (upper), on
+ *                [x_lo, min(x_hi, 0)] because x = -m/2 <= 0.
+ *   R(theta)   : first-order Taylor form at the cell centre, remainder
+ *                +-(1/2)(h_rx+h_ry+h_rz)^2 (every second partial of an entry of
+ *                Rx Ry Rz has magnitude <= 1).
+ *   Ind        : three-valued from depth-key intervals (Table 2 Ind, split at 0).
+ *   Prod       : interval transmittance products; colour sums kept as forms.
+ *   Cutoff     : a = 0 where o*exp(-m/2) < 1/255, relaxed soundly with ramps
+ *                whose width shrinks to zero with the cell.
+ *
+ * Parity of the "tightness" of these choices against the paper's CROWN numbers
+ * is unpinned (the paper's scenes are not available); their soundness and their
+ * exactness on point cells are pinned by the test-suite.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define NV 6            /* pose variables tx ty tz rx ry rz */
+#define KTAYLOR 8       /* MatrixInv Taylor order, default k = 8 (Sec. 3.3 footnote) */
+
+/* Algorithm constants shared by definition with the CUDA path (not by code). */
+static const double RHO_MAX = 1.0 - 1.0 / 1024.0;  /* MatrixInv usable while ||I-X X0|| < RHO_MAX */
+static const double CUT_RAMP = 0.5;   /* widest cutoff ramp, in units of m */
+static const double CLIP_RAMP = 0.25; /* blend width of the upper-alpha clip to o */
+static const double KEY_SLACK = 1e-9; /* relative widening of depth keys */
+static const double BOX_SLACK = 1e-9; /* relative widening of screen boxes */
+static const double ALPHA_MIN = 1.0 / 255.0;
+
+typedef struct { double c[NV]; double k; } lf;   /* sum_i c_i p_i + k */
+typedef struct { lf lo, hi; } bs;                 /* lo(p) <= v <= hi(p) */
+
+/* ------------------------------------------------------------------ forms */
+
+static double lf_min(const lf *f) { double s = f->k; for (int i = 0; i < NV; ++i) s -= fabs(f->c[i]); return s; }
+static double lf_max(const lf *f) { double s = f->k; for (int i = 0; i < NV; ++i) s += fabs(f->c[i]); return s; }
+static double bs_min(const bs *b) { return lf_min(&b->lo); }
+static double bs_max(const bs *b) { return lf_max(&b->hi); }
+
+static lf lf_cst(double v) { lf f; memset(&f, 0, sizeof f); f.k = v; return f; }
+static lf lf_scale(const lf *a, double s) { lf r; for (int i = 0; i < NV; ++i) r.c[i] = s * a->c[i]; r.k = s * a->k; return r; }
+static lf lf_add(const lf *a, const lf *b) { lf r; for (int i = 0; i < NV; ++i) r.c[i] = a->c[i] + b->c[i]; r.k = a->k + b->k; return r; }
+static lf lf_sub(const lf *a, const lf *b) { lf r; for (int i = 0; i < NV; ++i) r.c[i] = a->c[i] - b->c[i]; r.k = a->k - b->k; return r; }
+
+static bs bs_cst(double v) { bs b; b.lo = lf_cst(v); b.hi = lf_cst(v); return b; }
+static bs bs_add(bs a, bs b) { bs r; r.lo = lf_add(&a.lo, &b.lo); r.hi = lf_add(&a.hi, &b.hi); return r; }
+static bs bs_sub(bs a, bs b) { bs r; r.lo = lf_sub(&a.lo, &b.hi); r.hi = lf_sub(&a.hi, &b.lo); return r; }
+static bs bs_addc(bs a, double v) { a.lo.k += v; a.hi.k += v; return a; }
+/* constant * bounded scalar: a negative factor swaps the sides */
+static bs bs_scale(bs a, double s)
+{
+    bs r;
+    if (s >= 0) { r.lo = lf_scale(&a.lo, s); r.hi = lf_scale(&a.hi, s); }
+    else        { r.lo = lf_scale(&a.hi, s); r.hi = lf_scale(&a.lo, s); }
+    return r;
+}
+
+/* x*y: the lower planes y_lo x + x_lo y - x_lo y_lo and y_hi x + x_hi y - x_hi y_hi
+ * averaged give  y_m x + x_m y - (x_lo y_lo + x_hi y_hi)/2 <= x y ; the upper
+ * planes averaged give  y_m x + x_m y - (x_hi y_lo + x_lo y_hi)/2 >= x y, with
+ * x_m, y_m the interval midpoints.  x and y are then replaced by the side of
+ * their bounds that keeps the inequality (the sign of the slope decides). */
+static bs bs_mul(bs x, bs y)
+{
+    double xl = bs_min(&x), xh = bs_max(&x), yl = bs_min(&y), yh = bs_max(&y);
+    double xm = 0.5 * (xl + xh), ym = 0.5 * (yl + yh);
+    bs r;
+    lf a, b;
+    a = lf_scale(ym >= 0 ? &x.lo : &x.hi, ym);
+    b = lf_scale(xm >= 0 ? &y.lo : &y.hi, xm);
+    r.lo = lf_add(&a, &b);
+    r.lo.k -= 0.5 * (xl * yl + xh * yh);
+    a = lf_scale(ym >= 0 ? &x.hi : &x.lo, ym);
+    b = lf_scale(xm >= 0 ? &y.hi : &y.lo, xm);
+    r.hi = lf_add(&a, &b);
+    r.hi.k -= 0.5 * (xh * yl + xl * yh);
+    return r;
+}
+
+/* x^2: tangent at the midpoint c (2c x - c^2) below, secant (xl+xh) x - xl xh above. */
+static bs bs_sq(bs x)
+{
+    double xl = bs_min(&x), xh = bs_max(&x), c = 0.5 * (xl + xh), s = xl + xh;
+    bs r;
+    r.lo = lf_scale(c >= 0 ? &x.lo : &x.hi, 2.0 * c);
+    r.lo.k -= c * c;
+    r.hi = lf_scale(s >= 0 ? &x.hi : &x.lo, s);
+    r.hi.k -= xl * xh;
+    return r;
+}
+
+/* -------------------------------------------------------- scene and pose */
+
+/* rotation of a unit quaternion (w,x,y,z) */
+static void quat_to_R(const double q_in[4], double R[9])
+{
+    double n = sqrt(q_in[0] * q_in[0] + q_in[1] * q_in[1] + q_in[2] * q_in[2] + q_in[3] * q_in[3]);
+    double w = q_in[0] / n, x = q_in[1] / n, y = q_in[2] / n, z = q_in[3] / n;
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+static void mat3_mul(const double A[9], const double B[9], double C[9])
+{
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0;
+            for (int k = 0; k < 3; ++k) s += A[3 * i + k] * B[3 * k + j];
+            C[3 * i + j] = s;
+        }
+}
+
+/* Rx(a), Ry(b), Rz(g) and their first derivatives */
+static void rot_x(double a, double R[9], double D[9])
+{
+    double c = cos(a), s = sin(a);
+    double r[9] = {1, 0, 0, 0, c, -s, 0, s, c}, d[9] = {0, 0, 0, 0, -s, -c, 0, c, -s};
+    memcpy(R, r, sizeof r); memcpy(D, d, sizeof d);
+}
+static void rot_y(double b, double R[9], double D[9])
+{
+    double c = cos(b), s = sin(b);
+    double r[9] = {c, 0, s, 0, 1, 0, -s, 0, c}, d[9] = {-s, 0, c, 0, 0, 0, -c, 0, -s};
+    memcpy(R, r, sizeof r); memcpy(D, d, sizeof d);
+}
+static void rot_z(double g, double R[9], double D[9])
+{
+    double c = cos(g), s = sin(g);
+    double r[9] = {c, -s, 0, s, c, 0, 0, 0, 1}, d[9] = {-s, -c, 0, c, -s, 0, 0, 0, 0};
+    memcpy(R, r, sizeof r); memcpy(D, d, sizeof d);
+}
+
+/* camera-frame perturbation R_delta = Rx(rx) Ry(ry) Rz(rz); optionally its partials */
+static void rot_delta(const double th[3], double R[9], double dR[3][9])
+{
+    double X[9], dX[9], Y[9], dY[9], Z[9], dZ[9], T[9];
+    rot_x(th[0], X, dX); rot_y(th[1], Y, dY); rot_z(th[2], Z, dZ);
+    mat3_mul(X, Y, T); mat3_mul(T, Z, R);
+    if (dR) {
+        mat3_mul(dX, Y, T); mat3_mul(T, Z, dR[0]);
+        mat3_mul(X, dY, T); mat3_mul(T, Z, dR[1]);
+        mat3_mul(X, Y, T);  mat3_mul(T, dZ, dR[2]);
+    }
+}
+
+typedef struct {
+    int W, H;
+    double fx, fy, cx, cy, near_plane;
+    double R0[9];   /* nominal world->camera rotation */
+    double t0[3];   /* nominal camera centre */
+} camera;
+
+static camera make_camera(const double *intr, const double *R0, const double *t0)
+{
+    camera c;
+    c.W = (int)intr[0]; c.H = (int)intr[1];
+    c.fx = intr[2]; c.fy = intr[3]; c.cx = intr[4]; c.cy = intr[5]; c.near_plane = intr[6];
+    memcpy(c.R0, R0, sizeof c.R0); memcpy(c.t0, t0, sizeof c.t0);
+    return c;
+}
+
+/* covariance factor Mw = R(q) diag(exp(s)) (the footnote of Sec. 2.2 allows any
+ * square-root factor: Cov = Mw Mw^T) */
+static void cov_factor(const double *ls, const double *q, double Mw[9])
+{
+    double R[9];
+    quat_to_R(q, R);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Mw[3 * i + j] = R[3 * i + j] * exp(ls[j]);
+}
+
+/* ============================================================ GSplat ===== */
+
+/* Per-Gaussian quantities of Algorithm 1 at one concrete pose. */
+typedef struct {
+    double d, up[2], Mp[6], conic[4], o, tau, c[3];
+    int alive;
+} gconc;
+
+static void gsplat_gaussian(const camera *cam, const double Rwc[9], const double t[3],
+                            const double *uw, const double *ls, const double *q, double o,
+                            const double *rgb, gconc *g)
+{
+    double Mw[9], Mc[9], uc[3], diff[3];
+    cov_factor(ls, q, Mw);
+    for (int a = 0; a < 3; ++a) diff[a] = uw[a] - t[a];
+    for (int a = 0; a < 3; ++a) uc[a] = Rwc[3 * a] * diff[0] + Rwc[3 * a + 1] * diff[1] + Rwc[3 * a + 2] * diff[2];
+    mat3_mul(Rwc, Mw, Mc);
+    g->d = uc[2];
+    g->up[0] = cam->fx * uc[0] + cam->cx * uc[2];
+    g->up[1] = cam->fy * uc[1] + cam->cy * uc[2];
+    /* J of Algorithm 1 (the usual projection Jacobian scaled by d^2) */
+    double J[6] = {cam->fx * uc[2], 0, -cam->fx * uc[0], 0, cam->fy * uc[2], -cam->fy * uc[1]};
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 3; ++c)
+            g->Mp[3 * r + c] = J[3 * r] * Mc[c] + J[3 * r + 1] * Mc[3 + c] + J[3 * r + 2] * Mc[6 + c];
+    double X[4];
+    for (int r = 0; r < 2; ++r)
+        for (int s = 0; s < 2; ++s)
+            X[2 * r + s] = g->Mp[3 * r] * g->Mp[3 * s] + g->Mp[3 * r + 1] * g->Mp[3 * s + 1] + g->Mp[3 * r + 2] * g->Mp[3 * s + 2];
+    double det = X[0] * X[3] - X[1] * X[2];
+    g->conic[0] = X[3] / det; g->conic[1] = -X[1] / det; g->conic[2] = -X[2] / det; g->conic[3] = X[0] / det;
+    g->o = o;
+    g->tau = (o > 0) ? 2.0 * log(255.0 * o) : -INFINITY;
+    for (int k = 0; k < 3; ++k) g->c[k] = rgb[k];
+    g->alive = (g->d > cam->near_plane) && (det > 0) && (o > 0);
+}
+
+/* effective opacity at pixel u (Algorithm 1, lines 9-10) with the 1/255 cutoff */
+static double gsplat_alpha(const gconc *g, double ux, double uy)
+{
+    if (!g->alive) return 0.0;
+    double D[2] = {g->d * g->d * ux - g->d * g->up[0], g->d * g->d * uy - g->d * g->up[1]};
+    double q[3], m = 0;
+    for (int c = 0; c < 3; ++c) {
+        double w0 = g->conic[0] * g->Mp[c] + g->conic[1] * g->Mp[3 + c];
+        double w1 = g->conic[2] * g->Mp[c] + g->conic[3] * g->Mp[3 + c];
+        q[c] = D[0] * w0 + D[1] * w1;
+        m += q[c] * q[c];
+    }
+    if (m > g->tau) return 0.0;
+    return g->o * exp(-0.5 * m);
+}
+
+static void pose_camera(const camera *cam, const double *delta, double Rwc[9], double t[3])
+{
+    double Rd[9], RdT[9];
+    rot_delta(delta + 3, Rd, NULL);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) RdT[3 * i + j] = Rd[3 * j + i];
+    mat3_mul(RdT, cam->R0, Rwc);
+    for (int k = 0; k < 3; ++k) t[k] = cam->t0[k] + delta[k];
+}
+
+typedef struct { double key; int idx; } keyidx;
+static int cmp_keyidx(const void *a, const void *b)
+{
+    const keyidx *x = a, *y = b;
+    if (x->key < y->key) return -1;
+    if (x->key > y->key) return 1;
+    return x->idx - y->idx;
+}
+
+/* Concrete render of the whole image at one pose.  blend = 0: BlendSort
+ * (Algorithm 2); blend = 1: BlendInd (Algorithm 4).  out is [H][W][3]. */
+int orc_render_concrete(const double *uw, const double *ls, const double *quat, const double *opac,
+                        const double *rgb, int64_t n, const double *intr, const double *R0,
+                        const double *t0, const double *delta, int blend, double *out)
+{
+    camera cam = make_camera(intr, R0, t0);
+    double Rwc[9], t[3];
+    pose_camera(&cam, delta, Rwc, t);
+    gconc *G = (gconc *)malloc(sizeof(gconc) * (size_t)(n > 0 ? n : 1));
+    double *a = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    keyidx *order = (keyidx *)malloc(sizeof(keyidx) * (size_t)(n > 0 ? n : 1));
+    if (!G || !a || !order) { free(G); free(a); free(order); return 1; }
+    for (int64_t i = 0; i < n; ++i)
+        gsplat_gaussian(&cam, Rwc, t, uw + 3 * i, ls + 3 * i, quat + 4 * i, opac[i], rgb + 3 * i, &G[i]);
+    for (int64_t i = 0; i < n; ++i) { order[i].key = G[i].d; order[i].idx = (int)i; }
+    qsort(order, (size_t)n, sizeof(keyidx), cmp_keyidx);
+    for (int py = 0; py < cam.H; ++py)
+        for (int px = 0; px < cam.W; ++px) {
+            double ux = px + 0.5, uy = py + 0.5, pc[3] = {0, 0, 0};
+            for (int64_t i = 0; i < n; ++i) a[i] = gsplat_alpha(&G[i], ux, uy);
+            if (blend == 0) {
+                /* BlendSort: as, cs sorted by depth; Ts = cumulative product of (1 - as) */
+                double Ts = 1.0;
+                for (int64_t r = 0; r < n; ++r) {
+                    int i = order[r].idx;
+                    for (int ch = 0; ch < 3; ++ch) pc[ch] += Ts * a[i] * G[i].c[ch];
+                    Ts *= 1.0 - a[i];
+                }
+            } else {
+                /* BlendInd: V[i][j] = 1 - a[j] Ind(d[i] - d[j]); T[i] = prod_j V[i][j] */
+                for (int64_t i = 0; i < n; ++i) {
+                    if (a[i] == 0.0) continue;
+                    double T = 1.0;
+                    for (int64_t j = 0; j < n; ++j)
+                        if (G[i].d - G[j].d > 0) T *= 1.0 - a[j];
+                    for (int ch = 0; ch < 3; ++ch) pc[ch] += T * a[i] * G[i].c[ch];
+                }
+            }
+            double *o = out + 3 * ((size_t)py * cam.W + px);
+            for (int ch = 0; ch < 3; ++ch) o[ch] = pc[ch] < 0 ? 0 : (pc[ch] > 1 ? 1 : pc[ch]);
+        }
+    free(G); free(a); free(order);
+    return 0;
+}
+
+/* The concrete effective opacity of one Gaussian at one pixel and pose (for tests). */
+double orc_concrete_alpha(const double *uw, const double *ls, const double *quat, double opac,
+                          const double *intr, const double *R0, const double *t0, const double *delta,
+                          double ux, double uy)
+{
+    camera cam = make_camera(intr, R0, t0);
+    double Rwc[9], t[3], rgb[3] = {0, 0, 0};
+    gconc g;
+    pose_camera(&cam, delta, Rwc, t);
+    gsplat_gaussian(&cam, Rwc, t, uw, ls, quat, opac, rgb, &g);
+    return gsplat_alpha(&g, ux, uy);
+}
+
+/* ====================================================== AbstractSplat ===== */
+
+typedef struct {
+    double ctr[NV], h[NV];
+    bs Rd[9];      /* R_delta entries as forms over the rotation variables */
+    bs s[3];       /* s = R0 * delta_t (exact) */
+    double Rc[9];  /* R_delta at the cell centre */
+} cellforms;
+
+/* Pose linearisation of one cell. */
+static void cell_setup(const camera *cam, const double *lo, const double *hi, cellforms *cf)
+{
+    for (int k = 0; k < NV; ++k) { cf->ctr[k] = 0.5 * (lo[k] + hi[k]); cf->h[k] = 0.5 * (hi[k] - lo[k]); }
+    double R[9], dR[3][9];
+    rot_delta(cf->ctr + 3, R, dR);
+    memcpy(cf->Rc, R, sizeof R);
+    double hs = cf->h[3] + cf->h[4] + cf->h[5];
+    double rem = 0.5 * hs * hs;
+    for (int e = 0; e < 9; ++e) {
+        lf f = lf_cst(R[e]);
+        for (int k = 0; k < 3; ++k) f.c[3 + k] = dR[k][e] * cf->h[3 + k];
+        cf->Rd[e].lo = f; cf->Rd[e].lo.k -= rem;
+        cf->Rd[e].hi = f; cf->Rd[e].hi.k += rem;
+    }
+    for (int a = 0; a < 3; ++a) {
+        lf f = lf_cst(0);
+        for (int k = 0; k < 3; ++k) { f.c[k] = cam->R0[3 * a + k] * cf->h[k]; f.k += cam->R0[3 * a + k] * cf->ctr[k]; }
+        cf->s[a].lo = f; cf->s[a].hi = f;
+    }
+}
+
+void orc_rot_forms(const double *lo, const double *hi, double *out /* 9 x (lo[7], hi[7]) */)
+{
+    camera cam; memset(&cam, 0, sizeof cam); cam.R0[0] = cam.R0[4] = cam.R0[8] = 1;
+    cellforms cf;
+    cell_setup(&cam, lo, hi, &cf);
+    for (int e = 0; e < 9; ++e) {
+        for (int i = 0; i < NV; ++i) { out[14 * e + i] = cf.Rd[e].lo.c[i]; out[14 * e + 7 + i] = cf.Rd[e].hi.c[i]; }
+        out[14 * e + 6] = cf.Rd[e].lo.k; out[14 * e + 13] = cf.Rd[e].hi.k;
+    }
+}
+
+/* MatrixInv (Algorithm 3) on a 2x2 matrix of bounded scalars.  Returns 0 and
+ * fills conic on success, 1 when the reference matrix is not positive
+ * definite or ||I - X X0|| >= RHO_MAX (the assertion of Algorithm 3 fails). */
+static int matrix_inv(const bs X[4], int k, bs conic[4], double *rho_out)
+{
+    double Xh[4];
+    for (int e = 0; e < 4; ++e) Xh[e] = 0.5 * (bs_min(&X[e]) + bs_max(&X[e]));
+    double det = Xh[0] * Xh[3] - Xh[1] * Xh[2];
+    if (rho_out) *rho_out = INFINITY;
+    if (!(det > 0) || !(Xh[0] > 0)) return 1;
+    /* X0 = inverse of the centre matrix (Sec. 3.1, adjustment (1)) */
+    double X0[4] = {Xh[3] / det, -Xh[1] / det, -Xh[2] / det, Xh[0] / det};
+    /* IXX0 = I - X X0 : X0 is constant, so this is an exact linear map */
+    bs E[4];
+    for (int r = 0; r < 2; ++r)
+        for (int s = 0; s < 2; ++s) {
+            bs v = bs_add(bs_scale(X[2 * r], X0[s]), bs_scale(X[2 * r + 1], X0[2 + s]));
+            E[2 * r + s] = bs_addc(bs_scale(v, -1.0), r == s ? 1.0 : 0.0);
+        }
+    /* Norm(IXX0): Frobenius norm of the entrywise magnitude bound over the cell */
+    double rho2 = 0;
+    for (int e = 0; e < 4; ++e) {
+        double m = fmax(fabs(bs_min(&E[e])), fabs(bs_max(&E[e])));
+        rho2 += m * m;
+    }
+    double rho = sqrt(rho2);
+    if (rho_out) *rho_out = rho;
+    if (!(rho < RHO_MAX)) return 1;
+    /* Sum_{i=0..k} Pow(IXX0, i) with Pow evaluated left to right */
+    bs P[4], S[4];
+    for (int e = 0; e < 4; ++e) { P[e] = E[e]; S[e] = bs_addc(E[e], (e == 0 || e == 3) ? 1.0 : 0.0); }
+    for (int i = 2; i <= k; ++i) {
+        bs Q[4];
+        for (int r = 0; r < 2; ++r)
+            for (int s = 0; s < 2; ++s)
+                Q[2 * r + s] = bs_add(bs_mul(P[2 * r], E[s]), bs_mul(P[2 * r + 1], E[2 + s]));
+        for (int e = 0; e < 4; ++e) { P[e] = Q[e]; S[e] = bs_add(S[e], Q[e]); }
+    }
+    /* Xp = X0 * Sum (X0 constant) and the remainder bound Eps */
+    double nX0 = sqrt(X0[0] * X0[0] + X0[1] * X0[1] + X0[2] * X0[2] + X0[3] * X0[3]);
+    double eps = nX0 * pow(rho, k + 1) / (1.0 - rho);
+    for (int r = 0; r < 2; ++r)
+        for (int s = 0; s < 2; ++s) {
+            bs v = bs_add(bs_scale(S[s], X0[2 * r]), bs_scale(S[2 + s], X0[2 * r + 1]));
+            v.lo.k -= eps; v.hi.k += eps;
+            conic[2 * r + s] = v;
+        }
+    return 0;
+}
+
+/* Interval-matrix entry point for the pins: the four entries of X are
+ * independent, entry e = mid_e + half_e * p_e (symmetric != 0: entries 1 and
+ * 2 are the same variable, so Xl/Xu must agree there).  Returns the concretised
+ * bounds of MatrixInv's output. */
+int orc_matrixinv_interval(const double *Xl, const double *Xu, int k, int symmetric,
+                           double *out_l, double *out_u, double *rho)
+{
+    bs X[4], C[4];
+    for (int e = 0; e < 4; ++e) {
+        lf f = lf_cst(0.5 * (Xl[e] + Xu[e]));
+        f.c[(symmetric && e == 2) ? 1 : e] = 0.5 * (Xu[e] - Xl[e]);
+        X[e].lo = f; X[e].hi = f;
+    }
+    int st = matrix_inv(X, k, C, rho);
+    if (st) return st;
+    for (int e = 0; e < 4; ++e) { out_l[e] = bs_min(&C[e]); out_u[e] = bs_max(&C[e]); }
+    return 0;
+}
+
+/* Primitive relaxations on raw forms, for the pins.  Each form is 7 doubles
+ * (6 coefficients, then the constant); a bounded scalar is lo form, hi form. */
+static bs unpack_bs(const double *v)
+{
+    bs b;
+    for (int i = 0; i < NV; ++i) { b.lo.c[i] = v[i]; b.hi.c[i] = v[7 + i]; }
+    b.lo.k = v[6]; b.hi.k = v[13];
+    return b;
+}
+static void pack_bs(const bs *b, double *v)
+{
+    for (int i = 0; i < NV; ++i) { v[i] = b->lo.c[i]; v[7 + i] = b->hi.c[i]; }
+    v[6] = b->lo.k; v[13] = b->hi.k;
+}
+void orc_relax_mul(const double *x, const double *y, double *out) { bs r = bs_mul(unpack_bs(x), unpack_bs(y)); pack_bs(&r, out); }
+void orc_relax_sq(const double *x, double *out) { bs r = bs_sq(unpack_bs(x)); pack_bs(&r, out); }
+
+/* Per-(Gaussian, cell) record of the abstract pipeline (steps of Algorithm 1
+ * up to W = Conic * Mp). */
+typedef struct {
+    int valid;          /* contributes somewhere in the image */
+    int straddle;       /* depth interval straddles the near plane */
+    int fallback;       /* MatrixInv assertion failed: a in [0, o] on the box */
+    double rho;         /* ||I - X X0|| bound (INFINITY if X0 undefined) */
+    double klo, khi;    /* depth-key interval */
+    int px0, px1, py0, py1;  /* pixel box whose centres may see the Gaussian */
+    bs S, Px, Py;       /* S = d^2, P = d * up */
+    bs W[6];            /* W = Conic * Mp, row-major 2x3 */
+    double o, tau, c[3];
+} grec;
+
+/* Interval helpers for the screen box (sound enclosures, no correlation). */
+typedef struct { double l, u; } ival;
+static ival iv_mul(ival a, ival b)
+{
+    double p[4] = {a.l * b.l, a.l * b.u, a.u * b.l, a.u * b.u};
+    ival r = {p[0], p[0]};
+    for (int i = 1; i < 4; ++i) { r.l = fmin(r.l, p[i]); r.u = fmax(r.u, p[i]); }
+    return r;
+}
+static ival iv_scale(ival a, double s) { ival r = s >= 0 ? (ival){s * a.l, s * a.u} : (ival){s * a.u, s * a.l}; return r; }
+static ival iv_add(ival a, ival b) { ival r = {a.l + b.l, a.u + b.u}; return r; }
+static double iv_sqmax(ival a) { return fmax(a.l * a.l, a.u * a.u); }
+
+static void gaussian_record(const camera *cam, const cellforms *cf, const double *uw, const double *ls,
+                            const double *q, double o, const double *rgb, grec *g)
+{
+    memset(g, 0, sizeof *g);
+    g->o = o;
+    g->tau = (o > 0) ? 2.0 * log(255.0 * o) : -INFINITY;
+    for (int k = 0; k < 3; ++k) g->c[k] = rgb[k];
+    g->rho = INFINITY;
+    if (!(g->tau >= 0)) return;   /* o < 1/255: never reaches the cutoff */
+
+    /* a1: nominal camera-frame mean v = R0 (uw - t0) and N = R0 Mw */
+    double Mw[9], N[9], v[3];
+    cov_factor(ls, q, Mw);
+    mat3_mul(cam->R0, Mw, N);
+    for (int a = 0; a < 3; ++a) {
+        v[a] = 0;
+        for (int b = 0; b < 3; ++b) v[a] += cam->R0[3 * a + b] * (uw[b] - cam->t0[b]);
+    }
+    /* Algorithm 1, line 2: uc = R_delta^T (v - s) */
+    bs vms[3], uc[3];
+    for (int b = 0; b < 3; ++b) vms[b] = bs_sub(bs_cst(v[b]), cf->s[b]);
+    for (int a = 0; a < 3; ++a) {
+        uc[a] = bs_mul(cf->Rd[a], vms[0]);   /* R_delta[0][a] */
+        uc[a] = bs_add(uc[a], bs_mul(cf->Rd[3 + a], vms[1]));
+        uc[a] = bs_add(uc[a], bs_mul(cf->Rd[6 + a], vms[2]));
+    }
+    bs d = uc[2];                                  /* line 7 */
+    double dlo = bs_min(&d), dhi = bs_max(&d);
+    if (!(dhi > cam->near_plane)) return;          /* entirely at or behind the near plane */
+    g->straddle = !(dlo > cam->near_plane);
+
+    /* depth key: d minus the translation-only linear term shared by all Gaussians */
+    lf gk = lf_cst(0);
+    for (int k = 0; k < 3; ++k) {
+        double s = 0;
+        for (int b = 0; b < 3; ++b) s += cf->Rc[3 * b + 2] * cam->R0[3 * b + k];
+        gk.c[k] = -s * cf->h[k];
+    }
+    lf kl = lf_sub(&d.lo, &gk), kh = lf_sub(&d.hi, &gk);
+    g->klo = lf_min(&kl); g->khi = lf_max(&kh);
+    double kpad = KEY_SLACK * (1.0 + fmax(fabs(g->klo), fabs(g->khi)));
+    g->klo -= kpad; g->khi += kpad;
+
+    /* line 5: up = K uc */
+    bs up0 = bs_add(bs_scale(uc[0], cam->fx), bs_scale(uc[2], cam->cx));
+    bs up1 = bs_add(bs_scale(uc[1], cam->fy), bs_scale(uc[2], cam->cy));
+    /* line 3: Mc = R_delta^T N  (N constant) */
+    bs Mc[9];
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) {
+            bs s = bs_scale(cf->Rd[a], N[c]);
+            s = bs_add(s, bs_scale(cf->Rd[3 + a], N[3 + c]));
+            s = bs_add(s, bs_scale(cf->Rd[6 + a], N[6 + c]));
+            Mc[3 * a + c] = s;
+        }
+
+    /* screen box: centres of pixels that can lie in the ellipse m <= tau for
+     * some pose of the cell with d > near (interval arithmetic, FP64) */
+    {
+        double dl = fmax(dlo, cam->near_plane);
+        ival D = {dl, dhi};
+        ival U0 = {bs_min(&up0), bs_max(&up0)}, U1 = {bs_min(&up1), bs_max(&up1)};
+        ival ucx = {bs_min(&uc[0]), bs_max(&uc[0])}, ucy = {bs_min(&uc[1]), bs_max(&uc[1])};
+        ival mux = {fmin(U0.l / D.l, U0.l / D.u), fmax(U0.u / D.l, U0.u / D.u)};
+        ival muy = {fmin(U1.l / D.l, U1.l / D.u), fmax(U1.u / D.l, U1.u / D.u)};
+        double X00 = 0, X11 = 0;
+        for (int c = 0; c < 3; ++c) {
+            ival m0 = {bs_min(&Mc[c]), bs_max(&Mc[c])}, m1 = {bs_min(&Mc[3 + c]), bs_max(&Mc[3 + c])};
+            ival m2 = {bs_min(&Mc[6 + c]), bs_max(&Mc[6 + c])};
+            ival p0 = iv_scale(iv_add(iv_mul(D, m0), iv_scale(iv_mul(ucx, m2), -1.0)), cam->fx);
+            ival p1 = iv_scale(iv_add(iv_mul(D, m1), iv_scale(iv_mul(ucy, m2), -1.0)), cam->fy);
+            X00 += iv_sqmax(p0); X11 += iv_sqmax(p1);
+        }
+        double rx = sqrt(g->tau * X00) / (dl * dl), ry = sqrt(g->tau * X11) / (dl * dl);
+        double xl = mux.l - rx, xh = mux.u + rx, yl = muy.l - ry, yh = muy.u + ry;
+        xl -= BOX_SLACK * (1 + fabs(xl)); xh += BOX_SLACK * (1 + fabs(xh));
+        yl -= BOX_SLACK * (1 + fabs(yl)); yh += BOX_SLACK * (1 + fabs(yh));
+        if (!(xh >= xl) || !(yh >= yl)) return;      /* NaN guard */
+        double fx0 = ceil(xl - 0.5), fx1 = floor(xh - 0.5), fy0 = ceil(yl - 0.5), fy1 = floor(yh - 0.5);
+        fx0 = fmax(fx0, 0); fy0 = fmax(fy0, 0);
+        fx1 = fmin(fx1, cam->W - 1); fy1 = fmin(fy1, cam->H - 1);
+        if (fx0 > fx1 || fy0 > fy1) return;
+        g->px0 = (int)fx0; g->px1 = (int)fx1; g->py0 = (int)fy0; g->py1 = (int)fy1;
+    }
+    g->valid = 1;
+
+    /* line 4 and 6: J and Mp = J Mc (J entries are forms; products by Mul) */
+    bs J00 = bs_scale(d, cam->fx), J02 = bs_scale(uc[0], -cam->fx);
+    bs J11 = bs_scale(d, cam->fy), J12 = bs_scale(uc[1], -cam->fy);
+    bs Mp[6];
+    for (int c = 0; c < 3; ++c) {
+        Mp[c] = bs_add(bs_mul(J00, Mc[c]), bs_mul(J02, Mc[6 + c]));
+        Mp[3 + c] = bs_add(bs_mul(J11, Mc[3 + c]), bs_mul(J12, Mc[6 + c]));
+    }
+    /* line 8 argument: X = Mp Mp^T (squares on the diagonal) */
+    bs X[4];
+    X[0] = bs_add(bs_add(bs_sq(Mp[0]), bs_sq(Mp[1])), bs_sq(Mp[2]));
+    X[3] = bs_add(bs_add(bs_sq(Mp[3]), bs_sq(Mp[4])), bs_sq(Mp[5]));
+    X[1] = bs_add(bs_add(bs_mul(Mp[0], Mp[3]), bs_mul(Mp[1], Mp[4])), bs_mul(Mp[2], Mp[5]));
+    X[2] = X[1];
+    /* line 9 factors: S = d*d, P = d*up */
+    g->S = bs_sq(d);
+    g->Px = bs_mul(d, up0);
+    g->Py = bs_mul(d, up1);
+    /* line 8: Conic <- MatrixInv(X; X0, k) */
+    bs conic[4];
+    if (matrix_inv(X, KTAYLOR, conic, &g->rho)) { g->fallback = 1; return; }
+    /* W = Conic * Mp, so that q = Delta^T W */
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 3; ++c)
+            g->W[3 * r + c] = bs_add(bs_mul(conic[2 * r], Mp[c]), bs_mul(conic[2 * r + 1], Mp[3 + c]));
+}
+
+static double clamp01(double x) { return x < 0 ? 0 : (x > 1 ? 1 : x); }
+
+/* Effective-opacity bounds of one Gaussian at one pixel (Algorithm 1 lines
+ * 9-10 relaxed).  Produces lower/upper forms and their scalar enclosure. */
+typedef struct { lf L, U; double alo, ahi; double mlo, mhi, ramp; } galpha;
+
+static void gaussian_alpha(const grec *g, double ux, double uy, galpha *r)
+{
+    if (g->fallback) {
+        r->L = lf_cst(0); r->U = lf_cst(g->o); r->alo = 0; r->ahi = g->o;
+        r->mlo = -INFINITY; r->mhi = INFINITY; r->ramp = 0;
+        return;
+    }
+    /* Delta = d^2 u - d up = S u - P (u constant) */
+    bs Dx = bs_sub(bs_scale(g->S, ux), g->Px);
+    bs Dy = bs_sub(bs_scale(g->S, uy), g->Py);
+    /* q = Delta^T W ; m = q q^T */
+    bs m = bs_cst(0);
+    for (int c = 0; c < 3; ++c) {
+        bs qc = bs_add(bs_mul(Dx, g->W[c]), bs_mul(Dy, g->W[3 + c]));
+        m = bs_add(m, bs_sq(qc));
+    }
+    double mlo = bs_min(&m), mhi = bs_max(&m);
+    r->mlo = mlo; r->mhi = mhi;
+    /* Exp on x = -m/2 in [xl, xu], xu clipped at 0 since m >= 0 */
+    double xl = -0.5 * mhi, xu = fmin(-0.5 * mlo, 0.0);
+    if (xu < xl) xu = xl;
+    double El = exp(xl);
+    double slope = (xu > xl) ? (exp(xu) - El) / (xu - xl) : El;
+    /* lower: El (1 + x - xl) with x >= -m.hi/2 ; upper: El + slope (x - xl) with x <= -m.lo/2 */
+    lf Le = lf_scale(&m.hi, -0.5 * El); Le.k += El * (1.0 - xl);
+    lf Ue = lf_scale(&m.lo, -0.5 * slope); Ue.k += El - slope * xl;
+    lf La = lf_scale(&Le, g->o), Ua = lf_scale(&Ue, g->o);
+    /* upper side: blend toward the constant o when the form's maximum exceeds o */
+    double amax = lf_max(&Ua);
+    double lam = clamp01((g->o * (1.0 + CLIP_RAMP) - amax) / (g->o * CLIP_RAMP));
+    lf U1 = lf_scale(&Ua, lam); U1.k += (1.0 - lam) * g->o;
+    /* cutoff ramps: width shrinks with the m interval, zero on a point cell */
+    double ramp = fmin(CUT_RAMP, mhi - mlo);
+    if (!(ramp > 0)) ramp = 0;
+    r->ramp = ramp;
+    double psi2 = (mlo <= g->tau) ? 0.0 : (ramp > 0 ? clamp01((mlo - g->tau) / ramp) : 1.0);
+    double psi = (mhi > g->tau) ? 1.0 : (ramp > 0 ? clamp01((mhi - g->tau + ramp) / ramp) : 0.0);
+    r->U = lf_scale(&U1, 1.0 - psi2);
+    lf L2 = La; L2.k -= psi * ALPHA_MIN;
+    double l2min = lf_min(&L2), l2max = lf_max(&L2);
+    double mu = (l2min >= 0) ? 1.0 : ((l2max <= 0) ? 0.0 : l2max / (l2max - l2min));
+    r->L = lf_scale(&L2, mu);
+    if (g->straddle) r->L = lf_cst(0);
+    r->alo = fmax(0.0, lf_min(&r->L));
+    r->ahi = fmin(g->o, lf_max(&r->U));
+}
+
+/* Abstract render of one cell over the pixel window [px0,px1] x [py0,py1].
+ * out_lo/out_hi are [H][W][3] (only the window is written).  fragile, if
+ * given, is [H][W] and marks pixels where a threshold decision that the FP32
+ * path takes in single precision lies within a relative 1e-3 of its
+ * threshold (both outcomes are sound there). */
+int orc_render_abstract(const double *uw, const double *ls, const double *quat, const double *opac,
+                        const double *rgb, int64_t n, const double *intr, const double *R0,
+                        const double *t0, const double *cell_lo, const double *cell_hi,
+                        int px0, int px1, int py0, int py1, double *out_lo, double *out_hi,
+                        uint8_t *fragile)
+{
+    camera cam = make_camera(intr, R0, t0);
+    cellforms cf;
+    cell_setup(&cam, cell_lo, cell_hi, &cf);
+    grec *G = (grec *)malloc(sizeof(grec) * (size_t)(n > 0 ? n : 1));
+    if (!G) return 1;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i)
+        gaussian_record(&cam, &cf, uw + 3 * i, ls + 3 * i, quat + 4 * i, opac[i], rgb + 3 * i, &G[i]);
+
+    int npx = px1 - px0 + 1, npy = py1 - py0 + 1;
+    int status = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int pix = 0; pix < npx * npy; ++pix) {
+        int px = px0 + pix % npx, py = py0 + pix / npx;
+        double ux = px + 0.5, uy = py + 0.5;
+        int64_t cap = 256, K = 0;
+        int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * cap);
+        galpha *A = (galpha *)malloc(sizeof(galpha) * cap);
+        int frag = 0;
+        if (!idx || !A) { status = 1; free(idx); free(A); continue; }
+        for (int64_t i = 0; i < n; ++i) {
+            const grec *g = &G[i];
+            if (!g->valid || px < g->px0 || px > g->px1 || py < g->py0 || py > g->py1) continue;
+            if (K == cap) {
+                cap *= 2;
+                idx = (int64_t *)realloc(idx, sizeof(int64_t) * cap);
+                A = (galpha *)realloc(A, sizeof(galpha) * cap);
+                if (!idx || !A) { status = 1; break; }
+            }
+            idx[K] = i;
+            gaussian_alpha(g, ux, uy, &A[K]);
+            /* threshold decisions the FP32 path takes in single precision */
+            if (fabs(g->rho - RHO_MAX) < 1e-3) frag = 1;
+            if (!g->fallback && A[K].ramp < 0.05) {
+                /* a narrow ramp makes the cutoff nearly a step in m */
+                double tol = 1e-3 * fmax(1.0, g->tau), rp = A[K].ramp;
+                if (A[K].mhi > g->tau - rp - tol && A[K].mhi < g->tau + tol) frag = 1;
+                if (A[K].mlo > g->tau - tol && A[K].mlo < g->tau + rp + tol) frag = 1;
+            }
+            ++K;
+        }
+        if (!idx || !A) { free(idx); free(A); continue; }
+        /* BlendInd with interval Prod: for each i, T_lo over j that may be in
+         * front (not certainly behind), T_hi over j certainly in front */
+        lf lo[3], hi[3];
+        for (int ch = 0; ch < 3; ++ch) { lo[ch] = lf_cst(0); hi[ch] = lf_cst(0); }
+        for (int64_t a = 0; a < K; ++a) {
+            const grec *gi = &G[idx[a]];
+            double Tlo = 1.0, Thi = 1.0;
+            for (int64_t b = 0; b < K; ++b) {
+                if (b == a) continue;
+                const grec *gj = &G[idx[b]];
+                if (gj->khi < gi->klo) {               /* Ind(d_i - d_j) = 1 on the whole cell */
+                    Tlo *= 1.0 - A[b].ahi;
+                    Thi *= 1.0 - A[b].alo;
+                } else if (gj->klo < gi->khi) {        /* Ind(d_i - d_j) in {0, 1} */
+                    Tlo *= 1.0 - A[b].ahi;
+                }                                      /* else Ind(d_i - d_j) = 0 */
+            }
+            for (int ch = 0; ch < 3; ++ch) {
+                lf t = lf_scale(&A[a].L, Tlo * gi->c[ch]);
+                lo[ch] = lf_add(&lo[ch], &t);
+                t = lf_scale(&A[a].U, Thi * gi->c[ch]);
+                hi[ch] = lf_add(&hi[ch], &t);
+            }
+        }
+        size_t o = 3 * ((size_t)py * cam.W + px);
+        for (int ch = 0; ch < 3; ++ch) {
+            out_lo[o + ch] = clamp01(lf_min(&lo[ch]));
+            out_hi[o + ch] = clamp01(lf_max(&hi[ch]));
+        }
+        if (fragile) fragile[(size_t)py * cam.W + px] = (uint8_t)frag;
+        free(idx); free(A);
+    }
+    free(G);
+    return status;
+}
+
+/* Per-Gaussian record summary for one cell (for tests): valid, straddle,
+ * fallback, klo, khi, px0, px1, py0, py1, rho -> 10 doubles per Gaussian. */
+int orc_records(const double *uw, const double *ls, const double *quat, const double *opac,
+                const double *rgb, int64_t n, const double *intr, const double *R0, const double *t0,
+                const double *cell_lo, const double *cell_hi, double *out)
+{
+    camera cam = make_camera(intr, R0, t0);
+    cellforms cf;
+    cell_setup(&cam, cell_lo, cell_hi, &cf);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i) {
+        grec g;
+        gaussian_record(&cam, &cf, uw + 3 * i, ls + 3 * i, quat + 4 * i, opac[i], rgb + 3 * i, &g);
+        double *o = out + 10 * i;
+        o[0] = g.valid; o[1] = g.straddle; o[2] = g.fallback; o[3] = g.klo; o[4] = g.khi;
+        o[5] = g.px0; o[6] = g.px1; o[7] = g.py0; o[8] = g.py1; o[9] = g.rho;
+    }
+    return 0;
+}
+
+/* Thread count for the OpenMP loops (returns the count in effect). */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
+/* Soundness harness: renders the scene at each of npose poses (BlendSort) and
+ * compares with the bounds lo/hi ([H][W][3]).  Returns the largest violation
+ * max(lo - img, img - hi, 0) and writes the number of violating values. */
+double orc_check_samples(const double *uw, const double *ls, const double *quat, const double *opac,
+                         const double *rgb, int64_t n, const double *intr, const double *R0,
+                         const double *t0, const double *poses, int64_t npose, const double *lo,
+                         const double *hi, double tol, int64_t *nviol)
+{
+    camera cam = make_camera(intr, R0, t0);
+    size_t npix = (size_t)cam.W * cam.H * 3;
+    double worst = 0;
+    int64_t count = 0;
+#pragma omp parallel
+    {
+        double *img = (double *)malloc(sizeof(double) * npix);
+        double w_local = 0;
+        int64_t c_local = 0;
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t p = 0; p < npose; ++p) {
+            if (!img) continue;
+            orc_render_concrete(uw, ls, quat, opac, rgb, n, intr, R0, t0, poses + 6 * p, 0, img);
+            for (size_t e = 0; e < npix; ++e) {
+                double v = fmax(lo[e] - img[e], img[e] - hi[e]);
+                if (v > tol) ++c_local;
+                if (v > w_local) w_local = v;
+            }
+        }
+#pragma omp critical
+        {
+            if (w_local > worst) worst = w_local;
+            count += c_local;
+        }
+        free(img);
+    }
+    if (nviol) *nviol = count;
+    return worst;
+}
+
+/* Per-pixel range of the concrete renders over npose poses (the paper's
+ * "empirical" bounds of Sec. 4.2): emp_lo/emp_hi are [H][W][3]. */
+void orc_empirical_bounds(const double *uw, const double *ls, const double *quat, const double *opac,
+                          const double *rgb, int64_t n, const double *intr, const double *R0,
+                          const double *t0, const double *poses, int64_t npose, double *emp_lo,
+                          double *emp_hi)
+{
+    camera cam = make_camera(intr, R0, t0);
+    size_t npix = (size_t)cam.W * cam.H * 3;
+    for (size_t e = 0; e < npix; ++e) { emp_lo[e] = INFINITY; emp_hi[e] = -INFINITY; }
+#pragma omp parallel
+    {
+        double *img = (double *)malloc(sizeof(double) * npix);
+        double *l = (double *)malloc(sizeof(double) * npix), *h = (double *)malloc(sizeof(double) * npix);
+        if (l && h)
+            for (size_t e = 0; e < npix; ++e) { l[e] = INFINITY; h[e] = -INFINITY; }
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t p = 0; p < npose; ++p) {
+            if (!img || !l || !h) continue;
+            orc_render_concrete(uw, ls, quat, opac, rgb, n, intr, R0, t0, poses + 6 * p, 0, img);
+            for (size_t e = 0; e < npix; ++e) { l[e] = fmin(l[e], img[e]); h[e] = fmax(h[e], img[e]); }
+        }
+#pragma omp critical
+        {
+            if (l && h)
+                for (size_t e = 0; e < npix; ++e) { emp_lo[e] = fmin(emp_lo[e], l[e]); emp_hi[e] = fmax(emp_hi[e], h[e]); }
+        }
+        free(img); free(l); free(h);
+    }
+}

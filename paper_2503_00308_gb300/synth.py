@@ -1,0 +1,204 @@
+"""Seeded synthetic inputs: Gaussian-splat scenes, pinhole cameras and pose-cell grids.
+
+This module only draws random numbers and lays out arrays.  It holds none of
+the abstract-rendering arithmetic, so both the CUDA path and the CPU oracle can
+be fed from it without sharing any of the method's code.
+
+Scene records follow the paper's Gaussian tuple <uw, Mw, o, c> (Sec. 2.2): the
+covariance factor Mw is carried as a log-scale vector and a unit quaternion
+(w, x, y, z); colours are degree-0 RGB.  Cameras use the OpenCV frame (x right,
+y down, z forward); a nominal pose is a world->camera rotation R_wc and the
+camera centre t in world coordinates.  A pose cell is a box over
+delta = (tx, ty, tz, rx, ry, rz): a world-frame translation of the camera
+centre and XYZ Euler angles of a rotation applied in the camera frame.
+
+The named workloads mirror the synthetic scenes the paper's trained scenes
+(Table 3) are replaced by: a tiny 64-Gaussian check scene, a 10k-Gaussian
+object, the same object at 300k Gaussians and 800x800, and a 750k-Gaussian
+unbounded scene.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Scene:
+    uw: np.ndarray        # (n, 3) float32 means, world frame
+    logscale: np.ndarray  # (n, 3) float32 log of the per-axis scales
+    quat: np.ndarray      # (n, 4) float32 unit quaternions (w, x, y, z)
+    opacity: np.ndarray   # (n,)   float32 in (0, 1)
+    rgb: np.ndarray       # (n, 3) float32 in [0, 1]
+
+    @property
+    def n(self) -> int:
+        return int(self.uw.shape[0])
+
+    def subset(self, idx) -> "Scene":
+        return Scene(self.uw[idx].copy(), self.logscale[idx].copy(), self.quat[idx].copy(),
+                     self.opacity[idx].copy(), self.rgb[idx].copy())
+
+
+@dataclasses.dataclass
+class Camera:
+    width: int
+    height: int
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    near: float
+    R_wc: np.ndarray      # (3, 3) float64 world -> camera rotation
+    t: np.ndarray         # (3,) float64 camera centre in world coordinates
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    scene: Scene
+    camera: Camera
+    cells_lo: np.ndarray  # (n_cells, 6) float64
+    cells_hi: np.ndarray  # (n_cells, 6) float64
+
+    @property
+    def n_cells(self) -> int:
+        return int(self.cells_lo.shape[0])
+
+    def pixel_cells(self) -> int:
+        return self.camera.width * self.camera.height * self.n_cells
+
+
+def _sigmoid(x):
+    return 1.0 / (1.0 + np.exp(-x))
+
+
+def _unit_quats(rng, n):
+    q = rng.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    return q
+
+
+def object_scene(n: int, seed: int, mean_sd: float = 0.5, logscale_mu: float = -4.0,
+                 logscale_sd: float = 0.5, opacity_mu: float = 0.0) -> Scene:
+    """Object-centred scene: means N(0, mean_sd^2 I), log-scales N(mu, sd), random
+    rotations, opacity sigmoid(N(opacity_mu, 1)), RGB uniform [0, 1]."""
+    rng = np.random.default_rng(seed)
+    uw = rng.normal(scale=mean_sd, size=(n, 3))
+    ls = rng.normal(loc=logscale_mu, scale=logscale_sd, size=(n, 3))
+    q = _unit_quats(rng, n)
+    o = _sigmoid(rng.normal(loc=opacity_mu, size=n))
+    c = rng.uniform(size=(n, 3))
+    return Scene(uw.astype(np.float32), ls.astype(np.float32), q.astype(np.float32),
+                 o.astype(np.float32), c.astype(np.float32))
+
+
+def cube_scene(n: int, seed: int, half: float = 0.5, logscale_mu: float = -2.5,
+               logscale_sd: float = 0.3) -> Scene:
+    """Means uniform in [-half, half]^3 (the tiny check scene)."""
+    rng = np.random.default_rng(seed)
+    uw = rng.uniform(-half, half, size=(n, 3))
+    ls = rng.normal(loc=logscale_mu, scale=logscale_sd, size=(n, 3))
+    q = _unit_quats(rng, n)
+    o = _sigmoid(rng.normal(size=n))
+    c = rng.uniform(size=(n, 3))
+    return Scene(uw.astype(np.float32), ls.astype(np.float32), q.astype(np.float32),
+                 o.astype(np.float32), c.astype(np.float32))
+
+
+def box_scene(n: int, seed: int, extent=(20.0, 5.0, 20.0), logscale_mu: float = -3.0,
+              logscale_sd: float = 0.7, opacity_mu: float = 0.5) -> Scene:
+    """Unbounded scene: means uniform in an axis box centred on the origin (y is up/down)."""
+    rng = np.random.default_rng(seed)
+    ext = np.asarray(extent, dtype=np.float64)
+    uw = rng.uniform(-0.5, 0.5, size=(n, 3)) * ext
+    ls = rng.normal(loc=logscale_mu, scale=logscale_sd, size=(n, 3))
+    q = _unit_quats(rng, n)
+    o = _sigmoid(rng.normal(loc=opacity_mu, size=n))
+    c = rng.uniform(size=(n, 3))
+    return Scene(uw.astype(np.float32), ls.astype(np.float32), q.astype(np.float32),
+                 o.astype(np.float32), c.astype(np.float32))
+
+
+def look_camera(width: int, height: int, f: float, centre=(0.0, 0.0, -4.0), near: float = 0.2) -> Camera:
+    """Pinhole camera with identity orientation (looking along +z) at `centre`."""
+    return Camera(width, height, float(f), float(f), width / 2.0, height / 2.0, near,
+                  np.eye(3, dtype=np.float64), np.asarray(centre, dtype=np.float64))
+
+
+def cell_grid(halfwidth, splits) -> tuple[np.ndarray, np.ndarray]:
+    """Uniform split of the box prod_k [-halfwidth_k, halfwidth_k] into prod_k splits_k cells.
+
+    halfwidth and splits are length-6 sequences over (tx, ty, tz, rx, ry, rz);
+    translations in metres, rotations in radians.  Cells are enumerated with
+    the last dimension fastest."""
+    hw = np.asarray(halfwidth, dtype=np.float64)
+    sp = np.asarray(splits, dtype=np.int64)
+    assert hw.shape == (6,) and sp.shape == (6,) and np.all(sp >= 1)
+    edges = [np.linspace(-hw[k], hw[k], sp[k] + 1) for k in range(6)]
+    idx = np.stack(np.meshgrid(*[np.arange(s) for s in sp], indexing="ij"), axis=-1).reshape(-1, 6)
+    lo = np.empty(idx.shape, dtype=np.float64)
+    hi = np.empty(idx.shape, dtype=np.float64)
+    for k in range(6):
+        lo[:, k] = edges[k][idx[:, k]]
+        hi[:, k] = edges[k][idx[:, k] + 1]
+    return lo, hi
+
+
+def sample_poses(rng, lo, hi, n) -> np.ndarray:
+    """n poses drawn uniformly from the cell [lo, hi] (shape (n, 6))."""
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    return lo + (hi - lo) * rng.uniform(size=(n, 6))
+
+
+DEG = math.pi / 180.0
+
+
+def tiny64(seed: int = 0) -> Workload:
+    """64 Gaussians in [-0.5, 0.5]^3, 32x32 image, f = 32, camera at z = -3,
+    x-translation +-0.01 m as one cell."""
+    sc = cube_scene(64, seed)
+    cam = look_camera(32, 32, 32.0, centre=(0.0, 0.0, -3.0))
+    lo, hi = cell_grid([0.01, 0, 0, 0, 0, 0], [1] * 6)
+    return Workload("tiny64", sc, cam, lo, hi)
+
+
+def object10k(seed: int = 0, n: int = 10_000, width: int = 200, height: int = 200,
+              f: float = 220.0, splits=(2, 2, 2, 1, 2, 1)) -> Workload:
+    """10k-Gaussian object, 200x200, f = 220, camera at distance 4; pose box
+    +-5 cm translation x +-1 deg yaw split 2x2x2x2 = 16 cells."""
+    sc = object_scene(n, seed)
+    cam = look_camera(width, height, f, centre=(0.0, 0.0, -4.0))
+    lo, hi = cell_grid([0.05, 0.05, 0.05, 0.0, 1.0 * DEG, 0.0], splits)
+    return Workload("object10k", sc, cam, lo, hi)
+
+
+def object300k(seed: int = 0, n: int = 300_000, width: int = 800, height: int = 800,
+               f: float = 1100.0, splits=(2, 2, 2, 2, 2, 2)) -> Workload:
+    """The object scene at 300k Gaussians, 800x800, f = 1100, camera at distance 4;
+    full 6-DoF box +-2 cm / +-0.5 deg split 2^6 = 64 cells."""
+    sc = object_scene(n, seed)
+    cam = look_camera(width, height, f, centre=(0.0, 0.0, -4.0))
+    lo, hi = cell_grid([0.02, 0.02, 0.02, 0.5 * DEG, 0.5 * DEG, 0.5 * DEG], splits)
+    return Workload("object300k", sc, cam, lo, hi)
+
+
+def unbounded750k(seed: int = 0, n: int = 750_000, width: int = 1280, height: int = 720,
+                  f: float = 900.0, splits=(4, 2, 4, 2, 2, 2)) -> Workload:
+    """750k Gaussians in a 20 x 5 x 20 m box, camera at the origin looking +z,
+    1280x720, f = 900; +-10 cm / +-2 deg split into 256 cells."""
+    sc = box_scene(n, seed)
+    cam = look_camera(width, height, f, centre=(0.0, 0.0, 0.0))
+    lo, hi = cell_grid([0.10, 0.10, 0.10, 2 * DEG, 2 * DEG, 2 * DEG], splits)
+    return Workload("unbounded750k", sc, cam, lo, hi)
+
+
+WORKLOADS = {
+    "tiny64": tiny64,
+    "object10k": object10k,
+    "object300k": object300k,
+    "unbounded750k": unbounded750k,
+}
