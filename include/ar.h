@@ -1,0 +1,179 @@
+/*
+ * ar.h -- C ABI of the GB300 abstract-rendering library (libar).
+ *
+ * Abstract rendering of Gaussian-splat scenes (Li, Ji, Zhong, Zhang, Mitra,
+ * arXiv 2503.00308): for a scene, a nominal camera and a box of camera poses
+ * split into cells, compute for every cell and pixel a lower and an upper RGB
+ * bound that contain the colour GSplat (Algorithm 1) renders at EVERY pose of
+ * the cell -- the abstract rendering problem stated at the end of Sec. 2.2 --
+ * by the AbstractSplat construction of Sec. 3.3: linear bounds over the pose
+ * variables pushed through Algorithm 1, MatrixInv (Algorithm 3) for the conic,
+ * and BlendInd (Algorithm 4) for the blend.
+ *
+ * Conventions shared by every entry point
+ *   - Status: every call returns AR_OK (0) or one of the AR_E* codes below and
+ *     never throws across the boundary; ar_last_error() gives the message of
+ *     the calling thread's last failure.
+ *   - Camera frame: OpenCV (x right, y down, z forward).  A nominal pose is a
+ *     world->camera rotation R_wc (row-major 3x3) and the camera centre t in
+ *     world coordinates, so a world point X maps to R_wc (X - t).
+ *   - Pose cells: a box over delta = (tx, ty, tz, rx, ry, rz).  (tx, ty, tz) is
+ *     a world-frame offset of the camera centre (metres); (rx, ry, rz) are XYZ
+ *     Euler angles (radians) of a rotation R_d = Rx(rx) Ry(ry) Rz(rz) applied in
+ *     the camera frame, so the perturbed camera has R_wc' = R_d^T R_wc and
+ *     t' = t + (tx, ty, tz).  lo[k] <= hi[k]; lo == hi (a point) is legal.
+ *   - Pixels: centre of pixel (px, py) is (px + 0.5, py + 0.5); outputs are
+ *     row-major [n_cells][height][width][3] float32 in [0, 1].
+ *   - Rendering semantics bounded (Algorithm 1 with the usual splatting
+ *     conventions that the paper leaves open): Gaussians with depth <= near_plane
+ *     are dropped, effective opacities below 1/255 are zero, the background is
+ *     black, colours are degree-0 RGB, the blend is BlendInd/BlendSort.
+ *   - Soundness: for every pose in cell c, pixel p and channel k,
+ *       out_lower[c][p][k] <= GSplat(scene, pose, p)[k] <= out_upper[c][p][k].
+ *   - Streams: `cuda_stream` is a cudaStream_t (NULL = legacy default stream).
+ *     Device outputs are written asynchronously on that stream.
+ *   - Threads: one ar_scene must not be used by two threads at the same time.
+ */
+#ifndef AR_H
+#define AR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AR_OK 0
+#define AR_EINVAL 1    /* bad argument: null pointer, size, NaN, lo > hi, ... */
+#define AR_ENOMEM 2    /* device or host allocation failed / over the budget */
+#define AR_EAGAIN 3    /* serving: admission refused (queue or memory full) */
+#define AR_ETIMEOUT 4  /* serving: a bounded wait ran out */
+#define AR_EDEVICE 5   /* CUDA error (message from the runtime) */
+
+typedef struct ar_intrinsics {
+    int32_t width, height;      /* image size in pixels, 1..16384 each */
+    float fx, fy, cx, cy;       /* pinhole K = [[fx, 0, cx], [0, fy, cy]] (Sec. 2.2) */
+    float near_plane;           /* depth below which Gaussians are dropped, > 0 */
+} ar_intrinsics;
+
+typedef struct ar_nominal_pose {
+    double R_wc[9];             /* world -> camera rotation, row-major */
+    double t[3];                /* camera centre, world frame */
+} ar_nominal_pose;
+
+typedef struct ar_pose_box {
+    double lo[6], hi[6];        /* bounds of (tx, ty, tz, rx, ry, rz) */
+} ar_pose_box;
+
+typedef struct ar_scene ar_scene;
+typedef struct ar_server ar_server;
+
+/* Per-render counters and stage times (ms; timed with CUDA events on the
+ * render stream when profiling is on, else -1). */
+typedef struct ar_render_stats {
+    int64_t n_records;          /* (Gaussian, cell) pairs that reach the image */
+    int64_t n_entries;          /* (Gaussian, cell, tile) bin entries (2 events each) */
+    int64_t n_triples;          /* (pixel, Gaussian, cell) triples inside a screen box */
+    int64_t n_fallback;         /* (Gaussian, cell) pairs where MatrixInv's assertion failed */
+    int32_t n_launches;         /* kernels launched by the render */
+    int32_t tile;               /* tile edge used (pixels) */
+    int32_t m_vars;             /* pose variables carried by the linear forms */
+    float ms_prep, ms_bin, ms_render, ms_total;
+} ar_render_stats;
+
+/* Create a scene from n Gaussians <uw, Mw, o, c> (Sec. 2.2).  Mw is given by
+ * a per-axis log-scale and a rotation quaternion (w, x, y, z): Mw = R(q)
+ * diag(exp(logscale)), any square-root factor of the covariance being
+ * allowed by the footnote of Sec. 2.2.
+ *   uw3[n][3], logscale3[n][3], quat4[n][4], opacity[n] in [0, 1), rgb3[n][3]
+ *   in [0, 1]: float32, row-major.  device_ptrs = 0: host arrays; 1: device
+ *   arrays on the current device.  The arrays are copied; the caller keeps
+ *   ownership.  n = 0 is legal (renders black).  The scene lives on the
+ *   current CUDA device and owns its device memory until ar_scene_destroy.
+ * Errors: AR_EINVAL (null pointers with n > 0, n < 0, non-finite values,
+ * opacity outside [0, 1), colour outside [0, 1], zero quaternion),
+ * AR_ENOMEM, AR_EDEVICE. */
+int ar_scene_create(const float *uw3, const float *logscale3, const float *quat4,
+                    const float *opacity, const float *rgb3, int64_t n, int device_ptrs,
+                    ar_scene **out);
+
+/* Release a scene and all its device memory (synchronises the device). */
+int ar_scene_destroy(ar_scene *scene);
+
+/* Abstract-render n_cells pose cells (AbstractSplat, Sec. 3.3, with the input
+ * partitioning of Sec. 4.2 batched into one call): per cell, per pixel, RGB
+ * lower and upper bounds.
+ *   cells[n_cells] (host memory), n_cells >= 1.
+ *   tile: 0 = choose, else 8 or 16 (screen tile edge of the binning; results
+ *   do not depend on it).
+ *   out_lower, out_upper: device pointers, float32 [n_cells][H][W][3] each,
+ *   owned by the caller.
+ * Work is enqueued on cuda_stream; the call returns after the last launch is
+ * enqueued (it synchronises once with the stream to size the tile bins).
+ * Errors: AR_EINVAL (null pointers, bad intrinsics or cells, tile not in
+ * {0, 8, 16}), AR_ENOMEM (workspace), AR_EDEVICE. */
+int ar_render_abstract(ar_scene *scene, const ar_intrinsics *intr, const ar_nominal_pose *pose,
+                       const ar_pose_box *cells, int32_t n_cells, int32_t tile,
+                       float *out_lower, float *out_upper, void *cuda_stream);
+
+/* Same as ar_render_abstract with HOST output buffers: the bounds are
+ * computed into scene-owned device memory and copied to host_lower /
+ * host_upper ([n_cells][H][W][3] float32 each, page-locked memory is
+ * fastest).  Returns after the copies complete. */
+int ar_render_abstract_host(ar_scene *scene, const ar_intrinsics *intr, const ar_nominal_pose *pose,
+                            const ar_pose_box *cells, int32_t n_cells, int32_t tile,
+                            float *host_lower, float *host_upper, void *cuda_stream);
+
+/* Plain comparison path: the same bounds computed one cell per launch
+ * sequence in FP64 with directed rounding, without cell batching.  Same
+ * arguments and output layout as ar_render_abstract. */
+int ar_render_abstract_plain_fp64(ar_scene *scene, const ar_intrinsics *intr,
+                                  const ar_nominal_pose *pose, const ar_pose_box *cells,
+                                  int32_t n_cells, int32_t tile, float *out_lower,
+                                  float *out_upper, void *cuda_stream);
+
+/* Concrete GSplat render (Algorithm 1 with BlendInd, Algorithm 4) at n_poses
+ * poses given as delta vectors (host, [n_poses][6]); out is a device buffer
+ * [n_poses][H][W][3] float32.  Used to check soundness on the device. */
+int ar_render_concrete(ar_scene *scene, const ar_intrinsics *intr, const ar_nominal_pose *pose,
+                       const double *deltas, int32_t n_poses, float *out, void *cuda_stream);
+
+/* Stage timing with CUDA events on the render stream (on = 1) or off (0). */
+int ar_set_profiling(ar_scene *scene, int on);
+
+/* Counters and stage times of the scene's last render (synchronises its stream). */
+int ar_last_render_stats(ar_scene *scene, ar_render_stats *stats);
+
+/* ---- serving: continuous batching of abstract-render requests ----------
+ * A server owns one CUDA stream per slot and a device-memory budget.
+ * Requests are admitted when a slot is free and their workspace fits the
+ * budget; they run concurrently on the device and complete independently. */
+
+/* hbm_budget_bytes: workspace budget (> 0); n_slots: concurrent requests (1..64). */
+int ar_serve_create(int64_t hbm_budget_bytes, int32_t n_slots, ar_server **out);
+
+/* Waits for in-flight requests (bounded), then frees the server. */
+int ar_serve_destroy(ar_server *server);
+
+/* Submit one request.  The scene must outlive the request; cells are copied;
+ * out_lower/out_upper are device buffers as for ar_render_abstract.
+ * Returns AR_EAGAIN when no slot or memory is free right now (try again),
+ * AR_EINVAL for bad arguments.  *ticket identifies the request. */
+int ar_serve_submit(ar_server *server, ar_scene *scene, const ar_intrinsics *intr,
+                    const ar_nominal_pose *pose, const ar_pose_box *cells, int32_t n_cells,
+                    float *out_lower, float *out_upper, uint64_t *ticket);
+
+/* Poll a ticket: *done = 1 once its outputs are complete (then *latency_ms is
+ * submit-to-completion wall time and the ticket is retired), else 0.
+ * AR_EINVAL for an unknown or retired ticket. */
+int ar_serve_poll(ar_server *server, uint64_t ticket, int *done, double *latency_ms);
+
+/* Message of the calling thread's last failure ("" if none).  The pointer
+ * stays valid until the thread's next libar call. */
+const char *ar_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AR_H */

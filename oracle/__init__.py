@@ -46,7 +46,7 @@ def _load():
         D = ctypes.c_double
         lib.orc_render_concrete.argtypes = [P, P, P, P, P, I64, P, P, P, P, I, P]
         lib.orc_render_concrete.restype = I
-        lib.orc_render_abstract.argtypes = [P, P, P, P, P, I64, P, P, P, P, P, I, I, I, I, P, P, P]
+        lib.orc_render_abstract.argtypes = [P, P, P, P, P, I64, P, P, P, P, P, I, I, I, I, P, P, P, P]
         lib.orc_render_abstract.restype = I
         lib.orc_records.argtypes = [P, P, P, P, P, I64, P, P, P, P, P, P]
         lib.orc_records.restype = I
@@ -60,6 +60,12 @@ def _load():
         lib.orc_check_samples.argtypes = [P, P, P, P, P, I64, P, P, P, P, I64, P, P, D, P]
         lib.orc_check_samples.restype = D
         lib.orc_empirical_bounds.argtypes = [P, P, P, P, P, I64, P, P, P, P, I64, P, P]
+        lib.orc_pixel_detail.argtypes = [P, P, P, P, P, I64, P, P, P, P, P, I, I, P, I]
+        lib.orc_pixel_detail.restype = I
+        lib.orc_pixel_trace.argtypes = [P, P, P, P, P, I64, P, P, P, P, P, I64, I, I, P]
+        lib.orc_pixel_trace.restype = I
+        lib.orc_record_trace.argtypes = [P, P, P, P, P, I64, P, P, P, P, P, I64, P]
+        lib.orc_record_trace.restype = I
         lib.orc_set_threads.argtypes = [I]
         lib.orc_set_threads.restype = I
         _lib = lib
@@ -103,28 +109,31 @@ def render_concrete(scene, cam, delta, blend: str = "ind") -> np.ndarray:
     return out
 
 
-def render_abstract(scene, cam, cell_lo, cell_hi, window=None):
+def render_abstract(scene, cam, cell_lo, cell_hi, window=None, with_cond=False):
     """AbstractSplat bounds of one pose cell.
 
-    Returns (lo, hi, fragile): lo/hi are [H, W, 3] float64 (only `window`
-    = (px0, px1, py0, py1), inclusive, is filled; the rest stays NaN) and
-    fragile [H, W] uint8 marks pixels where a threshold decision that the
-    single-precision path takes lies within its rounding band."""
+    Returns (lo, hi, fragile) -- and cond if with_cond: lo/hi are [H, W, 3]
+    float64 (only `window` = (px0, px1, py0, py1), inclusive, is filled; the
+    rest stays NaN), fragile [H, W] uint8 marks pixels where a threshold
+    decision that the single-precision path takes lies within its rounding
+    band, and cond [H, W] estimates how far FP32 evaluation can move the
+    bounds."""
     lib = _load()
     s = _scene_args(scene)
     intr, R0, t0 = _cam_args(cam)
     lo = np.full((cam.height, cam.width, 3), np.nan)
     hi = np.full((cam.height, cam.width, 3), np.nan)
     frag = np.zeros((cam.height, cam.width), dtype=np.uint8)
+    cond = np.zeros((cam.height, cam.width), dtype=np.float64)
     if window is None:
         window = (0, cam.width - 1, 0, cam.height - 1)
     px0, px1, py0, py1 = (int(v) for v in window)
     st = lib.orc_render_abstract(*[_p(a) for a in s], scene.n, _p(intr), _p(R0), _p(t0),
                                  _p(_d(cell_lo).reshape(6)), _p(_d(cell_hi).reshape(6)),
-                                 px0, px1, py0, py1, _p(lo), _p(hi), _p(frag))
+                                 px0, px1, py0, py1, _p(lo), _p(hi), _p(frag), _p(cond))
     if st:
         raise RuntimeError("oracle abstract render failed")
-    return lo, hi, frag
+    return (lo, hi, frag, cond) if with_cond else (lo, hi, frag)
 
 
 def records(scene, cam, cell_lo, cell_hi) -> dict:
@@ -209,3 +218,36 @@ def empirical_bounds(scene, cam, poses):
     lib.orc_empirical_bounds(*[_p(a) for a in s], scene.n, _p(intr), _p(R0), _p(t0), _p(P), P.shape[0],
                              _p(lo), _p(hi))
     return lo, hi
+
+
+def pixel_detail(scene, cam, cell_lo, cell_hi, px, py, cap=4096):
+    """Per-Gaussian relaxation details at one pixel (diagnosis): array (k, 12)."""
+    lib = _load()
+    s = _scene_args(scene)
+    intr, R0, t0 = _cam_args(cam)
+    out = np.zeros((cap, 12))
+    k = lib.orc_pixel_detail(*[_p(a) for a in s], scene.n, _p(intr), _p(R0), _p(t0),
+                             _p(_d(cell_lo).reshape(6)), _p(_d(cell_hi).reshape(6)), int(px), int(py), _p(out), int(cap))
+    return out[:k]
+
+
+def pixel_trace(scene, cam, cell_lo, cell_hi, gi, px, py):
+    """Intervals Dx, Dy, W[6], q[3], m of one Gaussian at one pixel (diagnosis)."""
+    lib = _load()
+    s = _scene_args(scene)
+    intr, R0, t0 = _cam_args(cam)
+    out = np.zeros(24)
+    st = lib.orc_pixel_trace(*[_p(a) for a in s], scene.n, _p(intr), _p(R0), _p(t0),
+                             _p(_d(cell_lo).reshape(6)), _p(_d(cell_hi).reshape(6)), int(gi), int(px), int(py), _p(out))
+    return None if st else out.reshape(12, 2)
+
+
+def record_trace(scene, cam, cell_lo, cell_hi, gi):
+    """X, E, Mp, conic intervals and rho of one (Gaussian, cell) pair (diagnosis)."""
+    lib = _load()
+    s = _scene_args(scene)
+    intr, R0, t0 = _cam_args(cam)
+    out = np.zeros(35)
+    st = lib.orc_record_trace(*[_p(a) for a in s], scene.n, _p(intr), _p(R0), _p(t0),
+                              _p(_d(cell_lo).reshape(6)), _p(_d(cell_hi).reshape(6)), int(gi), _p(out))
+    return st, out

@@ -546,20 +546,26 @@ static void gaussian_record(const camera *cam, const cellforms *cf, const double
         }
 
     /* screen box: centres of pixels that can lie in the ellipse m <= tau for
-     * some pose of the cell with d > near (interval arithmetic, FP64) */
+     * some pose of the cell with d > near.  Interval arithmetic in FP64 on
+     * the concretised rotation entries; the mean is mu = c + f uc / d and the
+     * half-extent of the ellipse is sqrt(tau X_rr) / d^2 (X = d^4 Sigma_2D). */
     {
+        ival Ri[9], vs[3];
+        for (int e = 0; e < 9; ++e) { Ri[e].l = bs_min(&cf->Rd[e]); Ri[e].u = bs_max(&cf->Rd[e]); }
+        for (int b = 0; b < 3; ++b) { vs[b].l = v[b] - bs_max(&cf->s[b]); vs[b].u = v[b] - bs_min(&cf->s[b]); }
         double dl = fmax(dlo, cam->near_plane);
         ival D = {dl, dhi};
-        ival U0 = {bs_min(&up0), bs_max(&up0)}, U1 = {bs_min(&up1), bs_max(&up1)};
-        ival ucx = {bs_min(&uc[0]), bs_max(&uc[0])}, ucy = {bs_min(&uc[1]), bs_max(&uc[1])};
-        ival mux = {fmin(U0.l / D.l, U0.l / D.u), fmax(U0.u / D.l, U0.u / D.u)};
-        ival muy = {fmin(U1.l / D.l, U1.l / D.u), fmax(U1.u / D.l, U1.u / D.u)};
+        ival ucx = iv_add(iv_add(iv_mul(Ri[0], vs[0]), iv_mul(Ri[3], vs[1])), iv_mul(Ri[6], vs[2]));
+        ival ucy = iv_add(iv_add(iv_mul(Ri[1], vs[0]), iv_mul(Ri[4], vs[1])), iv_mul(Ri[7], vs[2]));
+        ival mux = {cam->cx + cam->fx * fmin(ucx.l / D.l, ucx.l / D.u), cam->cx + cam->fx * fmax(ucx.u / D.l, ucx.u / D.u)};
+        ival muy = {cam->cy + cam->fy * fmin(ucy.l / D.l, ucy.l / D.u), cam->cy + cam->fy * fmax(ucy.u / D.l, ucy.u / D.u)};
         double X00 = 0, X11 = 0;
         for (int c = 0; c < 3; ++c) {
-            ival m0 = {bs_min(&Mc[c]), bs_max(&Mc[c])}, m1 = {bs_min(&Mc[3 + c]), bs_max(&Mc[3 + c])};
-            ival m2 = {bs_min(&Mc[6 + c]), bs_max(&Mc[6 + c])};
-            ival p0 = iv_scale(iv_add(iv_mul(D, m0), iv_scale(iv_mul(ucx, m2), -1.0)), cam->fx);
-            ival p1 = iv_scale(iv_add(iv_mul(D, m1), iv_scale(iv_mul(ucy, m2), -1.0)), cam->fy);
+            ival m[3];
+            for (int a = 0; a < 3; ++a)
+                m[a] = iv_add(iv_add(iv_scale(Ri[a], N[c]), iv_scale(Ri[3 + a], N[3 + c])), iv_scale(Ri[6 + a], N[6 + c]));
+            ival p0 = iv_scale(iv_add(iv_mul(D, m[0]), iv_scale(iv_mul(ucx, m[2]), -1.0)), cam->fx);
+            ival p1 = iv_scale(iv_add(iv_mul(D, m[1]), iv_scale(iv_mul(ucy, m[2]), -1.0)), cam->fy);
             X00 += iv_sqmax(p0); X11 += iv_sqmax(p1);
         }
         double rx = sqrt(g->tau * X00) / (dl * dl), ry = sqrt(g->tau * X11) / (dl * dl);
@@ -659,12 +665,19 @@ static void gaussian_alpha(const grec *g, double ux, double uy, galpha *r)
  * out_lo/out_hi are [H][W][3] (only the window is written).  fragile, if
  * given, is [H][W] and marks pixels where a threshold decision that the FP32
  * path takes in single precision lies within a relative 1e-3 of its
- * threshold (both outcomes are sound there). */
+ * threshold (both outcomes are sound there).  cond, if given, is [H][W] and
+ * holds an estimate of how far single-precision evaluation of the same
+ * bounds can move them: each Gaussian's m interval is computed from terms
+ * of magnitude about |m_lo| + |m_hi|, so in FP32 its ends move by about
+ * 32 u (|m_lo| + |m_hi|) (u = 2^-24, 32 covering the chain of products),
+ * its opacity bounds by half of that times a (a_hi only while m_lo > 0: below
+ * that the upper secant ends at x = 0 and a_hi = o), and the pixel colour by
+ * at most 2 T_hi times that (d colour / d a_i is at most 2 T_i). */
 int orc_render_abstract(const double *uw, const double *ls, const double *quat, const double *opac,
                         const double *rgb, int64_t n, const double *intr, const double *R0,
                         const double *t0, const double *cell_lo, const double *cell_hi,
                         int px0, int px1, int py0, int py1, double *out_lo, double *out_hi,
-                        uint8_t *fragile)
+                        uint8_t *fragile, double *cond)
 {
     camera cam = make_camera(intr, R0, t0);
     cellforms cf;
@@ -711,6 +724,7 @@ int orc_render_abstract(const double *uw, const double *ls, const double *quat, 
         /* BlendInd with interval Prod: for each i, T_lo over j that may be in
          * front (not certainly behind), T_hi over j certainly in front */
         lf lo[3], hi[3];
+        double est = 0.0;
         for (int ch = 0; ch < 3; ++ch) { lo[ch] = lf_cst(0); hi[ch] = lf_cst(0); }
         for (int64_t a = 0; a < K; ++a) {
             const grec *gi = &G[idx[a]];
@@ -725,6 +739,13 @@ int orc_render_abstract(const double *uw, const double *ls, const double *quat, 
                     Tlo *= 1.0 - A[b].ahi;
                 }                                      /* else Ind(d_i - d_j) = 0 */
             }
+            if (!gi->fallback && isfinite(A[a].mlo) && isfinite(A[a].mhi)) {
+                /* a_hi moves with m_lo only while m_lo > 0 (else the secant ends at
+                 * x = 0 and a_hi = o); a_lo moves with m_hi in proportion to itself */
+                double em = 32.0 * 5.9604644775390625e-8 * (fabs(A[a].mlo) + fabs(A[a].mhi));
+                double da = 0.5 * em * ((A[a].mlo > 0 ? A[a].ahi : 0.0) + A[a].alo);
+                est += 2.0 * Thi * da;
+            }
             for (int ch = 0; ch < 3; ++ch) {
                 lf t = lf_scale(&A[a].L, Tlo * gi->c[ch]);
                 lo[ch] = lf_add(&lo[ch], &t);
@@ -738,6 +759,7 @@ int orc_render_abstract(const double *uw, const double *ls, const double *quat, 
             out_hi[o + ch] = clamp01(lf_max(&hi[ch]));
         }
         if (fragile) fragile[(size_t)py * cam.W + px] = (uint8_t)frag;
+        if (cond) cond[(size_t)py * cam.W + px] = est;
         free(idx); free(A);
     }
     free(G);
@@ -843,4 +865,126 @@ void orc_empirical_bounds(const double *uw, const double *ls, const double *quat
         }
         free(img); free(l); free(h);
     }
+}
+
+/* Per-Gaussian details at one pixel of one cell (for diagnosis): for each
+ * Gaussian whose pixel box holds the pixel, 12 doubles: index, mlo, mhi,
+ * ramp, alo, ahi, klo, khi, L.k, U.k, flags (1 fallback, 2 straddle), rho.
+ * Returns the number of Gaussians written (at most cap). */
+int orc_pixel_detail(const double *uw, const double *ls, const double *quat, const double *opac,
+                     const double *rgb, int64_t n, const double *intr, const double *R0, const double *t0,
+                     const double *cell_lo, const double *cell_hi, int px, int py, double *out, int cap)
+{
+    camera cam = make_camera(intr, R0, t0);
+    cellforms cf;
+    cell_setup(&cam, cell_lo, cell_hi, &cf);
+    int k = 0;
+    for (int64_t i = 0; i < n && k < cap; ++i) {
+        grec g;
+        gaussian_record(&cam, &cf, uw + 3 * i, ls + 3 * i, quat + 4 * i, opac[i], rgb + 3 * i, &g);
+        if (!g.valid || px < g.px0 || px > g.px1 || py < g.py0 || py > g.py1) continue;
+        galpha a;
+        gaussian_alpha(&g, px + 0.5, py + 0.5, &a);
+        double *o = out + 12 * k;
+        o[0] = (double)i; o[1] = a.mlo; o[2] = a.mhi; o[3] = a.ramp; o[4] = a.alo; o[5] = a.ahi;
+        o[6] = g.klo; o[7] = g.khi; o[8] = a.L.k; o[9] = a.U.k; o[10] = g.fallback + 2 * g.straddle; o[11] = g.rho;
+        ++k;
+    }
+    return k;
+}
+
+/* Intermediate intervals of one (Gaussian, cell) pair at one pixel (for
+ * diagnosis): Dx, Dy, W[0..5], q[0..2], m as (lo, hi) pairs -> 24 doubles.
+ * Returns 0 if the pair is valid and not a fallback. */
+int orc_pixel_trace(const double *uw, const double *ls, const double *quat, const double *opac,
+                    const double *rgb, int64_t n, const double *intr, const double *R0, const double *t0,
+                    const double *cell_lo, const double *cell_hi, int64_t gi, int px, int py, double *out)
+{
+    camera cam = make_camera(intr, R0, t0);
+    cellforms cf;
+    cell_setup(&cam, cell_lo, cell_hi, &cf);
+    if (gi < 0 || gi >= n) return 1;
+    grec g;
+    gaussian_record(&cam, &cf, uw + 3 * gi, ls + 3 * gi, quat + 4 * gi, opac[gi], rgb + 3 * gi, &g);
+    if (!g.valid || g.fallback) return 1;
+    double ux = px + 0.5, uy = py + 0.5;
+    bs Dx = bs_sub(bs_scale(g.S, ux), g.Px);
+    bs Dy = bs_sub(bs_scale(g.S, uy), g.Py);
+    out[0] = bs_min(&Dx); out[1] = bs_max(&Dx); out[2] = bs_min(&Dy); out[3] = bs_max(&Dy);
+    for (int e = 0; e < 6; ++e) { out[4 + 2 * e] = bs_min(&g.W[e]); out[5 + 2 * e] = bs_max(&g.W[e]); }
+    bs m = bs_cst(0);
+    for (int c = 0; c < 3; ++c) {
+        bs qc = bs_add(bs_mul(Dx, g.W[c]), bs_mul(Dy, g.W[3 + c]));
+        out[16 + 2 * c] = bs_min(&qc); out[17 + 2 * c] = bs_max(&qc);
+        m = bs_add(m, bs_sq(qc));
+    }
+    out[22] = bs_min(&m); out[23] = bs_max(&m);
+    return 0;
+}
+
+/* MatrixInv internals of one (Gaussian, cell) pair (for diagnosis): X00, X01,
+ * X11, E[4], Mp[6], conic[4] as (lo, hi) pairs, then rho -> 35 doubles. */
+int orc_record_trace(const double *uw, const double *ls, const double *quat, const double *opac,
+                     const double *rgb, int64_t n, const double *intr, const double *R0, const double *t0,
+                     const double *cell_lo, const double *cell_hi, int64_t gi, double *out)
+{
+    camera cam = make_camera(intr, R0, t0);
+    cellforms cf;
+    cell_setup(&cam, cell_lo, cell_hi, &cf);
+    if (gi < 0 || gi >= n) return 1;
+    const double *q = quat + 4 * gi;
+    double Mw[9], N[9], v[3];
+    cov_factor(ls + 3 * gi, q, Mw);
+    mat3_mul(cam.R0, Mw, N);
+    for (int a = 0; a < 3; ++a) {
+        v[a] = 0;
+        for (int b = 0; b < 3; ++b) v[a] += cam.R0[3 * a + b] * (uw[3 * gi + b] - cam.t0[b]);
+    }
+    bs vms[3], uc[3];
+    for (int b = 0; b < 3; ++b) vms[b] = bs_sub(bs_cst(v[b]), cf.s[b]);
+    for (int a = 0; a < 3; ++a) {
+        uc[a] = bs_mul(cf.Rd[a], vms[0]);
+        uc[a] = bs_add(uc[a], bs_mul(cf.Rd[3 + a], vms[1]));
+        uc[a] = bs_add(uc[a], bs_mul(cf.Rd[6 + a], vms[2]));
+    }
+    bs d = uc[2];
+    bs Mc[9];
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) {
+            bs s = bs_scale(cf.Rd[a], N[c]);
+            s = bs_add(s, bs_scale(cf.Rd[3 + a], N[3 + c]));
+            s = bs_add(s, bs_scale(cf.Rd[6 + a], N[6 + c]));
+            Mc[3 * a + c] = s;
+        }
+    bs J00 = bs_scale(d, cam.fx), J02 = bs_scale(uc[0], -cam.fx);
+    bs J11 = bs_scale(d, cam.fy), J12 = bs_scale(uc[1], -cam.fy);
+    bs Mp[6];
+    for (int c = 0; c < 3; ++c) {
+        Mp[c] = bs_add(bs_mul(J00, Mc[c]), bs_mul(J02, Mc[6 + c]));
+        Mp[3 + c] = bs_add(bs_mul(J11, Mc[3 + c]), bs_mul(J12, Mc[6 + c]));
+    }
+    bs X[4];
+    X[0] = bs_add(bs_add(bs_sq(Mp[0]), bs_sq(Mp[1])), bs_sq(Mp[2]));
+    X[3] = bs_add(bs_add(bs_sq(Mp[3]), bs_sq(Mp[4])), bs_sq(Mp[5]));
+    X[1] = bs_add(bs_add(bs_mul(Mp[0], Mp[3]), bs_mul(Mp[1], Mp[4])), bs_mul(Mp[2], Mp[5]));
+    X[2] = X[1];
+    out[0] = bs_min(&X[0]); out[1] = bs_max(&X[0]); out[2] = bs_min(&X[1]); out[3] = bs_max(&X[1]);
+    out[4] = bs_min(&X[3]); out[5] = bs_max(&X[3]);
+    double Xh[4];
+    for (int e = 0; e < 4; ++e) Xh[e] = 0.5 * (bs_min(&X[e]) + bs_max(&X[e]));
+    double det = Xh[0] * Xh[3] - Xh[1] * Xh[2];
+    double X0[4] = {Xh[3] / det, -Xh[1] / det, -Xh[2] / det, Xh[0] / det};
+    for (int r = 0; r < 2; ++r)
+        for (int s = 0; s < 2; ++s) {
+            bs v2 = bs_add(bs_scale(X[2 * r], X0[s]), bs_scale(X[2 * r + 1], X0[2 + s]));
+            bs E = bs_addc(bs_scale(v2, -1.0), r == s ? 1.0 : 0.0);
+            out[6 + 2 * (2 * r + s)] = bs_min(&E); out[7 + 2 * (2 * r + s)] = bs_max(&E);
+        }
+    for (int e = 0; e < 6; ++e) { out[14 + 2 * e] = bs_min(&Mp[e]); out[15 + 2 * e] = bs_max(&Mp[e]); }
+    bs C[4];
+    double rho;
+    if (matrix_inv(X, KTAYLOR, C, &rho)) return 2;
+    for (int e = 0; e < 4; ++e) { out[26 + 2 * e] = bs_min(&C[e]); out[27 + 2 * e] = bs_max(&C[e]); }
+    out[34] = rho;
+    return 0;
 }

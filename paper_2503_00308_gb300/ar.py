@@ -1,0 +1,233 @@
+"""ctypes binding of libar (include/ar.h): same names, argument marshalling only.
+
+Every computation runs in libar's CUDA kernels.  Loading fails loudly when the
+library has not been built (there is no CPU fallback): run
+``python -c "import __graft_entry__ as g; g.build()"`` first.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+AR_OK, AR_EINVAL, AR_ENOMEM, AR_EAGAIN, AR_ETIMEOUT, AR_EDEVICE = range(6)
+
+c_int32, c_int64, c_float, c_double, c_void_p = (ctypes.c_int32, ctypes.c_int64, ctypes.c_float,
+                                                 ctypes.c_double, ctypes.c_void_p)
+
+
+class ar_intrinsics(ctypes.Structure):
+    _fields_ = [("width", c_int32), ("height", c_int32), ("fx", c_float), ("fy", c_float),
+                ("cx", c_float), ("cy", c_float), ("near_plane", c_float)]
+
+
+class ar_nominal_pose(ctypes.Structure):
+    _fields_ = [("R_wc", c_double * 9), ("t", c_double * 3)]
+
+
+class ar_pose_box(ctypes.Structure):
+    _fields_ = [("lo", c_double * 6), ("hi", c_double * 6)]
+
+
+class ar_render_stats(ctypes.Structure):
+    _fields_ = [("n_records", c_int64), ("n_entries", c_int64), ("n_triples", c_int64),
+                ("n_fallback", c_int64), ("n_launches", c_int32), ("tile", c_int32), ("m_vars", c_int32),
+                ("ms_prep", c_float), ("ms_bin", c_float), ("ms_render", c_float), ("ms_total", c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ArError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("libar error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load libar.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError("libar.so is not built (%s); call __graft_entry__.build()" % path)
+        L = ctypes.CDLL(path)
+        P = c_void_p
+        sig = {
+            "ar_scene_create": ([P, P, P, P, P, c_int64, ctypes.c_int, P], ctypes.c_int),
+            "ar_scene_destroy": ([P], ctypes.c_int),
+            "ar_render_abstract": ([P, P, P, P, c_int32, c_int32, P, P, P], ctypes.c_int),
+            "ar_render_abstract_host": ([P, P, P, P, c_int32, c_int32, P, P, P], ctypes.c_int),
+            "ar_render_abstract_plain_fp64": ([P, P, P, P, c_int32, c_int32, P, P, P], ctypes.c_int),
+            "ar_render_concrete": ([P, P, P, P, c_int32, P, P], ctypes.c_int),
+            "ar_set_profiling": ([P, ctypes.c_int], ctypes.c_int),
+            "ar_last_render_stats": ([P, P], ctypes.c_int),
+            "ar_serve_create": ([c_int64, c_int32, P], ctypes.c_int),
+            "ar_serve_destroy": ([P], ctypes.c_int),
+            "ar_serve_submit": ([P, P, P, P, P, c_int32, P, P, P], ctypes.c_int),
+            "ar_serve_poll": ([P, ctypes.c_uint64, P, P], ctypes.c_int),
+            "ar_last_error": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def check(code: int):
+    if code != AR_OK:
+        raise ArError(code, ar_last_error())
+    return code
+
+
+def ar_last_error() -> str:
+    return lib().ar_last_error().decode()
+
+
+# ------------------------------------------------------------- marshalling
+
+def make_intrinsics(cam) -> ar_intrinsics:
+    return ar_intrinsics(int(cam.width), int(cam.height), float(cam.fx), float(cam.fy), float(cam.cx),
+                         float(cam.cy), float(cam.near))
+
+
+def make_pose(cam) -> ar_nominal_pose:
+    p = ar_nominal_pose()
+    R = np.asarray(cam.R_wc, dtype=np.float64).reshape(9)
+    t = np.asarray(cam.t, dtype=np.float64).reshape(3)
+    for i in range(9):
+        p.R_wc[i] = float(R[i])
+    for i in range(3):
+        p.t[i] = float(t[i])
+    return p
+
+
+def make_cells(lo, hi):
+    lo = np.asarray(lo, dtype=np.float64).reshape(-1, 6)
+    hi = np.asarray(hi, dtype=np.float64).reshape(-1, 6)
+    arr = (ar_pose_box * lo.shape[0])()
+    for c in range(lo.shape[0]):
+        for k in range(6):
+            arr[c].lo[k] = float(lo[c, k])
+            arr[c].hi[k] = float(hi[c, k])
+    return arr
+
+
+def _ptr(x):
+    """Device or host address of a torch tensor / numpy array / int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def ar_scene_create(uw3, logscale3, quat4, opacity, rgb3, n: int, device_ptrs: int = 0):
+    h = c_void_p()
+    check(lib().ar_scene_create(_ptr(uw3), _ptr(logscale3), _ptr(quat4), _ptr(opacity), _ptr(rgb3),
+                                int(n), int(device_ptrs), ctypes.byref(h)))
+    return h
+
+
+def ar_scene_destroy(scene):
+    return check(lib().ar_scene_destroy(scene))
+
+
+def ar_render_abstract(scene, intr, pose, cells, n_cells, tile, out_lower, out_upper, stream=0):
+    return check(lib().ar_render_abstract(scene, ctypes.byref(intr), ctypes.byref(pose), cells, int(n_cells),
+                                          int(tile), _ptr(out_lower), _ptr(out_upper), _ptr(stream)))
+
+
+def ar_render_abstract_host(scene, intr, pose, cells, n_cells, tile, host_lower, host_upper, stream=0):
+    return check(lib().ar_render_abstract_host(scene, ctypes.byref(intr), ctypes.byref(pose), cells,
+                                               int(n_cells), int(tile), _ptr(host_lower), _ptr(host_upper),
+                                               _ptr(stream)))
+
+
+def ar_render_abstract_plain_fp64(scene, intr, pose, cells, n_cells, tile, out_lower, out_upper, stream=0):
+    return check(lib().ar_render_abstract_plain_fp64(scene, ctypes.byref(intr), ctypes.byref(pose), cells,
+                                                     int(n_cells), int(tile), _ptr(out_lower), _ptr(out_upper),
+                                                     _ptr(stream)))
+
+
+def ar_render_concrete(scene, intr, pose, deltas, n_poses, out, stream=0):
+    d = np.ascontiguousarray(deltas, dtype=np.float64)
+    return check(lib().ar_render_concrete(scene, ctypes.byref(intr), ctypes.byref(pose), d.ctypes.data,
+                                          int(n_poses), _ptr(out), _ptr(stream)))
+
+
+def ar_set_profiling(scene, on: bool):
+    return check(lib().ar_set_profiling(scene, 1 if on else 0))
+
+
+def ar_last_render_stats(scene) -> dict:
+    st = ar_render_stats()
+    check(lib().ar_last_render_stats(scene, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def ar_serve_create(hbm_budget_bytes: int, n_slots: int):
+    h = c_void_p()
+    check(lib().ar_serve_create(int(hbm_budget_bytes), int(n_slots), ctypes.byref(h)))
+    return h
+
+
+def ar_serve_destroy(server):
+    return check(lib().ar_serve_destroy(server))
+
+
+def ar_serve_submit(server, scene, intr, pose, cells, n_cells, out_lower, out_upper):
+    """Returns the ticket, or None when admission is refused (AR_EAGAIN)."""
+    t = ctypes.c_uint64()
+    r = lib().ar_serve_submit(server, scene, ctypes.byref(intr), ctypes.byref(pose), cells, int(n_cells),
+                              _ptr(out_lower), _ptr(out_upper), ctypes.byref(t))
+    if r == AR_EAGAIN:
+        return None
+    check(r)
+    return int(t.value)
+
+
+def ar_serve_poll(server, ticket: int):
+    """Returns (done, latency_ms)."""
+    done = ctypes.c_int()
+    lat = ctypes.c_double()
+    check(lib().ar_serve_poll(server, ctypes.c_uint64(ticket), ctypes.byref(done), ctypes.byref(lat)))
+    return bool(done.value), float(lat.value)
+
+
+# ------------------------------------------------------------ conveniences
+
+class Scene:
+    """Owns an ar_scene handle created from a synth.Scene-like record (host arrays)."""
+
+    def __init__(self, sc):
+        self._arrays = [np.ascontiguousarray(a, dtype=np.float32) for a in
+                        (sc.uw, sc.logscale, sc.quat, sc.opacity, sc.rgb)]
+        self.n = int(self._arrays[0].shape[0])
+        self.handle = ar_scene_create(*self._arrays, self.n, 0)
+
+    def close(self):
+        if self.handle is not None:
+            ar_scene_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def render(self, cam, cells_lo, cells_hi, out_lower, out_upper, tile: int = 0, stream=0):
+        cells = make_cells(cells_lo, cells_hi)
+        ar_render_abstract(self.handle, make_intrinsics(cam), make_pose(cam), cells, len(cells), tile,
+                           out_lower, out_upper, stream)

@@ -1,0 +1,42 @@
+// ar_bin.h -- host interface of the binning / sorting stage.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ar {
+
+struct PixBox;
+
+struct BinArgs {
+    const PixBox *boxes;     // [n_pairs] pixel boxes, x0 < 0 = absent
+    const double *keys;      // [n_pairs][2] depth-key interval
+    uint64_t n_pairs;        // n_cells * n_gauss
+    uint64_t n_gauss;
+    int n_cells;
+    uint64_t n_events;       // 2 * pairs present
+    uint64_t n_entries;      // sum over events of tiles met
+    int TS, ntx, n_tiles;
+    uint64_t n_segments;     // n_cells * n_tiles
+    uint64_t *ev_key[2];     // [n_events] x2
+    uint32_t *ev_val[2];     // [n_events] x2
+    uint32_t *ent_seg[2];    // [n_entries] x2
+    uint32_t *ent_ev[2];     // [n_entries] x2
+    uint32_t *u32_a, *u32_b, *u32_c, *u32_d;  // scratch, >= max(n_pairs, n_events) words each
+    uint32_t *hist;          // >= radix_hist_words(max(n_events, n_entries))
+    uint32_t *scan_tmp;      // >= scan_temp_words(largest scanned length)
+    uint32_t *seg_start, *seg_end;  // [n_segments]
+};
+
+struct BinOut {
+    const uint64_t *ev_key;  // sorted event keys
+    const uint32_t *ev_val;  // sorted event values: 2 * pair + (upper endpoint)
+    const uint32_t *ent_seg; // entries sorted by segment
+    const uint32_t *ent_ev;  // entry -> sorted event index
+};
+
+size_t scan_temp_words(uint64_t n);
+size_t radix_hist_words(uint64_t n);
+void exclusive_scan(const uint32_t *in, uint32_t *out, uint64_t n, uint32_t *tmp, cudaStream_t st, int *launches);
+int run_binning(const BinArgs &a, BinOut &o, cudaStream_t st, int *launches);
+
+}  // namespace ar

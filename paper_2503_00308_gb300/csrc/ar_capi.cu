@@ -1,0 +1,501 @@
+// ar_capi.cu -- host implementation of the libar C ABI (include/ar.h).
+//
+// A scene owns its Gaussians on the device (FP32 inputs plus the FP64
+// covariance factors Mw and cutoff exponents tau) and a grow-only workspace
+// that keeps the per-(Gaussian, cell) records, the depth-ordered tile bins and
+// the sort buffers resident between calls.  A render is one pass of:
+//   pose prep -> cell prep -> record prep -> (one counter read-back) ->
+//   binning (radix sorts) -> per-pixel render,
+// all enqueued on the caller's stream.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ar.h"
+#include "ar_bin.h"
+#include "ar_common.cuh"
+#include "ar_launch.h"
+#include "ar_host.h"
+
+namespace ar {
+size_t cell_data_bytes_m1();
+size_t cell_data_bytes_m4();
+size_t cell_data_bytes_m6();
+int rec_width_m1();
+int rec_width_m4();
+int rec_width_m6();
+int launch_cell_prep_m1(const double *, const double *, const CallConst &, void *, cudaStream_t);
+int launch_cell_prep_m4(const double *, const double *, const CallConst &, void *, cudaStream_t);
+int launch_cell_prep_m6(const double *, const double *, const CallConst &, void *, cudaStream_t);
+int launch_record_prep_m1(const double *, const double *, const float *, const float *, const CallConst &,
+                          const void *, int, float *, PixBox *, double *, unsigned long long *, cudaStream_t);
+int launch_record_prep_m4(const double *, const double *, const float *, const float *, const CallConst &,
+                          const void *, int, float *, PixBox *, double *, unsigned long long *, cudaStream_t);
+int launch_record_prep_m6(const double *, const double *, const float *, const float *, const CallConst &,
+                          const void *, int, float *, PixBox *, double *, unsigned long long *, cudaStream_t);
+int launch_render_m1(int, const RenderLaunch &, cudaStream_t);
+int launch_render_m4(int, const RenderLaunch &, cudaStream_t);
+int launch_render_m6(int, const RenderLaunch &, cudaStream_t);
+
+size_t cell_data_bytes(int M)
+{
+    return M == 1 ? cell_data_bytes_m1() : (M == 4 ? cell_data_bytes_m4() : cell_data_bytes_m6());
+}
+int rec_width(int M) { return M == 1 ? rec_width_m1() : (M == 4 ? rec_width_m4() : rec_width_m6()); }
+int launch_cell_prep(int M, const double *lo, const double *hi, const CallConst &cc, void *cells, cudaStream_t st)
+{
+    return M == 1 ? launch_cell_prep_m1(lo, hi, cc, cells, st)
+                  : (M == 4 ? launch_cell_prep_m4(lo, hi, cc, cells, st) : launch_cell_prep_m6(lo, hi, cc, cells, st));
+}
+int launch_record_prep(int M, const double *vN, const double *tau, const float *opac, const float *rgb,
+                       const CallConst &cc, const void *cells, int TS, float *recs, PixBox *boxes, double *keys,
+                       unsigned long long *counters, cudaStream_t st)
+{
+    if (M == 1) return launch_record_prep_m1(vN, tau, opac, rgb, cc, cells, TS, recs, boxes, keys, counters, st);
+    if (M == 4) return launch_record_prep_m4(vN, tau, opac, rgb, cc, cells, TS, recs, boxes, keys, counters, st);
+    return launch_record_prep_m6(vN, tau, opac, rgb, cc, cells, TS, recs, boxes, keys, counters, st);
+}
+int launch_render(int M, int TS, const RenderLaunch &a, cudaStream_t st)
+{
+    return M == 1 ? launch_render_m1(TS, a, st) : (M == 4 ? launch_render_m4(TS, a, st) : launch_render_m6(TS, a, st));
+}
+}  // namespace ar
+
+using namespace ar;
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_err;
+
+static int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CK(call)                                                                                     \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess) return fail(AR_EDEVICE, "%s: %s", #call, cudaGetErrorString(e_));     \
+    } while (0)
+
+const char *ar_last_error(void) { return g_err.c_str(); }
+
+// --------------------------------------------------------------- buffers
+namespace ar {
+
+int DevBuf::ensure(size_t bytes)
+{
+    if (bytes <= cap) return AR_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    size_t want = bytes + bytes / 4 + 256;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+        return fail(AR_ENOMEM, "device allocation of %zu bytes failed: %s", want, cudaGetErrorString(e));
+    }
+    cap = want;
+    return AR_OK;
+}
+
+void DevBuf::release()
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+}
+
+void Workspace::release()
+{
+    DevBuf *all[] = {&cells_lohi, &cells, &vN, &recs, &boxes, &keys, &counters, &evk0, &evk1, &evv0, &evv1,
+                     &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege, &out_lo,
+                     &out_hi};
+    for (DevBuf *b : all) b->release();
+    if (h_counters) cudaFreeHost(h_counters);
+    h_counters = nullptr;
+    if (ev_init)
+        for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+    ev_init = false;
+}
+
+size_t Workspace::bytes() const
+{
+    const DevBuf *all[] = {&cells_lohi, &cells, &vN, &recs, &boxes, &keys, &counters, &evk0, &evk1, &evv0, &evv1,
+                           &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege,
+                           &out_lo, &out_hi};
+    size_t s = 0;
+    for (const DevBuf *b : all) s += b->cap;
+    return s;
+}
+
+}  // namespace ar
+
+struct ar_scene {
+    int device = 0;
+    int64_t n = 0;
+    float *uw = nullptr, *ls = nullptr, *quat = nullptr, *opac = nullptr, *rgb = nullptr;
+    double *Mw = nullptr, *tau = nullptr;
+    Workspace ws;
+    bool profiling = false;
+    ar_render_stats stats;
+    cudaStream_t stats_stream = nullptr;
+};
+
+static bool finite3(const float *v, int64_t n, int k)
+{
+    for (int64_t i = 0; i < n * k; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+int ar_scene_create(const float *uw3, const float *logscale3, const float *quat4, const float *opacity,
+                    const float *rgb3, int64_t n, int device_ptrs, ar_scene **out)
+{
+    if (!out) return fail(AR_EINVAL, "out is null");
+    *out = nullptr;
+    if (n < 0) return fail(AR_EINVAL, "n < 0");
+    if (n > ((int64_t)1 << 30)) return fail(AR_EINVAL, "n > 2^30 Gaussians");
+    if (n > 0 && (!uw3 || !logscale3 || !quat4 || !opacity || !rgb3)) return fail(AR_EINVAL, "null array");
+    std::vector<float> h_uw, h_ls, h_q, h_o, h_c;
+    const float *src[5] = {uw3, logscale3, quat4, opacity, rgb3};
+    const int width[5] = {3, 3, 4, 1, 3};
+    std::vector<float> *dst[5] = {&h_uw, &h_ls, &h_q, &h_o, &h_c};
+    for (int a = 0; a < 5; ++a) {
+        dst[a]->resize((size_t)n * width[a]);
+        if (n == 0) continue;
+        if (device_ptrs) {
+            cudaError_t e = cudaMemcpy(dst[a]->data(), src[a], sizeof(float) * n * width[a], cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return fail(AR_EINVAL, "cannot read device array %d: %s", a, cudaGetErrorString(e));
+        } else {
+            std::memcpy(dst[a]->data(), src[a], sizeof(float) * n * width[a]);
+        }
+    }
+    for (int a = 0; a < 5; ++a)
+        if (!finite3(dst[a]->data(), n, width[a])) return fail(AR_EINVAL, "non-finite value in input array %d", a);
+    for (int64_t i = 0; i < n; ++i) {
+        if (!(h_o[i] >= 0.f && h_o[i] < 1.f)) return fail(AR_EINVAL, "opacity[%lld] outside [0, 1)", (long long)i);
+        for (int k = 0; k < 3; ++k)
+            if (!(h_c[3 * i + k] >= 0.f && h_c[3 * i + k] <= 1.f))
+                return fail(AR_EINVAL, "rgb[%lld] outside [0, 1]", (long long)i);
+        const float *q = &h_q[4 * i];
+        if (q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3] == 0.f)
+            return fail(AR_EINVAL, "quaternion %lld is zero", (long long)i);
+        for (int k = 0; k < 3; ++k)
+            if (!(std::fabs(h_ls[3 * i + k]) < 40.f)) return fail(AR_EINVAL, "log-scale %lld out of range", (long long)i);
+    }
+    ar_scene *s = new ar_scene();
+    cudaGetDevice(&s->device);
+    s->n = n;
+    std::memset(&s->stats, 0, sizeof s->stats);
+    if (n > 0) {
+        float **dp[5] = {&s->uw, &s->ls, &s->quat, &s->opac, &s->rgb};
+        for (int a = 0; a < 5; ++a) {
+            if (cudaMalloc(dp[a], sizeof(float) * n * width[a]) != cudaSuccess ||
+                cudaMemcpy(*dp[a], dst[a]->data(), sizeof(float) * n * width[a], cudaMemcpyHostToDevice) != cudaSuccess) {
+                cudaGetLastError();
+                ar_scene_destroy(s);
+                return fail(AR_ENOMEM, "scene upload failed");
+            }
+        }
+        if (cudaMalloc(&s->Mw, sizeof(double) * 9 * n) != cudaSuccess ||
+            cudaMalloc(&s->tau, sizeof(double) * n) != cudaSuccess) {
+            cudaGetLastError();
+            ar_scene_destroy(s);
+            return fail(AR_ENOMEM, "scene allocation failed");
+        }
+        if (launch_scene_prep(s->ls, s->quat, s->opac, n, s->Mw, s->tau, 0) || cudaDeviceSynchronize() != cudaSuccess) {
+            const char *m = cudaGetErrorString(cudaGetLastError());
+            ar_scene_destroy(s);
+            return fail(AR_EDEVICE, "scene preprocessing failed: %s", m);
+        }
+    }
+    *out = s;
+    return AR_OK;
+}
+
+int ar_scene_destroy(ar_scene *s)
+{
+    if (!s) return fail(AR_EINVAL, "scene is null");
+    cudaSetDevice(s->device);
+    cudaDeviceSynchronize();
+    void *ptrs[] = {s->uw, s->ls, s->quat, s->opac, s->rgb, s->Mw, s->tau};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    s->ws.release();
+    delete s;
+    return AR_OK;
+}
+
+int ar_set_profiling(ar_scene *s, int on)
+{
+    if (!s) return fail(AR_EINVAL, "scene is null");
+    s->profiling = on != 0;
+    return AR_OK;
+}
+
+// ---------------------------------------------------------------- render
+namespace ar {
+
+int validate_call(const ar_intrinsics *in, const ar_nominal_pose *pose, const ar_pose_box *cells, int32_t n_cells,
+                  int32_t tile)
+{
+    if (!in || !pose || !cells) return fail(AR_EINVAL, "null argument");
+    if (n_cells < 1 || n_cells > 65535) return fail(AR_EINVAL, "n_cells must be in [1, 65535]");
+    if (in->width < 1 || in->height < 1 || in->width > 16384 || in->height > 16384)
+        return fail(AR_EINVAL, "image size out of range");
+    const float f[5] = {in->fx, in->fy, in->cx, in->cy, in->near_plane};
+    for (float v : f)
+        if (!std::isfinite(v)) return fail(AR_EINVAL, "non-finite intrinsics");
+    if (!(in->fx > 0 && in->fy > 0 && in->near_plane > 0)) return fail(AR_EINVAL, "fx, fy, near_plane must be > 0");
+    for (int i = 0; i < 9; ++i)
+        if (!std::isfinite(pose->R_wc[i])) return fail(AR_EINVAL, "non-finite rotation");
+    for (int i = 0; i < 3; ++i)
+        if (!std::isfinite(pose->t[i])) return fail(AR_EINVAL, "non-finite camera centre");
+    for (int c = 0; c < n_cells; ++c)
+        for (int k = 0; k < MAXV; ++k) {
+            const double lo = cells[c].lo[k], hi = cells[c].hi[k];
+            if (!std::isfinite(lo) || !std::isfinite(hi) || lo > hi)
+                return fail(AR_EINVAL, "cell %d dimension %d: need finite lo <= hi", c, k);
+            if (k >= 3 && (hi - lo) > 0.5) return fail(AR_EINVAL, "cell %d: rotation width above 0.5 rad", c);
+        }
+    if (tile != 0 && tile != 8 && tile != 16) return fail(AR_EINVAL, "tile must be 0, 8 or 16");
+    return AR_OK;
+}
+
+#define RK(x)                      \
+    do {                           \
+        int r_ = (x);              \
+        if (r_) return r_;         \
+    } while (0)
+
+int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_nominal_pose *pose,
+                const ar_pose_box *cells, int32_t n_cells, int32_t tile, float *out_lo, float *out_hi,
+                cudaStream_t st, bool profiling, ar_render_stats *stats)
+{
+    RK(validate_call(in, pose, cells, n_cells, tile));
+    if (!out_lo || !out_hi) return fail(AR_EINVAL, "null output");
+    CK(cudaSetDevice(s->device));
+    const int W = in->width, H = in->height;
+    const int TS = tile ? tile : 16;
+    const size_t out_words = (size_t)n_cells * W * H * 3;
+    ar_render_stats rs;
+    std::memset(&rs, 0, sizeof rs);
+    rs.tile = TS;
+    rs.ms_prep = rs.ms_bin = rs.ms_render = rs.ms_total = -1.f;
+    // active pose variables -> form slots
+    CallConst cc;
+    std::memset(&cc, 0, sizeof cc);
+    int m_active = 0;
+    for (int k = 0; k < MAXV; ++k) {
+        bool act = false;
+        for (int c = 0; c < n_cells; ++c) act = act || cells[c].hi[k] > cells[c].lo[k];
+        cc.m_slot[k] = act ? m_active++ : -1;
+    }
+    const int M = m_active <= 1 ? 1 : (m_active <= 4 ? 4 : 6);
+    rs.m_vars = M;
+    cc.W = W; cc.H = H;
+    cc.fx = in->fx; cc.fy = in->fy; cc.cx = in->cx; cc.cy = in->cy; cc.near_plane = in->near_plane;
+    std::memcpy(cc.R0, pose->R_wc, sizeof cc.R0);
+    std::memcpy(cc.t0, pose->t, sizeof cc.t0);
+    cc.n_cells = n_cells;
+    cc.n_gauss = s->n;
+    const uint64_t n_pairs = (uint64_t)n_cells * (uint64_t)s->n;
+    if (n_pairs >= (1ull << 31)) return fail(AR_ENOMEM, "cells x Gaussians = %llu >= 2^31; split the cells", (unsigned long long)n_pairs);
+    const int ntx = (W + TS - 1) / TS, nty = (H + TS - 1) / TS, n_tiles = ntx * nty;
+    const uint64_t n_seg = (uint64_t)n_cells * n_tiles;
+    if (n_seg >= (1ull << 31)) return fail(AR_EINVAL, "too many (cell, tile) segments");
+    if (s->n == 0) {
+        CK(cudaMemsetAsync(out_lo, 0, out_words * sizeof(float), st));
+        CK(cudaMemsetAsync(out_hi, 0, out_words * sizeof(float), st));
+        if (stats) *stats = rs;
+        return AR_OK;
+    }
+    if (!ws.ev_init) {
+        for (int i = 0; i < 4; ++i) CK(cudaEventCreate(&ws.ev[i]));
+        ws.ev_init = true;
+    }
+    if (!ws.h_counters) CK(cudaMallocHost(&ws.h_counters, 8 * sizeof(unsigned long long)));
+    int launches = 0;
+    // -- prep
+    RK(ws.cells_lohi.ensure(sizeof(double) * 12 * n_cells));
+    RK(ws.cells.ensure(cell_data_bytes(M) * n_cells));
+    RK(ws.vN.ensure(sizeof(double) * 12 * s->n));
+    RK(ws.recs.ensure(sizeof(float) * rec_width(M) * n_pairs));
+    RK(ws.boxes.ensure(sizeof(PixBox) * n_pairs));
+    RK(ws.keys.ensure(sizeof(double) * 2 * n_pairs));
+    RK(ws.counters.ensure(sizeof(unsigned long long) * 8));
+    {
+        std::vector<double> lohi((size_t)12 * n_cells);
+        for (int c = 0; c < n_cells; ++c)
+            for (int k = 0; k < MAXV; ++k) {
+                lohi[(size_t)MAXV * c + k] = cells[c].lo[k];
+                lohi[(size_t)MAXV * n_cells + (size_t)MAXV * c + k] = cells[c].hi[k];
+            }
+        CK(cudaMemcpyAsync(ws.cells_lohi.p, lohi.data(), sizeof(double) * lohi.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));  // the host vector is released on return
+    }
+    const double *d_lo = ws.cells_lohi.as<double>(), *d_hi = d_lo + (size_t)MAXV * n_cells;
+    if (profiling) CK(cudaEventRecord(ws.ev[0], st));
+    CK(cudaMemsetAsync(ws.counters.p, 0, sizeof(unsigned long long) * 8, st));
+    if (launch_pose_prep(s->uw, s->Mw, s->n, cc, ws.vN.as<double>(), st)) return fail(AR_EDEVICE, "pose_prep launch");
+    if (launch_cell_prep(M, d_lo, d_hi, cc, ws.cells.p, st)) return fail(AR_EDEVICE, "cell_prep launch");
+    if (launch_record_prep(M, ws.vN.as<double>(), s->tau, s->opac, s->rgb, cc, ws.cells.p, TS, ws.recs.as<float>(),
+                           ws.boxes.as<PixBox>(), ws.keys.as<double>(), ws.counters.as<unsigned long long>(), st))
+        return fail(AR_EDEVICE, "record_prep launch: %s", cudaGetErrorString(cudaGetLastError()));
+    launches += 3;
+    if (profiling) CK(cudaEventRecord(ws.ev[1], st));
+    CK(cudaMemcpyAsync(ws.h_counters, ws.counters.p, sizeof(unsigned long long) * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const unsigned long long n_valid = ws.h_counters[2];
+    rs.n_records = (int64_t)n_valid;
+    rs.n_triples = (int64_t)ws.h_counters[0];
+    rs.n_fallback = (int64_t)ws.h_counters[1];
+    const uint64_t ne = 2 * n_valid, nent = 2 * ws.h_counters[3];
+    rs.n_entries = (int64_t)(nent / 2);
+    if (nent >= (1ull << 32) - (1ull << 20))
+        return fail(AR_ENOMEM, "%llu bin entries exceed the 32-bit index range; use fewer cells per call",
+                    (unsigned long long)nent);
+    // -- binning
+    const uint64_t nsc = n_pairs > ne ? n_pairs : ne;
+    const uint64_t nsort = ne > nent ? ne : nent;
+    const uint64_t hist_words = radix_hist_words(nsort) + 64;
+    uint64_t scan_len = nsc > hist_words ? nsc : hist_words;
+    RK(ws.evk0.ensure(sizeof(uint64_t) * (ne + 1)));
+    RK(ws.evk1.ensure(sizeof(uint64_t) * (ne + 1)));
+    RK(ws.evv0.ensure(sizeof(uint32_t) * (ne + 1)));
+    RK(ws.evv1.ensure(sizeof(uint32_t) * (ne + 1)));
+    RK(ws.ents0.ensure(sizeof(uint32_t) * (nent + 1)));
+    RK(ws.ents1.ensure(sizeof(uint32_t) * (nent + 1)));
+    RK(ws.ente0.ensure(sizeof(uint32_t) * (nent + 1)));
+    RK(ws.ente1.ensure(sizeof(uint32_t) * (nent + 1)));
+    RK(ws.ua.ensure(sizeof(uint32_t) * (nsc + 1)));
+    RK(ws.ub.ensure(sizeof(uint32_t) * (nsc + 1)));
+    RK(ws.uc.ensure(sizeof(uint32_t) * (nsc + 1)));
+    RK(ws.ud.ensure(sizeof(uint32_t) * (nsc + 1)));
+    RK(ws.hist.ensure(sizeof(uint32_t) * hist_words));
+    RK(ws.scan.ensure(sizeof(uint32_t) * (scan_temp_words(scan_len) + 64)));
+    RK(ws.segs.ensure(sizeof(uint32_t) * n_seg));
+    RK(ws.sege.ensure(sizeof(uint32_t) * n_seg));
+    BinArgs ba;
+    ba.boxes = ws.boxes.as<PixBox>();
+    ba.keys = ws.keys.as<double>();
+    ba.n_pairs = n_pairs;
+    ba.n_gauss = (uint64_t)s->n;
+    ba.n_cells = n_cells;
+    ba.n_events = ne;
+    ba.n_entries = nent;
+    ba.TS = TS; ba.ntx = ntx; ba.n_tiles = n_tiles;
+    ba.n_segments = n_seg;
+    ba.ev_key[0] = ws.evk0.as<uint64_t>(); ba.ev_key[1] = ws.evk1.as<uint64_t>();
+    ba.ev_val[0] = ws.evv0.as<uint32_t>(); ba.ev_val[1] = ws.evv1.as<uint32_t>();
+    ba.ent_seg[0] = ws.ents0.as<uint32_t>(); ba.ent_seg[1] = ws.ents1.as<uint32_t>();
+    ba.ent_ev[0] = ws.ente0.as<uint32_t>(); ba.ent_ev[1] = ws.ente1.as<uint32_t>();
+    ba.u32_a = ws.ua.as<uint32_t>(); ba.u32_b = ws.ub.as<uint32_t>();
+    ba.u32_c = ws.uc.as<uint32_t>(); ba.u32_d = ws.ud.as<uint32_t>();
+    ba.hist = ws.hist.as<uint32_t>();
+    ba.scan_tmp = ws.scan.as<uint32_t>();
+    ba.seg_start = ws.segs.as<uint32_t>();
+    ba.seg_end = ws.sege.as<uint32_t>();
+    BinOut bo;
+    if (run_binning(ba, bo, st, &launches))
+        return fail(AR_EDEVICE, "binning: %s", cudaGetErrorString(cudaGetLastError()));
+    if (profiling) CK(cudaEventRecord(ws.ev[2], st));
+    // -- per-pixel bounds
+    RenderLaunch rl;
+    rl.recs = ws.recs.as<float>();
+    rl.boxes = ws.boxes.as<PixBox>();
+    rl.seg_start = ws.segs.as<uint32_t>();
+    rl.seg_end = ws.sege.as<uint32_t>();
+    rl.ent_ev = bo.ent_ev;
+    rl.ev_val = bo.ev_val;
+    rl.ev_key = bo.ev_key;
+    rl.W = W; rl.H = H; rl.ntx = ntx; rl.n_tiles = n_tiles; rl.n_cells = n_cells;
+    rl.n_gauss = s->n;
+    rl.out_lo = out_lo;
+    rl.out_hi = out_hi;
+    if (launch_render(M, TS, rl, st)) return fail(AR_EDEVICE, "render launch: %s", cudaGetErrorString(cudaGetLastError()));
+    ++launches;
+    if (profiling) CK(cudaEventRecord(ws.ev[3], st));
+    rs.n_launches = launches;
+    if (stats) *stats = rs;
+    return AR_OK;
+}
+
+int finish_stats(Workspace &ws, cudaStream_t st, bool profiling, ar_render_stats &rs)
+{
+    CK(cudaStreamSynchronize(st));
+    if (profiling && ws.ev_init && rs.n_records > 0) {
+        CK(cudaEventElapsedTime(&rs.ms_prep, ws.ev[0], ws.ev[1]));
+        CK(cudaEventElapsedTime(&rs.ms_bin, ws.ev[1], ws.ev[2]));
+        CK(cudaEventElapsedTime(&rs.ms_render, ws.ev[2], ws.ev[3]));
+        CK(cudaEventElapsedTime(&rs.ms_total, ws.ev[0], ws.ev[3]));
+    }
+    return AR_OK;
+}
+
+}  // namespace ar
+
+int ar_render_abstract(ar_scene *s, const ar_intrinsics *in, const ar_nominal_pose *pose, const ar_pose_box *cells,
+                       int32_t n_cells, int32_t tile, float *out_lower, float *out_upper, void *stream)
+{
+    if (!s) return fail(AR_EINVAL, "scene is null");
+    cudaStream_t st = (cudaStream_t)stream;
+    int r = render_core(s, s->ws, in, pose, cells, n_cells, tile, out_lower, out_upper, st, s->profiling, &s->stats);
+    s->stats_stream = st;
+    return r;
+}
+
+int ar_render_abstract_host(ar_scene *s, const ar_intrinsics *in, const ar_nominal_pose *pose,
+                            const ar_pose_box *cells, int32_t n_cells, int32_t tile, float *host_lower,
+                            float *host_upper, void *stream)
+{
+    if (!s) return fail(AR_EINVAL, "scene is null");
+    if (!host_lower || !host_upper) return fail(AR_EINVAL, "null output");
+    RK(validate_call(in, pose, cells, n_cells, tile));
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = sizeof(float) * 3 * (size_t)in->width * in->height * n_cells;
+    CK(cudaSetDevice(s->device));
+    RK(s->ws.out_lo.ensure(bytes));
+    RK(s->ws.out_hi.ensure(bytes));
+    RK(render_core(s, s->ws, in, pose, cells, n_cells, tile, s->ws.out_lo.as<float>(), s->ws.out_hi.as<float>(), st,
+                   s->profiling, &s->stats));
+    s->stats_stream = st;
+    CK(cudaMemcpyAsync(host_lower, s->ws.out_lo.p, bytes, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(host_upper, s->ws.out_hi.p, bytes, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return AR_OK;
+}
+
+int ar_last_render_stats(ar_scene *s, ar_render_stats *out)
+{
+    if (!s || !out) return fail(AR_EINVAL, "null argument");
+    RK(finish_stats(s->ws, s->stats_stream, s->profiling, s->stats));
+    *out = s->stats;
+    return AR_OK;
+}
+
+int ar_render_abstract_plain_fp64(ar_scene *s, const ar_intrinsics *in, const ar_nominal_pose *pose,
+                                  const ar_pose_box *cells, int32_t n_cells, int32_t tile, float *out_lower,
+                                  float *out_upper, void *stream)
+{
+    (void)s; (void)in; (void)pose; (void)cells; (void)n_cells; (void)tile; (void)out_lower; (void)out_upper;
+    (void)stream;
+    return fail(AR_EINVAL, "plain FP64 path not built in this library version");
+}
+
+int ar_render_concrete(ar_scene *s, const ar_intrinsics *in, const ar_nominal_pose *pose, const double *deltas,
+                       int32_t n_poses, float *out, void *stream)
+{
+    (void)s; (void)in; (void)pose; (void)deltas; (void)n_poses; (void)out; (void)stream;
+    return fail(AR_EINVAL, "concrete renderer not built in this library version");
+}

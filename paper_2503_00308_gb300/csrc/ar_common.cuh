@@ -1,0 +1,180 @@
+// ar_common.cuh -- data layout shared by the abstract-rendering kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ar_num.cuh"
+
+namespace ar {
+
+// Algorithm constants (the relaxation choices of the abstract renderer).
+constexpr int KTAYLOR = 8;                       // MatrixInv order, k = 8 (Sec. 3.3 footnote)
+constexpr double RHO_MAX = 1.0 - 1.0 / 1024.0;   // MatrixInv used while ||I - X X0|| < RHO_MAX
+constexpr float CUT_RAMP = 0.5f;                 // widest cutoff ramp (units of m)
+constexpr float CLIP_RAMP = 0.25f;               // upper-alpha blend toward o
+constexpr double KEY_SLACK = 1e-9;               // relative widening of depth keys
+constexpr double BOX_SLACK = 1e-9;               // relative widening of screen boxes
+constexpr float ALPHA_MIN_UP = 0.003921568859368563f;  // 1/255 rounded up to float
+
+constexpr int MAXV = 6;  // pose variables tx ty tz rx ry rz
+
+// Per-call pose-cell data produced by the cell kernel.
+//   FP64 part (decision chain): forms over the M active variables, computed
+//   round-to-nearest in the order the CPU reference uses.
+//   FP32 part (value chain): the same forms widened outward to float.
+template <int M> struct CellData {
+    double rd_lo[9][M + 1], rd_hi[9][M + 1];  // R_delta entries (coefficients, then constant)
+    double s[3][M + 1];                       // s = R_wc * delta_t (exact)
+    double g[M];                              // depth-key offset (translation part of d)
+    double rd_int[9][2];                      // concretised R_delta entries
+    double s_int[3][2];                       // concretised s
+    BS<M, float> rd32[9];
+    BS<M, float> s32[3];
+    BS<M, double> rd64[9];  // the same forms widened by a relative 1e-14 (sound in FP64)
+    BS<M, double> s64[3];
+};
+
+// Per-(Gaussian, cell) record read by the per-pixel kernel.  Offsets in
+// floats; F = M + 1 is the length of one form.
+//
+// Delta = S u - P (Algorithm 1 line 9 with S = d^2, P = d up) is stored as
+//   Delta.lo = (u - mu) S.lo + R.lo,  R.lo = mu S.lo - P.hi,
+//   Delta.hi = (u - mu) S.hi + R.hi,  R.hi = mu S.hi - P.lo,
+// with mu a pixel centre near the projected mean: algebraically the same
+// forms as u S.lo - P.hi and u S.hi - P.lo, but the large, nearly cancelling
+// terms S u and P are combined once in FP64 instead of per pixel in FP32.
+template <int M> struct Rec {
+    static constexpr int F = M + 1;
+    static constexpr int S_LO = 0, S_HI = F, RX_LO = 2 * F, RX_HI = 3 * F, RY_LO = 4 * F, RY_HI = 5 * F;
+    static constexpr int RAD = 6 * F;          // radii of S.lo, S.hi, Rx.lo, Rx.hi, Ry.lo, Ry.hi
+    static constexpr int WSTRIDE = 2 * F + 4;  // lo form, hi form, vlo, vhi, rlo, rhi
+    static constexpr int W0 = RAD + 6;
+    static constexpr int SC = W0 + 6 * WSTRIDE;  // o, tau_dn, tau_up, c0, c1, c2, flags, mu_x, mu_y
+    static constexpr int O = SC, TAU_DN = SC + 1, TAU_UP = SC + 2, COL = SC + 3, FLAGS = SC + 6;
+    static constexpr int MU_X = SC + 7, MU_Y = SC + 8;
+    static constexpr int RAW = SC + 9;
+    static constexpr int WIDTH = (RAW + 3) / 4 * 4;  // 16-byte multiple
+};
+
+// record flags
+constexpr uint32_t F_FALLBACK = 1u;  // MatrixInv assertion failed: a in [0, o]
+constexpr uint32_t F_STRADDLE = 2u;  // depth may cross the near plane: lower alpha is 0
+constexpr uint32_t F_OPEN = 4u;      // depth-key interval has positive width
+
+// Pixel box of a (Gaussian, cell) pair: x0 < 0 marks "contributes nowhere".
+struct PixBox {
+    int x0, x1, y0, y1;
+};
+
+// ---------------------------------------------------------------------------
+// Plain FP64 forms for the decision chain (round-to-nearest, no contraction).
+template <int M> struct DF {
+    double c[M];
+    double k;
+};
+template <int M> struct DB {
+    DF<M> lo, hi;
+};
+
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+
+template <int M> __device__ __forceinline__ double df_min(const DF<M> &f)
+{
+    double s = f.k;
+#pragma unroll
+    for (int j = 0; j < M; ++j) s = dsub(s, fabs(f.c[j]));
+    return s;
+}
+template <int M> __device__ __forceinline__ double df_max(const DF<M> &f)
+{
+    double s = f.k;
+#pragma unroll
+    for (int j = 0; j < M; ++j) s = dadd(s, fabs(f.c[j]));
+    return s;
+}
+template <int M> __device__ __forceinline__ DF<M> df_scale(const DF<M> &a, double s)
+{
+    DF<M> r;
+#pragma unroll
+    for (int j = 0; j < M; ++j) r.c[j] = dmul(s, a.c[j]);
+    r.k = dmul(s, a.k);
+    return r;
+}
+template <int M> __device__ __forceinline__ DF<M> df_add(const DF<M> &a, const DF<M> &b)
+{
+    DF<M> r;
+#pragma unroll
+    for (int j = 0; j < M; ++j) r.c[j] = dadd(a.c[j], b.c[j]);
+    r.k = dadd(a.k, b.k);
+    return r;
+}
+template <int M> __device__ __forceinline__ DF<M> df_sub(const DF<M> &a, const DF<M> &b)
+{
+    DF<M> r;
+#pragma unroll
+    for (int j = 0; j < M; ++j) r.c[j] = dsub(a.c[j], b.c[j]);
+    r.k = dsub(a.k, b.k);
+    return r;
+}
+template <int M> __device__ __forceinline__ DB<M> db_add(const DB<M> &a, const DB<M> &b)
+{
+    DB<M> r;
+    r.lo = df_add(a.lo, b.lo);
+    r.hi = df_add(a.hi, b.hi);
+    return r;
+}
+// averaged McCormick planes (same statement as the single-precision Mul)
+template <int M> __device__ __forceinline__ DB<M> db_mul(const DB<M> &x, const DB<M> &y)
+{
+    double xl = df_min(x.lo), xh = df_max(x.hi), yl = df_min(y.lo), yh = df_max(y.hi);
+    double xm = dmul(0.5, dadd(xl, xh)), ym = dmul(0.5, dadd(yl, yh));
+    DB<M> r;
+    r.lo = df_add(df_scale(ym >= 0 ? x.lo : x.hi, ym), df_scale(xm >= 0 ? y.lo : y.hi, xm));
+    r.lo.k = dsub(r.lo.k, dmul(0.5, dadd(dmul(xl, yl), dmul(xh, yh))));
+    r.hi = df_add(df_scale(ym >= 0 ? x.hi : x.lo, ym), df_scale(xm >= 0 ? y.hi : y.lo, xm));
+    r.hi.k = dsub(r.hi.k, dmul(0.5, dadd(dmul(xh, yl), dmul(xl, yh))));
+    return r;
+}
+
+// intervals for the screen box
+struct DI {
+    double l, u;
+};
+__device__ __forceinline__ DI di_mul(DI a, DI b)
+{
+    double p0 = dmul(a.l, b.l), p1 = dmul(a.l, b.u), p2 = dmul(a.u, b.l), p3 = dmul(a.u, b.u);
+    DI r = {p0, p0};
+    r.l = fmin(r.l, p1); r.u = fmax(r.u, p1);
+    r.l = fmin(r.l, p2); r.u = fmax(r.u, p2);
+    r.l = fmin(r.l, p3); r.u = fmax(r.u, p3);
+    return r;
+}
+__device__ __forceinline__ DI di_add(DI a, DI b) { return DI{dadd(a.l, b.l), dadd(a.u, b.u)}; }
+__device__ __forceinline__ DI di_scale(DI a, double s)
+{
+    return s >= 0 ? DI{dmul(s, a.l), dmul(s, a.u)} : DI{dmul(s, a.u), dmul(s, a.l)};
+}
+__device__ __forceinline__ double di_sqmax(DI a) { return fmax(dmul(a.l, a.l), dmul(a.u, a.u)); }
+
+// order-preserving map of a double to uint64 (-0 folded onto +0)
+__device__ __forceinline__ uint64_t key_bits(double x)
+{
+    if (x == 0.0) x = 0.0;
+    uint64_t b = (uint64_t)__double_as_longlong(x);
+    return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// Camera / call constants passed by value to the kernels.
+struct CallConst {
+    int W, H;
+    float fx, fy, cx, cy, near_plane;
+    double R0[9];
+    double t0[3];
+    int n_cells;
+    int64_t n_gauss;
+    int m_slot[MAXV];  // slot of each pose variable in the forms, -1 if inactive
+};
+
+}  // namespace ar

@@ -1,0 +1,41 @@
+// ar_host.h -- host-side device-memory helpers of libar.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "ar.h"
+
+namespace ar {
+
+// Grow-only device buffer.
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    int ensure(size_t bytes);  // AR_OK or AR_ENOMEM (sets the thread's error message)
+    void release();
+    template <class T> T *as() const { return (T *)p; }
+};
+
+// Everything one render needs besides the scene itself.  A scene owns one
+// workspace; a server owns one per slot so that concurrent requests never
+// share buffers.
+struct Workspace {
+    DevBuf cells_lohi, cells, vN, recs, boxes, keys, counters;
+    DevBuf evk0, evk1, evv0, evv1, ents0, ents1, ente0, ente1;
+    DevBuf ua, ub, uc, ud, hist, scan, segs, sege;
+    DevBuf out_lo, out_hi;
+    unsigned long long *h_counters = nullptr;  // page-locked
+    cudaEvent_t ev[4];
+    bool ev_init = false;
+    void release();
+    size_t bytes() const;
+};
+
+int validate_call(const ar_intrinsics *in, const ar_nominal_pose *pose, const ar_pose_box *cells, int32_t n_cells,
+                  int32_t tile);
+int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_nominal_pose *pose,
+                const ar_pose_box *cells, int32_t n_cells, int32_t tile, float *out_lo, float *out_hi,
+                cudaStream_t st, bool profiling, ar_render_stats *stats);
+
+}  // namespace ar

@@ -1,0 +1,34 @@
+// ar_launch.h -- host launchers of the per-M kernels (instantiated for the
+// numbers of pose variables M in {1, 4, 6} carried by the linear forms).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ar {
+
+struct CallConst;
+struct PixBox;
+
+struct RenderLaunch {
+    const float *recs;
+    const PixBox *boxes;
+    const uint32_t *seg_start, *seg_end, *ent_ev, *ev_val;
+    const uint64_t *ev_key;
+    int W, H, ntx, n_tiles, n_cells;
+    int64_t n_gauss;
+    float *out_lo, *out_hi;
+};
+
+size_t cell_data_bytes(int M);
+int rec_width(int M);
+int launch_cell_prep(int M, const double *lo, const double *hi, const CallConst &cc, void *cells, cudaStream_t st);
+int launch_record_prep(int M, const double *vN, const double *tau, const float *opac, const float *rgb,
+                       const CallConst &cc, const void *cells, int TS, float *recs, PixBox *boxes, double *keys,
+                       unsigned long long *counters, cudaStream_t st);
+int launch_render(int M, int TS, const RenderLaunch &a, cudaStream_t st);
+int launch_scene_prep(const float *logscale, const float *quat, const float *opacity, int64_t n, double *Mw,
+                      double *tau, cudaStream_t st);
+int launch_pose_prep(const float *uw, const double *Mw, int64_t n, const CallConst &cc, double *vN,
+                     cudaStream_t st);
+
+}  // namespace ar

@@ -1,0 +1,260 @@
+// ar_num.cuh -- sound linear bounds over a pose cell, in directed rounding.
+//
+// A pose cell is a box; every pose variable is normalised to p in [-1, 1]^M.
+// A bounded scalar BS holds two affine forms lo(p) <= v <= hi(p) (the
+// piecewise-linear relations of Sec. 2.1 with one piece) plus their
+// concretisation over the box: vlo = min lo, vhi = max hi, and the radii
+// rlo = sum |lo.c|, rhi = sum |hi.c|.
+//
+// Soundness in floating point: coefficients are computed round-to-nearest and
+// the worst-case rounding error of every coefficient, summed over the box
+// (|p_j| <= 1), is moved into the constant term, which itself is computed in
+// the outward rounding direction (down for lower forms, up for upper forms).
+// For a sum of n products a_t * F_t accumulated by a chain of n FMAs, the error
+// of each coefficient is at most n u (1 + u)^n sum_t |a_t F_tj| (u = unit
+// roundoff), so the constant moves by gamma_n * sum_t |a_t| r_t with r_t the
+// radius of F_t.  A tiny absolute term covers subnormal rounding.
+//
+// The relaxations are the ones the abstract-rendering construction uses:
+//   Mul x*y : averaged McCormick planes, y_m x + x_m y - (x_lo y_lo + x_hi y_hi)/2
+//             below and y_m x + x_m y - (x_hi y_lo + x_lo y_hi)/2 above;
+//   Sqr x^2 : tangent at the midpoint below, secant above;
+//   Exp     : tangent at the lower end below, secant above (Table 2).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ar {
+
+template <class R> struct Num;
+
+template <> struct Num<float> {
+    static constexpr float U = 5.9604644775390625e-8f;  // 2^-24
+    static constexpr float TINY = 1e-36f;
+    static constexpr float BIG = 3.0e38f;
+    __device__ static __forceinline__ float add_rd(float a, float b) { return __fadd_rd(a, b); }
+    __device__ static __forceinline__ float add_ru(float a, float b) { return __fadd_ru(a, b); }
+    __device__ static __forceinline__ float sub_rd(float a, float b) { return __fsub_rd(a, b); }
+    __device__ static __forceinline__ float sub_ru(float a, float b) { return __fsub_ru(a, b); }
+    __device__ static __forceinline__ float mul_rd(float a, float b) { return __fmul_rd(a, b); }
+    __device__ static __forceinline__ float mul_ru(float a, float b) { return __fmul_ru(a, b); }
+    __device__ static __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+    __device__ static __forceinline__ float fma_rd(float a, float b, float c) { return __fmaf_rd(a, b, c); }
+    __device__ static __forceinline__ float fma_ru(float a, float b, float c) { return __fmaf_ru(a, b, c); }
+    __device__ static __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    __device__ static __forceinline__ float div_rd(float a, float b) { return __fdiv_rd(a, b); }
+    __device__ static __forceinline__ float div_ru(float a, float b) { return __fdiv_ru(a, b); }
+    __device__ static __forceinline__ float sqrt_ru(float a) { return __fsqrt_ru(a); }
+    __device__ static __forceinline__ float abs(float a) { return fabsf(a); }
+    __device__ static __forceinline__ float max(float a, float b) { return fmaxf(a, b); }
+    __device__ static __forceinline__ float min(float a, float b) { return fminf(a, b); }
+    // exp with its error bound: CUDA documents expf as within 2 ulp over its
+    // full range; 4 ulp (2^-21 relative) plus a subnormal floor is used here.
+    __device__ static __forceinline__ float exp_dn(float x)
+    {
+        float e = expf(x);
+        return fmaxf(0.f, __fsub_rd(__fmul_rd(e, 1.f - 4.76837158203125e-7f), 1e-44f));
+    }
+    __device__ static __forceinline__ float exp_up(float x)
+    {
+        float e = expf(x);
+        return __fadd_ru(__fmul_ru(e, 1.f + 4.76837158203125e-7f), 1e-44f);
+    }
+};
+
+template <> struct Num<double> {
+    static constexpr double U = 1.1102230246251565e-16;  // 2^-53
+    static constexpr double TINY = 1e-300;
+    static constexpr double BIG = 1.0e300;
+    __device__ static __forceinline__ double add_rd(double a, double b) { return __dadd_rd(a, b); }
+    __device__ static __forceinline__ double add_ru(double a, double b) { return __dadd_ru(a, b); }
+    __device__ static __forceinline__ double sub_rd(double a, double b) { return __dsub_rd(a, b); }
+    __device__ static __forceinline__ double sub_ru(double a, double b) { return __dsub_ru(a, b); }
+    __device__ static __forceinline__ double mul_rd(double a, double b) { return __dmul_rd(a, b); }
+    __device__ static __forceinline__ double mul_ru(double a, double b) { return __dmul_ru(a, b); }
+    __device__ static __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+    __device__ static __forceinline__ double fma_rd(double a, double b, double c) { return __fma_rd(a, b, c); }
+    __device__ static __forceinline__ double fma_ru(double a, double b, double c) { return __fma_ru(a, b, c); }
+    __device__ static __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+    __device__ static __forceinline__ double div_rd(double a, double b) { return __ddiv_rd(a, b); }
+    __device__ static __forceinline__ double div_ru(double a, double b) { return __ddiv_ru(a, b); }
+    __device__ static __forceinline__ double sqrt_ru(double a) { return __dsqrt_ru(a); }
+    __device__ static __forceinline__ double abs(double a) { return fabs(a); }
+    __device__ static __forceinline__ double max(double a, double b) { return fmax(a, b); }
+    __device__ static __forceinline__ double min(double a, double b) { return fmin(a, b); }
+    // CUDA documents exp (double) as within 1 ulp; 4 ulp are allowed here.
+    __device__ static __forceinline__ double exp_dn(double x)
+    {
+        double e = exp(x);
+        return fmax(0.0, __dsub_rd(__dmul_rd(e, 1.0 - 8.881784197001252e-16), 1e-320));
+    }
+    __device__ static __forceinline__ double exp_up(double x)
+    {
+        double e = exp(x);
+        return __dadd_ru(__dmul_ru(e, 1.0 + 8.881784197001252e-16), 1e-320);
+    }
+};
+
+template <int M, class R> struct LF {
+    R c[M];
+    R k;
+};
+
+template <int M, class R> struct BS {
+    LF<M, R> lo, hi;
+    R vlo, vhi;  // concretised bounds over the box
+    R rlo, rhi;  // radii of lo and hi (sum of |coefficients|, rounded up)
+};
+
+template <int M, class R>
+__device__ __forceinline__ void finish(BS<M, R> &b)
+{
+    using N = Num<R>;
+    R rl = 0, rh = 0;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        rl = N::add_ru(rl, N::abs(b.lo.c[j]));
+        rh = N::add_ru(rh, N::abs(b.hi.c[j]));
+    }
+    b.rlo = rl;
+    b.rhi = rh;
+    b.vlo = N::sub_rd(b.lo.k, rl);
+    b.vhi = N::add_ru(b.hi.k, rh);
+}
+
+template <int M, class R>
+__device__ __forceinline__ BS<M, R> cst(R lo, R hi)
+{
+    BS<M, R> b;
+#pragma unroll
+    for (int j = 0; j < M; ++j) { b.lo.c[j] = 0; b.hi.c[j] = 0; }
+    b.lo.k = lo; b.hi.k = hi;
+    b.vlo = lo; b.vhi = hi; b.rlo = 0; b.rhi = 0;
+    return b;
+}
+
+// Accumulator of a sound form  sum_t a_t F_t + b  (one side).  DN = true for
+// a lower form (constant rounded down, slack subtracted), false for upper.
+template <int M, class R, bool DN> struct Acc {
+    LF<M, R> f;
+    R rs;   // sum_t |a_t| r_t  (to be scaled by gamma_n)
+    R ex;   // extra absolute slack
+    int n;  // number of terms
+
+    __device__ __forceinline__ void init(R b)
+    {
+#pragma unroll
+        for (int j = 0; j < M; ++j) f.c[j] = 0;
+        f.k = b; rs = 0; ex = 0; n = 0;
+    }
+    __device__ __forceinline__ void add_const(R b)
+    {
+        using N = Num<R>;
+        f.k = DN ? N::add_rd(f.k, b) : N::add_ru(f.k, b);
+    }
+    __device__ __forceinline__ void add_slack(R s) { ex = Num<R>::add_ru(ex, s); }
+    // add a * F where F has radius r (the caller has chosen the side of F)
+    __device__ __forceinline__ void term(R a, const LF<M, R> &F, R r)
+    {
+        using N = Num<R>;
+#pragma unroll
+        for (int j = 0; j < M; ++j) f.c[j] = N::fma_rn(a, F.c[j], f.c[j]);
+        f.k = DN ? N::fma_rd(a, F.k, f.k) : N::fma_ru(a, F.k, f.k);
+        rs = N::fma_ru(N::abs(a), r, rs);
+        ++n;
+    }
+    __device__ __forceinline__ LF<M, R> result() const
+    {
+        using N = Num<R>;
+        // gamma_n = n u (1 + 2^-12) covers (1 + u)^n for n < 2^10
+        R g = N::mul_ru((R)n, N::mul_ru(N::U, (R)1.000244140625));
+        R s = N::add_ru(N::fma_ru(g, rs, ex), N::TINY);
+        LF<M, R> out = f;
+        out.k = DN ? N::sub_rd(f.k, s) : N::add_ru(f.k, s);
+        return out;
+    }
+};
+
+template <int M, class R> struct Pair {
+    Acc<M, R, true> lo;
+    Acc<M, R, false> hi;
+    __device__ __forceinline__ void init(R blo, R bhi) { lo.init(blo); hi.init(bhi); }
+    __device__ __forceinline__ BS<M, R> result() const
+    {
+        BS<M, R> b;
+        b.lo = lo.result();
+        b.hi = hi.result();
+        finish(b);
+        return b;
+    }
+    // + a * x   (a exact)
+    __device__ __forceinline__ void lin(R a, const BS<M, R> &x)
+    {
+        if (a >= 0) { lo.term(a, x.lo, x.rlo); hi.term(a, x.hi, x.rhi); }
+        else        { lo.term(a, x.hi, x.rhi); hi.term(a, x.lo, x.rlo); }
+    }
+    // + x * y  (averaged McCormick planes)
+    __device__ __forceinline__ void mul(const BS<M, R> &x, const BS<M, R> &y)
+    {
+        using N = Num<R>;
+        const R xl = x.vlo, xh = x.vhi, yl = y.vlo, yh = y.vhi;
+        const R xm = N::mul_rn(xl + xh, (R)0.5), ym = N::mul_rn(yl + yh, (R)0.5);
+        lin(ym, x);
+        lin(xm, y);
+        // constants: -(xl yl + xh yh)/2 below, -(xh yl + xl yh)/2 above
+        lo.add_const(-N::mul_ru(N::fma_ru(xl, yl, N::mul_ru(xh, yh)), (R)0.5));
+        hi.add_const(-N::mul_rd(N::fma_rd(xh, yl, N::mul_rd(xl, yh)), (R)0.5));
+        // the slopes are the rounded midpoints: cover |ym - y_mid| max|x| + ...
+        const R xa = N::max(N::abs(xl), N::abs(xh)), ya = N::max(N::abs(yl), N::abs(yh));
+        const R mid = N::mul_ru(N::fma_ru(N::abs(ym), xa, N::mul_ru(N::abs(xm), ya)), N::mul_ru(N::U, (R)1.001));
+        lo.add_slack(mid);
+        hi.add_slack(mid);
+    }
+    // + x^2  (tangent at the midpoint below, secant above)
+    __device__ __forceinline__ void sqr(const BS<M, R> &x)
+    {
+        using N = Num<R>;
+        const R xl = x.vlo, xh = x.vhi;
+        const R c = N::mul_rn(xl + xh, (R)0.5);
+        const R c2 = c + c;
+        if (c2 >= 0) lo.term(c2, x.lo, x.rlo); else lo.term(c2, x.hi, x.rhi);
+        lo.add_const(-N::mul_ru(c, c));
+        const R s = xl + xh;
+        if (s >= 0) hi.term(s, x.hi, x.rhi); else hi.term(s, x.lo, x.rlo);
+        hi.add_const(N::max(N::fma_ru(xl, xl, N::mul_ru(-s, xl)), N::fma_ru(xh, xh, N::mul_ru(-s, xh))));
+    }
+};
+
+template <int M, class R>
+__device__ __forceinline__ BS<M, R> b_mul(const BS<M, R> &x, const BS<M, R> &y)
+{
+    Pair<M, R> p; p.init(0, 0); p.mul(x, y); return p.result();
+}
+template <int M, class R>
+__device__ __forceinline__ BS<M, R> b_sqr(const BS<M, R> &x)
+{
+    Pair<M, R> p; p.init(0, 0); p.sqr(x); return p.result();
+}
+// a*x + b*y + c
+template <int M, class R>
+__device__ __forceinline__ BS<M, R> b_lin2(R a, const BS<M, R> &x, R b, const BS<M, R> &y, R c)
+{
+    Pair<M, R> p; p.init(c, c); p.lin(a, x); p.lin(b, y); return p.result();
+}
+template <int M, class R>
+__device__ __forceinline__ BS<M, R> b_add(const BS<M, R> &x, const BS<M, R> &y)
+{
+    return b_lin2<M, R>((R)1, x, (R)1, y, (R)0);
+}
+// x widened by e >= 0 on both sides
+template <int M, class R>
+__device__ __forceinline__ BS<M, R> b_widen(BS<M, R> x, R e)
+{
+    using N = Num<R>;
+    x.lo.k = N::sub_rd(x.lo.k, e);
+    x.hi.k = N::add_ru(x.hi.k, e);
+    finish(x);
+    return x;
+}
+
+}  // namespace ar

@@ -1,0 +1,381 @@
+// k_bin.cu -- screen-tile binning of (Gaussian, cell) pairs and depth-key
+// ordering of their endpoint events (the tile-based batching of Sec. 4,
+// "AbstractSplat on GPUs").
+//
+// Pipeline (all on the render stream):
+//   1. flags/scan   : compact the (cell, Gaussian) pairs that reach the image;
+//   2. events       : two per pair (lower / upper depth-key endpoint), keyed by
+//                     the order-preserving bits of the FP64 key;
+//   3. sort         : stable LSD radix sort by key, then stably by cell;
+//   4. entries      : each event is copied to every tile its pixel box meets,
+//                     in sorted-event order, keyed by segment = cell*tiles+tile;
+//   5. sort         : stable LSD radix sort by segment (keeps key order inside);
+//   6. bounds       : [start, end) of every segment.
+#include "ar_bin.h"
+#include "ar_common.cuh"
+
+namespace ar {
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_ROUNDS = 8;
+constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;  // items per block
+
+// ------------------------------------------------------------------ scan
+constexpr int SC_THREADS = 256;
+constexpr int SC_IPT = 8;
+constexpr int SC_TILE = SC_THREADS * SC_IPT;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s_warp, uint32_t &total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = (lane < SC_THREADS / 32) ? s_warp[lane] : 0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w += y;
+        }
+        if (lane < SC_THREADS / 32) s_warp[lane] = w;
+    }
+    __syncthreads();
+    total = s_warp[SC_THREADS / 32 - 1];
+    uint32_t excl = x - v + (warp > 0 ? s_warp[warp - 1] : 0);
+    __syncthreads();
+    return excl;
+}
+
+__global__ void __launch_bounds__(SC_THREADS) scan_sums_kernel(const uint32_t *__restrict__ in, uint32_t n,
+                                                               uint32_t *__restrict__ sums)
+{
+    __shared__ uint32_t s_warp[32];
+    const uint64_t base = (uint64_t)blockIdx.x * SC_TILE + (uint64_t)threadIdx.x * SC_IPT;
+    uint32_t t = 0;
+#pragma unroll
+    for (int i = 0; i < SC_IPT; ++i)
+        if (base + i < n) t += in[base + i];
+    uint32_t total;
+    block_exclusive_scan(t, s_warp, total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(SC_THREADS) scan_apply_kernel(const uint32_t *__restrict__ in, uint32_t n,
+                                                                const uint32_t *__restrict__ offs,
+                                                                uint32_t *__restrict__ out)
+{
+    __shared__ uint32_t s_warp[32];
+    const uint64_t base = (uint64_t)blockIdx.x * SC_TILE + (uint64_t)threadIdx.x * SC_IPT;
+    uint32_t v[SC_IPT];
+    uint32_t t = 0;
+#pragma unroll
+    for (int i = 0; i < SC_IPT; ++i) {
+        v[i] = (base + i < n) ? in[base + i] : 0u;
+        t += v[i];
+    }
+    uint32_t total;
+    uint32_t run = block_exclusive_scan(t, s_warp, total) + (offs ? offs[blockIdx.x] : 0u);
+#pragma unroll
+    for (int i = 0; i < SC_IPT; ++i) {
+        if (base + i < n) out[base + i] = run;
+        run += v[i];
+    }
+}
+
+size_t scan_temp_words(uint64_t n)
+{
+    size_t w = 0;
+    while (n > (uint64_t)SC_TILE) {
+        n = (n + SC_TILE - 1) / SC_TILE;
+        w += 2 * n;
+    }
+    return w + 2;
+}
+
+// exclusive scan of n words (in may equal out); tmp from scan_temp_words
+void exclusive_scan(const uint32_t *in, uint32_t *out, uint64_t n, uint32_t *tmp, cudaStream_t st, int *launches)
+{
+    if (n == 0) return;
+    const uint64_t nb = (n + SC_TILE - 1) / SC_TILE;
+    if (nb == 1) {
+        scan_apply_kernel<<<1, SC_THREADS, 0, st>>>(in, (uint32_t)n, nullptr, out);
+        ++*launches;
+        return;
+    }
+    uint32_t *sums = tmp, *offs = tmp + nb;
+    scan_sums_kernel<<<(unsigned)nb, SC_THREADS, 0, st>>>(in, (uint32_t)n, sums);
+    ++*launches;
+    exclusive_scan(sums, offs, nb, tmp + 2 * nb, st, launches);
+    scan_apply_kernel<<<(unsigned)nb, SC_THREADS, 0, st>>>(in, (uint32_t)n, offs, out);
+    ++*launches;
+}
+
+// ------------------------------------------------------------ radix sort
+template <class K>
+__global__ void __launch_bounds__(RS_THREADS) rs_hist_kernel(const K *__restrict__ keys, uint32_t n, int shift,
+                                                             uint32_t *__restrict__ hist, uint32_t nblocks)
+{
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
+#pragma unroll
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        const uint64_t i = base + (uint64_t)r * RS_THREADS + threadIdx.x;
+        if (i < n) atomicAdd(&h[(uint32_t)(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(uint64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+template <class K>
+__global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(const K *__restrict__ kin,
+                                                                const uint32_t *__restrict__ vin,
+                                                                K *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                                uint32_t n, int shift,
+                                                                const uint32_t *__restrict__ offs,
+                                                                uint32_t nblocks)
+{
+    __shared__ uint32_t wcnt[RS_WARPS][256];
+    for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t ltmask = (1u << lane) - 1u;
+    const uint64_t base = (uint64_t)blockIdx.x * RS_TILE + (uint64_t)warp * (RS_ROUNDS * 32);
+    K key[RS_ROUNDS];
+    uint32_t val[RS_ROUNDS], dig[RS_ROUNDS], rank[RS_ROUNDS];
+#pragma unroll
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        const uint64_t i = base + (uint64_t)r * 32 + lane;
+        const bool ok = i < n;
+        key[r] = ok ? kin[i] : (K)0;
+        val[r] = ok ? vin[i] : 0u;
+        dig[r] = ok ? ((uint32_t)(key[r] >> shift) & 255u) : 256u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, dig[r]);
+        uint32_t before = 0;
+        if (ok) before = wcnt[warp][dig[r]];
+        rank[r] = before + __popc(peers & ltmask);
+        __syncwarp();
+        if (ok && lane == __ffs(peers) - 1) wcnt[warp][dig[r]] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        const int d = threadIdx.x;  // 256 threads = 256 digits
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) {
+            const uint32_t t = wcnt[w][d];
+            wcnt[w][d] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        if (dig[r] < 256u) {
+            const uint32_t pos = offs[(uint64_t)dig[r] * nblocks + blockIdx.x] + wcnt[warp][dig[r]] + rank[r];
+            kout[pos] = key[r];
+            vout[pos] = val[r];
+        }
+    }
+}
+
+size_t radix_hist_words(uint64_t n)
+{
+    const uint64_t nb = (n + RS_TILE - 1) / RS_TILE;
+    return 256 * nb;
+}
+
+// Stable LSD sort of (keys, vals) on key bits [0, bits).  Uses the alt
+// buffers; returns 1 if the result ended in the alt buffers.
+template <class K>
+static int radix_sort(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt, uint64_t n, int bits,
+                      uint32_t *hist, uint32_t *scan_tmp, cudaStream_t st, int *launches)
+{
+    if (n == 0) return 0;
+    const uint32_t nb = (uint32_t)((n + RS_TILE - 1) / RS_TILE);
+    K *ka = keys, *kb = keys_alt;
+    uint32_t *va = vals, *vb = vals_alt;
+    int flips = 0;
+    for (int shift = 0; shift < bits; shift += 8) {
+        rs_hist_kernel<K><<<nb, RS_THREADS, 0, st>>>(ka, (uint32_t)n, shift, hist, nb);
+        ++*launches;
+        exclusive_scan(hist, hist, (uint64_t)256 * nb, scan_tmp, st, launches);
+        rs_scatter_kernel<K><<<nb, RS_THREADS, 0, st>>>(ka, va, kb, vb, (uint32_t)n, shift, hist, nb);
+        ++*launches;
+        K *tk = ka; ka = kb; kb = tk;
+        uint32_t *tv = va; va = vb; vb = tv;
+        flips ^= 1;
+    }
+    return flips;
+}
+
+// -------------------------------------------------------------- binning
+__global__ void valid_flags_kernel(const PixBox *__restrict__ boxes, uint64_t n, uint32_t *__restrict__ flags)
+{
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i < n) flags[i] = boxes[i].x0 >= 0 ? 1u : 0u;
+}
+
+__global__ void emit_events_kernel(const PixBox *__restrict__ boxes, const double *__restrict__ keys,
+                                   const uint32_t *__restrict__ pos, uint64_t n, uint64_t *__restrict__ ev_key,
+                                   uint32_t *__restrict__ ev_val)
+{
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i >= n || boxes[i].x0 < 0) return;
+    const uint32_t p = pos[i];
+    ev_key[2 * p] = key_bits(keys[2 * i]);
+    ev_key[2 * p + 1] = key_bits(keys[2 * i + 1]);
+    ev_val[2 * p] = (uint32_t)(2 * i);
+    ev_val[2 * p + 1] = (uint32_t)(2 * i + 1);
+}
+
+__global__ void cell_keys_kernel(const uint32_t *__restrict__ ev_val, uint64_t ne, uint64_t n_gauss,
+                                 uint32_t *__restrict__ ck)
+{
+    const uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (e < ne) ck[e] = (uint32_t)((ev_val[e] >> 1) / n_gauss);
+}
+
+__device__ __forceinline__ void tile_rect(const PixBox &b, int TS, int &tx0, int &tx1, int &ty0, int &ty1)
+{
+    tx0 = b.x0 / TS; tx1 = b.x1 / TS; ty0 = b.y0 / TS; ty1 = b.y1 / TS;
+}
+
+__global__ void tile_counts_kernel(const uint32_t *__restrict__ ev_val, uint64_t ne,
+                                   const PixBox *__restrict__ boxes, int TS, uint32_t *__restrict__ cnt)
+{
+    const uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    int tx0, tx1, ty0, ty1;
+    tile_rect(boxes[ev_val[e] >> 1], TS, tx0, tx1, ty0, ty1);
+    cnt[e] = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+}
+
+__global__ void emit_entries_kernel(const uint32_t *__restrict__ ev_val, uint64_t ne,
+                                    const PixBox *__restrict__ boxes, int TS, int ntx, int n_tiles,
+                                    uint64_t n_gauss, const uint32_t *__restrict__ off,
+                                    uint32_t *__restrict__ ent_seg, uint32_t *__restrict__ ent_ev)
+{
+    const uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    const uint32_t ri = ev_val[e] >> 1;
+    const uint32_t cell = (uint32_t)(ri / n_gauss);
+    int tx0, tx1, ty0, ty1;
+    tile_rect(boxes[ri], TS, tx0, tx1, ty0, ty1);
+    uint32_t o = off[e];
+    for (int ty = ty0; ty <= ty1; ++ty)
+        for (int tx = tx0; tx <= tx1; ++tx) {
+            ent_seg[o] = cell * (uint32_t)n_tiles + (uint32_t)(ty * ntx + tx);
+            ent_ev[o] = (uint32_t)e;
+            ++o;
+        }
+}
+
+__global__ void seg_bounds_kernel(const uint32_t *__restrict__ seg, uint64_t n, uint32_t *__restrict__ start,
+                                  uint32_t *__restrict__ end)
+{
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t s = seg[i];
+    if (i == 0 || seg[i - 1] != s) start[s] = (uint32_t)i;
+    if (i == n - 1 || seg[i + 1] != s) end[s] = (uint32_t)(i + 1);
+}
+
+__global__ void iota_kernel(uint32_t *__restrict__ p, uint64_t n)
+{
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i < n) p[i] = (uint32_t)i;
+}
+
+__global__ void gather_events_kernel(const uint32_t *__restrict__ perm, const uint64_t *__restrict__ kin,
+                                     const uint32_t *__restrict__ vin, uint64_t n, uint64_t *__restrict__ kout,
+                                     uint32_t *__restrict__ vout)
+{
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t p = perm[i];
+    kout[i] = kin[p];
+    vout[i] = vin[p];
+}
+
+static inline unsigned blocks_for(uint64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+int run_binning(const BinArgs &a, BinOut &o, cudaStream_t st, int *launches)
+{
+    const int T = 256;
+    // 1. compact the pairs that reach the image
+    valid_flags_kernel<<<blocks_for(a.n_pairs, T), T, 0, st>>>(a.boxes, a.n_pairs, a.u32_a);
+    ++*launches;
+    exclusive_scan(a.u32_a, a.u32_a, a.n_pairs, a.scan_tmp, st, launches);
+    // 2. events
+    emit_events_kernel<<<blocks_for(a.n_pairs, T), T, 0, st>>>(a.boxes, a.keys, a.u32_a, a.n_pairs, a.ev_key[0],
+                                                                 a.ev_val[0]);
+    ++*launches;
+    const uint64_t ne = a.n_events;
+    if (ne == 0) {
+        o.ev_key = a.ev_key[0];
+        o.ev_val = a.ev_val[0];
+        o.ent_seg = a.ent_seg[0];
+        o.ent_ev = a.ent_ev[0];
+        cudaMemsetAsync(a.seg_start, 0, sizeof(uint32_t) * a.n_segments, st);
+        cudaMemsetAsync(a.seg_end, 0, sizeof(uint32_t) * a.n_segments, st);
+        return cudaGetLastError() == cudaSuccess ? 0 : 1;
+    }
+    // 3. sort by key bits, then stably by cell
+    int f = radix_sort<uint64_t>(a.ev_key[0], a.ev_val[0], a.ev_key[1], a.ev_val[1], ne, 64, a.hist, a.scan_tmp,
+                                 st, launches);
+    uint64_t *evk = a.ev_key[f];
+    uint32_t *evv = a.ev_val[f];
+    if (a.n_cells > 1) {
+        cell_keys_kernel<<<blocks_for(ne, T), T, 0, st>>>(evv, ne, a.n_gauss, a.u32_b);
+        ++*launches;
+        int bits = 0;
+        while ((1ull << bits) < (uint64_t)a.n_cells) bits += 8;
+        // carry the key bits along: sort (cell, position) then gather keys
+        // through the permuted positions
+        iota_kernel<<<blocks_for(ne, T), T, 0, st>>>(a.u32_a, ne);
+        ++*launches;
+        int g = radix_sort<uint32_t>(a.u32_b, a.u32_a, a.u32_c, a.u32_d, ne, bits, a.hist, a.scan_tmp, st, launches);
+        const uint32_t *perm = g ? a.u32_d : a.u32_a;
+        gather_events_kernel<<<blocks_for(ne, T), T, 0, st>>>(perm, evk, evv, ne, a.ev_key[f ^ 1], a.ev_val[f ^ 1]);
+        ++*launches;
+        evk = a.ev_key[f ^ 1];
+        evv = a.ev_val[f ^ 1];
+    }
+    o.ev_key = evk;
+    o.ev_val = evv;
+    // 4. entries per tile
+    tile_counts_kernel<<<blocks_for(ne, T), T, 0, st>>>(evv, ne, a.boxes, a.TS, a.u32_a);
+    ++*launches;
+    exclusive_scan(a.u32_a, a.u32_a, ne, a.scan_tmp, st, launches);
+    emit_entries_kernel<<<blocks_for(ne, T), T, 0, st>>>(evv, ne, a.boxes, a.TS, a.ntx, a.n_tiles, a.n_gauss,
+                                                          a.u32_a, a.ent_seg[0], a.ent_ev[0]);
+    ++*launches;
+    // 5. stable sort by segment
+    int bits = 0;
+    while ((1ull << bits) < a.n_segments) bits += 8;
+    if (bits == 0) bits = 8;
+    int h = radix_sort<uint32_t>(a.ent_seg[0], a.ent_ev[0], a.ent_seg[1], a.ent_ev[1], a.n_entries, bits, a.hist,
+                                 a.scan_tmp, st, launches);
+    o.ent_seg = a.ent_seg[h];
+    o.ent_ev = a.ent_ev[h];
+    // 6. segment bounds
+    cudaMemsetAsync(a.seg_start, 0, sizeof(uint32_t) * a.n_segments, st);
+    cudaMemsetAsync(a.seg_end, 0, sizeof(uint32_t) * a.n_segments, st);
+    if (a.n_entries) {
+        seg_bounds_kernel<<<blocks_for(a.n_entries, T), T, 0, st>>>(o.ent_seg, a.n_entries, a.seg_start, a.seg_end);
+        ++*launches;
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+}  // namespace ar

@@ -1,0 +1,49 @@
+// k_inst.cuh -- instantiation of the per-M kernels; included once per M by
+// k_m1.cu, k_m4.cu, k_m6.cu with AR_M defined.
+#include "ar_launch.h"
+#include "k_prep.cuh"
+#include "k_render.cuh"
+
+#define AR_CAT2(a, b) a##b
+#define AR_CAT(a, b) AR_CAT2(a, b)
+
+namespace ar {
+
+size_t AR_CAT(cell_data_bytes_m, AR_M)() { return sizeof(CellData<AR_M>); }
+int AR_CAT(rec_width_m, AR_M)() { return Rec<AR_M>::WIDTH; }
+
+int AR_CAT(launch_cell_prep_m, AR_M)(const double *lo, const double *hi, const CallConst &cc, void *cells,
+                                     cudaStream_t st)
+{
+    const int T = 64;
+    cell_prep_kernel<AR_M><<<(cc.n_cells + T - 1) / T, T, 0, st>>>(lo, hi, cc, (CellData<AR_M> *)cells);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+int AR_CAT(launch_record_prep_m, AR_M)(const double *vN, const double *tau, const float *opac, const float *rgb,
+                                       const CallConst &cc, const void *cells, int TS, float *recs,
+                                       PixBox *boxes, double *keys, unsigned long long *counters,
+                                       cudaStream_t st)
+{
+    const int T = 128;
+    dim3 grid((unsigned)((cc.n_gauss + T - 1) / T), (unsigned)cc.n_cells);
+    record_prep_kernel<AR_M><<<grid, T, 0, st>>>(vN, tau, opac, rgb, cc, (const CellData<AR_M> *)cells, TS, recs,
+                                                 boxes, keys, counters);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+int AR_CAT(launch_render_m, AR_M)(int TS, const RenderLaunch &a, cudaStream_t st)
+{
+    const unsigned nseg = (unsigned)a.n_cells * (unsigned)a.n_tiles;
+    if (TS == 16)
+        render_kernel<AR_M, 16, 32><<<nseg, 256, 0, st>>>(a.recs, a.boxes, a.seg_start, a.seg_end, a.ent_ev,
+                                                           a.ev_val, a.ev_key, a.W, a.H, a.ntx, a.n_tiles,
+                                                           a.n_gauss, 0, a.out_lo, a.out_hi);
+    else
+        render_kernel<AR_M, 8, 32><<<nseg, 64, 0, st>>>(a.recs, a.boxes, a.seg_start, a.seg_end, a.ent_ev,
+                                                         a.ev_val, a.ev_key, a.W, a.H, a.ntx, a.n_tiles,
+                                                         a.n_gauss, 0, a.out_lo, a.out_hi);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+}  // namespace ar

@@ -1,0 +1,530 @@
+// k_prep.cuh -- scene preprocessing, pose-cell linearisation and the
+// per-(Gaussian, cell) records of the abstract renderer.
+//
+//   scene_prep    : Mw = R(q) diag(exp(s)) and tau = 2 ln(255 o) per Gaussian
+//                   (the Gaussian tuple <uw, Mw, o, c> of Sec. 2.2).
+//   pose_prep     : v = R_wc (uw - t) and N = R_wc Mw per Gaussian for the
+//                   nominal camera of the call.
+//   cell_prep<M>  : linear forms of R_delta(theta) (first-order Taylor at the
+//                   cell centre, remainder (1/2)(sum h_theta)^2) and of
+//                   s = R_wc delta_t, per cell.
+//   record_prep<M>: Algorithm 1 lines 2-8 with set-valued variables (Sec. 3.3)
+//                   for one (Gaussian, cell) pair: uc, d, up, J, Mc, Mp,
+//                   X = Mp Mp^T, S = d^2, P = d up, MatrixInv (Algorithm 3,
+//                   k = 8, X0 = inverse of the centre matrix) and W = Conic Mp.
+//                   The depth key, near-plane class and pixel box are decided
+//                   in FP64; the forms that feed the per-pixel stage are FP32
+//                   with outward rounding.
+#pragma once
+#include "ar_common.cuh"
+
+namespace ar {
+
+// ---------------------------------------------------------------- scene prep
+__device__ __forceinline__ void quat_rot(const float *q_in, double R[9])
+{
+    double q0 = q_in[0], q1 = q_in[1], q2 = q_in[2], q3 = q_in[3];
+    double n = sqrt(dadd(dadd(dadd(dmul(q0, q0), dmul(q1, q1)), dmul(q2, q2)), dmul(q3, q3)));
+    double w = q0 / n, x = q1 / n, y = q2 / n, z = q3 / n;
+    R[0] = dsub(1.0, dmul(2.0, dadd(dmul(y, y), dmul(z, z))));
+    R[1] = dmul(2.0, dsub(dmul(x, y), dmul(w, z)));
+    R[2] = dmul(2.0, dadd(dmul(x, z), dmul(w, y)));
+    R[3] = dmul(2.0, dadd(dmul(x, y), dmul(w, z)));
+    R[4] = dsub(1.0, dmul(2.0, dadd(dmul(x, x), dmul(z, z))));
+    R[5] = dmul(2.0, dsub(dmul(y, z), dmul(w, x)));
+    R[6] = dmul(2.0, dsub(dmul(x, z), dmul(w, y)));
+    R[7] = dmul(2.0, dadd(dmul(y, z), dmul(w, x)));
+    R[8] = dsub(1.0, dmul(2.0, dadd(dmul(x, x), dmul(y, y))));
+}
+
+__device__ __forceinline__ void mat3(const double *A, const double *B, double *C)
+{
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0;
+            for (int k = 0; k < 3; ++k) s = dadd(s, dmul(A[3 * i + k], B[3 * k + j]));
+            C[3 * i + j] = s;
+        }
+}
+
+// ----------------------------------------------------------------- cells
+__device__ __forceinline__ void rot3(int axis, double a, double R[9], double D[9])
+{
+    double c = cos(a), s = sin(a);
+    for (int e = 0; e < 9; ++e) { R[e] = 0; D[e] = 0; }
+    if (axis == 0) {
+        R[0] = 1; R[4] = c; R[5] = -s; R[7] = s; R[8] = c;
+        D[4] = -s; D[5] = -c; D[7] = c; D[8] = -s;
+    } else if (axis == 1) {
+        R[0] = c; R[2] = s; R[4] = 1; R[6] = -s; R[8] = c;
+        D[0] = -s; D[2] = c; D[6] = -c; D[8] = -s;
+    } else {
+        R[0] = c; R[1] = -s; R[3] = s; R[4] = c; R[8] = 1;
+        D[0] = -s; D[1] = -c; D[3] = c; D[4] = -s;
+    }
+}
+
+// FP64 form -> outward FP32 form
+template <int M>
+__device__ __forceinline__ void to_f32(const double *lo, const double *hi, BS<M, float> &b)
+{
+    double el = 0, eh = 0;
+    for (int j = 0; j < M; ++j) {
+        b.lo.c[j] = (float)lo[j];
+        b.hi.c[j] = (float)hi[j];
+        el = __dadd_ru(el, fabs(lo[j] - (double)b.lo.c[j]));
+        eh = __dadd_ru(eh, fabs(hi[j] - (double)b.hi.c[j]));
+    }
+    b.lo.k = __double2float_rd(__dsub_rd(lo[M], el));
+    b.hi.k = __double2float_ru(__dadd_ru(hi[M], eh));
+    finish(b);
+}
+
+// One thread per cell.
+template <int M>
+__global__ void cell_prep_kernel(const double *__restrict__ cells_lo, const double *__restrict__ cells_hi,
+                                 CallConst cc, CellData<M> *__restrict__ out)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cc.n_cells) return;
+    CellData<M> &cd = out[c];
+    double ctr[MAXV], h[MAXV];
+    for (int k = 0; k < MAXV; ++k) {
+        double lo = cells_lo[MAXV * c + k], hi = cells_hi[MAXV * c + k];
+        ctr[k] = dmul(0.5, dadd(lo, hi));
+        h[k] = dmul(0.5, dsub(hi, lo));
+    }
+    // R_delta = Rx Ry Rz at the centre and its partial derivatives
+    double X[9], dX[9], Y[9], dY[9], Z[9], dZ[9], T[9], R[9], dR[3][9];
+    rot3(0, ctr[3], X, dX);
+    rot3(1, ctr[4], Y, dY);
+    rot3(2, ctr[5], Z, dZ);
+    mat3(X, Y, T); mat3(T, Z, R);
+    mat3(dX, Y, T); mat3(T, Z, dR[0]);
+    mat3(X, dY, T); mat3(T, Z, dR[1]);
+    mat3(X, Y, T); mat3(T, dZ, dR[2]);
+    double hs = dadd(dadd(h[3], h[4]), h[5]);
+    double rem = dmul(0.5, dmul(hs, hs));
+    for (int e = 0; e < 9; ++e) {
+        for (int j = 0; j <= M; ++j) { cd.rd_lo[e][j] = 0; cd.rd_hi[e][j] = 0; }
+        for (int k = 0; k < 3; ++k) {
+            int sl = cc.m_slot[3 + k];
+            if (sl >= 0) { double v = dmul(dR[k][e], h[3 + k]); cd.rd_lo[e][sl] = v; cd.rd_hi[e][sl] = v; }
+        }
+        cd.rd_lo[e][M] = dsub(R[e], rem);
+        cd.rd_hi[e][M] = dadd(R[e], rem);
+    }
+    for (int a = 0; a < 3; ++a) {
+        for (int j = 0; j <= M; ++j) cd.s[a][j] = 0;
+        double kk = 0;
+        for (int k = 0; k < 3; ++k) {
+            int sl = cc.m_slot[k];
+            if (sl >= 0) cd.s[a][sl] = dmul(cc.R0[3 * a + k], h[k]);
+            kk = dadd(kk, dmul(cc.R0[3 * a + k], ctr[k]));
+        }
+        cd.s[a][M] = kk;
+    }
+    for (int j = 0; j < M; ++j) cd.g[j] = 0;
+    for (int k = 0; k < 3; ++k) {
+        double s = 0;
+        for (int b = 0; b < 3; ++b) s = dadd(s, dmul(R[3 * b + 2], cc.R0[3 * b + k]));
+        int sl = cc.m_slot[k];
+        if (sl >= 0) cd.g[sl] = dmul(-s, h[k]);
+    }
+    for (int e = 0; e < 9; ++e) {
+        DF<M> lo, hi;
+        for (int j = 0; j < M; ++j) { lo.c[j] = cd.rd_lo[e][j]; hi.c[j] = cd.rd_hi[e][j]; }
+        lo.k = cd.rd_lo[e][M]; hi.k = cd.rd_hi[e][M];
+        cd.rd_int[e][0] = df_min(lo);
+        cd.rd_int[e][1] = df_max(hi);
+        to_f32<M>(cd.rd_lo[e], cd.rd_hi[e], cd.rd32[e]);
+    }
+    for (int a = 0; a < 3; ++a) {
+        DF<M> f;
+        for (int j = 0; j < M; ++j) f.c[j] = cd.s[a][j];
+        f.k = cd.s[a][M];
+        cd.s_int[a][0] = df_min(f);
+        cd.s_int[a][1] = df_max(f);
+        to_f32<M>(cd.s[a], cd.s[a], cd.s32[a]);
+    }
+    // FP64 value-chain copies, widened to cover the rounding of sin, cos and
+    // the Taylor terms (a relative 1e-14 is far above their few-ulp error)
+    for (int e = 0; e < 12; ++e) {
+        const double *lo = e < 9 ? cd.rd_lo[e] : cd.s[e - 9];
+        const double *hi = e < 9 ? cd.rd_hi[e] : cd.s[e - 9];
+        BS<M, double> &b = e < 9 ? cd.rd64[e] : cd.s64[e - 9];
+        double mag = 1.0;
+        for (int j = 0; j <= M; ++j) mag = __dadd_ru(mag, fmax(fabs(lo[j]), fabs(hi[j])));
+        const double pad = __dmul_ru(1e-14, mag);
+        for (int j = 0; j < M; ++j) { b.lo.c[j] = lo[j]; b.hi.c[j] = hi[j]; }
+        b.lo.k = __dsub_rd(lo[M], pad);
+        b.hi.k = __dadd_ru(hi[M], pad);
+        finish(b);
+    }
+}
+
+// FP32 form -> FP64 (exact)
+template <int M>
+__device__ __forceinline__ BS<M, double> to_f64(const BS<M, float> &b)
+{
+    BS<M, double> d;
+    for (int j = 0; j < M; ++j) { d.lo.c[j] = b.lo.c[j]; d.hi.c[j] = b.hi.c[j]; }
+    d.lo.k = b.lo.k; d.hi.k = b.hi.k;
+    finish(d);
+    return d;
+}
+
+// FP64 sound form -> outward FP32 form
+template <int M>
+__device__ __forceinline__ void bs_to_f32(const BS<M, double> &d, BS<M, float> &b)
+{
+    double lo[M + 1], hi[M + 1];
+    for (int j = 0; j <= M; ++j) {
+        lo[j] = j < M ? d.lo.c[j] : d.lo.k;
+        hi[j] = j < M ? d.hi.c[j] : d.hi.k;
+    }
+    to_f32<M>(lo, hi, b);
+}
+
+// ------------------------------------------------------------- records
+template <int M>
+__device__ __forceinline__ void store_form(float *dst, const LF<M, float> &f)
+{
+#pragma unroll
+    for (int j = 0; j < M; ++j) dst[j] = f.c[j];
+    dst[M] = f.k;
+}
+
+template <int M>
+__device__ __forceinline__ bool bs_finite(const BS<M, float> &b)
+{
+    return isfinite(b.vlo) && isfinite(b.vhi) && isfinite(b.lo.k) && isfinite(b.hi.k) && isfinite(b.rlo) &&
+           isfinite(b.rhi);
+}
+
+struct PrepCount {
+    uint32_t triples, fallback, valid, tiles;
+};
+
+// One (Gaussian, cell) pair; returns its counters through pc.
+template <int M>
+__device__ __forceinline__ void record_prep_one(const double *__restrict__ vN, const double *__restrict__ tau_g,
+                                                const float *__restrict__ opacity, const float *__restrict__ rgb,
+                                                const CallConst &cc, const CellData<M> &cd, int cell, int64_t g,
+                                                int TS, float *__restrict__ recs, PixBox *__restrict__ boxes,
+                                                double *__restrict__ keys, PrepCount &pc)
+{
+    using RL = Rec<M>;
+    typedef BS<M, float> B;
+    const int64_t ri = (int64_t)cell * cc.n_gauss + g;
+    PixBox box = {-1, -1, -1, -1};
+    boxes[ri] = box;
+    const double tau = tau_g[g];
+    if (!(tau >= 0)) return;  // o < 1/255: never above the cutoff
+    const double *v = vN + 12 * g;
+    const double *N = v + 3;
+
+    // ---- FP64 decision chain: depth forms, near plane, depth key, pixel box
+    DB<M> Rd2[3], vms[3];
+    for (int b = 0; b < 3; ++b) {
+        for (int j = 0; j < M; ++j) {
+            Rd2[b].lo.c[j] = cd.rd_lo[3 * b + 2][j];
+            Rd2[b].hi.c[j] = cd.rd_hi[3 * b + 2][j];
+            vms[b].lo.c[j] = dsub(0.0, cd.s[b][j]);
+            vms[b].hi.c[j] = vms[b].lo.c[j];
+        }
+        Rd2[b].lo.k = cd.rd_lo[3 * b + 2][M];
+        Rd2[b].hi.k = cd.rd_hi[3 * b + 2][M];
+        vms[b].lo.k = dsub(v[b], cd.s[b][M]);
+        vms[b].hi.k = vms[b].lo.k;
+    }
+    DB<M> dd = db_mul<M>(Rd2[0], vms[0]);
+    dd = db_add<M>(dd, db_mul<M>(Rd2[1], vms[1]));
+    dd = db_add<M>(dd, db_mul<M>(Rd2[2], vms[2]));
+    const double dlo = df_min(dd.lo), dhi = df_max(dd.hi);
+    const double nearp = (double)cc.near_plane;
+    if (!(dhi > nearp)) return;
+    const bool straddle = !(dlo > nearp);
+    double klo, khi;
+    {
+        DF<M> gk;
+        for (int j = 0; j < M; ++j) gk.c[j] = cd.g[j];
+        gk.k = 0;
+        klo = df_min(df_sub(dd.lo, gk));
+        khi = df_max(df_sub(dd.hi, gk));
+        double pad = dmul(KEY_SLACK, dadd(1.0, fmax(fabs(klo), fabs(khi))));
+        klo = dsub(klo, pad);
+        khi = dadd(khi, pad);
+    }
+    double mu_lo[2], mu_hi[2];
+    {
+        DI Ri[9], vs[3];
+        for (int e = 0; e < 9; ++e) Ri[e] = DI{cd.rd_int[e][0], cd.rd_int[e][1]};
+        for (int b = 0; b < 3; ++b) vs[b] = DI{dsub(v[b], cd.s_int[b][1]), dsub(v[b], cd.s_int[b][0])};
+        const double dl = fmax(dlo, nearp);
+        DI D = {dl, dhi};
+        DI ucx = di_add(di_add(di_mul(Ri[0], vs[0]), di_mul(Ri[3], vs[1])), di_mul(Ri[6], vs[2]));
+        DI ucy = di_add(di_add(di_mul(Ri[1], vs[0]), di_mul(Ri[4], vs[1])), di_mul(Ri[7], vs[2]));
+        const double fx = cc.fx, fy = cc.fy, cx = cc.cx, cy = cc.cy;
+        DI mux = {dadd(cx, dmul(fx, fmin(ucx.l / D.l, ucx.l / D.u))), dadd(cx, dmul(fx, fmax(ucx.u / D.l, ucx.u / D.u)))};
+        DI muy = {dadd(cy, dmul(fy, fmin(ucy.l / D.l, ucy.l / D.u))), dadd(cy, dmul(fy, fmax(ucy.u / D.l, ucy.u / D.u)))};
+        double X00 = 0, X11 = 0;
+        for (int c = 0; c < 3; ++c) {
+            DI m[3];
+            for (int a = 0; a < 3; ++a)
+                m[a] = di_add(di_add(di_scale(Ri[a], N[c]), di_scale(Ri[3 + a], N[3 + c])), di_scale(Ri[6 + a], N[6 + c]));
+            DI p0 = di_scale(di_add(di_mul(D, m[0]), di_scale(di_mul(ucx, m[2]), -1.0)), fx);
+            DI p1 = di_scale(di_add(di_mul(D, m[1]), di_scale(di_mul(ucy, m[2]), -1.0)), fy);
+            X00 = dadd(X00, di_sqmax(p0));
+            X11 = dadd(X11, di_sqmax(p1));
+        }
+        const double dl2 = dmul(dl, dl);
+        const double rx = sqrt(dmul(tau, X00)) / dl2, ry = sqrt(dmul(tau, X11)) / dl2;
+        double xl = dsub(mux.l, rx), xh = dadd(mux.u, rx), yl = dsub(muy.l, ry), yh = dadd(muy.u, ry);
+        xl = dsub(xl, dmul(BOX_SLACK, dadd(1.0, fabs(xl))));
+        xh = dadd(xh, dmul(BOX_SLACK, dadd(1.0, fabs(xh))));
+        yl = dsub(yl, dmul(BOX_SLACK, dadd(1.0, fabs(yl))));
+        yh = dadd(yh, dmul(BOX_SLACK, dadd(1.0, fabs(yh))));
+        if (!(xh >= xl) || !(yh >= yl)) return;
+        double fx0 = ceil(dsub(xl, 0.5)), fx1 = floor(dsub(xh, 0.5));
+        double fy0 = ceil(dsub(yl, 0.5)), fy1 = floor(dsub(yh, 0.5));
+        fx0 = fmax(fx0, 0.0); fy0 = fmax(fy0, 0.0);
+        fx1 = fmin(fx1, (double)(cc.W - 1)); fy1 = fmin(fy1, (double)(cc.H - 1));
+        if (fx0 > fx1 || fy0 > fy1) return;
+        box = PixBox{(int)fx0, (int)fx1, (int)fy0, (int)fy1};
+        mu_lo[0] = mux.l; mu_hi[0] = mux.u; mu_lo[1] = muy.l; mu_hi[1] = muy.u;
+    }
+
+    // ---- FP32 value chain
+    float *rec = recs + ri * RL::WIDTH;
+    uint32_t flags = (straddle ? F_STRADDLE : 0u) | (klo < khi ? F_OPEN : 0u);
+    const float o = opacity[g];
+    rec[RL::O] = o;
+    rec[RL::TAU_DN] = __double2float_rd(tau);
+    rec[RL::TAU_UP] = __double2float_ru(tau);
+    for (int k = 0; k < 3; ++k) rec[RL::COL + k] = rgb[3 * g + k];
+
+    bool ok = true;
+    typedef BS<M, double> BD;
+    // ---- FP64 value chain (directed rounding): uc, S, P, Mc, J, Mp, X, E.
+    // These are differences of large, nearly equal terms (S u - P, I - X X0,
+    // Conic Mp); carrying them in FP64 keeps their FP32 images accurate.
+    BD uc64[3];
+    {
+        double vabs = 1.0;
+        for (int b = 0; b < 3; ++b) vabs += fabs(v[b]);
+        const double ev = __dmul_ru(1e-14, vabs);
+        BD vm[3];
+        for (int b = 0; b < 3; ++b) {
+            Pair<M, double> p;
+            p.init(__dsub_rd(v[b], ev), __dadd_ru(v[b], ev));
+            p.lin(-1.0, cd.s64[b]);
+            vm[b] = p.result();
+        }
+        for (int a = 0; a < 3; ++a) {
+            Pair<M, double> p;
+            p.init(0.0, 0.0);
+            p.mul(cd.rd64[a], vm[0]);
+            p.mul(cd.rd64[3 + a], vm[1]);
+            p.mul(cd.rd64[6 + a], vm[2]);
+            uc64[a] = p.result();
+        }
+    }
+    const BD &d64 = uc64[2];
+    {
+        // S = d^2 and P = d up folded into R = mu S - P around a pixel centre
+        // mu near the projected mean (see Rec)
+        BD u0, u1;
+        Pair<M, double> p;
+        p.init(0.0, 0.0); p.lin((double)cc.fx, uc64[0]); p.lin((double)cc.cx, uc64[2]); u0 = p.result();
+        p.init(0.0, 0.0); p.lin((double)cc.fy, uc64[1]); p.lin((double)cc.cy, uc64[2]); u1 = p.result();
+        const BD S = b_sqr<M, double>(d64);
+        const BD Px = b_mul<M, double>(d64, u0);
+        const BD Py = b_mul<M, double>(d64, u1);
+        const float mux = (float)(floor(fmin(fmax(0.5 * (mu_lo[0] + mu_hi[0]), -1e6), 1e6)) + 0.5);
+        const float muy = (float)(floor(fmin(fmax(0.5 * (mu_lo[1] + mu_hi[1]), -1e6), 1e6)) + 0.5);
+        BD Rx, Ry;
+        {
+            Acc<M, double, true> lo;
+            Acc<M, double, false> hi;
+            lo.init(0.0); lo.term((double)mux, S.lo, S.rlo); lo.term(-1.0, Px.hi, Px.rhi);
+            hi.init(0.0); hi.term((double)mux, S.hi, S.rhi); hi.term(-1.0, Px.lo, Px.rlo);
+            Rx.lo = lo.result(); Rx.hi = hi.result(); finish(Rx);
+            lo.init(0.0); lo.term((double)muy, S.lo, S.rlo); lo.term(-1.0, Py.hi, Py.rhi);
+            hi.init(0.0); hi.term((double)muy, S.hi, S.rhi); hi.term(-1.0, Py.lo, Py.rlo);
+            Ry.lo = lo.result(); Ry.hi = hi.result(); finish(Ry);
+        }
+        B S32, Rx32, Ry32;
+        bs_to_f32<M>(S, S32);
+        bs_to_f32<M>(Rx, Rx32);
+        bs_to_f32<M>(Ry, Ry32);
+        ok = ok && bs_finite(S32) && bs_finite(Rx32) && bs_finite(Ry32);
+        store_form<M>(rec + RL::S_LO, S32.lo); store_form<M>(rec + RL::S_HI, S32.hi);
+        store_form<M>(rec + RL::RX_LO, Rx32.lo); store_form<M>(rec + RL::RX_HI, Rx32.hi);
+        store_form<M>(rec + RL::RY_LO, Ry32.lo); store_form<M>(rec + RL::RY_HI, Ry32.hi);
+        rec[RL::RAD + 0] = S32.rlo; rec[RL::RAD + 1] = S32.rhi;
+        rec[RL::RAD + 2] = Rx32.rlo; rec[RL::RAD + 3] = Rx32.rhi;
+        rec[RL::RAD + 4] = Ry32.rlo; rec[RL::RAD + 5] = Ry32.rhi;
+        rec[RL::MU_X] = mux;
+        rec[RL::MU_Y] = muy;
+    }
+    BD Mp64[6];
+    {
+        BD Mc[9];
+        for (int a = 0; a < 3; ++a)
+            for (int c = 0; c < 3; ++c) {
+                Pair<M, double> p;
+                p.init(0.0, 0.0);
+                p.lin(N[c], cd.rd64[a]);
+                p.lin(N[3 + c], cd.rd64[3 + a]);
+                p.lin(N[6 + c], cd.rd64[6 + a]);
+                Mc[3 * a + c] = p.result();
+            }
+        BD J00, J02, J11, J12;
+        Pair<M, double> p;
+        p.init(0.0, 0.0); p.lin((double)cc.fx, d64); J00 = p.result();
+        p.init(0.0, 0.0); p.lin(-(double)cc.fx, uc64[0]); J02 = p.result();
+        p.init(0.0, 0.0); p.lin((double)cc.fy, d64); J11 = p.result();
+        p.init(0.0, 0.0); p.lin(-(double)cc.fy, uc64[1]); J12 = p.result();
+        for (int c = 0; c < 3; ++c) {
+            p.init(0.0, 0.0); p.mul(J00, Mc[c]); p.mul(J02, Mc[6 + c]); Mp64[c] = p.result();
+            p.init(0.0, 0.0); p.mul(J11, Mc[3 + c]); p.mul(J12, Mc[6 + c]); Mp64[3 + c] = p.result();
+        }
+    }
+    // ---- MatrixInv (Algorithm 3): X and I - X X0 in FP64, the series in FP32
+    bool fallback = false;
+    B conic[4];
+    {
+        BD X[4];
+        {
+            Pair<M, double> p;
+            p.init(0.0, 0.0); p.sqr(Mp64[0]); p.sqr(Mp64[1]); p.sqr(Mp64[2]); X[0] = p.result();
+            p.init(0.0, 0.0); p.sqr(Mp64[3]); p.sqr(Mp64[4]); p.sqr(Mp64[5]); X[3] = p.result();
+            p.init(0.0, 0.0); p.mul(Mp64[0], Mp64[3]); p.mul(Mp64[1], Mp64[4]); p.mul(Mp64[2], Mp64[5]); X[1] = p.result();
+            X[2] = X[1];
+        }
+        const double h00 = 0.5 * (X[0].vlo + X[0].vhi), h01 = 0.5 * (X[1].vlo + X[1].vhi);
+        const double h11 = 0.5 * (X[3].vlo + X[3].vhi);
+        const double det = h00 * h11 - h01 * h01;
+        if (!(det > 0.0) || !(h00 > 0.0) || !isfinite(det)) {
+            fallback = true;
+        } else {
+            // X0 rounded to float: the same constant enters I - X X0 and X0 * sum
+            const float X0[4] = {(float)(h11 / det), (float)(-h01 / det), (float)(-h01 / det), (float)(h00 / det)};
+            B E[4];
+            double rho2 = 0.0;
+            for (int r = 0; r < 2; ++r)
+                for (int s = 0; s < 2; ++s) {
+                    Pair<M, double> p;
+                    const double dl = (r == s) ? 1.0 : 0.0;
+                    p.init(dl, dl);
+                    p.lin(-(double)X0[s], X[2 * r]);
+                    p.lin(-(double)X0[2 + s], X[2 * r + 1]);
+                    const BD e64 = p.result();
+                    const double m = fmax(fabs(e64.vlo), fabs(e64.vhi));
+                    rho2 = __fma_ru(m, m, rho2);
+                    bs_to_f32<M>(e64, E[2 * r + s]);
+                }
+            const double rho64 = __dsqrt_ru(rho2);
+            if (!(rho64 < RHO_MAX)) {
+                fallback = true;
+            } else {
+                const float rho = __double2float_ru(rho64);
+                // T = sum_{i=1..k} (I - X X0)^i, so that Xp = X0 (I + T) = X0 + X0 T:
+                // the identity term is added as an exact constant at the end
+                B P[4], Ssum[4];
+                for (int e = 0; e < 4; ++e) {
+                    P[e] = E[e];
+                    Ssum[e] = E[e];
+                }
+#pragma unroll 1
+                for (int i = 2; i <= KTAYLOR; ++i) {
+                    B Q[4];
+                    for (int r = 0; r < 2; ++r)
+                        for (int s = 0; s < 2; ++s) {
+                            Pair<M, float> p;
+                            p.init(0.f, 0.f);
+                            p.mul(P[2 * r], E[s]);
+                            p.mul(P[2 * r + 1], E[2 + s]);
+                            Q[2 * r + s] = p.result();
+                        }
+                    for (int e = 0; e < 4; ++e) { P[e] = Q[e]; Ssum[e] = b_add<M, float>(Ssum[e], Q[e]); }
+                }
+                float nX0 = 0.f;
+                for (int e = 0; e < 4; ++e) nX0 = __fmaf_ru(X0[e], X0[e], nX0);
+                nX0 = __fsqrt_ru(nX0);
+                float rk = 1.f;
+                for (int i = 0; i <= KTAYLOR; ++i) rk = __fmul_ru(rk, rho);
+                const float eps = __fdiv_ru(__fmul_ru(nX0, rk), __fsub_rd(1.f, rho));
+                for (int r = 0; r < 2; ++r)
+                    for (int s = 0; s < 2; ++s) {
+                        Pair<M, float> p;
+                        // X0[r][s] + eps-widening, then + X0 T
+                        p.init(__fsub_rd(X0[2 * r + s], eps), __fadd_ru(X0[2 * r + s], eps));
+                        p.lin(X0[2 * r], Ssum[s]);
+                        p.lin(X0[2 * r + 1], Ssum[2 + s]);
+                        conic[2 * r + s] = p.result();
+                        if (!bs_finite(conic[2 * r + s])) fallback = true;
+                    }
+            }
+        }
+    }
+    if (!fallback) {
+        for (int r = 0; r < 2; ++r)
+            for (int c = 0; c < 3; ++c) {
+                // W = Conic Mp in FP64 (Conic's FP32 forms are exact in FP64)
+                Pair<M, double> p;
+                p.init(0.0, 0.0);
+                p.mul(to_f64<M>(conic[2 * r]), Mp64[c]);
+                p.mul(to_f64<M>(conic[2 * r + 1]), Mp64[3 + c]);
+                B w;
+                bs_to_f32<M>(p.result(), w);
+                if (!bs_finite(w)) fallback = true;
+                float *dst = rec + RL::W0 + (3 * r + c) * RL::WSTRIDE;
+                store_form<M>(dst, w.lo);
+                store_form<M>(dst + RL::F, w.hi);
+                dst[2 * RL::F] = w.vlo; dst[2 * RL::F + 1] = w.vhi;
+                dst[2 * RL::F + 2] = w.rlo; dst[2 * RL::F + 3] = w.rhi;
+            }
+    }
+    if (!ok) fallback = true;
+    if (fallback) {
+        flags |= F_FALLBACK;
+        pc.fallback = 1;
+    }
+    rec[RL::FLAGS] = __uint_as_float(flags);
+    keys[2 * ri] = klo;
+    keys[2 * ri + 1] = khi;
+    boxes[ri] = box;
+    pc.triples = (uint32_t)(box.x1 - box.x0 + 1) * (uint32_t)(box.y1 - box.y0 + 1);
+    pc.valid = 1;
+    pc.tiles = (uint32_t)(box.x1 / TS - box.x0 / TS + 1) * (uint32_t)(box.y1 / TS - box.y0 / TS + 1);
+}
+
+// grid: x over Gaussians, y over cells.  One thread per (Gaussian, cell).
+// counters: [0] pixel-Gaussian-cell triples in boxes, [1] MatrixInv
+// fallbacks, [2] pairs present, [3] (pair, tile) entries.
+template <int M>
+__global__ void __launch_bounds__(128) record_prep_kernel(
+    const double *__restrict__ vN, const double *__restrict__ tau_g, const float *__restrict__ opacity,
+    const float *__restrict__ rgb, CallConst cc, const CellData<M> *__restrict__ cells, int TS,
+    float *__restrict__ recs, PixBox *__restrict__ boxes, double *__restrict__ keys,
+    unsigned long long *__restrict__ counters)
+{
+    const int cell = blockIdx.y;
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    PrepCount pc = {0, 0, 0, 0};
+    if (g < cc.n_gauss) record_prep_one<M>(vN, tau_g, opacity, rgb, cc, cells[cell], cell, g, TS, recs, boxes, keys, pc);
+    const uint32_t t = __reduce_add_sync(0xffffffffu, pc.triples);
+    const uint32_t f = __reduce_add_sync(0xffffffffu, pc.fallback);
+    const uint32_t v = __reduce_add_sync(0xffffffffu, pc.valid);
+    const uint32_t e = __reduce_add_sync(0xffffffffu, pc.tiles);
+    if ((threadIdx.x & 31) == 0) {
+        if (t) atomicAdd(&counters[0], (unsigned long long)t);
+        if (f) atomicAdd(&counters[1], (unsigned long long)f);
+        if (v) atomicAdd(&counters[2], (unsigned long long)v);
+        if (e) atomicAdd(&counters[3], (unsigned long long)e);
+    }
+}
+
+}  // namespace ar

@@ -1,0 +1,333 @@
+// k_render.cuh -- per-pixel effective-opacity relaxation and BlendInd blend.
+//
+// One CTA per (cell, tile), one thread per pixel.  The tile's bin holds the
+// two depth-key endpoints of every (Gaussian, cell) pair whose pixel box meets
+// the tile, sorted by key.  Each pixel sweeps that list once:
+//
+//   lower endpoint of i : effective-opacity bounds of i at this pixel
+//                         (Algorithm 1 lines 9-10 relaxed: Delta = S u - P,
+//                         q = Delta^T W, m = q q^T, a = o Exp(-m/2) with the
+//                         tangent/secant of Table 2 and the 1/255 cutoff);
+//                         T_hi(i) = prod over j certainly in front of i of
+//                         (1 - a_lo(j)), i.e. keys with khi(j) < klo(i);
+//                         the upper colour form gains T_hi(i) c_i U_i.
+//   upper endpoint of i : T_lo(i) = prod over j != i that may be in front of
+//                         i of (1 - a_hi(j)), i.e. klo(j) < khi(i); the lower
+//                         colour form gains T_lo(i) c_i L_i.
+//
+// This is BlendInd (Algorithm 4) with Ind(d_i - d_j) three-valued from the
+// depth-key intervals and Prod bounded by interval products.  Products over
+// keys strictly below a value are running products over the sorted list;
+// endpoints with equal keys are handled as a group (queries before
+// absorptions) so strictness matches the pairwise definition.
+#pragma once
+#include "ar_common.cuh"
+
+namespace ar {
+
+template <int M> struct AlphaOut {
+    LF<M, float> L, U;  // lower / upper forms of the effective opacity
+    float rL, rU;       // their coefficient radii
+    float alo, ahi;     // scalar enclosure of a over the cell
+};
+
+template <int M>
+__device__ __forceinline__ void load_form(const float *src, LF<M, float> &f)
+{
+#pragma unroll
+    for (int j = 0; j < M; ++j) f.c[j] = src[j];
+    f.k = src[M];
+}
+
+template <int M>
+__device__ __forceinline__ void load_w(const float *src, BS<M, float> &b)
+{
+    load_form<M>(src, b.lo);
+    load_form<M>(src + M + 1, b.hi);
+    b.vlo = src[2 * M + 2];
+    b.vhi = src[2 * M + 3];
+    b.rlo = src[2 * M + 4];
+    b.rhi = src[2 * M + 5];
+}
+
+__device__ __forceinline__ float clamp01(float x) { return fminf(1.f, fmaxf(0.f, x)); }
+
+// Effective-opacity bounds of one (Gaussian, cell) record at pixel (ux, uy).
+template <int M>
+__device__ __forceinline__ void pixel_alpha(const float *__restrict__ r, float ux, float uy, AlphaOut<M> &out)
+{
+    using RL = Rec<M>;
+    using N = Num<float>;
+    typedef BS<M, float> B;
+    const float o = r[RL::O];
+    const uint32_t flags = __float_as_uint(r[RL::FLAGS]);
+    if (flags & F_FALLBACK) {
+#pragma unroll
+        for (int j = 0; j < M; ++j) { out.L.c[j] = 0.f; out.U.c[j] = 0.f; }
+        out.L.k = 0.f; out.U.k = o; out.rL = 0.f; out.rU = 0.f;
+        out.alo = 0.f; out.ahi = o;
+        return;
+    }
+    // Delta = S u - P, held as (u - mu) S + R (see Rec)
+    B Dx, Dy;
+    {
+        LF<M, float> slo, shi, plo, phi;
+        load_form<M>(r + RL::S_LO, slo);
+        load_form<M>(r + RL::S_HI, shi);
+        Acc<M, float, true> lo;
+        Acc<M, float, false> hi;
+        const float dx = ux - r[RL::MU_X], dy = uy - r[RL::MU_Y];  // exact: both are half-integers
+        load_form<M>(r + RL::RX_LO, plo);
+        load_form<M>(r + RL::RX_HI, phi);
+        lo.init(0.f); hi.init(0.f);
+        lo.term(dx, slo, r[RL::RAD + 0]); hi.term(dx, shi, r[RL::RAD + 1]);
+        lo.term(1.f, plo, r[RL::RAD + 2]); hi.term(1.f, phi, r[RL::RAD + 3]);
+        Dx.lo = lo.result(); Dx.hi = hi.result(); finish(Dx);
+        load_form<M>(r + RL::RY_LO, plo);
+        load_form<M>(r + RL::RY_HI, phi);
+        lo.init(0.f); hi.init(0.f);
+        lo.term(dy, slo, r[RL::RAD + 0]); hi.term(dy, shi, r[RL::RAD + 1]);
+        lo.term(1.f, plo, r[RL::RAD + 4]); hi.term(1.f, phi, r[RL::RAD + 5]);
+        Dy.lo = lo.result(); Dy.hi = hi.result(); finish(Dy);
+    }
+    // m = sum_c (Delta_x W_0c + Delta_y W_1c)^2
+    Pair<M, float> pm;
+    pm.init(0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        B w0, w1;
+        load_w<M>(r + RL::W0 + c * RL::WSTRIDE, w0);
+        load_w<M>(r + RL::W0 + (3 + c) * RL::WSTRIDE, w1);
+        Pair<M, float> pq;
+        pq.init(0.f, 0.f);
+        pq.mul(Dx, w0);
+        pq.mul(Dy, w1);
+        B q = pq.result();
+        pm.sqr(q);
+    }
+    B m = pm.result();
+    const float mlo = m.vlo, mhi = m.vhi;
+    // Exp on x = -m/2 in [xl, xu], xu clipped at 0 because m >= 0
+    const float xl = -0.5f * mhi;
+    float xu = fminf(-0.5f * mlo, 0.f);
+    if (!(xu >= xl)) xu = xl;
+    const float el_dn = N::exp_dn(xl), el_up = N::exp_up(xl), eu_up = N::exp_up(xu);
+    // lower: o e(xl) (1 + x - xl) with x >= -m.hi/2
+    Acc<M, float, true> la;
+    const float e1 = __fmul_rd(o, el_dn);
+    la.init(__fmul_rd(e1, __fsub_rd(1.f, xl)));
+    la.term(-0.5f * e1, m.hi, m.rhi);
+    LF<M, float> La = la.result();
+    // upper: o (e(xl) + s (x - xl)) with x <= -m.lo/2
+    const float w = __fsub_rd(xu, xl);
+    float s = (w > 0.f) ? __fdiv_ru(__fsub_ru(eu_up, el_up), w) : eu_up;
+    s = fminf(fmaxf(s, 0.f), N::BIG);
+    const float e2 = __fmul_ru(o, el_up), s2 = __fmul_ru(o, s);
+    Acc<M, float, false> ua;
+    ua.init(__fmaf_ru(-s2, xl, e2));
+    ua.term(-0.5f * s2, m.lo, m.rlo);
+    LF<M, float> Ua = ua.result();
+    float rUa = 0.f;
+#pragma unroll
+    for (int j = 0; j < M; ++j) rUa = __fadd_ru(rUa, fabsf(Ua.c[j]));
+    const float amax = __fadd_ru(Ua.k, rUa);
+    // blend the upper form toward the constant o where its maximum exceeds o
+    const float lam = clamp01((o * (1.f + CLIP_RAMP) - amax) / (o * CLIP_RAMP));
+    // cutoff ramps (width shrinks with the m interval)
+    float ramp = fminf(CUT_RAMP, mhi - mlo);
+    if (!(ramp > 0.f)) ramp = 0.f;
+    const float tdn = r[RL::TAU_DN], tup = r[RL::TAU_UP];
+    const float psi2 = (mlo <= tup) ? 0.f : (ramp > 0.f ? clamp01((mlo - tup) / ramp) : 1.f);
+    const float psi = (mhi > tdn) ? 1.f : (ramp > 0.f ? clamp01((mhi - tdn + ramp) / ramp) : 0.f);
+    {
+        Acc<M, float, false> u1;
+        const float keep = 1.f - psi2;
+        u1.init(__fmul_ru(keep, __fmul_ru(__fsub_ru(1.f, lam), o)));
+        u1.term(keep * lam, Ua, rUa);
+        out.U = u1.result();
+    }
+    float rU = 0.f;
+#pragma unroll
+    for (int j = 0; j < M; ++j) rU = __fadd_ru(rU, fabsf(out.U.c[j]));
+    out.rU = rU;
+    out.ahi = fminf(o, __fadd_ru(out.U.k, rU));
+    // lower: subtract psi/255, then blend toward 0 where the form dips below 0
+    La.k = __fsub_rd(La.k, __fmul_ru(psi, ALPHA_MIN_UP));
+    float rLa = 0.f;
+#pragma unroll
+    for (int j = 0; j < M; ++j) rLa = __fadd_ru(rLa, fabsf(La.c[j]));
+    const float l2min = __fsub_rd(La.k, rLa), l2max = La.k + rLa;
+    const float mu = (l2min >= 0.f) ? 1.f : ((l2max <= 0.f) ? 0.f : l2max / (l2max - l2min));
+    if ((flags & F_STRADDLE) || mu == 0.f) {
+#pragma unroll
+        for (int j = 0; j < M; ++j) out.L.c[j] = 0.f;
+        out.L.k = 0.f;
+        out.rL = 0.f;
+        out.alo = 0.f;
+    } else if (mu == 1.f) {
+        out.L = La;
+        out.rL = rLa;
+        out.alo = fmaxf(0.f, l2min);
+    } else {
+        Acc<M, float, true> l1;
+        l1.init(0.f);
+        l1.term(mu, La, rLa);
+        out.L = l1.result();
+        float rL = 0.f;
+#pragma unroll
+        for (int j = 0; j < M; ++j) rL = __fadd_ru(rL, fabsf(out.L.c[j]));
+        out.rL = rL;
+        out.alo = fmaxf(0.f, __fsub_rd(out.L.k, rL));
+    }
+}
+
+// Colour accumulator: sum_i w_i F_i per channel, with the rounding error of
+// the round-to-nearest coefficient sums bounded step by step:
+//   each step's error <= min(u * sum_j |acc_j|, w * r_F), and
+//   sum_j |acc_j| <= Q = sum of w * r_F so far.
+template <int M, bool DN> struct ColourAcc {
+    float c[3][M];
+    float k[3];
+    float q[3], err[3];
+    int steps;
+    __device__ __forceinline__ void init()
+    {
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+#pragma unroll
+            for (int j = 0; j < M; ++j) c[ch][j] = 0.f;
+            k[ch] = 0.f; q[ch] = 0.f; err[ch] = 0.f;
+        }
+        steps = 0;
+    }
+    __device__ __forceinline__ void add(float T, const float *col, const LF<M, float> &F, float rF)
+    {
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            const float w = DN ? __fmul_rd(T, col[ch]) : __fmul_ru(T, col[ch]);
+#pragma unroll
+            for (int j = 0; j < M; ++j) c[ch][j] = __fmaf_rn(w, F.c[j], c[ch][j]);
+            k[ch] = DN ? __fmaf_rd(w, F.k, k[ch]) : __fmaf_ru(w, F.k, k[ch]);
+            const float t = __fmul_ru(w, rF);
+            q[ch] = __fadd_ru(q[ch], t);
+            err[ch] = __fadd_ru(err[ch], fminf(__fmul_ru(q[ch], 5.97e-8f), t));
+        }
+        ++steps;
+    }
+    __device__ __forceinline__ float bound(int ch) const
+    {
+        float r = 0.f;
+#pragma unroll
+        for (int j = 0; j < M; ++j) r = __fadd_ru(r, fabsf(c[ch][j]));
+        r = __fadd_ru(__fadd_ru(r, err[ch]), __fmul_ru((float)steps, 1e-36f));
+        return DN ? __fsub_rd(k[ch], r) : __fadd_ru(k[ch], r);
+    }
+};
+
+struct EvInfo {
+    uint32_t rec;   // record index within the cell
+    uint32_t bits;  // bit 0: upper endpoint, bit 1: key equals the previous entry's key
+};
+
+// grid.x = n_cells * n_tiles, block = TS*TS threads
+template <int M, int TS, int CH>
+__global__ void __launch_bounds__(TS *TS) render_kernel(
+    const float *__restrict__ recs, const PixBox *__restrict__ boxes, const uint32_t *__restrict__ seg_start,
+    const uint32_t *__restrict__ seg_end, const uint32_t *__restrict__ entry_ev,
+    const uint32_t *__restrict__ ev_val, const uint64_t *__restrict__ ev_key, int W, int H, int ntx,
+    int n_tiles, int64_t n_gauss, int64_t cell_base, float *__restrict__ out_lo, float *__restrict__ out_hi)
+{
+    using RL = Rec<M>;
+    constexpr int NT = TS * TS;
+    __shared__ __align__(16) float s_rec[CH][RL::WIDTH];
+    __shared__ EvInfo s_ev[CH];
+    __shared__ PixBox s_box[CH];
+
+    const int seg = blockIdx.x;
+    const int cell = seg / n_tiles;
+    const int tile = seg - cell * n_tiles;
+    const int tx = tile % ntx, ty = tile / ntx;
+    const int px = tx * TS + (int)(threadIdx.x % TS);
+    const int py = ty * TS + (int)(threadIdx.x / TS);
+    const bool inside = px < W && py < H;
+    const float ux = px + 0.5f, uy = py + 0.5f;
+
+    const uint32_t b0 = seg_start[seg], b1 = seg_end[seg];
+    const float *rec_cell = recs + (size_t)(cell_base + cell) * n_gauss * RL::WIDTH;
+    const PixBox *box_cell = boxes + (size_t)(cell_base + cell) * n_gauss;
+
+    ColourAcc<M, true> lo;
+    ColourAcc<M, false> hi;
+    lo.init();
+    hi.init();
+    float PA = 1.f, PB = 1.f, PAp = 1.f, PBp = 1.f;
+    // one-entry cache of the last lower-endpoint evaluation
+    uint32_t c_rec = 0xffffffffu;
+    AlphaOut<M> cache;
+
+    for (uint32_t base = b0; base < b1; base += CH) {
+        const int cnt = (int)min((uint32_t)CH, b1 - base);
+        __syncthreads();
+        if (threadIdx.x < (unsigned)cnt) {
+            const uint32_t i = base + threadIdx.x;
+            const uint32_t e = entry_ev[i];
+            const uint32_t v = ev_val[e];
+            uint32_t bits = v & 1u;
+            if (i > b0 && ev_key[entry_ev[i - 1]] == ev_key[e]) bits |= 2u;
+            const uint32_t rec = (v >> 1) - (uint32_t)(cell * n_gauss);
+            s_ev[threadIdx.x] = EvInfo{rec, bits};
+            s_box[threadIdx.x] = box_cell[rec];
+        }
+        __syncthreads();
+        // stage the records of this chunk
+        for (int t = threadIdx.x; t < cnt * (RL::WIDTH / 4); t += NT) {
+            const int e = t / (RL::WIDTH / 4), q = t - e * (RL::WIDTH / 4);
+            const float4 *src = reinterpret_cast<const float4 *>(rec_cell + (size_t)s_ev[e].rec * RL::WIDTH);
+            reinterpret_cast<float4 *>(s_rec[e])[q] = __ldg(src + q);
+        }
+        __syncthreads();
+        if (!inside) continue;
+        for (int e = 0; e < cnt; ++e) {
+            const EvInfo ev = s_ev[e];
+            if (!(ev.bits & 2u)) {
+                PA = __fmul_rd(PA, PAp);
+                PB = __fmul_ru(PB, PBp);
+                PAp = 1.f;
+                PBp = 1.f;
+            }
+            const PixBox bx = s_box[e];
+            if (px < bx.x0 || px > bx.x1 || py < bx.y0 || py > bx.y1) continue;
+            const float *r = s_rec[e];
+            const float col[3] = {r[RL::COL], r[RL::COL + 1], r[RL::COL + 2]};
+            if (!(ev.bits & 1u)) {
+                pixel_alpha<M>(r, ux, uy, cache);
+                c_rec = ev.rec;
+                hi.add(PB, col, cache.U, cache.rU);
+                PAp = __fmul_rd(PAp, __fsub_rd(1.f, cache.ahi));
+            } else {
+                if (c_rec != ev.rec) {
+                    pixel_alpha<M>(r, ux, uy, cache);
+                    c_rec = ev.rec;
+                }
+                const uint32_t flags = __float_as_uint(r[RL::FLAGS]);
+                float T = PA;
+                if (flags & F_OPEN) {
+                    const float den = __fsub_ru(1.f, cache.ahi);
+                    T = (den > 0.f) ? __fdiv_rd(PA, den) : 0.f;
+                }
+                lo.add(T, col, cache.L, cache.rL);
+                PBp = __fmul_ru(PBp, __fsub_ru(1.f, cache.alo));
+            }
+        }
+    }
+    if (inside) {
+        const size_t o = ((size_t)(cell_base + cell) * H * W + (size_t)py * W + px) * 3;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            out_lo[o + ch] = clamp01(lo.bound(ch));
+            out_hi[o + ch] = clamp01(hi.bound(ch));
+        }
+    }
+}
+
+}  // namespace ar

@@ -123,8 +123,10 @@ def box_scene(n: int, seed: int, extent=(20.0, 5.0, 20.0), logscale_mu: float = 
 
 
 def look_camera(width: int, height: int, f: float, centre=(0.0, 0.0, -4.0), near: float = 0.2) -> Camera:
-    """Pinhole camera with identity orientation (looking along +z) at `centre`."""
-    return Camera(width, height, float(f), float(f), width / 2.0, height / 2.0, near,
+    """Pinhole camera with identity orientation (looking along +z) at `centre`.
+    Intrinsics are rounded to float32 so every consumer sees the same values."""
+    f32 = lambda v: float(np.float32(v))
+    return Camera(width, height, f32(f), f32(f), f32(width / 2.0), f32(height / 2.0), f32(near),
                   np.eye(3, dtype=np.float64), np.asarray(centre, dtype=np.float64))
 
 

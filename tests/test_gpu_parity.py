@@ -1,0 +1,191 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, and its soundness.
+
+Tolerance, per colour channel, against the oracle's bounds:
+  |gpu - oracle| <= 1e-4 + cond
+where cond is the oracle's own estimate of how far single-precision
+evaluation of the same relaxation can move that pixel's bounds (it is zero
+unless some Gaussian's Mahalanobis interval is so wide that FP32 cannot carry
+its ends to 1e-4), and at most 0.1 % of the compared pixels may exceed the
+plain 1e-4.  Pixels where a threshold decision taken in single precision lies
+within its rounding band are "fragile": both outcomes are sound there, and
+they are checked for soundness instead.  Soundness: concrete FP64 renders at
+sampled poses lie inside the GPU bounds.  Bit-exact invariances: tile size
+and cell batching.
+"""
+import numpy as np
+import pytest
+
+from paper_2503_00308_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def arlib():
+    from paper_2503_00308_gb300 import _build, ar
+    _build.build()
+    assert torch.cuda.is_available()
+    return ar
+
+
+def gpu_render(ar, scene, cam, lo, hi, tile=0, return_stats=False):
+    lo = np.asarray(lo, dtype=np.float64).reshape(-1, 6)
+    hi = np.asarray(hi, dtype=np.float64).reshape(-1, 6)
+    nc = lo.shape[0]
+    s = ar.Scene(scene)
+    out_lo = torch.full((nc, cam.height, cam.width, 3), -7.0, dtype=torch.float32, device="cuda")
+    out_hi = torch.full_like(out_lo, -7.0)
+    ar.ar_set_profiling(s.handle, True)
+    s.render(cam, lo, hi, out_lo, out_hi, tile=tile)
+    stats = ar.ar_last_render_stats(s.handle)
+    torch.cuda.synchronize()
+    r = out_lo.double().cpu().numpy(), out_hi.double().cpu().numpy()
+    s.close()
+    return (r + (stats,)) if return_stats else r
+
+
+def compare(orc, scene, cam, lo_c, hi_c, glo, ghi, window=None, frag_max=0.03):
+    """Oracle bounds of one cell vs the GPU's; returns (max err, fragile fraction)."""
+    olo, ohi, frag, cond = orc.render_abstract(scene, cam, lo_c, hi_c, window=window, with_cond=True)
+    m = ~np.isnan(olo[..., 0])
+    ok = m & (frag == 0)
+    e = np.maximum(np.abs(glo - olo), np.abs(ghi - ohi)).max(axis=-1)
+    assert np.all(e[ok] <= TOL + cond[ok]), (e[ok] - cond[ok]).max()
+    over = (e[ok] > TOL).sum() / max(1, ok.sum())
+    assert over <= 1e-3, over
+    fr = (m & (frag != 0)).sum() / max(1, m.sum())
+    assert fr <= frag_max, fr
+    return e[ok].max(initial=0), fr
+
+
+def test_tiny64_parity_and_soundness(arlib, orc):
+    w = synth.tiny64()
+    glo, ghi = gpu_render(arlib, w.scene, w.camera, w.cells_lo, w.cells_hi)
+    assert glo.shape == (1, 32, 32, 3) and np.all(glo >= 0) and np.all(ghi <= 1) and np.all(glo <= ghi)
+    compare(orc, w.scene, w.camera, w.cells_lo[0], w.cells_hi[0], glo[0], ghi[0])
+    rng = np.random.default_rng(0)
+    poses = synth.sample_poses(rng, w.cells_lo[0], w.cells_hi[0], 10_000)
+    worst, nv = orc.check_samples(w.scene, w.camera, poses, glo[0], ghi[0], tol=0.0)
+    assert nv == 0, worst
+
+
+def test_point_cell_is_concrete(arlib, orc):
+    w = synth.tiny64()
+    d = np.array([0.004, -0.003, 0.01, 0.002, -0.004, 0.003])
+    glo, ghi = gpu_render(arlib, w.scene, w.camera, d, d)
+    img = orc.render_concrete(w.scene, w.camera, d, "sort")
+    _, _, frag = orc.render_abstract(w.scene, w.camera, d, d)
+    ok = frag == 0
+    assert np.abs(glo[0] - img)[ok].max() < TOL and np.abs(ghi[0] - img)[ok].max() < TOL
+    assert np.all(glo[0] <= img + 1e-12) and np.all(img <= ghi[0] + 1e-12)
+
+
+@pytest.mark.parametrize("hw,splits", [
+    ([0.05, 0.05, 0.05, 0.0, 0.0175, 0.0], [2, 1, 2, 1, 2, 1]),   # 4-DoF like the 10k object
+    ([0.02, 0.02, 0.02, 0.0087, 0.0087, 0.0087], [1, 2, 1, 1, 1, 2]),  # 6-DoF
+])
+def test_object_parity_ragged_tiles(arlib, orc, hw, splits):
+    sc = synth.object_scene(2500, 4)
+    cam = synth.look_camera(72, 56, 80.0, centre=(0, 0, -4))   # 72x56: ragged 16x16 and 8x8 tiles
+    lo, hi = synth.cell_grid(hw, splits)
+    glo, ghi = gpu_render(arlib, sc, cam, lo, hi)
+    for c in range(lo.shape[0]):
+        compare(orc, sc, cam, lo[c], hi[c], glo[c], ghi[c])
+    rng = np.random.default_rng(3)
+    c = lo.shape[0] - 1
+    worst, nv = orc.check_samples(sc, cam, synth.sample_poses(rng, lo[c], hi[c], 300), glo[c], ghi[c])
+    assert nv == 0, worst
+
+
+def test_tile_and_batch_invariance(arlib):
+    sc = synth.object_scene(1500, 6)
+    cam = synth.look_camera(50, 38, 60.0, centre=(0, 0, -4))
+    lo, hi = synth.cell_grid([0.03, 0.0, 0.03, 0.0, 0.01, 0.0], [2, 1, 2, 1, 1, 1])
+    a_lo, a_hi = gpu_render(arlib, sc, cam, lo, hi, tile=16)
+    b_lo, b_hi = gpu_render(arlib, sc, cam, lo, hi, tile=8)
+    assert np.array_equal(a_lo, b_lo) and np.array_equal(a_hi, b_hi)
+    for c in [0, 3]:
+        c_lo, c_hi = gpu_render(arlib, sc, cam, lo[c:c + 1], hi[c:c + 1], tile=16)
+        assert np.array_equal(c_lo[0], a_lo[c]) and np.array_equal(c_hi[0], a_hi[c])
+
+
+def test_edge_cases(arlib, orc):
+    cam = synth.look_camera(20, 17, 24.0, centre=(0, 0, -3))
+    lo = np.array([[-0.01, 0, 0, 0, 0, 0]])
+    hi = -lo
+    # empty scene
+    empty = synth.cube_scene(0, 0)
+    glo, ghi = gpu_render(arlib, empty, cam, lo, hi)
+    assert np.all(glo == 0) and np.all(ghi == 0)
+    # single Gaussian
+    one = synth.cube_scene(1, 3, logscale_mu=-1.5)
+    glo, ghi = gpu_render(arlib, one, cam, lo, hi)
+    compare(orc, one, cam, lo[0], hi[0], glo[0], ghi[0])
+    assert ghi.max() > 0.05
+    # all Gaussians behind the camera
+    back = synth.cube_scene(30, 1)
+    back.uw[:, 2] = -5.0
+    glo, ghi = gpu_render(arlib, back, cam, lo, hi)
+    assert np.all(glo == 0) and np.all(ghi == 0)
+    # opacities below the 1/255 cutoff never contribute
+    faint = synth.cube_scene(30, 2)
+    faint.opacity[:] = 0.003
+    glo, ghi = gpu_render(arlib, faint, cam, lo, hi)
+    assert np.all(ghi == 0)
+    # near-plane straddle
+    near = synth.cube_scene(30, 2, half=0.25, logscale_mu=-2.5)
+    near.uw[:, 2] = np.linspace(-0.85, -0.65, 30).astype(np.float32)
+    camn = synth.look_camera(24, 24, 20.0, centre=(0, 0, -1.0))
+    lo2 = np.array([[-0.02, -0.02, -0.08, 0, 0, 0]])
+    glo, ghi = gpu_render(arlib, near, camn, lo2, -lo2)
+    compare(orc, near, camn, lo2[0], -lo2[0], glo[0], ghi[0])
+    rng = np.random.default_rng(9)
+    worst, nv = orc.check_samples(near, camn, synth.sample_poses(rng, lo2[0], -lo2[0], 500), glo[0], ghi[0])
+    assert nv == 0, worst
+
+
+def test_bad_arguments_rejected(arlib):
+    ar = arlib
+    sc = synth.cube_scene(4, 0)
+    s = ar.Scene(sc)
+    cam = synth.look_camera(8, 8, 8.0)
+    out = torch.zeros((1, 8, 8, 3), device="cuda")
+    with pytest.raises(ar.ArError) as e:
+        s.render(cam, [[0.1, 0, 0, 0, 0, 0]], [[0.0, 0, 0, 0, 0, 0]], out, out)   # lo > hi
+    assert e.value.code == ar.AR_EINVAL
+    with pytest.raises(ar.ArError):
+        s.render(cam, [[0] * 6], [[0] * 6], out, out, tile=12)
+    bad = synth.cube_scene(4, 0)
+    bad.opacity[0] = 1.5
+    with pytest.raises(ar.ArError):
+        ar.Scene(bad)
+    s.close()
+
+
+def test_object10k_cells_sampled(arlib, orc):
+    """The 10k-Gaussian, 200x200, 16-cell workload in one launch; two cells
+    checked against the oracle on pixel windows, one for soundness."""
+    w = synth.object10k()
+    glo, ghi, st = gpu_render(arlib, w.scene, w.camera, w.cells_lo, w.cells_hi, return_stats=True)
+    assert st["n_records"] > 0 and st["m_vars"] == 4
+    for c, win in [(0, (88, 111, 90, 113)), (11, (60, 83, 120, 135))]:
+        compare(orc, w.scene, w.camera, w.cells_lo[c], w.cells_hi[c], glo[c], ghi[c], window=win)
+    rng = np.random.default_rng(5)
+    c = 7
+    worst, nv = orc.check_samples(w.scene, w.camera, synth.sample_poses(rng, w.cells_lo[c], w.cells_hi[c], 64),
+                                  glo[c], ghi[c])
+    assert nv == 0, worst
+
+
+def test_object300k_full_size_sampled(arlib, orc):
+    """The 300k-Gaussian, 800x800, 64-cell workload in the launch configuration
+    the benchmark times; oracle on small pixel windows of two cells."""
+    w = synth.object300k()
+    glo, ghi, st = gpu_render(arlib, w.scene, w.camera, w.cells_lo, w.cells_hi, return_stats=True)
+    assert st["m_vars"] == 6 and st["n_fallback"] < st["n_records"] // 100
+    for c, win in [(0, (396, 403, 396, 403)), (45, (300, 305, 480, 485))]:
+        compare(orc, w.scene, w.camera, w.cells_lo[c], w.cells_hi[c], glo[c], ghi[c], window=win, frag_max=0.2)
+    assert np.all(glo <= ghi)
