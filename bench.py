@@ -31,20 +31,14 @@ UNIT = "pixel-cells/s"
 SMS, FP32_LANES, MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_MHZ * 1e6 / 1e12   # FMA = 2 flops
 
-# FP32 operations of the per-(pixel, Gaussian, cell) relaxation as defined
-# (Delta, q, m, Exp, cutoff ramps and both colour accumulations), FMA = 2,
-# counted once per triple inside a screen box.  See the derivation in the
-# design notes; M is the number of pose variables in the forms.
+# FP32 operations of the per-(pixel, Gaussian, cell) relaxation, counted once
+# per triple inside a screen box (FMA = 2 flops; an IEEE divide or expf = 10):
+# Delta (2 forms), q (3 x two averaged-McCormick products), m (3 squares),
+# the Exp/cutoff/clip stage and both colour accumulations, including the
+# rounding-error terms that keep FP32 bounds sound.  With M pose variables
+# this is 49 M + 132 FMAs and 15 M + 340 other operations: 113 M + 604 flops.
 def flops_per_triple(M: int) -> int:
-    F = M + 1
-    delta = 2 * 2 * (2 * 2 * F) + 2 * 2 * (2 * M)          # two forms x two sides x 2 FMA per coeff + concretise
-    mul = 2 * (2 * 2 * F) + 20                               # one averaged-McCormick product (both sides)
-    q = 3 * (2 * mul + 2 * (2 * M))                          # 3 components: 2 products + concretise
-    sq = 2 * F * 2 + 12                                      # tangent + secant
-    m = 3 * sq + 2 * (2 * M)
-    exp_stage = 2 * (2 * F) + 4 * M + 60                     # two forms from m, radii, ramps, exp
-    accum = 2 * 3 * (2 * F + 6)                              # lower + upper colour forms, 3 channels
-    return delta + q + m + exp_stage + accum
+    return 113 * M + 604
 
 
 def parse():
