@@ -124,6 +124,30 @@ int ar_render_abstract_host(ar_scene *scene, const ar_intrinsics *intr, const ar
                             const ar_pose_box *cells, int32_t n_cells, int32_t tile,
                             float *host_lower, float *host_upper, void *cuda_stream);
 
+/* ar_render_abstract without any allocation.  The paper has no counterpart:
+ * this entry point exists for callers that may not allocate memory while
+ * they run (a real-time loop or embedded verifier that fixes its memory up
+ * front, or a host under a strict GPU memory budget where cudaMalloc would
+ * stall or fail).  It computes the same bounds with the same kernels, but
+ * places every per-call buffer in one 64 MiB array compiled into libar
+ * instead of growing the scene's workspace, and calls neither cudaMalloc,
+ * cudaFree nor any other allocating routine.
+ *   - Every GPU that loads libar holds the 64 MiB array until the process
+ *     exits.  Requests whose buffers need more (roughly: many cells x
+ *     Gaussians, or many tile entries) fail with AR_ENOMEM and a message
+ *     naming the limit; the outputs are then left untouched.
+ *   - The first call on each device looks up the array's device address;
+ *     make that first call before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents: two
+ *     calls that overlap on the GPU (different streams or threads without
+ *     ordering) race and corrupt each other's results.  Serialise them.
+ *   - The call synchronises once with cuda_stream (to read two counters),
+ *     like ar_render_abstract.
+ * Arguments, output layout and other errors as for ar_render_abstract. */
+int ar_render_abstract_noalloc(ar_scene *scene, const ar_intrinsics *intr, const ar_nominal_pose *pose,
+                               const ar_pose_box *cells, int32_t n_cells, int32_t tile,
+                               float *out_lower, float *out_upper, void *cuda_stream);
+
 /* Plain comparison path: the same bounds computed one cell per launch
  * sequence in FP64 with directed rounding, without cell batching.  Same
  * arguments and output layout as ar_render_abstract. */

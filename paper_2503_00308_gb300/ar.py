@@ -65,6 +65,7 @@ def lib():
             "ar_render_abstract": ([P, P, P, P, c_int32, c_int32, P, P, P], ctypes.c_int),
             "ar_render_abstract_host": ([P, P, P, P, c_int32, c_int32, P, P, P], ctypes.c_int),
             "ar_render_abstract_plain_fp64": ([P, P, P, P, c_int32, c_int32, P, P, P], ctypes.c_int),
+            "ar_render_abstract_noalloc": ([P, P, P, P, c_int32, c_int32, P, P, P], ctypes.c_int),
             "ar_render_concrete": ([P, P, P, P, c_int32, P, P], ctypes.c_int),
             "ar_set_profiling": ([P, ctypes.c_int], ctypes.c_int),
             "ar_last_render_stats": ([P, P], ctypes.c_int),
@@ -158,6 +159,13 @@ def ar_render_abstract_plain_fp64(scene, intr, pose, cells, n_cells, tile, out_l
     return check(lib().ar_render_abstract_plain_fp64(scene, ctypes.byref(intr), ctypes.byref(pose), cells,
                                                      int(n_cells), int(tile), _ptr(out_lower), _ptr(out_upper),
                                                      _ptr(stream)))
+
+
+def ar_render_abstract_noalloc(scene, intr, pose, cells, n_cells, tile, out_lower, out_upper, stream=0):
+    """The abstract render without any allocation (fixed 64 MiB scratch inside libar)."""
+    return check(lib().ar_render_abstract_noalloc(scene, ctypes.byref(intr), ctypes.byref(pose), cells,
+                                                  int(n_cells), int(tile), _ptr(out_lower), _ptr(out_upper),
+                                                  _ptr(stream)))
 
 
 def ar_render_concrete(scene, intr, pose, deltas, n_poses, out, stream=0):

@@ -88,6 +88,14 @@ static int fail(int code, const char *fmt, ...)
 
 const char *ar_last_error(void) { return g_err.c_str(); }
 
+namespace ar {
+int set_last_error(int code, const char *msg)
+{
+    g_err = msg;
+    return code;
+}
+}  // namespace ar
+
 // --------------------------------------------------------------- buffers
 namespace ar {
 
@@ -140,16 +148,6 @@ size_t Workspace::bytes() const
 
 }  // namespace ar
 
-struct ar_scene {
-    int device = 0;
-    int64_t n = 0;
-    float *uw = nullptr, *ls = nullptr, *quat = nullptr, *opac = nullptr, *rgb = nullptr;
-    double *Mw = nullptr, *tau = nullptr;
-    Workspace ws;
-    bool profiling = false;
-    ar_render_stats stats;
-    cudaStream_t stats_stream = nullptr;
-};
 
 static bool finite3(const float *v, int64_t n, int k)
 {

@@ -32,6 +32,8 @@ struct Workspace {
     size_t bytes() const;
 };
 
+int set_last_error(int code, const char *msg);  // sets ar_last_error() for this thread
+
 int validate_call(const ar_intrinsics *in, const ar_nominal_pose *pose, const ar_pose_box *cells, int32_t n_cells,
                   int32_t tile);
 int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_nominal_pose *pose,
@@ -39,3 +41,15 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
                 cudaStream_t st, bool profiling, ar_render_stats *stats);
 
 }  // namespace ar
+
+// A scene: the Gaussians on one device plus the workspace of its renders.
+struct ar_scene {
+    int device = 0;
+    int64_t n = 0;
+    float *uw = nullptr, *ls = nullptr, *quat = nullptr, *opac = nullptr, *rgb = nullptr;
+    double *Mw = nullptr, *tau = nullptr;
+    ar::Workspace ws;
+    bool profiling = false;
+    ar_render_stats stats;
+    cudaStream_t stats_stream = nullptr;
+};
