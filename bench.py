@@ -214,7 +214,7 @@ def run_ours(args, rank, world, local, pg):
     if rank != 0:
         return
     M = stats["m_vars"]
-    flops = flops_per_triple(M) * stats["n_triples"]
+    flops = flops_per_triple(M) * stats["n_evaluated"]
     r_ms = statistics.mean(render_ms)
     achieved = flops / (r_ms / 1e3) / 1e12
     line = {
@@ -230,12 +230,13 @@ def run_ours(args, rank, world, local, pg):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
                      "kernel": "render_kernel", "kernel_ms": r_ms,
-                     "flops_per_triple": flops_per_triple(M), "triples": stats["n_triples"],
+                     "flops_per_triple": flops_per_triple(M), "triples_evaluated": stats["n_evaluated"],
+                     "triples_in_boxes": stats["n_triples"],
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal, no measured FP32 peak)"},
         "stages_ms": {"prep": stats["ms_prep"], "bin": stats["ms_bin"], "render": stats["ms_render"],
                       "total": stats["ms_total"]},
         "counts": {"records": stats["n_records"], "entries": stats["n_entries"], "triples": stats["n_triples"],
-                   "fallback": stats["n_fallback"]},
+                   "evaluated": stats["n_evaluated"], "fallback": stats["n_fallback"]},
     }
     if not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_window)

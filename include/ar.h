@@ -79,6 +79,8 @@ typedef struct ar_render_stats {
     int32_t tile;               /* tile edge used (pixels) */
     int32_t m_vars;             /* pose variables carried by the linear forms */
     float ms_prep, ms_bin, ms_render, ms_total;
+    int64_t n_evaluated;        /* per-pixel opacity evaluations (triples the sweep reached
+                                   before each pixel's bounds were settled) */
 } ar_render_stats;
 
 /* Create a scene from n Gaussians <uw, Mw, o, c> (Sec. 2.2).  Mw is given by
@@ -104,8 +106,10 @@ int ar_scene_destroy(ar_scene *scene);
  * partitioning of Sec. 4.2 batched into one call): per cell, per pixel, RGB
  * lower and upper bounds.
  *   cells[n_cells] (host memory), n_cells >= 1.
- *   tile: 0 = choose, else 8 or 16 (screen tile edge of the binning; results
- *   do not depend on it).
+ *   tile: 0 = choose, else 8 or 16 (screen tile edge of the binning; the
+ *   bounds do not depend on it beyond 1e-7: a pixel stops sweeping once what
+ *   is left of its tile's list can move its bounds by less than 5e-8, and
+ *   widens them by that much).
  *   out_lower, out_upper: device pointers, float32 [n_cells][H][W][3] each,
  *   owned by the caller.
  * Work is enqueued on cuda_stream; the call returns after the last launch is

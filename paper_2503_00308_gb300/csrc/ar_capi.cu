@@ -194,6 +194,11 @@ int ar_scene_create(const float *uw3, const float *logscale3, const float *quat4
     ar_scene *s = new ar_scene();
     cudaGetDevice(&s->device);
     s->n = n;
+    {
+        double omax = 0.0;
+        for (int64_t i = 0; i < n; ++i) omax = std::fmax(omax, (double)h_o[i]);
+        s->k_open = (float)(1.0 / (1.0 - omax)) * 1.0001f + 1e-6f;
+    }
     std::memset(&s->stats, 0, sizeof s->stats);
     if (n > 0) {
         float **dp[5] = {&s->uw, &s->ls, &s->quat, &s->opac, &s->rgb};
@@ -419,8 +424,10 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
     rl.ev_key = bo.ev_key;
     rl.W = W; rl.H = H; rl.ntx = ntx; rl.n_tiles = n_tiles; rl.n_cells = n_cells;
     rl.n_gauss = s->n;
+    rl.k_open = s->k_open;
     rl.out_lo = out_lo;
     rl.out_hi = out_hi;
+    rl.n_eval = ws.counters.as<unsigned long long>() + 4;
     if (launch_render(M, TS, rl, st)) return fail(AR_EDEVICE, "render launch: %s", cudaGetErrorString(cudaGetLastError()));
     ++launches;
     if (profiling) CK(cudaEventRecord(ws.ev[3], st));
@@ -432,6 +439,11 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
 int finish_stats(Workspace &ws, cudaStream_t st, bool profiling, ar_render_stats &rs)
 {
     CK(cudaStreamSynchronize(st));
+    if (rs.n_records > 0 && ws.counters.p) {
+        unsigned long long ev = 0;
+        CK(cudaMemcpy(&ev, ws.counters.as<unsigned long long>() + 4, sizeof ev, cudaMemcpyDeviceToHost));
+        rs.n_evaluated = (int64_t)ev;
+    }
     if (profiling && ws.ev_init && rs.n_records > 0) {
         CK(cudaEventElapsedTime(&rs.ms_prep, ws.ev[0], ws.ev[1]));
         CK(cudaEventElapsedTime(&rs.ms_bin, ws.ev[1], ws.ev[2]));

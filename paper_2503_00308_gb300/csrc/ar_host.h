@@ -48,6 +48,7 @@ struct ar_scene {
     int64_t n = 0;
     float *uw = nullptr, *ls = nullptr, *quat = nullptr, *opac = nullptr, *rgb = nullptr;
     double *Mw = nullptr, *tau = nullptr;
+    float k_open = 1.f;  // 1 / (1 - largest opacity), rounded up (bounds skipped lower-sum terms)
     ar::Workspace ws;
     bool profiling = false;
     ar_render_stats stats;

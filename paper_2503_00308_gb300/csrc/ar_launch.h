@@ -16,7 +16,9 @@ struct RenderLaunch {
     const uint64_t *ev_key;
     int W, H, ntx, n_tiles, n_cells;
     int64_t n_gauss;
+    float k_open;                     // 1 / (1 - largest opacity), rounded up
     float *out_lo, *out_hi;
+    unsigned long long *n_eval;       // optional counter of per-pixel opacity evaluations
 };
 
 size_t cell_data_bytes(int M);

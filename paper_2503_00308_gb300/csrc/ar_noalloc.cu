@@ -201,8 +201,10 @@ int ar_render_abstract_noalloc(ar_scene *s, const ar_intrinsics *in, const ar_no
     rl.ev_key = bo.ev_key;
     rl.W = W; rl.H = H; rl.ntx = ntx; rl.n_tiles = n_tiles; rl.n_cells = n_cells;
     rl.n_gauss = s->n;
+    rl.k_open = s->k_open;
     rl.out_lo = out_lower;
     rl.out_hi = out_upper;
+    rl.n_eval = nullptr;
     if (launch_render(M, TS, rl, st)) return set_last_error(AR_EDEVICE, cudaGetErrorString(cudaGetLastError()));
     return AR_OK;
 }

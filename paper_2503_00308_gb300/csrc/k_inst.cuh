@@ -38,11 +38,11 @@ int AR_CAT(launch_render_m, AR_M)(int TS, const RenderLaunch &a, cudaStream_t st
     if (TS == 16)
         render_kernel<AR_M, 16, 32><<<nseg, 256, 0, st>>>(a.recs, a.boxes, a.seg_start, a.seg_end, a.ent_ev,
                                                            a.ev_val, a.ev_key, a.W, a.H, a.ntx, a.n_tiles,
-                                                           a.n_gauss, 0, a.out_lo, a.out_hi);
+                                                           a.n_gauss, 0, a.k_open, a.out_lo, a.out_hi, a.n_eval);
     else
         render_kernel<AR_M, 8, 32><<<nseg, 64, 0, st>>>(a.recs, a.boxes, a.seg_start, a.seg_end, a.ent_ev,
                                                          a.ev_val, a.ev_key, a.W, a.H, a.ntx, a.n_tiles,
-                                                         a.n_gauss, 0, a.out_lo, a.out_hi);
+                                                         a.n_gauss, 0, a.k_open, a.out_lo, a.out_hi, a.n_eval);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 

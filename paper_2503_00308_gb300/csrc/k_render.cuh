@@ -214,13 +214,26 @@ template <int M, bool DN> struct ColourAcc {
         }
         ++steps;
     }
-    __device__ __forceinline__ float bound(int ch) const
+    __device__ __forceinline__ float radius(int ch) const
     {
         float r = 0.f;
 #pragma unroll
         for (int j = 0; j < M; ++j) r = __fadd_ru(r, fabsf(c[ch][j]));
-        r = __fadd_ru(__fadd_ru(r, err[ch]), __fmul_ru((float)steps, 1e-36f));
+        return __fadd_ru(__fadd_ru(r, err[ch]), __fmul_ru((float)steps, 1e-36f));
+    }
+    // the outward concretisation of the accumulated form
+    __device__ __forceinline__ float bound(int ch) const
+    {
+        const float r = radius(ch);
         return DN ? __fsub_rd(k[ch], r) : __fadd_ru(k[ch], r);
+    }
+    // constant minus radius rounded up: at least the computed lower bound
+    __device__ __forceinline__ float upper_min(int ch) const
+    {
+        float r = 0.f;
+#pragma unroll
+        for (int j = 0; j < M; ++j) r = __fadd_rd(r, fabsf(c[ch][j]));
+        return __fsub_ru(k[ch], __fadd_rd(r, err[ch]));
     }
 };
 
@@ -229,13 +242,35 @@ struct EvInfo {
     uint32_t bits;  // bit 0: upper endpoint, bit 1: key equals the previous entry's key
 };
 
+// Early exit, only where the clipped result is already decided, so that the
+// output is bit-identical to the full sweep (and independent of the tile):
+//  - upper: a later term T_hi c U has U >= a >= 0 at every pose of the cell,
+//    so the constant of its U form is >= 0 and the upward-rounded constant of
+//    the upper sum only grows; its final bound is at least that constant, so
+//    once the constant is >= 1 in every channel the clipped bound is 1;
+//  - lower: a later term T_lo c L has max|L| <= 1 over the cell (so its
+//    constant plus its coefficient radius is <= 1) and T_lo at most the
+//    product absorbed so far over (1 - its own opacity) <= PA / (1 - o_max);
+//    with E = (events left) PA / (1 - o_max) the final constant is at most
+//    the current one + E and the final radius at least the current one - E,
+//    so once (constant - radius) + 2E <= 0 in every channel the clipped
+//    bound is 0.
+// Otherwise a side also stops once twice the bound on everything the
+// remaining events could still add is below EXIT_EPS (E as above for the
+// lower side; for the upper side (events left) x 1.1 x PB, since T_hi of a
+// later Gaussian is at most PB and max U <= 1.1); the bound is then widened
+// by that amount, which keeps it sound and within EXIT_EPS of the full sweep.
+// A pixel stops when both sides have; a tile stops when all its pixels have.
+constexpr float EXIT_EPS = 5e-8f;
+
 // grid.x = n_cells * n_tiles, block = TS*TS threads
 template <int M, int TS, int CH>
 __global__ void __launch_bounds__(TS *TS) render_kernel(
     const float *__restrict__ recs, const PixBox *__restrict__ boxes, const uint32_t *__restrict__ seg_start,
     const uint32_t *__restrict__ seg_end, const uint32_t *__restrict__ entry_ev,
     const uint32_t *__restrict__ ev_val, const uint64_t *__restrict__ ev_key, int W, int H, int ntx,
-    int n_tiles, int64_t n_gauss, int64_t cell_base, float *__restrict__ out_lo, float *__restrict__ out_hi)
+    int n_tiles, int64_t n_gauss, int64_t cell_base, float k_open, float *__restrict__ out_lo,
+    float *__restrict__ out_hi, unsigned long long *__restrict__ n_eval)
 {
     using RL = Rec<M>;
     constexpr int NT = TS * TS;
@@ -264,10 +299,32 @@ __global__ void __launch_bounds__(TS *TS) render_kernel(
     // one-entry cache of the last lower-endpoint evaluation
     uint32_t c_rec = 0xffffffffu;
     AlphaOut<M> cache;
+    bool done = !inside;
+    float lo_adj = 0.f, hi_adj = 0.f;  // -1: decided 0 / 1; >= 0: widening for skipped events
+    uint32_t evals = 0;
 
     for (uint32_t base = b0; base < b1; base += CH) {
         const int cnt = (int)min((uint32_t)CH, b1 - base);
-        __syncthreads();
+        if (!done) {
+            const float left = (float)(b1 - base);
+            // PA is rounded down; 1.01 covers its relative error for < 10^5 factors
+            const float elo2 = __fmul_ru(2.f, __fmul_ru(__fmul_ru(left, __fmul_ru(PA, 1.01f)), k_open));
+            const float ehi2 = __fmul_ru(2.2f, __fmul_ru(left, PB));
+            bool lo_zero = true, hi_one = true;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                lo_zero = lo_zero && __fadd_ru(lo.upper_min(ch), elo2) <= 0.f;
+                hi_one = hi_one && hi.k[ch] >= 1.f;
+            }
+            const bool lo_dec = lo_zero || elo2 <= EXIT_EPS;
+            const bool hi_dec = hi_one || ehi2 <= EXIT_EPS;
+            if (lo_dec && hi_dec) {
+                done = true;
+                lo_adj = lo_zero ? -1.f : elo2;
+                hi_adj = hi_one ? -1.f : ehi2;
+            }
+        }
+        if (__syncthreads_and(done)) break;
         if (threadIdx.x < (unsigned)cnt) {
             const uint32_t i = base + threadIdx.x;
             const uint32_t e = entry_ev[i];
@@ -286,7 +343,7 @@ __global__ void __launch_bounds__(TS *TS) render_kernel(
             reinterpret_cast<float4 *>(s_rec[e])[q] = __ldg(src + q);
         }
         __syncthreads();
-        if (!inside) continue;
+        if (done) continue;
         for (int e = 0; e < cnt; ++e) {
             const EvInfo ev = s_ev[e];
             if (!(ev.bits & 2u)) {
@@ -302,6 +359,7 @@ __global__ void __launch_bounds__(TS *TS) render_kernel(
             if (!(ev.bits & 1u)) {
                 pixel_alpha<M>(r, ux, uy, cache);
                 c_rec = ev.rec;
+                ++evals;
                 hi.add(PB, col, cache.U, cache.rU);
                 PAp = __fmul_rd(PAp, __fsub_rd(1.f, cache.ahi));
             } else {
@@ -324,9 +382,13 @@ __global__ void __launch_bounds__(TS *TS) render_kernel(
         const size_t o = ((size_t)(cell_base + cell) * H * W + (size_t)py * W + px) * 3;
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
-            out_lo[o + ch] = clamp01(lo.bound(ch));
-            out_hi[o + ch] = clamp01(hi.bound(ch));
+            out_lo[o + ch] = lo_adj < 0.f ? 0.f : clamp01(__fsub_rd(lo.bound(ch), lo_adj));
+            out_hi[o + ch] = hi_adj < 0.f ? 1.f : clamp01(__fadd_ru(hi.bound(ch), hi_adj));
         }
+    }
+    if (n_eval) {
+        const uint32_t w = __reduce_add_sync(0xffffffffu, evals);
+        if ((threadIdx.x & 31) == 0 && w) atomicAdd(n_eval, (unsigned long long)w);
     }
 }
 
