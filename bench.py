@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-window", type=int, default=16, help="edge of the oracle's pixel sample")
+    ap.add_argument("--cells", type=int, default=0, help="use only the first N cells (profiling slices)")
     return ap.parse_args()
 
 
@@ -152,6 +153,9 @@ def run_ours(args, rank, world, local, pg):
         pg.barrier()
     torch.cuda.set_device(local)
     w = synth.WORKLOADS[args.workload]()
+    if args.cells:
+        w.cells_lo, w.cells_hi = w.cells_lo[:args.cells], w.cells_hi[:args.cells]
+        w.name += "[%d cells]" % w.n_cells
     cam = w.camera
     nc = w.n_cells
     s = ar.Scene(w.scene)
@@ -236,7 +240,8 @@ def run_ours(args, rank, world, local, pg):
         "stages_ms": {"prep": stats["ms_prep"], "bin": stats["ms_bin"], "render": stats["ms_render"],
                       "total": stats["ms_total"]},
         "counts": {"records": stats["n_records"], "entries": stats["n_entries"], "triples": stats["n_triples"],
-                   "evaluated": stats["n_evaluated"], "fallback": stats["n_fallback"]},
+                   "evaluated": stats["n_evaluated"], "reevaluated": stats["n_reevaluated"],
+                   "fallback": stats["n_fallback"]},
     }
     if not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_window)

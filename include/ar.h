@@ -81,6 +81,8 @@ typedef struct ar_render_stats {
     float ms_prep, ms_bin, ms_render, ms_total;
     int64_t n_evaluated;        /* per-pixel opacity evaluations (triples the sweep reached
                                    before each pixel's bounds were settled) */
+    int64_t n_reevaluated;      /* evaluations repeated at an upper depth endpoint because the
+                                   lower endpoint's result had left the per-pixel ring */
 } ar_render_stats;
 
 /* Create a scene from n Gaussians <uw, Mw, o, c> (Sec. 2.2).  Mw is given by

@@ -25,6 +25,7 @@ struct BinArgs {
     uint32_t *hist;          // >= radix_hist_words(max(n_events, n_entries))
     uint32_t *scan_tmp;      // >= scan_temp_words(largest scanned length)
     uint32_t *seg_start, *seg_end;  // [n_segments]
+    uint32_t *seg_k[2], *seg_v[2];  // [n_segments] x2 each: segment order by length
 };
 
 struct BinOut {
@@ -32,6 +33,7 @@ struct BinOut {
     const uint32_t *ev_val;  // sorted event values: 2 * pair + (upper endpoint)
     const uint32_t *ent_seg; // entries sorted by segment
     const uint32_t *ent_ev;  // entry -> sorted event index
+    const uint32_t *seg_order;  // segments, longest first
 };
 
 size_t scan_temp_words(uint64_t n);

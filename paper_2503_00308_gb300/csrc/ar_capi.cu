@@ -126,8 +126,8 @@ void DevBuf::release()
 void Workspace::release()
 {
     DevBuf *all[] = {&cells_lohi, &cells, &vN, &recs, &boxes, &keys, &counters, &evk0, &evk1, &evv0, &evv1,
-                     &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege, &out_lo,
-                     &out_hi};
+                     &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege, &segk0,
+                     &segk1, &segv0, &segv1, &work, &out_lo, &out_hi};
     for (DevBuf *b : all) b->release();
     if (h_counters) cudaFreeHost(h_counters);
     h_counters = nullptr;
@@ -140,7 +140,7 @@ size_t Workspace::bytes() const
 {
     const DevBuf *all[] = {&cells_lohi, &cells, &vN, &recs, &boxes, &keys, &counters, &evk0, &evk1, &evv0, &evv1,
                            &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege,
-                           &out_lo, &out_hi};
+                           &segk0, &segk1, &segv0, &segv1, &work, &out_lo, &out_hi};
     size_t s = 0;
     for (const DevBuf *b : all) s += b->cap;
     return s;
@@ -371,7 +371,7 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
     // -- binning
     const uint64_t nsc = n_pairs > ne ? n_pairs : ne;
     const uint64_t nsort = ne > nent ? ne : nent;
-    const uint64_t hist_words = radix_hist_words(nsort) + 64;
+    const uint64_t hist_words = radix_hist_words(nsort > n_seg ? nsort : n_seg) + 64;
     uint64_t scan_len = nsc > hist_words ? nsc : hist_words;
     RK(ws.evk0.ensure(sizeof(uint64_t) * (ne + 1)));
     RK(ws.evk1.ensure(sizeof(uint64_t) * (ne + 1)));
@@ -389,6 +389,11 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
     RK(ws.scan.ensure(sizeof(uint32_t) * (scan_temp_words(scan_len) + 64)));
     RK(ws.segs.ensure(sizeof(uint32_t) * n_seg));
     RK(ws.sege.ensure(sizeof(uint32_t) * n_seg));
+    RK(ws.segk0.ensure(sizeof(uint32_t) * n_seg));
+    RK(ws.segk1.ensure(sizeof(uint32_t) * n_seg));
+    RK(ws.segv0.ensure(sizeof(uint32_t) * n_seg));
+    RK(ws.segv1.ensure(sizeof(uint32_t) * n_seg));
+    RK(ws.work.ensure(256));
     BinArgs ba;
     ba.boxes = ws.boxes.as<PixBox>();
     ba.keys = ws.keys.as<double>();
@@ -409,6 +414,8 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
     ba.scan_tmp = ws.scan.as<uint32_t>();
     ba.seg_start = ws.segs.as<uint32_t>();
     ba.seg_end = ws.sege.as<uint32_t>();
+    ba.seg_k[0] = ws.segk0.as<uint32_t>(); ba.seg_k[1] = ws.segk1.as<uint32_t>();
+    ba.seg_v[0] = ws.segv0.as<uint32_t>(); ba.seg_v[1] = ws.segv1.as<uint32_t>();
     BinOut bo;
     if (run_binning(ba, bo, st, &launches))
         return fail(AR_EDEVICE, "binning: %s", cudaGetErrorString(cudaGetLastError()));
@@ -419,6 +426,8 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
     rl.boxes = ws.boxes.as<PixBox>();
     rl.seg_start = ws.segs.as<uint32_t>();
     rl.seg_end = ws.sege.as<uint32_t>();
+    rl.seg_order = bo.seg_order;
+    rl.work = ws.work.as<unsigned int>();
     rl.ent_ev = bo.ent_ev;
     rl.ev_val = bo.ev_val;
     rl.ev_key = bo.ev_key;
@@ -427,7 +436,7 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
     rl.k_open = s->k_open;
     rl.out_lo = out_lo;
     rl.out_hi = out_hi;
-    rl.n_eval = ws.counters.as<unsigned long long>() + 4;
+    rl.counters = ws.counters.as<unsigned long long>() + 4;
     if (launch_render(M, TS, rl, st)) return fail(AR_EDEVICE, "render launch: %s", cudaGetErrorString(cudaGetLastError()));
     ++launches;
     if (profiling) CK(cudaEventRecord(ws.ev[3], st));
@@ -440,9 +449,10 @@ int finish_stats(Workspace &ws, cudaStream_t st, bool profiling, ar_render_stats
 {
     CK(cudaStreamSynchronize(st));
     if (rs.n_records > 0 && ws.counters.p) {
-        unsigned long long ev = 0;
-        CK(cudaMemcpy(&ev, ws.counters.as<unsigned long long>() + 4, sizeof ev, cudaMemcpyDeviceToHost));
-        rs.n_evaluated = (int64_t)ev;
+        unsigned long long ev[2] = {0, 0};
+        CK(cudaMemcpy(ev, ws.counters.as<unsigned long long>() + 4, sizeof ev, cudaMemcpyDeviceToHost));
+        rs.n_evaluated = (int64_t)ev[0];
+        rs.n_reevaluated = (int64_t)ev[1];
     }
     if (profiling && ws.ev_init && rs.n_records > 0) {
         CK(cudaEventElapsedTime(&rs.ms_prep, ws.ev[0], ws.ev[1]));

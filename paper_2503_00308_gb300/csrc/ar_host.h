@@ -23,7 +23,7 @@ struct DevBuf {
 struct Workspace {
     DevBuf cells_lohi, cells, vN, recs, boxes, keys, counters;
     DevBuf evk0, evk1, evv0, evv1, ents0, ents1, ente0, ente1;
-    DevBuf ua, ub, uc, ud, hist, scan, segs, sege;
+    DevBuf ua, ub, uc, ud, hist, scan, segs, sege, segk0, segk1, segv0, segv1, work;
     DevBuf out_lo, out_hi;
     unsigned long long *h_counters = nullptr;  // page-locked
     cudaEvent_t ev[4];

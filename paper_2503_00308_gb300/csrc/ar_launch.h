@@ -12,13 +12,14 @@ struct PixBox;
 struct RenderLaunch {
     const float *recs;
     const PixBox *boxes;
-    const uint32_t *seg_start, *seg_end, *ent_ev, *ev_val;
+    const uint32_t *seg_start, *seg_end, *seg_order, *ent_ev, *ev_val;
     const uint64_t *ev_key;
     int W, H, ntx, n_tiles, n_cells;
     int64_t n_gauss;
     float k_open;                     // 1 / (1 - largest opacity), rounded up
     float *out_lo, *out_hi;
-    unsigned long long *n_eval;       // optional counter of per-pixel opacity evaluations
+    unsigned long long *counters;     // optional: [0] opacity evaluations, [1] re-evaluations
+    unsigned int *work;               // segment counter of the persistent grid (zeroed by the launcher)
 };
 
 size_t cell_data_bytes(int M);

@@ -141,6 +141,9 @@ int ar_render_abstract_noalloc(ar_scene *s, const ar_intrinsics *in, const ar_no
     double *keys = A.take<double>(2 * n_pairs);
     unsigned long long *counters = A.take<unsigned long long>(8);
     uint32_t *seg_start = A.take<uint32_t>(n_seg), *seg_end = A.take<uint32_t>(n_seg);
+    uint32_t *seg_k0 = A.take<uint32_t>(n_seg), *seg_k1 = A.take<uint32_t>(n_seg);
+    uint32_t *seg_v0 = A.take<uint32_t>(n_seg), *seg_v1 = A.take<uint32_t>(n_seg);
+    unsigned int *work = A.take<unsigned int>(64);
     if (A.over) return too_big("the per-(Gaussian, cell) records", A.used);
 
     // pose cells: lo and hi rows straight from the caller's array (no staging copy)
@@ -161,7 +164,7 @@ int ar_render_abstract_noalloc(ar_scene *s, const ar_intrinsics *in, const ar_no
     // buffers sized by the counts
     const uint64_t nsc = n_pairs > ne ? n_pairs : ne;
     const uint64_t nsort = ne > nent ? ne : nent;
-    const uint64_t hist_words = radix_hist_words(nsort) + 64;
+    const uint64_t hist_words = radix_hist_words(nsort > n_seg ? nsort : n_seg) + 64;
     const uint64_t scan_len = nsc > hist_words ? nsc : hist_words;
     BinArgs ba;
     ba.boxes = boxes;
@@ -187,6 +190,8 @@ int ar_render_abstract_noalloc(ar_scene *s, const ar_intrinsics *in, const ar_no
     ba.scan_tmp = A.take<uint32_t>(scan_temp_words(scan_len) + 64);
     ba.seg_start = seg_start;
     ba.seg_end = seg_end;
+    ba.seg_k[0] = seg_k0; ba.seg_k[1] = seg_k1;
+    ba.seg_v[0] = seg_v0; ba.seg_v[1] = seg_v1;
     if (A.over) return too_big("the depth-sorted tile bins", A.used);
     int launches = 0;
     BinOut bo;
@@ -196,6 +201,8 @@ int ar_render_abstract_noalloc(ar_scene *s, const ar_intrinsics *in, const ar_no
     rl.boxes = boxes;
     rl.seg_start = seg_start;
     rl.seg_end = seg_end;
+    rl.seg_order = bo.seg_order;
+    rl.work = work;
     rl.ent_ev = bo.ent_ev;
     rl.ev_val = bo.ev_val;
     rl.ev_key = bo.ev_key;
@@ -204,7 +211,7 @@ int ar_render_abstract_noalloc(ar_scene *s, const ar_intrinsics *in, const ar_no
     rl.k_open = s->k_open;
     rl.out_lo = out_lower;
     rl.out_hi = out_upper;
-    rl.n_eval = nullptr;
+    rl.counters = nullptr;
     if (launch_render(M, TS, rl, st)) return set_last_error(AR_EDEVICE, cudaGetErrorString(cudaGetLastError()));
     return AR_OK;
 }

@@ -280,6 +280,16 @@ __global__ void emit_entries_kernel(const uint32_t *__restrict__ ev_val, uint64_
         }
 }
 
+// key = ~length so that an ascending stable sort puts the longest first
+__global__ void seg_len_kernel(const uint32_t *__restrict__ start, const uint32_t *__restrict__ end, uint64_t n,
+                               uint32_t *__restrict__ key, uint32_t *__restrict__ val)
+{
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    key[i] = ~(end[i] - start[i]);
+    val[i] = (uint32_t)i;
+}
+
 __global__ void seg_bounds_kernel(const uint32_t *__restrict__ seg, uint64_t n, uint32_t *__restrict__ start,
                                   uint32_t *__restrict__ end)
 {
@@ -328,6 +338,9 @@ int run_binning(const BinArgs &a, BinOut &o, cudaStream_t st, int *launches)
         o.ent_ev = a.ent_ev[0];
         cudaMemsetAsync(a.seg_start, 0, sizeof(uint32_t) * a.n_segments, st);
         cudaMemsetAsync(a.seg_end, 0, sizeof(uint32_t) * a.n_segments, st);
+        iota_kernel<<<blocks_for(a.n_segments, T), T, 0, st>>>(a.seg_v[0], a.n_segments);
+        ++*launches;
+        o.seg_order = a.seg_v[0];
         return cudaGetLastError() == cudaSuccess ? 0 : 1;
     }
     // 3. sort by key bits, then stably by cell
@@ -375,6 +388,13 @@ int run_binning(const BinArgs &a, BinOut &o, cudaStream_t st, int *launches)
         seg_bounds_kernel<<<blocks_for(a.n_entries, T), T, 0, st>>>(o.ent_seg, a.n_entries, a.seg_start, a.seg_end);
         ++*launches;
     }
+    // 7. schedule: segments by decreasing length (load balance of the render)
+    seg_len_kernel<<<blocks_for(a.n_segments, T), T, 0, st>>>(a.seg_start, a.seg_end, a.n_segments, a.seg_k[0],
+                                                               a.seg_v[0]);
+    ++*launches;
+    int q = radix_sort<uint32_t>(a.seg_k[0], a.seg_v[0], a.seg_k[1], a.seg_v[1], a.n_segments, 32, a.hist,
+                                 a.scan_tmp, st, launches);
+    o.seg_order = a.seg_v[q];
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 

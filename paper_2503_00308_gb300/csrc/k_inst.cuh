@@ -32,18 +32,32 @@ int AR_CAT(launch_record_prep_m, AR_M)(const double *vN, const double *tau, cons
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 
+template <int TS>
+static int launch_render_ts(const RenderLaunch &a, cudaStream_t st)
+{
+    constexpr int CH = 32, RING = 16;
+    typedef RenderSmem<AR_M, TS, CH, RING> SM;
+    auto kern = render_kernel<AR_M, TS, CH, RING>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::BYTES) != cudaSuccess)
+        return 1;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TS * TS, SM::BYTES) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const uint32_t nseg = (uint32_t)a.n_cells * (uint32_t)a.n_tiles;
+    uint32_t grid = (uint32_t)(sms * per_sm);
+    if (grid > nseg) grid = nseg;
+    if (cudaMemsetAsync(a.work, 0, sizeof(unsigned int), st) != cudaSuccess) return 1;
+    kern<<<grid, TS * TS, SM::BYTES, st>>>(a.recs, a.boxes, a.seg_start, a.seg_end, a.seg_order, a.ent_ev, a.ev_val,
+                                           a.ev_key, a.W, a.H, a.ntx, a.n_tiles, nseg, a.n_gauss, a.k_open, a.out_lo,
+                                           a.out_hi, a.counters, a.work);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
 int AR_CAT(launch_render_m, AR_M)(int TS, const RenderLaunch &a, cudaStream_t st)
 {
-    const unsigned nseg = (unsigned)a.n_cells * (unsigned)a.n_tiles;
-    if (TS == 16)
-        render_kernel<AR_M, 16, 32><<<nseg, 256, 0, st>>>(a.recs, a.boxes, a.seg_start, a.seg_end, a.ent_ev,
-                                                           a.ev_val, a.ev_key, a.W, a.H, a.ntx, a.n_tiles,
-                                                           a.n_gauss, 0, a.k_open, a.out_lo, a.out_hi, a.n_eval);
-    else
-        render_kernel<AR_M, 8, 32><<<nseg, 64, 0, st>>>(a.recs, a.boxes, a.seg_start, a.seg_end, a.ent_ev,
-                                                         a.ev_val, a.ev_key, a.W, a.H, a.ntx, a.n_tiles,
-                                                         a.n_gauss, 0, a.k_open, a.out_lo, a.out_hi, a.n_eval);
-    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+    return TS == 16 ? launch_render_ts<16>(a, st) : launch_render_ts<8>(a, st);
 }
 
 }  // namespace ar

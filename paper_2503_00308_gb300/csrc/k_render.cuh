@@ -263,132 +263,193 @@ struct EvInfo {
 // A pixel stops when both sides have; a tile stops when all its pixels have.
 constexpr float EXIT_EPS = 5e-8f;
 
-// grid.x = n_cells * n_tiles, block = TS*TS threads
-template <int M, int TS, int CH>
-__global__ void __launch_bounds__(TS *TS) render_kernel(
+// Shared-memory layout of the render kernel (dynamic, one CTA per SM):
+//   records staged for a chunk of CH events, their event info and pixel boxes,
+//   and a per-thread ring of the last RING opacity evaluations made at lower
+//   endpoints (record id + alo, ahi, rL, L), stored column-per-thread so that
+//   every access is bank-conflict free.  The ring lets the upper endpoint of
+//   a Gaussian reuse the evaluation made at its lower endpoint.
+template <int M, int TS, int CH, int RING> struct RenderSmem {
+    static constexpr int NT = TS * TS;
+    static constexpr int PAY = M + 4;  // alo, ahi, rL, L.k, L.c[M]
+    static constexpr size_t REC = sizeof(float) * CH * Rec<M>::WIDTH;
+    static constexpr size_t EV = sizeof(EvInfo) * CH;
+    static constexpr size_t BOX = sizeof(PixBox) * CH;
+    static constexpr size_t RID = sizeof(uint32_t) * RING * NT;
+    static constexpr size_t RPAY = sizeof(float) * RING * PAY * NT;
+    static constexpr size_t BYTES = REC + EV + BOX + RID + RPAY + 16;
+};
+
+// Persistent grid: each CTA takes (cell, tile) segments, longest first, from
+// an atomic counter until none are left; block = TS*TS threads.
+template <int M, int TS, int CH, int RING>
+__global__ void __launch_bounds__(TS *TS, 1) render_kernel(
     const float *__restrict__ recs, const PixBox *__restrict__ boxes, const uint32_t *__restrict__ seg_start,
-    const uint32_t *__restrict__ seg_end, const uint32_t *__restrict__ entry_ev,
-    const uint32_t *__restrict__ ev_val, const uint64_t *__restrict__ ev_key, int W, int H, int ntx,
-    int n_tiles, int64_t n_gauss, int64_t cell_base, float k_open, float *__restrict__ out_lo,
-    float *__restrict__ out_hi, unsigned long long *__restrict__ n_eval)
+    const uint32_t *__restrict__ seg_end, const uint32_t *__restrict__ seg_order,
+    const uint32_t *__restrict__ entry_ev, const uint32_t *__restrict__ ev_val,
+    const uint64_t *__restrict__ ev_key, int W, int H, int ntx, int n_tiles, uint32_t n_seg, int64_t n_gauss,
+    float k_open, float *__restrict__ out_lo, float *__restrict__ out_hi,
+    unsigned long long *__restrict__ counters, unsigned int *__restrict__ work)
 {
     using RL = Rec<M>;
+    using SM = RenderSmem<M, TS, CH, RING>;
     constexpr int NT = TS * TS;
-    __shared__ __align__(16) float s_rec[CH][RL::WIDTH];
-    __shared__ EvInfo s_ev[CH];
-    __shared__ PixBox s_box[CH];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float(*s_rec)[RL::WIDTH] = reinterpret_cast<float(*)[RL::WIDTH]>(smem_raw);
+    EvInfo *s_ev = reinterpret_cast<EvInfo *>(smem_raw + SM::REC);
+    PixBox *s_box = reinterpret_cast<PixBox *>(smem_raw + SM::REC + SM::EV);
+    uint32_t *s_rid = reinterpret_cast<uint32_t *>(smem_raw + SM::REC + SM::EV + SM::BOX);
+    float *s_pay = reinterpret_cast<float *>(smem_raw + SM::REC + SM::EV + SM::BOX + SM::RID);
+    uint32_t *s_next = reinterpret_cast<uint32_t *>(smem_raw + SM::REC + SM::EV + SM::BOX + SM::RID + SM::RPAY);
+    const int tid = threadIdx.x;
+    uint32_t evals = 0, recomp = 0;
 
-    const int seg = blockIdx.x;
-    const int cell = seg / n_tiles;
-    const int tile = seg - cell * n_tiles;
-    const int tx = tile % ntx, ty = tile / ntx;
-    const int px = tx * TS + (int)(threadIdx.x % TS);
-    const int py = ty * TS + (int)(threadIdx.x / TS);
-    const bool inside = px < W && py < H;
-    const float ux = px + 0.5f, uy = py + 0.5f;
+    for (;;) {
+        if (tid == 0) *s_next = atomicAdd(work, 1u);
+        __syncthreads();
+        const uint32_t wk = *s_next;
+        __syncthreads();
+        if (wk >= n_seg) break;
+        const uint32_t seg = seg_order[wk];
+        const int cell = (int)(seg / (uint32_t)n_tiles);
+        const int tile = (int)(seg - (uint32_t)cell * (uint32_t)n_tiles);
+        const int tx = tile % ntx, ty = tile / ntx;
+        const int px = tx * TS + (tid % TS);
+        const int py = ty * TS + (tid / TS);
+        const bool inside = px < W && py < H;
+        const float ux = px + 0.5f, uy = py + 0.5f;
+        const uint32_t b0 = seg_start[seg], b1 = seg_end[seg];
+        const float *rec_cell = recs + (size_t)cell * n_gauss * RL::WIDTH;
+        const PixBox *box_cell = boxes + (size_t)cell * n_gauss;
 
-    const uint32_t b0 = seg_start[seg], b1 = seg_end[seg];
-    const float *rec_cell = recs + (size_t)(cell_base + cell) * n_gauss * RL::WIDTH;
-    const PixBox *box_cell = boxes + (size_t)(cell_base + cell) * n_gauss;
+        ColourAcc<M, true> lo;
+        ColourAcc<M, false> hi;
+        lo.init();
+        hi.init();
+        float PA = 1.f, PB = 1.f, PAp = 1.f, PBp = 1.f;
+        uint32_t c_rec = 0xffffffffu;  // register copy of the latest evaluation
+        AlphaOut<M> cache;
+#pragma unroll
+        for (int k = 0; k < RING; ++k) s_rid[k * NT + tid] = 0xffffffffu;
+        uint32_t head = 0;
+        bool done = !inside;
+        float lo_adj = 0.f, hi_adj = 0.f;  // -1: decided 0 / 1; >= 0: widening for skipped events
 
-    ColourAcc<M, true> lo;
-    ColourAcc<M, false> hi;
-    lo.init();
-    hi.init();
-    float PA = 1.f, PB = 1.f, PAp = 1.f, PBp = 1.f;
-    // one-entry cache of the last lower-endpoint evaluation
-    uint32_t c_rec = 0xffffffffu;
-    AlphaOut<M> cache;
-    bool done = !inside;
-    float lo_adj = 0.f, hi_adj = 0.f;  // -1: decided 0 / 1; >= 0: widening for skipped events
-    uint32_t evals = 0;
-
-    for (uint32_t base = b0; base < b1; base += CH) {
-        const int cnt = (int)min((uint32_t)CH, b1 - base);
-        if (!done) {
-            const float left = (float)(b1 - base);
-            // PA is rounded down; 1.01 covers its relative error for < 10^5 factors
-            const float elo2 = __fmul_ru(2.f, __fmul_ru(__fmul_ru(left, __fmul_ru(PA, 1.01f)), k_open));
-            const float ehi2 = __fmul_ru(2.2f, __fmul_ru(left, PB));
-            bool lo_zero = true, hi_one = true;
+        for (uint32_t base = b0; base < b1; base += CH) {
+            const int cnt = (int)min((uint32_t)CH, b1 - base);
+            if (!done) {
+                const float left = (float)(b1 - base);
+                // PA is rounded down; 1.01 covers its relative error for < 10^5 factors
+                const float elo2 = __fmul_ru(2.f, __fmul_ru(__fmul_ru(left, __fmul_ru(PA, 1.01f)), k_open));
+                const float ehi2 = __fmul_ru(2.2f, __fmul_ru(left, PB));
+                bool lo_zero = true, hi_one = true;
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    lo_zero = lo_zero && __fadd_ru(lo.upper_min(ch), elo2) <= 0.f;
+                    hi_one = hi_one && hi.k[ch] >= 1.f;
+                }
+                const bool lo_dec = lo_zero || elo2 <= EXIT_EPS;
+                const bool hi_dec = hi_one || ehi2 <= EXIT_EPS;
+                if (lo_dec && hi_dec) {
+                    done = true;
+                    lo_adj = lo_zero ? -1.f : elo2;
+                    hi_adj = hi_one ? -1.f : ehi2;
+                }
+            }
+            if (__syncthreads_and(done)) break;
+            if (tid < cnt) {
+                const uint32_t i = base + tid;
+                const uint32_t e = entry_ev[i];
+                const uint32_t v = ev_val[e];
+                uint32_t bits = v & 1u;
+                if (i > b0 && ev_key[entry_ev[i - 1]] == ev_key[e]) bits |= 2u;
+                const uint32_t rec = (v >> 1) - (uint32_t)(cell * n_gauss);
+                s_ev[tid] = EvInfo{rec, bits};
+                s_box[tid] = box_cell[rec];
+            }
+            __syncthreads();
+            for (int t = tid; t < cnt * (RL::WIDTH / 4); t += NT) {
+                const int e = t / (RL::WIDTH / 4), q = t - e * (RL::WIDTH / 4);
+                const float4 *src = reinterpret_cast<const float4 *>(rec_cell + (size_t)s_ev[e].rec * RL::WIDTH);
+                reinterpret_cast<float4 *>(s_rec[e])[q] = __ldg(src + q);
+            }
+            __syncthreads();
+            if (done) continue;
+            for (int e = 0; e < cnt; ++e) {
+                const EvInfo ev = s_ev[e];
+                if (!(ev.bits & 2u)) {
+                    PA = __fmul_rd(PA, PAp);
+                    PB = __fmul_ru(PB, PBp);
+                    PAp = 1.f;
+                    PBp = 1.f;
+                }
+                const PixBox bx = s_box[e];
+                if (px < bx.x0 || px > bx.x1 || py < bx.y0 || py > bx.y1) continue;
+                const float *r = s_rec[e];
+                const bool lower = !(ev.bits & 1u);
+                bool have = !lower && c_rec == ev.rec;
+                if (!lower && !have) {
+#pragma unroll
+                    for (int k = 0; k < RING; ++k) {
+                        if (s_rid[k * NT + tid] == ev.rec) {
+                            const float *pp = s_pay + (size_t)k * SM::PAY * NT + tid;
+                            cache.alo = pp[0];
+                            cache.ahi = pp[NT];
+                            cache.rL = pp[2 * NT];
+                            cache.L.k = pp[3 * NT];
+#pragma unroll
+                            for (int j = 0; j < M; ++j) cache.L.c[j] = pp[(4 + j) * NT];
+                            have = true;
+                        }
+                    }
+                }
+                if (!have) {
+                    pixel_alpha<M>(r, ux, uy, cache);
+                    if (lower) ++evals; else ++recomp;
+                }
+                c_rec = ev.rec;
+                const float col[3] = {r[RL::COL], r[RL::COL + 1], r[RL::COL + 2]};
+                if (lower) {
+                    hi.add(PB, col, cache.U, cache.rU);
+                    PAp = __fmul_rd(PAp, __fsub_rd(1.f, cache.ahi));
+                    const int k = (int)(head % RING);
+                    ++head;
+                    s_rid[k * NT + tid] = ev.rec;
+                    float *pp = s_pay + (size_t)k * SM::PAY * NT + tid;
+                    pp[0] = cache.alo;
+                    pp[NT] = cache.ahi;
+                    pp[2 * NT] = cache.rL;
+                    pp[3 * NT] = cache.L.k;
+#pragma unroll
+                    for (int j = 0; j < M; ++j) pp[(4 + j) * NT] = cache.L.c[j];
+                } else {
+                    const uint32_t flags = __float_as_uint(r[RL::FLAGS]);
+                    float T = PA;
+                    if (flags & F_OPEN) {
+                        const float den = __fsub_ru(1.f, cache.ahi);
+                        T = (den > 0.f) ? __fdiv_rd(PA, den) : 0.f;
+                    }
+                    lo.add(T, col, cache.L, cache.rL);
+                    PBp = __fmul_ru(PBp, __fsub_ru(1.f, cache.alo));
+                }
+            }
+        }
+        if (inside) {
+            const size_t o = ((size_t)cell * H * W + (size_t)py * W + px) * 3;
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
-                lo_zero = lo_zero && __fadd_ru(lo.upper_min(ch), elo2) <= 0.f;
-                hi_one = hi_one && hi.k[ch] >= 1.f;
-            }
-            const bool lo_dec = lo_zero || elo2 <= EXIT_EPS;
-            const bool hi_dec = hi_one || ehi2 <= EXIT_EPS;
-            if (lo_dec && hi_dec) {
-                done = true;
-                lo_adj = lo_zero ? -1.f : elo2;
-                hi_adj = hi_one ? -1.f : ehi2;
-            }
-        }
-        if (__syncthreads_and(done)) break;
-        if (threadIdx.x < (unsigned)cnt) {
-            const uint32_t i = base + threadIdx.x;
-            const uint32_t e = entry_ev[i];
-            const uint32_t v = ev_val[e];
-            uint32_t bits = v & 1u;
-            if (i > b0 && ev_key[entry_ev[i - 1]] == ev_key[e]) bits |= 2u;
-            const uint32_t rec = (v >> 1) - (uint32_t)(cell * n_gauss);
-            s_ev[threadIdx.x] = EvInfo{rec, bits};
-            s_box[threadIdx.x] = box_cell[rec];
-        }
-        __syncthreads();
-        // stage the records of this chunk
-        for (int t = threadIdx.x; t < cnt * (RL::WIDTH / 4); t += NT) {
-            const int e = t / (RL::WIDTH / 4), q = t - e * (RL::WIDTH / 4);
-            const float4 *src = reinterpret_cast<const float4 *>(rec_cell + (size_t)s_ev[e].rec * RL::WIDTH);
-            reinterpret_cast<float4 *>(s_rec[e])[q] = __ldg(src + q);
-        }
-        __syncthreads();
-        if (done) continue;
-        for (int e = 0; e < cnt; ++e) {
-            const EvInfo ev = s_ev[e];
-            if (!(ev.bits & 2u)) {
-                PA = __fmul_rd(PA, PAp);
-                PB = __fmul_ru(PB, PBp);
-                PAp = 1.f;
-                PBp = 1.f;
-            }
-            const PixBox bx = s_box[e];
-            if (px < bx.x0 || px > bx.x1 || py < bx.y0 || py > bx.y1) continue;
-            const float *r = s_rec[e];
-            const float col[3] = {r[RL::COL], r[RL::COL + 1], r[RL::COL + 2]};
-            if (!(ev.bits & 1u)) {
-                pixel_alpha<M>(r, ux, uy, cache);
-                c_rec = ev.rec;
-                ++evals;
-                hi.add(PB, col, cache.U, cache.rU);
-                PAp = __fmul_rd(PAp, __fsub_rd(1.f, cache.ahi));
-            } else {
-                if (c_rec != ev.rec) {
-                    pixel_alpha<M>(r, ux, uy, cache);
-                    c_rec = ev.rec;
-                }
-                const uint32_t flags = __float_as_uint(r[RL::FLAGS]);
-                float T = PA;
-                if (flags & F_OPEN) {
-                    const float den = __fsub_ru(1.f, cache.ahi);
-                    T = (den > 0.f) ? __fdiv_rd(PA, den) : 0.f;
-                }
-                lo.add(T, col, cache.L, cache.rL);
-                PBp = __fmul_ru(PBp, __fsub_ru(1.f, cache.alo));
+                out_lo[o + ch] = lo_adj < 0.f ? 0.f : clamp01(__fsub_rd(lo.bound(ch), lo_adj));
+                out_hi[o + ch] = hi_adj < 0.f ? 1.f : clamp01(__fadd_ru(hi.bound(ch), hi_adj));
             }
         }
     }
-    if (inside) {
-        const size_t o = ((size_t)(cell_base + cell) * H * W + (size_t)py * W + px) * 3;
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            out_lo[o + ch] = lo_adj < 0.f ? 0.f : clamp01(__fsub_rd(lo.bound(ch), lo_adj));
-            out_hi[o + ch] = hi_adj < 0.f ? 1.f : clamp01(__fadd_ru(hi.bound(ch), hi_adj));
+    if (counters) {
+        const uint32_t a = __reduce_add_sync(0xffffffffu, evals);
+        const uint32_t b = __reduce_add_sync(0xffffffffu, recomp);
+        if ((tid & 31) == 0) {
+            if (a) atomicAdd(&counters[0], (unsigned long long)a);
+            if (b) atomicAdd(&counters[1], (unsigned long long)b);
         }
-    }
-    if (n_eval) {
-        const uint32_t w = __reduce_add_sync(0xffffffffu, evals);
-        if ((threadIdx.x & 31) == 0 && w) atomicAdd(n_eval, (unsigned long long)w);
     }
 }
 
