@@ -79,8 +79,9 @@ typedef struct ar_render_stats {
     int32_t tile;               /* tile edge used (pixels) */
     int32_t m_vars;             /* pose variables carried by the linear forms */
     float ms_prep, ms_bin, ms_render, ms_total;
-    int64_t n_evaluated;        /* per-pixel opacity evaluations (triples the sweep reached
-                                   before each pixel's bounds were settled) */
+    int64_t n_evaluated;        /* per-pixel opacity relaxations evaluated (triples the sweep
+                                   reached before each pixel's bounds were settled; MatrixInv
+                                   fallbacks, which are constant, are not counted) */
     int64_t n_reevaluated;      /* evaluations repeated at an upper depth endpoint because the
                                    lower endpoint's result had left the per-pixel ring */
 } ar_render_stats;
@@ -167,6 +168,13 @@ int ar_render_abstract_plain_fp64(ar_scene *scene, const ar_intrinsics *intr,
  * [n_poses][H][W][3] float32.  Used to check soundness on the device. */
 int ar_render_concrete(ar_scene *scene, const ar_intrinsics *intr, const ar_nominal_pose *pose,
                        const double *deltas, int32_t n_poses, float *out, void *cuda_stream);
+
+/* Device-memory limit (bytes, >= 1 MiB) for the scene's render workspace.
+ * ar_render_abstract splits the cells of a call into batches whose
+ * per-(Gaussian, cell) records take about a third of this limit, and runs the
+ * pipeline once per batch (the bounds are the same as in one batch).
+ * Default 24 GiB. */
+int ar_set_workspace_limit(ar_scene *scene, int64_t bytes);
 
 /* Stage timing with CUDA events on the render stream (on = 1) or off (0). */
 int ar_set_profiling(ar_scene *scene, int on);

@@ -69,6 +69,7 @@ def lib():
             "ar_render_abstract_noalloc": ([P, P, P, P, c_int32, c_int32, P, P, P], ctypes.c_int),
             "ar_render_concrete": ([P, P, P, P, c_int32, P, P], ctypes.c_int),
             "ar_set_profiling": ([P, ctypes.c_int], ctypes.c_int),
+            "ar_set_workspace_limit": ([P, c_int64], ctypes.c_int),
             "ar_last_render_stats": ([P, P], ctypes.c_int),
             "ar_serve_create": ([c_int64, c_int32, P], ctypes.c_int),
             "ar_serve_destroy": ([P], ctypes.c_int),
@@ -173,6 +174,10 @@ def ar_render_concrete(scene, intr, pose, deltas, n_poses, out, stream=0):
     d = np.ascontiguousarray(deltas, dtype=np.float64)
     return check(lib().ar_render_concrete(scene, ctypes.byref(intr), ctypes.byref(pose), d.ctypes.data,
                                           int(n_poses), _ptr(out), _ptr(stream)))
+
+
+def ar_set_workspace_limit(scene, nbytes: int):
+    return check(lib().ar_set_workspace_limit(scene, int(nbytes)))
 
 
 def ar_set_profiling(scene, on: bool):

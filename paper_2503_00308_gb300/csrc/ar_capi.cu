@@ -131,9 +131,8 @@ void Workspace::release()
     for (DevBuf *b : all) b->release();
     if (h_counters) cudaFreeHost(h_counters);
     h_counters = nullptr;
-    if (ev_init)
-        for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
-    ev_init = false;
+    for (cudaEvent_t e : evs) cudaEventDestroy(e);
+    evs.clear();
 }
 
 size_t Workspace::bytes() const
@@ -239,6 +238,14 @@ int ar_scene_destroy(ar_scene *s)
     return AR_OK;
 }
 
+int ar_set_workspace_limit(ar_scene *s, int64_t bytes)
+{
+    if (!s) return fail(AR_EINVAL, "scene is null");
+    if (bytes < (int64_t)1 << 20) return fail(AR_EINVAL, "workspace limit below 1 MiB");
+    s->ws_limit = bytes;
+    return AR_OK;
+}
+
 int ar_set_profiling(ar_scene *s, int on)
 {
     if (!s) return fail(AR_EINVAL, "scene is null");
@@ -281,94 +288,40 @@ int validate_call(const ar_intrinsics *in, const ar_nominal_pose *pose, const ar
         if (r_) return r_;         \
     } while (0)
 
-int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_nominal_pose *pose,
-                const ar_pose_box *cells, int32_t n_cells, int32_t tile, float *out_lo, float *out_hi,
-                cudaStream_t st, bool profiling, ar_render_stats *stats)
+// One batch of cells through the whole pipeline.  cc describes the batch
+// (n_cells = cells in the batch, slots shared by every batch of the call).
+static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, int TS, const double *d_lo,
+                        const double *d_hi, float *out_lo, float *out_hi, cudaStream_t st, bool profiling,
+                        int batch, ar_render_stats &rs, int &launches)
 {
-    RK(validate_call(in, pose, cells, n_cells, tile));
-    if (!out_lo || !out_hi) return fail(AR_EINVAL, "null output");
-    CK(cudaSetDevice(s->device));
-    const int W = in->width, H = in->height;
-    const int TS = tile ? tile : 16;
-    const size_t out_words = (size_t)n_cells * W * H * 3;
-    ar_render_stats rs;
-    std::memset(&rs, 0, sizeof rs);
-    rs.tile = TS;
-    rs.ms_prep = rs.ms_bin = rs.ms_render = rs.ms_total = -1.f;
-    // active pose variables -> form slots
-    CallConst cc;
-    std::memset(&cc, 0, sizeof cc);
-    int m_active = 0;
-    for (int k = 0; k < MAXV; ++k) {
-        bool act = false;
-        for (int c = 0; c < n_cells; ++c) act = act || cells[c].hi[k] > cells[c].lo[k];
-        cc.m_slot[k] = act ? m_active++ : -1;
-    }
-    const int M = m_active <= 1 ? 1 : (m_active <= 4 ? 4 : 6);
-    rs.m_vars = M;
-    cc.W = W; cc.H = H;
-    cc.fx = in->fx; cc.fy = in->fy; cc.cx = in->cx; cc.cy = in->cy; cc.near_plane = in->near_plane;
-    std::memcpy(cc.R0, pose->R_wc, sizeof cc.R0);
-    std::memcpy(cc.t0, pose->t, sizeof cc.t0);
-    cc.n_cells = n_cells;
-    cc.n_gauss = s->n;
+    const int W = cc.W, H = cc.H, n_cells = cc.n_cells;
     const uint64_t n_pairs = (uint64_t)n_cells * (uint64_t)s->n;
-    if (n_pairs >= (1ull << 31)) return fail(AR_ENOMEM, "cells x Gaussians = %llu >= 2^31; split the cells", (unsigned long long)n_pairs);
     const int ntx = (W + TS - 1) / TS, nty = (H + TS - 1) / TS, n_tiles = ntx * nty;
     const uint64_t n_seg = (uint64_t)n_cells * n_tiles;
-    if (n_seg >= (1ull << 31)) return fail(AR_EINVAL, "too many (cell, tile) segments");
-    if (s->n == 0) {
-        CK(cudaMemsetAsync(out_lo, 0, out_words * sizeof(float), st));
-        CK(cudaMemsetAsync(out_hi, 0, out_words * sizeof(float), st));
-        if (stats) *stats = rs;
-        return AR_OK;
-    }
-    if (!ws.ev_init) {
-        for (int i = 0; i < 4; ++i) CK(cudaEventCreate(&ws.ev[i]));
-        ws.ev_init = true;
-    }
-    if (!ws.h_counters) CK(cudaMallocHost(&ws.h_counters, 8 * sizeof(unsigned long long)));
-    int launches = 0;
-    // -- prep
-    RK(ws.cells_lohi.ensure(sizeof(double) * 12 * n_cells));
     RK(ws.cells.ensure(cell_data_bytes(M) * n_cells));
-    RK(ws.vN.ensure(sizeof(double) * 12 * s->n));
     RK(ws.recs.ensure(sizeof(float) * rec_width(M) * n_pairs));
     RK(ws.boxes.ensure(sizeof(PixBox) * n_pairs));
     RK(ws.keys.ensure(sizeof(double) * 2 * n_pairs));
-    RK(ws.counters.ensure(sizeof(unsigned long long) * 8));
-    {
-        std::vector<double> lohi((size_t)12 * n_cells);
-        for (int c = 0; c < n_cells; ++c)
-            for (int k = 0; k < MAXV; ++k) {
-                lohi[(size_t)MAXV * c + k] = cells[c].lo[k];
-                lohi[(size_t)MAXV * n_cells + (size_t)MAXV * c + k] = cells[c].hi[k];
-            }
-        CK(cudaMemcpyAsync(ws.cells_lohi.p, lohi.data(), sizeof(double) * lohi.size(), cudaMemcpyHostToDevice, st));
-        CK(cudaStreamSynchronize(st));  // the host vector is released on return
-    }
-    const double *d_lo = ws.cells_lohi.as<double>(), *d_hi = d_lo + (size_t)MAXV * n_cells;
-    if (profiling) CK(cudaEventRecord(ws.ev[0], st));
+    cudaEvent_t *ev = &ws.evs[4 * batch];
+    if (profiling) CK(cudaEventRecord(ev[0], st));
     CK(cudaMemsetAsync(ws.counters.p, 0, sizeof(unsigned long long) * 8, st));
-    if (launch_pose_prep(s->uw, s->Mw, s->n, cc, ws.vN.as<double>(), st)) return fail(AR_EDEVICE, "pose_prep launch");
     if (launch_cell_prep(M, d_lo, d_hi, cc, ws.cells.p, st)) return fail(AR_EDEVICE, "cell_prep launch");
     if (launch_record_prep(M, ws.vN.as<double>(), s->tau, s->opac, s->rgb, cc, ws.cells.p, TS, ws.recs.as<float>(),
                            ws.boxes.as<PixBox>(), ws.keys.as<double>(), ws.counters.as<unsigned long long>(), st))
         return fail(AR_EDEVICE, "record_prep launch: %s", cudaGetErrorString(cudaGetLastError()));
-    launches += 3;
-    if (profiling) CK(cudaEventRecord(ws.ev[1], st));
+    launches += 2;
+    if (profiling) CK(cudaEventRecord(ev[1], st));
     CK(cudaMemcpyAsync(ws.h_counters, ws.counters.p, sizeof(unsigned long long) * 4, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     const unsigned long long n_valid = ws.h_counters[2];
-    rs.n_records = (int64_t)n_valid;
-    rs.n_triples = (int64_t)ws.h_counters[0];
-    rs.n_fallback = (int64_t)ws.h_counters[1];
+    rs.n_records += (int64_t)n_valid;
+    rs.n_triples += (int64_t)ws.h_counters[0];
+    rs.n_fallback += (int64_t)ws.h_counters[1];
     const uint64_t ne = 2 * n_valid, nent = 2 * ws.h_counters[3];
-    rs.n_entries = (int64_t)(nent / 2);
+    rs.n_entries += (int64_t)(nent / 2);
     if (nent >= (1ull << 32) - (1ull << 20))
-        return fail(AR_ENOMEM, "%llu bin entries exceed the 32-bit index range; use fewer cells per call",
+        return fail(AR_ENOMEM, "%llu bin entries exceed the 32-bit index range; lower the workspace limit",
                     (unsigned long long)nent);
-    // -- binning
     const uint64_t nsc = n_pairs > ne ? n_pairs : ne;
     const uint64_t nsort = ne > nent ? ne : nent;
     const uint64_t hist_words = radix_hist_words(nsort > n_seg ? nsort : n_seg) + 64;
@@ -419,8 +372,7 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
     BinOut bo;
     if (run_binning(ba, bo, st, &launches))
         return fail(AR_EDEVICE, "binning: %s", cudaGetErrorString(cudaGetLastError()));
-    if (profiling) CK(cudaEventRecord(ws.ev[2], st));
-    // -- per-pixel bounds
+    if (profiling) CK(cudaEventRecord(ev[2], st));
     RenderLaunch rl;
     rl.recs = ws.recs.as<float>();
     rl.boxes = ws.boxes.as<PixBox>();
@@ -436,10 +388,97 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
     rl.k_open = s->k_open;
     rl.out_lo = out_lo;
     rl.out_hi = out_hi;
-    rl.counters = ws.counters.as<unsigned long long>() + 4;
+    rl.counters = ws.counters.as<unsigned long long>() + 8 + 2 * batch;
     if (launch_render(M, TS, rl, st)) return fail(AR_EDEVICE, "render launch: %s", cudaGetErrorString(cudaGetLastError()));
     ++launches;
-    if (profiling) CK(cudaEventRecord(ws.ev[3], st));
+    if (profiling) CK(cudaEventRecord(ev[3], st));
+    return AR_OK;
+}
+
+int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_nominal_pose *pose,
+                const ar_pose_box *cells, int32_t n_cells, int32_t tile, float *out_lo, float *out_hi,
+                cudaStream_t st, bool profiling, ar_render_stats *stats)
+{
+    RK(validate_call(in, pose, cells, n_cells, tile));
+    if (!out_lo || !out_hi) return fail(AR_EINVAL, "null output");
+    CK(cudaSetDevice(s->device));
+    const int W = in->width, H = in->height;
+    const int TS = tile ? tile : 16;
+    const size_t out_words = (size_t)n_cells * W * H * 3;
+    ar_render_stats rs;
+    std::memset(&rs, 0, sizeof rs);
+    rs.tile = TS;
+    rs.ms_prep = rs.ms_bin = rs.ms_render = rs.ms_total = -1.f;
+    // active pose variables -> form slots (over all cells, so every batch agrees)
+    CallConst cc;
+    std::memset(&cc, 0, sizeof cc);
+    int m_active = 0;
+    for (int k = 0; k < MAXV; ++k) {
+        bool act = false;
+        for (int c = 0; c < n_cells; ++c) act = act || cells[c].hi[k] > cells[c].lo[k];
+        cc.m_slot[k] = act ? m_active++ : -1;
+    }
+    const int M = m_active <= 1 ? 1 : (m_active <= 4 ? 4 : 6);
+    rs.m_vars = M;
+    cc.W = W; cc.H = H;
+    cc.fx = in->fx; cc.fy = in->fy; cc.cx = in->cx; cc.cy = in->cy; cc.near_plane = in->near_plane;
+    std::memcpy(cc.R0, pose->R_wc, sizeof cc.R0);
+    std::memcpy(cc.t0, pose->t, sizeof cc.t0);
+    cc.n_gauss = s->n;
+    if (s->n == 0) {
+        CK(cudaMemsetAsync(out_lo, 0, out_words * sizeof(float), st));
+        CK(cudaMemsetAsync(out_hi, 0, out_words * sizeof(float), st));
+        ws.n_batches = 0;
+        if (stats) *stats = rs;
+        return AR_OK;
+    }
+    // cells per batch: the records of a batch stay within the workspace limit
+    // (about a third of the workspace goes to records), and pairs below 2^31
+    const size_t rec_bytes = sizeof(float) * rec_width(M) + 64;
+    const size_t per_cell = rec_bytes * (size_t)s->n;
+    int64_t per_batch = (int64_t)((s->ws_limit / 3) / (per_cell ? per_cell : 1));
+    const int64_t pair_cap = (int64_t)(((1ull << 31) - 1) / (uint64_t)s->n);
+    if (per_batch > pair_cap) per_batch = pair_cap;
+    if (per_batch < 1) per_batch = 1;
+    if (per_batch > n_cells) per_batch = n_cells;
+    const int n_batches = (int)((n_cells + per_batch - 1) / per_batch);
+    const int ntx = (W + TS - 1) / TS, nty = (H + TS - 1) / TS;
+    if ((uint64_t)per_batch * (uint64_t)ntx * (uint64_t)nty >= (1ull << 31))
+        return fail(AR_EINVAL, "too many (cell, tile) segments");
+    if (!ws.h_counters) CK(cudaMallocHost(&ws.h_counters, 8 * sizeof(unsigned long long)));
+    while ((int)ws.evs.size() < 4 * n_batches) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        ws.evs.push_back(e);
+    }
+    RK(ws.cells_lohi.ensure(sizeof(double) * 12 * n_cells));
+    RK(ws.vN.ensure(sizeof(double) * 12 * s->n));
+    RK(ws.counters.ensure(sizeof(unsigned long long) * (8 + 2 * n_batches)));
+    {
+        std::vector<double> lohi((size_t)12 * n_cells);
+        for (int c = 0; c < n_cells; ++c)
+            for (int k = 0; k < MAXV; ++k) {
+                lohi[(size_t)MAXV * c + k] = cells[c].lo[k];
+                lohi[(size_t)MAXV * n_cells + (size_t)MAXV * c + k] = cells[c].hi[k];
+            }
+        CK(cudaMemcpyAsync(ws.cells_lohi.p, lohi.data(), sizeof(double) * lohi.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));  // the host vector is released on return
+    }
+    const double *d_lo = ws.cells_lohi.as<double>(), *d_hi = d_lo + (size_t)MAXV * n_cells;
+    CK(cudaMemsetAsync(ws.counters.as<unsigned long long>() + 8, 0, sizeof(unsigned long long) * 2 * n_batches, st));
+    int launches = 0;
+    if (launch_pose_prep(s->uw, s->Mw, s->n, cc, ws.vN.as<double>(), st)) return fail(AR_EDEVICE, "pose_prep launch");
+    ++launches;
+    for (int b = 0; b < n_batches; ++b) {
+        const int c0 = (int)(b * per_batch);
+        const int nb = (int)(c0 + per_batch <= n_cells ? per_batch : n_cells - c0);
+        CallConst cb = cc;
+        cb.n_cells = nb;
+        const size_t off = (size_t)c0 * W * H * 3;
+        RK(render_batch(s, ws, cb, M, TS, d_lo + (size_t)MAXV * c0, d_hi + (size_t)MAXV * c0, out_lo + off,
+                        out_hi + off, st, profiling, b, rs, launches));
+    }
+    ws.n_batches = n_batches;
     rs.n_launches = launches;
     if (stats) *stats = rs;
     return AR_OK;
@@ -448,17 +487,26 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
 int finish_stats(Workspace &ws, cudaStream_t st, bool profiling, ar_render_stats &rs)
 {
     CK(cudaStreamSynchronize(st));
-    if (rs.n_records > 0 && ws.counters.p) {
-        unsigned long long ev[2] = {0, 0};
-        CK(cudaMemcpy(ev, ws.counters.as<unsigned long long>() + 4, sizeof ev, cudaMemcpyDeviceToHost));
-        rs.n_evaluated = (int64_t)ev[0];
-        rs.n_reevaluated = (int64_t)ev[1];
+    if (ws.n_batches > 0 && ws.counters.p) {
+        std::vector<unsigned long long> ev(2 * ws.n_batches);
+        CK(cudaMemcpy(ev.data(), ws.counters.as<unsigned long long>() + 8, sizeof(unsigned long long) * ev.size(),
+                      cudaMemcpyDeviceToHost));
+        rs.n_evaluated = rs.n_reevaluated = 0;
+        for (int b = 0; b < ws.n_batches; ++b) {
+            rs.n_evaluated += (int64_t)ev[2 * b];
+            rs.n_reevaluated += (int64_t)ev[2 * b + 1];
+        }
     }
-    if (profiling && ws.ev_init && rs.n_records > 0) {
-        CK(cudaEventElapsedTime(&rs.ms_prep, ws.ev[0], ws.ev[1]));
-        CK(cudaEventElapsedTime(&rs.ms_bin, ws.ev[1], ws.ev[2]));
-        CK(cudaEventElapsedTime(&rs.ms_render, ws.ev[2], ws.ev[3]));
-        CK(cudaEventElapsedTime(&rs.ms_total, ws.ev[0], ws.ev[3]));
+    if (profiling && ws.n_batches > 0) {
+        rs.ms_prep = rs.ms_bin = rs.ms_render = 0.f;
+        for (int b = 0; b < ws.n_batches; ++b) {
+            float t;
+            const cudaEvent_t *e = &ws.evs[4 * b];
+            CK(cudaEventElapsedTime(&t, e[0], e[1])); rs.ms_prep += t;
+            CK(cudaEventElapsedTime(&t, e[1], e[2])); rs.ms_bin += t;
+            CK(cudaEventElapsedTime(&t, e[2], e[3])); rs.ms_render += t;
+        }
+        CK(cudaEventElapsedTime(&rs.ms_total, ws.evs[0], ws.evs[4 * (ws.n_batches - 1) + 3]));
     }
     return AR_OK;
 }

@@ -4,6 +4,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "ar.h"
 
 namespace ar {
@@ -26,8 +28,8 @@ struct Workspace {
     DevBuf ua, ub, uc, ud, hist, scan, segs, sege, segk0, segk1, segv0, segv1, work;
     DevBuf out_lo, out_hi;
     unsigned long long *h_counters = nullptr;  // page-locked
-    cudaEvent_t ev[4];
-    bool ev_init = false;
+    std::vector<cudaEvent_t> evs;              // 4 per cell batch (stage timing)
+    int n_batches = 0;                         // cell batches of the last render
     void release();
     size_t bytes() const;
 };
@@ -49,6 +51,7 @@ struct ar_scene {
     float *uw = nullptr, *ls = nullptr, *quat = nullptr, *opac = nullptr, *rgb = nullptr;
     double *Mw = nullptr, *tau = nullptr;
     float k_open = 1.f;  // 1 / (1 - largest opacity), rounded up (bounds skipped lower-sum terms)
+    int64_t ws_limit = int64_t(24) << 30;  // workspace limit that sizes the cell batches
     ar::Workspace ws;
     bool profiling = false;
     ar_render_stats stats;

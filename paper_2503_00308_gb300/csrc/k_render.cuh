@@ -405,7 +405,10 @@ __global__ void __launch_bounds__(TS *TS, 1) render_kernel(
                 }
                 if (!have) {
                     pixel_alpha<M>(r, ux, uy, cache);
-                    if (lower) ++evals; else ++recomp;
+                    // a MatrixInv fallback is a constant [0, o]: not an evaluation
+                    if (!(__float_as_uint(r[RL::FLAGS]) & F_FALLBACK)) {
+                        if (lower) ++evals; else ++recomp;
+                    }
                 }
                 c_rec = ev.rec;
                 const float col[3] = {r[RL::COL], r[RL::COL + 1], r[RL::COL + 2]};

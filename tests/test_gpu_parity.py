@@ -190,3 +190,24 @@ def test_object300k_full_size_sampled(arlib, orc):
     for c, win in [(0, (396, 403, 396, 403)), (45, (300, 305, 480, 485))]:
         compare(orc, w.scene, w.camera, w.cells_lo[c], w.cells_hi[c], glo[c], ghi[c], window=win, frag_max=0.2)
     assert np.all(glo <= ghi)
+
+
+def test_cell_batches_are_bit_identical(arlib):
+    """A small workspace limit splits the cells into batches; bounds must not change."""
+    ar = arlib
+    sc = synth.object_scene(3000, 12)
+    cam = synth.look_camera(60, 44, 70.0, centre=(0, 0, -4))
+    lo, hi = synth.cell_grid([0.03, 0.0, 0.03, 0.01, 0.0, 0.0], [2, 1, 2, 2, 1, 1])
+    ref_lo, ref_hi = gpu_render(ar, sc, cam, lo, hi)
+    s = ar.Scene(sc)
+    ar.ar_set_workspace_limit(s.handle, 4 << 20)     # records of about one cell per batch
+    out_lo = torch.empty((lo.shape[0], cam.height, cam.width, 3), device="cuda")
+    out_hi = torch.empty_like(out_lo)
+    ar.ar_set_profiling(s.handle, True)
+    s.render(cam, lo, hi, out_lo, out_hi)
+    st = ar.ar_last_render_stats(s.handle)
+    torch.cuda.synchronize()
+    assert np.array_equal(out_lo.double().cpu().numpy(), ref_lo)
+    assert np.array_equal(out_hi.double().cpu().numpy(), ref_hi)
+    assert st["n_records"] > 0 and st["ms_render"] > 0
+    s.close()
