@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-window", type=int, default=16, help="edge of the oracle's pixel sample")
     ap.add_argument("--cells", type=int, default=0, help="use only the first N cells (profiling slices)")
+    ap.add_argument("--plain-cells", type=int, default=1,
+                    help="cells timed through the plain FP64 one-cell-per-launch path (0: skip)")
     return ap.parse_args()
 
 
@@ -140,6 +142,32 @@ def run_reference(args, rank):
                              "sample": vals[0]["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def plain_path(ar, s, w, intr, pose, args, sp, value):
+    """The plain FP64 path (one cell per launch sequence, FP64 records and
+    per-pixel arithmetic, no early stopping) on the first cells of the same
+    workload; one untimed run, then one timed with CUDA events."""
+    import torch
+    k = min(args.plain_cells, w.n_cells)
+    cam = w.camera
+    cells = ar.make_cells(w.cells_lo[:k], w.cells_hi[:k])
+    o_lo = torch.empty((k, cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
+    o_hi = torch.empty_like(o_lo)
+    stream = torch.cuda.current_stream()
+    ar.ar_render_abstract_plain_fp64(s.handle, intr, pose, cells, k, args.tile, o_lo, o_hi, sp)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    ar.ar_render_abstract_plain_fp64(s.handle, intr, pose, cells, k, args.tile, o_lo, o_hi, sp)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    st = ar.ar_last_render_stats(s.handle)
+    pv = k * cam.width * cam.height / (ms / 1e3)
+    return {"value": pv, "unit": UNIT, "cells": k, "ms": ms, "dtype": "f64", "warmup": 1, "steps": 1,
+            "stages_ms": {"prep": st["ms_prep"], "bin": st["ms_bin"], "render": st["ms_render"]},
+            "speedup": value / pv}
 
 
 def run_ours(args, rank, world, local, pg):
@@ -243,6 +271,8 @@ def run_ours(args, rank, world, local, pg):
                    "evaluated": stats["n_evaluated"], "reevaluated": stats["n_reevaluated"],
                    "fallback": stats["n_fallback"]},
     }
+    if args.plain_cells > 0:
+        line["plain_path"] = plain_path(ar, s, w, intr, pose, args, sp, value)
     if not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_window)
     print(json.dumps(line), flush=True)

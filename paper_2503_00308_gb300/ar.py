@@ -245,3 +245,8 @@ class Scene:
         cells = make_cells(cells_lo, cells_hi)
         ar_render_abstract(self.handle, make_intrinsics(cam), make_pose(cam), cells, len(cells), tile,
                            out_lower, out_upper, stream)
+
+    def render_plain_fp64(self, cam, cells_lo, cells_hi, out_lower, out_upper, tile: int = 0, stream=0):
+        cells = make_cells(cells_lo, cells_hi)
+        ar_render_abstract_plain_fp64(self.handle, make_intrinsics(cam), make_pose(cam), cells, len(cells), tile,
+                                      out_lower, out_upper, stream)

@@ -39,6 +39,15 @@ int launch_record_prep_m6(const double *, const double *, const float *, const f
 int launch_render_m1(int, const RenderLaunch &, cudaStream_t);
 int launch_render_m4(int, const RenderLaunch &, cudaStream_t);
 int launch_render_m6(int, const RenderLaunch &, cudaStream_t);
+int launch_record_prep64_m1(const double *, const double *, const float *, const float *, const CallConst &,
+                            const void *, int, double *, PixBox *, double *, unsigned long long *, cudaStream_t);
+int launch_record_prep64_m4(const double *, const double *, const float *, const float *, const CallConst &,
+                            const void *, int, double *, PixBox *, double *, unsigned long long *, cudaStream_t);
+int launch_record_prep64_m6(const double *, const double *, const float *, const float *, const CallConst &,
+                            const void *, int, double *, PixBox *, double *, unsigned long long *, cudaStream_t);
+int launch_render_plain_m1(int, const RenderLaunch &, cudaStream_t);
+int launch_render_plain_m4(int, const RenderLaunch &, cudaStream_t);
+int launch_render_plain_m6(int, const RenderLaunch &, cudaStream_t);
 
 size_t cell_data_bytes(int M)
 {
@@ -61,6 +70,19 @@ int launch_record_prep(int M, const double *vN, const double *tau, const float *
 int launch_render(int M, int TS, const RenderLaunch &a, cudaStream_t st)
 {
     return M == 1 ? launch_render_m1(TS, a, st) : (M == 4 ? launch_render_m4(TS, a, st) : launch_render_m6(TS, a, st));
+}
+int launch_record_prep64(int M, const double *vN, const double *tau, const float *opac, const float *rgb,
+                         const CallConst &cc, const void *cells, int TS, double *recs, PixBox *boxes, double *keys,
+                         unsigned long long *counters, cudaStream_t st)
+{
+    if (M == 1) return launch_record_prep64_m1(vN, tau, opac, rgb, cc, cells, TS, recs, boxes, keys, counters, st);
+    if (M == 4) return launch_record_prep64_m4(vN, tau, opac, rgb, cc, cells, TS, recs, boxes, keys, counters, st);
+    return launch_record_prep64_m6(vN, tau, opac, rgb, cc, cells, TS, recs, boxes, keys, counters, st);
+}
+int launch_render_plain(int M, int TS, const RenderLaunch &a, cudaStream_t st)
+{
+    return M == 1 ? launch_render_plain_m1(TS, a, st)
+                  : (M == 4 ? launch_render_plain_m4(TS, a, st) : launch_render_plain_m6(TS, a, st));
 }
 }  // namespace ar
 
@@ -290,25 +312,30 @@ int validate_call(const ar_intrinsics *in, const ar_nominal_pose *pose, const ar
 
 // One batch of cells through the whole pipeline.  cc describes the batch
 // (n_cells = cells in the batch, slots shared by every batch of the call).
+// plain: FP64 records and the plain FP64 renderer instead of the FP32 ones.
 static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, int TS, const double *d_lo,
                         const double *d_hi, float *out_lo, float *out_hi, cudaStream_t st, bool profiling,
-                        int batch, ar_render_stats &rs, int &launches)
+                        int batch, ar_render_stats &rs, int &launches, bool plain)
 {
     const int W = cc.W, H = cc.H, n_cells = cc.n_cells;
     const uint64_t n_pairs = (uint64_t)n_cells * (uint64_t)s->n;
     const int ntx = (W + TS - 1) / TS, nty = (H + TS - 1) / TS, n_tiles = ntx * nty;
     const uint64_t n_seg = (uint64_t)n_cells * n_tiles;
     RK(ws.cells.ensure(cell_data_bytes(M) * n_cells));
-    RK(ws.recs.ensure(sizeof(float) * rec_width(M) * n_pairs));
+    RK(ws.recs.ensure((plain ? sizeof(double) : sizeof(float)) * rec_width(M) * n_pairs));
     RK(ws.boxes.ensure(sizeof(PixBox) * n_pairs));
     RK(ws.keys.ensure(sizeof(double) * 2 * n_pairs));
     cudaEvent_t *ev = &ws.evs[4 * batch];
     if (profiling) CK(cudaEventRecord(ev[0], st));
     CK(cudaMemsetAsync(ws.counters.p, 0, sizeof(unsigned long long) * 8, st));
     if (launch_cell_prep(M, d_lo, d_hi, cc, ws.cells.p, st)) return fail(AR_EDEVICE, "cell_prep launch");
-    if (launch_record_prep(M, ws.vN.as<double>(), s->tau, s->opac, s->rgb, cc, ws.cells.p, TS, ws.recs.as<float>(),
-                           ws.boxes.as<PixBox>(), ws.keys.as<double>(), ws.counters.as<unsigned long long>(), st))
-        return fail(AR_EDEVICE, "record_prep launch: %s", cudaGetErrorString(cudaGetLastError()));
+    const int rp = plain ? launch_record_prep64(M, ws.vN.as<double>(), s->tau, s->opac, s->rgb, cc, ws.cells.p, TS,
+                                                ws.recs.as<double>(), ws.boxes.as<PixBox>(), ws.keys.as<double>(),
+                                                ws.counters.as<unsigned long long>(), st)
+                         : launch_record_prep(M, ws.vN.as<double>(), s->tau, s->opac, s->rgb, cc, ws.cells.p, TS,
+                                              ws.recs.as<float>(), ws.boxes.as<PixBox>(), ws.keys.as<double>(),
+                                              ws.counters.as<unsigned long long>(), st);
+    if (rp) return fail(AR_EDEVICE, "record_prep launch: %s", cudaGetErrorString(cudaGetLastError()));
     launches += 2;
     if (profiling) CK(cudaEventRecord(ev[1], st));
     CK(cudaMemcpyAsync(ws.h_counters, ws.counters.p, sizeof(unsigned long long) * 4, cudaMemcpyDeviceToHost, st));
@@ -375,6 +402,7 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
     if (profiling) CK(cudaEventRecord(ev[2], st));
     RenderLaunch rl;
     rl.recs = ws.recs.as<float>();
+    rl.recs64 = ws.recs.as<double>();
     rl.boxes = ws.boxes.as<PixBox>();
     rl.seg_start = ws.segs.as<uint32_t>();
     rl.seg_end = ws.sege.as<uint32_t>();
@@ -389,7 +417,8 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
     rl.out_lo = out_lo;
     rl.out_hi = out_hi;
     rl.counters = ws.counters.as<unsigned long long>() + 8 + 2 * batch;
-    if (launch_render(M, TS, rl, st)) return fail(AR_EDEVICE, "render launch: %s", cudaGetErrorString(cudaGetLastError()));
+    if (plain ? launch_render_plain(M, TS, rl, st) : launch_render(M, TS, rl, st))
+        return fail(AR_EDEVICE, "render launch: %s", cudaGetErrorString(cudaGetLastError()));
     ++launches;
     if (profiling) CK(cudaEventRecord(ev[3], st));
     return AR_OK;
@@ -397,7 +426,7 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
 
 int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_nominal_pose *pose,
                 const ar_pose_box *cells, int32_t n_cells, int32_t tile, float *out_lo, float *out_hi,
-                cudaStream_t st, bool profiling, ar_render_stats *stats)
+                cudaStream_t st, bool profiling, ar_render_stats *stats, bool plain)
 {
     RK(validate_call(in, pose, cells, n_cells, tile));
     if (!out_lo || !out_hi) return fail(AR_EINVAL, "null output");
@@ -434,13 +463,14 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
     }
     // cells per batch: the records of a batch stay within the workspace limit
     // (about a third of the workspace goes to records), and pairs below 2^31
-    const size_t rec_bytes = sizeof(float) * rec_width(M) + 64;
+    const size_t rec_bytes = (plain ? sizeof(double) : sizeof(float)) * rec_width(M) + 64;
     const size_t per_cell = rec_bytes * (size_t)s->n;
     int64_t per_batch = (int64_t)((s->ws_limit / 3) / (per_cell ? per_cell : 1));
     const int64_t pair_cap = (int64_t)(((1ull << 31) - 1) / (uint64_t)s->n);
     if (per_batch > pair_cap) per_batch = pair_cap;
     if (per_batch < 1) per_batch = 1;
     if (per_batch > n_cells) per_batch = n_cells;
+    if (plain) per_batch = 1;  // the plain path: one cell per launch sequence
     const int n_batches = (int)((n_cells + per_batch - 1) / per_batch);
     const int ntx = (W + TS - 1) / TS, nty = (H + TS - 1) / TS;
     if ((uint64_t)per_batch * (uint64_t)ntx * (uint64_t)nty >= (1ull << 31))
@@ -476,7 +506,7 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
         cb.n_cells = nb;
         const size_t off = (size_t)c0 * W * H * 3;
         RK(render_batch(s, ws, cb, M, TS, d_lo + (size_t)MAXV * c0, d_hi + (size_t)MAXV * c0, out_lo + off,
-                        out_hi + off, st, profiling, b, rs, launches));
+                        out_hi + off, st, profiling, b, rs, launches, plain));
     }
     ws.n_batches = n_batches;
     rs.n_launches = launches;
@@ -556,9 +586,12 @@ int ar_render_abstract_plain_fp64(ar_scene *s, const ar_intrinsics *in, const ar
                                   const ar_pose_box *cells, int32_t n_cells, int32_t tile, float *out_lower,
                                   float *out_upper, void *stream)
 {
-    (void)s; (void)in; (void)pose; (void)cells; (void)n_cells; (void)tile; (void)out_lower; (void)out_upper;
-    (void)stream;
-    return fail(AR_EINVAL, "plain FP64 path not built in this library version");
+    if (!s) return fail(AR_EINVAL, "scene is null");
+    cudaStream_t st = (cudaStream_t)stream;
+    int r = render_core(s, s->ws, in, pose, cells, n_cells, tile, out_lower, out_upper, st, s->profiling, &s->stats,
+                        true);
+    s->stats_stream = st;
+    return r;
 }
 
 int ar_render_concrete(ar_scene *s, const ar_intrinsics *in, const ar_nominal_pose *pose, const double *deltas,

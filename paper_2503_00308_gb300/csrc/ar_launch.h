@@ -11,6 +11,7 @@ struct PixBox;
 
 struct RenderLaunch {
     const float *recs;
+    const double *recs64 = nullptr;   // FP64 records (plain renderer only)
     const PixBox *boxes;
     const uint32_t *seg_start, *seg_end, *seg_order, *ent_ev, *ev_val;
     const uint64_t *ev_key;
@@ -29,6 +30,10 @@ int launch_record_prep(int M, const double *vN, const double *tau, const float *
                        const CallConst &cc, const void *cells, int TS, float *recs, PixBox *boxes, double *keys,
                        unsigned long long *counters, cudaStream_t st);
 int launch_render(int M, int TS, const RenderLaunch &a, cudaStream_t st);
+int launch_record_prep64(int M, const double *vN, const double *tau, const float *opac, const float *rgb,
+                         const CallConst &cc, const void *cells, int TS, double *recs, PixBox *boxes, double *keys,
+                         unsigned long long *counters, cudaStream_t st);
+int launch_render_plain(int M, int TS, const RenderLaunch &a, cudaStream_t st);
 int launch_scene_prep(const float *logscale, const float *quat, const float *opacity, int64_t n, double *Mw,
                       double *tau, cudaStream_t st);
 int launch_pose_prep(const float *uw, const double *Mw, int64_t n, const CallConst &cc, double *vN,

@@ -32,6 +32,33 @@ int AR_CAT(launch_record_prep_m, AR_M)(const double *vN, const double *tau, cons
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 
+int AR_CAT(launch_record_prep64_m, AR_M)(const double *vN, const double *tau, const float *opac, const float *rgb,
+                                         const CallConst &cc, const void *cells, int TS, double *recs,
+                                         PixBox *boxes, double *keys, unsigned long long *counters,
+                                         cudaStream_t st)
+{
+    const int T = 128;
+    dim3 grid((unsigned)((cc.n_gauss + T - 1) / T), (unsigned)cc.n_cells);
+    record_prep_kernel<AR_M, double><<<grid, T, 0, st>>>(vN, tau, opac, rgb, cc, (const CellData<AR_M> *)cells,
+                                                         TS, recs, boxes, keys, counters);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+template <int TS>
+static int launch_render_plain_ts(const RenderLaunch &a, cudaStream_t st)
+{
+    const uint32_t nseg = (uint32_t)a.n_cells * (uint32_t)a.n_tiles;
+    render_plain_kernel<AR_M, TS, 32><<<nseg, TS * TS, 0, st>>>(a.recs64, a.boxes, a.seg_start, a.seg_end, a.ent_ev,
+                                                                a.ev_val, a.ev_key, a.W, a.H, a.ntx, a.n_tiles,
+                                                                a.n_gauss, a.out_lo, a.out_hi);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+int AR_CAT(launch_render_plain_m, AR_M)(int TS, const RenderLaunch &a, cudaStream_t st)
+{
+    return TS == 16 ? launch_render_plain_ts<16>(a, st) : launch_render_plain_ts<8>(a, st);
+}
+
 template <int TS>
 static int launch_render_ts(const RenderLaunch &a, cudaStream_t st)
 {

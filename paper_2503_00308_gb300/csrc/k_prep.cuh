@@ -163,7 +163,9 @@ __global__ void cell_prep_kernel(const double *__restrict__ cells_lo, const doub
     }
 }
 
-// FP32 form -> FP64 (exact)
+// FP32 form -> FP64 (exact); an FP64 form passes through
+template <int M>
+__device__ __forceinline__ const BS<M, double> &to_f64(const BS<M, double> &b) { return b; }
 template <int M>
 __device__ __forceinline__ BS<M, double> to_f64(const BS<M, float> &b)
 {
@@ -185,18 +187,32 @@ __device__ __forceinline__ void bs_to_f32(const BS<M, double> &d, BS<M, float> &
     }
     to_f32<M>(lo, hi, b);
 }
+// FP64 sound form -> record precision (FP32 outward, or FP64 as it is)
+template <int M>
+__device__ __forceinline__ void bs_to_rec(const BS<M, double> &d, BS<M, float> &b) { bs_to_f32<M>(d, b); }
+template <int M>
+__device__ __forceinline__ void bs_to_rec(const BS<M, double> &d, BS<M, double> &b) { b = d; }
+
+// scalars in the record precision, rounded down / up
+__device__ __forceinline__ void rec_dn(double x, float &y) { y = __double2float_rd(x); }
+__device__ __forceinline__ void rec_dn(double x, double &y) { y = x; }
+__device__ __forceinline__ void rec_up(double x, float &y) { y = __double2float_ru(x); }
+__device__ __forceinline__ void rec_up(double x, double &y) { y = x; }
+// the flags word: a float's bit pattern, or a double's value
+__device__ __forceinline__ void rec_put_flags(float *dst, uint32_t f) { *dst = __uint_as_float(f); }
+__device__ __forceinline__ void rec_put_flags(double *dst, uint32_t f) { *dst = (double)f; }
 
 // ------------------------------------------------------------- records
-template <int M>
-__device__ __forceinline__ void store_form(float *dst, const LF<M, float> &f)
+template <int M, class R>
+__device__ __forceinline__ void store_form(R *dst, const LF<M, R> &f)
 {
 #pragma unroll
     for (int j = 0; j < M; ++j) dst[j] = f.c[j];
     dst[M] = f.k;
 }
 
-template <int M>
-__device__ __forceinline__ bool bs_finite(const BS<M, float> &b)
+template <int M, class R>
+__device__ __forceinline__ bool bs_finite(const BS<M, R> &b)
 {
     return isfinite(b.vlo) && isfinite(b.vhi) && isfinite(b.lo.k) && isfinite(b.hi.k) && isfinite(b.rlo) &&
            isfinite(b.rhi);
@@ -206,16 +222,20 @@ struct PrepCount {
     uint32_t triples, fallback, valid, tiles;
 };
 
-// One (Gaussian, cell) pair; returns its counters through pc.
-template <int M>
+// One (Gaussian, cell) pair; returns its counters through pc.  RO is the
+// precision of the stored record: float for the batched renderer (FP32 value
+// chain with outward rounding), double for the plain FP64 renderer, where
+// the same steps run with every value kept in FP64.
+template <int M, class RO = float>
 __device__ __forceinline__ void record_prep_one(const double *__restrict__ vN, const double *__restrict__ tau_g,
                                                 const float *__restrict__ opacity, const float *__restrict__ rgb,
                                                 const CallConst &cc, const CellData<M> &cd, int cell, int64_t g,
-                                                int TS, float *__restrict__ recs, PixBox *__restrict__ boxes,
+                                                int TS, RO *__restrict__ recs, PixBox *__restrict__ boxes,
                                                 double *__restrict__ keys, PrepCount &pc)
 {
     using RL = Rec<M>;
-    typedef BS<M, float> B;
+    using NO = Num<RO>;
+    typedef BS<M, RO> B;
     const int64_t ri = (int64_t)cell * cc.n_gauss + g;
     PixBox box = {-1, -1, -1, -1};
     boxes[ri] = box;
@@ -295,13 +315,13 @@ __device__ __forceinline__ void record_prep_one(const double *__restrict__ vN, c
         mu_lo[0] = mux.l; mu_hi[0] = mux.u; mu_lo[1] = muy.l; mu_hi[1] = muy.u;
     }
 
-    // ---- FP32 value chain
-    float *rec = recs + ri * RL::WIDTH;
+    // ---- value chain (record precision)
+    RO *rec = recs + ri * RL::WIDTH;
     uint32_t flags = (straddle ? F_STRADDLE : 0u) | (klo < khi ? F_OPEN : 0u);
     const float o = opacity[g];
     rec[RL::O] = o;
-    rec[RL::TAU_DN] = __double2float_rd(tau);
-    rec[RL::TAU_UP] = __double2float_ru(tau);
+    rec_dn(tau, rec[RL::TAU_DN]);
+    rec_up(tau, rec[RL::TAU_UP]);
     for (int k = 0; k < 3; ++k) rec[RL::COL + k] = rgb[3 * g + k];
 
     bool ok = true;
@@ -341,8 +361,8 @@ __device__ __forceinline__ void record_prep_one(const double *__restrict__ vN, c
         const BD S = b_sqr<M, double>(d64);
         const BD Px = b_mul<M, double>(d64, u0);
         const BD Py = b_mul<M, double>(d64, u1);
-        const float mux = (float)(floor(fmin(fmax(0.5 * (mu_lo[0] + mu_hi[0]), -1e6), 1e6)) + 0.5);
-        const float muy = (float)(floor(fmin(fmax(0.5 * (mu_lo[1] + mu_hi[1]), -1e6), 1e6)) + 0.5);
+        const RO mux = (RO)(floor(fmin(fmax(0.5 * (mu_lo[0] + mu_hi[0]), -1e6), 1e6)) + 0.5);
+        const RO muy = (RO)(floor(fmin(fmax(0.5 * (mu_lo[1] + mu_hi[1]), -1e6), 1e6)) + 0.5);
         BD Rx, Ry;
         {
             Acc<M, double, true> lo;
@@ -355,9 +375,9 @@ __device__ __forceinline__ void record_prep_one(const double *__restrict__ vN, c
             Ry.lo = lo.result(); Ry.hi = hi.result(); finish(Ry);
         }
         B S32, Rx32, Ry32;
-        bs_to_f32<M>(S, S32);
-        bs_to_f32<M>(Rx, Rx32);
-        bs_to_f32<M>(Ry, Ry32);
+        bs_to_rec<M>(S, S32);
+        bs_to_rec<M>(Rx, Rx32);
+        bs_to_rec<M>(Ry, Ry32);
         ok = ok && bs_finite(S32) && bs_finite(Rx32) && bs_finite(Ry32);
         store_form<M>(rec + RL::S_LO, S32.lo); store_form<M>(rec + RL::S_HI, S32.hi);
         store_form<M>(rec + RL::RX_LO, Rx32.lo); store_form<M>(rec + RL::RX_HI, Rx32.hi);
@@ -409,8 +429,9 @@ __device__ __forceinline__ void record_prep_one(const double *__restrict__ vN, c
         if (!(det > 0.0) || !(h00 > 0.0) || !isfinite(det)) {
             fallback = true;
         } else {
-            // X0 rounded to float: the same constant enters I - X X0 and X0 * sum
-            const float X0[4] = {(float)(h11 / det), (float)(-h01 / det), (float)(-h01 / det), (float)(h00 / det)};
+            // X0 rounded to the record precision: the same constant enters
+            // I - X X0 and X0 * sum
+            const RO X0[4] = {(RO)(h11 / det), (RO)(-h01 / det), (RO)(-h01 / det), (RO)(h00 / det)};
             B E[4];
             double rho2 = 0.0;
             for (int r = 0; r < 2; ++r)
@@ -423,13 +444,14 @@ __device__ __forceinline__ void record_prep_one(const double *__restrict__ vN, c
                     const BD e64 = p.result();
                     const double m = fmax(fabs(e64.vlo), fabs(e64.vhi));
                     rho2 = __fma_ru(m, m, rho2);
-                    bs_to_f32<M>(e64, E[2 * r + s]);
+                    bs_to_rec<M>(e64, E[2 * r + s]);
                 }
             const double rho64 = __dsqrt_ru(rho2);
             if (!(rho64 < RHO_MAX)) {
                 fallback = true;
             } else {
-                const float rho = __double2float_ru(rho64);
+                RO rho;
+                rec_up(rho64, rho);
                 // T = sum_{i=1..k} (I - X X0)^i, so that Xp = X0 (I + T) = X0 + X0 T:
                 // the identity term is added as an exact constant at the end
                 B P[4], Ssum[4];
@@ -442,25 +464,25 @@ __device__ __forceinline__ void record_prep_one(const double *__restrict__ vN, c
                     B Q[4];
                     for (int r = 0; r < 2; ++r)
                         for (int s = 0; s < 2; ++s) {
-                            Pair<M, float> p;
-                            p.init(0.f, 0.f);
+                            Pair<M, RO> p;
+                            p.init(0, 0);
                             p.mul(P[2 * r], E[s]);
                             p.mul(P[2 * r + 1], E[2 + s]);
                             Q[2 * r + s] = p.result();
                         }
-                    for (int e = 0; e < 4; ++e) { P[e] = Q[e]; Ssum[e] = b_add<M, float>(Ssum[e], Q[e]); }
+                    for (int e = 0; e < 4; ++e) { P[e] = Q[e]; Ssum[e] = b_add<M, RO>(Ssum[e], Q[e]); }
                 }
-                float nX0 = 0.f;
-                for (int e = 0; e < 4; ++e) nX0 = __fmaf_ru(X0[e], X0[e], nX0);
-                nX0 = __fsqrt_ru(nX0);
-                float rk = 1.f;
-                for (int i = 0; i <= KTAYLOR; ++i) rk = __fmul_ru(rk, rho);
-                const float eps = __fdiv_ru(__fmul_ru(nX0, rk), __fsub_rd(1.f, rho));
+                RO nX0 = 0;
+                for (int e = 0; e < 4; ++e) nX0 = NO::fma_ru(X0[e], X0[e], nX0);
+                nX0 = NO::sqrt_ru(nX0);
+                RO rk = 1;
+                for (int i = 0; i <= KTAYLOR; ++i) rk = NO::mul_ru(rk, rho);
+                const RO eps = NO::div_ru(NO::mul_ru(nX0, rk), NO::sub_rd(RO(1), rho));
                 for (int r = 0; r < 2; ++r)
                     for (int s = 0; s < 2; ++s) {
-                        Pair<M, float> p;
+                        Pair<M, RO> p;
                         // X0[r][s] + eps-widening, then + X0 T
-                        p.init(__fsub_rd(X0[2 * r + s], eps), __fadd_ru(X0[2 * r + s], eps));
+                        p.init(NO::sub_rd(X0[2 * r + s], eps), NO::add_ru(X0[2 * r + s], eps));
                         p.lin(X0[2 * r], Ssum[s]);
                         p.lin(X0[2 * r + 1], Ssum[2 + s]);
                         conic[2 * r + s] = p.result();
@@ -472,15 +494,15 @@ __device__ __forceinline__ void record_prep_one(const double *__restrict__ vN, c
     if (!fallback) {
         for (int r = 0; r < 2; ++r)
             for (int c = 0; c < 3; ++c) {
-                // W = Conic Mp in FP64 (Conic's FP32 forms are exact in FP64)
+                // W = Conic Mp in FP64 (FP32 Conic forms are exact in FP64)
                 Pair<M, double> p;
                 p.init(0.0, 0.0);
                 p.mul(to_f64<M>(conic[2 * r]), Mp64[c]);
                 p.mul(to_f64<M>(conic[2 * r + 1]), Mp64[3 + c]);
                 B w;
-                bs_to_f32<M>(p.result(), w);
+                bs_to_rec<M>(p.result(), w);
                 if (!bs_finite(w)) fallback = true;
-                float *dst = rec + RL::W0 + (3 * r + c) * RL::WSTRIDE;
+                RO *dst = rec + RL::W0 + (3 * r + c) * RL::WSTRIDE;
                 store_form<M>(dst, w.lo);
                 store_form<M>(dst + RL::F, w.hi);
                 dst[2 * RL::F] = w.vlo; dst[2 * RL::F + 1] = w.vhi;
@@ -492,7 +514,7 @@ __device__ __forceinline__ void record_prep_one(const double *__restrict__ vN, c
         flags |= F_FALLBACK;
         pc.fallback = 1;
     }
-    rec[RL::FLAGS] = __uint_as_float(flags);
+    rec_put_flags(rec + RL::FLAGS, flags);
     keys[2 * ri] = klo;
     keys[2 * ri + 1] = khi;
     boxes[ri] = box;
@@ -504,17 +526,17 @@ __device__ __forceinline__ void record_prep_one(const double *__restrict__ vN, c
 // grid: x over Gaussians, y over cells.  One thread per (Gaussian, cell).
 // counters: [0] pixel-Gaussian-cell triples in boxes, [1] MatrixInv
 // fallbacks, [2] pairs present, [3] (pair, tile) entries.
-template <int M>
+template <int M, class RO = float>
 __global__ void __launch_bounds__(128) record_prep_kernel(
     const double *__restrict__ vN, const double *__restrict__ tau_g, const float *__restrict__ opacity,
     const float *__restrict__ rgb, CallConst cc, const CellData<M> *__restrict__ cells, int TS,
-    float *__restrict__ recs, PixBox *__restrict__ boxes, double *__restrict__ keys,
+    RO *__restrict__ recs, PixBox *__restrict__ boxes, double *__restrict__ keys,
     unsigned long long *__restrict__ counters)
 {
     const int cell = blockIdx.y;
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     PrepCount pc = {0, 0, 0, 0};
-    if (g < cc.n_gauss) record_prep_one<M>(vN, tau_g, opacity, rgb, cc, cells[cell], cell, g, TS, recs, boxes, keys, pc);
+    if (g < cc.n_gauss) record_prep_one<M, RO>(vN, tau_g, opacity, rgb, cc, cells[cell], cell, g, TS, recs, boxes, keys, pc);
     const uint32_t t = __reduce_add_sync(0xffffffffu, pc.triples);
     const uint32_t f = __reduce_add_sync(0xffffffffu, pc.fallback);
     const uint32_t v = __reduce_add_sync(0xffffffffu, pc.valid);

@@ -25,25 +25,25 @@
 
 namespace ar {
 
-template <int M> struct AlphaOut {
-    LF<M, float> L, U;  // lower / upper forms of the effective opacity
-    float rL, rU;       // their coefficient radii
-    float alo, ahi;     // scalar enclosure of a over the cell
+template <int M, class R = float> struct AlphaOut {
+    LF<M, R> L, U;  // lower / upper forms of the effective opacity
+    R rL, rU;       // their coefficient radii
+    R alo, ahi;     // scalar enclosure of a over the cell
 };
 
-template <int M>
-__device__ __forceinline__ void load_form(const float *src, LF<M, float> &f)
+template <int M, class R>
+__device__ __forceinline__ void load_form(const R *src, LF<M, R> &f)
 {
 #pragma unroll
     for (int j = 0; j < M; ++j) f.c[j] = src[j];
     f.k = src[M];
 }
 
-template <int M>
-__device__ __forceinline__ void load_w(const float *src, BS<M, float> &b)
+template <int M, class R>
+__device__ __forceinline__ void load_w(const R *src, BS<M, R> &b)
 {
-    load_form<M>(src, b.lo);
-    load_form<M>(src + M + 1, b.hi);
+    load_form<M, R>(src, b.lo);
+    load_form<M, R>(src + M + 1, b.hi);
     b.vlo = src[2 * M + 2];
     b.vhi = src[2 * M + 3];
     b.rlo = src[2 * M + 4];
@@ -51,189 +51,197 @@ __device__ __forceinline__ void load_w(const float *src, BS<M, float> &b)
 }
 
 __device__ __forceinline__ float clamp01(float x) { return fminf(1.f, fmaxf(0.f, x)); }
+__device__ __forceinline__ double clamp01(double x) { return fmin(1.0, fmax(0.0, x)); }
+
+// flags word of a record: the bit pattern of a float, or the value of a double
+__device__ __forceinline__ uint32_t rec_flags(const float *r, int at) { return __float_as_uint(r[at]); }
+__device__ __forceinline__ uint32_t rec_flags(const double *r, int at) { return (uint32_t)r[at]; }
 
 // Effective-opacity bounds of one (Gaussian, cell) record at pixel (ux, uy).
-template <int M>
-__device__ __forceinline__ void pixel_alpha(const float *__restrict__ r, float ux, float uy, AlphaOut<M> &out)
+template <int M, class R = float>
+__device__ __forceinline__ void pixel_alpha(const R *__restrict__ r, R ux, R uy, AlphaOut<M, R> &out)
 {
     using RL = Rec<M>;
-    using N = Num<float>;
-    typedef BS<M, float> B;
-    const float o = r[RL::O];
-    const uint32_t flags = __float_as_uint(r[RL::FLAGS]);
+    using N = Num<R>;
+    typedef BS<M, R> B;
+    const R o = r[RL::O];
+    const uint32_t flags = rec_flags(r, RL::FLAGS);
     if (flags & F_FALLBACK) {
 #pragma unroll
-        for (int j = 0; j < M; ++j) { out.L.c[j] = 0.f; out.U.c[j] = 0.f; }
-        out.L.k = 0.f; out.U.k = o; out.rL = 0.f; out.rU = 0.f;
-        out.alo = 0.f; out.ahi = o;
+        for (int j = 0; j < M; ++j) { out.L.c[j] = 0; out.U.c[j] = 0; }
+        out.L.k = 0; out.U.k = o; out.rL = 0; out.rU = 0;
+        out.alo = 0; out.ahi = o;
         return;
     }
     // Delta = S u - P, held as (u - mu) S + R (see Rec)
     B Dx, Dy;
     {
-        LF<M, float> slo, shi, plo, phi;
-        load_form<M>(r + RL::S_LO, slo);
-        load_form<M>(r + RL::S_HI, shi);
-        Acc<M, float, true> lo;
-        Acc<M, float, false> hi;
-        const float dx = ux - r[RL::MU_X], dy = uy - r[RL::MU_Y];  // exact: both are half-integers
-        load_form<M>(r + RL::RX_LO, plo);
-        load_form<M>(r + RL::RX_HI, phi);
-        lo.init(0.f); hi.init(0.f);
+        LF<M, R> slo, shi, plo, phi;
+        load_form<M, R>(r + RL::S_LO, slo);
+        load_form<M, R>(r + RL::S_HI, shi);
+        Acc<M, R, true> lo;
+        Acc<M, R, false> hi;
+        const R dx = ux - r[RL::MU_X], dy = uy - r[RL::MU_Y];  // exact: both are half-integers
+        load_form<M, R>(r + RL::RX_LO, plo);
+        load_form<M, R>(r + RL::RX_HI, phi);
+        lo.init(0); hi.init(0);
         lo.term(dx, slo, r[RL::RAD + 0]); hi.term(dx, shi, r[RL::RAD + 1]);
-        lo.term(1.f, plo, r[RL::RAD + 2]); hi.term(1.f, phi, r[RL::RAD + 3]);
+        lo.term(1, plo, r[RL::RAD + 2]); hi.term(1, phi, r[RL::RAD + 3]);
         Dx.lo = lo.result(); Dx.hi = hi.result(); finish(Dx);
-        load_form<M>(r + RL::RY_LO, plo);
-        load_form<M>(r + RL::RY_HI, phi);
-        lo.init(0.f); hi.init(0.f);
+        load_form<M, R>(r + RL::RY_LO, plo);
+        load_form<M, R>(r + RL::RY_HI, phi);
+        lo.init(0); hi.init(0);
         lo.term(dy, slo, r[RL::RAD + 0]); hi.term(dy, shi, r[RL::RAD + 1]);
-        lo.term(1.f, plo, r[RL::RAD + 4]); hi.term(1.f, phi, r[RL::RAD + 5]);
+        lo.term(1, plo, r[RL::RAD + 4]); hi.term(1, phi, r[RL::RAD + 5]);
         Dy.lo = lo.result(); Dy.hi = hi.result(); finish(Dy);
     }
     // m = sum_c (Delta_x W_0c + Delta_y W_1c)^2
-    Pair<M, float> pm;
-    pm.init(0.f, 0.f);
+    Pair<M, R> pm;
+    pm.init(0, 0);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         B w0, w1;
-        load_w<M>(r + RL::W0 + c * RL::WSTRIDE, w0);
-        load_w<M>(r + RL::W0 + (3 + c) * RL::WSTRIDE, w1);
-        Pair<M, float> pq;
-        pq.init(0.f, 0.f);
+        load_w<M, R>(r + RL::W0 + c * RL::WSTRIDE, w0);
+        load_w<M, R>(r + RL::W0 + (3 + c) * RL::WSTRIDE, w1);
+        Pair<M, R> pq;
+        pq.init(0, 0);
         pq.mul(Dx, w0);
         pq.mul(Dy, w1);
         B q = pq.result();
         pm.sqr(q);
     }
     B m = pm.result();
-    const float mlo = m.vlo, mhi = m.vhi;
+    const R mlo = m.vlo, mhi = m.vhi;
     // Exp on x = -m/2 in [xl, xu], xu clipped at 0 because m >= 0
-    const float xl = -0.5f * mhi;
-    float xu = fminf(-0.5f * mlo, 0.f);
+    const R xl = R(-0.5) * mhi;
+    R xu = N::min(R(-0.5) * mlo, R(0));
     if (!(xu >= xl)) xu = xl;
-    const float el_dn = N::exp_dn(xl), el_up = N::exp_up(xl), eu_up = N::exp_up(xu);
+    const R el_dn = N::exp_dn(xl), el_up = N::exp_up(xl), eu_up = N::exp_up(xu);
     // lower: o e(xl) (1 + x - xl) with x >= -m.hi/2
-    Acc<M, float, true> la;
-    const float e1 = __fmul_rd(o, el_dn);
-    la.init(__fmul_rd(e1, __fsub_rd(1.f, xl)));
-    la.term(-0.5f * e1, m.hi, m.rhi);
-    LF<M, float> La = la.result();
+    Acc<M, R, true> la;
+    const R e1 = N::mul_rd(o, el_dn);
+    la.init(N::mul_rd(e1, N::sub_rd(R(1), xl)));
+    la.term(R(-0.5) * e1, m.hi, m.rhi);
+    LF<M, R> La = la.result();
     // upper: o (e(xl) + s (x - xl)) with x <= -m.lo/2
-    const float w = __fsub_rd(xu, xl);
-    float s = (w > 0.f) ? __fdiv_ru(__fsub_ru(eu_up, el_up), w) : eu_up;
-    s = fminf(fmaxf(s, 0.f), N::BIG);
-    const float e2 = __fmul_ru(o, el_up), s2 = __fmul_ru(o, s);
-    Acc<M, float, false> ua;
-    ua.init(__fmaf_ru(-s2, xl, e2));
-    ua.term(-0.5f * s2, m.lo, m.rlo);
-    LF<M, float> Ua = ua.result();
-    float rUa = 0.f;
+    const R w = N::sub_rd(xu, xl);
+    R s = (w > R(0)) ? N::div_ru(N::sub_ru(eu_up, el_up), w) : eu_up;
+    s = N::min(N::max(s, R(0)), N::BIG);
+    const R e2 = N::mul_ru(o, el_up), s2 = N::mul_ru(o, s);
+    Acc<M, R, false> ua;
+    ua.init(N::fma_ru(-s2, xl, e2));
+    ua.term(R(-0.5) * s2, m.lo, m.rlo);
+    LF<M, R> Ua = ua.result();
+    R rUa = 0;
 #pragma unroll
-    for (int j = 0; j < M; ++j) rUa = __fadd_ru(rUa, fabsf(Ua.c[j]));
-    const float amax = __fadd_ru(Ua.k, rUa);
+    for (int j = 0; j < M; ++j) rUa = N::add_ru(rUa, N::abs(Ua.c[j]));
+    const R amax = N::add_ru(Ua.k, rUa);
     // blend the upper form toward the constant o where its maximum exceeds o
-    const float lam = clamp01((o * (1.f + CLIP_RAMP) - amax) / (o * CLIP_RAMP));
+    const R lam = clamp01((o * (R(1) + R(CLIP_RAMP)) - amax) / (o * R(CLIP_RAMP)));
     // cutoff ramps (width shrinks with the m interval)
-    float ramp = fminf(CUT_RAMP, mhi - mlo);
-    if (!(ramp > 0.f)) ramp = 0.f;
-    const float tdn = r[RL::TAU_DN], tup = r[RL::TAU_UP];
-    const float psi2 = (mlo <= tup) ? 0.f : (ramp > 0.f ? clamp01((mlo - tup) / ramp) : 1.f);
-    const float psi = (mhi > tdn) ? 1.f : (ramp > 0.f ? clamp01((mhi - tdn + ramp) / ramp) : 0.f);
+    R ramp = N::min(R(CUT_RAMP), mhi - mlo);
+    if (!(ramp > R(0))) ramp = 0;
+    const R tdn = r[RL::TAU_DN], tup = r[RL::TAU_UP];
+    const R psi2 = (mlo <= tup) ? R(0) : (ramp > R(0) ? clamp01((mlo - tup) / ramp) : R(1));
+    const R psi = (mhi > tdn) ? R(1) : (ramp > R(0) ? clamp01((mhi - tdn + ramp) / ramp) : R(0));
     {
-        Acc<M, float, false> u1;
-        const float keep = 1.f - psi2;
-        u1.init(__fmul_ru(keep, __fmul_ru(__fsub_ru(1.f, lam), o)));
+        Acc<M, R, false> u1;
+        const R keep = R(1) - psi2;
+        u1.init(N::mul_ru(keep, N::mul_ru(N::sub_ru(R(1), lam), o)));
         u1.term(keep * lam, Ua, rUa);
         out.U = u1.result();
     }
-    float rU = 0.f;
+    R rU = 0;
 #pragma unroll
-    for (int j = 0; j < M; ++j) rU = __fadd_ru(rU, fabsf(out.U.c[j]));
+    for (int j = 0; j < M; ++j) rU = N::add_ru(rU, N::abs(out.U.c[j]));
     out.rU = rU;
-    out.ahi = fminf(o, __fadd_ru(out.U.k, rU));
+    out.ahi = N::min(o, N::add_ru(out.U.k, rU));
     // lower: subtract psi/255, then blend toward 0 where the form dips below 0
-    La.k = __fsub_rd(La.k, __fmul_ru(psi, ALPHA_MIN_UP));
-    float rLa = 0.f;
+    La.k = N::sub_rd(La.k, N::mul_ru(psi, R(ALPHA_MIN_UP)));
+    R rLa = 0;
 #pragma unroll
-    for (int j = 0; j < M; ++j) rLa = __fadd_ru(rLa, fabsf(La.c[j]));
-    const float l2min = __fsub_rd(La.k, rLa), l2max = La.k + rLa;
-    const float mu = (l2min >= 0.f) ? 1.f : ((l2max <= 0.f) ? 0.f : l2max / (l2max - l2min));
-    if ((flags & F_STRADDLE) || mu == 0.f) {
+    for (int j = 0; j < M; ++j) rLa = N::add_ru(rLa, N::abs(La.c[j]));
+    const R l2min = N::sub_rd(La.k, rLa), l2max = La.k + rLa;
+    const R mu = (l2min >= R(0)) ? R(1) : ((l2max <= R(0)) ? R(0) : l2max / (l2max - l2min));
+    if ((flags & F_STRADDLE) || mu == R(0)) {
 #pragma unroll
-        for (int j = 0; j < M; ++j) out.L.c[j] = 0.f;
-        out.L.k = 0.f;
-        out.rL = 0.f;
-        out.alo = 0.f;
-    } else if (mu == 1.f) {
+        for (int j = 0; j < M; ++j) out.L.c[j] = 0;
+        out.L.k = 0;
+        out.rL = 0;
+        out.alo = 0;
+    } else if (mu == R(1)) {
         out.L = La;
         out.rL = rLa;
-        out.alo = fmaxf(0.f, l2min);
+        out.alo = N::max(R(0), l2min);
     } else {
-        Acc<M, float, true> l1;
-        l1.init(0.f);
+        Acc<M, R, true> l1;
+        l1.init(0);
         l1.term(mu, La, rLa);
         out.L = l1.result();
-        float rL = 0.f;
+        R rL = 0;
 #pragma unroll
-        for (int j = 0; j < M; ++j) rL = __fadd_ru(rL, fabsf(out.L.c[j]));
+        for (int j = 0; j < M; ++j) rL = N::add_ru(rL, N::abs(out.L.c[j]));
         out.rL = rL;
-        out.alo = fmaxf(0.f, __fsub_rd(out.L.k, rL));
+        out.alo = N::max(R(0), N::sub_rd(out.L.k, rL));
     }
 }
 
 // Colour accumulator: sum_i w_i F_i per channel, with the rounding error of
 // the round-to-nearest coefficient sums bounded step by step:
 //   each step's error <= min(u * sum_j |acc_j|, w * r_F), and
-//   sum_j |acc_j| <= Q = sum of w * r_F so far.
-template <int M, bool DN> struct ColourAcc {
-    float c[3][M];
-    float k[3];
-    float q[3], err[3];
+//   sum_j |acc_j| <= Q = sum of w * r_F so far (times 1.01 for the error
+//   already accumulated, valid below 10^5 steps in FP32).
+template <int M, bool DN, class R = float> struct ColourAcc {
+    using N = Num<R>;
+    R c[3][M];
+    R k[3];
+    R q[3], err[3];
     int steps;
     __device__ __forceinline__ void init()
     {
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
 #pragma unroll
-            for (int j = 0; j < M; ++j) c[ch][j] = 0.f;
-            k[ch] = 0.f; q[ch] = 0.f; err[ch] = 0.f;
+            for (int j = 0; j < M; ++j) c[ch][j] = 0;
+            k[ch] = 0; q[ch] = 0; err[ch] = 0;
         }
         steps = 0;
     }
-    __device__ __forceinline__ void add(float T, const float *col, const LF<M, float> &F, float rF)
+    __device__ __forceinline__ void add(R T, const R *col, const LF<M, R> &F, R rF)
     {
+        const R u = N::U * R(1.01);
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
-            const float w = DN ? __fmul_rd(T, col[ch]) : __fmul_ru(T, col[ch]);
+            const R w = DN ? N::mul_rd(T, col[ch]) : N::mul_ru(T, col[ch]);
 #pragma unroll
-            for (int j = 0; j < M; ++j) c[ch][j] = __fmaf_rn(w, F.c[j], c[ch][j]);
-            k[ch] = DN ? __fmaf_rd(w, F.k, k[ch]) : __fmaf_ru(w, F.k, k[ch]);
-            const float t = __fmul_ru(w, rF);
-            q[ch] = __fadd_ru(q[ch], t);
-            err[ch] = __fadd_ru(err[ch], fminf(__fmul_ru(q[ch], 5.97e-8f), t));
+            for (int j = 0; j < M; ++j) c[ch][j] = N::fma_rn(w, F.c[j], c[ch][j]);
+            k[ch] = DN ? N::fma_rd(w, F.k, k[ch]) : N::fma_ru(w, F.k, k[ch]);
+            const R t = N::mul_ru(w, rF);
+            q[ch] = N::add_ru(q[ch], t);
+            err[ch] = N::add_ru(err[ch], N::min(N::mul_ru(q[ch], u), t));
         }
         ++steps;
     }
-    __device__ __forceinline__ float radius(int ch) const
+    __device__ __forceinline__ R radius(int ch) const
     {
-        float r = 0.f;
+        R r = 0;
 #pragma unroll
-        for (int j = 0; j < M; ++j) r = __fadd_ru(r, fabsf(c[ch][j]));
-        return __fadd_ru(__fadd_ru(r, err[ch]), __fmul_ru((float)steps, 1e-36f));
+        for (int j = 0; j < M; ++j) r = N::add_ru(r, N::abs(c[ch][j]));
+        return N::add_ru(N::add_ru(r, err[ch]), N::mul_ru((R)steps, N::TINY));
     }
     // the outward concretisation of the accumulated form
-    __device__ __forceinline__ float bound(int ch) const
+    __device__ __forceinline__ R bound(int ch) const
     {
-        const float r = radius(ch);
-        return DN ? __fsub_rd(k[ch], r) : __fadd_ru(k[ch], r);
+        const R r = radius(ch);
+        return DN ? N::sub_rd(k[ch], r) : N::add_ru(k[ch], r);
     }
     // constant minus radius rounded up: at least the computed lower bound
-    __device__ __forceinline__ float upper_min(int ch) const
+    __device__ __forceinline__ R upper_min(int ch) const
     {
-        float r = 0.f;
+        R r = 0;
 #pragma unroll
-        for (int j = 0; j < M; ++j) r = __fadd_rd(r, fabsf(c[ch][j]));
-        return __fsub_ru(k[ch], __fadd_rd(r, err[ch]));
+        for (int j = 0; j < M; ++j) r = N::add_rd(r, N::abs(c[ch][j]));
+        return N::sub_ru(k[ch], N::add_rd(r, err[ch]));
     }
 };
 
@@ -452,6 +460,101 @@ __global__ void __launch_bounds__(TS *TS, 1) render_kernel(
         if ((tid & 31) == 0) {
             if (a) atomicAdd(&counters[0], (unsigned long long)a);
             if (b) atomicAdd(&counters[1], (unsigned long long)b);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Plain FP64 renderer: the comparison path for the batched FP32 renderer.
+// One CTA per (cell, tile) segment, one thread per pixel; FP64 records and
+// FP64 arithmetic (outward rounded), every event of the segment swept (no
+// early exit), and the opacity bounds evaluated again at each upper endpoint
+// (no cache).  The host drives it one cell per launch sequence.
+template <int M, int TS, int CH>
+__global__ void __launch_bounds__(TS *TS) render_plain_kernel(
+    const double *__restrict__ recs, const PixBox *__restrict__ boxes, const uint32_t *__restrict__ seg_start,
+    const uint32_t *__restrict__ seg_end, const uint32_t *__restrict__ entry_ev, const uint32_t *__restrict__ ev_val,
+    const uint64_t *__restrict__ ev_key, int W, int H, int ntx, int n_tiles, int64_t n_gauss,
+    float *__restrict__ out_lo, float *__restrict__ out_hi)
+{
+    using RL = Rec<M>;
+    using N = Num<double>;
+    __shared__ __align__(16) double s_rec[CH][RL::WIDTH];
+    __shared__ EvInfo s_ev[CH];
+    __shared__ PixBox s_box[CH];
+    const int tid = threadIdx.x;
+    const uint32_t seg = blockIdx.x;
+    const int cell = (int)(seg / (uint32_t)n_tiles);
+    const int tile = (int)(seg - (uint32_t)cell * (uint32_t)n_tiles);
+    const int px = (tile % ntx) * TS + (tid % TS);
+    const int py = (tile / ntx) * TS + (tid / TS);
+    const bool inside = px < W && py < H;
+    const double ux = px + 0.5, uy = py + 0.5;
+    const uint32_t b0 = seg_start[seg], b1 = seg_end[seg];
+    const double *rec_cell = recs + (size_t)cell * n_gauss * RL::WIDTH;
+    const PixBox *box_cell = boxes + (size_t)cell * n_gauss;
+
+    ColourAcc<M, true, double> lo;
+    ColourAcc<M, false, double> hi;
+    lo.init();
+    hi.init();
+    double PA = 1, PB = 1, PAp = 1, PBp = 1;
+    AlphaOut<M, double> a;
+    for (uint32_t base = b0; base < b1; base += CH) {
+        const int cnt = (int)min((uint32_t)CH, b1 - base);
+        if (tid < cnt) {
+            const uint32_t i = base + tid;
+            const uint32_t e = entry_ev[i];
+            const uint32_t v = ev_val[e];
+            uint32_t bits = v & 1u;
+            if (i > b0 && ev_key[entry_ev[i - 1]] == ev_key[e]) bits |= 2u;
+            const uint32_t rec = (v >> 1) - (uint32_t)(cell * n_gauss);
+            s_ev[tid] = EvInfo{rec, bits};
+            s_box[tid] = box_cell[rec];
+        }
+        __syncthreads();
+        for (int t = tid; t < cnt * (RL::WIDTH / 2); t += TS * TS) {
+            const int e = t / (RL::WIDTH / 2), q = t - e * (RL::WIDTH / 2);
+            const double2 *src = reinterpret_cast<const double2 *>(rec_cell + (size_t)s_ev[e].rec * RL::WIDTH);
+            reinterpret_cast<double2 *>(s_rec[e])[q] = src[q];
+        }
+        __syncthreads();
+        if (inside) {
+            for (int e = 0; e < cnt; ++e) {
+                const EvInfo ev = s_ev[e];
+                if (!(ev.bits & 2u)) {
+                    PA = N::mul_rd(PA, PAp);
+                    PB = N::mul_ru(PB, PBp);
+                    PAp = 1;
+                    PBp = 1;
+                }
+                const PixBox bx = s_box[e];
+                if (px < bx.x0 || px > bx.x1 || py < bx.y0 || py > bx.y1) continue;
+                const double *r = s_rec[e];
+                pixel_alpha<M, double>(r, ux, uy, a);
+                const double col[3] = {r[RL::COL], r[RL::COL + 1], r[RL::COL + 2]};
+                if (!(ev.bits & 1u)) {
+                    hi.add(PB, col, a.U, a.rU);
+                    PAp = N::mul_rd(PAp, N::sub_rd(1.0, a.ahi));
+                } else {
+                    double T = PA;
+                    if ((uint32_t)r[RL::FLAGS] & F_OPEN) {
+                        const double den = N::sub_ru(1.0, a.ahi);
+                        T = (den > 0.0) ? N::div_rd(PA, den) : 0.0;
+                    }
+                    lo.add(T, col, a.L, a.rL);
+                    PBp = N::mul_ru(PBp, N::sub_ru(1.0, a.alo));
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (inside) {
+        const size_t o = ((size_t)cell * H * W + (size_t)py * W + px) * 3;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            out_lo[o + ch] = __double2float_rd(clamp01(lo.bound(ch)));
+            out_hi[o + ch] = __double2float_ru(clamp01(hi.bound(ch)));
         }
     }
 }
