@@ -53,6 +53,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-window", type=int, default=16, help="edge of the oracle's pixel sample")
     ap.add_argument("--cells", type=int, default=0, help="use only the first N cells (profiling slices)")
+    ap.add_argument("--serve-requests", type=int, default=32, help="requests in the serving mix (0: skip)")
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-budget-gb", type=float, default=96.0)
+    ap.add_argument("--serve-load", type=float, default=0.9,
+                    help="offered load of the Poisson stream, as a fraction of the one-at-a-time capacity")
     ap.add_argument("--plain-cells", type=int, default=1,
                     help="cells timed through the plain FP64 one-cell-per-launch path (0: skip)")
     return ap.parse_args()
@@ -170,6 +175,91 @@ def plain_path(ar, s, w, intr, pose, args, sp, value):
             "speedup": value / pv}
 
 
+def serving(ar, args, sp):
+    """The serving mix: a seeded Poisson stream of requests over resident
+    10k / 300k / 750k-Gaussian scenes (200x200 to 1280x720, 1 to 256 cells).
+
+    (1) one request at a time, closed loop, through ar_render_abstract: the
+        plain one-request-per-launch path; its mean service time sets the
+        arrival rate (offered load = --serve-load of its capacity);
+    (2) the same arrival stream through a one-slot server (no overlap);
+    (3) the same stream through an --serve-slots server (continuous batching);
+    (4) capacity: every request submitted at once, to both servers.
+    Latency is submit-to-completion, measured by the server."""
+    import numpy as np
+    import torch
+
+    from paper_2503_00308_gb300 import synth
+    reqs = synth.serving_mix(args.serve_requests, seed=0)
+    scenes = {k: ar.Scene(synth.SERVE_SCENES[k]()) for k in sorted({q.scene for q in reqs})}
+    outs = []
+    for q in reqs:
+        o = torch.empty((q.cells_lo.shape[0], q.camera.height, q.camera.width, 3), dtype=torch.float32,
+                        device="cuda")
+        outs.append((o, torch.empty_like(o)))
+    units = [q.pixel_cells() for q in reqs]
+    # warm-up: the largest request of each scene
+    for k, sc in scenes.items():
+        i = max((j for j, q in enumerate(reqs) if q.scene == k), key=lambda j: units[j])
+        sc.render(reqs[i].camera, reqs[i].cells_lo, reqs[i].cells_hi, outs[i][0], outs[i][1], stream=sp)
+    torch.cuda.synchronize()
+    service = []
+    for q, (a, b) in zip(reqs, outs):
+        t0 = time.perf_counter()
+        scenes[q.scene].render(q.camera, q.cells_lo, q.cells_hi, a, b, stream=sp)
+        torch.cuda.synchronize()
+        service.append(time.perf_counter() - t0)
+    total = float(sum(units))
+    mean_gap = statistics.mean(service) / args.serve_load
+    arrivals = np.cumsum([q.gap * mean_gap for q in reqs])
+    arrivals -= arrivals[0]
+
+    def stream(slots, burst=False):
+        at = np.zeros_like(arrivals) if burst else arrivals
+        srv = ar.Server(int(args.serve_budget_gb * (1 << 30)), slots)
+        lat, end = [None] * len(reqs), [None] * len(reqs)
+        pending, i = {}, 0
+        t0 = time.perf_counter()
+        while i < len(reqs) or pending:
+            now = time.perf_counter() - t0
+            while i < len(reqs) and at[i] <= now:
+                q = reqs[i]
+                t = srv.submit(scenes[q.scene], q.camera, q.cells_lo, q.cells_hi, outs[i][0], outs[i][1])
+                assert t is not None
+                pending[t] = i
+                i += 1
+            for t in list(pending):
+                done, ms = srv.poll(t)
+                if done:
+                    lat[pending[t]] = ms
+                    end[pending[t]] = time.perf_counter() - t0
+                    del pending[t]
+            time.sleep(0.0002)
+        srv.close()
+        span = max(end)
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(np.mean(lat)), "bounds_per_s": total / span, "makespan_s": span}
+
+    one = stream(1)
+    many = stream(args.serve_slots)
+    one_b = stream(1, burst=True)
+    many_b = stream(args.serve_slots, burst=True)
+    for sc in scenes.values():
+        sc.close()
+    return {"requests": len(reqs), "pixel_cells": int(total), "slots": args.serve_slots,
+            "budget_gb": args.serve_budget_gb, "offered_load": args.serve_load,
+            "mean_interarrival_ms": mean_gap * 1e3, "unit": UNIT,
+            "one_at_a_time_closed_loop": {"bounds_per_s": total / sum(service),
+                                          "p50_service_ms": float(np.percentile(service, 50) * 1e3),
+                                          "p99_service_ms": float(np.percentile(service, 99) * 1e3)},
+            "one_slot_server": one, "continuous_batching": many,
+            "saturated": {"one_slot_bounds_per_s": one_b["bounds_per_s"],
+                          "continuous_batching_bounds_per_s": many_b["bounds_per_s"],
+                          "one_slot_makespan_s": one_b["makespan_s"],
+                          "continuous_batching_makespan_s": many_b["makespan_s"]},
+            "p50_ms": many["p50_ms"], "p99_ms": many["p99_ms"], "bounds_per_s": many["bounds_per_s"]}
+
+
 def run_ours(args, rank, world, local, pg):
     import numpy as np
     import torch
@@ -273,6 +363,8 @@ def run_ours(args, rank, world, local, pg):
     }
     if args.plain_cells > 0:
         line["plain_path"] = plain_path(ar, s, w, intr, pose, args, sp, value)
+    if args.serve_requests > 0:
+        line["serving"] = serving(ar, args, sp)
     if not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_window)
     print(json.dumps(line), flush=True)

@@ -46,7 +46,7 @@ extern "C" {
 #define AR_OK 0
 #define AR_EINVAL 1    /* bad argument: null pointer, size, NaN, lo > hi, ... */
 #define AR_ENOMEM 2    /* device or host allocation failed / over the budget */
-#define AR_EAGAIN 3    /* serving: admission refused (queue or memory full) */
+#define AR_EAGAIN 3    /* serving: request queue full, try again */
 #define AR_ETIMEOUT 4  /* serving: a bounded wait ran out */
 #define AR_EDEVICE 5   /* CUDA error (message from the runtime) */
 
@@ -183,27 +183,42 @@ int ar_set_profiling(ar_scene *scene, int on);
 int ar_last_render_stats(ar_scene *scene, ar_render_stats *stats);
 
 /* ---- serving: continuous batching of abstract-render requests ----------
- * A server owns one CUDA stream per slot and a device-memory budget.
- * Requests are admitted when a slot is free and their workspace fits the
- * budget; they run concurrently on the device and complete independently. */
+ * (The paper has no counterpart: it renders one query at a time.)
+ * A server owns n_slots slots; each is a host worker thread with its own
+ * non-blocking CUDA stream and workspace, so requests in different slots run
+ * their whole pipelines concurrently on the device.  Submitted requests wait
+ * in a FIFO (up to 1024); a slot that frees up admits the oldest request whose
+ * workspace estimate fits the budget next to what the other slots hold, or a
+ * later one that fits while leaving room for the oldest (backfilling).
+ * Idle slots' workspaces are released when the oldest request does not fit.
+ * Results are bit-identical to ar_render_abstract of the same request. */
 
-/* hbm_budget_bytes: workspace budget (> 0); n_slots: concurrent requests (1..64). */
+/* hbm_budget_bytes: workspace budget (>= 1 MiB) shared by the slots, beside
+ * the scenes and the callers' output buffers; n_slots: concurrent requests
+ * (1..64).  The server uses the current CUDA device.  AR_EINVAL for bad
+ * arguments, AR_EDEVICE if a stream cannot be created. */
 int ar_serve_create(int64_t hbm_budget_bytes, int32_t n_slots, ar_server **out);
 
-/* Waits for in-flight requests (bounded), then frees the server. */
+/* Drops queued requests (their tickets become unknown), waits for running
+ * ones to finish, then frees the server's streams and workspaces. */
 int ar_serve_destroy(ar_server *server);
 
-/* Submit one request.  The scene must outlive the request; cells are copied;
- * out_lower/out_upper are device buffers as for ar_render_abstract.
- * Returns AR_EAGAIN when no slot or memory is free right now (try again),
- * AR_EINVAL for bad arguments.  *ticket identifies the request. */
+/* Submit one request (non-blocking).  The scene must live on the server's
+ * device and outlive the request; intrinsics, pose and cells are copied;
+ * out_lower/out_upper are device buffers as for ar_render_abstract (tile
+ * chosen automatically) and must not be touched until the ticket is done.
+ * Returns AR_EAGAIN when the queue is full (try again later), AR_EINVAL for
+ * bad arguments (validated as for ar_render_abstract).  *ticket identifies
+ * the request. */
 int ar_serve_submit(ar_server *server, ar_scene *scene, const ar_intrinsics *intr,
                     const ar_nominal_pose *pose, const ar_pose_box *cells, int32_t n_cells,
                     float *out_lower, float *out_upper, uint64_t *ticket);
 
-/* Poll a ticket: *done = 1 once its outputs are complete (then *latency_ms is
- * submit-to-completion wall time and the ticket is retired), else 0.
- * AR_EINVAL for an unknown or retired ticket. */
+/* Poll a ticket: *done = 1 once its outputs are complete; then *latency_ms is
+ * the submit-to-completion wall time, the ticket is retired, and the return
+ * value is the request's own status (AR_OK, or the code its render failed
+ * with, the message in ar_last_error).  *done = 0 (and *latency_ms = -1) while
+ * it waits or runs.  AR_EINVAL for an unknown or retired ticket. */
 int ar_serve_poll(ar_server *server, uint64_t ticket, int *done, double *latency_ms);
 
 /* Message of the calling thread's last failure ("" if none).  The pointer

@@ -250,3 +250,29 @@ class Scene:
         cells = make_cells(cells_lo, cells_hi)
         ar_render_abstract_plain_fp64(self.handle, make_intrinsics(cam), make_pose(cam), cells, len(cells), tile,
                                       out_lower, out_upper, stream)
+
+
+class Server:
+    """Owns an ar_server handle (continuous batching over n_slots streams)."""
+
+    def __init__(self, hbm_budget_bytes: int, n_slots: int):
+        self.handle = ar_serve_create(hbm_budget_bytes, n_slots)
+
+    def submit(self, scene: "Scene", cam, cells_lo, cells_hi, out_lower, out_upper):
+        cells = make_cells(cells_lo, cells_hi)
+        return ar_serve_submit(self.handle, scene.handle, make_intrinsics(cam), make_pose(cam), cells, len(cells),
+                               out_lower, out_upper)
+
+    def poll(self, ticket: int):
+        return ar_serve_poll(self.handle, ticket)
+
+    def close(self):
+        if self.handle is not None:
+            ar_serve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

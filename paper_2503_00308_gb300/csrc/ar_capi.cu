@@ -426,7 +426,7 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
 
 int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_nominal_pose *pose,
                 const ar_pose_box *cells, int32_t n_cells, int32_t tile, float *out_lo, float *out_hi,
-                cudaStream_t st, bool profiling, ar_render_stats *stats, bool plain)
+                cudaStream_t st, bool profiling, ar_render_stats *stats, bool plain, int64_t ws_limit)
 {
     RK(validate_call(in, pose, cells, n_cells, tile));
     if (!out_lo || !out_hi) return fail(AR_EINVAL, "null output");
@@ -465,7 +465,8 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
     // (about a third of the workspace goes to records), and pairs below 2^31
     const size_t rec_bytes = (plain ? sizeof(double) : sizeof(float)) * rec_width(M) + 64;
     const size_t per_cell = rec_bytes * (size_t)s->n;
-    int64_t per_batch = (int64_t)((s->ws_limit / 3) / (per_cell ? per_cell : 1));
+    const int64_t limit = ws_limit > 0 ? ws_limit : s->ws_limit;
+    int64_t per_batch = (int64_t)((limit / 3) / (per_cell ? per_cell : 1));
     const int64_t pair_cap = (int64_t)(((1ull << 31) - 1) / (uint64_t)s->n);
     if (per_batch > pair_cap) per_batch = pair_cap;
     if (per_batch < 1) per_batch = 1;

@@ -40,7 +40,8 @@ int validate_call(const ar_intrinsics *in, const ar_nominal_pose *pose, const ar
                   int32_t tile);
 int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_nominal_pose *pose,
                 const ar_pose_box *cells, int32_t n_cells, int32_t tile, float *out_lo, float *out_hi,
-                cudaStream_t st, bool profiling, ar_render_stats *stats, bool plain = false);
+                cudaStream_t st, bool profiling, ar_render_stats *stats, bool plain = false,
+                int64_t ws_limit = 0);
 
 }  // namespace ar
 

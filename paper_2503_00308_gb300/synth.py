@@ -204,3 +204,52 @@ WORKLOADS = {
     "object300k": object300k,
     "unbounded750k": unbounded750k,
 }
+
+
+# ------------------------------------------------------------------ serving mix
+SERVE_SCENES = {"object10k": lambda: object_scene(10_000, 0),
+                "object300k": lambda: object_scene(300_000, 0),
+                "unbounded750k": lambda: box_scene(750_000, 0)}
+
+_SPLITS = {1: (1, 1, 1, 1, 1, 1), 4: (2, 1, 2, 1, 1, 1), 16: (2, 2, 2, 1, 2, 1), 64: (2, 2, 2, 2, 2, 2),
+           256: (4, 2, 4, 2, 2, 2)}
+
+
+@dataclasses.dataclass
+class Request:
+    scene: str            # key of SERVE_SCENES
+    camera: Camera
+    cells_lo: np.ndarray
+    cells_hi: np.ndarray
+    gap: float            # unit-mean exponential inter-arrival gap (scale by the mean interval)
+
+    def pixel_cells(self) -> int:
+        return self.cells_lo.shape[0] * self.camera.width * self.camera.height
+
+
+def serving_mix(n_requests: int, seed: int = 0, max_out_bytes: float = 1.5e9) -> list[Request]:
+    """A seeded stream of abstract-render requests over the resident 10k / 300k /
+    750k scenes: resolutions 200x200 to 1280x720, 6-DoF pose boxes of 1 to 256
+    cells, Poisson arrivals (unit-mean exponential gaps).  Cell counts are
+    lowered (by 4x steps) until both bound images of a request fit in
+    max_out_bytes."""
+    rng = np.random.default_rng(seed)
+    names = ["object10k", "object300k", "unbounded750k"]
+    sizes = [(200, 200), (400, 300), (640, 480), (800, 800), (1280, 720)]
+    counts = [1, 4, 16, 64, 256]
+    out = []
+    for _ in range(n_requests):
+        name = names[int(rng.choice(3, p=[0.5, 0.3, 0.2]))]
+        w, h = sizes[int(rng.integers(0, len(sizes)))]
+        nc = counts[int(rng.choice(5, p=[0.3, 0.3, 0.2, 0.15, 0.05]))]
+        while nc > 1 and nc * w * h * 24 > max_out_bytes:
+            nc //= 4
+        if name == "unbounded750k":
+            cam = look_camera(w, h, 0.703 * w, centre=(0.0, 0.0, 0.0))
+            hw = [0.10, 0.10, 0.10, 2 * DEG, 2 * DEG, 2 * DEG]
+        else:
+            cam = look_camera(w, h, 1.1 * w if name == "object10k" else 1.375 * w, centre=(0.0, 0.0, -4.0))
+            hw = [0.02, 0.02, 0.02, 0.5 * DEG, 0.5 * DEG, 0.5 * DEG]
+        lo, hi = cell_grid(hw, _SPLITS[nc])
+        out.append(Request(name, cam, lo, hi, float(rng.exponential())))
+    return out
