@@ -355,11 +355,11 @@ def run_ours(args, rank, world, local, pg):
                      "flops_per_triple": flops_per_triple(M), "triples_evaluated": stats["n_evaluated"],
                      "triples_in_boxes": stats["n_triples"],
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal, no measured FP32 peak)"},
-        "stages_ms": {"prep": stats["ms_prep"], "bin": stats["ms_bin"], "render": stats["ms_render"],
-                      "total": stats["ms_total"]},
+        "stages_ms": {"prep": stats["ms_prep"], "bin": stats["ms_bin"], "build": stats["ms_build"],
+                      "render": stats["ms_render"], "total": stats["ms_total"]},
         "counts": {"records": stats["n_records"], "entries": stats["n_entries"], "triples": stats["n_triples"],
                    "evaluated": stats["n_evaluated"], "reevaluated": stats["n_reevaluated"],
-                   "fallback": stats["n_fallback"]},
+                   "fallback": stats["n_fallback"], "built": stats["n_built"], "restarted": stats["n_restarted"]},
     }
     if args.plain_cells > 0:
         line["plain_path"] = plain_path(ar, s, w, intr, pose, args, sp, value)

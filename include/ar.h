@@ -74,7 +74,8 @@ typedef struct ar_render_stats {
     int64_t n_records;          /* (Gaussian, cell) pairs that reach the image */
     int64_t n_entries;          /* (Gaussian, cell, tile) bin entries (2 events each) */
     int64_t n_triples;          /* (pixel, Gaussian, cell) triples inside a screen box */
-    int64_t n_fallback;         /* (Gaussian, cell) pairs where MatrixInv's assertion failed */
+    int64_t n_fallback;         /* (Gaussian, cell) pairs where MatrixInv's assertion failed
+                                   (among the pairs whose records were built) */
     int32_t n_launches;         /* kernels launched by the render */
     int32_t tile;               /* tile edge used (pixels) */
     int32_t m_vars;             /* pose variables carried by the linear forms */
@@ -84,6 +85,13 @@ typedef struct ar_render_stats {
                                    fallbacks, which are constant, are not counted) */
     int64_t n_reevaluated;      /* evaluations repeated at an upper depth endpoint because the
                                    lower endpoint's result had left the per-pixel ring */
+    int64_t n_built;            /* pairs whose record value part (the per-pixel forms, MatrixInv
+                                   included) was built: the FP32 renderer builds only the pairs
+                                   its tiles can reach before their pixels stop */
+    int64_t n_restarted;        /* (cell, tile) sweeps abandoned because they reached entries
+                                   beyond their window of built records, then swept again */
+    float ms_build;             /* record value parts built on demand (included in neither
+                                   ms_prep nor ms_render; ms_render is the per-pixel sweep) */
 } ar_render_stats;
 
 /* Create a scene from n Gaussians <uw, Mw, o, c> (Sec. 2.2).  Mw is given by

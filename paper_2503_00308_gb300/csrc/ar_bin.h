@@ -41,4 +41,13 @@ size_t radix_hist_words(uint64_t n);
 void exclusive_scan(const uint32_t *in, uint32_t *out, uint64_t n, uint32_t *tmp, cudaStream_t st, int *launches);
 int run_binning(const BinArgs &a, BinOut &o, cudaStream_t st, int *launches);
 
+// Windowed rounds of the renderer.  launch_demand claims (state 0 -> 1) the
+// pairs whose lower endpoints lie in the first `window` entries of the
+// active segments and lists them in work (count is incremented); the grid is
+// sized from max_active, the count of active segments is read on the device.
+void launch_set_u32(uint32_t *p, uint32_t v, cudaStream_t st);
+void launch_demand(const uint32_t *active, const uint32_t *n_active, uint32_t max_active, const uint32_t *seg_start,
+                   const uint32_t *seg_end, const uint32_t *ent_ev, const uint32_t *ev_val, uint32_t window,
+                   uint32_t *state, uint32_t *work, uint32_t *count, cudaStream_t st);
+
 }  // namespace ar

@@ -21,6 +21,12 @@
 #include "ar_host.h"
 
 namespace ar {
+// stage events of one cell batch: start, after prep, after binning, then per
+// windowed round: after the record build, after the render
+constexpr int kEventsPerBatch = 9;
+}  // namespace ar
+
+namespace ar {
 size_t cell_data_bytes_m1();
 size_t cell_data_bytes_m4();
 size_t cell_data_bytes_m6();
@@ -45,6 +51,12 @@ int launch_record_prep64_m4(const double *, const double *, const float *, const
                             const void *, int, double *, PixBox *, double *, unsigned long long *, cudaStream_t);
 int launch_record_prep64_m6(const double *, const double *, const float *, const float *, const CallConst &,
                             const void *, int, double *, PixBox *, double *, unsigned long long *, cudaStream_t);
+int launch_record_build_m1(const double *, const CallConst &, const void *, int64_t, const uint32_t *,
+                           const uint32_t *, float *, unsigned long long *, cudaStream_t);
+int launch_record_build_m4(const double *, const CallConst &, const void *, int64_t, const uint32_t *,
+                           const uint32_t *, float *, unsigned long long *, cudaStream_t);
+int launch_record_build_m6(const double *, const CallConst &, const void *, int64_t, const uint32_t *,
+                           const uint32_t *, float *, unsigned long long *, cudaStream_t);
 int launch_render_plain_m1(int, const RenderLaunch &, cudaStream_t);
 int launch_render_plain_m4(int, const RenderLaunch &, cudaStream_t);
 int launch_render_plain_m6(int, const RenderLaunch &, cudaStream_t);
@@ -78,6 +90,14 @@ int launch_record_prep64(int M, const double *vN, const double *tau, const float
     if (M == 1) return launch_record_prep64_m1(vN, tau, opac, rgb, cc, cells, TS, recs, boxes, keys, counters, st);
     if (M == 4) return launch_record_prep64_m4(vN, tau, opac, rgb, cc, cells, TS, recs, boxes, keys, counters, st);
     return launch_record_prep64_m6(vN, tau, opac, rgb, cc, cells, TS, recs, boxes, keys, counters, st);
+}
+int launch_record_build(int M, const double *vN, const CallConst &cc, const void *cells, int64_t n_gauss,
+                        const uint32_t *work, const uint32_t *count, float *recs, unsigned long long *counters,
+                        cudaStream_t st)
+{
+    if (M == 1) return launch_record_build_m1(vN, cc, cells, n_gauss, work, count, recs, counters, st);
+    if (M == 4) return launch_record_build_m4(vN, cc, cells, n_gauss, work, count, recs, counters, st);
+    return launch_record_build_m6(vN, cc, cells, n_gauss, work, count, recs, counters, st);
 }
 int launch_render_plain(int M, int TS, const RenderLaunch &a, cudaStream_t st)
 {
@@ -149,7 +169,7 @@ void Workspace::release()
 {
     DevBuf *all[] = {&cells_lohi, &cells, &vN, &recs, &boxes, &keys, &counters, &evk0, &evk1, &evv0, &evv1,
                      &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege, &segk0,
-                     &segk1, &segv0, &segv1, &work, &out_lo, &out_hi};
+                     &segk1, &segv0, &segv1, &work, &state, &wlist, &act0, &act1, &words, &out_lo, &out_hi};
     for (DevBuf *b : all) b->release();
     if (h_counters) cudaFreeHost(h_counters);
     h_counters = nullptr;
@@ -161,7 +181,8 @@ size_t Workspace::bytes() const
 {
     const DevBuf *all[] = {&cells_lohi, &cells, &vN, &recs, &boxes, &keys, &counters, &evk0, &evk1, &evv0, &evv1,
                            &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege,
-                           &segk0, &segk1, &segv0, &segv1, &work, &out_lo, &out_hi};
+                           &segk0, &segk1, &segv0, &segv1, &work, &state, &wlist, &act0, &act1, &words,
+                           &out_lo, &out_hi};
     size_t s = 0;
     for (const DevBuf *b : all) s += b->cap;
     return s;
@@ -325,7 +346,8 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
     RK(ws.recs.ensure((plain ? sizeof(double) : sizeof(float)) * rec_width(M) * n_pairs));
     RK(ws.boxes.ensure(sizeof(PixBox) * n_pairs));
     RK(ws.keys.ensure(sizeof(double) * 2 * n_pairs));
-    cudaEvent_t *ev = &ws.evs[4 * batch];
+
+    cudaEvent_t *ev = &ws.evs[kEventsPerBatch * batch];
     if (profiling) CK(cudaEventRecord(ev[0], st));
     CK(cudaMemsetAsync(ws.counters.p, 0, sizeof(unsigned long long) * 8, st));
     if (launch_cell_prep(M, d_lo, d_hi, cc, ws.cells.p, st)) return fail(AR_EDEVICE, "cell_prep launch");
@@ -416,11 +438,58 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
     rl.k_open = s->k_open;
     rl.out_lo = out_lo;
     rl.out_hi = out_hi;
-    rl.counters = ws.counters.as<unsigned long long>() + 8 + 2 * batch;
-    if (plain ? launch_render_plain(M, TS, rl, st) : launch_render(M, TS, rl, st))
-        return fail(AR_EDEVICE, "render launch: %s", cudaGetErrorString(cudaGetLastError()));
-    ++launches;
-    if (profiling) CK(cudaEventRecord(ev[3], st));
+    rl.counters = ws.counters.as<unsigned long long>() + 8 + 5 * batch;
+    if (plain) {
+        if (profiling) CK(cudaEventRecord(ev[3], st));
+        if (launch_render_plain(M, TS, rl, st))
+            return fail(AR_EDEVICE, "render launch: %s", cudaGetErrorString(cudaGetLastError()));
+        ++launches;
+        if (profiling)
+            for (int k = 4; k < kEventsPerBatch; ++k) CK(cudaEventRecord(ev[k], st));
+    } else {
+        RK(ws.state.ensure(sizeof(uint32_t) * n_pairs));
+        RK(ws.wlist.ensure(sizeof(uint32_t) * n_pairs));
+        RK(ws.act0.ensure(sizeof(uint32_t) * n_seg));
+        RK(ws.act1.ensure(sizeof(uint32_t) * n_seg));
+        RK(ws.words.ensure(sizeof(uint32_t) * 4));
+        RK(run_windowed_render(M, TS, rl, cc, ws.cells.p, ws.vN.as<double>(), n_pairs, n_seg, ws.state.as<uint32_t>(),
+                               ws.wlist.as<uint32_t>(), ws.act0.as<uint32_t>(), ws.act1.as<uint32_t>(),
+                               ws.words.as<uint32_t>(), rl.counters + 2, st, &launches,
+                               profiling ? ev + 3 : nullptr));
+    }
+    return AR_OK;
+}
+
+int run_windowed_render(int M, int TS, RenderLaunch rl, const CallConst &cc, const void *cells, const double *vN,
+                        uint64_t n_pairs, uint64_t n_seg, uint32_t *state, uint32_t *wlist, uint32_t *act0,
+                        uint32_t *act1, uint32_t *words, unsigned long long *build_counters, cudaStream_t st,
+                        int *launches, cudaEvent_t *ev)
+{
+    static const uint32_t kWindow[3] = {512u, 8192u, 0xffffffffu};
+    uint32_t *act[2] = {act0, act1};
+    CK(cudaMemsetAsync(state, 0, sizeof(uint32_t) * n_pairs, st));
+    launch_set_u32(words + 1, (uint32_t)n_seg, st);
+    ++*launches;
+    for (int r = 0; r < 3; ++r) {
+        uint32_t *cur_n = words + 1 + (r & 1), *nxt_n = words + 1 + ((r + 1) & 1);
+        const uint32_t *cur = r == 0 ? rl.seg_order : act[(r - 1) & 1];
+        CK(cudaMemsetAsync(words, 0, sizeof(uint32_t), st));
+        CK(cudaMemsetAsync(nxt_n, 0, sizeof(uint32_t), st));
+        launch_demand(cur, cur_n, (uint32_t)n_seg, rl.seg_start, rl.seg_end, rl.ent_ev, rl.ev_val, kWindow[r], state,
+                      wlist, words, st);
+        if (launch_record_build(M, vN, cc, cells, rl.n_gauss, wlist, words, rl.recs, build_counters, st))
+            return fail(AR_EDEVICE, "record build launch: %s", cudaGetErrorString(cudaGetLastError()));
+        if (ev) CK(cudaEventRecord(ev[2 * r], st));
+        rl.active = cur;
+        rl.n_active = cur_n;
+        rl.window = kWindow[r];
+        rl.next_active = act[r & 1];
+        rl.n_next = nxt_n;
+        if (launch_render(M, TS, rl, st))
+            return fail(AR_EDEVICE, "render launch: %s", cudaGetErrorString(cudaGetLastError()));
+        if (ev) CK(cudaEventRecord(ev[2 * r + 1], st));
+        *launches += 3;
+    }
     return AR_OK;
 }
 
@@ -437,7 +506,7 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
     ar_render_stats rs;
     std::memset(&rs, 0, sizeof rs);
     rs.tile = TS;
-    rs.ms_prep = rs.ms_bin = rs.ms_render = rs.ms_total = -1.f;
+    rs.ms_prep = rs.ms_bin = rs.ms_render = rs.ms_total = rs.ms_build = -1.f;
     // active pose variables -> form slots (over all cells, so every batch agrees)
     CallConst cc;
     std::memset(&cc, 0, sizeof cc);
@@ -477,14 +546,14 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
     if ((uint64_t)per_batch * (uint64_t)ntx * (uint64_t)nty >= (1ull << 31))
         return fail(AR_EINVAL, "too many (cell, tile) segments");
     if (!ws.h_counters) CK(cudaMallocHost(&ws.h_counters, 8 * sizeof(unsigned long long)));
-    while ((int)ws.evs.size() < 4 * n_batches) {
+    while ((int)ws.evs.size() < kEventsPerBatch * n_batches) {
         cudaEvent_t e;
         CK(cudaEventCreate(&e));
         ws.evs.push_back(e);
     }
     RK(ws.cells_lohi.ensure(sizeof(double) * 12 * n_cells));
     RK(ws.vN.ensure(sizeof(double) * 12 * s->n));
-    RK(ws.counters.ensure(sizeof(unsigned long long) * (8 + 2 * n_batches)));
+    RK(ws.counters.ensure(sizeof(unsigned long long) * (8 + 5 * n_batches)));
     {
         std::vector<double> lohi((size_t)12 * n_cells);
         for (int c = 0; c < n_cells; ++c)
@@ -496,7 +565,7 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
         CK(cudaStreamSynchronize(st));  // the host vector is released on return
     }
     const double *d_lo = ws.cells_lohi.as<double>(), *d_hi = d_lo + (size_t)MAXV * n_cells;
-    CK(cudaMemsetAsync(ws.counters.as<unsigned long long>() + 8, 0, sizeof(unsigned long long) * 2 * n_batches, st));
+    CK(cudaMemsetAsync(ws.counters.as<unsigned long long>() + 8, 0, sizeof(unsigned long long) * 5 * n_batches, st));
     int launches = 0;
     if (launch_pose_prep(s->uw, s->Mw, s->n, cc, ws.vN.as<double>(), st)) return fail(AR_EDEVICE, "pose_prep launch");
     ++launches;
@@ -510,6 +579,8 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
                         out_hi + off, st, profiling, b, rs, launches, plain));
     }
     ws.n_batches = n_batches;
+    ws.fallback_prep = rs.n_fallback;
+    ws.built_prep = plain ? rs.n_records : 0;
     rs.n_launches = launches;
     if (stats) *stats = rs;
     return AR_OK;
@@ -519,25 +590,34 @@ int finish_stats(Workspace &ws, cudaStream_t st, bool profiling, ar_render_stats
 {
     CK(cudaStreamSynchronize(st));
     if (ws.n_batches > 0 && ws.counters.p) {
-        std::vector<unsigned long long> ev(2 * ws.n_batches);
+        std::vector<unsigned long long> ev(5 * ws.n_batches);
         CK(cudaMemcpy(ev.data(), ws.counters.as<unsigned long long>() + 8, sizeof(unsigned long long) * ev.size(),
                       cudaMemcpyDeviceToHost));
         rs.n_evaluated = rs.n_reevaluated = 0;
+        rs.n_fallback = ws.fallback_prep;
+        rs.n_built = ws.built_prep;
+        rs.n_restarted = 0;
         for (int b = 0; b < ws.n_batches; ++b) {
-            rs.n_evaluated += (int64_t)ev[2 * b];
-            rs.n_reevaluated += (int64_t)ev[2 * b + 1];
+            rs.n_evaluated += (int64_t)ev[5 * b];
+            rs.n_reevaluated += (int64_t)ev[5 * b + 1];
+            rs.n_fallback += (int64_t)ev[5 * b + 2];
+            rs.n_built += (int64_t)ev[5 * b + 3];
+            rs.n_restarted += (int64_t)ev[5 * b + 4];
         }
     }
     if (profiling && ws.n_batches > 0) {
-        rs.ms_prep = rs.ms_bin = rs.ms_render = 0.f;
+        rs.ms_prep = rs.ms_bin = rs.ms_render = rs.ms_build = 0.f;
         for (int b = 0; b < ws.n_batches; ++b) {
             float t;
-            const cudaEvent_t *e = &ws.evs[4 * b];
+            const cudaEvent_t *e = &ws.evs[kEventsPerBatch * b];
             CK(cudaEventElapsedTime(&t, e[0], e[1])); rs.ms_prep += t;
             CK(cudaEventElapsedTime(&t, e[1], e[2])); rs.ms_bin += t;
-            CK(cudaEventElapsedTime(&t, e[2], e[3])); rs.ms_render += t;
+            for (int r = 0; r < 3; ++r) {
+                CK(cudaEventElapsedTime(&t, e[2 + 2 * r], e[3 + 2 * r])); rs.ms_build += t;
+                CK(cudaEventElapsedTime(&t, e[3 + 2 * r], e[4 + 2 * r])); rs.ms_render += t;
+            }
         }
-        CK(cudaEventElapsedTime(&rs.ms_total, ws.evs[0], ws.evs[4 * (ws.n_batches - 1) + 3]));
+        CK(cudaEventElapsedTime(&rs.ms_total, ws.evs[0], ws.evs[kEventsPerBatch * ws.n_batches - 1]));
     }
     return AR_OK;
 }

@@ -26,10 +26,13 @@ struct Workspace {
     DevBuf cells_lohi, cells, vN, recs, boxes, keys, counters;
     DevBuf evk0, evk1, evv0, evv1, ents0, ents1, ente0, ente1;
     DevBuf ua, ub, uc, ud, hist, scan, segs, sege, segk0, segk1, segv0, segv1, work;
+    DevBuf state, wlist, act0, act1, words;  // windowed rounds: pair states, build list, active segments
     DevBuf out_lo, out_hi;
     unsigned long long *h_counters = nullptr;  // page-locked
-    std::vector<cudaEvent_t> evs;              // 4 per cell batch (stage timing)
+    std::vector<cudaEvent_t> evs;              // 9 per cell batch (stage timing)
     int n_batches = 0;                         // cell batches of the last render
+    int64_t fallback_prep = 0;                 // MatrixInv fallbacks counted by the record kernel
+    int64_t built_prep = 0;                    // records built completely by the record kernel
     void release();
     size_t bytes() const;
 };
@@ -38,6 +41,16 @@ int set_last_error(int code, const char *msg);  // sets ar_last_error() for this
 
 int validate_call(const ar_intrinsics *in, const ar_nominal_pose *pose, const ar_pose_box *cells, int32_t n_cells,
                   int32_t tile);
+struct RenderLaunch;
+struct CallConst;
+// The FP32 render of one batch in windowed rounds (see render_kernel):
+// demand -> build -> render per round, windows 512, 8192, then unlimited.
+// state [n_pairs] (zeroed here), wlist [n_pairs], act0/act1 [n_seg], words [4];
+// build_counters: [0] fallbacks, [1] records built (optional).
+int run_windowed_render(int M, int TS, RenderLaunch rl, const CallConst &cc, const void *cells, const double *vN,
+                        uint64_t n_pairs, uint64_t n_seg, uint32_t *state, uint32_t *wlist, uint32_t *act0,
+                        uint32_t *act1, uint32_t *words, unsigned long long *build_counters, cudaStream_t st,
+                        int *launches, cudaEvent_t *ev = nullptr);
 int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_nominal_pose *pose,
                 const ar_pose_box *cells, int32_t n_cells, int32_t tile, float *out_lo, float *out_hi,
                 cudaStream_t st, bool profiling, ar_render_stats *stats, bool plain = false,

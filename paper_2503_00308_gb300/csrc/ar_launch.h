@@ -10,16 +10,22 @@ struct CallConst;
 struct PixBox;
 
 struct RenderLaunch {
-    const float *recs;
+    float *recs;                      // FP32 records
     const double *recs64 = nullptr;   // FP64 records (plain renderer only)
     const PixBox *boxes;
     const uint32_t *seg_start, *seg_end, *seg_order, *ent_ev, *ev_val;
+    // windowed rounds (FP32 renderer): segments active[0, *n_active) are swept;
+    // one that needs entries beyond `window` is appended to next_active
+    const uint32_t *active = nullptr, *n_active = nullptr;
+    uint32_t *next_active = nullptr, *n_next = nullptr;
+    uint32_t window = 0xffffffffu;
     const uint64_t *ev_key;
     int W, H, ntx, n_tiles, n_cells;
     int64_t n_gauss;
     float k_open;                     // 1 / (1 - largest opacity), rounded up
     float *out_lo, *out_hi;
-    unsigned long long *counters;     // optional: [0] opacity evaluations, [1] re-evaluations
+    unsigned long long *counters;     // optional: [0] opacity evaluations, [1] re-evaluations,
+                                      // [4] segments abandoned for a wider window ([2], [3]: record build)
     unsigned int *work;               // segment counter of the persistent grid (zeroed by the launcher)
 };
 
@@ -34,6 +40,10 @@ int launch_record_prep64(int M, const double *vN, const double *tau, const float
                          const CallConst &cc, const void *cells, int TS, double *recs, PixBox *boxes, double *keys,
                          unsigned long long *counters, cudaStream_t st);
 int launch_render_plain(int M, int TS, const RenderLaunch &a, cudaStream_t st);
+// value parts of the records listed in work[0, *count); counters: [0] fallbacks, [1] built
+int launch_record_build(int M, const double *vN, const CallConst &cc, const void *cells, int64_t n_gauss,
+                        const uint32_t *work, const uint32_t *count, float *recs, unsigned long long *counters,
+                        cudaStream_t st);
 int launch_scene_prep(const float *logscale, const float *quat, const float *opacity, int64_t n, double *Mw,
                       double *tau, cudaStream_t st);
 int launch_pose_prep(const float *uw, const double *Mw, int64_t n, const CallConst &cc, double *vN,

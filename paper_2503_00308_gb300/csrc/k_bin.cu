@@ -398,4 +398,58 @@ int run_binning(const BinArgs &a, BinOut &o, cudaStream_t st, int *launches)
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 
+// ------------------------------------------------------------ windowed rounds
+__global__ void set_u32_kernel(uint32_t *p, uint32_t v) { *p = v; }
+
+// For each active segment, the lower endpoints among its first `window`
+// entries: every pair not yet claimed (state 0 -> 1) is appended to work.
+// One block per active segment (grid-stride over the active list).
+__global__ void __launch_bounds__(256) demand_kernel(const uint32_t *__restrict__ active,
+                                                     const uint32_t *__restrict__ n_active,
+                                                     const uint32_t *__restrict__ seg_start,
+                                                     const uint32_t *__restrict__ seg_end,
+                                                     const uint32_t *__restrict__ ent_ev,
+                                                     const uint32_t *__restrict__ ev_val, uint32_t window,
+                                                     uint32_t *__restrict__ state, uint32_t *__restrict__ work,
+                                                     uint32_t *__restrict__ count)
+{
+    const uint32_t na = *n_active;
+    const int lane = threadIdx.x & 31;
+    for (uint32_t a = blockIdx.x; a < na; a += gridDim.x) {
+        const uint32_t seg = active[a];
+        const uint32_t b0 = seg_start[seg], b1 = seg_end[seg];
+        const uint32_t e1 = (b1 - b0 > window) ? b0 + window : b1;
+        for (uint32_t i0 = b0; i0 < e1; i0 += blockDim.x) {
+            const uint32_t i = i0 + threadIdx.x;
+            bool claim = false;
+            uint32_t p = 0;
+            if (i < e1) {
+                const uint32_t v = ev_val[ent_ev[i]];
+                p = v >> 1;
+                claim = !(v & 1u) && state[p] == 0u && atomicCAS(&state[p], 0u, 1u) == 0u;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, claim);
+            if (m) {
+                const int leader = __ffs(m) - 1;
+                uint32_t at = 0;
+                if (lane == leader) at = atomicAdd(count, (uint32_t)__popc(m));
+                at = __shfl_sync(0xffffffffu, at, leader);
+                if (claim) work[at + __popc(m & ((1u << lane) - 1u))] = p;
+            }
+        }
+    }
+}
+
+void launch_set_u32(uint32_t *p, uint32_t v, cudaStream_t st) { set_u32_kernel<<<1, 1, 0, st>>>(p, v); }
+
+void launch_demand(const uint32_t *active, const uint32_t *n_active, uint32_t max_active, const uint32_t *seg_start,
+                   const uint32_t *seg_end, const uint32_t *ent_ev, const uint32_t *ev_val, uint32_t window,
+                   uint32_t *state, uint32_t *work, uint32_t *count, cudaStream_t st)
+{
+    unsigned grid = max_active < 152u * 16u ? max_active : 152u * 16u;
+    if (grid == 0) grid = 1;
+    demand_kernel<<<grid, 256, 0, st>>>(active, n_active, seg_start, seg_end, ent_ev, ev_val, window, state, work,
+                                        count);
+}
+
 }  // namespace ar

@@ -27,8 +27,9 @@ int AR_CAT(launch_record_prep_m, AR_M)(const double *vN, const double *tau, cons
 {
     const int T = 128;
     dim3 grid((unsigned)((cc.n_gauss + T - 1) / T), (unsigned)cc.n_cells);
-    record_prep_kernel<AR_M><<<grid, T, 0, st>>>(vN, tau, opac, rgb, cc, (const CellData<AR_M> *)cells, TS, recs,
-                                                 boxes, keys, counters);
+    // decision part only: the value parts are built by the renderer on demand
+    record_prep_kernel<AR_M, float, false><<<grid, T, 0, st>>>(vN, tau, opac, rgb, cc, (const CellData<AR_M> *)cells,
+                                                               TS, recs, boxes, keys, counters);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 
@@ -76,9 +77,24 @@ static int launch_render_ts(const RenderLaunch &a, cudaStream_t st)
     uint32_t grid = (uint32_t)(sms * per_sm);
     if (grid > nseg) grid = nseg;
     if (cudaMemsetAsync(a.work, 0, sizeof(unsigned int), st) != cudaSuccess) return 1;
-    kern<<<grid, TS * TS, SM::BYTES, st>>>(a.recs, a.boxes, a.seg_start, a.seg_end, a.seg_order, a.ent_ev, a.ev_val,
-                                           a.ev_key, a.W, a.H, a.ntx, a.n_tiles, nseg, a.n_gauss, a.k_open, a.out_lo,
+    kern<<<grid, TS * TS, SM::BYTES, st>>>(a.recs, a.boxes, a.seg_start, a.seg_end, a.active, a.n_active, a.window,
+                                           a.next_active, a.n_next, a.ent_ev, a.ev_val,
+                                           a.ev_key, a.W, a.H, a.ntx, a.n_tiles, a.n_gauss, a.k_open, a.out_lo,
                                            a.out_hi, a.counters, a.work);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+int AR_CAT(launch_record_build_m, AR_M)(const double *vN, const CallConst &cc, const void *cells, int64_t n_gauss,
+                                        const uint32_t *work, const uint32_t *count, float *recs,
+                                        unsigned long long *counters, cudaStream_t st)
+{
+    auto kern = record_build_kernel<AR_M>;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    kern<<<sms * per_sm, 128, 0, st>>>(vN, cc.fx, cc.fy, cc.cx, cc.cy, (const CellData<AR_M> *)cells, n_gauss, work,
+                                       count, recs, counters);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 

@@ -222,25 +222,27 @@ struct PrepCount {
     uint32_t triples, fallback, valid, tiles;
 };
 
-// One (Gaussian, cell) pair; returns its counters through pc.  RO is the
+// The decision part of one (Gaussian, cell) pair: depth forms, near-plane
+// class, depth key, pixel box and projected-mean interval, all in FP64.  It
+// writes the pair's key interval and box, and the scalar fields of its record
+// (o, tau, colour, flags F_STRADDLE / F_OPEN, the pixel centre mu); returns
+// the flags word, or -1 when the pair contributes to no pixel.  RO is the
 // precision of the stored record: float for the batched renderer (FP32 value
 // chain with outward rounding), double for the plain FP64 renderer, where
 // the same steps run with every value kept in FP64.
 template <int M, class RO = float>
-__device__ __forceinline__ void record_prep_one(const double *__restrict__ vN, const double *__restrict__ tau_g,
-                                                const float *__restrict__ opacity, const float *__restrict__ rgb,
-                                                const CallConst &cc, const CellData<M> &cd, int cell, int64_t g,
-                                                int TS, RO *__restrict__ recs, PixBox *__restrict__ boxes,
-                                                double *__restrict__ keys, PrepCount &pc)
+__device__ __forceinline__ int64_t record_decide(const double *__restrict__ vN, const double *__restrict__ tau_g,
+                                                 const float *__restrict__ opacity, const float *__restrict__ rgb,
+                                                 const CallConst &cc, const CellData<M> &cd, int cell, int64_t g,
+                                                 int TS, RO *__restrict__ recs, PixBox *__restrict__ boxes,
+                                                 double *__restrict__ keys, PrepCount &pc)
 {
     using RL = Rec<M>;
-    using NO = Num<RO>;
-    typedef BS<M, RO> B;
     const int64_t ri = (int64_t)cell * cc.n_gauss + g;
     PixBox box = {-1, -1, -1, -1};
     boxes[ri] = box;
     const double tau = tau_g[g];
-    if (!(tau >= 0)) return;  // o < 1/255: never above the cutoff
+    if (!(tau >= 0)) return -1;  // o < 1/255: never above the cutoff
     const double *v = vN + 12 * g;
     const double *N = v + 3;
 
@@ -263,7 +265,7 @@ __device__ __forceinline__ void record_prep_one(const double *__restrict__ vN, c
     dd = db_add<M>(dd, db_mul<M>(Rd2[2], vms[2]));
     const double dlo = df_min(dd.lo), dhi = df_max(dd.hi);
     const double nearp = (double)cc.near_plane;
-    if (!(dhi > nearp)) return;
+    if (!(dhi > nearp)) return -1;
     const bool straddle = !(dlo > nearp);
     double klo, khi;
     {
@@ -305,25 +307,50 @@ __device__ __forceinline__ void record_prep_one(const double *__restrict__ vN, c
         xh = dadd(xh, dmul(BOX_SLACK, dadd(1.0, fabs(xh))));
         yl = dsub(yl, dmul(BOX_SLACK, dadd(1.0, fabs(yl))));
         yh = dadd(yh, dmul(BOX_SLACK, dadd(1.0, fabs(yh))));
-        if (!(xh >= xl) || !(yh >= yl)) return;
+        if (!(xh >= xl) || !(yh >= yl)) return -1;
         double fx0 = ceil(dsub(xl, 0.5)), fx1 = floor(dsub(xh, 0.5));
         double fy0 = ceil(dsub(yl, 0.5)), fy1 = floor(dsub(yh, 0.5));
         fx0 = fmax(fx0, 0.0); fy0 = fmax(fy0, 0.0);
         fx1 = fmin(fx1, (double)(cc.W - 1)); fy1 = fmin(fy1, (double)(cc.H - 1));
-        if (fx0 > fx1 || fy0 > fy1) return;
+        if (fx0 > fx1 || fy0 > fy1) return -1;
         box = PixBox{(int)fx0, (int)fx1, (int)fy0, (int)fy1};
         mu_lo[0] = mux.l; mu_hi[0] = mux.u; mu_lo[1] = muy.l; mu_hi[1] = muy.u;
     }
 
-    // ---- value chain (record precision)
     RO *rec = recs + ri * RL::WIDTH;
-    uint32_t flags = (straddle ? F_STRADDLE : 0u) | (klo < khi ? F_OPEN : 0u);
-    const float o = opacity[g];
-    rec[RL::O] = o;
+    const uint32_t flags = (straddle ? F_STRADDLE : 0u) | (klo < khi ? F_OPEN : 0u);
+    rec[RL::O] = opacity[g];
     rec_dn(tau, rec[RL::TAU_DN]);
     rec_up(tau, rec[RL::TAU_UP]);
     for (int k = 0; k < 3; ++k) rec[RL::COL + k] = rgb[3 * g + k];
+    // pixel centre near the projected mean, the expansion point of R = mu S - P
+    rec[RL::MU_X] = (RO)(floor(fmin(fmax(0.5 * (mu_lo[0] + mu_hi[0]), -1e6), 1e6)) + 0.5);
+    rec[RL::MU_Y] = (RO)(floor(fmin(fmax(0.5 * (mu_lo[1] + mu_hi[1]), -1e6), 1e6)) + 0.5);
+    rec_put_flags(rec + RL::FLAGS, flags);
+    keys[2 * ri] = klo;
+    keys[2 * ri + 1] = khi;
+    boxes[ri] = box;
+    pc.triples = (uint32_t)(box.x1 - box.x0 + 1) * (uint32_t)(box.y1 - box.y0 + 1);
+    pc.valid = 1;
+    pc.tiles = (uint32_t)(box.x1 / TS - box.x0 / TS + 1) * (uint32_t)(box.y1 / TS - box.y0 / TS + 1);
+    return flags;
+}
 
+// The value part of one (Gaussian, cell) pair: the forms the per-pixel stage
+// reads, S = d^2 and R = mu S - P (Algorithm 1 lines 2-8 with set-valued
+// variables), MatrixInv (Algorithm 3) and W = Conic Mp.  v points at the
+// Gaussian's v (3) and N (9); rec holds the scalar fields record_decide wrote,
+// mu_x / mu_y and flags are their values; fx, fy, cx, cy the intrinsics.  Writes the forms and the flags word
+// (with F_FALLBACK where the MatrixInv assertion fails or a form is not
+// finite) and returns that word.
+template <int M, class RO = float>
+__device__ __forceinline__ uint32_t record_value(const double *__restrict__ v, float fx, float fy, float cx, float cy,
+                                                 const CellData<M> &cd, RO mux, RO muy, uint32_t flags, RO *rec)
+{
+    using RL = Rec<M>;
+    using NO = Num<RO>;
+    typedef BS<M, RO> B;
+    const double *N = v + 3;
     bool ok = true;
     typedef BS<M, double> BD;
     // ---- FP64 value chain (directed rounding): uc, S, P, Mc, J, Mp, X, E.
@@ -356,13 +383,11 @@ __device__ __forceinline__ void record_prep_one(const double *__restrict__ vN, c
         // mu near the projected mean (see Rec)
         BD u0, u1;
         Pair<M, double> p;
-        p.init(0.0, 0.0); p.lin((double)cc.fx, uc64[0]); p.lin((double)cc.cx, uc64[2]); u0 = p.result();
-        p.init(0.0, 0.0); p.lin((double)cc.fy, uc64[1]); p.lin((double)cc.cy, uc64[2]); u1 = p.result();
+        p.init(0.0, 0.0); p.lin((double)fx, uc64[0]); p.lin((double)cx, uc64[2]); u0 = p.result();
+        p.init(0.0, 0.0); p.lin((double)fy, uc64[1]); p.lin((double)cy, uc64[2]); u1 = p.result();
         const BD S = b_sqr<M, double>(d64);
         const BD Px = b_mul<M, double>(d64, u0);
         const BD Py = b_mul<M, double>(d64, u1);
-        const RO mux = (RO)(floor(fmin(fmax(0.5 * (mu_lo[0] + mu_hi[0]), -1e6), 1e6)) + 0.5);
-        const RO muy = (RO)(floor(fmin(fmax(0.5 * (mu_lo[1] + mu_hi[1]), -1e6), 1e6)) + 0.5);
         BD Rx, Ry;
         {
             Acc<M, double, true> lo;
@@ -385,8 +410,6 @@ __device__ __forceinline__ void record_prep_one(const double *__restrict__ vN, c
         rec[RL::RAD + 0] = S32.rlo; rec[RL::RAD + 1] = S32.rhi;
         rec[RL::RAD + 2] = Rx32.rlo; rec[RL::RAD + 3] = Rx32.rhi;
         rec[RL::RAD + 4] = Ry32.rlo; rec[RL::RAD + 5] = Ry32.rhi;
-        rec[RL::MU_X] = mux;
-        rec[RL::MU_Y] = muy;
     }
     BD Mp64[6];
     {
@@ -402,10 +425,10 @@ __device__ __forceinline__ void record_prep_one(const double *__restrict__ vN, c
             }
         BD J00, J02, J11, J12;
         Pair<M, double> p;
-        p.init(0.0, 0.0); p.lin((double)cc.fx, d64); J00 = p.result();
-        p.init(0.0, 0.0); p.lin(-(double)cc.fx, uc64[0]); J02 = p.result();
-        p.init(0.0, 0.0); p.lin((double)cc.fy, d64); J11 = p.result();
-        p.init(0.0, 0.0); p.lin(-(double)cc.fy, uc64[1]); J12 = p.result();
+        p.init(0.0, 0.0); p.lin((double)fx, d64); J00 = p.result();
+        p.init(0.0, 0.0); p.lin(-(double)fx, uc64[0]); J02 = p.result();
+        p.init(0.0, 0.0); p.lin((double)fy, d64); J11 = p.result();
+        p.init(0.0, 0.0); p.lin(-(double)fy, uc64[1]); J12 = p.result();
         for (int c = 0; c < 3; ++c) {
             p.init(0.0, 0.0); p.mul(J00, Mc[c]); p.mul(J02, Mc[6 + c]); Mp64[c] = p.result();
             p.init(0.0, 0.0); p.mul(J11, Mc[3 + c]); p.mul(J12, Mc[6 + c]); Mp64[3 + c] = p.result();
@@ -510,23 +533,17 @@ __device__ __forceinline__ void record_prep_one(const double *__restrict__ vN, c
             }
     }
     if (!ok) fallback = true;
-    if (fallback) {
-        flags |= F_FALLBACK;
-        pc.fallback = 1;
-    }
+    if (fallback) flags |= F_FALLBACK;
     rec_put_flags(rec + RL::FLAGS, flags);
-    keys[2 * ri] = klo;
-    keys[2 * ri + 1] = khi;
-    boxes[ri] = box;
-    pc.triples = (uint32_t)(box.x1 - box.x0 + 1) * (uint32_t)(box.y1 - box.y0 + 1);
-    pc.valid = 1;
-    pc.tiles = (uint32_t)(box.x1 / TS - box.x0 / TS + 1) * (uint32_t)(box.y1 / TS - box.y0 / TS + 1);
+    return flags;
 }
 
 // grid: x over Gaussians, y over cells.  One thread per (Gaussian, cell).
+// VALUE = false builds only the decision part (the value part is then built
+// on demand by the renderer).
 // counters: [0] pixel-Gaussian-cell triples in boxes, [1] MatrixInv
 // fallbacks, [2] pairs present, [3] (pair, tile) entries.
-template <int M, class RO = float>
+template <int M, class RO = float, bool VALUE = true>
 __global__ void __launch_bounds__(128) record_prep_kernel(
     const double *__restrict__ vN, const double *__restrict__ tau_g, const float *__restrict__ opacity,
     const float *__restrict__ rgb, CallConst cc, const CellData<M> *__restrict__ cells, int TS,
@@ -536,7 +553,16 @@ __global__ void __launch_bounds__(128) record_prep_kernel(
     const int cell = blockIdx.y;
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     PrepCount pc = {0, 0, 0, 0};
-    if (g < cc.n_gauss) record_prep_one<M, RO>(vN, tau_g, opacity, rgb, cc, cells[cell], cell, g, TS, recs, boxes, keys, pc);
+    if (g < cc.n_gauss) {
+        const int64_t fl = record_decide<M, RO>(vN, tau_g, opacity, rgb, cc, cells[cell], cell, g, TS, recs, boxes,
+                                                keys, pc);
+        if (VALUE && fl >= 0) {
+            RO *rec = recs + ((int64_t)cell * cc.n_gauss + g) * Rec<M>::WIDTH;
+            const uint32_t f = record_value<M, RO>(vN + 12 * g, cc.fx, cc.fy, cc.cx, cc.cy, cells[cell], rec[Rec<M>::MU_X],
+                                                   rec[Rec<M>::MU_Y], (uint32_t)fl, rec);
+            pc.fallback = (f & F_FALLBACK) ? 1u : 0u;
+        }
+    }
     const uint32_t t = __reduce_add_sync(0xffffffffu, pc.triples);
     const uint32_t f = __reduce_add_sync(0xffffffffu, pc.fallback);
     const uint32_t v = __reduce_add_sync(0xffffffffu, pc.valid);
@@ -546,6 +572,40 @@ __global__ void __launch_bounds__(128) record_prep_kernel(
         if (f) atomicAdd(&counters[1], (unsigned long long)f);
         if (v) atomicAdd(&counters[2], (unsigned long long)v);
         if (e) atomicAdd(&counters[3], (unsigned long long)e);
+    }
+}
+
+// Builds the value part of the records listed in work[0, *count) (pair
+// indices within the batch, cell * n_gauss + g), whose decision part the
+// record kernel wrote.  Grid-stride over the list; the grid is sized on the
+// host without knowing the count.
+// counters: [0] MatrixInv fallbacks among the records built, [1] records built.
+template <int M>
+__global__ void __launch_bounds__(128) record_build_kernel(
+    const double *__restrict__ vN, float fx, float fy, float cx, float cy, const CellData<M> *__restrict__ cells,
+    int64_t n_gauss, const uint32_t *__restrict__ work, const uint32_t *__restrict__ count, float *__restrict__ recs,
+    unsigned long long *__restrict__ counters)
+{
+    using RL = Rec<M>;
+    const uint32_t n = *count;
+    uint32_t built = 0, fb = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t p = work[i];
+        const int cell = (int)(p / (uint64_t)n_gauss);
+        const int64_t g = (int64_t)p - (int64_t)cell * n_gauss;
+        float *rec = recs + (size_t)p * RL::WIDTH;
+        const uint32_t f = record_value<M, float>(vN + 12 * g, fx, fy, cx, cy, cells[cell], rec[RL::MU_X],
+                                                  rec[RL::MU_Y], __float_as_uint(rec[RL::FLAGS]), rec);
+        ++built;
+        if (f & F_FALLBACK) ++fb;
+    }
+    if (counters) {
+        const uint32_t a = __reduce_add_sync(0xffffffffu, fb);
+        const uint32_t b = __reduce_add_sync(0xffffffffu, built);
+        if ((threadIdx.x & 31) == 0) {
+            if (a) atomicAdd(&counters[0], (unsigned long long)a);
+            if (b) atomicAdd(&counters[1], (unsigned long long)b);
+        }
     }
 }
 

@@ -288,14 +288,24 @@ template <int M, int TS, int CH, int RING> struct RenderSmem {
     static constexpr size_t BYTES = REC + EV + BOX + RID + RPAY + 16;
 };
 
-// Persistent grid: each CTA takes (cell, tile) segments, longest first, from
-// an atomic counter until none are left; block = TS*TS threads.
+// Persistent grid: each CTA takes (cell, tile) segments from the active list
+// (longest first in the first round) through an atomic counter until none
+// are left; block = TS*TS threads.
+//
+// Windowed rounds: only the records of the pairs whose lower endpoints lie in
+// the first `window` entries of an active segment have been built.  A
+// segment that would stage an entry beyond its window before all its pixels
+// have stopped is abandoned (no output written) and appended to next_active;
+// the next round builds the records of a wider window and sweeps it again
+// from its start.  The sweep is deterministic, so the restarted segment
+// gives the same bounds it would have given in one pass.
 template <int M, int TS, int CH, int RING>
 __global__ void __launch_bounds__(TS *TS, 1) render_kernel(
     const float *__restrict__ recs, const PixBox *__restrict__ boxes, const uint32_t *__restrict__ seg_start,
-    const uint32_t *__restrict__ seg_end, const uint32_t *__restrict__ seg_order,
+    const uint32_t *__restrict__ seg_end, const uint32_t *__restrict__ active, const uint32_t *__restrict__ n_active,
+    uint32_t window, uint32_t *__restrict__ next_active, uint32_t *__restrict__ n_next,
     const uint32_t *__restrict__ entry_ev, const uint32_t *__restrict__ ev_val,
-    const uint64_t *__restrict__ ev_key, int W, int H, int ntx, int n_tiles, uint32_t n_seg, int64_t n_gauss,
+    const uint64_t *__restrict__ ev_key, int W, int H, int ntx, int n_tiles, int64_t n_gauss,
     float k_open, float *__restrict__ out_lo, float *__restrict__ out_hi,
     unsigned long long *__restrict__ counters, unsigned int *__restrict__ work)
 {
@@ -311,6 +321,7 @@ __global__ void __launch_bounds__(TS *TS, 1) render_kernel(
     uint32_t *s_next = reinterpret_cast<uint32_t *>(smem_raw + SM::REC + SM::EV + SM::BOX + SM::RID + SM::RPAY);
     const int tid = threadIdx.x;
     uint32_t evals = 0, recomp = 0;
+    const uint32_t n_seg = *n_active;
 
     for (;;) {
         if (tid == 0) *s_next = atomicAdd(work, 1u);
@@ -318,7 +329,7 @@ __global__ void __launch_bounds__(TS *TS, 1) render_kernel(
         const uint32_t wk = *s_next;
         __syncthreads();
         if (wk >= n_seg) break;
-        const uint32_t seg = seg_order[wk];
+        const uint32_t seg = active[wk];
         const int cell = (int)(seg / (uint32_t)n_tiles);
         const int tile = (int)(seg - (uint32_t)cell * (uint32_t)n_tiles);
         const int tx = tile % ntx, ty = tile / ntx;
@@ -342,6 +353,8 @@ __global__ void __launch_bounds__(TS *TS, 1) render_kernel(
         uint32_t head = 0;
         bool done = !inside;
         float lo_adj = 0.f, hi_adj = 0.f;  // -1: decided 0 / 1; >= 0: widening for skipped events
+        bool abandoned = false;
+        uint32_t seg_evals = 0, seg_recomp = 0;
 
         for (uint32_t base = b0; base < b1; base += CH) {
             const int cnt = (int)min((uint32_t)CH, b1 - base);
@@ -365,6 +378,10 @@ __global__ void __launch_bounds__(TS *TS, 1) render_kernel(
                 }
             }
             if (__syncthreads_and(done)) break;
+            if (base + (uint32_t)cnt - b0 > window) {  // records beyond the window are not built
+                abandoned = true;
+                break;
+            }
             if (tid < cnt) {
                 const uint32_t i = base + tid;
                 const uint32_t e = entry_ev[i];
@@ -415,7 +432,7 @@ __global__ void __launch_bounds__(TS *TS, 1) render_kernel(
                     pixel_alpha<M>(r, ux, uy, cache);
                     // a MatrixInv fallback is a constant [0, o]: not an evaluation
                     if (!(__float_as_uint(r[RL::FLAGS]) & F_FALLBACK)) {
-                        if (lower) ++evals; else ++recomp;
+                        if (lower) ++seg_evals; else ++seg_recomp;
                     }
                 }
                 c_rec = ev.rec;
@@ -445,6 +462,15 @@ __global__ void __launch_bounds__(TS *TS, 1) render_kernel(
                 }
             }
         }
+        if (abandoned) {
+            if (tid == 0) {
+                next_active[atomicAdd(n_next, 1u)] = seg;
+                if (counters) atomicAdd(&counters[4], 1ull);
+            }
+            continue;
+        }
+        evals += seg_evals;
+        recomp += seg_recomp;
         if (inside) {
             const size_t o = ((size_t)cell * H * W + (size_t)py * W + px) * 3;
 #pragma unroll

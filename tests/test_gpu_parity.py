@@ -211,3 +211,25 @@ def test_cell_batches_are_bit_identical(arlib):
     assert np.array_equal(out_hi.double().cpu().numpy(), ref_hi)
     assert st["n_records"] > 0 and st["ms_render"] > 0
     s.close()
+
+
+def test_windowed_rounds_restart(arlib, orc):
+    """Faint, dense scenes: tiles never stop early, so sweeps outgrow the first
+    (512-entry) and second (8192-entry) windows of built records and are swept
+    again; the bounds match the oracle and the plain FP64 path."""
+    sc = synth.object_scene(4500, 9, mean_sd=0.15, logscale_mu=-2.6)
+    sc.opacity[:] = np.float32(0.02)
+    cam = synth.look_camera(40, 24, 60.0, centre=(0, 0, -4))
+    lo, hi = synth.cell_grid([0.01, 0.0, 0.01, 0.0, 0.0, 0.0], [1, 1, 1, 1, 1, 1])
+    glo, ghi, st = gpu_render(arlib, sc, cam, lo, hi, tile=16, return_stats=True)
+    assert st["n_restarted"] > 0, st
+    assert st["n_built"] == st["n_records"]          # every record is reached
+    compare(orc, sc, cam, lo[0], hi[0], glo[0], ghi[0], window=(8, 4, 16, 12))
+    s = arlib.Scene(sc)
+    plo = torch.empty((1, cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
+    phi = torch.empty_like(plo)
+    s.render_plain_fp64(cam, lo, hi, plo, phi)
+    torch.cuda.synchronize()
+    d = np.maximum(np.abs(glo - plo.double().cpu().numpy()), np.abs(ghi - phi.double().cpu().numpy()))
+    assert d.max() <= 2 * TOL, d.max()
+    s.close()
