@@ -250,24 +250,29 @@ struct EvInfo {
     uint32_t bits;  // bit 0: upper endpoint, bit 1: key equals the previous entry's key
 };
 
-// Early exit, only where the clipped result is already decided, so that the
-// output is bit-identical to the full sweep (and independent of the tile):
+// Early exit.  Write PA, PB for the running transmittance products and
+// n_open for the Gaussians of this pixel whose lower endpoint has been swept
+// but not yet their upper one.  Every depth-key interval is open (klo < khi:
+// the keys are padded), so the lower endpoint of a Gaussian that has not yet
+// started precedes, with a strictly smaller key, the upper endpoint of every
+// Gaussian behind it.
 //  - upper: a later term T_hi c U has U >= a >= 0 at every pose of the cell,
 //    so the constant of its U form is >= 0 and the upward-rounded constant of
 //    the upper sum only grows; its final bound is at least that constant, so
-//    once the constant is >= 1 in every channel the clipped bound is 1;
-//  - lower: a later term T_lo c L has max|L| <= 1 over the cell (so its
-//    constant plus its coefficient radius is <= 1) and T_lo at most the
-//    product absorbed so far over (1 - its own opacity) <= PA / (1 - o_max);
-//    with E = (events left) PA / (1 - o_max) the final constant is at most
-//    the current one + E and the final radius at least the current one - E,
-//    so once (constant - radius) + 2E <= 0 in every channel the clipped
+//    once the constant is >= 1 in every channel the clipped bound is 1.
+//    Otherwise the remaining terms add at most Eh = (events left) 1.1 PB to
+//    the maximum over the cell (T_hi <= PB, max U <= 1.0625 o).
+//  - lower: a later term T_lo c L has |L| <= a_hi over the cell.  For the
+//    Gaussians not yet started, taken in the order of their upper endpoints,
+//    T_lo(i_k) <= PA prod_{l<k} (1 - a_hi(i_l)) (the division by 1 - a_hi at
+//    the upper endpoint removes i_k's own factor), so their terms telescope
+//    to at most PA; each open Gaussian adds at most PA / (1 - o_max).  So
+//    the remaining terms move the minimum over the cell by at most
+//    El = PA (1 + n_open / (1 - o_max)) (times 1.01 for the rounding of PA),
+//    and once (constant - radius) + El <= 0 in every channel the clipped
 //    bound is 0.
-// Otherwise a side also stops once twice the bound on everything the
-// remaining events could still add is below EXIT_EPS (E as above for the
-// lower side; for the upper side (events left) x 1.1 x PB, since T_hi of a
-// later Gaussian is at most PB and max U <= 1.1); the bound is then widened
-// by that amount, which keeps it sound and within EXIT_EPS of the full sweep.
+// Otherwise a side also stops once its E is below EXIT_EPS; its bound is then
+// widened by E, which keeps it sound and within EXIT_EPS of the full sweep.
 // A pixel stops when both sides have; a tile stops when all its pixels have.
 constexpr float EXIT_EPS = 5e-8f;
 
@@ -346,6 +351,7 @@ __global__ void __launch_bounds__(TS *TS, 1) render_kernel(
         lo.init();
         hi.init();
         float PA = 1.f, PB = 1.f, PAp = 1.f, PBp = 1.f;
+        int n_open = 0;  // Gaussians of this pixel between their two endpoints
         uint32_t c_rec = 0xffffffffu;  // register copy of the latest evaluation
         AlphaOut<M> cache;
 #pragma unroll
@@ -361,8 +367,8 @@ __global__ void __launch_bounds__(TS *TS, 1) render_kernel(
             if (!done) {
                 const float left = (float)(b1 - base);
                 // PA is rounded down; 1.01 covers its relative error for < 10^5 factors
-                const float elo2 = __fmul_ru(2.f, __fmul_ru(__fmul_ru(left, __fmul_ru(PA, 1.01f)), k_open));
-                const float ehi2 = __fmul_ru(2.2f, __fmul_ru(left, PB));
+                const float elo2 = __fmul_ru(__fmul_ru(PA, 1.01f), __fmaf_ru((float)n_open, k_open, 1.f));
+                const float ehi2 = __fmul_ru(1.1f, __fmul_ru(left, PB));
                 bool lo_zero = true, hi_one = true;
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch) {
@@ -412,6 +418,7 @@ __global__ void __launch_bounds__(TS *TS, 1) render_kernel(
                 if (px < bx.x0 || px > bx.x1 || py < bx.y0 || py > bx.y1) continue;
                 const float *r = s_rec[e];
                 const bool lower = !(ev.bits & 1u);
+                n_open += lower ? 1 : -1;
                 bool have = !lower && c_rec == ev.rec;
                 if (!lower && !have) {
 #pragma unroll
