@@ -8,8 +8,9 @@
 //                     the order-preserving bits of the FP64 key;
 //   3. sort         : stable LSD radix sort by key, then stably by cell;
 //   4. entries      : each event is copied to every tile its pixel box meets,
-//                     in sorted-event order, keyed by segment = cell*tiles+tile;
-//   5. sort         : stable LSD radix sort by segment (keeps key order inside);
+//                     in sorted-event order (cell-major), keyed by tile and cell;
+//   5. sort         : stable LSD radix sort by tile (keeps the cell-major key
+//                     order inside, so every (cell, tile) segment is contiguous);
 //   6. bounds       : [start, end) of every segment.
 #include "ar_bin.h"
 #include "ar_common.cuh"
@@ -135,6 +136,10 @@ __global__ void __launch_bounds__(RS_THREADS) rs_hist_kernel(const K *__restrict
     hist[(uint64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
+// Scatter of one radix pass.  Each block ranks its RS_TILE items by digit
+// (stable: warps in order, rounds in order, lanes in order), reorders them by
+// digit in shared memory, then writes every digit run to its global offset
+// with consecutive threads on consecutive addresses.
 template <class K>
 __global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(const K *__restrict__ kin,
                                                                 const uint32_t *__restrict__ vin,
@@ -144,11 +149,17 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(const K *__restr
                                                                 uint32_t nblocks)
 {
     __shared__ uint32_t wcnt[RS_WARPS][256];
+    __shared__ uint32_t dstart[256];   // block-local start of each digit run
+    __shared__ uint32_t gbase[256];    // global start of each digit run of this block
+    __shared__ uint32_t s_warp[RS_WARPS];
+    __shared__ K s_key[RS_TILE];
+    __shared__ uint32_t s_val[RS_TILE];
     for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t ltmask = (1u << lane) - 1u;
-    const uint64_t base = (uint64_t)blockIdx.x * RS_TILE + (uint64_t)warp * (RS_ROUNDS * 32);
+    const uint64_t blk0 = (uint64_t)blockIdx.x * RS_TILE;
+    const uint64_t base = blk0 + (uint64_t)warp * (RS_ROUNDS * 32);
     K key[RS_ROUNDS];
     uint32_t val[RS_ROUNDS], dig[RS_ROUNDS], rank[RS_ROUNDS];
 #pragma unroll
@@ -168,6 +179,7 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(const K *__restr
     }
     __syncthreads();
     {
+        // per digit: warp prefix, block total, then the block-local start
         const int d = threadIdx.x;  // 256 threads = 256 digits
         uint32_t run = 0;
 #pragma unroll
@@ -176,15 +188,36 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(const K *__restr
             wcnt[w][d] = run;
             run += t;
         }
+        uint32_t x = run;  // inclusive scan of the totals over the 256 digits
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        uint32_t wpre = 0;
+        for (int w = 0; w < warp; ++w) wpre += s_warp[w];
+        dstart[d] = wpre + x - run;
+        gbase[d] = offs[(uint64_t)d * nblocks + blockIdx.x];
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < RS_ROUNDS; ++r) {
         if (dig[r] < 256u) {
-            const uint32_t pos = offs[(uint64_t)dig[r] * nblocks + blockIdx.x] + wcnt[warp][dig[r]] + rank[r];
-            kout[pos] = key[r];
-            vout[pos] = val[r];
+            const uint32_t lp = dstart[dig[r]] + wcnt[warp][dig[r]] + rank[r];
+            s_key[lp] = key[r];
+            s_val[lp] = val[r];
         }
+    }
+    __syncthreads();
+    const uint32_t cnt = n - blk0 < (uint64_t)RS_TILE ? (uint32_t)(n - blk0) : (uint32_t)RS_TILE;
+    for (uint32_t j = threadIdx.x; j < cnt; j += RS_THREADS) {
+        const K k = s_key[j];
+        const uint32_t d = (uint32_t)(k >> shift) & 255u;
+        const uint32_t pos = gbase[d] + (j - dstart[d]);
+        kout[pos] = k;
+        vout[pos] = s_val[j];
     }
 }
 
@@ -194,18 +227,18 @@ size_t radix_hist_words(uint64_t n)
     return 256 * nb;
 }
 
-// Stable LSD sort of (keys, vals) on key bits [0, bits).  Uses the alt
-// buffers; returns 1 if the result ended in the alt buffers.
+// Stable LSD sort of (keys, vals) on key bits [shift0, shift0 + bits).  Uses
+// the alt buffers; returns 1 if the result ended in the alt buffers.
 template <class K>
 static int radix_sort(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt, uint64_t n, int bits,
-                      uint32_t *hist, uint32_t *scan_tmp, cudaStream_t st, int *launches)
+                      uint32_t *hist, uint32_t *scan_tmp, cudaStream_t st, int *launches, int shift0 = 0)
 {
     if (n == 0) return 0;
     const uint32_t nb = (uint32_t)((n + RS_TILE - 1) / RS_TILE);
     K *ka = keys, *kb = keys_alt;
     uint32_t *va = vals, *vb = vals_alt;
     int flips = 0;
-    for (int shift = 0; shift < bits; shift += 8) {
+    for (int shift = shift0; shift < shift0 + bits; shift += 8) {
         rs_hist_kernel<K><<<nb, RS_THREADS, 0, st>>>(ka, (uint32_t)n, shift, hist, nb);
         ++*launches;
         exclusive_scan(hist, hist, (uint64_t)256 * nb, scan_tmp, st, launches);
@@ -260,8 +293,21 @@ __global__ void tile_counts_kernel(const uint32_t *__restrict__ ev_val, uint64_t
     cnt[e] = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
 }
 
+// Entry keys: (tile << cb) | cell when cb >= 0 (the entries of one cell are
+// contiguous and in key order, so a stable sort on the tile bits alone leaves
+// every (cell, tile) segment contiguous and in key order), else the segment
+// cell * n_tiles + tile.
+__device__ __forceinline__ uint32_t entry_key(uint32_t cell, uint32_t tile, int cb, int n_tiles)
+{
+    return cb >= 0 ? ((tile << cb) | cell) : cell * (uint32_t)n_tiles + tile;
+}
+__device__ __forceinline__ uint32_t entry_segment(uint32_t key, int cb, int n_tiles)
+{
+    return cb >= 0 ? (key & ((1u << cb) - 1u)) * (uint32_t)n_tiles + (key >> cb) : key;
+}
+
 __global__ void emit_entries_kernel(const uint32_t *__restrict__ ev_val, uint64_t ne,
-                                    const PixBox *__restrict__ boxes, int TS, int ntx, int n_tiles,
+                                    const PixBox *__restrict__ boxes, int TS, int ntx, int n_tiles, int cb,
                                     uint64_t n_gauss, const uint32_t *__restrict__ off,
                                     uint32_t *__restrict__ ent_seg, uint32_t *__restrict__ ent_ev)
 {
@@ -274,7 +320,7 @@ __global__ void emit_entries_kernel(const uint32_t *__restrict__ ev_val, uint64_
     uint32_t o = off[e];
     for (int ty = ty0; ty <= ty1; ++ty)
         for (int tx = tx0; tx <= tx1; ++tx) {
-            ent_seg[o] = cell * (uint32_t)n_tiles + (uint32_t)(ty * ntx + tx);
+            ent_seg[o] = entry_key(cell, (uint32_t)(ty * ntx + tx), cb, n_tiles);
             ent_ev[o] = (uint32_t)e;
             ++o;
         }
@@ -290,14 +336,15 @@ __global__ void seg_len_kernel(const uint32_t *__restrict__ start, const uint32_
     val[i] = (uint32_t)i;
 }
 
-__global__ void seg_bounds_kernel(const uint32_t *__restrict__ seg, uint64_t n, uint32_t *__restrict__ start,
-                                  uint32_t *__restrict__ end)
+__global__ void seg_bounds_kernel(const uint32_t *__restrict__ key, uint64_t n, int cb, int n_tiles,
+                                  uint32_t *__restrict__ start, uint32_t *__restrict__ end)
 {
     const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const uint32_t s = seg[i];
-    if (i == 0 || seg[i - 1] != s) start[s] = (uint32_t)i;
-    if (i == n - 1 || seg[i + 1] != s) end[s] = (uint32_t)(i + 1);
+    const uint32_t k = key[i];
+    const uint32_t s = entry_segment(k, cb, n_tiles);
+    if (i == 0 || key[i - 1] != k) start[s] = (uint32_t)i;
+    if (i == n - 1 || key[i + 1] != k) end[s] = (uint32_t)(i + 1);
 }
 
 __global__ void iota_kernel(uint32_t *__restrict__ p, uint64_t n)
@@ -370,22 +417,34 @@ int run_binning(const BinArgs &a, BinOut &o, cudaStream_t st, int *launches)
     tile_counts_kernel<<<blocks_for(ne, T), T, 0, st>>>(evv, ne, a.boxes, a.TS, a.u32_a);
     ++*launches;
     exclusive_scan(a.u32_a, a.u32_a, ne, a.scan_tmp, st, launches);
-    emit_entries_kernel<<<blocks_for(ne, T), T, 0, st>>>(evv, ne, a.boxes, a.TS, a.ntx, a.n_tiles, a.n_gauss,
-                                                          a.u32_a, a.ent_seg[0], a.ent_ev[0]);
+    // entry keys: tile bits above cell bits when both fit in 32 bits
+    int cb = 0, tb = 0;
+    while ((1ull << cb) < (uint64_t)a.n_cells) ++cb;
+    while ((1ull << tb) < (uint64_t)a.n_tiles) ++tb;
+    if (tb == 0) tb = 1;
+    const bool packed = cb + tb <= 32;
+    emit_entries_kernel<<<blocks_for(ne, T), T, 0, st>>>(evv, ne, a.boxes, a.TS, a.ntx, a.n_tiles, packed ? cb : -1,
+                                                          a.n_gauss, a.u32_a, a.ent_seg[0], a.ent_ev[0]);
     ++*launches;
-    // 5. stable sort by segment
-    int bits = 0;
-    while ((1ull << bits) < a.n_segments) bits += 8;
-    if (bits == 0) bits = 8;
-    int h = radix_sort<uint32_t>(a.ent_seg[0], a.ent_ev[0], a.ent_seg[1], a.ent_ev[1], a.n_entries, bits, a.hist,
+    // 5. stable sort by tile (packed keys) or by segment
+    int h;
+    if (packed) {
+        h = radix_sort<uint32_t>(a.ent_seg[0], a.ent_ev[0], a.ent_seg[1], a.ent_ev[1], a.n_entries, tb, a.hist,
+                                 a.scan_tmp, st, launches, cb);
+    } else {
+        int bits = 0;
+        while ((1ull << bits) < a.n_segments) bits += 8;
+        h = radix_sort<uint32_t>(a.ent_seg[0], a.ent_ev[0], a.ent_seg[1], a.ent_ev[1], a.n_entries, bits, a.hist,
                                  a.scan_tmp, st, launches);
+    }
     o.ent_seg = a.ent_seg[h];
     o.ent_ev = a.ent_ev[h];
     // 6. segment bounds
     cudaMemsetAsync(a.seg_start, 0, sizeof(uint32_t) * a.n_segments, st);
     cudaMemsetAsync(a.seg_end, 0, sizeof(uint32_t) * a.n_segments, st);
     if (a.n_entries) {
-        seg_bounds_kernel<<<blocks_for(a.n_entries, T), T, 0, st>>>(o.ent_seg, a.n_entries, a.seg_start, a.seg_end);
+        seg_bounds_kernel<<<blocks_for(a.n_entries, T), T, 0, st>>>(o.ent_seg, a.n_entries, packed ? cb : -1,
+                                                                     a.n_tiles, a.seg_start, a.seg_end);
         ++*launches;
     }
     // 7. schedule: segments by decreasing length (load balance of the render)
