@@ -41,6 +41,27 @@ def flops_per_triple(M: int) -> int:
     return 113 * M + 604
 
 
+# DRAM bytes of the render kernel per opacity evaluation, from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of the first 4 cells of the
+# 300k-Gaussian workload: 68.6 MB over 117.5M evaluations.  Valid only for the
+# kernel sources it was taken from (their SHA-256 below); otherwise the
+# roofline's traffic is reported as null.
+RENDER_TRAFFIC = {"bytes_per_evaluation": 68600576 / 117536120,
+                  "sources": ["k_render.cuh", "ar_num.cuh", "ar_common.cuh", "k_inst.cuh"],
+                  "sha256": "366f2b4bb4533d70462849c1c4088eb6e03f7b41d4cbab5fe02231feeaa1b6fb"}
+
+
+def render_traffic(n_evaluated: int):
+    import hashlib
+    h = hashlib.sha256()
+    for f in RENDER_TRAFFIC["sources"]:
+        with open(os.path.join(ROOT, "paper_2503_00308_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != RENDER_TRAFFIC["sha256"]:
+        return None
+    return RENDER_TRAFFIC["bytes_per_evaluation"] * n_evaluated
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -350,7 +371,8 @@ def run_ours(args, rank, world, local, pg):
         "e2e": e2e,
         "gpu_launches": int(stats["n_launches"]) * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": render_traffic(stats["n_evaluated"]),
+                     "traffic_unit": "DRAM bytes per render step (all render_kernel launches of the step)",
                      "kernel": "render_kernel", "kernel_ms": r_ms,
                      "flops_per_triple": flops_per_triple(M), "triples_evaluated": stats["n_evaluated"],
                      "triples_in_boxes": stats["n_triples"],
