@@ -169,8 +169,11 @@ void Workspace::release()
 {
     DevBuf *all[] = {&cells_lohi, &cells, &vN, &recs, &boxes, &keys, &counters, &evk0, &evk1, &evv0, &evv1,
                      &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege, &segk0,
-                     &segk1, &segv0, &segv1, &work, &state, &wlist, &act0, &act1, &words, &out_lo, &out_hi};
+                     &segk1, &segv0, &segv1, &work, &state, &wlist, &act0, &act1, &words, &whist, &out_lo, &out_hi};
     for (DevBuf *b : all) b->release();
+    if (h_whist) cudaFreeHost(h_whist);
+    h_whist = nullptr;
+    whist_pending = false;
     if (h_counters) cudaFreeHost(h_counters);
     h_counters = nullptr;
     for (cudaEvent_t e : evs) cudaEventDestroy(e);
@@ -182,7 +185,7 @@ size_t Workspace::bytes() const
     const DevBuf *all[] = {&cells_lohi, &cells, &vN, &recs, &boxes, &keys, &counters, &evk0, &evk1, &evv0, &evv1,
                            &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege,
                            &segk0, &segk1, &segv0, &segv1, &work, &state, &wlist, &act0, &act1, &words,
-                           &out_lo, &out_hi};
+                           &whist, &out_lo, &out_hi};
     size_t s = 0;
     for (const DevBuf *b : all) s += b->cap;
     return s;
@@ -362,6 +365,11 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
     if (profiling) CK(cudaEventRecord(ev[1], st));
     CK(cudaMemcpyAsync(ws.h_counters, ws.counters.p, sizeof(unsigned long long) * 4, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (ws.whist_pending) {
+        // the previous render's histogram arrived with this synchronisation
+        ws.w0 = learned_window(ws.h_whist);
+        ws.whist_pending = false;
+    }
     const unsigned long long n_valid = ws.h_counters[2];
     rs.n_records += (int64_t)n_valid;
     rs.n_triples += (int64_t)ws.h_counters[0];
@@ -452,20 +460,39 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
         RK(ws.act0.ensure(sizeof(uint32_t) * n_seg));
         RK(ws.act1.ensure(sizeof(uint32_t) * n_seg));
         RK(ws.words.ensure(sizeof(uint32_t) * 4));
+        rl.sweep_hist = ws.whist.as<uint32_t>();
         RK(run_windowed_render(M, TS, rl, cc, ws.cells.p, ws.vN.as<double>(), n_pairs, n_seg, ws.state.as<uint32_t>(),
                                ws.wlist.as<uint32_t>(), ws.act0.as<uint32_t>(), ws.act1.as<uint32_t>(),
                                ws.words.as<uint32_t>(), rl.counters + 2, st, &launches,
-                               profiling ? ev + 3 : nullptr));
+                               profiling ? ev + 3 : nullptr, ws.w0));
     }
     return AR_OK;
+}
+
+uint32_t learned_window(const uint32_t *hist256)
+{
+    uint64_t total = 0;
+    for (int b = 0; b < 256; ++b) total += hist256[b];
+    if (total == 0) return 512u;
+    const uint64_t keep = total - total / 200;  // 99.5 %
+    uint64_t run = 0;
+    int b = 0;
+    for (; b < 256; ++b) {
+        run += hist256[b];
+        if (run >= keep) break;
+    }
+    uint32_t w = 32u * (uint32_t)(b + 2);  // the bucket's end plus one chunk of margin
+    if (w < 128u) w = 128u;
+    if (w > 4096u) w = 4096u;
+    return w;
 }
 
 int run_windowed_render(int M, int TS, RenderLaunch rl, const CallConst &cc, const void *cells, const double *vN,
                         uint64_t n_pairs, uint64_t n_seg, uint32_t *state, uint32_t *wlist, uint32_t *act0,
                         uint32_t *act1, uint32_t *words, unsigned long long *build_counters, cudaStream_t st,
-                        int *launches, cudaEvent_t *ev)
+                        int *launches, cudaEvent_t *ev, uint32_t w0)
 {
-    static const uint32_t kWindow[3] = {512u, 8192u, 0xffffffffu};
+    const uint32_t kWindow[3] = {w0, w0 < 8192u ? 8192u : 0xffffffffu, 0xffffffffu};
     uint32_t *act[2] = {act0, act1};
     CK(cudaMemsetAsync(state, 0, sizeof(uint32_t) * n_pairs, st));
     launch_set_u32(words + 1, (uint32_t)n_seg, st);
@@ -565,6 +592,9 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
         CK(cudaStreamSynchronize(st));  // the host vector is released on return
     }
     const double *d_lo = ws.cells_lohi.as<double>(), *d_hi = d_lo + (size_t)MAXV * n_cells;
+    RK(ws.whist.ensure(sizeof(uint32_t) * 256));
+    if (!ws.h_whist) CK(cudaMallocHost(&ws.h_whist, sizeof(uint32_t) * 256));
+    CK(cudaMemsetAsync(ws.whist.p, 0, sizeof(uint32_t) * 256, st));
     CK(cudaMemsetAsync(ws.counters.as<unsigned long long>() + 8, 0, sizeof(unsigned long long) * 5 * n_batches, st));
     int launches = 0;
     if (launch_pose_prep(s->uw, s->Mw, s->n, cc, ws.vN.as<double>(), st)) return fail(AR_EDEVICE, "pose_prep launch");
@@ -577,6 +607,11 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
         const size_t off = (size_t)c0 * W * H * 3;
         RK(render_batch(s, ws, cb, M, TS, d_lo + (size_t)MAXV * c0, d_hi + (size_t)MAXV * c0, out_lo + off,
                         out_hi + off, st, profiling, b, rs, launches, plain));
+    }
+    if (!plain) {
+        // for the next render's first window (read after its first synchronisation)
+        CK(cudaMemcpyAsync(ws.h_whist, ws.whist.p, sizeof(uint32_t) * 256, cudaMemcpyDeviceToHost, st));
+        ws.whist_pending = true;
     }
     ws.n_batches = n_batches;
     ws.fallback_prep = rs.n_fallback;

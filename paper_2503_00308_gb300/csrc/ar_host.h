@@ -27,6 +27,10 @@ struct Workspace {
     DevBuf evk0, evk1, evv0, evv1, ents0, ents1, ente0, ente1;
     DevBuf ua, ub, uc, ud, hist, scan, segs, sege, segk0, segk1, segv0, segv1, work;
     DevBuf state, wlist, act0, act1, words;  // windowed rounds: pair states, build list, active segments
+    DevBuf whist;                            // [256] sweep-length histogram of the current render
+    uint32_t *h_whist = nullptr;             // page-locked copy of the last render's histogram
+    bool whist_pending = false;              // h_whist holds a render not yet learned from
+    uint32_t w0 = 512;                       // first window of the windowed rounds
     DevBuf out_lo, out_hi;
     unsigned long long *h_counters = nullptr;  // page-locked
     std::vector<cudaEvent_t> evs;              // 9 per cell batch (stage timing)
@@ -44,13 +48,16 @@ int validate_call(const ar_intrinsics *in, const ar_nominal_pose *pose, const ar
 struct RenderLaunch;
 struct CallConst;
 // The FP32 render of one batch in windowed rounds (see render_kernel):
-// demand -> build -> render per round, windows 512, 8192, then unlimited.
+// demand -> build -> render per round, windows w0, 8192, then unlimited.
 // state [n_pairs] (zeroed here), wlist [n_pairs], act0/act1 [n_seg], words [4];
 // build_counters: [0] fallbacks, [1] records built (optional).
 int run_windowed_render(int M, int TS, RenderLaunch rl, const CallConst &cc, const void *cells, const double *vN,
                         uint64_t n_pairs, uint64_t n_seg, uint32_t *state, uint32_t *wlist, uint32_t *act0,
                         uint32_t *act1, uint32_t *words, unsigned long long *build_counters, cudaStream_t st,
-                        int *launches, cudaEvent_t *ev = nullptr);
+                        int *launches, cudaEvent_t *ev = nullptr, uint32_t w0 = 512u);
+// First window from the sweep histogram of an earlier render: the smallest
+// multiple of 32 entries that covers 99.5 % of its segments, in [128, 4096].
+uint32_t learned_window(const uint32_t *hist256);
 int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_nominal_pose *pose,
                 const ar_pose_box *cells, int32_t n_cells, int32_t tile, float *out_lo, float *out_hi,
                 cudaStream_t st, bool profiling, ar_render_stats *stats, bool plain = false,

@@ -19,6 +19,7 @@ struct RenderLaunch {
     const uint32_t *active = nullptr, *n_active = nullptr;
     uint32_t *next_active = nullptr, *n_next = nullptr;
     uint32_t window = 0xffffffffu;
+    uint32_t *sweep_hist = nullptr;   // optional [256]: completed segments by entries swept / 32
     const uint64_t *ev_key;
     int W, H, ntx, n_tiles, n_cells;
     int64_t n_gauss;

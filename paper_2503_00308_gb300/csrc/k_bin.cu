@@ -306,24 +306,55 @@ __device__ __forceinline__ uint32_t entry_segment(uint32_t key, int cb, int n_ti
     return cb >= 0 ? (key & ((1u << cb) - 1u)) * (uint32_t)n_tiles + (key >> cb) : key;
 }
 
+// Each warp owns 32 consecutive events, whose entries form one contiguous
+// range of the output (off is their exclusive scan).  The lanes stride over
+// that range, so every store instruction writes 32 consecutive words; each
+// lane finds the event of its entry by a binary search over the warp's 32
+// offsets (shuffles).  Launch with a multiple of 32 threads per block.
 __global__ void emit_entries_kernel(const uint32_t *__restrict__ ev_val, uint64_t ne,
                                     const PixBox *__restrict__ boxes, int TS, int ntx, int n_tiles, int cb,
                                     uint64_t n_gauss, const uint32_t *__restrict__ off,
                                     uint32_t *__restrict__ ent_seg, uint32_t *__restrict__ ent_ev)
 {
-    const uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    if (e >= ne) return;
-    const uint32_t ri = ev_val[e] >> 1;
-    const uint32_t cell = (uint32_t)(ri / n_gauss);
-    int tx0, tx1, ty0, ty1;
-    tile_rect(boxes[ri], TS, tx0, tx1, ty0, ty1);
-    uint32_t o = off[e];
-    for (int ty = ty0; ty <= ty1; ++ty)
-        for (int tx = tx0; tx <= tx1; ++tx) {
-            ent_seg[o] = entry_key(cell, (uint32_t)(ty * ntx + tx), cb, n_tiles);
-            ent_ev[o] = (uint32_t)e;
-            ++o;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const uint64_t e0 = ((blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5) * 32u;
+    if (e0 >= ne) return;  // uniform across the warp
+    const uint64_t e = e0 + (uint64_t)lane;
+    uint32_t myoff = 0xffffffffu, myend = 0, cell = 0;
+    int tx0 = 0, ty0 = 0, tw = 1;
+    if (e < ne) {
+        const uint32_t ri = ev_val[e] >> 1;
+        cell = (uint32_t)(ri / n_gauss);
+        int tx1, ty1;
+        tile_rect(boxes[ri], TS, tx0, tx1, ty0, ty1);
+        tw = tx1 - tx0 + 1;
+        myoff = off[e];
+        myend = myoff + (uint32_t)(tw * (ty1 - ty0 + 1));
+    }
+    const uint32_t start = __shfl_sync(full, myoff, 0);
+    uint32_t end = myend;
+#pragma unroll
+    for (int d = 16; d; d >>= 1) end = max(end, __shfl_xor_sync(full, end, d));
+    for (uint32_t b = start; b < end; b += 32u) {
+        const uint32_t o = b + (uint32_t)lane;
+        int j = 0;  // last lane whose offset is <= o (offsets ascend; idle lanes hold ~0)
+#pragma unroll
+        for (int step = 16; step; step >>= 1) {
+            const int cand = j + step;
+            const uint32_t oc = __shfl_sync(full, myoff, cand & 31);
+            if (cand < 32 && oc <= o) j = cand;
         }
+        const uint32_t oj = __shfl_sync(full, myoff, j);
+        const uint32_t cj = __shfl_sync(full, cell, j);
+        const int x0 = __shfl_sync(full, tx0, j), y0 = __shfl_sync(full, ty0, j), w = __shfl_sync(full, tw, j);
+        if (o < end) {
+            const uint32_t k = o - oj;
+            const uint32_t ty = (uint32_t)y0 + k / (uint32_t)w, tx = (uint32_t)x0 + k % (uint32_t)w;
+            ent_seg[o] = entry_key(cj, ty * (uint32_t)ntx + tx, cb, n_tiles);
+            ent_ev[o] = (uint32_t)(e0 + (uint64_t)j);
+        }
+    }
 }
 
 // key = ~length so that an ascending stable sort puts the longest first

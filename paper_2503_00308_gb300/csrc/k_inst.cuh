@@ -78,7 +78,7 @@ static int launch_render_ts(const RenderLaunch &a, cudaStream_t st)
     if (grid > nseg) grid = nseg;
     if (cudaMemsetAsync(a.work, 0, sizeof(unsigned int), st) != cudaSuccess) return 1;
     kern<<<grid, TS * TS, SM::BYTES, st>>>(a.recs, a.boxes, a.seg_start, a.seg_end, a.active, a.n_active, a.window,
-                                           a.next_active, a.n_next, a.ent_ev, a.ev_val,
+                                           a.next_active, a.n_next, a.sweep_hist, a.ent_ev, a.ev_val,
                                            a.ev_key, a.W, a.H, a.ntx, a.n_tiles, a.n_gauss, a.k_open, a.out_lo,
                                            a.out_hi, a.counters, a.work);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;

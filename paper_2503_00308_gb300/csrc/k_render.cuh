@@ -309,6 +309,7 @@ __global__ void __launch_bounds__(TS *TS, 1) render_kernel(
     const float *__restrict__ recs, const PixBox *__restrict__ boxes, const uint32_t *__restrict__ seg_start,
     const uint32_t *__restrict__ seg_end, const uint32_t *__restrict__ active, const uint32_t *__restrict__ n_active,
     uint32_t window, uint32_t *__restrict__ next_active, uint32_t *__restrict__ n_next,
+    uint32_t *__restrict__ sweep_hist,
     const uint32_t *__restrict__ entry_ev, const uint32_t *__restrict__ ev_val,
     const uint64_t *__restrict__ ev_key, int W, int H, int ntx, int n_tiles, int64_t n_gauss,
     float k_open, float *__restrict__ out_lo, float *__restrict__ out_hi,
@@ -360,6 +361,7 @@ __global__ void __launch_bounds__(TS *TS, 1) render_kernel(
         bool done = !inside;
         float lo_adj = 0.f, hi_adj = 0.f;  // -1: decided 0 / 1; >= 0: widening for skipped events
         bool abandoned = false;
+        uint32_t swept = b1 - b0;  // entries swept before the tile stopped
         uint32_t seg_evals = 0, seg_recomp = 0;
 
         for (uint32_t base = b0; base < b1; base += CH) {
@@ -383,7 +385,10 @@ __global__ void __launch_bounds__(TS *TS, 1) render_kernel(
                     hi_adj = hi_one ? -1.f : ehi2;
                 }
             }
-            if (__syncthreads_and(done)) break;
+            if (__syncthreads_and(done)) {
+                swept = base - b0;
+                break;
+            }
             if (base + (uint32_t)cnt - b0 > window) {  // records beyond the window are not built
                 abandoned = true;
                 break;
@@ -476,6 +481,7 @@ __global__ void __launch_bounds__(TS *TS, 1) render_kernel(
             }
             continue;
         }
+        if (sweep_hist && tid == 0) atomicAdd(&sweep_hist[min(swept / 32u, 255u)], 1u);
         evals += seg_evals;
         recomp += seg_recomp;
         if (inside) {
