@@ -21,39 +21,41 @@ constexpr int MAXV = 6;  // pose variables tx ty tz rx ry rz
 // Per-call pose-cell data produced by the cell kernel.
 //   FP64 part (decision chain): forms over the M active variables, computed
 //   round-to-nearest in the order the CPU reference uses.
-//   FP32 part (value chain): the same forms widened outward to float.
+//   FP64 value-chain copies: the same forms widened to be sound in FP64.
 template <int M> struct CellData {
     double rd_lo[9][M + 1], rd_hi[9][M + 1];  // R_delta entries (coefficients, then constant)
     double s[3][M + 1];                       // s = R_wc * delta_t (exact)
     double g[M];                              // depth-key offset (translation part of d)
     double rd_int[9][2];                      // concretised R_delta entries
     double s_int[3][2];                       // concretised s
-    BS<M, float> rd32[9];
-    BS<M, float> s32[3];
-    BS<M, double> rd64[9];  // the same forms widened by a relative 1e-14 (sound in FP64)
-    BS<M, double> s64[3];
+    SB<M, double> rd64[9];  // the same forms widened by a relative 1e-14 (sound in FP64)
+    SB<M, double> s64[3];
 };
 
-// Per-(Gaussian, cell) record read by the per-pixel kernel.  Offsets in
-// floats; F = M + 1 is the length of one form.
+// Per-(Gaussian, cell) record read by the per-pixel kernel, in elements of
+// the record precision (float for the batched renderer, double for the plain
+// one).  A bounded scalar with shared coefficients is stored as c[M], klo,
+// khi, r (SB), the W entries also with their concretisation vlo, vhi.
 //
 // Delta = S u - P (Algorithm 1 line 9 with S = d^2, P = d up) is stored as
 //   Delta.lo = (u - mu) S.lo + R.lo,  R.lo = mu S.lo - P.hi,
 //   Delta.hi = (u - mu) S.hi + R.hi,  R.hi = mu S.hi - P.lo,
 // with mu a pixel centre near the projected mean: algebraically the same
-// forms as u S.lo - P.hi and u S.hi - P.lo, but the large, nearly cancelling
-// terms S u and P are combined once in FP64 instead of per pixel in FP32.
+// forms as u S.lo - P.hi and u S.hi - P.lo (sound because u > 0), but the
+// large, nearly cancelling terms S u and P are combined once in FP64 instead
+// of per pixel.  GAP_S bounds, over the cell, how far the stored S forms lie
+// outside the FP64 ones R was formed from (their outward conversion); where
+// u - mu < 0 the pixel stage widens Delta by |u - mu| GAP_S.
 template <int M> struct Rec {
-    static constexpr int F = M + 1;
-    static constexpr int S_LO = 0, S_HI = F, RX_LO = 2 * F, RX_HI = 3 * F, RY_LO = 4 * F, RY_HI = 5 * F;
-    static constexpr int RAD = 6 * F;          // radii of S.lo, S.hi, Rx.lo, Rx.hi, Ry.lo, Ry.hi
-    static constexpr int WSTRIDE = 2 * F + 4;  // lo form, hi form, vlo, vhi, rlo, rhi
-    static constexpr int W0 = RAD + 6;
-    static constexpr int SC = W0 + 6 * WSTRIDE;  // o, tau_dn, tau_up, c0, c1, c2, flags, mu_x, mu_y
+    static constexpr int SBW = M + 3;            // c[M], klo, khi, r
+    static constexpr int S = 0, RX = SBW, RY = 2 * SBW;
+    static constexpr int WS = M + 5;             // c[M], klo, khi, vlo, vhi, r
+    static constexpr int W0 = 3 * SBW;           // W_rc at W0 + (3 r + c) WS
+    static constexpr int SC = W0 + 6 * WS;       // o, tau_dn, tau_up, c0, c1, c2, flags, mu_x, mu_y, gap_s
     static constexpr int O = SC, TAU_DN = SC + 1, TAU_UP = SC + 2, COL = SC + 3, FLAGS = SC + 6;
-    static constexpr int MU_X = SC + 7, MU_Y = SC + 8;
-    static constexpr int RAW = SC + 9;
-    static constexpr int WIDTH = (RAW + 3) / 4 * 4;  // 16-byte multiple
+    static constexpr int MU_X = SC + 7, MU_Y = SC + 8, GAP_S = SC + 9;
+    static constexpr int RAW = SC + 10;
+    static constexpr int WIDTH = (RAW + 3) / 4 * 4;  // 16-byte multiple (float)
 };
 
 // record flags

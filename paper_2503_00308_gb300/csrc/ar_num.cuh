@@ -153,6 +153,17 @@ template <int M, class R, bool DN> struct Acc {
         f.k = DN ? N::add_rd(f.k, b) : N::add_ru(f.k, b);
     }
     __device__ __forceinline__ void add_slack(R s) { ex = Num<R>::add_ru(ex, s); }
+    // add a * (Fc . p + Fk) where the form has radius r (the caller has
+    // chosen the side of the form)
+    __device__ __forceinline__ void term_ck(R a, const R *Fc, R Fk, R r)
+    {
+        using N = Num<R>;
+#pragma unroll
+        for (int j = 0; j < M; ++j) f.c[j] = N::fma_rn(a, Fc[j], f.c[j]);
+        f.k = DN ? N::fma_rd(a, Fk, f.k) : N::fma_ru(a, Fk, f.k);
+        rs = N::fma_ru(N::abs(a), r, rs);
+        ++n;
+    }
     // add a * F where F has radius r (the caller has chosen the side of F)
     __device__ __forceinline__ void term(R a, const LF<M, R> &F, R r)
     {
@@ -224,6 +235,155 @@ template <int M, class R> struct Pair {
         hi.add_const(N::max(N::fma_ru(xl, xl, N::mul_ru(-s, xl)), N::fma_ru(xh, xh, N::mul_ru(-s, xh))));
     }
 };
+
+// ---------------------------------------------------------------------------
+// Bounded scalars with shared coefficients.  Every operation of the value
+// chain gives the lower and the upper form the same coefficients: the pose
+// forms differ only in their constants (Taylor remainder), the McCormick
+// planes of a product share their slopes (y_m x + x_m y), the tangent and
+// secant of a square share the slope x_lo + x_hi, and linear maps act on both
+// alike.  So the pair is held as lo(p) = c.p + klo, hi(p) = c.p + khi with one
+// coefficient vector, computed once; r = sum |c| (rounded up), and the
+// concretisation is vlo = klo - r, vhi = khi + r.
+template <int M, class R> struct SB {
+    R c[M];
+    R klo, khi;
+    R r;
+    R vlo, vhi;
+};
+
+template <int M, class R>
+__device__ __forceinline__ void sb_finish(SB<M, R> &b)
+{
+    using N = Num<R>;
+    R r = 0;
+#pragma unroll
+    for (int j = 0; j < M; ++j) r = N::add_ru(r, N::abs(b.c[j]));
+    b.r = r;
+    b.vlo = N::sub_rd(b.klo, r);
+    b.vhi = N::add_ru(b.khi, r);
+}
+
+template <int M, class R>
+__device__ __forceinline__ SB<M, R> sb_cst(R lo, R hi)
+{
+    SB<M, R> b;
+#pragma unroll
+    for (int j = 0; j < M; ++j) b.c[j] = 0;
+    b.klo = lo; b.khi = hi; b.r = 0; b.vlo = lo; b.vhi = hi;
+    return b;
+}
+
+// Accumulator of sum_t a_t X_t + b for both sides at once.  Coefficients are
+// summed round-to-nearest; their worst-case error summed over the box,
+// gamma_n sum_t |a_t| r_t, and any extra slack move into the constants, which
+// are themselves rounded outward (see Acc).
+template <int M, class R> struct SAcc {
+    R c[M];
+    R klo, khi;
+    R rs;   // sum_t |a_t| r_t
+    R ex;   // extra absolute slack
+    int n;
+
+    __device__ __forceinline__ void init(R blo, R bhi)
+    {
+#pragma unroll
+        for (int j = 0; j < M; ++j) c[j] = 0;
+        klo = blo; khi = bhi; rs = 0; ex = 0; n = 0;
+    }
+    __device__ __forceinline__ void add_const(R dlo, R dhi)
+    {
+        using N = Num<R>;
+        klo = N::add_rd(klo, dlo);
+        khi = N::add_ru(khi, dhi);
+    }
+    __device__ __forceinline__ void add_slack(R s) { ex = Num<R>::add_ru(ex, s); }
+    // + a x, the side of x chosen by the sign of a
+    __device__ __forceinline__ void term(R a, const SB<M, R> &x)
+    {
+        using N = Num<R>;
+#pragma unroll
+        for (int j = 0; j < M; ++j) c[j] = N::fma_rn(a, x.c[j], c[j]);
+        if (a >= 0) {
+            klo = N::fma_rd(a, x.klo, klo);
+            khi = N::fma_ru(a, x.khi, khi);
+        } else {
+            klo = N::fma_rd(a, x.khi, klo);
+            khi = N::fma_ru(a, x.klo, khi);
+        }
+        rs = N::fma_ru(N::abs(a), x.r, rs);
+        ++n;
+    }
+    // + a x with x's lower form in the lower sum and its upper form in the
+    // upper sum whatever the sign of a (only where an exact identity with
+    // another term makes the pair sound, e.g. (u - mu) S + (mu S - P))
+    __device__ __forceinline__ void term_same_side(R a, const SB<M, R> &x)
+    {
+        using N = Num<R>;
+#pragma unroll
+        for (int j = 0; j < M; ++j) c[j] = N::fma_rn(a, x.c[j], c[j]);
+        klo = N::fma_rd(a, x.klo, klo);
+        khi = N::fma_ru(a, x.khi, khi);
+        rs = N::fma_ru(N::abs(a), x.r, rs);
+        ++n;
+    }
+    // + x * y  (averaged McCormick planes)
+    __device__ __forceinline__ void mul(const SB<M, R> &x, const SB<M, R> &y)
+    {
+        using N = Num<R>;
+        const R xl = x.vlo, xh = x.vhi, yl = y.vlo, yh = y.vhi;
+        const R xm = N::mul_rn(xl + xh, (R)0.5), ym = N::mul_rn(yl + yh, (R)0.5);
+        term(ym, x);
+        term(xm, y);
+        // constants: -(xl yl + xh yh)/2 below, -(xh yl + xl yh)/2 above
+        add_const(-N::mul_ru(N::fma_ru(xl, yl, N::mul_ru(xh, yh)), (R)0.5),
+                  -N::mul_rd(N::fma_rd(xh, yl, N::mul_rd(xl, yh)), (R)0.5));
+        // the slopes are the rounded midpoints: cover |ym - y_mid| max|x| + ...
+        const R xa = N::max(N::abs(xl), N::abs(xh)), ya = N::max(N::abs(yl), N::abs(yh));
+        add_slack(N::mul_ru(N::fma_ru(N::abs(ym), xa, N::mul_ru(N::abs(xm), ya)), N::mul_ru(N::U, (R)1.001)));
+    }
+    // + x^2  (tangent at the midpoint c below, secant above; both have slope
+    // x_lo + x_hi = 2c)
+    __device__ __forceinline__ void sqr(const SB<M, R> &x)
+    {
+        using N = Num<R>;
+        const R xl = x.vlo, xh = x.vhi;
+        const R s = xl + xh;
+        const R c = N::mul_rn(s, (R)0.5);
+        term(s, x);
+        add_const(-N::mul_ru(c, c), N::max(N::fma_ru(xl, xl, N::mul_ru(-s, xl)), N::fma_ru(xh, xh, N::mul_ru(-s, xh))));
+    }
+    __device__ __forceinline__ SB<M, R> result() const
+    {
+        using N = Num<R>;
+        // gamma_n = n u (1 + 2^-12) covers (1 + u)^n for n < 2^10
+        const R g = N::mul_ru((R)n, N::mul_ru(N::U, (R)1.000244140625));
+        const R sl = N::add_ru(N::fma_ru(g, rs, ex), N::TINY);
+        SB<M, R> b;
+#pragma unroll
+        for (int j = 0; j < M; ++j) b.c[j] = c[j];
+        b.klo = N::sub_rd(klo, sl);
+        b.khi = N::add_ru(khi, sl);
+        sb_finish(b);
+        return b;
+    }
+};
+
+template <int M, class R>
+__device__ __forceinline__ SB<M, R> sb_mul(const SB<M, R> &x, const SB<M, R> &y)
+{
+    SAcc<M, R> p; p.init(0, 0); p.mul(x, y); return p.result();
+}
+template <int M, class R>
+__device__ __forceinline__ SB<M, R> sb_sqr(const SB<M, R> &x)
+{
+    SAcc<M, R> p; p.init(0, 0); p.sqr(x); return p.result();
+}
+template <int M, class R>
+__device__ __forceinline__ SB<M, R> sb_add(const SB<M, R> &x, const SB<M, R> &y)
+{
+    SAcc<M, R> p; p.init(0, 0); p.term((R)1, x); p.term((R)1, y); return p.result();
+}
 
 template <int M, class R>
 __device__ __forceinline__ BS<M, R> b_mul(const BS<M, R> &x, const BS<M, R> &y)

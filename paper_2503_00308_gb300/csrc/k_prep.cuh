@@ -64,22 +64,6 @@ __device__ __forceinline__ void rot3(int axis, double a, double R[9], double D[9
     }
 }
 
-// FP64 form -> outward FP32 form
-template <int M>
-__device__ __forceinline__ void to_f32(const double *lo, const double *hi, BS<M, float> &b)
-{
-    double el = 0, eh = 0;
-    for (int j = 0; j < M; ++j) {
-        b.lo.c[j] = (float)lo[j];
-        b.hi.c[j] = (float)hi[j];
-        el = __dadd_ru(el, fabs(lo[j] - (double)b.lo.c[j]));
-        eh = __dadd_ru(eh, fabs(hi[j] - (double)b.hi.c[j]));
-    }
-    b.lo.k = __double2float_rd(__dsub_rd(lo[M], el));
-    b.hi.k = __double2float_ru(__dadd_ru(hi[M], eh));
-    finish(b);
-}
-
 // One thread per cell.
 template <int M>
 __global__ void cell_prep_kernel(const double *__restrict__ cells_lo, const double *__restrict__ cells_hi,
@@ -137,7 +121,6 @@ __global__ void cell_prep_kernel(const double *__restrict__ cells_lo, const doub
         lo.k = cd.rd_lo[e][M]; hi.k = cd.rd_hi[e][M];
         cd.rd_int[e][0] = df_min(lo);
         cd.rd_int[e][1] = df_max(hi);
-        to_f32<M>(cd.rd_lo[e], cd.rd_hi[e], cd.rd32[e]);
     }
     for (int a = 0; a < 3; ++a) {
         DF<M> f;
@@ -145,53 +128,64 @@ __global__ void cell_prep_kernel(const double *__restrict__ cells_lo, const doub
         f.k = cd.s[a][M];
         cd.s_int[a][0] = df_min(f);
         cd.s_int[a][1] = df_max(f);
-        to_f32<M>(cd.s[a], cd.s[a], cd.s32[a]);
     }
     // FP64 value-chain copies, widened to cover the rounding of sin, cos and
-    // the Taylor terms (a relative 1e-14 is far above their few-ulp error)
+    // the Taylor terms (a relative 1e-14 is far above their few-ulp error);
+    // the lower and upper forms share their coefficients
     for (int e = 0; e < 12; ++e) {
         const double *lo = e < 9 ? cd.rd_lo[e] : cd.s[e - 9];
         const double *hi = e < 9 ? cd.rd_hi[e] : cd.s[e - 9];
-        BS<M, double> &b = e < 9 ? cd.rd64[e] : cd.s64[e - 9];
+        SB<M, double> &b = e < 9 ? cd.rd64[e] : cd.s64[e - 9];
         double mag = 1.0;
         for (int j = 0; j <= M; ++j) mag = __dadd_ru(mag, fmax(fabs(lo[j]), fabs(hi[j])));
         const double pad = __dmul_ru(1e-14, mag);
-        for (int j = 0; j < M; ++j) { b.lo.c[j] = lo[j]; b.hi.c[j] = hi[j]; }
-        b.lo.k = __dsub_rd(lo[M], pad);
-        b.hi.k = __dadd_ru(hi[M], pad);
-        finish(b);
+        for (int j = 0; j < M; ++j) b.c[j] = lo[j];
+        b.klo = __dsub_rd(lo[M], pad);
+        b.khi = __dadd_ru(hi[M], pad);
+        sb_finish(b);
     }
 }
 
 // FP32 form -> FP64 (exact); an FP64 form passes through
 template <int M>
-__device__ __forceinline__ const BS<M, double> &to_f64(const BS<M, double> &b) { return b; }
+__device__ __forceinline__ const SB<M, double> &to_f64(const SB<M, double> &b) { return b; }
 template <int M>
-__device__ __forceinline__ BS<M, double> to_f64(const BS<M, float> &b)
+__device__ __forceinline__ SB<M, double> to_f64(const SB<M, float> &b)
 {
-    BS<M, double> d;
-    for (int j = 0; j < M; ++j) { d.lo.c[j] = b.lo.c[j]; d.hi.c[j] = b.hi.c[j]; }
-    d.lo.k = b.lo.k; d.hi.k = b.hi.k;
-    finish(d);
+    SB<M, double> d;
+    for (int j = 0; j < M; ++j) d.c[j] = b.c[j];
+    d.klo = b.klo;
+    d.khi = b.khi;
+    sb_finish(d);
     return d;
 }
 
-// FP64 sound form -> outward FP32 form
+// FP64 sound form -> outward FP32 form: coefficients rounded to nearest,
+// their error over the box moved into the outward-rounded constants.  Returns
+// a bound, over the box, of how far either FP32 form lies outside the FP64
+// one (the conversion gap).
 template <int M>
-__device__ __forceinline__ void bs_to_f32(const BS<M, double> &d, BS<M, float> &b)
+__device__ __forceinline__ double sb_to_f32(const SB<M, double> &d, SB<M, float> &b)
 {
-    double lo[M + 1], hi[M + 1];
-    for (int j = 0; j <= M; ++j) {
-        lo[j] = j < M ? d.lo.c[j] : d.lo.k;
-        hi[j] = j < M ? d.hi.c[j] : d.hi.k;
+    double e = 0;
+    for (int j = 0; j < M; ++j) {
+        b.c[j] = (float)d.c[j];
+        e = __dadd_ru(e, fabs(d.c[j] - (double)b.c[j]));
     }
-    to_f32<M>(lo, hi, b);
+    b.klo = __double2float_rd(__dsub_rd(d.klo, e));
+    b.khi = __double2float_ru(__dadd_ru(d.khi, e));
+    sb_finish(b);
+    return __dadd_ru(e, fmax(__dsub_ru(d.klo, (double)b.klo), __dsub_ru((double)b.khi, d.khi)));
 }
 // FP64 sound form -> record precision (FP32 outward, or FP64 as it is)
 template <int M>
-__device__ __forceinline__ void bs_to_rec(const BS<M, double> &d, BS<M, float> &b) { bs_to_f32<M>(d, b); }
+__device__ __forceinline__ double sb_to_rec(const SB<M, double> &d, SB<M, float> &b) { return sb_to_f32<M>(d, b); }
 template <int M>
-__device__ __forceinline__ void bs_to_rec(const BS<M, double> &d, BS<M, double> &b) { b = d; }
+__device__ __forceinline__ double sb_to_rec(const SB<M, double> &d, SB<M, double> &b)
+{
+    b = d;
+    return 0.0;
+}
 
 // scalars in the record precision, rounded down / up
 __device__ __forceinline__ void rec_dn(double x, float &y) { y = __double2float_rd(x); }
@@ -203,19 +197,33 @@ __device__ __forceinline__ void rec_put_flags(float *dst, uint32_t f) { *dst = _
 __device__ __forceinline__ void rec_put_flags(double *dst, uint32_t f) { *dst = (double)f; }
 
 // ------------------------------------------------------------- records
+// c[M], klo, khi, r (the S and R entries of a record)
 template <int M, class R>
-__device__ __forceinline__ void store_form(R *dst, const LF<M, R> &f)
+__device__ __forceinline__ void store_sb(R *dst, const SB<M, R> &b)
 {
 #pragma unroll
-    for (int j = 0; j < M; ++j) dst[j] = f.c[j];
-    dst[M] = f.k;
+    for (int j = 0; j < M; ++j) dst[j] = b.c[j];
+    dst[M] = b.klo;
+    dst[M + 1] = b.khi;
+    dst[M + 2] = b.r;
+}
+// c[M], klo, khi, vlo, vhi, r (the W entries)
+template <int M, class R>
+__device__ __forceinline__ void store_sbw(R *dst, const SB<M, R> &b)
+{
+#pragma unroll
+    for (int j = 0; j < M; ++j) dst[j] = b.c[j];
+    dst[M] = b.klo;
+    dst[M + 1] = b.khi;
+    dst[M + 2] = b.vlo;
+    dst[M + 3] = b.vhi;
+    dst[M + 4] = b.r;
 }
 
 template <int M, class R>
-__device__ __forceinline__ bool bs_finite(const BS<M, R> &b)
+__device__ __forceinline__ bool sb_finite(const SB<M, R> &b)
 {
-    return isfinite(b.vlo) && isfinite(b.vhi) && isfinite(b.lo.k) && isfinite(b.hi.k) && isfinite(b.rlo) &&
-           isfinite(b.rhi);
+    return isfinite(b.vlo) && isfinite(b.vhi) && isfinite(b.klo) && isfinite(b.khi) && isfinite(b.r);
 }
 
 struct PrepCount {
@@ -349,10 +357,11 @@ __device__ __forceinline__ uint32_t record_value(const double *__restrict__ v, f
 {
     using RL = Rec<M>;
     using NO = Num<RO>;
-    typedef BS<M, RO> B;
+    typedef SB<M, RO> B;
+    typedef SB<M, double> BD;
+    typedef SAcc<M, double> AD;
     const double *N = v + 3;
     bool ok = true;
-    typedef BS<M, double> BD;
     // ---- FP64 value chain (directed rounding): uc, S, P, Mc, J, Mp, X, E.
     // These are differences of large, nearly equal terms (S u - P, I - X X0,
     // Conic Mp); carrying them in FP64 keeps their FP32 images accurate.
@@ -363,13 +372,13 @@ __device__ __forceinline__ uint32_t record_value(const double *__restrict__ v, f
         const double ev = __dmul_ru(1e-14, vabs);
         BD vm[3];
         for (int b = 0; b < 3; ++b) {
-            Pair<M, double> p;
+            AD p;
             p.init(__dsub_rd(v[b], ev), __dadd_ru(v[b], ev));
-            p.lin(-1.0, cd.s64[b]);
+            p.term(-1.0, cd.s64[b]);
             vm[b] = p.result();
         }
         for (int a = 0; a < 3; ++a) {
-            Pair<M, double> p;
+            AD p;
             p.init(0.0, 0.0);
             p.mul(cd.rd64[a], vm[0]);
             p.mul(cd.rd64[3 + a], vm[1]);
@@ -382,65 +391,56 @@ __device__ __forceinline__ uint32_t record_value(const double *__restrict__ v, f
         // S = d^2 and P = d up folded into R = mu S - P around a pixel centre
         // mu near the projected mean (see Rec)
         BD u0, u1;
-        Pair<M, double> p;
-        p.init(0.0, 0.0); p.lin((double)fx, uc64[0]); p.lin((double)cx, uc64[2]); u0 = p.result();
-        p.init(0.0, 0.0); p.lin((double)fy, uc64[1]); p.lin((double)cy, uc64[2]); u1 = p.result();
-        const BD S = b_sqr<M, double>(d64);
-        const BD Px = b_mul<M, double>(d64, u0);
-        const BD Py = b_mul<M, double>(d64, u1);
+        AD p;
+        p.init(0.0, 0.0); p.term((double)fx, uc64[0]); p.term((double)cx, uc64[2]); u0 = p.result();
+        p.init(0.0, 0.0); p.term((double)fy, uc64[1]); p.term((double)cy, uc64[2]); u1 = p.result();
+        const BD S = sb_sqr<M, double>(d64);
+        const BD Px = sb_mul<M, double>(d64, u0);
+        const BD Py = sb_mul<M, double>(d64, u1);
         BD Rx, Ry;
-        {
-            Acc<M, double, true> lo;
-            Acc<M, double, false> hi;
-            lo.init(0.0); lo.term((double)mux, S.lo, S.rlo); lo.term(-1.0, Px.hi, Px.rhi);
-            hi.init(0.0); hi.term((double)mux, S.hi, S.rhi); hi.term(-1.0, Px.lo, Px.rlo);
-            Rx.lo = lo.result(); Rx.hi = hi.result(); finish(Rx);
-            lo.init(0.0); lo.term((double)muy, S.lo, S.rlo); lo.term(-1.0, Py.hi, Py.rhi);
-            hi.init(0.0); hi.term((double)muy, S.hi, S.rhi); hi.term(-1.0, Py.lo, Py.rlo);
-            Ry.lo = lo.result(); Ry.hi = hi.result(); finish(Ry);
-        }
+        p.init(0.0, 0.0); p.term_same_side((double)mux, S); p.term(-1.0, Px); Rx = p.result();
+        p.init(0.0, 0.0); p.term_same_side((double)muy, S); p.term(-1.0, Py); Ry = p.result();
         B S32, Rx32, Ry32;
-        bs_to_rec<M>(S, S32);
-        bs_to_rec<M>(Rx, Rx32);
-        bs_to_rec<M>(Ry, Ry32);
-        ok = ok && bs_finite(S32) && bs_finite(Rx32) && bs_finite(Ry32);
-        store_form<M>(rec + RL::S_LO, S32.lo); store_form<M>(rec + RL::S_HI, S32.hi);
-        store_form<M>(rec + RL::RX_LO, Rx32.lo); store_form<M>(rec + RL::RX_HI, Rx32.hi);
-        store_form<M>(rec + RL::RY_LO, Ry32.lo); store_form<M>(rec + RL::RY_HI, Ry32.hi);
-        rec[RL::RAD + 0] = S32.rlo; rec[RL::RAD + 1] = S32.rhi;
-        rec[RL::RAD + 2] = Rx32.rlo; rec[RL::RAD + 3] = Rx32.rhi;
-        rec[RL::RAD + 4] = Ry32.rlo; rec[RL::RAD + 5] = Ry32.rhi;
+        const double gap = sb_to_rec<M>(S, S32);
+        sb_to_rec<M>(Rx, Rx32);
+        sb_to_rec<M>(Ry, Ry32);
+        ok = ok && sb_finite(S32) && sb_finite(Rx32) && sb_finite(Ry32);
+        store_sb<M>(rec + RL::S, S32);
+        store_sb<M>(rec + RL::RX, Rx32);
+        store_sb<M>(rec + RL::RY, Ry32);
+        rec_up(gap, rec[RL::GAP_S]);
     }
     BD Mp64[6];
     {
         BD Mc[9];
         for (int a = 0; a < 3; ++a)
             for (int c = 0; c < 3; ++c) {
-                Pair<M, double> p;
+                AD p;
                 p.init(0.0, 0.0);
-                p.lin(N[c], cd.rd64[a]);
-                p.lin(N[3 + c], cd.rd64[3 + a]);
-                p.lin(N[6 + c], cd.rd64[6 + a]);
+                p.term(N[c], cd.rd64[a]);
+                p.term(N[3 + c], cd.rd64[3 + a]);
+                p.term(N[6 + c], cd.rd64[6 + a]);
                 Mc[3 * a + c] = p.result();
             }
         BD J00, J02, J11, J12;
-        Pair<M, double> p;
-        p.init(0.0, 0.0); p.lin((double)fx, d64); J00 = p.result();
-        p.init(0.0, 0.0); p.lin(-(double)fx, uc64[0]); J02 = p.result();
-        p.init(0.0, 0.0); p.lin((double)fy, d64); J11 = p.result();
-        p.init(0.0, 0.0); p.lin(-(double)fy, uc64[1]); J12 = p.result();
+        AD p;
+        p.init(0.0, 0.0); p.term((double)fx, d64); J00 = p.result();
+        p.init(0.0, 0.0); p.term(-(double)fx, uc64[0]); J02 = p.result();
+        p.init(0.0, 0.0); p.term((double)fy, d64); J11 = p.result();
+        p.init(0.0, 0.0); p.term(-(double)fy, uc64[1]); J12 = p.result();
         for (int c = 0; c < 3; ++c) {
             p.init(0.0, 0.0); p.mul(J00, Mc[c]); p.mul(J02, Mc[6 + c]); Mp64[c] = p.result();
             p.init(0.0, 0.0); p.mul(J11, Mc[3 + c]); p.mul(J12, Mc[6 + c]); Mp64[3 + c] = p.result();
         }
     }
-    // ---- MatrixInv (Algorithm 3): X and I - X X0 in FP64, the series in FP32
+    // ---- MatrixInv (Algorithm 3): X and I - X X0 in FP64, the series in the
+    // record precision
     bool fallback = false;
     B conic[4];
     {
         BD X[4];
         {
-            Pair<M, double> p;
+            AD p;
             p.init(0.0, 0.0); p.sqr(Mp64[0]); p.sqr(Mp64[1]); p.sqr(Mp64[2]); X[0] = p.result();
             p.init(0.0, 0.0); p.sqr(Mp64[3]); p.sqr(Mp64[4]); p.sqr(Mp64[5]); X[3] = p.result();
             p.init(0.0, 0.0); p.mul(Mp64[0], Mp64[3]); p.mul(Mp64[1], Mp64[4]); p.mul(Mp64[2], Mp64[5]); X[1] = p.result();
@@ -459,15 +459,15 @@ __device__ __forceinline__ uint32_t record_value(const double *__restrict__ v, f
             double rho2 = 0.0;
             for (int r = 0; r < 2; ++r)
                 for (int s = 0; s < 2; ++s) {
-                    Pair<M, double> p;
+                    AD p;
                     const double dl = (r == s) ? 1.0 : 0.0;
                     p.init(dl, dl);
-                    p.lin(-(double)X0[s], X[2 * r]);
-                    p.lin(-(double)X0[2 + s], X[2 * r + 1]);
+                    p.term(-(double)X0[s], X[2 * r]);
+                    p.term(-(double)X0[2 + s], X[2 * r + 1]);
                     const BD e64 = p.result();
                     const double m = fmax(fabs(e64.vlo), fabs(e64.vhi));
                     rho2 = __fma_ru(m, m, rho2);
-                    bs_to_rec<M>(e64, E[2 * r + s]);
+                    sb_to_rec<M>(e64, E[2 * r + s]);
                 }
             const double rho64 = __dsqrt_ru(rho2);
             if (!(rho64 < RHO_MAX)) {
@@ -487,13 +487,13 @@ __device__ __forceinline__ uint32_t record_value(const double *__restrict__ v, f
                     B Q[4];
                     for (int r = 0; r < 2; ++r)
                         for (int s = 0; s < 2; ++s) {
-                            Pair<M, RO> p;
+                            SAcc<M, RO> p;
                             p.init(0, 0);
                             p.mul(P[2 * r], E[s]);
                             p.mul(P[2 * r + 1], E[2 + s]);
                             Q[2 * r + s] = p.result();
                         }
-                    for (int e = 0; e < 4; ++e) { P[e] = Q[e]; Ssum[e] = b_add<M, RO>(Ssum[e], Q[e]); }
+                    for (int e = 0; e < 4; ++e) { P[e] = Q[e]; Ssum[e] = sb_add<M, RO>(Ssum[e], Q[e]); }
                 }
                 RO nX0 = 0;
                 for (int e = 0; e < 4; ++e) nX0 = NO::fma_ru(X0[e], X0[e], nX0);
@@ -503,13 +503,13 @@ __device__ __forceinline__ uint32_t record_value(const double *__restrict__ v, f
                 const RO eps = NO::div_ru(NO::mul_ru(nX0, rk), NO::sub_rd(RO(1), rho));
                 for (int r = 0; r < 2; ++r)
                     for (int s = 0; s < 2; ++s) {
-                        Pair<M, RO> p;
+                        SAcc<M, RO> p;
                         // X0[r][s] + eps-widening, then + X0 T
                         p.init(NO::sub_rd(X0[2 * r + s], eps), NO::add_ru(X0[2 * r + s], eps));
-                        p.lin(X0[2 * r], Ssum[s]);
-                        p.lin(X0[2 * r + 1], Ssum[2 + s]);
+                        p.term(X0[2 * r], Ssum[s]);
+                        p.term(X0[2 * r + 1], Ssum[2 + s]);
                         conic[2 * r + s] = p.result();
-                        if (!bs_finite(conic[2 * r + s])) fallback = true;
+                        if (!sb_finite(conic[2 * r + s])) fallback = true;
                     }
             }
         }
@@ -518,18 +518,14 @@ __device__ __forceinline__ uint32_t record_value(const double *__restrict__ v, f
         for (int r = 0; r < 2; ++r)
             for (int c = 0; c < 3; ++c) {
                 // W = Conic Mp in FP64 (FP32 Conic forms are exact in FP64)
-                Pair<M, double> p;
+                AD p;
                 p.init(0.0, 0.0);
                 p.mul(to_f64<M>(conic[2 * r]), Mp64[c]);
                 p.mul(to_f64<M>(conic[2 * r + 1]), Mp64[3 + c]);
                 B w;
-                bs_to_rec<M>(p.result(), w);
-                if (!bs_finite(w)) fallback = true;
-                RO *dst = rec + RL::W0 + (3 * r + c) * RL::WSTRIDE;
-                store_form<M>(dst, w.lo);
-                store_form<M>(dst + RL::F, w.hi);
-                dst[2 * RL::F] = w.vlo; dst[2 * RL::F + 1] = w.vhi;
-                dst[2 * RL::F + 2] = w.rlo; dst[2 * RL::F + 3] = w.rhi;
+                sb_to_rec<M>(p.result(), w);
+                if (!sb_finite(w)) fallback = true;
+                store_sbw<M>(rec + RL::W0 + (3 * r + c) * RL::WS, w);
             }
     }
     if (!ok) fallback = true;

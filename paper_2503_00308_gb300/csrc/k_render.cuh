@@ -31,23 +31,28 @@ template <int M, class R = float> struct AlphaOut {
     R alo, ahi;     // scalar enclosure of a over the cell
 };
 
+// c[M], klo, khi, r (S and R entries; vlo, vhi are not needed)
 template <int M, class R>
-__device__ __forceinline__ void load_form(const R *src, LF<M, R> &f)
+__device__ __forceinline__ void load_sb(const R *src, SB<M, R> &b)
 {
 #pragma unroll
-    for (int j = 0; j < M; ++j) f.c[j] = src[j];
-    f.k = src[M];
+    for (int j = 0; j < M; ++j) b.c[j] = src[j];
+    b.klo = src[M];
+    b.khi = src[M + 1];
+    b.r = src[M + 2];
 }
 
+// c[M], klo, khi, vlo, vhi, r (W entries)
 template <int M, class R>
-__device__ __forceinline__ void load_w(const R *src, BS<M, R> &b)
+__device__ __forceinline__ void load_sbw(const R *src, SB<M, R> &b)
 {
-    load_form<M, R>(src, b.lo);
-    load_form<M, R>(src + M + 1, b.hi);
-    b.vlo = src[2 * M + 2];
-    b.vhi = src[2 * M + 3];
-    b.rlo = src[2 * M + 4];
-    b.rhi = src[2 * M + 5];
+#pragma unroll
+    for (int j = 0; j < M; ++j) b.c[j] = src[j];
+    b.klo = src[M];
+    b.khi = src[M + 1];
+    b.vlo = src[M + 2];
+    b.vhi = src[M + 3];
+    b.r = src[M + 4];
 }
 
 __device__ __forceinline__ float clamp01(float x) { return fminf(1.f, fmaxf(0.f, x)); }
@@ -63,7 +68,6 @@ __device__ __forceinline__ void pixel_alpha(const R *__restrict__ r, R ux, R uy,
 {
     using RL = Rec<M>;
     using N = Num<R>;
-    typedef BS<M, R> B;
     const R o = r[RL::O];
     const uint32_t flags = rec_flags(r, RL::FLAGS);
     if (flags & F_FALLBACK) {
@@ -73,44 +77,46 @@ __device__ __forceinline__ void pixel_alpha(const R *__restrict__ r, R ux, R uy,
         out.alo = 0; out.ahi = o;
         return;
     }
-    // Delta = S u - P, held as (u - mu) S + R (see Rec)
+    // Delta = S u - P, held as (u - mu) S + R (see Rec): the lower form takes
+    // S.lo and R.lo whatever the sign of u - mu (the pair is u S.lo - P.hi
+    // exactly); where u - mu < 0 the conversion gap of S is covered
+    typedef SB<M, R> B;
     B Dx, Dy;
     {
-        LF<M, R> slo, shi, plo, phi;
-        load_form<M, R>(r + RL::S_LO, slo);
-        load_form<M, R>(r + RL::S_HI, shi);
-        Acc<M, R, true> lo;
-        Acc<M, R, false> hi;
+        B S, Rr;
+        load_sb<M, R>(r + RL::S, S);
         const R dx = ux - r[RL::MU_X], dy = uy - r[RL::MU_Y];  // exact: both are half-integers
-        load_form<M, R>(r + RL::RX_LO, plo);
-        load_form<M, R>(r + RL::RX_HI, phi);
-        lo.init(0); hi.init(0);
-        lo.term(dx, slo, r[RL::RAD + 0]); hi.term(dx, shi, r[RL::RAD + 1]);
-        lo.term(1, plo, r[RL::RAD + 2]); hi.term(1, phi, r[RL::RAD + 3]);
-        Dx.lo = lo.result(); Dx.hi = hi.result(); finish(Dx);
-        load_form<M, R>(r + RL::RY_LO, plo);
-        load_form<M, R>(r + RL::RY_HI, phi);
-        lo.init(0); hi.init(0);
-        lo.term(dy, slo, r[RL::RAD + 0]); hi.term(dy, shi, r[RL::RAD + 1]);
-        lo.term(1, plo, r[RL::RAD + 4]); hi.term(1, phi, r[RL::RAD + 5]);
-        Dy.lo = lo.result(); Dy.hi = hi.result(); finish(Dy);
+        const R gap = r[RL::GAP_S];
+        SAcc<M, R> a;
+        load_sb<M, R>(r + RL::RX, Rr);
+        a.init(0, 0);
+        a.term_same_side(dx, S);
+        a.term((R)1, Rr);
+        if (dx < (R)0) a.add_slack(N::mul_ru(-dx, gap));
+        Dx = a.result();
+        load_sb<M, R>(r + RL::RY, Rr);
+        a.init(0, 0);
+        a.term_same_side(dy, S);
+        a.term((R)1, Rr);
+        if (dy < (R)0) a.add_slack(N::mul_ru(-dy, gap));
+        Dy = a.result();
     }
     // m = sum_c (Delta_x W_0c + Delta_y W_1c)^2
-    Pair<M, R> pm;
+    SAcc<M, R> pm;
     pm.init(0, 0);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         B w0, w1;
-        load_w<M, R>(r + RL::W0 + c * RL::WSTRIDE, w0);
-        load_w<M, R>(r + RL::W0 + (3 + c) * RL::WSTRIDE, w1);
-        Pair<M, R> pq;
+        load_sbw<M, R>(r + RL::W0 + c * RL::WS, w0);
+        load_sbw<M, R>(r + RL::W0 + (3 + c) * RL::WS, w1);
+        SAcc<M, R> pq;
         pq.init(0, 0);
         pq.mul(Dx, w0);
         pq.mul(Dy, w1);
-        B q = pq.result();
+        const B q = pq.result();
         pm.sqr(q);
     }
-    B m = pm.result();
+    const B m = pm.result();
     const R mlo = m.vlo, mhi = m.vhi;
     // Exp on x = -m/2 in [xl, xu], xu clipped at 0 because m >= 0
     const R xl = R(-0.5) * mhi;
@@ -121,7 +127,7 @@ __device__ __forceinline__ void pixel_alpha(const R *__restrict__ r, R ux, R uy,
     Acc<M, R, true> la;
     const R e1 = N::mul_rd(o, el_dn);
     la.init(N::mul_rd(e1, N::sub_rd(R(1), xl)));
-    la.term(R(-0.5) * e1, m.hi, m.rhi);
+    la.term_ck(R(-0.5) * e1, m.c, m.khi, m.r);
     LF<M, R> La = la.result();
     // upper: o (e(xl) + s (x - xl)) with x <= -m.lo/2
     const R w = N::sub_rd(xu, xl);
@@ -130,7 +136,7 @@ __device__ __forceinline__ void pixel_alpha(const R *__restrict__ r, R ux, R uy,
     const R e2 = N::mul_ru(o, el_up), s2 = N::mul_ru(o, s);
     Acc<M, R, false> ua;
     ua.init(N::fma_ru(-s2, xl, e2));
-    ua.term(R(-0.5) * s2, m.lo, m.rlo);
+    ua.term_ck(R(-0.5) * s2, m.c, m.klo, m.r);
     LF<M, R> Ua = ua.result();
     R rUa = 0;
 #pragma unroll
