@@ -282,12 +282,14 @@ struct EvInfo {
 // A pixel stops when both sides have; a tile stops when all its pixels have.
 constexpr float EXIT_EPS = 5e-8f;
 
-// Shared-memory layout of the render kernel (dynamic, one CTA per SM):
+// Shared-memory layout of the render kernel (dynamic; about 104 KB at six
+// pose variables, tile 16 and a ring of 8, so two CTAs fit on an SM):
 //   records staged for a chunk of CH events, their event info and pixel boxes,
 //   and a per-thread ring of the last RING opacity evaluations made at lower
 //   endpoints (record id + alo, ahi, rL, L), stored column-per-thread so that
 //   every access is bank-conflict free.  The ring lets the upper endpoint of
-//   a Gaussian reuse the evaluation made at its lower endpoint.
+//   a Gaussian reuse the evaluation made at its lower endpoint; an upper
+//   endpoint whose evaluation has left the ring evaluates again.
 template <int M, int TS, int CH, int RING> struct RenderSmem {
     static constexpr int NT = TS * TS;
     static constexpr int PAY = M + 4;  // alo, ahi, rL, L.k, L.c[M]
@@ -297,6 +299,13 @@ template <int M, int TS, int CH, int RING> struct RenderSmem {
     static constexpr size_t RID = sizeof(uint32_t) * RING * NT;
     static constexpr size_t RPAY = sizeof(float) * RING * PAY * NT;
     static constexpr size_t BYTES = REC + EV + BOX + RID + RPAY + 16;
+};
+
+// Two 256-thread CTAs share an SM (16 warps: the sweep is latency-bound, and
+// 128 registers per thread cost it a few spills but double the warps that hide
+// the FMA latency); 64-thread CTAs are not limited.
+template <int TS> struct RenderOcc {
+    static constexpr int MIN_BLOCKS = TS * TS >= 256 ? 2 : 1;
 };
 
 // Persistent grid: each CTA takes (cell, tile) segments from the active list
@@ -311,7 +320,7 @@ template <int M, int TS, int CH, int RING> struct RenderSmem {
 // from its start.  The sweep is deterministic, so the restarted segment
 // gives the same bounds it would have given in one pass.
 template <int M, int TS, int CH, int RING>
-__global__ void __launch_bounds__(TS *TS, 1) render_kernel(
+__global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kernel(
     const float *__restrict__ recs, const PixBox *__restrict__ boxes, const uint32_t *__restrict__ seg_start,
     const uint32_t *__restrict__ seg_end, const uint32_t *__restrict__ active, const uint32_t *__restrict__ n_active,
     uint32_t window, uint32_t *__restrict__ next_active, uint32_t *__restrict__ n_next,
