@@ -45,6 +45,8 @@ template <> struct Num<float> {
     __device__ static __forceinline__ float div_rd(float a, float b) { return __fdiv_rd(a, b); }
     __device__ static __forceinline__ float div_ru(float a, float b) { return __fdiv_ru(a, b); }
     __device__ static __forceinline__ float sqrt_ru(float a) { return __fsqrt_ru(a); }
+    // a / b to a few ulp, for weights where any value in [0, 1] is sound
+    __device__ static __forceinline__ float div_weight(float a, float b) { return __fdividef(a, b); }
     __device__ static __forceinline__ float abs(float a) { return fabsf(a); }
     __device__ static __forceinline__ float max(float a, float b) { return fmaxf(a, b); }
     __device__ static __forceinline__ float min(float a, float b) { return fminf(a, b); }
@@ -79,6 +81,7 @@ template <> struct Num<double> {
     __device__ static __forceinline__ double div_rd(double a, double b) { return __ddiv_rd(a, b); }
     __device__ static __forceinline__ double div_ru(double a, double b) { return __ddiv_ru(a, b); }
     __device__ static __forceinline__ double sqrt_ru(double a) { return __dsqrt_ru(a); }
+    __device__ static __forceinline__ double div_weight(double a, double b) { return a / b; }
     __device__ static __forceinline__ double abs(double a) { return fabs(a); }
     __device__ static __forceinline__ double max(double a, double b) { return fmax(a, b); }
     __device__ static __forceinline__ double min(double a, double b) { return fmin(a, b); }

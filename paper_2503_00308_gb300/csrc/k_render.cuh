@@ -143,13 +143,16 @@ __device__ __forceinline__ void pixel_alpha(const R *__restrict__ r, R ux, R uy,
     for (int j = 0; j < M; ++j) rUa = N::add_ru(rUa, N::abs(Ua.c[j]));
     const R amax = N::add_ru(Ua.k, rUa);
     // blend the upper form toward the constant o where its maximum exceeds o
-    const R lam = clamp01((o * (R(1) + R(CLIP_RAMP)) - amax) / (o * R(CLIP_RAMP)));
+    // The blend weights lam, psi2 (where m_lo > tau), psi (where m_hi <= tau)
+    // and mu keep the bounds sound at any value in [0, 1], so they are divided
+    // to a few ulp and clamped (a non-finite quotient clamps into [0, 1] too).
+    const R lam = clamp01(N::div_weight(o * (R(1) + R(CLIP_RAMP)) - amax, o * R(CLIP_RAMP)));
     // cutoff ramps (width shrinks with the m interval)
     R ramp = N::min(R(CUT_RAMP), mhi - mlo);
     if (!(ramp > R(0))) ramp = 0;
     const R tdn = r[RL::TAU_DN], tup = r[RL::TAU_UP];
-    const R psi2 = (mlo <= tup) ? R(0) : (ramp > R(0) ? clamp01((mlo - tup) / ramp) : R(1));
-    const R psi = (mhi > tdn) ? R(1) : (ramp > R(0) ? clamp01((mhi - tdn + ramp) / ramp) : R(0));
+    const R psi2 = (mlo <= tup) ? R(0) : (ramp > R(0) ? clamp01(N::div_weight(mlo - tup, ramp)) : R(1));
+    const R psi = (mhi > tdn) ? R(1) : (ramp > R(0) ? clamp01(N::div_weight(mhi - tdn + ramp, ramp)) : R(0));
     {
         Acc<M, R, false> u1;
         const R keep = R(1) - psi2;
@@ -168,7 +171,7 @@ __device__ __forceinline__ void pixel_alpha(const R *__restrict__ r, R ux, R uy,
 #pragma unroll
     for (int j = 0; j < M; ++j) rLa = N::add_ru(rLa, N::abs(La.c[j]));
     const R l2min = N::sub_rd(La.k, rLa), l2max = La.k + rLa;
-    const R mu = (l2min >= R(0)) ? R(1) : ((l2max <= R(0)) ? R(0) : l2max / (l2max - l2min));
+    const R mu = (l2min >= R(0)) ? R(1) : ((l2max <= R(0)) ? R(0) : clamp01(N::div_weight(l2max, l2max - l2min)));
     if ((flags & F_STRADDLE) || mu == R(0)) {
 #pragma unroll
         for (int j = 0; j < M; ++j) out.L.c[j] = 0;
@@ -354,8 +357,11 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
         const int cell = (int)(seg / (uint32_t)n_tiles);
         const int tile = (int)(seg - (uint32_t)cell * (uint32_t)n_tiles);
         const int tx = tile % ntx, ty = tile / ntx;
-        const int px = tx * TS + (tid % TS);
-        const int py = ty * TS + (tid / TS);
+        // each warp covers an 8 x 4 block of the tile, so that the pixel boxes
+        // of small Gaussians cut fewer warps and warps finish together
+        const int wb = tid >> 5, ln = tid & 31;
+        const int px = tx * TS + (wb % (TS / 8)) * 8 + (ln & 7);
+        const int py = ty * TS + (wb / (TS / 8)) * 4 + (ln >> 3);
         const bool inside = px < W && py < H;
         const float ux = px + 0.5f, uy = py + 0.5f;
         const uint32_t b0 = seg_start[seg], b1 = seg_end[seg];
