@@ -46,16 +46,18 @@ template <int M> struct CellData {
 // of per pixel.  GAP_S bounds, over the cell, how far the stored S forms lie
 // outside the FP64 ones R was formed from (their outward conversion); where
 // u - mu < 0 the pixel stage widens Delta by |u - mu| GAP_S.
+// Every entry starts on a multiple of 4 elements, so that the pixel stage reads
+// it with 16-byte vector loads.
 template <int M> struct Rec {
-    static constexpr int SBW = M + 3;            // c[M], klo, khi, r
+    static constexpr int SBW = (M + 3 + 3) / 4 * 4;  // c[M], klo, khi, r (padded)
     static constexpr int S = 0, RX = SBW, RY = 2 * SBW;
-    static constexpr int WS = M + 5;             // c[M], klo, khi, vlo, vhi, r
-    static constexpr int W0 = 3 * SBW;           // W_rc at W0 + (3 r + c) WS
-    static constexpr int SC = W0 + 6 * WS;       // o, tau_dn, tau_up, c0, c1, c2, flags, mu_x, mu_y, gap_s
+    static constexpr int WS = (M + 5 + 3) / 4 * 4;   // c[M], klo, khi, vlo, vhi, r (padded)
+    static constexpr int W0 = 3 * SBW;               // W_rc at W0 + (3 r + c) WS
+    static constexpr int SC = W0 + 6 * WS;           // o, tau_dn, tau_up, c0, c1, c2, flags, mu_x, mu_y, gap_s
     static constexpr int O = SC, TAU_DN = SC + 1, TAU_UP = SC + 2, COL = SC + 3, FLAGS = SC + 6;
     static constexpr int MU_X = SC + 7, MU_Y = SC + 8, GAP_S = SC + 9;
-    static constexpr int RAW = SC + 10;
-    static constexpr int WIDTH = (RAW + 3) / 4 * 4;  // 16-byte multiple (float)
+    static constexpr int SCW = 12;
+    static constexpr int WIDTH = SC + SCW;            // a multiple of 4 elements
 };
 
 // record flags

@@ -31,28 +31,46 @@ template <int M, class R = float> struct AlphaOut {
     R alo, ahi;     // scalar enclosure of a over the cell
 };
 
+// n elements (a multiple of 4, 16-byte aligned) copied with 16-byte loads
+template <int n>
+__device__ __forceinline__ void load_vec(const float *src, float *dst)
+{
+#pragma unroll
+    for (int q = 0; q < n / 4; ++q) reinterpret_cast<float4 *>(dst)[q] = reinterpret_cast<const float4 *>(src)[q];
+}
+template <int n>
+__device__ __forceinline__ void load_vec(const double *src, double *dst)
+{
+#pragma unroll
+    for (int q = 0; q < n / 2; ++q) reinterpret_cast<double2 *>(dst)[q] = reinterpret_cast<const double2 *>(src)[q];
+}
+
 // c[M], klo, khi, r (S and R entries; vlo, vhi are not needed)
 template <int M, class R>
 __device__ __forceinline__ void load_sb(const R *src, SB<M, R> &b)
 {
+    R v[Rec<M>::SBW];
+    load_vec<Rec<M>::SBW>(src, v);
 #pragma unroll
-    for (int j = 0; j < M; ++j) b.c[j] = src[j];
-    b.klo = src[M];
-    b.khi = src[M + 1];
-    b.r = src[M + 2];
+    for (int j = 0; j < M; ++j) b.c[j] = v[j];
+    b.klo = v[M];
+    b.khi = v[M + 1];
+    b.r = v[M + 2];
 }
 
 // c[M], klo, khi, vlo, vhi, r (W entries)
 template <int M, class R>
 __device__ __forceinline__ void load_sbw(const R *src, SB<M, R> &b)
 {
+    R v[Rec<M>::WS];
+    load_vec<Rec<M>::WS>(src, v);
 #pragma unroll
-    for (int j = 0; j < M; ++j) b.c[j] = src[j];
-    b.klo = src[M];
-    b.khi = src[M + 1];
-    b.vlo = src[M + 2];
-    b.vhi = src[M + 3];
-    b.r = src[M + 4];
+    for (int j = 0; j < M; ++j) b.c[j] = v[j];
+    b.klo = v[M];
+    b.khi = v[M + 1];
+    b.vlo = v[M + 2];
+    b.vhi = v[M + 3];
+    b.r = v[M + 4];
 }
 
 __device__ __forceinline__ float clamp01(float x) { return fminf(1.f, fmaxf(0.f, x)); }
