@@ -63,8 +63,9 @@ int AR_CAT(launch_render_plain_m, AR_M)(int TS, const RenderLaunch &a, cudaStrea
 template <int TS>
 static int launch_render_ts(const RenderLaunch &a, cudaStream_t st)
 {
-    // ring of 8 keeps two 256-thread CTAs within the shared memory of an SM
-    constexpr int CH = 32, RING = 8;
+    // double-buffered chunks and a ring of 6 keep two 256-thread CTAs within
+    // the shared memory of an SM
+    constexpr int CH = 32, RING = 6;
     typedef RenderSmem<AR_M, TS, CH, RING> SM;
     auto kern = render_kernel<AR_M, TS, CH, RING>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::BYTES) != cudaSuccess)

@@ -303,9 +303,11 @@ struct EvInfo {
 // A pixel stops when both sides have; a tile stops when all its pixels have.
 constexpr float EXIT_EPS = 5e-8f;
 
-// Shared-memory layout of the render kernel (dynamic; about 104 KB at six
-// pose variables, tile 16 and a ring of 8, so two CTAs fit on an SM):
-//   records staged for a chunk of CH events, their event info and pixel boxes,
+// Shared-memory layout of the render kernel (dynamic; about 100 KB at six
+// pose variables, tile 16 and a ring of 6, so two CTAs fit on an SM):
+//   two buffers, each with the records staged for a chunk of CH events, their
+//   event info and pixel boxes (the next chunk is copied in while the current
+//   one is swept),
 //   and a per-thread ring of the last RING opacity evaluations made at lower
 //   endpoints (record id + alo, ahi, rL, L), stored column-per-thread so that
 //   every access is bank-conflict free.  The ring lets the upper endpoint of
@@ -314,13 +316,21 @@ constexpr float EXIT_EPS = 5e-8f;
 template <int M, int TS, int CH, int RING> struct RenderSmem {
     static constexpr int NT = TS * TS;
     static constexpr int PAY = M + 4;  // alo, ahi, rL, L.k, L.c[M]
-    static constexpr size_t REC = sizeof(float) * CH * Rec<M>::WIDTH;
-    static constexpr size_t EV = sizeof(EvInfo) * CH;
-    static constexpr size_t BOX = sizeof(PixBox) * CH;
+    static constexpr size_t REC = 2 * sizeof(float) * CH * Rec<M>::WIDTH;  // two chunk buffers
+    static constexpr size_t EV = 2 * sizeof(EvInfo) * CH;
+    static constexpr size_t BOX = 2 * sizeof(PixBox) * CH;
     static constexpr size_t RID = sizeof(uint32_t) * RING * NT;
     static constexpr size_t RPAY = sizeof(float) * RING * PAY * NT;
     static constexpr size_t BYTES = REC + EV + BOX + RID + RPAY + 16;
 };
+
+// 16-byte asynchronous global -> shared copies (completed by cp_async_wait_all)
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // Two 256-thread CTAs share an SM (16 warps: the sweep is latency-bound, and
 // 128 registers per thread cost it a few spills but double the warps that hide
@@ -355,9 +365,9 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
     using SM = RenderSmem<M, TS, CH, RING>;
     constexpr int NT = TS * TS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float(*s_rec)[RL::WIDTH] = reinterpret_cast<float(*)[RL::WIDTH]>(smem_raw);
-    EvInfo *s_ev = reinterpret_cast<EvInfo *>(smem_raw + SM::REC);
-    PixBox *s_box = reinterpret_cast<PixBox *>(smem_raw + SM::REC + SM::EV);
+    float(*s_rec2)[RL::WIDTH] = reinterpret_cast<float(*)[RL::WIDTH]>(smem_raw);        // [2 * CH]
+    EvInfo *s_ev2 = reinterpret_cast<EvInfo *>(smem_raw + SM::REC);                    // [2 * CH]
+    PixBox *s_box2 = reinterpret_cast<PixBox *>(smem_raw + SM::REC + SM::EV);          // [2 * CH]
     uint32_t *s_rid = reinterpret_cast<uint32_t *>(smem_raw + SM::REC + SM::EV + SM::BOX);
     float *s_pay = reinterpret_cast<float *>(smem_raw + SM::REC + SM::EV + SM::BOX + SM::RID);
     uint32_t *s_next = reinterpret_cast<uint32_t *>(smem_raw + SM::REC + SM::EV + SM::BOX + SM::RID + SM::RPAY);
@@ -403,7 +413,39 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
         uint32_t swept = b1 - b0;  // entries swept before the tile stopped
         uint32_t seg_evals = 0, seg_recomp = 0;
 
-        for (uint32_t base = b0; base < b1; base += CH) {
+        // Copy the chunk starting at entry sb into buffer bf: warp w takes
+        // events EPW w .. EPW w + EPW - 1, its first EPW lanes read their event
+        // info, and the whole warp copies their record rows asynchronously.
+        constexpr int NWARP = NT / 32, EPW = CH / NWARP, ROW4 = RL::WIDTH / 4;
+        static_assert(CH % NWARP == 0 && EPW <= 32, "chunk must split evenly over the warps");
+        auto stage = [&](int bf, uint32_t sb) {
+            const int k0 = wb * EPW;
+            uint32_t rec = 0;
+            const bool have_ev = ln < EPW && sb + (uint32_t)(k0 + ln) < b1;
+            if (have_ev) {
+                const uint32_t i = sb + (uint32_t)(k0 + ln);
+                const uint32_t e = entry_ev[i];
+                const uint32_t v = ev_val[e];
+                uint32_t bits = v & 1u;
+                if (i > b0 && ev_key[entry_ev[i - 1]] == ev_key[e]) bits |= 2u;
+                rec = (v >> 1) - (uint32_t)(cell * n_gauss);
+                s_ev2[bf * CH + k0 + ln] = EvInfo{rec, bits};
+                s_box2[bf * CH + k0 + ln] = box_cell[rec];
+            }
+            const uint32_t nv = __ballot_sync(0xffffffffu, have_ev);
+            for (int q0 = 0; q0 < EPW * ROW4; q0 += 32) {
+                const int q = q0 + ln;
+                const int k = min(q / ROW4, EPW - 1);
+                const uint32_t rk = __shfl_sync(0xffffffffu, rec, k);
+                if (q < EPW * ROW4 && ((nv >> k) & 1u)) {
+                    const int part = q - k * ROW4;
+                    cp_async16(&s_rec2[bf * CH + k0 + k][4 * part], rec_cell + (size_t)rk * RL::WIDTH + 4 * part);
+                }
+            }
+        };
+        int buf = 0;
+        if (b0 < b1) stage(0, b0);
+        for (uint32_t base = b0; base < b1; base += CH, buf ^= 1) {
             const int cnt = (int)min((uint32_t)CH, b1 - base);
             if (!done) {
                 const float left = (float)(b1 - base);
@@ -424,7 +466,8 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
                     hi_adj = hi_one ? -1.f : ehi2;
                 }
             }
-            if (__syncthreads_and(done)) {
+            cp_async_wait_all();  // this thread's copies of the current chunk
+            if (__syncthreads_and(done)) {  // ... and everyone's, now visible
                 swept = base - b0;
                 break;
             }
@@ -432,23 +475,12 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
                 abandoned = true;
                 break;
             }
-            if (tid < cnt) {
-                const uint32_t i = base + tid;
-                const uint32_t e = entry_ev[i];
-                const uint32_t v = ev_val[e];
-                uint32_t bits = v & 1u;
-                if (i > b0 && ev_key[entry_ev[i - 1]] == ev_key[e]) bits |= 2u;
-                const uint32_t rec = (v >> 1) - (uint32_t)(cell * n_gauss);
-                s_ev[tid] = EvInfo{rec, bits};
-                s_box[tid] = box_cell[rec];
-            }
-            __syncthreads();
-            for (int t = tid; t < cnt * (RL::WIDTH / 4); t += NT) {
-                const int e = t / (RL::WIDTH / 4), q = t - e * (RL::WIDTH / 4);
-                const float4 *src = reinterpret_cast<const float4 *>(rec_cell + (size_t)s_ev[e].rec * RL::WIDTH);
-                reinterpret_cast<float4 *>(s_rec[e])[q] = __ldg(src + q);
-            }
-            __syncthreads();
+            // the next chunk streams in while this one is swept; the buffer it
+            // overwrites was swept by every thread before the barrier above
+            if (base + CH < b1) stage(buf ^ 1, base + CH);
+            const EvInfo *s_ev = s_ev2 + buf * CH;
+            const PixBox *s_box = s_box2 + buf * CH;
+            float(*s_rec)[RL::WIDTH] = s_rec2 + buf * CH;
             if (done) continue;
             for (int e = 0; e < cnt; ++e) {
                 const EvInfo ev = s_ev[e];
