@@ -124,20 +124,33 @@ template <int M> __device__ __forceinline__ DF<M> df_sub(const DF<M> &a, const D
 }
 template <int M> __device__ __forceinline__ DB<M> db_add(const DB<M> &a, const DB<M> &b)
 {
-    DB<M> r;
-    r.lo = df_add(a.lo, b.lo);
-    r.hi = df_add(a.hi, b.hi);
+    DB<M> r;  // shared coefficients (see db_mul)
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        r.lo.c[j] = dadd(a.lo.c[j], b.lo.c[j]);
+        r.hi.c[j] = r.lo.c[j];
+    }
+    r.lo.k = dadd(a.lo.k, b.lo.k);
+    r.hi.k = dadd(a.hi.k, b.hi.k);
     return r;
 }
-// averaged McCormick planes (same statement as the single-precision Mul)
+// averaged McCormick planes (same statement as the single-precision Mul).
+// The lower and upper forms of every operand here share their coefficients
+// (the pose forms differ only in their constants), so the coefficients of the
+// product are computed once; each is the same IEEE expression either way.
 template <int M> __device__ __forceinline__ DB<M> db_mul(const DB<M> &x, const DB<M> &y)
 {
     double xl = df_min(x.lo), xh = df_max(x.hi), yl = df_min(y.lo), yh = df_max(y.hi);
     double xm = dmul(0.5, dadd(xl, xh)), ym = dmul(0.5, dadd(yl, yh));
     DB<M> r;
-    r.lo = df_add(df_scale(ym >= 0 ? x.lo : x.hi, ym), df_scale(xm >= 0 ? y.lo : y.hi, xm));
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        r.lo.c[j] = dadd(dmul(ym, x.lo.c[j]), dmul(xm, y.lo.c[j]));
+        r.hi.c[j] = r.lo.c[j];
+    }
+    r.lo.k = dadd(dmul(ym, (ym >= 0 ? x.lo : x.hi).k), dmul(xm, (xm >= 0 ? y.lo : y.hi).k));
     r.lo.k = dsub(r.lo.k, dmul(0.5, dadd(dmul(xl, yl), dmul(xh, yh))));
-    r.hi = df_add(df_scale(ym >= 0 ? x.hi : x.lo, ym), df_scale(xm >= 0 ? y.hi : y.lo, xm));
+    r.hi.k = dadd(dmul(ym, (ym >= 0 ? x.hi : x.lo).k), dmul(xm, (xm >= 0 ? y.hi : y.lo).k));
     r.hi.k = dsub(r.hi.k, dmul(0.5, dadd(dmul(xh, yl), dmul(xl, yh))));
     return r;
 }
@@ -154,6 +167,12 @@ __device__ __forceinline__ DI di_mul(DI a, DI b)
     r.l = fmin(r.l, p2); r.u = fmax(r.u, p2);
     r.l = fmin(r.l, p3); r.u = fmax(r.u, p3);
     return r;
+}
+// di_mul for a > 0 (a.l > 0): the extreme products are picked by the sign of
+// b's ends, so the result is the same pair of IEEE products di_mul selects
+__device__ __forceinline__ DI di_mul_pos(DI a, DI b)
+{
+    return DI{b.l >= 0 ? dmul(a.l, b.l) : dmul(a.u, b.l), b.u >= 0 ? dmul(a.u, b.u) : dmul(a.l, b.u)};
 }
 __device__ __forceinline__ DI di_add(DI a, DI b) { return DI{dadd(a.l, b.l), dadd(a.u, b.u)}; }
 __device__ __forceinline__ DI di_scale(DI a, double s)

@@ -303,8 +303,9 @@ __device__ __forceinline__ int64_t record_decide(const double *__restrict__ vN, 
             DI m[3];
             for (int a = 0; a < 3; ++a)
                 m[a] = di_add(di_add(di_scale(Ri[a], N[c]), di_scale(Ri[3 + a], N[3 + c])), di_scale(Ri[6 + a], N[6 + c]));
-            DI p0 = di_scale(di_add(di_mul(D, m[0]), di_scale(di_mul(ucx, m[2]), -1.0)), fx);
-            DI p1 = di_scale(di_add(di_mul(D, m[1]), di_scale(di_mul(ucy, m[2]), -1.0)), fy);
+            // D = [max(d_lo, near), d_hi] is positive
+            DI p0 = di_scale(di_add(di_mul_pos(D, m[0]), di_scale(di_mul(ucx, m[2]), -1.0)), fx);
+            DI p1 = di_scale(di_add(di_mul_pos(D, m[1]), di_scale(di_mul(ucy, m[2]), -1.0)), fy);
             X00 = dadd(X00, di_sqmax(p0));
             X11 = dadd(X11, di_sqmax(p1));
         }
