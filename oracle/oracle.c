@@ -57,6 +57,7 @@ static const double RHO_MAX = 1.0 - 1.0 / 1024.0;  /* MatrixInv usable while ||I
 static const double CUT_RAMP = 0.5;   /* widest cutoff ramp, in units of m */
 static const double CLIP_RAMP = 0.25; /* blend width of the upper-alpha clip to o */
 static const double KEY_SLACK = 1e-9; /* relative widening of depth keys */
+static const double GUARD = 0.65;     /* guard band: 1.3 x the half-extent, as a fraction of W and H */
 static const double BOX_SLACK = 1e-9; /* relative widening of screen boxes */
 static const double ALPHA_MIN = 1.0 / 255.0;
 
@@ -238,6 +239,13 @@ static void gsplat_gaussian(const camera *cam, const double Rwc[9], const double
     g->tau = (o > 0) ? 2.0 * log(255.0 * o) : -INFINITY;
     for (int k = 0; k < 3; ++k) g->c[k] = rgb[k];
     g->alive = (g->d > cam->near_plane) && (det > 0) && (o > 0);
+    if (g->alive) {
+        /* frustum guard band (3DGS convention): the projected mean must lie
+         * within 1.3 times the image half-extent around the principal point */
+        const double gx = GUARD * cam->W, gy = GUARD * cam->H;
+        const double u = cam->cx + cam->fx * uc[0] / uc[2], w = cam->cy + cam->fy * uc[1] / uc[2];
+        g->alive = (u >= cam->cx - gx) && (u <= cam->cx + gx) && (w >= cam->cy - gy) && (w <= cam->cy + gy);
+    }
 }
 
 /* effective opacity at pixel u (Algorithm 1, lines 9-10) with the 1/255 cutoff */
@@ -559,6 +567,16 @@ static void gaussian_record(const camera *cam, const cellforms *cf, const double
         ival ucy = iv_add(iv_add(iv_mul(Ri[1], vs[0]), iv_mul(Ri[4], vs[1])), iv_mul(Ri[7], vs[2]));
         ival mux = {cam->cx + cam->fx * fmin(ucx.l / D.l, ucx.l / D.u), cam->cx + cam->fx * fmax(ucx.u / D.l, ucx.u / D.u)};
         ival muy = {cam->cy + cam->fy * fmin(ucy.l / D.l, ucy.l / D.u), cam->cy + cam->fy * fmax(ucy.u / D.l, ucy.u / D.u)};
+        /* frustum guard band: a mean outside it at every pose of the cell
+         * drops the pair; outside it at some pose makes the lower alpha 0 */
+        {
+            const double gx = GUARD * cam->W, gy = GUARD * cam->H;
+            const double ml = mux.l - BOX_SLACK * (1 + fabs(mux.l)), mh = mux.u + BOX_SLACK * (1 + fabs(mux.u));
+            const double nl = muy.l - BOX_SLACK * (1 + fabs(muy.l)), nh = muy.u + BOX_SLACK * (1 + fabs(muy.u));
+            if (ml > cam->cx + gx || mh < cam->cx - gx || nl > cam->cy + gy || nh < cam->cy - gy) return;
+            if (!(ml >= cam->cx - gx && mh <= cam->cx + gx && nl >= cam->cy - gy && nh <= cam->cy + gy))
+                g->straddle = 1;
+        }
         double X00 = 0, X11 = 0;
         for (int c = 0; c < 3; ++c) {
             ival m[3];

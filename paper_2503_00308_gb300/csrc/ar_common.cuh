@@ -14,6 +14,7 @@ constexpr float CUT_RAMP = 0.5f;                 // widest cutoff ramp (units of
 constexpr float CLIP_RAMP = 0.25f;               // upper-alpha blend toward o
 constexpr double KEY_SLACK = 1e-9;               // relative widening of depth keys
 constexpr double BOX_SLACK = 1e-9;               // relative widening of screen boxes
+constexpr double GUARD = 0.65;                   // frustum guard band: 1.3 x the half-extent (fraction of W, H)
 constexpr float ALPHA_MIN_UP = 0.003921568859368563f;  // 1/255 rounded up to float
 
 constexpr int MAXV = 6;  // pose variables tx ty tz rx ry rz

@@ -274,7 +274,7 @@ __device__ __forceinline__ int64_t record_decide(const double *__restrict__ vN, 
     const double dlo = df_min(dd.lo), dhi = df_max(dd.hi);
     const double nearp = (double)cc.near_plane;
     if (!(dhi > nearp)) return -1;
-    const bool straddle = !(dlo > nearp);
+    bool straddle = !(dlo > nearp);
     double klo, khi;
     {
         DF<M> gk;
@@ -298,6 +298,19 @@ __device__ __forceinline__ int64_t record_decide(const double *__restrict__ vN, 
         const double fx = cc.fx, fy = cc.fy, cx = cc.cx, cy = cc.cy;
         DI mux = {dadd(cx, dmul(fx, fmin(ucx.l / D.l, ucx.l / D.u))), dadd(cx, dmul(fx, fmax(ucx.u / D.l, ucx.u / D.u)))};
         DI muy = {dadd(cy, dmul(fy, fmin(ucy.l / D.l, ucy.l / D.u))), dadd(cy, dmul(fy, fmax(ucy.u / D.l, ucy.u / D.u)))};
+        // frustum guard band (3DGS convention): a mean outside it at every
+        // pose of the cell drops the pair; outside it at some pose makes the
+        // lower alpha 0
+        {
+            const double gx = dmul(GUARD, (double)cc.W), gy = dmul(GUARD, (double)cc.H);
+            const double ml = dsub(mux.l, dmul(BOX_SLACK, dadd(1.0, fabs(mux.l))));
+            const double mh = dadd(mux.u, dmul(BOX_SLACK, dadd(1.0, fabs(mux.u))));
+            const double nl = dsub(muy.l, dmul(BOX_SLACK, dadd(1.0, fabs(muy.l))));
+            const double nh = dadd(muy.u, dmul(BOX_SLACK, dadd(1.0, fabs(muy.u))));
+            if (ml > dadd(cx, gx) || mh < dsub(cx, gx) || nl > dadd(cy, gy) || nh < dsub(cy, gy)) return -1;
+            if (!(ml >= dsub(cx, gx) && mh <= dadd(cx, gx) && nl >= dsub(cy, gy) && nh <= dadd(cy, gy)))
+                straddle = true;
+        }
         double X00 = 0, X11 = 0;
         for (int c = 0; c < 3; ++c) {
             DI m[3];

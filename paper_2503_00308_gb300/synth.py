@@ -109,11 +109,20 @@ def cube_scene(n: int, seed: int, half: float = 0.5, logscale_mu: float = -2.5,
 
 
 def box_scene(n: int, seed: int, extent=(20.0, 5.0, 20.0), logscale_mu: float = -3.0,
-              logscale_sd: float = 0.7, opacity_mu: float = 0.5) -> Scene:
-    """Unbounded scene: means uniform in an axis box centred on the origin (y is up/down)."""
+              logscale_sd: float = 0.7, opacity_mu: float = 0.5, clear_centre=None,
+              clear_radius: float = 0.0) -> Scene:
+    """Unbounded scene: means uniform in an axis box centred on the origin (y is up/down).
+    Means closer than clear_radius to clear_centre are drawn again (a capture
+    position has free space around it)."""
     rng = np.random.default_rng(seed)
     ext = np.asarray(extent, dtype=np.float64)
     uw = rng.uniform(-0.5, 0.5, size=(n, 3)) * ext
+    if clear_radius > 0:
+        c = np.asarray(clear_centre, dtype=np.float64)
+        bad = np.linalg.norm(uw - c, axis=1) < clear_radius
+        while bad.any():
+            uw[bad] = rng.uniform(-0.5, 0.5, size=(int(bad.sum()), 3)) * ext
+            bad = np.linalg.norm(uw - c, axis=1) < clear_radius
     ls = rng.normal(loc=logscale_mu, scale=logscale_sd, size=(n, 3))
     q = _unit_quats(rng, n)
     o = _sigmoid(rng.normal(loc=opacity_mu, size=n))
@@ -189,10 +198,11 @@ def object300k(seed: int = 0, n: int = 300_000, width: int = 800, height: int = 
 
 
 def unbounded750k(seed: int = 0, n: int = 750_000, width: int = 1280, height: int = 720,
-                  f: float = 900.0, splits=(4, 2, 4, 2, 2, 2)) -> Workload:
+                  f: float = 900.0, splits=(4, 2, 4, 2, 2, 2), clear_radius: float = 2.0) -> Workload:
     """750k Gaussians in a 20 x 5 x 20 m box, camera at the origin looking +z,
-    1280x720, f = 900; +-10 cm / +-2 deg split into 256 cells."""
-    sc = box_scene(n, seed)
+    1280x720, f = 900; +-10 cm / +-2 deg split into 256 cells.  No Gaussian
+    lies within clear_radius of the camera."""
+    sc = box_scene(n, seed, clear_centre=(0.0, 0.0, 0.0), clear_radius=clear_radius)
     cam = look_camera(width, height, f, centre=(0.0, 0.0, 0.0))
     lo, hi = cell_grid([0.10, 0.10, 0.10, 2 * DEG, 2 * DEG, 2 * DEG], splits)
     return Workload("unbounded750k", sc, cam, lo, hi)
@@ -209,7 +219,7 @@ WORKLOADS = {
 # ------------------------------------------------------------------ serving mix
 SERVE_SCENES = {"object10k": lambda: object_scene(10_000, 0),
                 "object300k": lambda: object_scene(300_000, 0),
-                "unbounded750k": lambda: box_scene(750_000, 0)}
+                "unbounded750k": lambda: box_scene(750_000, 0, clear_centre=(0.0, 0.0, 0.0), clear_radius=2.0)}
 
 _SPLITS = {1: (1, 1, 1, 1, 1, 1), 4: (2, 1, 2, 1, 1, 1), 16: (2, 2, 2, 1, 2, 1), 64: (2, 2, 2, 2, 2, 2),
            256: (4, 2, 4, 2, 2, 2)}

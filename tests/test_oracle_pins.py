@@ -420,3 +420,50 @@ def test_near_plane_drop_is_sound(orc):
     worst, nv = orc.check_samples(sc, cam, poses, lo, hi, tol=1e-12)
     assert nv == 0, worst
     assert hi[8, 8, 0] > 0.5 and lo[8, 8, 0] == 0.0
+
+
+# ------------------------------------------------ frustum guard band (3DGS)
+# A 16x16 image with f = 16 and cx = 8: the guard band keeps projected means
+# with |u - 8| <= 0.65 * 16 = 10.4, i.e. u <= 18.4.  A wide opaque Gaussian at
+# depth 1 and lateral offset x projects its mean to u = 8 + 16 x.
+
+def _guard_scene(x):
+    sc = synth.cube_scene(1, 0)
+    sc.uw[:] = [[x, 0.0, 0.0]]
+    sc.logscale[:] = -0.5          # sigma 0.61 m: about 10 px, reaching well into the image
+    sc.quat[:] = [1, 0, 0, 0]
+    sc.opacity[:] = 0.9
+    sc.rgb[:] = [[1, 1, 1]]
+    return sc
+
+
+def test_guard_band_concrete(orc):
+    cam = synth.look_camera(16, 16, 16.0, centre=(0, 0, -1.0))
+    zero = np.zeros(6)
+    inside = orc.render_concrete(_guard_scene(0.6), cam, zero, "sort")    # u = 17.6
+    outside = orc.render_concrete(_guard_scene(0.7), cam, zero, "sort")   # u = 19.2
+    assert inside[8, 15, 0] > 0.2 and inside[8, 8, 0] > 0.01
+    assert np.all(outside == 0.0)
+
+
+def test_guard_band_abstract_drop(orc):
+    cam = synth.look_camera(16, 16, 16.0, centre=(0, 0, -1.0))
+    clo = np.array([-0.001, 0, 0, 0, 0, 0])
+    rec = orc.records(_guard_scene(0.7), cam, clo, -clo)
+    assert rec["valid"][0] == 0
+    lo, hi, _ = orc.render_abstract(_guard_scene(0.7), cam, clo, -clo)
+    assert np.all(lo == 0.0) and np.all(hi == 0.0)
+
+
+def test_guard_band_crossing_is_sound(orc):
+    # the camera's x translation moves the mean across u = 18.4 inside the cell
+    sc = _guard_scene(0.65)
+    cam = synth.look_camera(16, 16, 16.0, centre=(0, 0, -1.0))
+    clo = np.array([-0.05, 0, 0, 0, 0, 0])
+    rec = orc.records(sc, cam, clo, -clo)
+    assert rec["valid"][0] == 1 and rec["straddle"][0] == 1
+    lo, hi, _ = orc.render_abstract(sc, cam, clo, -clo)
+    poses = np.linspace(clo, -clo, 201)
+    worst, nv = orc.check_samples(sc, cam, poses, lo, hi, tol=1e-12)
+    assert nv == 0, worst
+    assert np.all(lo == 0.0) and hi[8, 15, 0] > 0.2
