@@ -198,10 +198,11 @@ def object300k(seed: int = 0, n: int = 300_000, width: int = 800, height: int = 
 
 
 def unbounded750k(seed: int = 0, n: int = 750_000, width: int = 1280, height: int = 720,
-                  f: float = 900.0, splits=(4, 2, 4, 2, 2, 2), clear_radius: float = 2.0) -> Workload:
-    """750k Gaussians in a 20 x 5 x 20 m box, camera at the origin looking +z,
-    1280x720, f = 900; +-10 cm / +-2 deg split into 256 cells.  No Gaussian
-    lies within clear_radius of the camera."""
+                  f: float = 900.0, splits=(4, 2, 4, 2, 2, 2), clear_radius: float = 0.0) -> Workload:
+    """750k Gaussians in a 20 x 5 x 20 m box, camera at the origin looking +z
+    (inside the scene, so near-plane straddles occur), 1280x720, f = 900;
+    +-10 cm / +-2 deg split into 256 cells.  clear_radius > 0 keeps Gaussians
+    that far from the camera."""
     sc = box_scene(n, seed, clear_centre=(0.0, 0.0, 0.0), clear_radius=clear_radius)
     cam = look_camera(width, height, f, centre=(0.0, 0.0, 0.0))
     lo, hi = cell_grid([0.10, 0.10, 0.10, 2 * DEG, 2 * DEG, 2 * DEG], splits)
@@ -219,7 +220,7 @@ WORKLOADS = {
 # ------------------------------------------------------------------ serving mix
 SERVE_SCENES = {"object10k": lambda: object_scene(10_000, 0),
                 "object300k": lambda: object_scene(300_000, 0),
-                "unbounded750k": lambda: box_scene(750_000, 0, clear_centre=(0.0, 0.0, 0.0), clear_radius=2.0)}
+                "unbounded750k": lambda: box_scene(750_000, 0)}
 
 _SPLITS = {1: (1, 1, 1, 1, 1, 1), 4: (2, 1, 2, 1, 1, 1), 16: (2, 2, 2, 1, 2, 1), 64: (2, 2, 2, 2, 2, 2),
            256: (4, 2, 4, 2, 2, 2)}

@@ -233,3 +233,22 @@ def test_windowed_rounds_restart(arlib, orc):
     d = np.maximum(np.abs(glo - plo.double().cpu().numpy()), np.abs(ghi - phi.double().cpu().numpy()))
     assert d.max() <= 2 * TOL, d.max()
     s.close()
+
+
+def test_guard_band_parity(arlib, orc):
+    """Gaussians spread far beyond the frustum and close to the camera plane:
+    the guard band drops or half-keeps them identically on both sides."""
+    rng = np.random.default_rng(17)
+    sc = synth.cube_scene(400, 5, half=1.0, logscale_mu=-1.8)
+    sc.uw[:, 0] = rng.uniform(-3.0, 3.0, size=400).astype(np.float32)
+    sc.uw[:, 2] = rng.uniform(-0.6, 1.0, size=400).astype(np.float32)
+    cam = synth.look_camera(40, 32, 36.0, centre=(0, 0, -1.0))
+    lo, hi = synth.cell_grid([0.05, 0.02, 0.05, 0.0, 0.0087, 0.0], [2, 1, 1, 1, 1, 1])
+    rec = orc.records(sc, cam, lo[0], hi[0])
+    assert rec["straddle"].sum() > 0
+    glo, ghi = gpu_render(arlib, sc, cam, lo, hi)
+    for c in range(lo.shape[0]):
+        compare(orc, sc, cam, lo[c], hi[c], glo[c], ghi[c])
+        poses = synth.sample_poses(np.random.default_rng(c), lo[c], hi[c], 300)
+        worst, nv = orc.check_samples(sc, cam, poses, glo[c], ghi[c])
+        assert nv == 0, worst
