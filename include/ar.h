@@ -171,9 +171,17 @@ int ar_render_abstract_plain_fp64(ar_scene *scene, const ar_intrinsics *intr,
                                   int32_t n_cells, int32_t tile, float *out_lower,
                                   float *out_upper, void *cuda_stream);
 
-/* Concrete GSplat render (Algorithm 1 with BlendInd, Algorithm 4) at n_poses
- * poses given as delta vectors (host, [n_poses][6]); out is a device buffer
- * [n_poses][H][W][3] float32.  Used to check soundness on the device. */
+/* Concrete GSplat render (Algorithm 1, blended as BlendInd, Algorithm 4:
+ * Gaussians of equal depth do not occlude each other) at n_poses poses, for
+ * checking the abstract bounds on the device.  deltas: host, [n_poses][6]
+ * (tx, ty, tz, rx, ry, rz) relative to the nominal pose, as in ar_pose_box;
+ * out: device, [n_poses][H][W][3] float32, each value the FP64 colour
+ * clipped to [0, 1] and rounded to nearest.  Computed in FP64 with the same
+ * 1/255 cutoff, near plane and frustum guard band as the abstract render;
+ * a pixel stops once its transmittance is below 1e-13 (the colour left out
+ * is below that).  One pose per pipeline pass (projection, binning, blend);
+ * uses the scene's workspace, so it must not overlap a render of the same
+ * scene.  AR_EINVAL for bad arguments or non-finite deltas. */
 int ar_render_concrete(ar_scene *scene, const ar_intrinsics *intr, const ar_nominal_pose *pose,
                        const double *deltas, int32_t n_poses, float *out, void *cuda_stream);
 

@@ -247,6 +247,11 @@ class Scene:
         ar_render_abstract(self.handle, make_intrinsics(cam), make_pose(cam), cells, len(cells), tile,
                            out_lower, out_upper, stream)
 
+    def render_concrete(self, cam, deltas, out, stream=0):
+        """Concrete renders at the poses deltas ([n][6]) into out ([n][H][W][3], device)."""
+        d = np.ascontiguousarray(np.asarray(deltas, dtype=np.float64).reshape(-1, 6))
+        ar_render_concrete(self.handle, make_intrinsics(cam), make_pose(cam), d, d.shape[0], out, stream)
+
     def render_plain_fp64(self, cam, cells_lo, cells_hi, out_lower, out_upper, tile: int = 0, stream=0):
         cells = make_cells(cells_lo, cells_hi)
         ar_render_abstract_plain_fp64(self.handle, make_intrinsics(cam), make_pose(cam), cells, len(cells), tile,

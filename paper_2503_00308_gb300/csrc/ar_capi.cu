@@ -334,6 +334,65 @@ int validate_call(const ar_intrinsics *in, const ar_nominal_pose *pose, const ar
         if (r_) return r_;         \
     } while (0)
 
+// Sizes the binning buffers of the workspace and runs the binning of n_pairs
+// (cell, Gaussian) pairs with ne events and nent (event, tile) entries.
+static int bin_pairs(Workspace &ws, const PixBox *boxes, const double *keys, uint64_t n_pairs, uint64_t n_gauss,
+                     int n_cells, uint64_t ne, uint64_t nent, int TS, int ntx, int n_tiles, cudaStream_t st,
+                     BinOut &bo, int &launches)
+{
+    const uint64_t n_seg = (uint64_t)n_cells * n_tiles;
+    const uint64_t nsc = n_pairs > ne ? n_pairs : ne;
+    const uint64_t nsort = ne > nent ? ne : nent;
+    const uint64_t hist_words = radix_hist_words(nsort > n_seg ? nsort : n_seg) + 64;
+    uint64_t scan_len = nsc > hist_words ? nsc : hist_words;
+    RK(ws.evk0.ensure(sizeof(uint64_t) * (ne + 1)));
+    RK(ws.evk1.ensure(sizeof(uint64_t) * (ne + 1)));
+    RK(ws.evv0.ensure(sizeof(uint32_t) * (ne + 1)));
+    RK(ws.evv1.ensure(sizeof(uint32_t) * (ne + 1)));
+    RK(ws.ents0.ensure(sizeof(uint32_t) * (nent + 1)));
+    RK(ws.ents1.ensure(sizeof(uint32_t) * (nent + 1)));
+    RK(ws.ente0.ensure(sizeof(uint32_t) * (nent + 1)));
+    RK(ws.ente1.ensure(sizeof(uint32_t) * (nent + 1)));
+    RK(ws.ua.ensure(sizeof(uint32_t) * (nsc + 1)));
+    RK(ws.ub.ensure(sizeof(uint32_t) * (nsc + 1)));
+    RK(ws.uc.ensure(sizeof(uint32_t) * (nsc + 1)));
+    RK(ws.ud.ensure(sizeof(uint32_t) * (nsc + 1)));
+    RK(ws.hist.ensure(sizeof(uint32_t) * hist_words));
+    RK(ws.scan.ensure(sizeof(uint32_t) * (scan_temp_words(scan_len) + 64)));
+    RK(ws.segs.ensure(sizeof(uint32_t) * n_seg));
+    RK(ws.sege.ensure(sizeof(uint32_t) * n_seg));
+    RK(ws.segk0.ensure(sizeof(uint32_t) * n_seg));
+    RK(ws.segk1.ensure(sizeof(uint32_t) * n_seg));
+    RK(ws.segv0.ensure(sizeof(uint32_t) * n_seg));
+    RK(ws.segv1.ensure(sizeof(uint32_t) * n_seg));
+    RK(ws.work.ensure(256));
+    BinArgs ba;
+    ba.boxes = boxes;
+    ba.keys = keys;
+    ba.n_pairs = n_pairs;
+    ba.n_gauss = n_gauss;
+    ba.n_cells = n_cells;
+    ba.n_events = ne;
+    ba.n_entries = nent;
+    ba.TS = TS; ba.ntx = ntx; ba.n_tiles = n_tiles;
+    ba.n_segments = n_seg;
+    ba.ev_key[0] = ws.evk0.as<uint64_t>(); ba.ev_key[1] = ws.evk1.as<uint64_t>();
+    ba.ev_val[0] = ws.evv0.as<uint32_t>(); ba.ev_val[1] = ws.evv1.as<uint32_t>();
+    ba.ent_seg[0] = ws.ents0.as<uint32_t>(); ba.ent_seg[1] = ws.ents1.as<uint32_t>();
+    ba.ent_ev[0] = ws.ente0.as<uint32_t>(); ba.ent_ev[1] = ws.ente1.as<uint32_t>();
+    ba.u32_a = ws.ua.as<uint32_t>(); ba.u32_b = ws.ub.as<uint32_t>();
+    ba.u32_c = ws.uc.as<uint32_t>(); ba.u32_d = ws.ud.as<uint32_t>();
+    ba.hist = ws.hist.as<uint32_t>();
+    ba.scan_tmp = ws.scan.as<uint32_t>();
+    ba.seg_start = ws.segs.as<uint32_t>();
+    ba.seg_end = ws.sege.as<uint32_t>();
+    ba.seg_k[0] = ws.segk0.as<uint32_t>(); ba.seg_k[1] = ws.segk1.as<uint32_t>();
+    ba.seg_v[0] = ws.segv0.as<uint32_t>(); ba.seg_v[1] = ws.segv1.as<uint32_t>();
+    if (run_binning(ba, bo, st, &launches))
+        return fail(AR_EDEVICE, "binning: %s", cudaGetErrorString(cudaGetLastError()));
+    return AR_OK;
+}
+
 // One batch of cells through the whole pipeline.  cc describes the batch
 // (n_cells = cells in the batch, slots shared by every batch of the call).
 // plain: FP64 records and the plain FP64 renderer instead of the FP32 ones.
@@ -379,56 +438,9 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
     if (nent >= (1ull << 32) - (1ull << 20))
         return fail(AR_ENOMEM, "%llu bin entries exceed the 32-bit index range; lower the workspace limit",
                     (unsigned long long)nent);
-    const uint64_t nsc = n_pairs > ne ? n_pairs : ne;
-    const uint64_t nsort = ne > nent ? ne : nent;
-    const uint64_t hist_words = radix_hist_words(nsort > n_seg ? nsort : n_seg) + 64;
-    uint64_t scan_len = nsc > hist_words ? nsc : hist_words;
-    RK(ws.evk0.ensure(sizeof(uint64_t) * (ne + 1)));
-    RK(ws.evk1.ensure(sizeof(uint64_t) * (ne + 1)));
-    RK(ws.evv0.ensure(sizeof(uint32_t) * (ne + 1)));
-    RK(ws.evv1.ensure(sizeof(uint32_t) * (ne + 1)));
-    RK(ws.ents0.ensure(sizeof(uint32_t) * (nent + 1)));
-    RK(ws.ents1.ensure(sizeof(uint32_t) * (nent + 1)));
-    RK(ws.ente0.ensure(sizeof(uint32_t) * (nent + 1)));
-    RK(ws.ente1.ensure(sizeof(uint32_t) * (nent + 1)));
-    RK(ws.ua.ensure(sizeof(uint32_t) * (nsc + 1)));
-    RK(ws.ub.ensure(sizeof(uint32_t) * (nsc + 1)));
-    RK(ws.uc.ensure(sizeof(uint32_t) * (nsc + 1)));
-    RK(ws.ud.ensure(sizeof(uint32_t) * (nsc + 1)));
-    RK(ws.hist.ensure(sizeof(uint32_t) * hist_words));
-    RK(ws.scan.ensure(sizeof(uint32_t) * (scan_temp_words(scan_len) + 64)));
-    RK(ws.segs.ensure(sizeof(uint32_t) * n_seg));
-    RK(ws.sege.ensure(sizeof(uint32_t) * n_seg));
-    RK(ws.segk0.ensure(sizeof(uint32_t) * n_seg));
-    RK(ws.segk1.ensure(sizeof(uint32_t) * n_seg));
-    RK(ws.segv0.ensure(sizeof(uint32_t) * n_seg));
-    RK(ws.segv1.ensure(sizeof(uint32_t) * n_seg));
-    RK(ws.work.ensure(256));
-    BinArgs ba;
-    ba.boxes = ws.boxes.as<PixBox>();
-    ba.keys = ws.keys.as<double>();
-    ba.n_pairs = n_pairs;
-    ba.n_gauss = (uint64_t)s->n;
-    ba.n_cells = n_cells;
-    ba.n_events = ne;
-    ba.n_entries = nent;
-    ba.TS = TS; ba.ntx = ntx; ba.n_tiles = n_tiles;
-    ba.n_segments = n_seg;
-    ba.ev_key[0] = ws.evk0.as<uint64_t>(); ba.ev_key[1] = ws.evk1.as<uint64_t>();
-    ba.ev_val[0] = ws.evv0.as<uint32_t>(); ba.ev_val[1] = ws.evv1.as<uint32_t>();
-    ba.ent_seg[0] = ws.ents0.as<uint32_t>(); ba.ent_seg[1] = ws.ents1.as<uint32_t>();
-    ba.ent_ev[0] = ws.ente0.as<uint32_t>(); ba.ent_ev[1] = ws.ente1.as<uint32_t>();
-    ba.u32_a = ws.ua.as<uint32_t>(); ba.u32_b = ws.ub.as<uint32_t>();
-    ba.u32_c = ws.uc.as<uint32_t>(); ba.u32_d = ws.ud.as<uint32_t>();
-    ba.hist = ws.hist.as<uint32_t>();
-    ba.scan_tmp = ws.scan.as<uint32_t>();
-    ba.seg_start = ws.segs.as<uint32_t>();
-    ba.seg_end = ws.sege.as<uint32_t>();
-    ba.seg_k[0] = ws.segk0.as<uint32_t>(); ba.seg_k[1] = ws.segk1.as<uint32_t>();
-    ba.seg_v[0] = ws.segv0.as<uint32_t>(); ba.seg_v[1] = ws.segv1.as<uint32_t>();
     BinOut bo;
-    if (run_binning(ba, bo, st, &launches))
-        return fail(AR_EDEVICE, "binning: %s", cudaGetErrorString(cudaGetLastError()));
+    RK(bin_pairs(ws, ws.boxes.as<PixBox>(), ws.keys.as<double>(), n_pairs, (uint64_t)s->n, n_cells, ne, nent, TS, ntx,
+                 n_tiles, st, bo, launches));
     if (profiling) CK(cudaEventRecord(ev[2], st));
     RenderLaunch rl;
     rl.recs = ws.recs.as<float>();
@@ -713,6 +725,65 @@ int ar_render_abstract_plain_fp64(ar_scene *s, const ar_intrinsics *in, const ar
 int ar_render_concrete(ar_scene *s, const ar_intrinsics *in, const ar_nominal_pose *pose, const double *deltas,
                        int32_t n_poses, float *out, void *stream)
 {
-    (void)s; (void)in; (void)pose; (void)deltas; (void)n_poses; (void)out; (void)stream;
-    return fail(AR_EINVAL, "concrete renderer not built in this library version");
+    if (!s) return fail(AR_EINVAL, "scene is null");
+    if (!deltas || !out) return fail(AR_EINVAL, "null argument");
+    if (n_poses < 1) return fail(AR_EINVAL, "n_poses must be >= 1");
+    // the intrinsics and pose checks of the abstract render, on a point cell
+    ar_pose_box pt;
+    for (int k = 0; k < MAXV; ++k) pt.lo[k] = pt.hi[k] = 0.0;
+    RK(validate_call(in, pose, &pt, 1, 16));
+    for (int64_t i = 0; i < (int64_t)n_poses * MAXV; ++i)
+        if (!std::isfinite(deltas[i])) return fail(AR_EINVAL, "non-finite pose delta");
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(s->device));
+    Workspace &ws = s->ws;
+    const int W = in->width, H = in->height, TS = 16;
+    const int ntx = (W + TS - 1) / TS, nty = (H + TS - 1) / TS, n_tiles = ntx * nty;
+    const size_t img = (size_t)W * H * 3;
+    if (s->n == 0) {
+        CK(cudaMemsetAsync(out, 0, sizeof(float) * img * n_poses, st));
+        return AR_OK;
+    }
+    CallConst cc;
+    std::memset(&cc, 0, sizeof cc);
+    cc.W = W; cc.H = H;
+    cc.fx = in->fx; cc.fy = in->fy; cc.cx = in->cx; cc.cy = in->cy; cc.near_plane = in->near_plane;
+    std::memcpy(cc.R0, pose->R_wc, sizeof cc.R0);
+    std::memcpy(cc.t0, pose->t, sizeof cc.t0);
+    cc.n_cells = 1;
+    cc.n_gauss = s->n;
+    const uint64_t n = (uint64_t)s->n;
+    if (!ws.h_counters) CK(cudaMallocHost(&ws.h_counters, 8 * sizeof(unsigned long long)));
+    RK(ws.cells_lohi.ensure(sizeof(double) * MAXV * n_poses));
+    RK(ws.cells.ensure(concrete_pose_bytes()));
+    RK(ws.recs.ensure(sizeof(double) * concrete_rec_width() * n));
+    RK(ws.boxes.ensure(sizeof(PixBox) * n));
+    RK(ws.keys.ensure(sizeof(double) * 2 * n));
+    RK(ws.counters.ensure(sizeof(unsigned long long) * 8));
+    CK(cudaMemcpyAsync(ws.cells_lohi.p, deltas, sizeof(double) * MAXV * n_poses, cudaMemcpyHostToDevice, st));
+    int launches = 0;
+    for (int p = 0; p < n_poses; ++p) {
+        float *o = out + img * p;
+        CK(cudaMemsetAsync(ws.counters.p, 0, sizeof(unsigned long long) * 8, st));
+        if (launch_concrete_pose(ws.cells_lohi.as<double>() + (size_t)MAXV * p, cc, ws.cells.p, st) ||
+            launch_concrete_prep(s->uw, s->Mw, s->tau, s->opac, s->rgb, cc, ws.cells.p, TS, ws.recs.as<double>(),
+                                 ws.boxes.as<PixBox>(), ws.keys.as<double>(), ws.counters.as<unsigned long long>(),
+                                 st))
+            return fail(AR_EDEVICE, "concrete prep launch: %s", cudaGetErrorString(cudaGetLastError()));
+        CK(cudaMemcpyAsync(ws.h_counters, ws.counters.p, sizeof(unsigned long long) * 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const uint64_t ne = 2 * ws.h_counters[2], nent = 2 * ws.h_counters[3];
+        if (ne == 0) {
+            CK(cudaMemsetAsync(o, 0, sizeof(float) * img, st));
+            continue;
+        }
+        if (nent >= (1ull << 32) - (1ull << 20)) return fail(AR_ENOMEM, "too many tile entries for one pose");
+        BinOut bo;
+        RK(bin_pairs(ws, ws.boxes.as<PixBox>(), ws.keys.as<double>(), n, n, 1, ne, nent, TS, ntx, n_tiles, st, bo,
+                     launches));
+        if (launch_concrete_render(ws.recs.as<double>(), ws.boxes.as<PixBox>(), ws.segs.as<uint32_t>(),
+                                   ws.sege.as<uint32_t>(), bo.ent_ev, bo.ev_val, bo.ev_key, W, H, ntx, n_tiles, o, st))
+            return fail(AR_EDEVICE, "concrete render launch: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    return AR_OK;
 }

@@ -45,6 +45,16 @@ int launch_render_plain(int M, int TS, const RenderLaunch &a, cudaStream_t st);
 int launch_record_build(int M, const double *vN, const CallConst &cc, const void *cells, int64_t n_gauss,
                         const uint32_t *work, const uint32_t *count, float *recs, unsigned long long *counters,
                         cudaStream_t st);
+// concrete render (k_concrete.cu)
+size_t concrete_pose_bytes();
+int concrete_rec_width();
+int launch_concrete_pose(const double *delta, const CallConst &cc, void *pose, cudaStream_t st);
+int launch_concrete_prep(const float *uw, const double *Mw, const double *tau, const float *opac, const float *rgb,
+                         const CallConst &cc, const void *pose, int TS, double *recs, PixBox *boxes, double *keys,
+                         unsigned long long *counters, cudaStream_t st);
+int launch_concrete_render(const double *recs, const PixBox *boxes, const uint32_t *seg_start, const uint32_t *seg_end,
+                           const uint32_t *ent_ev, const uint32_t *ev_val, const uint64_t *ev_key, int W, int H,
+                           int ntx, int n_tiles, float *out, cudaStream_t st);
 int launch_scene_prep(const float *logscale, const float *quat, const float *opacity, int64_t n, double *Mw,
                       double *tau, cudaStream_t st);
 int launch_pose_prep(const float *uw, const double *Mw, int64_t n, const CallConst &cc, double *vN,
