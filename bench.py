@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="object300k")
-    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--tile", type=int, default=0, help="0: the library's autotuner picks the tile edge")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-window", type=int, default=16, help="edge of the oracle's pixel sample")
@@ -365,7 +365,8 @@ def run_ours(args, rank, world, local, pg):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name, "gaussians": w.scene.n, "image": "%dx%d" % (cam.width, cam.height),
-                   "cells": nc, "pose_vars": M, "tile": args.tile,
+                   "cells": nc, "pose_vars": M, "tile": stats["tile"],
+                   "tile_choice": "autotuned" if args.tile == 0 else "fixed",
                    "l2": "working set (records + bins, tens of GB) far larger than L2; no flush needed"},
         "clocks": clk,
         "e2e": e2e,

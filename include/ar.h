@@ -120,7 +120,9 @@ int ar_scene_destroy(ar_scene *scene);
  *   tile: 0 = choose, else 8 or 16 (screen tile edge of the binning; the
  *   bounds do not depend on it beyond 1e-7: a pixel stops sweeping once what
  *   is left of its tile's list can move its bounds by less than 5e-8, and
- *   widens them by that much).
+ *   widens them by that much).  With 0, the first call for a given image
+ *   size and number of pose variables times the pipeline with both edges on
+ *   its first two cells and keeps the faster for the scene (autotuner).
  *   out_lower, out_upper: device pointers, float32 [n_cells][H][W][3] each,
  *   owned by the caller.
  * Work is enqueued on cuda_stream; the call returns after the last launch is

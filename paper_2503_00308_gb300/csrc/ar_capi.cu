@@ -532,6 +532,58 @@ int run_windowed_render(int M, int TS, RenderLaunch rl, const CallConst &cc, con
     return AR_OK;
 }
 
+// The tile autotuner: for tile = 0, the first render of a scene at a given
+// image size and number of pose variables times the whole pipeline with tile
+// edges 16 and 8 on the first two cells of the call (each twice, keeping the
+// second timing, so that workspace growth is not counted), and keeps the
+// faster for every later render with the same key.  The bounds do not depend
+// on the tile beyond 1e-7.
+static int tuned_tile(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_nominal_pose *pose,
+                      const ar_pose_box *cells, int32_t n_cells, float *out_lo, float *out_hi, cudaStream_t st,
+                      int64_t ws_limit, int *TS)
+{
+    int m_active = 0;
+    for (int k = 0; k < MAXV; ++k) {
+        bool act = false;
+        for (int c = 0; c < n_cells; ++c) act = act || cells[c].hi[k] > cells[c].lo[k];
+        m_active += act;
+    }
+    const int M = m_active <= 1 ? 1 : (m_active <= 4 ? 4 : 6);
+    std::lock_guard<std::mutex> lock(s->tune_mu);
+    for (const TunedTile &t : s->tuned)
+        if (t.W == in->width && t.H == in->height && t.M == M) {
+            *TS = t.TS;
+            return AR_OK;
+        }
+    const int32_t k = n_cells < 2 ? n_cells : 2;
+    const int cand[2] = {16, 8};
+    float best = 0.f;
+    int best_ts = 16;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int r = AR_OK;
+    for (int i = 0; i < 4 && r == AR_OK; ++i) {
+        const int ts = cand[i % 2];
+        CK(cudaEventRecord(e0, st));
+        r = render_core(s, ws, in, pose, cells, k, ts, out_lo, out_hi, st, false, nullptr, false, ws_limit);
+        CK(cudaEventRecord(e1, st));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (i >= 2 && (i == 2 || ms < best)) {
+            best = ms;
+            best_ts = ts;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    RK(r);
+    s->tuned.push_back(TunedTile{in->width, in->height, M, best_ts});
+    *TS = best_ts;
+    return AR_OK;
+}
+
 int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_nominal_pose *pose,
                 const ar_pose_box *cells, int32_t n_cells, int32_t tile, float *out_lo, float *out_hi,
                 cudaStream_t st, bool profiling, ar_render_stats *stats, bool plain, int64_t ws_limit)
@@ -539,6 +591,8 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
     RK(validate_call(in, pose, cells, n_cells, tile));
     if (!out_lo || !out_hi) return fail(AR_EINVAL, "null output");
     CK(cudaSetDevice(s->device));
+    if (tile == 0 && !plain && s->n > 0)
+        RK(tuned_tile(s, ws, in, pose, cells, n_cells, out_lo, out_hi, st, ws_limit, &tile));
     const int W = in->width, H = in->height;
     const int TS = tile ? tile : 16;
     const size_t out_words = (size_t)n_cells * W * H * 3;

@@ -4,6 +4,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <vector>
 
 #include "ar.h"
@@ -47,6 +48,9 @@ int validate_call(const ar_intrinsics *in, const ar_nominal_pose *pose, const ar
                   int32_t tile);
 struct RenderLaunch;
 struct CallConst;
+struct TunedTile {
+    int W, H, M, TS;
+};
 // The FP32 render of one batch in windowed rounds (see render_kernel):
 // demand -> build -> render per round, windows w0, 8192, then unlimited.
 // state [n_pairs] (zeroed here), wlist [n_pairs], act0/act1 [n_seg], words [4];
@@ -77,4 +81,7 @@ struct ar_scene {
     bool profiling = false;
     ar_render_stats stats;
     cudaStream_t stats_stream = nullptr;
+    // tile edges chosen by the autotuner, per (width, height, pose variables)
+    std::mutex tune_mu;
+    std::vector<ar::TunedTile> tuned;
 };

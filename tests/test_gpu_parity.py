@@ -252,3 +252,26 @@ def test_guard_band_parity(arlib, orc):
         poses = synth.sample_poses(np.random.default_rng(c), lo[c], hi[c], 300)
         worst, nv = orc.check_samples(sc, cam, poses, glo[c], ghi[c])
         assert nv == 0, worst
+
+
+def test_autotuned_tile(arlib):
+    """tile = 0: the autotuner picks 8 or 16 once per (size, pose variables)
+    and the bounds equal those of that tile edge."""
+    sc = synth.object_scene(1500, 6)
+    cam = synth.look_camera(50, 38, 60.0, centre=(0, 0, -4))
+    lo, hi = synth.cell_grid([0.03, 0.0, 0.03, 0.0, 0.01, 0.0], [2, 1, 2, 1, 1, 1])
+    s = arlib.Scene(sc)
+    arlib.ar_set_profiling(s.handle, True)
+    outs = []
+    for tile in (0, 0):
+        a = torch.empty((lo.shape[0], cam.height, cam.width, 3), device="cuda")
+        b = torch.empty_like(a)
+        s.render(cam, lo, hi, a, b, tile=tile)
+        outs.append((a, b, arlib.ar_last_render_stats(s.handle)["tile"]))
+    assert outs[0][2] in (8, 16) and outs[1][2] == outs[0][2]
+    a = torch.empty_like(outs[0][0])
+    b = torch.empty_like(a)
+    s.render(cam, lo, hi, a, b, tile=outs[0][2])
+    torch.cuda.synchronize()
+    assert torch.equal(a, outs[0][0]) and torch.equal(b, outs[0][1]) and torch.equal(a, outs[1][0])
+    s.close()
