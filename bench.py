@@ -43,12 +43,12 @@ def flops_per_triple(M: int) -> int:
 
 # DRAM bytes of the render kernel per opacity evaluation, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the first 4 cells of the
-# 300k-Gaussian workload: 68.6 MB over 117.5M evaluations.  Valid only for the
+# 300k-Gaussian workload: 73.4 MB over 117.5M evaluations.  Valid only for the
 # kernel sources it was taken from (their SHA-256 below); otherwise the
 # roofline's traffic is reported as null.
-RENDER_TRAFFIC = {"bytes_per_evaluation": 68600576 / 117536120,
+RENDER_TRAFFIC = {"bytes_per_evaluation": 73403904 / 117536086,
                   "sources": ["k_render.cuh", "ar_num.cuh", "ar_common.cuh", "k_inst.cuh"],
-                  "sha256": "366f2b4bb4533d70462849c1c4088eb6e03f7b41d4cbab5fe02231feeaa1b6fb"}
+                  "sha256": "21a8df0badabdb12ad77925df52ffc91993192c249ad80585e0eea9d989fe0d1"}
 
 
 def render_traffic(n_evaluated: int):
