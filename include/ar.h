@@ -191,7 +191,7 @@ int ar_render_concrete(ar_scene *scene, const ar_intrinsics *intr, const ar_nomi
  * ar_render_abstract splits the cells of a call into batches whose
  * per-(Gaussian, cell) records take about a third of this limit, and runs the
  * pipeline once per batch (the bounds are the same as in one batch).
- * Default 24 GiB. */
+ * Default 64 GiB. */
 int ar_set_workspace_limit(ar_scene *scene, int64_t bytes);
 
 /* Stage timing with CUDA events on the render stream (on = 1) or off (0). */

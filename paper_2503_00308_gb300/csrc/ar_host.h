@@ -76,7 +76,7 @@ struct ar_scene {
     float *uw = nullptr, *ls = nullptr, *quat = nullptr, *opac = nullptr, *rgb = nullptr;
     double *Mw = nullptr, *tau = nullptr;
     float k_open = 1.f;  // 1 / (1 - largest opacity), rounded up (bounds skipped lower-sum terms)
-    int64_t ws_limit = int64_t(24) << 30;  // workspace limit that sizes the cell batches
+    int64_t ws_limit = int64_t(64) << 30;  // workspace limit that sizes the cell batches
     ar::Workspace ws;
     bool profiling = false;
     ar_render_stats stats;

@@ -378,6 +378,29 @@ __global__ void seg_bounds_kernel(const uint32_t *__restrict__ key, uint64_t n, 
     if (i == n - 1 || key[i + 1] != k) end[s] = (uint32_t)(i + 1);
 }
 
+// Packed keys come out of the tile sort in ascending order (tile, then cell),
+// so each segment's range is found by two binary searches over the keys.
+__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t *__restrict__ a, uint32_t n, uint32_t v)
+{
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = lo + (hi - lo) / 2;
+        if (a[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+__global__ void seg_bounds_search_kernel(const uint32_t *__restrict__ key, uint32_t n, int cb, int n_cells,
+                                         int n_tiles, uint32_t *__restrict__ start, uint32_t *__restrict__ end)
+{
+    const uint64_t sg = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (sg >= (uint64_t)n_cells * (uint64_t)n_tiles) return;
+    const uint32_t cell = (uint32_t)(sg / (uint64_t)n_tiles), tile = (uint32_t)(sg % (uint64_t)n_tiles);
+    const uint32_t k = (tile << cb) | cell;
+    const uint32_t b = lower_bound_u32(key, n, k);
+    start[sg] = b;
+    end[sg] = (b < n && key[b] == k) ? (k == 0xffffffffu ? n : lower_bound_u32(key, n, k + 1u)) : b;
+}
+
 __global__ void iota_kernel(uint32_t *__restrict__ p, uint64_t n)
 {
     const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
@@ -471,12 +494,19 @@ int run_binning(const BinArgs &a, BinOut &o, cudaStream_t st, int *launches)
     o.ent_seg = a.ent_seg[h];
     o.ent_ev = a.ent_ev[h];
     // 6. segment bounds
-    cudaMemsetAsync(a.seg_start, 0, sizeof(uint32_t) * a.n_segments, st);
-    cudaMemsetAsync(a.seg_end, 0, sizeof(uint32_t) * a.n_segments, st);
-    if (a.n_entries) {
-        seg_bounds_kernel<<<blocks_for(a.n_entries, T), T, 0, st>>>(o.ent_seg, a.n_entries, packed ? cb : -1,
-                                                                     a.n_tiles, a.seg_start, a.seg_end);
+    if (packed) {
+        seg_bounds_search_kernel<<<blocks_for(a.n_segments, T), T, 0, st>>>(o.ent_seg, (uint32_t)a.n_entries, cb,
+                                                                            a.n_cells, a.n_tiles, a.seg_start,
+                                                                            a.seg_end);
         ++*launches;
+    } else {
+        cudaMemsetAsync(a.seg_start, 0, sizeof(uint32_t) * a.n_segments, st);
+        cudaMemsetAsync(a.seg_end, 0, sizeof(uint32_t) * a.n_segments, st);
+        if (a.n_entries) {
+            seg_bounds_kernel<<<blocks_for(a.n_entries, T), T, 0, st>>>(o.ent_seg, a.n_entries, -1, a.n_tiles,
+                                                                         a.seg_start, a.seg_end);
+            ++*launches;
+        }
     }
     // 7. schedule: segments by decreasing length (load balance of the render)
     seg_len_kernel<<<blocks_for(a.n_segments, T), T, 0, st>>>(a.seg_start, a.seg_end, a.n_segments, a.seg_k[0],
