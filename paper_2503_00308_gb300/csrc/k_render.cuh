@@ -278,8 +278,8 @@ struct EvInfo {
 };
 
 // Early exit.  Write PA, PB for the running transmittance products and
-// n_open for the Gaussians of this pixel whose lower endpoint has been swept
-// but not yet their upper one.  Every depth-key interval is open (klo < khi:
+// "open" for the Gaussians of this pixel whose lower endpoint has been swept
+// but not yet their upper one (n_open of them).  Every depth-key interval is open (klo < khi:
 // the keys are padded), so the lower endpoint of a Gaussian that has not yet
 // started precedes, with a strictly smaller key, the upper endpoint of every
 // Gaussian behind it.
@@ -293,15 +293,26 @@ struct EvInfo {
 //    Gaussians not yet started, taken in the order of their upper endpoints,
 //    T_lo(i_k) <= PA prod_{l<k} (1 - a_hi(i_l)) (the division by 1 - a_hi at
 //    the upper endpoint removes i_k's own factor), so their terms telescope
-//    to at most PA; each open Gaussian adds at most PA / (1 - o_max).  So
-//    the remaining terms move the minimum over the cell by at most
-//    El = PA (1 + n_open / (1 - o_max)) (times 1.01 for the rounding of PA),
-//    and once (constant - radius) + El <= 0 in every channel the clipped
-//    bound is 0.
+//    to at most PA; an open Gaussian i adds at most T_lo(i) a_hi(i) <=
+//    PA a_hi(i) / (1 - a_hi(i)).  open_w is the sum of these ratios over the
+//    open Gaussians, each rounded up and kept with upward-rounded additions
+//    and subtractions (so it is never below the exact sum); n_open / (1 -
+//    o_max) bounds it too.  So the remaining terms move the minimum over the
+//    cell by at most El = PA (1 + min(open_w, n_open / (1 - o_max))) (times
+//    1.01 for the rounding of PA), and once (constant - radius) + El <= 0 in
+//    every channel the clipped bound is 0.
 // Otherwise a side also stops once its E is below EXIT_EPS; its bound is then
 // widened by E, which keeps it sound and within EXIT_EPS of the full sweep.
 // A pixel stops when both sides have; a tile stops when all its pixels have.
 constexpr float EXIT_EPS = 5e-8f;
+
+// a / (1 - a) rounded up, for 0 <= a < 1 (__fdividef is within 2 ulp here;
+// the factor 1 + 2^-21 covers that)
+__device__ __forceinline__ float open_ratio_up(float a)
+{
+    const float den = __fsub_rd(1.f, a);
+    return den > 0.f ? __fmul_ru(__fdividef(a, den), 1.000000477f) : 3.0e38f;
+}
 
 // Shared-memory layout of the render kernel (dynamic; about 100 KB at six
 // pose variables, tile 16 and a ring of 6, so two CTAs fit on an SM):
@@ -401,7 +412,8 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
         lo.init();
         hi.init();
         float PA = 1.f, PB = 1.f, PAp = 1.f, PBp = 1.f;
-        int n_open = 0;  // Gaussians of this pixel between their two endpoints
+        int n_open = 0;      // Gaussians of this pixel between their two endpoints
+        float open_w = 0.f;  // sum over them of a_hi / (1 - a_hi), rounded up
         uint32_t c_rec = 0xffffffffu;  // register copy of the latest evaluation
         AlphaOut<M> cache;
 #pragma unroll
@@ -450,7 +462,8 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
             if (!done) {
                 const float left = (float)(b1 - base);
                 // PA is rounded down; 1.01 covers its relative error for < 10^5 factors
-                const float elo2 = __fmul_ru(__fmul_ru(PA, 1.01f), __fmaf_ru((float)n_open, k_open, 1.f));
+                const float ow = fminf(open_w, __fmul_ru((float)n_open, k_open));
+                const float elo2 = __fmul_ru(__fmul_ru(PA, 1.01f), __fadd_ru(ow, 1.f));
                 const float ehi2 = __fmul_ru(1.1f, __fmul_ru(left, PB));
                 bool lo_zero = true, hi_one = true;
 #pragma unroll
@@ -523,6 +536,7 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
                 if (lower) {
                     hi.add(PB, col, cache.U, cache.rU);
                     PAp = __fmul_rd(PAp, __fsub_rd(1.f, cache.ahi));
+                    open_w = __fadd_ru(open_w, open_ratio_up(cache.ahi));
                     const int k = (int)(head % RING);
                     ++head;
                     s_rid[k * NT + tid] = ev.rec;
@@ -534,6 +548,7 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
 #pragma unroll
                     for (int j = 0; j < M; ++j) pp[(4 + j) * NT] = cache.L.c[j];
                 } else {
+                    open_w = fmaxf(0.f, __fsub_ru(open_w, open_ratio_up(cache.ahi)));
                     const uint32_t flags = __float_as_uint(r[RL::FLAGS]);
                     float T = PA;
                     if (flags & F_OPEN) {
