@@ -98,6 +98,22 @@ def dist_setup(args):
     return rank, world, local, pg
 
 
+def max_over_ranks(x: float, pg) -> float:
+    """The maximum of x over all ranks (x itself without a process group)."""
+    if pg is None:
+        return x
+    import torch
+    dev = "cuda" if pg.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Units all ranks processed per second, timed by the slowest rank."""
+    return units_per_rank * world / (ms_max / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle samples during the timed region."""
 
@@ -327,14 +343,11 @@ def run_ours(args, rank, world, local, pg):
     ev1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop() if clocks else None
-    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, pg)
     if pg is not None:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
         pg.barrier()
     units = w.pixel_cells() * world
-    value = units / (ms / 1e3)
+    value = whole_job_rate(w.pixel_cells(), world, ms)
 
     # end to end through the host-buffer entry point: per step the pose cells
     # go host -> device and both bound images come back device -> host
@@ -347,11 +360,7 @@ def run_ours(args, rank, world, local, pg):
         t0 = time.perf_counter()
         for _ in range(args.steps):
             ar.ar_render_abstract_host(s.handle, intr, pose, cells, nc, args.tile, h_lo, h_hi, sp)
-        dt = (time.perf_counter() - t0) / args.steps
-        if pg is not None:
-            t = torch.tensor([dt], device="cuda")
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks((time.perf_counter() - t0) / args.steps, pg)
         e2e = {"value": units / dt, "unit": UNIT, "h2d_bytes_per_step": nc * 96,
                "d2h_bytes_per_step": 2 * out_lo.numel() * 4}
     if rank != 0:
