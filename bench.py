@@ -46,9 +46,9 @@ def flops_per_triple(M: int) -> int:
 # 300k-Gaussian workload: 73.4 MB over 117.5M evaluations.  Valid only for the
 # kernel sources it was taken from (their SHA-256 below); otherwise the
 # roofline's traffic is reported as null.
-RENDER_TRAFFIC = {"bytes_per_evaluation": 73403904 / 117536086,
+RENDER_TRAFFIC = {"bytes_per_evaluation": (43775232 + 18682368) / 101959073,
                   "sources": ["k_render.cuh", "ar_num.cuh", "ar_common.cuh", "k_inst.cuh"],
-                  "sha256": "21a8df0badabdb12ad77925df52ffc91993192c249ad80585e0eea9d989fe0d1"}
+                  "sha256": "04e746fa92b13294c1124e2869bfbcb00ce3d59b4b6fc682261cb5563aafcdb5"}
 
 
 def render_traffic(n_evaluated: int):

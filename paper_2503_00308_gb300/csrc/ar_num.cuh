@@ -47,6 +47,24 @@ template <> struct Num<float> {
     __device__ static __forceinline__ float sqrt_ru(float a) { return __fsqrt_ru(a); }
     // a / b to a few ulp, for weights where any value in [0, 1] is sound
     __device__ static __forceinline__ float div_weight(float a, float b) { return __fdividef(a, b); }
+    // a / b rounded up (div_pos_up) or down (div_pos_dn) for a >= 0, b > 0.
+    // CUDA documents __fdividef as within 2 ulp for b in [2^-126, 2^126]; with
+    // a >= 2^-100 and b in [2^-120, 2^20] the quotient is normal, so its
+    // relative error is at most 2^-22 and a directed product with 1 +- 2^-21
+    // moves it past the exact value.  Other operands take the correctly
+    // rounded division.
+    __device__ static __forceinline__ bool fast_div_ok(float a, float b)
+    {
+        return a >= 0x1p-100f && b >= 0x1p-120f && b <= 0x1p20f;
+    }
+    __device__ static __forceinline__ float div_pos_up(float a, float b)
+    {
+        return fast_div_ok(a, b) ? __fmul_ru(__fdividef(a, b), 1.f + 4.76837158203125e-7f) : __fdiv_ru(a, b);
+    }
+    __device__ static __forceinline__ float div_pos_dn(float a, float b)
+    {
+        return fast_div_ok(a, b) ? __fmul_rd(__fdividef(a, b), 1.f - 4.76837158203125e-7f) : __fdiv_rd(a, b);
+    }
     __device__ static __forceinline__ float abs(float a) { return fabsf(a); }
     __device__ static __forceinline__ float max(float a, float b) { return fmaxf(a, b); }
     __device__ static __forceinline__ float min(float a, float b) { return fminf(a, b); }
@@ -82,6 +100,8 @@ template <> struct Num<double> {
     __device__ static __forceinline__ double div_ru(double a, double b) { return __ddiv_ru(a, b); }
     __device__ static __forceinline__ double sqrt_ru(double a) { return __dsqrt_ru(a); }
     __device__ static __forceinline__ double div_weight(double a, double b) { return a / b; }
+    __device__ static __forceinline__ double div_pos_up(double a, double b) { return __ddiv_ru(a, b); }
+    __device__ static __forceinline__ double div_pos_dn(double a, double b) { return __ddiv_rd(a, b); }
     __device__ static __forceinline__ double abs(double a) { return fabs(a); }
     __device__ static __forceinline__ double max(double a, double b) { return fmax(a, b); }
     __device__ static __forceinline__ double min(double a, double b) { return fmin(a, b); }
@@ -176,6 +196,16 @@ template <int M, class R, bool DN> struct Acc {
         f.k = DN ? N::fma_rd(a, F.k, f.k) : N::fma_ru(a, F.k, f.k);
         rs = N::fma_ru(N::abs(a), r, rs);
         ++n;
+    }
+    // An upper bound on sum_j |c_j| of the result without summing it: each
+    // coefficient is a chain of n rounded FMAs, so sum_j |c_j| <= (1 + gamma_n)
+    // sum_t |a_t| r_t, plus a floor for subnormal rounding.  Tight where the
+    // terms cannot cancel (one term).
+    __device__ __forceinline__ R radius_bound() const
+    {
+        using N = Num<R>;
+        const R g = N::mul_ru((R)n, N::mul_ru(N::U, (R)1.000244140625));
+        return N::fma_ru(rs, N::add_ru((R)1, g), N::TINY);
     }
     __device__ __forceinline__ LF<M, R> result() const
     {

@@ -149,16 +149,14 @@ __device__ __forceinline__ void pixel_alpha(const R *__restrict__ r, R ux, R uy,
     LF<M, R> La = la.result();
     // upper: o (e(xl) + s (x - xl)) with x <= -m.lo/2
     const R w = N::sub_rd(xu, xl);
-    R s = (w > R(0)) ? N::div_ru(N::sub_ru(eu_up, el_up), w) : eu_up;
+    R s = (w > R(0)) ? N::div_pos_up(N::sub_ru(eu_up, el_up), w) : eu_up;
     s = N::min(N::max(s, R(0)), N::BIG);
     const R e2 = N::mul_ru(o, el_up), s2 = N::mul_ru(o, s);
     Acc<M, R, false> ua;
     ua.init(N::fma_ru(-s2, xl, e2));
     ua.term_ck(R(-0.5) * s2, m.c, m.klo, m.r);
     LF<M, R> Ua = ua.result();
-    R rUa = 0;
-#pragma unroll
-    for (int j = 0; j < M; ++j) rUa = N::add_ru(rUa, N::abs(Ua.c[j]));
+    const R rUa = ua.radius_bound();
     const R amax = N::add_ru(Ua.k, rUa);
     // blend the upper form toward the constant o where its maximum exceeds o
     // The blend weights lam, psi2 (where m_lo > tau), psi (where m_hi <= tau)
@@ -177,17 +175,12 @@ __device__ __forceinline__ void pixel_alpha(const R *__restrict__ r, R ux, R uy,
         u1.init(N::mul_ru(keep, N::mul_ru(N::sub_ru(R(1), lam), o)));
         u1.term(keep * lam, Ua, rUa);
         out.U = u1.result();
+        out.rU = u1.radius_bound();
     }
-    R rU = 0;
-#pragma unroll
-    for (int j = 0; j < M; ++j) rU = N::add_ru(rU, N::abs(out.U.c[j]));
-    out.rU = rU;
-    out.ahi = N::min(o, N::add_ru(out.U.k, rU));
+    out.ahi = N::min(o, N::add_ru(out.U.k, out.rU));
     // lower: subtract psi/255, then blend toward 0 where the form dips below 0
     La.k = N::sub_rd(La.k, N::mul_ru(psi, R(ALPHA_MIN_UP)));
-    R rLa = 0;
-#pragma unroll
-    for (int j = 0; j < M; ++j) rLa = N::add_ru(rLa, N::abs(La.c[j]));
+    const R rLa = la.radius_bound();
     const R l2min = N::sub_rd(La.k, rLa), l2max = La.k + rLa;
     const R mu = (l2min >= R(0)) ? R(1) : ((l2max <= R(0)) ? R(0) : clamp01(N::div_weight(l2max, l2max - l2min)));
     if ((flags & F_STRADDLE) || mu == R(0)) {
@@ -205,11 +198,8 @@ __device__ __forceinline__ void pixel_alpha(const R *__restrict__ r, R ux, R uy,
         l1.init(0);
         l1.term(mu, La, rLa);
         out.L = l1.result();
-        R rL = 0;
-#pragma unroll
-        for (int j = 0; j < M; ++j) rL = N::add_ru(rL, N::abs(out.L.c[j]));
-        out.rL = rL;
-        out.alo = N::max(R(0), N::sub_rd(out.L.k, rL));
+        out.rL = l1.radius_bound();
+        out.alo = N::max(R(0), N::sub_rd(out.L.k, out.rL));
     }
 }
 
@@ -218,11 +208,13 @@ __device__ __forceinline__ void pixel_alpha(const R *__restrict__ r, R ux, R uy,
 //   each step's error <= min(u * sum_j |acc_j|, w * r_F), and
 //   sum_j |acc_j| <= Q = sum of w * r_F so far (times 1.01 for the error
 //   already accumulated, valid below 10^5 steps in FP32).
+// Colours lie in [0, 1], so every channel's weight w = T c is at most T and
+// one pair Q, err computed with T in place of w bounds all three channels.
 template <int M, bool DN, class R = float> struct ColourAcc {
     using N = Num<R>;
     R c[3][M];
     R k[3];
-    R q[3], err[3];
+    R q, err;
     int steps;
     __device__ __forceinline__ void init()
     {
@@ -230,8 +222,10 @@ template <int M, bool DN, class R = float> struct ColourAcc {
         for (int ch = 0; ch < 3; ++ch) {
 #pragma unroll
             for (int j = 0; j < M; ++j) c[ch][j] = 0;
-            k[ch] = 0; q[ch] = 0; err[ch] = 0;
+            k[ch] = 0;
         }
+        q = 0;
+        err = 0;
         steps = 0;
     }
     __device__ __forceinline__ void add(R T, const R *col, const LF<M, R> &F, R rF)
@@ -243,10 +237,10 @@ template <int M, bool DN, class R = float> struct ColourAcc {
 #pragma unroll
             for (int j = 0; j < M; ++j) c[ch][j] = N::fma_rn(w, F.c[j], c[ch][j]);
             k[ch] = DN ? N::fma_rd(w, F.k, k[ch]) : N::fma_ru(w, F.k, k[ch]);
-            const R t = N::mul_ru(w, rF);
-            q[ch] = N::add_ru(q[ch], t);
-            err[ch] = N::add_ru(err[ch], N::min(N::mul_ru(q[ch], u), t));
         }
+        const R t = N::mul_ru(T, rF);
+        q = N::add_ru(q, t);
+        err = N::add_ru(err, N::min(N::mul_ru(q, u), t));
         ++steps;
     }
     __device__ __forceinline__ R radius(int ch) const
@@ -254,7 +248,7 @@ template <int M, bool DN, class R = float> struct ColourAcc {
         R r = 0;
 #pragma unroll
         for (int j = 0; j < M; ++j) r = N::add_ru(r, N::abs(c[ch][j]));
-        return N::add_ru(N::add_ru(r, err[ch]), N::mul_ru((R)steps, N::TINY));
+        return N::add_ru(N::add_ru(r, err), N::mul_ru((R)steps, N::TINY));
     }
     // the outward concretisation of the accumulated form
     __device__ __forceinline__ R bound(int ch) const
@@ -268,7 +262,7 @@ template <int M, bool DN, class R = float> struct ColourAcc {
         R r = 0;
 #pragma unroll
         for (int j = 0; j < M; ++j) r = N::add_rd(r, N::abs(c[ch][j]));
-        return N::sub_ru(k[ch], N::add_rd(r, err[ch]));
+        return N::sub_ru(k[ch], N::add_rd(r, err));
     }
 };
 
@@ -553,7 +547,7 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
                     float T = PA;
                     if (flags & F_OPEN) {
                         const float den = __fsub_ru(1.f, cache.ahi);
-                        T = (den > 0.f) ? __fdiv_rd(PA, den) : 0.f;
+                        T = (den > 0.f) ? Num<float>::div_pos_dn(PA, den) : 0.f;
                     }
                     lo.add(T, col, cache.L, cache.rL);
                     PBp = __fmul_ru(PBp, __fsub_ru(1.f, cache.alo));
