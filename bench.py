@@ -43,7 +43,7 @@ def flops_per_triple(M: int) -> int:
 
 # DRAM bytes of the render kernel per opacity evaluation, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the first 4 cells of the
-# 300k-Gaussian workload: 73.4 MB over 117.5M evaluations.  Valid only for the
+# 300k-Gaussian workload: 62.5 MB over 102.0M evaluations.  Valid only for the
 # kernel sources it was taken from (their SHA-256 below); otherwise the
 # roofline's traffic is reported as null.
 RENDER_TRAFFIC = {"bytes_per_evaluation": (43775232 + 18682368) / 101959073,
@@ -391,7 +391,7 @@ def run_ours(args, rank, world, local, pg):
                       "render": stats["ms_render"], "total": stats["ms_total"]},
         "counts": {"records": stats["n_records"], "entries": stats["n_entries"], "triples": stats["n_triples"],
                    "evaluated": stats["n_evaluated"], "reevaluated": stats["n_reevaluated"],
-                   "fallback": stats["n_fallback"], "built": stats["n_built"], "restarted": stats["n_restarted"]},
+                   "fallback": stats["n_fallback"], "split": stats["n_split"], "built": stats["n_built"], "restarted": stats["n_restarted"]},
     }
     if args.plain_cells > 0:
         line["plain_path"] = plain_path(ar, s, w, intr, pose, args, sp, value)

@@ -75,7 +75,8 @@ typedef struct ar_render_stats {
     int64_t n_entries;          /* (Gaussian, cell, tile) bin entries (2 events each) */
     int64_t n_triples;          /* (pixel, Gaussian, cell) triples inside a screen box */
     int64_t n_fallback;         /* (Gaussian, cell) pairs where MatrixInv's assertion failed
-                                   (among the pairs whose records were built) */
+                                   even on the split pieces of the cell, so that the opacity is
+                                   bounded by [0, o] (among the pairs whose records were built) */
     int32_t n_launches;         /* kernels launched by the render */
     int32_t tile;               /* tile edge used (pixels) */
     int32_t m_vars;             /* pose variables carried by the linear forms */
@@ -92,6 +93,9 @@ typedef struct ar_render_stats {
                                    beyond their window of built records, then swept again */
     float ms_build;             /* record value parts built on demand (included in neither
                                    ms_prep nor ms_render; ms_render is the per-pixel sweep) */
+    int64_t n_split;            /* (Gaussian, cell) pairs whose MatrixInv held only after the
+                                   cell was split into pieces (Sec. 3.1, adjustment (2); among
+                                   the pairs whose records were built) */
 } ar_render_stats;
 
 /* Create a scene from n Gaussians <uw, Mw, o, c> (Sec. 2.2).  Mw is given by

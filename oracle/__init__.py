@@ -52,6 +52,8 @@ def _load():
         lib.orc_records.restype = I
         lib.orc_matrixinv_interval.argtypes = [P, P, I, I, P, P, P]
         lib.orc_matrixinv_interval.restype = I
+        lib.orc_matrixinv_cell.argtypes = [P, P, I, P, P, P]
+        lib.orc_matrixinv_cell.restype = I
         lib.orc_relax_mul.argtypes = [P, P, P]
         lib.orc_relax_sq.argtypes = [P, P]
         lib.orc_rot_forms.argtypes = [P, P, P]
@@ -141,10 +143,11 @@ def records(scene, cam, cell_lo, cell_hi) -> dict:
     lib = _load()
     s = _scene_args(scene)
     intr, R0, t0 = _cam_args(cam)
-    out = np.zeros((scene.n, 10), dtype=np.float64)
+    out = np.zeros((scene.n, 13), dtype=np.float64)
     lib.orc_records(*[_p(a) for a in s], scene.n, _p(intr), _p(R0), _p(t0),
                     _p(_d(cell_lo).reshape(6)), _p(_d(cell_hi).reshape(6)), _p(out))
-    keys = ["valid", "straddle", "fallback", "klo", "khi", "px0", "px1", "py0", "py1", "rho"]
+    keys = ["valid", "straddle", "fallback", "klo", "khi", "px0", "px1", "py0", "py1", "rho",
+            "pieces", "korder", "rho_margin"]
     return {k: out[:, i] for i, k in enumerate(keys)}
 
 
@@ -169,6 +172,24 @@ def matrixinv_interval(Xl, Xu, k: int = 8, symmetric: bool = False):
     if st:
         return None
     return ol.reshape(2, 2), ou.reshape(2, 2), float(rho[0])
+
+
+def matrixinv_cell(Xl, Xu, symmetric: bool = False):
+    """The pipeline's MatrixInv on an interval 2x2 matrix (entries as in
+    matrixinv_interval): adaptive Taylor order, and input splitting where the
+    assertion fails on the whole box (Sec. 3.1, adjustments (2) and (3)).
+    Returns (lower, upper, info) with info = {"pieces", "k", "rho"}, or None if
+    even the split fails."""
+    lib = _load()
+    xl = _d(Xl).reshape(4)
+    xu = _d(Xu).reshape(4)
+    ol = np.zeros(4)
+    ou = np.zeros(4)
+    info = np.zeros(3)
+    st = lib.orc_matrixinv_cell(_p(xl), _p(xu), 1 if symmetric else 0, _p(ol), _p(ou), _p(info))
+    if st:
+        return None
+    return ol.reshape(2, 2), ou.reshape(2, 2), {"pieces": int(info[0]), "k": int(info[1]), "rho": float(info[2])}
 
 
 def relax_mul(x, y) -> np.ndarray:

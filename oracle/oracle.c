@@ -51,6 +51,8 @@
 
 #define NV 6            /* pose variables tx ty tz rx ry rz */
 #define KTAYLOR 8       /* MatrixInv Taylor order, default k = 8 (Sec. 3.3 footnote) */
+#define KMAX 24         /* adjustment (3) of Sec. 3.1: k grows from KTAYLOR up to KMAX */
+#define SPLIT_DEPTH 6   /* adjustment (2) of Sec. 3.1: at most 6 bisections of a pose cell */
 
 /* Algorithm constants shared by definition with the CUDA path (not by code). */
 static const double RHO_MAX = 1.0 - 1.0 / 1024.0;  /* MatrixInv usable while ||I-X X0|| < RHO_MAX */
@@ -60,6 +62,7 @@ static const double KEY_SLACK = 1e-9; /* relative widening of depth keys */
 static const double GUARD = 0.65;     /* guard band: 1.3 x the half-extent, as a fraction of W and H */
 static const double BOX_SLACK = 1e-9; /* relative widening of screen boxes */
 static const double ALPHA_MIN = 1.0 / 255.0;
+static const double EPS_TOL = 5.9604644775390625e-8;  /* 2^-24: k grows until Eps <= EPS_TOL ||X0||_F */
 
 typedef struct { double c[NV]; double k; } lf;   /* sum_i c_i p_i + k */
 typedef struct { lf lo, hi; } bs;                 /* lo(p) <= v <= hi(p) */
@@ -386,8 +389,11 @@ void orc_rot_forms(const double *lo, const double *hi, double *out /* 9 x (lo[7]
 
 /* MatrixInv (Algorithm 3) on a 2x2 matrix of bounded scalars.  Returns 0 and
  * fills conic on success, 1 when the reference matrix is not positive
- * definite or ||I - X X0|| >= RHO_MAX (the assertion of Algorithm 3 fails). */
-static int matrix_inv(const bs X[4], int k, bs conic[4], double *rho_out)
+ * definite or ||I - X X0|| >= RHO_MAX (the assertion of Algorithm 3 fails).
+ * k > 0 fixes the Taylor order; k <= 0 applies adjustment (3) of Sec. 3.1:
+ * starting from the default KTAYLOR, k grows while the remainder bound Eps
+ * exceeds EPS_TOL ||X0||_F, up to KMAX.  The order used goes to *k_out. */
+static int matrix_inv(const bs X[4], int k, bs conic[4], double *rho_out, int *k_out)
 {
     double Xh[4];
     for (int e = 0; e < 4; ++e) Xh[e] = 0.5 * (bs_min(&X[e]) + bs_max(&X[e]));
@@ -412,6 +418,12 @@ static int matrix_inv(const bs X[4], int k, bs conic[4], double *rho_out)
     double rho = sqrt(rho2);
     if (rho_out) *rho_out = rho;
     if (!(rho < RHO_MAX)) return 1;
+    /* Eps / ||X0|| = rho^(k+1) / (1 - rho) decides the adaptive order */
+    if (k <= 0) {
+        k = KTAYLOR;
+        while (k < KMAX && pow(rho, k + 1) / (1.0 - rho) > EPS_TOL) ++k;
+    }
+    if (k_out) *k_out = k;
     /* Sum_{i=0..k} Pow(IXX0, i) with Pow evaluated left to right */
     bs P[4], S[4];
     for (int e = 0; e < 4; ++e) { P[e] = E[e]; S[e] = bs_addc(E[e], (e == 0 || e == 3) ? 1.0 : 0.0); }
@@ -434,20 +446,146 @@ static int matrix_inv(const bs X[4], int k, bs conic[4], double *rho_out)
     return 0;
 }
 
-/* Interval-matrix entry point for the pins: the four entries of X are
- * independent, entry e = mid_e + half_e * p_e (symmetric != 0: entries 1 and
- * 2 are the same variable, so Xl/Xu must agree there).  Returns the concretised
- * bounds of MatrixInv's output. */
-int orc_matrixinv_interval(const double *Xl, const double *Xu, int k, int symmetric,
-                           double *out_l, double *out_u, double *rho)
+/* Interval forms of a 2x2 matrix whose entries are independent: entry e =
+ * mid_e + half_e * p_e (symmetric != 0: entries 1 and 2 are the same
+ * variable p_1, so Xl/Xu must agree there). */
+static void interval_forms(const double *Xl, const double *Xu, int symmetric, bs X[4])
 {
-    bs X[4], C[4];
     for (int e = 0; e < 4; ++e) {
         lf f = lf_cst(0.5 * (Xl[e] + Xu[e]));
         f.c[(symmetric && e == 2) ? 1 : e] = 0.5 * (Xu[e] - Xl[e]);
         X[e].lo = f; X[e].hi = f;
     }
-    int st = matrix_inv(X, k, C, rho);
+}
+
+/* A form over the cell restricted to the sub-box p = ctr + h p' (p' in
+ * [-1,1]^NV), written over p'. */
+static lf lf_restrict(const lf *f, const double ctr[NV], const double h[NV])
+{
+    lf r;
+    r.k = f->k;
+    for (int i = 0; i < NV; ++i) { r.c[i] = f->c[i] * h[i]; r.k += f->c[i] * ctr[i]; }
+    return r;
+}
+
+/* The pose variable along which a piece is bisected: the one on which X
+ * varies most there, i.e. the largest sum over X00, X01, X11 of the larger
+ * |coefficient| of the two sides (the first such variable on a tie). */
+static int split_var(const bs Xr[4])
+{
+    int js = 0;
+    double best = -1.0;
+    for (int j = 0; j < NV; ++j) {
+        double v = 0;
+        for (int e = 0; e < 4; ++e) {
+            if (e == 2) continue;  /* X10 = X01 */
+            v += fmax(fabs(Xr[e].lo.c[j]), fabs(Xr[e].hi.c[j]));
+        }
+        if (v > best) { best = v; js = j; }
+    }
+    return js;
+}
+
+typedef struct {
+    double lo[4], hi[4];  /* hull of the pieces' concretised outputs */
+    int pieces;           /* pieces MatrixInv succeeded on */
+    int kmax;             /* largest Taylor order used */
+    double margin;        /* smallest |rho - RHO_MAX| over the boxes tried */
+} splitacc;
+
+/* Adjustment (2) of Sec. 3.1: divide the input range until the assertion of
+ * Algorithm 3 holds.  The linear bounds of X are taken on the piece p = ctr
+ * + h p' of the pose cell (depth bisections deep) and MatrixInv runs there;
+ * a piece on which the assertion fails is bisected along split_var, the
+ * lower half first, down to SPLIT_DEPTH bisections.  The pieces' outputs are
+ * forms over different boxes, so they are joined as constants: the least
+ * lower and the greatest upper concretised bound of each entry.  Returns 1 if
+ * a piece at the depth limit still fails. */
+static int matinv_split(const bs X[4], const double ctr[NV], const double h[NV], int depth, splitacc *a)
+{
+    bs Xr[4], C[4];
+    for (int e = 0; e < 4; ++e) {
+        Xr[e].lo = lf_restrict(&X[e].lo, ctr, h);
+        Xr[e].hi = lf_restrict(&X[e].hi, ctr, h);
+    }
+    double rho;
+    int k = 0;
+    const int st = matrix_inv(Xr, 0, C, &rho, &k);
+    a->margin = fmin(a->margin, fabs(rho - RHO_MAX));
+    if (st == 0) {
+        for (int e = 0; e < 4; ++e) { a->lo[e] = fmin(a->lo[e], bs_min(&C[e])); a->hi[e] = fmax(a->hi[e], bs_max(&C[e])); }
+        ++a->pieces;
+        if (k > a->kmax) a->kmax = k;
+        return 0;
+    }
+    if (depth >= SPLIT_DEPTH) return 1;
+    const int js = split_var(Xr);
+    double c2[NV], h2[NV];
+    memcpy(c2, ctr, sizeof c2);
+    memcpy(h2, h, sizeof h2);
+    h2[js] = 0.5 * h[js];
+    c2[js] = ctr[js] - h2[js];
+    if (matinv_split(X, c2, h2, depth + 1, a)) return 1;
+    c2[js] = ctr[js] + h2[js];
+    return matinv_split(X, c2, h2, depth + 1, a);
+}
+
+/* MatrixInv over the whole cell (adaptive order); where its assertion fails,
+ * MatrixInv with input splitting (matinv_split from the whole cell), conic
+ * then holding constant forms.  Returns 1 when even the split fails (the R5
+ * fallback).  *pieces is 0 when no split was needed. */
+static int matrix_inv_cell(const bs X[4], bs conic[4], double *rho, int *korder, int *pieces, double *margin)
+{
+    *pieces = 0;
+    *korder = 0;
+    const int st = matrix_inv(X, 0, conic, rho, korder);
+    *margin = fabs(*rho - RHO_MAX);
+    if (st == 0) return 0;
+    splitacc a;
+    for (int e = 0; e < 4; ++e) { a.lo[e] = INFINITY; a.hi[e] = -INFINITY; }
+    a.pieces = 0;
+    a.kmax = 0;
+    a.margin = *margin;
+    double ctr[NV], h[NV];
+    for (int j = 0; j < NV; ++j) { ctr[j] = 0.0; h[j] = 1.0; }
+    const int fail = matinv_split(X, ctr, h, 0, &a);
+    *margin = a.margin;
+    if (fail) return 1;
+    for (int e = 0; e < 4; ++e) { conic[e].lo = lf_cst(a.lo[e]); conic[e].hi = lf_cst(a.hi[e]); }
+    *pieces = a.pieces;
+    *korder = a.kmax;
+    return 0;
+}
+
+/* Interval-matrix entry points for the pins (entries as in interval_forms).
+ * They return the concretised bounds of MatrixInv's output.
+ * orc_matrixinv_interval: MatrixInv on the whole box, order k (k <= 0: the
+ * adaptive order); returns 1 where the assertion fails.
+ * orc_matrixinv_cell: the pipeline's MatrixInv (adaptive order, input
+ * splitting where the assertion fails) on a symmetric box; info gets the
+ * pieces (0: no split), the Taylor order and rho on the whole box; returns 1
+ * if the split fails, 2 if the box is not symmetric. */
+int orc_matrixinv_interval(const double *Xl, const double *Xu, int k, int symmetric,
+                           double *out_l, double *out_u, double *rho)
+{
+    bs X[4], C[4];
+    interval_forms(Xl, Xu, symmetric, X);
+    int st = matrix_inv(X, k, C, rho, NULL);
+    if (st) return st;
+    for (int e = 0; e < 4; ++e) { out_l[e] = bs_min(&C[e]); out_u[e] = bs_max(&C[e]); }
+    return 0;
+}
+
+int orc_matrixinv_cell(const double *Xl, const double *Xu, int symmetric, double *out_l, double *out_u,
+                       double *info)
+{
+    bs X[4], C[4];
+    if (Xl[1] != Xl[2] || Xu[1] != Xu[2]) return 2;  /* the split works on symmetric boxes */
+    interval_forms(Xl, Xu, symmetric, X);
+    double rho, margin;
+    int korder, pieces;
+    int st = matrix_inv_cell(X, C, &rho, &korder, &pieces, &margin);
+    info[0] = pieces; info[1] = korder; info[2] = rho;
     if (st) return st;
     for (int e = 0; e < 4; ++e) { out_l[e] = bs_min(&C[e]); out_u[e] = bs_max(&C[e]); }
     return 0;
@@ -475,8 +613,11 @@ void orc_relax_sq(const double *x, double *out) { bs r = bs_sq(unpack_bs(x)); pa
 typedef struct {
     int valid;          /* contributes somewhere in the image */
     int straddle;       /* depth interval straddles the near plane */
-    int fallback;       /* MatrixInv assertion failed: a in [0, o] on the box */
-    double rho;         /* ||I - X X0|| bound (INFINITY if X0 undefined) */
+    int fallback;       /* MatrixInv failed even with input splitting: a in [0, o] on the box */
+    double rho;         /* ||I - X X0|| bound on the whole cell (INFINITY if X0 undefined) */
+    int pieces;         /* pieces of the input split (0: MatrixInv held on the whole cell) */
+    int korder;         /* Taylor order used (the largest over the pieces) */
+    double rho_margin;  /* smallest |rho - RHO_MAX| over the boxes MatrixInv was tried on */
     double klo, khi;    /* depth-key interval */
     int px0, px1, py0, py1;  /* pixel box whose centres may see the Gaussian */
     bs S, Px, Py;       /* S = d^2, P = d * up */
@@ -617,9 +758,10 @@ static void gaussian_record(const camera *cam, const cellforms *cf, const double
     g->S = bs_sq(d);
     g->Px = bs_mul(d, up0);
     g->Py = bs_mul(d, up1);
-    /* line 8: Conic <- MatrixInv(X; X0, k) */
+    /* line 8: Conic <- MatrixInv(X; X0, k), with the adaptive order and the
+     * input splitting of Sec. 3.1 */
     bs conic[4];
-    if (matrix_inv(X, KTAYLOR, conic, &g->rho)) { g->fallback = 1; return; }
+    if (matrix_inv_cell(X, conic, &g->rho, &g->korder, &g->pieces, &g->rho_margin)) { g->fallback = 1; return; }
     /* W = Conic * Mp, so that q = Delta^T W */
     for (int r = 0; r < 2; ++r)
         for (int c = 0; c < 3; ++c)
@@ -729,7 +871,7 @@ int orc_render_abstract(const double *uw, const double *ls, const double *quat, 
             idx[K] = i;
             gaussian_alpha(g, ux, uy, &A[K]);
             /* threshold decisions the FP32 path takes in single precision */
-            if (fabs(g->rho - RHO_MAX) < 1e-3) frag = 1;
+            if (g->rho_margin < 1e-3) frag = 1;
             if (!g->fallback && A[K].ramp < 0.05) {
                 /* a narrow ramp makes the cutoff nearly a step in m */
                 double tol = 1e-3 * fmax(1.0, g->tau), rp = A[K].ramp;
@@ -785,7 +927,8 @@ int orc_render_abstract(const double *uw, const double *ls, const double *quat, 
 }
 
 /* Per-Gaussian record summary for one cell (for tests): valid, straddle,
- * fallback, klo, khi, px0, px1, py0, py1, rho -> 10 doubles per Gaussian. */
+ * fallback, klo, khi, px0, px1, py0, py1, rho, pieces, korder, rho_margin ->
+ * 13 doubles per Gaussian. */
 int orc_records(const double *uw, const double *ls, const double *quat, const double *opac,
                 const double *rgb, int64_t n, const double *intr, const double *R0, const double *t0,
                 const double *cell_lo, const double *cell_hi, double *out)
@@ -797,9 +940,10 @@ int orc_records(const double *uw, const double *ls, const double *quat, const do
     for (int64_t i = 0; i < n; ++i) {
         grec g;
         gaussian_record(&cam, &cf, uw + 3 * i, ls + 3 * i, quat + 4 * i, opac[i], rgb + 3 * i, &g);
-        double *o = out + 10 * i;
+        double *o = out + 13 * i;
         o[0] = g.valid; o[1] = g.straddle; o[2] = g.fallback; o[3] = g.klo; o[4] = g.khi;
         o[5] = g.px0; o[6] = g.px1; o[7] = g.py0; o[8] = g.py1; o[9] = g.rho;
+        o[10] = g.pieces; o[11] = g.korder; o[12] = g.rho_margin;
     }
     return 0;
 }
@@ -1001,7 +1145,7 @@ int orc_record_trace(const double *uw, const double *ls, const double *quat, con
     for (int e = 0; e < 6; ++e) { out[14 + 2 * e] = bs_min(&Mp[e]); out[15 + 2 * e] = bs_max(&Mp[e]); }
     bs C[4];
     double rho;
-    if (matrix_inv(X, KTAYLOR, C, &rho)) return 2;
+    if (matrix_inv(X, 0, C, &rho, NULL)) return 2;
     for (int e = 0; e < 4; ++e) { out[26 + 2 * e] = bs_min(&C[e]); out[27 + 2 * e] = bs_max(&C[e]); }
     out[34] = rho;
     return 0;

@@ -37,7 +37,7 @@ class ar_render_stats(ctypes.Structure):
                 ("n_fallback", c_int64), ("n_launches", c_int32), ("tile", c_int32), ("m_vars", c_int32),
                 ("ms_prep", c_float), ("ms_bin", c_float), ("ms_render", c_float), ("ms_total", c_float),
                 ("n_evaluated", c_int64), ("n_reevaluated", c_int64), ("n_built", c_int64),
-                ("n_restarted", c_int64), ("ms_build", c_float)]
+                ("n_restarted", c_int64), ("ms_build", c_float), ("n_split", c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

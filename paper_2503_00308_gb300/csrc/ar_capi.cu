@@ -24,6 +24,10 @@ namespace ar {
 // stage events of one cell batch: start, after prep, after binning, then per
 // windowed round: after the record build, after the render
 constexpr int kEventsPerBatch = 9;
+// device counters of one cell batch: opacity evaluations, re-evaluations,
+// MatrixInv fallbacks and records built (record build), MatrixInv input
+// splits (record build), segments restarted (render)
+constexpr int kCountersPerBatch = 6;
 }  // namespace ar
 
 namespace ar {
@@ -422,7 +426,7 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
     if (rp) return fail(AR_EDEVICE, "record_prep launch: %s", cudaGetErrorString(cudaGetLastError()));
     launches += 2;
     if (profiling) CK(cudaEventRecord(ev[1], st));
-    CK(cudaMemcpyAsync(ws.h_counters, ws.counters.p, sizeof(unsigned long long) * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ws.h_counters, ws.counters.p, sizeof(unsigned long long) * 5, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (ws.whist_pending) {
         // the previous render's histogram arrived with this synchronisation
@@ -433,6 +437,7 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
     rs.n_records += (int64_t)n_valid;
     rs.n_triples += (int64_t)ws.h_counters[0];
     rs.n_fallback += (int64_t)ws.h_counters[1];
+    rs.n_split += (int64_t)ws.h_counters[4];
     const uint64_t ne = 2 * n_valid, nent = 2 * ws.h_counters[3];
     rs.n_entries += (int64_t)(nent / 2);
     if (nent >= (1ull << 32) - (1ull << 20))
@@ -458,7 +463,7 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
     rl.k_open = s->k_open;
     rl.out_lo = out_lo;
     rl.out_hi = out_hi;
-    rl.counters = ws.counters.as<unsigned long long>() + 8 + 5 * batch;
+    rl.counters = ws.counters.as<unsigned long long>() + 8 + kCountersPerBatch * batch;
     if (plain) {
         if (profiling) CK(cudaEventRecord(ev[3], st));
         if (launch_render_plain(M, TS, rl, st))
@@ -646,7 +651,7 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
     }
     RK(ws.cells_lohi.ensure(sizeof(double) * 12 * n_cells));
     RK(ws.vN.ensure(sizeof(double) * 12 * s->n));
-    RK(ws.counters.ensure(sizeof(unsigned long long) * (8 + 5 * n_batches)));
+    RK(ws.counters.ensure(sizeof(unsigned long long) * (8 + kCountersPerBatch * n_batches)));
     {
         std::vector<double> lohi((size_t)12 * n_cells);
         for (int c = 0; c < n_cells; ++c)
@@ -661,7 +666,7 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
     RK(ws.whist.ensure(sizeof(uint32_t) * 256));
     if (!ws.h_whist) CK(cudaMallocHost(&ws.h_whist, sizeof(uint32_t) * 256));
     CK(cudaMemsetAsync(ws.whist.p, 0, sizeof(uint32_t) * 256, st));
-    CK(cudaMemsetAsync(ws.counters.as<unsigned long long>() + 8, 0, sizeof(unsigned long long) * 5 * n_batches, st));
+    CK(cudaMemsetAsync(ws.counters.as<unsigned long long>() + 8, 0, sizeof(unsigned long long) * kCountersPerBatch * n_batches, st));
     int launches = 0;
     if (launch_pose_prep(s->uw, s->Mw, s->n, cc, ws.vN.as<double>(), st)) return fail(AR_EDEVICE, "pose_prep launch");
     ++launches;
@@ -681,6 +686,7 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
     }
     ws.n_batches = n_batches;
     ws.fallback_prep = rs.n_fallback;
+    ws.split_prep = rs.n_split;
     ws.built_prep = plain ? rs.n_records : 0;
     rs.n_launches = launches;
     if (stats) *stats = rs;
@@ -691,19 +697,22 @@ int finish_stats(Workspace &ws, cudaStream_t st, bool profiling, ar_render_stats
 {
     CK(cudaStreamSynchronize(st));
     if (ws.n_batches > 0 && ws.counters.p) {
-        std::vector<unsigned long long> ev(5 * ws.n_batches);
+        std::vector<unsigned long long> ev(kCountersPerBatch * ws.n_batches);
         CK(cudaMemcpy(ev.data(), ws.counters.as<unsigned long long>() + 8, sizeof(unsigned long long) * ev.size(),
                       cudaMemcpyDeviceToHost));
         rs.n_evaluated = rs.n_reevaluated = 0;
         rs.n_fallback = ws.fallback_prep;
         rs.n_built = ws.built_prep;
+        rs.n_split = ws.split_prep;
         rs.n_restarted = 0;
         for (int b = 0; b < ws.n_batches; ++b) {
-            rs.n_evaluated += (int64_t)ev[5 * b];
-            rs.n_reevaluated += (int64_t)ev[5 * b + 1];
-            rs.n_fallback += (int64_t)ev[5 * b + 2];
-            rs.n_built += (int64_t)ev[5 * b + 3];
-            rs.n_restarted += (int64_t)ev[5 * b + 4];
+            const unsigned long long *c = &ev[(size_t)kCountersPerBatch * b];
+            rs.n_evaluated += (int64_t)c[0];
+            rs.n_reevaluated += (int64_t)c[1];
+            rs.n_fallback += (int64_t)c[2];
+            rs.n_built += (int64_t)c[3];
+            rs.n_split += (int64_t)c[4];
+            rs.n_restarted += (int64_t)c[5];
         }
     }
     if (profiling && ws.n_batches > 0) {
@@ -824,7 +833,7 @@ int ar_render_concrete(ar_scene *s, const ar_intrinsics *in, const ar_nominal_po
                                  ws.boxes.as<PixBox>(), ws.keys.as<double>(), ws.counters.as<unsigned long long>(),
                                  st))
             return fail(AR_EDEVICE, "concrete prep launch: %s", cudaGetErrorString(cudaGetLastError()));
-        CK(cudaMemcpyAsync(ws.h_counters, ws.counters.p, sizeof(unsigned long long) * 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(ws.h_counters, ws.counters.p, sizeof(unsigned long long) * 5, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         const uint64_t ne = 2 * ws.h_counters[2], nent = 2 * ws.h_counters[3];
         if (ne == 0) {

@@ -9,6 +9,9 @@ namespace ar {
 
 // Algorithm constants (the relaxation choices of the abstract renderer).
 constexpr int KTAYLOR = 8;                       // MatrixInv order, k = 8 (Sec. 3.3 footnote)
+constexpr int KMAX = 24;                         // adaptive order: k grows from KTAYLOR up to KMAX (Sec. 3.1 (3))
+constexpr double EPS_TOL = 5.9604644775390625e-8;  // 2^-24: k grows until Eps <= EPS_TOL ||X0||_F
+constexpr int SPLIT_DEPTH = 6;                   // input splitting: at most 6 bisections of a cell (Sec. 3.1 (2))
 constexpr double RHO_MAX = 1.0 - 1.0 / 1024.0;   // MatrixInv used while ||I - X X0|| < RHO_MAX
 constexpr float CUT_RAMP = 0.5f;                 // widest cutoff ramp (units of m)
 constexpr float CLIP_RAMP = 0.25f;               // upper-alpha blend toward o
@@ -62,9 +65,10 @@ template <int M> struct Rec {
 };
 
 // record flags
-constexpr uint32_t F_FALLBACK = 1u;  // MatrixInv assertion failed: a in [0, o]
+constexpr uint32_t F_FALLBACK = 1u;  // MatrixInv failed, even on split pieces: a in [0, o]
 constexpr uint32_t F_STRADDLE = 2u;  // depth may cross the near plane: lower alpha is 0
 constexpr uint32_t F_OPEN = 4u;      // depth-key interval has positive width
+constexpr uint32_t F_SPLIT = 8u;     // MatrixInv held only after splitting the cell (constant Conic)
 
 // Pixel box of a (Gaussian, cell) pair: x0 < 0 marks "contributes nowhere".
 struct PixBox {

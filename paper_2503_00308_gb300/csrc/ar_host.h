@@ -37,6 +37,7 @@ struct Workspace {
     std::vector<cudaEvent_t> evs;              // 9 per cell batch (stage timing)
     int n_batches = 0;                         // cell batches of the last render
     int64_t fallback_prep = 0;                 // MatrixInv fallbacks counted by the record kernel
+    int64_t split_prep = 0;                    // MatrixInv input splits counted by the record kernel
     int64_t built_prep = 0;                    // records built completely by the record kernel
     void release();
     size_t bytes() const;

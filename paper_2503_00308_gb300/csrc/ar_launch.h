@@ -26,7 +26,7 @@ struct RenderLaunch {
     float k_open;                     // 1 / (1 - largest opacity), rounded up
     float *out_lo, *out_hi;
     unsigned long long *counters;     // optional: [0] opacity evaluations, [1] re-evaluations,
-                                      // [4] segments abandoned for a wider window ([2], [3]: record build)
+                                      // [5] segments abandoned for a wider window ([2]-[4]: record build)
     unsigned int *work;               // segment counter of the persistent grid (zeroed by the launcher)
 };
 
@@ -41,7 +41,7 @@ int launch_record_prep64(int M, const double *vN, const double *tau, const float
                          const CallConst &cc, const void *cells, int TS, double *recs, PixBox *boxes, double *keys,
                          unsigned long long *counters, cudaStream_t st);
 int launch_render_plain(int M, int TS, const RenderLaunch &a, cudaStream_t st);
-// value parts of the records listed in work[0, *count); counters: [0] fallbacks, [1] built
+// value parts of the records listed in work[0, *count); counters: [0] fallbacks, [1] built, [2] split
 int launch_record_build(int M, const double *vN, const CallConst &cc, const void *cells, int64_t n_gauss,
                         const uint32_t *work, const uint32_t *count, float *recs, unsigned long long *counters,
                         cudaStream_t st);

@@ -227,7 +227,7 @@ __device__ __forceinline__ bool sb_finite(const SB<M, R> &b)
 }
 
 struct PrepCount {
-    uint32_t triples, fallback, valid, tiles;
+    uint32_t triples, fallback, valid, tiles, split;
 };
 
 // The decision part of one (Gaussian, cell) pair: depth forms, near-plane
@@ -358,6 +358,194 @@ __device__ __forceinline__ int64_t record_decide(const double *__restrict__ vN, 
     return flags;
 }
 
+// MatrixInv (Algorithm 3) on X, FP64 forms over a box (X10 = X01): X0 is
+// the inverse of the centre matrix (adjustment (1) of Sec. 3.1), rounded to
+// the record precision so that the same constant enters I - X X0 and X0 *
+// sum; E = I - X X0 and its Frobenius norm bound rho are formed in FP64, the
+// series in the record precision.  The order starts at the default KTAYLOR
+// and grows while the remainder bound rho^(k+1) / (1 - rho) exceeds EPS_TOL
+// (relative to ||X0||_F), up to KMAX (adjustment (3)).  Returns false when
+// the centre matrix is not positive definite or rho >= RHO_MAX.
+template <int M, class RO>
+__device__ __forceinline__ bool matinv_box(const SB<M, double> X[4], SB<M, RO> conic[4])
+{
+    using NO = Num<RO>;
+    typedef SB<M, RO> B;
+    typedef SB<M, double> BD;
+    typedef SAcc<M, double> AD;
+    const double h00 = 0.5 * (X[0].vlo + X[0].vhi), h01 = 0.5 * (X[1].vlo + X[1].vhi);
+    const double h11 = 0.5 * (X[3].vlo + X[3].vhi);
+    const double det = h00 * h11 - h01 * h01;
+    if (!(det > 0.0) || !(h00 > 0.0) || !isfinite(det)) return false;
+    const RO X0[4] = {(RO)(h11 / det), (RO)(-h01 / det), (RO)(-h01 / det), (RO)(h00 / det)};
+    B E[4];
+    double rho2 = 0.0;
+    for (int r = 0; r < 2; ++r)
+        for (int s = 0; s < 2; ++s) {
+            AD p;
+            const double dl = (r == s) ? 1.0 : 0.0;
+            p.init(dl, dl);
+            p.term(-(double)X0[s], X[2 * r]);
+            p.term(-(double)X0[2 + s], X[2 * r + 1]);
+            const BD e64 = p.result();
+            const double m = fmax(fabs(e64.vlo), fabs(e64.vhi));
+            rho2 = __fma_ru(m, m, rho2);
+            sb_to_rec<M>(e64, E[2 * r + s]);
+        }
+    const double rho64 = __dsqrt_ru(rho2);
+    if (!(rho64 < RHO_MAX)) return false;
+    int k = KTAYLOR;
+    {
+        double rk = 1.0;  // rho^(k+1), for the adaptive order
+        for (int i = 0; i <= KTAYLOR; ++i) rk *= rho64;
+        while (k < KMAX && rk / (1.0 - rho64) > EPS_TOL) {
+            rk *= rho64;
+            ++k;
+        }
+    }
+    RO rho;
+    rec_up(rho64, rho);
+    // T = sum_{i=1..k} (I - X X0)^i, so that Xp = X0 (I + T) = X0 + X0 T: the
+    // identity term is added as an exact constant at the end
+    B P[4], Ssum[4];
+    for (int e = 0; e < 4; ++e) {
+        P[e] = E[e];
+        Ssum[e] = E[e];
+    }
+#pragma unroll 1
+    for (int i = 2; i <= k; ++i) {
+        B Q[4];
+        for (int r = 0; r < 2; ++r)
+            for (int s = 0; s < 2; ++s) {
+                SAcc<M, RO> p;
+                p.init(0, 0);
+                p.mul(P[2 * r], E[s]);
+                p.mul(P[2 * r + 1], E[2 + s]);
+                Q[2 * r + s] = p.result();
+            }
+        for (int e = 0; e < 4; ++e) { P[e] = Q[e]; Ssum[e] = sb_add<M, RO>(Ssum[e], Q[e]); }
+    }
+    RO nX0 = 0;
+    for (int e = 0; e < 4; ++e) nX0 = NO::fma_ru(X0[e], X0[e], nX0);
+    nX0 = NO::sqrt_ru(nX0);
+    RO rk = 1;
+    for (int i = 0; i <= k; ++i) rk = NO::mul_ru(rk, rho);
+    const RO eps = NO::div_ru(NO::mul_ru(nX0, rk), NO::sub_rd(RO(1), rho));
+    for (int r = 0; r < 2; ++r)
+        for (int s = 0; s < 2; ++s) {
+            SAcc<M, RO> p;
+            // X0[r][s] + eps-widening, then + X0 T
+            p.init(NO::sub_rd(X0[2 * r + s], eps), NO::add_ru(X0[2 * r + s], eps));
+            p.term(X0[2 * r], Ssum[s]);
+            p.term(X0[2 * r + 1], Ssum[2 + s]);
+            conic[2 * r + s] = p.result();
+        }
+    return true;
+}
+
+// x restricted to the sub-box p = ctr + h p' of the cell, as a form over p'
+// (h is a power of two, so the coefficients scale exactly; the constants
+// take c . ctr rounded outward).
+template <int M>
+__device__ __forceinline__ SB<M, double> sb_restrict(const SB<M, double> &x, const double *ctr, const double *h)
+{
+    SB<M, double> y;
+    double klo = x.klo, khi = x.khi;
+    for (int j = 0; j < M; ++j) {
+        y.c[j] = x.c[j] * h[j];
+        klo = __fma_rd(x.c[j], ctr[j], klo);
+        khi = __fma_ru(x.c[j], ctr[j], khi);
+    }
+    y.klo = __dsub_rd(klo, 1e-300);  // covers a subnormal c h
+    y.khi = __dadd_ru(khi, 1e-300);
+    sb_finish(y);
+    return y;
+}
+
+// The pose variable a piece is bisected along: the one on which X varies most
+// there (the largest sum over X00, X01, X11 of |c_j|; the first on a tie).
+template <int M>
+__device__ __forceinline__ int split_var(const SB<M, double> Xr[4])
+{
+    int js = 0;
+    double best = -1.0;
+    for (int j = 0; j < M; ++j) {
+        const double v = fabs(Xr[0].c[j]) + fabs(Xr[1].c[j]) + fabs(Xr[3].c[j]);
+        if (v > best) {
+            best = v;
+            js = j;
+        }
+    }
+    return js;
+}
+
+// Adjustment (2) of Sec. 3.1, for a cell on which MatrixInv failed: the cell
+// is bisected along split_var, depth first and lower half first, and each
+// piece that still fails is bisected again, down to SPLIT_DEPTH bisections,
+// until MatrixInv holds on every piece.  The pieces' outputs are forms over
+// different boxes, so they are joined as constant forms: each entry is
+// bounded by the least lower and the greatest upper concretised bound over
+// the pieces.  Returns the number of pieces, or 0 if a piece at the depth
+// limit still fails.  At most one pending sibling per level waits on the
+// stack, so SPLIT_DEPTH + 1 entries suffice.
+template <int M, class RO>
+__device__ __noinline__ int matinv_split(const SB<M, double> X[4], SB<M, RO> conic[4])
+{
+    struct Piece {
+        double ctr[M], h[M];
+        int depth;
+    };
+    Piece st[SPLIT_DEPTH + 1];
+    int top = 0;
+    RO lo[4], hi[4];
+    for (int e = 0; e < 4; ++e) {
+        lo[e] = Num<RO>::BIG;
+        hi[e] = -Num<RO>::BIG;
+    }
+    // push the two halves of a piece, the upper one first
+    auto push_halves = [&](const double *ctr, const double *h, int depth, const SB<M, double> Xr[4]) {
+        const int js = split_var<M>(Xr);
+        for (int side = 1; side >= 0; --side) {
+            Piece &q = st[top++];
+            for (int j = 0; j < M; ++j) {
+                q.ctr[j] = ctr[j];
+                q.h[j] = h[j];
+            }
+            q.h[js] = 0.5 * h[js];
+            q.ctr[js] = side ? ctr[js] + q.h[js] : ctr[js] - q.h[js];
+            q.depth = depth + 1;
+        }
+    };
+    {
+        double ctr[M], h[M];
+        for (int j = 0; j < M; ++j) {
+            ctr[j] = 0.0;
+            h[j] = 1.0;
+        }
+        push_halves(ctr, h, 0, X);
+    }
+    int pieces = 0;
+    while (top > 0) {
+        const Piece q = st[--top];
+        SB<M, double> Xr[4];
+        for (int e = 0; e < 4; ++e) Xr[e] = sb_restrict<M>(X[e], q.ctr, q.h);
+        SB<M, RO> C[4];
+        if (matinv_box<M, RO>(Xr, C)) {
+            for (int e = 0; e < 4; ++e) {
+                lo[e] = Num<RO>::min(lo[e], C[e].vlo);
+                hi[e] = Num<RO>::max(hi[e], C[e].vhi);
+            }
+            ++pieces;
+        } else if (q.depth < SPLIT_DEPTH) {
+            push_halves(q.ctr, q.h, q.depth, Xr);
+        } else {
+            return 0;
+        }
+    }
+    for (int e = 0; e < 4; ++e) conic[e] = sb_cst<M, RO>(lo[e], hi[e]);
+    return pieces;
+}
+
 // The value part of one (Gaussian, cell) pair: the forms the per-pixel stage
 // reads, S = d^2 and R = mu S - P (Algorithm 1 lines 2-8 with set-valued
 // variables), MatrixInv (Algorithm 3) and W = Conic Mp.  v points at the
@@ -447,8 +635,8 @@ __device__ __forceinline__ uint32_t record_value(const double *__restrict__ v, f
             p.init(0.0, 0.0); p.mul(J11, Mc[3 + c]); p.mul(J12, Mc[6 + c]); Mp64[3 + c] = p.result();
         }
     }
-    // ---- MatrixInv (Algorithm 3): X and I - X X0 in FP64, the series in the
-    // record precision
+    // ---- MatrixInv (Algorithm 3) with the adaptive order and, where its
+    // assertion fails on the cell, the input splitting of Sec. 3.1
     bool fallback = false;
     B conic[4];
     {
@@ -460,73 +648,13 @@ __device__ __forceinline__ uint32_t record_value(const double *__restrict__ v, f
             p.init(0.0, 0.0); p.mul(Mp64[0], Mp64[3]); p.mul(Mp64[1], Mp64[4]); p.mul(Mp64[2], Mp64[5]); X[1] = p.result();
             X[2] = X[1];
         }
-        const double h00 = 0.5 * (X[0].vlo + X[0].vhi), h01 = 0.5 * (X[1].vlo + X[1].vhi);
-        const double h11 = 0.5 * (X[3].vlo + X[3].vhi);
-        const double det = h00 * h11 - h01 * h01;
-        if (!(det > 0.0) || !(h00 > 0.0) || !isfinite(det)) {
-            fallback = true;
-        } else {
-            // X0 rounded to the record precision: the same constant enters
-            // I - X X0 and X0 * sum
-            const RO X0[4] = {(RO)(h11 / det), (RO)(-h01 / det), (RO)(-h01 / det), (RO)(h00 / det)};
-            B E[4];
-            double rho2 = 0.0;
-            for (int r = 0; r < 2; ++r)
-                for (int s = 0; s < 2; ++s) {
-                    AD p;
-                    const double dl = (r == s) ? 1.0 : 0.0;
-                    p.init(dl, dl);
-                    p.term(-(double)X0[s], X[2 * r]);
-                    p.term(-(double)X0[2 + s], X[2 * r + 1]);
-                    const BD e64 = p.result();
-                    const double m = fmax(fabs(e64.vlo), fabs(e64.vhi));
-                    rho2 = __fma_ru(m, m, rho2);
-                    sb_to_rec<M>(e64, E[2 * r + s]);
-                }
-            const double rho64 = __dsqrt_ru(rho2);
-            if (!(rho64 < RHO_MAX)) {
-                fallback = true;
-            } else {
-                RO rho;
-                rec_up(rho64, rho);
-                // T = sum_{i=1..k} (I - X X0)^i, so that Xp = X0 (I + T) = X0 + X0 T:
-                // the identity term is added as an exact constant at the end
-                B P[4], Ssum[4];
-                for (int e = 0; e < 4; ++e) {
-                    P[e] = E[e];
-                    Ssum[e] = E[e];
-                }
-#pragma unroll 1
-                for (int i = 2; i <= KTAYLOR; ++i) {
-                    B Q[4];
-                    for (int r = 0; r < 2; ++r)
-                        for (int s = 0; s < 2; ++s) {
-                            SAcc<M, RO> p;
-                            p.init(0, 0);
-                            p.mul(P[2 * r], E[s]);
-                            p.mul(P[2 * r + 1], E[2 + s]);
-                            Q[2 * r + s] = p.result();
-                        }
-                    for (int e = 0; e < 4; ++e) { P[e] = Q[e]; Ssum[e] = sb_add<M, RO>(Ssum[e], Q[e]); }
-                }
-                RO nX0 = 0;
-                for (int e = 0; e < 4; ++e) nX0 = NO::fma_ru(X0[e], X0[e], nX0);
-                nX0 = NO::sqrt_ru(nX0);
-                RO rk = 1;
-                for (int i = 0; i <= KTAYLOR; ++i) rk = NO::mul_ru(rk, rho);
-                const RO eps = NO::div_ru(NO::mul_ru(nX0, rk), NO::sub_rd(RO(1), rho));
-                for (int r = 0; r < 2; ++r)
-                    for (int s = 0; s < 2; ++s) {
-                        SAcc<M, RO> p;
-                        // X0[r][s] + eps-widening, then + X0 T
-                        p.init(NO::sub_rd(X0[2 * r + s], eps), NO::add_ru(X0[2 * r + s], eps));
-                        p.term(X0[2 * r], Ssum[s]);
-                        p.term(X0[2 * r + 1], Ssum[2 + s]);
-                        conic[2 * r + s] = p.result();
-                        if (!sb_finite(conic[2 * r + s])) fallback = true;
-                    }
-            }
+        if (!matinv_box<M, RO>(X, conic)) {
+            if (matinv_split<M, RO>(X, conic) > 0) flags |= F_SPLIT;
+            else fallback = true;
         }
+        if (!fallback)
+            for (int e = 0; e < 4; ++e)
+                if (!sb_finite(conic[e])) fallback = true;
     }
     if (!fallback) {
         for (int r = 0; r < 2; ++r)
@@ -552,7 +680,8 @@ __device__ __forceinline__ uint32_t record_value(const double *__restrict__ v, f
 // VALUE = false builds only the decision part (the value part is then built
 // on demand by the renderer).
 // counters: [0] pixel-Gaussian-cell triples in boxes, [1] MatrixInv
-// fallbacks, [2] pairs present, [3] (pair, tile) entries.
+// fallbacks, [2] pairs present, [3] (pair, tile) entries, [4] pairs whose
+// MatrixInv needed input splitting.
 template <int M, class RO = float, bool VALUE = true>
 __global__ void __launch_bounds__(128) record_prep_kernel(
     const double *__restrict__ vN, const double *__restrict__ tau_g, const float *__restrict__ opacity,
@@ -562,7 +691,7 @@ __global__ void __launch_bounds__(128) record_prep_kernel(
 {
     const int cell = blockIdx.y;
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    PrepCount pc = {0, 0, 0, 0};
+    PrepCount pc = {0, 0, 0, 0, 0};
     if (g < cc.n_gauss) {
         const int64_t fl = record_decide<M, RO>(vN, tau_g, opacity, rgb, cc, cells[cell], cell, g, TS, recs, boxes,
                                                 keys, pc);
@@ -571,17 +700,20 @@ __global__ void __launch_bounds__(128) record_prep_kernel(
             const uint32_t f = record_value<M, RO>(vN + 12 * g, cc.fx, cc.fy, cc.cx, cc.cy, cells[cell], rec[Rec<M>::MU_X],
                                                    rec[Rec<M>::MU_Y], (uint32_t)fl, rec);
             pc.fallback = (f & F_FALLBACK) ? 1u : 0u;
+            pc.split = (f & F_SPLIT) ? 1u : 0u;
         }
     }
     const uint32_t t = __reduce_add_sync(0xffffffffu, pc.triples);
     const uint32_t f = __reduce_add_sync(0xffffffffu, pc.fallback);
     const uint32_t v = __reduce_add_sync(0xffffffffu, pc.valid);
     const uint32_t e = __reduce_add_sync(0xffffffffu, pc.tiles);
+    const uint32_t sp = __reduce_add_sync(0xffffffffu, pc.split);
     if ((threadIdx.x & 31) == 0) {
         if (t) atomicAdd(&counters[0], (unsigned long long)t);
         if (f) atomicAdd(&counters[1], (unsigned long long)f);
         if (v) atomicAdd(&counters[2], (unsigned long long)v);
         if (e) atomicAdd(&counters[3], (unsigned long long)e);
+        if (sp) atomicAdd(&counters[4], (unsigned long long)sp);
     }
 }
 
@@ -589,7 +721,8 @@ __global__ void __launch_bounds__(128) record_prep_kernel(
 // indices within the batch, cell * n_gauss + g), whose decision part the
 // record kernel wrote.  Grid-stride over the list; the grid is sized on the
 // host without knowing the count.
-// counters: [0] MatrixInv fallbacks among the records built, [1] records built.
+// counters: [0] MatrixInv fallbacks among the records built, [1] records
+// built, [2] records whose MatrixInv needed input splitting.
 template <int M>
 __global__ void __launch_bounds__(128) record_build_kernel(
     const double *__restrict__ vN, float fx, float fy, float cx, float cy, const CellData<M> *__restrict__ cells,
@@ -598,7 +731,7 @@ __global__ void __launch_bounds__(128) record_build_kernel(
 {
     using RL = Rec<M>;
     const uint32_t n = *count;
-    uint32_t built = 0, fb = 0;
+    uint32_t built = 0, fb = 0, sp = 0;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const uint32_t p = work[i];
         const int cell = (int)(p / (uint64_t)n_gauss);
@@ -608,13 +741,16 @@ __global__ void __launch_bounds__(128) record_build_kernel(
                                                   rec[RL::MU_Y], __float_as_uint(rec[RL::FLAGS]), rec);
         ++built;
         if (f & F_FALLBACK) ++fb;
+        if (f & F_SPLIT) ++sp;
     }
     if (counters) {
         const uint32_t a = __reduce_add_sync(0xffffffffu, fb);
         const uint32_t b = __reduce_add_sync(0xffffffffu, built);
+        const uint32_t c = __reduce_add_sync(0xffffffffu, sp);
         if ((threadIdx.x & 31) == 0) {
             if (a) atomicAdd(&counters[0], (unsigned long long)a);
             if (b) atomicAdd(&counters[1], (unsigned long long)b);
+            if (c) atomicAdd(&counters[2], (unsigned long long)c);
         }
     }
 }

@@ -557,7 +557,7 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
         if (abandoned) {
             if (tid == 0) {
                 next_active[atomicAdd(n_next, 1u)] = seg;
-                if (counters) atomicAdd(&counters[4], 1ull);
+                if (counters) atomicAdd(&counters[5], 1ull);
             }
             continue;
         }

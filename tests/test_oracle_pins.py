@@ -180,6 +180,81 @@ def test_matrixinv_point_is_inverse(orc):
 def test_matrixinv_rejects_wide_box(orc):
     # the assertion of Algorithm 3 fails when ||I - X X0|| >= 1
     assert orc.matrixinv_interval([[0.1, -1], [-1, 0.1]], [[2, 1], [1, 2]]) is None
+    # the box holds singular matrices (x = y = 1, z = 1), so no piece of it
+    # can pass the assertion either: input splitting fails too
+    assert orc.matrixinv_cell([[0.1, -1], [-1, 0.1]], [[2, 1], [1, 2]], symmetric=True) is None
+
+
+# ------------------------------------------ MatrixInv adjustments of Sec. 3.1
+
+def test_matrixinv_adaptive_order_example1(orc):
+    # adjustment (3): k grows from the default 8 until Eps <= 2^-24 ||X0||_F.
+    # Worked by hand for Example 1 (rho = 0.2722): rho^(k+1) / (1 - rho) <=
+    # 5.96e-8 needs k + 1 >= ln(4.34e-8) / ln(0.2722) = 13.03, so k = 13.
+    ex = json.load(open(os.path.join(GOLDEN, "matrixinv_example1.json")))
+    Xl, Xu = np.array(ex["X_lower"]), np.array(ex["X_upper"])
+    lo, hi, info = orc.matrixinv_cell(Xl, Xu, symmetric=True)
+    assert info["pieces"] == 0 and abs(info["rho"] - 0.2722) < 1e-4
+    assert info["k"] == 13
+    hl, hu = _inverse_hull(Xl, Xu, symmetric=True)
+    assert np.all(lo <= hl + 1e-12) and np.all(hi >= hu - 1e-12)     # Lemma 1 over the box
+    lo8, hi8, _ = orc.matrixinv_interval(Xl, Xu, k=8, symmetric=True)
+    assert np.linalg.norm(hi - lo) <= np.linalg.norm(hi8 - lo8)       # a smaller remainder
+
+
+def test_matrixinv_split_diagonal_box(orc):
+    # X = diag(x, y) with x, y in [0.5, 4]: the centre is 2.25 I, so I - X X0
+    # = diag(1 - x/2.25, 1 - y/2.25) with entries up to 1.75/2.25, and
+    # rho = sqrt(2) 0.7778 = 1.0999 >= 1 (worked by hand): the assertion of
+    # Algorithm 3 fails on the whole box and the input range is divided
+    Xl = np.array([[0.5, 0.0], [0.0, 0.5]])
+    Xu = np.array([[4.0, 0.0], [0.0, 4.0]])
+    assert orc.matrixinv_interval(Xl, Xu, k=8, symmetric=True) is None
+    lo, hi, info = orc.matrixinv_cell(Xl, Xu, symmetric=True)
+    assert abs(info["rho"] - math.sqrt(2) * 1.75 / 2.25) < 1e-12
+    assert 2 <= info["pieces"] <= 64
+    # the exact hull of the inverse: diag([1/4, 2], [1/4, 2]) with a zero off-diagonal
+    assert lo[0, 0] <= 0.25 and hi[0, 0] >= 2.0 and lo[1, 1] <= 0.25 and hi[1, 1] >= 2.0
+    assert lo[0, 1] <= 0.0 <= hi[0, 1] and lo[1, 0] <= 0.0 <= hi[1, 0]
+
+
+def test_matrixinv_split_brute_force(orc):
+    # positive definite throughout (det >= 0.6^2 - 0.5^2 > 0) but too wide for
+    # one expansion: x, y in [0.6, 5], z in [-0.5, 0.5] gives rho = 1.16
+    Xl = np.array([[0.6, -0.5], [-0.5, 0.6]])
+    Xu = np.array([[5.0, 0.5], [0.5, 5.0]])
+    assert orc.matrixinv_interval(Xl, Xu, k=8, symmetric=True) is None
+    lo, hi, info = orc.matrixinv_cell(Xl, Xu, symmetric=True)
+    assert info["pieces"] >= 2
+    hl, hu = _inverse_hull(Xl, Xu, n=41, symmetric=True)
+    assert np.all(lo <= hl + 1e-12) and np.all(hi >= hu - 1e-12)
+    rng = np.random.default_rng(8)
+    a, d = rng.uniform(0.6, 5.0, size=(2, 20000))
+    b = rng.uniform(-0.5, 0.5, size=20000)
+    inv = np.linalg.inv(np.stack([a, b, b, d], axis=-1).reshape(-1, 2, 2))
+    assert np.all(inv >= lo - 1e-12) and np.all(inv <= hi + 1e-12)
+
+
+def test_matrixinv_split_scene_sound(orc):
+    # Gaussians 0.9-1.5 m from the camera under a +-5 cm / +-2.5 deg cell:
+    # MatrixInv fails on the whole cell for some pairs, input splitting
+    # recovers some of them, and the render stays sound (Theorem 1) at
+    # sampled poses
+    sc = synth.cube_scene(60, 3, half=0.3)
+    cam = synth.look_camera(32, 32, 28.0, centre=(0, 0, -1.2))
+    clo = np.array([-0.05, -0.05, -0.05, -2.5 * synth.DEG, -2.5 * synth.DEG, -2.5 * synth.DEG])
+    rec = orc.records(sc, cam, clo, -clo)
+    v = rec["valid"] > 0
+    split = v & (rec["pieces"] > 0)
+    assert split.sum() >= 2
+    assert np.all(rec["rho"][split] >= 1.0 - 1.0 / 1024.0)     # split only where the assertion failed
+    assert np.all(rec["fallback"][split] == 0) and np.all(rec["pieces"][split] <= 64)
+    assert np.all(rec["korder"][v & (rec["fallback"] == 0)] >= 8)
+    lo, hi, _ = orc.render_abstract(sc, cam, clo, -clo)
+    rng = np.random.default_rng(21)
+    poses = np.concatenate([synth.sample_poses(rng, clo, -clo, 3000), _corners(clo, -clo)])
+    worst, nv = orc.check_samples(sc, cam, poses, lo, hi, tol=1e-12)
+    assert nv == 0, worst
 
 
 # ------------------------------------------------------------ concrete render
