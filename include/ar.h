@@ -191,6 +191,19 @@ int ar_render_abstract_plain_fp64(ar_scene *scene, const ar_intrinsics *intr,
 int ar_render_concrete(ar_scene *scene, const ar_intrinsics *intr, const ar_nominal_pose *pose,
                        const double *deltas, int32_t n_poses, float *out, void *cuda_stream);
 
+/* Test and diagnosis hook: the decision part of every (Gaussian, cell)
+ * record of one pose cell, as the batched renderer computes it (Algorithm 1
+ * lines 2-7 with set-valued variables: depth, near-plane class, depth key,
+ * pixel box; the frustum guard band).  out: host, [n][10] doubles per
+ * Gaussian: valid, straddle, k_lo, k_hi, px0, px1, py0, py1, mu_x, mu_y
+ * (all 0 where the pair reaches no pixel; mu is the pixel centre the pixel
+ * stage expands around).  The decisions are taken in FP64 in the order of the
+ * oracle's steps, so they are bit-identical to a plain FP64 implementation.
+ * Synchronous (default stream); uses the scene's workspace, so it must not
+ * overlap a render of the same scene.  AR_EINVAL for bad arguments. */
+int ar_debug_records(ar_scene *scene, const ar_intrinsics *intr, const ar_nominal_pose *pose,
+                     const ar_pose_box *cell, double *out);
+
 /* Device-memory limit (bytes, >= 1 MiB) for the scene's render workspace.
  * ar_render_abstract splits the cells of a call into batches whose
  * per-(Gaussian, cell) records take about a third of this limit, and runs the

@@ -871,7 +871,8 @@ int orc_render_abstract(const double *uw, const double *ls, const double *quat, 
             idx[K] = i;
             gaussian_alpha(g, ux, uy, &A[K]);
             /* threshold decisions the FP32 path takes in single precision */
-            if (g->rho_margin < 1e-3) frag = 1;
+            /* rho is FP64 on both sides; their forms differ by rounding only */
+            if (g->rho_margin < 1e-6) frag = 1;
             if (!g->fallback && A[K].ramp < 0.05) {
                 /* a narrow ramp makes the cutoff nearly a step in m */
                 double tol = 1e-3 * fmax(1.0, g->tau), rp = A[K].ramp;

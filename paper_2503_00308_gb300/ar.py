@@ -69,6 +69,7 @@ def lib():
             "ar_render_abstract_plain_fp64": ([P, P, P, P, c_int32, c_int32, P, P, P], ctypes.c_int),
             "ar_render_abstract_noalloc": ([P, P, P, P, c_int32, c_int32, P, P, P], ctypes.c_int),
             "ar_render_concrete": ([P, P, P, P, c_int32, P, P], ctypes.c_int),
+            "ar_debug_records": ([P, P, P, P, P], ctypes.c_int),
             "ar_set_profiling": ([P, ctypes.c_int], ctypes.c_int),
             "ar_set_workspace_limit": ([P, c_int64], ctypes.c_int),
             "ar_last_render_stats": ([P, P], ctypes.c_int),
@@ -177,6 +178,14 @@ def ar_render_concrete(scene, intr, pose, deltas, n_poses, out, stream=0):
                                           int(n_poses), _ptr(out), _ptr(stream)))
 
 
+def ar_debug_records(scene, intr, pose, cell, n: int) -> np.ndarray:
+    """Decision part of the records of one cell: [n, 10] (valid, straddle,
+    k_lo, k_hi, px0, px1, py0, py1, mu_x, mu_y)."""
+    out = np.zeros((n, 10), dtype=np.float64)
+    check(lib().ar_debug_records(scene, ctypes.byref(intr), ctypes.byref(pose), ctypes.byref(cell), out.ctypes.data))
+    return out
+
+
 def ar_set_workspace_limit(scene, nbytes: int):
     return check(lib().ar_set_workspace_limit(scene, int(nbytes)))
 
@@ -251,6 +260,10 @@ class Scene:
         """Concrete renders at the poses deltas ([n][6]) into out ([n][H][W][3], device)."""
         d = np.ascontiguousarray(np.asarray(deltas, dtype=np.float64).reshape(-1, 6))
         ar_render_concrete(self.handle, make_intrinsics(cam), make_pose(cam), d, d.shape[0], out, stream)
+
+    def debug_records(self, cam, cell_lo, cell_hi) -> np.ndarray:
+        cells = make_cells(np.reshape(cell_lo, (1, 6)), np.reshape(cell_hi, (1, 6)))
+        return ar_debug_records(self.handle, make_intrinsics(cam), make_pose(cam), cells[0], self.n)
 
     def render_plain_fp64(self, cam, cells_lo, cells_hi, out_lower, out_upper, tile: int = 0, stream=0):
         cells = make_cells(cells_lo, cells_hi)

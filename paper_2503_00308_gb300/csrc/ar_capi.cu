@@ -37,6 +37,9 @@ size_t cell_data_bytes_m6();
 int rec_width_m1();
 int rec_width_m4();
 int rec_width_m6();
+int rec_scalar_offset_m1();
+int rec_scalar_offset_m4();
+int rec_scalar_offset_m6();
 int launch_cell_prep_m1(const double *, const double *, const CallConst &, void *, cudaStream_t);
 int launch_cell_prep_m4(const double *, const double *, const CallConst &, void *, cudaStream_t);
 int launch_cell_prep_m6(const double *, const double *, const CallConst &, void *, cudaStream_t);
@@ -70,6 +73,11 @@ size_t cell_data_bytes(int M)
     return M == 1 ? cell_data_bytes_m1() : (M == 4 ? cell_data_bytes_m4() : cell_data_bytes_m6());
 }
 int rec_width(int M) { return M == 1 ? rec_width_m1() : (M == 4 ? rec_width_m4() : rec_width_m6()); }
+// offset of the scalar fields (o, tau, colour, flags, mu) within a record
+static int rec_scalar_offset(int M)
+{
+    return M == 1 ? rec_scalar_offset_m1() : (M == 4 ? rec_scalar_offset_m4() : rec_scalar_offset_m6());
+}
 int launch_cell_prep(int M, const double *lo, const double *hi, const CallConst &cc, void *cells, cudaStream_t st)
 {
     return M == 1 ? launch_cell_prep_m1(lo, hi, cc, cells, st)
@@ -589,6 +597,28 @@ static int tuned_tile(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const
     return AR_OK;
 }
 
+// The per-call constants of a render; returns the number of pose variables
+// the forms carry (1, 4 or 6): the active variables of the call, taken over
+// all cells so that every batch agrees on the form slots.
+static int call_const(const ar_scene *s, const ar_intrinsics *in, const ar_nominal_pose *pose,
+                      const ar_pose_box *cells, int32_t n_cells, CallConst &cc)
+{
+    std::memset(&cc, 0, sizeof cc);
+    int m_active = 0;
+    for (int k = 0; k < MAXV; ++k) {
+        bool act = false;
+        for (int c = 0; c < n_cells; ++c) act = act || cells[c].hi[k] > cells[c].lo[k];
+        cc.m_slot[k] = act ? m_active++ : -1;
+    }
+    cc.W = in->width; cc.H = in->height;
+    cc.fx = in->fx; cc.fy = in->fy; cc.cx = in->cx; cc.cy = in->cy; cc.near_plane = in->near_plane;
+    std::memcpy(cc.R0, pose->R_wc, sizeof cc.R0);
+    std::memcpy(cc.t0, pose->t, sizeof cc.t0);
+    cc.n_gauss = s->n;
+    cc.n_cells = n_cells;
+    return m_active <= 1 ? 1 : (m_active <= 4 ? 4 : 6);
+}
+
 int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_nominal_pose *pose,
                 const ar_pose_box *cells, int32_t n_cells, int32_t tile, float *out_lo, float *out_hi,
                 cudaStream_t st, bool profiling, ar_render_stats *stats, bool plain, int64_t ws_limit)
@@ -605,22 +635,9 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
     std::memset(&rs, 0, sizeof rs);
     rs.tile = TS;
     rs.ms_prep = rs.ms_bin = rs.ms_render = rs.ms_total = rs.ms_build = -1.f;
-    // active pose variables -> form slots (over all cells, so every batch agrees)
     CallConst cc;
-    std::memset(&cc, 0, sizeof cc);
-    int m_active = 0;
-    for (int k = 0; k < MAXV; ++k) {
-        bool act = false;
-        for (int c = 0; c < n_cells; ++c) act = act || cells[c].hi[k] > cells[c].lo[k];
-        cc.m_slot[k] = act ? m_active++ : -1;
-    }
-    const int M = m_active <= 1 ? 1 : (m_active <= 4 ? 4 : 6);
+    const int M = call_const(s, in, pose, cells, n_cells, cc);
     rs.m_vars = M;
-    cc.W = W; cc.H = H;
-    cc.fx = in->fx; cc.fy = in->fy; cc.cx = in->cx; cc.cy = in->cy; cc.near_plane = in->near_plane;
-    std::memcpy(cc.R0, pose->R_wc, sizeof cc.R0);
-    std::memcpy(cc.t0, pose->t, sizeof cc.t0);
-    cc.n_gauss = s->n;
     if (s->n == 0) {
         CK(cudaMemsetAsync(out_lo, 0, out_words * sizeof(float), st));
         CK(cudaMemsetAsync(out_hi, 0, out_words * sizeof(float), st));
@@ -847,6 +864,63 @@ int ar_render_concrete(ar_scene *s, const ar_intrinsics *in, const ar_nominal_po
         if (launch_concrete_render(ws.recs.as<double>(), ws.boxes.as<PixBox>(), ws.segs.as<uint32_t>(),
                                    ws.sege.as<uint32_t>(), bo.ent_ev, bo.ev_val, bo.ev_key, W, H, ntx, n_tiles, o, st))
             return fail(AR_EDEVICE, "concrete render launch: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    return AR_OK;
+}
+
+int ar_debug_records(ar_scene *s, const ar_intrinsics *in, const ar_nominal_pose *pose, const ar_pose_box *cell,
+                     double *out)
+{
+    if (!s || !out) return fail(AR_EINVAL, "null argument");
+    RK(validate_call(in, pose, cell, 1, 16));
+    CK(cudaSetDevice(s->device));
+    if (s->n == 0) return AR_OK;
+    Workspace &ws = s->ws;
+    CallConst cc;
+    const int M = call_const(s, in, pose, cell, 1, cc);
+    const int64_t n = s->n;
+    cudaStream_t st = 0;
+    RK(ws.cells_lohi.ensure(sizeof(double) * 2 * MAXV));
+    RK(ws.vN.ensure(sizeof(double) * 12 * n));
+    RK(ws.cells.ensure(cell_data_bytes(M)));
+    RK(ws.recs.ensure(sizeof(float) * rec_width(M) * n));
+    RK(ws.boxes.ensure(sizeof(PixBox) * n));
+    RK(ws.keys.ensure(sizeof(double) * 2 * n));
+    RK(ws.counters.ensure(sizeof(unsigned long long) * 8));
+    double lohi[2 * MAXV];
+    for (int k = 0; k < MAXV; ++k) { lohi[k] = cell->lo[k]; lohi[MAXV + k] = cell->hi[k]; }
+    CK(cudaMemcpy(ws.cells_lohi.p, lohi, sizeof lohi, cudaMemcpyHostToDevice));
+    CK(cudaMemset(ws.counters.p, 0, sizeof(unsigned long long) * 8));
+    const double *d_lo = ws.cells_lohi.as<double>(), *d_hi = d_lo + MAXV;
+    if (launch_pose_prep(s->uw, s->Mw, s->n, cc, ws.vN.as<double>(), st) ||
+        launch_cell_prep(M, d_lo, d_hi, cc, ws.cells.p, st) ||
+        launch_record_prep(M, ws.vN.as<double>(), s->tau, s->opac, s->rgb, cc, ws.cells.p, 16, ws.recs.as<float>(),
+                           ws.boxes.as<PixBox>(), ws.keys.as<double>(), ws.counters.as<unsigned long long>(), st))
+        return fail(AR_EDEVICE, "record prep launch: %s", cudaGetErrorString(cudaGetLastError()));
+    const int w = rec_width(M);
+    std::vector<PixBox> boxes((size_t)n);
+    std::vector<double> keys((size_t)2 * n);
+    std::vector<float> recs((size_t)w * n);
+    CK(cudaMemcpy(boxes.data(), ws.boxes.p, sizeof(PixBox) * n, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(keys.data(), ws.keys.p, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(recs.data(), ws.recs.p, sizeof(float) * w * n, cudaMemcpyDeviceToHost));
+    const int sc = rec_scalar_offset(M);
+    for (int64_t g = 0; g < n; ++g) {
+        double *o = out + 10 * g;
+        const PixBox &b = boxes[(size_t)g];
+        const bool valid = b.x0 >= 0;
+        for (int k = 0; k < 10; ++k) o[k] = 0.0;
+        if (!valid) continue;
+        const float *r = &recs[(size_t)w * g];
+        uint32_t flags;
+        std::memcpy(&flags, &r[sc + 6], sizeof flags);
+        o[0] = 1.0;
+        o[1] = (flags & 2u) ? 1.0 : 0.0;
+        o[2] = keys[2 * g];
+        o[3] = keys[2 * g + 1];
+        o[4] = b.x0; o[5] = b.x1; o[6] = b.y0; o[7] = b.y1;
+        o[8] = r[sc + 7];
+        o[9] = r[sc + 8];
     }
     return AR_OK;
 }

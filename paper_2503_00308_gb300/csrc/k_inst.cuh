@@ -11,6 +11,7 @@ namespace ar {
 
 size_t AR_CAT(cell_data_bytes_m, AR_M)() { return sizeof(CellData<AR_M>); }
 int AR_CAT(rec_width_m, AR_M)() { return Rec<AR_M>::WIDTH; }
+int AR_CAT(rec_scalar_offset_m, AR_M)() { return Rec<AR_M>::SC; }
 
 int AR_CAT(launch_cell_prep_m, AR_M)(const double *lo, const double *hi, const CallConst &cc, void *cells,
                                      cudaStream_t st)

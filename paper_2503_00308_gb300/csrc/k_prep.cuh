@@ -286,59 +286,14 @@ __device__ __forceinline__ int64_t record_decide(const double *__restrict__ vN, 
         klo = dsub(klo, pad);
         khi = dadd(khi, pad);
     }
-    double mu_lo[2], mu_hi[2];
-    {
-        DI Ri[9], vs[3];
-        for (int e = 0; e < 9; ++e) Ri[e] = DI{cd.rd_int[e][0], cd.rd_int[e][1]};
-        for (int b = 0; b < 3; ++b) vs[b] = DI{dsub(v[b], cd.s_int[b][1]), dsub(v[b], cd.s_int[b][0])};
-        const double dl = fmax(dlo, nearp);
-        DI D = {dl, dhi};
-        DI ucx = di_add(di_add(di_mul(Ri[0], vs[0]), di_mul(Ri[3], vs[1])), di_mul(Ri[6], vs[2]));
-        DI ucy = di_add(di_add(di_mul(Ri[1], vs[0]), di_mul(Ri[4], vs[1])), di_mul(Ri[7], vs[2]));
-        const double fx = cc.fx, fy = cc.fy, cx = cc.cx, cy = cc.cy;
-        DI mux = {dadd(cx, dmul(fx, fmin(ucx.l / D.l, ucx.l / D.u))), dadd(cx, dmul(fx, fmax(ucx.u / D.l, ucx.u / D.u)))};
-        DI muy = {dadd(cy, dmul(fy, fmin(ucy.l / D.l, ucy.l / D.u))), dadd(cy, dmul(fy, fmax(ucy.u / D.l, ucy.u / D.u)))};
-        // frustum guard band (3DGS convention): a mean outside it at every
-        // pose of the cell drops the pair; outside it at some pose makes the
-        // lower alpha 0
-        {
-            const double gx = dmul(GUARD, (double)cc.W), gy = dmul(GUARD, (double)cc.H);
-            const double ml = dsub(mux.l, dmul(BOX_SLACK, dadd(1.0, fabs(mux.l))));
-            const double mh = dadd(mux.u, dmul(BOX_SLACK, dadd(1.0, fabs(mux.u))));
-            const double nl = dsub(muy.l, dmul(BOX_SLACK, dadd(1.0, fabs(muy.l))));
-            const double nh = dadd(muy.u, dmul(BOX_SLACK, dadd(1.0, fabs(muy.u))));
-            if (ml > dadd(cx, gx) || mh < dsub(cx, gx) || nl > dadd(cy, gy) || nh < dsub(cy, gy)) return -1;
-            if (!(ml >= dsub(cx, gx) && mh <= dadd(cx, gx) && nl >= dsub(cy, gy) && nh <= dadd(cy, gy)))
-                straddle = true;
-        }
-        double X00 = 0, X11 = 0;
-        for (int c = 0; c < 3; ++c) {
-            DI m[3];
-            for (int a = 0; a < 3; ++a)
-                m[a] = di_add(di_add(di_scale(Ri[a], N[c]), di_scale(Ri[3 + a], N[3 + c])), di_scale(Ri[6 + a], N[6 + c]));
-            // D = [max(d_lo, near), d_hi] is positive
-            DI p0 = di_scale(di_add(di_mul_pos(D, m[0]), di_scale(di_mul(ucx, m[2]), -1.0)), fx);
-            DI p1 = di_scale(di_add(di_mul_pos(D, m[1]), di_scale(di_mul(ucy, m[2]), -1.0)), fy);
-            X00 = dadd(X00, di_sqmax(p0));
-            X11 = dadd(X11, di_sqmax(p1));
-        }
-        const double dl2 = dmul(dl, dl);
-        const double rx = sqrt(dmul(tau, X00)) / dl2, ry = sqrt(dmul(tau, X11)) / dl2;
-        double xl = dsub(mux.l, rx), xh = dadd(mux.u, rx), yl = dsub(muy.l, ry), yh = dadd(muy.u, ry);
-        xl = dsub(xl, dmul(BOX_SLACK, dadd(1.0, fabs(xl))));
-        xh = dadd(xh, dmul(BOX_SLACK, dadd(1.0, fabs(xh))));
-        yl = dsub(yl, dmul(BOX_SLACK, dadd(1.0, fabs(yl))));
-        yh = dadd(yh, dmul(BOX_SLACK, dadd(1.0, fabs(yh))));
-        if (!(xh >= xl) || !(yh >= yl)) return -1;
-        double fx0 = ceil(dsub(xl, 0.5)), fx1 = floor(dsub(xh, 0.5));
-        double fy0 = ceil(dsub(yl, 0.5)), fy1 = floor(dsub(yh, 0.5));
-        fx0 = fmax(fx0, 0.0); fy0 = fmax(fy0, 0.0);
-        fx1 = fmin(fx1, (double)(cc.W - 1)); fy1 = fmin(fy1, (double)(cc.H - 1));
-        if (fx0 > fx1 || fy0 > fy1) return -1;
-        box = PixBox{(int)fx0, (int)fx1, (int)fy0, (int)fy1};
-        mu_lo[0] = mux.l; mu_hi[0] = mux.u; mu_lo[1] = muy.l; mu_hi[1] = muy.u;
-    }
-
+    // screen box, projected-mean pixel centre and guard band: decided from
+    // FP32 enclosures of the FP64 values where they settle every decision,
+    // else in FP64 (the same values either way)
+    PixBox box;
+    double mu_px[2];
+    int sr = screen_fp32(cd.rd_int, cd.s_int, v, N, dlo, dhi, tau, cc, box, mu_px, straddle);
+    if (sr == SCREEN_UNDECIDED) sr = screen_fp64(cd.rd_int, cd.s_int, v, N, dlo, dhi, tau, cc, box, mu_px, straddle);
+    if (sr == SCREEN_DROP) return -1;
     RO *rec = recs + ri * RL::WIDTH;
     const uint32_t flags = (straddle ? F_STRADDLE : 0u) | (klo < khi ? F_OPEN : 0u);
     rec[RL::O] = opacity[g];
@@ -346,8 +301,8 @@ __device__ __forceinline__ int64_t record_decide(const double *__restrict__ vN, 
     rec_up(tau, rec[RL::TAU_UP]);
     for (int k = 0; k < 3; ++k) rec[RL::COL + k] = rgb[3 * g + k];
     // pixel centre near the projected mean, the expansion point of R = mu S - P
-    rec[RL::MU_X] = (RO)(floor(fmin(fmax(0.5 * (mu_lo[0] + mu_hi[0]), -1e6), 1e6)) + 0.5);
-    rec[RL::MU_Y] = (RO)(floor(fmin(fmax(0.5 * (mu_lo[1] + mu_hi[1]), -1e6), 1e6)) + 0.5);
+    rec[RL::MU_X] = (RO)mu_px[0];
+    rec[RL::MU_Y] = (RO)mu_px[1];
     rec_put_flags(rec + RL::FLAGS, flags);
     keys[2 * ri] = klo;
     keys[2 * ri + 1] = khi;
