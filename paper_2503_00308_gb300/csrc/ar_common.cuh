@@ -186,6 +186,92 @@ __device__ __forceinline__ DI di_scale(DI a, double s)
 }
 __device__ __forceinline__ double di_sqmax(DI a) { return fmax(dmul(a.l, a.l), dmul(a.u, a.u)); }
 
+// ---------------------------------------------------------------------------
+// FP32 enclosures of FP64 values, to take FP64 decisions at FP32 cost.  An
+// E32 holds floats lo <= hi with lo <= x <= hi for the double x that an FP64
+// expression (rounded to nearest at every step) computes.  Each operation
+// maps enclosures of its FP64 operands to an enclosure of its FP64 result:
+// its directed FP32 results bracket the exact result of the operation for
+// every operand value in the enclosures, and as floats are doubles, rounding
+// that exact result to the nearest double stays between them (rounding is
+// monotone and leaves representable values fixed).  e_chk clears ok for a
+// value beyond 1e30 in magnitude, an infinity or a NaN, so that no NaN or
+// infinity can enter a later operation unnoticed; the caller then decides in
+// FP64.
+struct E32 {
+    float lo, hi;
+};
+struct EI {  // enclosures of both ends of an FP64 interval (a DI)
+    E32 l, u;
+};
+__device__ __forceinline__ E32 e_chk(E32 x, bool &ok)
+{
+    ok = ok && fabsf(x.lo) <= 1e30f && fabsf(x.hi) <= 1e30f;
+    return x;
+}
+__device__ __forceinline__ E32 e_of(double x) { return E32{__double2float_rd(x), __double2float_ru(x)}; }
+__device__ __forceinline__ E32 e_add(E32 a, E32 b) { return E32{__fadd_rd(a.lo, b.lo), __fadd_ru(a.hi, b.hi)}; }
+__device__ __forceinline__ E32 e_sub(E32 a, E32 b) { return E32{__fsub_rd(a.lo, b.hi), __fsub_ru(a.hi, b.lo)}; }
+__device__ __forceinline__ E32 e_neg(E32 a) { return E32{-a.hi, -a.lo}; }
+__device__ __forceinline__ E32 e_min(E32 a, E32 b) { return E32{fminf(a.lo, b.lo), fminf(a.hi, b.hi)}; }
+__device__ __forceinline__ E32 e_max(E32 a, E32 b) { return E32{fmaxf(a.lo, b.lo), fmaxf(a.hi, b.hi)}; }
+__device__ __forceinline__ E32 e_hull(E32 a, E32 b) { return E32{fminf(a.lo, b.lo), fmaxf(a.hi, b.hi)}; }
+__device__ __forceinline__ E32 e_mul(E32 a, E32 b)
+{
+    const float l = fminf(fminf(__fmul_rd(a.lo, b.lo), __fmul_rd(a.lo, b.hi)),
+                          fminf(__fmul_rd(a.hi, b.lo), __fmul_rd(a.hi, b.hi)));
+    const float h = fmaxf(fmaxf(__fmul_ru(a.lo, b.lo), __fmul_ru(a.lo, b.hi)),
+                          fmaxf(__fmul_ru(a.hi, b.lo), __fmul_ru(a.hi, b.hi)));
+    return E32{l, h};
+}
+// a / d for d > 0 (d.lo > 0)
+__device__ __forceinline__ E32 e_div_pos(E32 a, E32 d)
+{
+    return E32{fminf(__fdiv_rd(a.lo, d.lo), __fdiv_rd(a.lo, d.hi)), fmaxf(__fdiv_ru(a.hi, d.lo), __fdiv_ru(a.hi, d.hi))};
+}
+// sqrt of an FP64 value x >= 0
+__device__ __forceinline__ E32 e_sqrt(E32 a) { return E32{__fsqrt_rd(fmaxf(a.lo, 0.f)), __fsqrt_ru(a.hi)}; }
+__device__ __forceinline__ E32 e_abs(E32 a)
+{
+    if (a.lo >= 0.f) return a;
+    if (a.hi <= 0.f) return e_neg(a);
+    return E32{0.f, fmaxf(-a.lo, a.hi)};
+}
+// a > b: 1 certainly, 0 certainly not, -1 not settled by the enclosures
+__device__ __forceinline__ int e_gt(E32 a, E32 b) { return a.lo > b.hi ? 1 : (a.hi <= b.lo ? 0 : -1); }
+// a >= b, likewise
+__device__ __forceinline__ int e_ge(E32 a, E32 b) { return a.lo >= b.hi ? 1 : (a.hi < b.lo ? 0 : -1); }
+// the interval operations of the screen box (di_*), on enclosures
+__device__ __forceinline__ EI ei_add(EI a, EI b, bool &ok)
+{
+    return EI{e_chk(e_add(a.l, b.l), ok), e_chk(e_add(a.u, b.u), ok)};
+}
+__device__ __forceinline__ EI ei_mul(EI a, EI b, bool &ok)
+{
+    const E32 p0 = e_mul(a.l, b.l), p1 = e_mul(a.l, b.u), p2 = e_mul(a.u, b.l), p3 = e_mul(a.u, b.u);
+    return EI{e_chk(e_min(e_min(p0, p1), e_min(p2, p3)), ok), e_chk(e_max(e_max(p0, p1), e_max(p2, p3)), ok)};
+}
+// di_mul_pos: the product is picked by the sign of b's ends; where that sign
+// is not settled, the hull of both candidates
+__device__ __forceinline__ EI ei_mul_pos(EI a, EI b, bool &ok)
+{
+    const E32 l1 = e_mul(a.l, b.l), l2 = e_mul(a.u, b.l);
+    const E32 u1 = e_mul(a.u, b.u), u2 = e_mul(a.l, b.u);
+    const E32 l = b.l.lo >= 0.f ? l1 : (b.l.hi < 0.f ? l2 : e_hull(l1, l2));
+    const E32 u = b.u.lo >= 0.f ? u1 : (b.u.hi < 0.f ? u2 : e_hull(u1, u2));
+    return EI{e_chk(l, ok), e_chk(u, ok)};
+}
+// di_scale by an exact double s (the branch on its sign is exact)
+__device__ __forceinline__ EI ei_scale(EI a, double s, bool &ok)
+{
+    const E32 se = e_of(s);
+    return s >= 0 ? EI{e_chk(e_mul(se, a.l), ok), e_chk(e_mul(se, a.u), ok)}
+                  : EI{e_chk(e_mul(se, a.u), ok), e_chk(e_mul(se, a.l), ok)};
+}
+// di_scale by -1 (exact)
+__device__ __forceinline__ EI ei_neg(EI a) { return EI{e_neg(a.u), e_neg(a.l)}; }
+__device__ __forceinline__ E32 ei_sqmax(EI a) { return e_max(e_mul(a.l, a.l), e_mul(a.u, a.u)); }
+
 // order-preserving map of a double to uint64 (-0 folded onto +0)
 __device__ __forceinline__ uint64_t key_bits(double x)
 {

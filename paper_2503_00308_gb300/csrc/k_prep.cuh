@@ -230,6 +230,170 @@ struct PrepCount {
     uint32_t triples, fallback, valid, tiles, split;
 };
 
+// ---- screen box (Algorithm 1 lines 3-5 on intervals): the pixel box of the
+// centres that can lie in the ellipse m <= tau at some pose of the cell with
+// d > near, the projected-mean pixel centre mu_px (the expansion point of the
+// pixel stage) and the frustum guard band.  Inputs: the concretised R_delta
+// entries Ri and s, the Gaussian's v and N, its depth interval [dlo, dhi] and
+// tau.  Returns SCREEN_DROP when the pair reaches no pixel, SCREEN_KEEP with
+// box and mu_px set (and straddle set where the guard band is crossed).
+enum { SCREEN_DROP = 0, SCREEN_KEEP = 1, SCREEN_UNDECIDED = 2 };
+
+// The definition, in FP64 with round-to-nearest steps in a fixed order.
+static __device__ __noinline__ int screen_fp64(const double (*rd_int)[2], const double (*s_int)[2], const double *v,
+                                        const double *N, double dlo, double dhi, double tau, const CallConst &cc,
+                                        PixBox &box, double *mu_px, bool &straddle)
+{
+    const double nearp = (double)cc.near_plane;
+    DI Ri[9], vs[3];
+    for (int e = 0; e < 9; ++e) Ri[e] = DI{rd_int[e][0], rd_int[e][1]};
+    for (int b = 0; b < 3; ++b) vs[b] = DI{dsub(v[b], s_int[b][1]), dsub(v[b], s_int[b][0])};
+    const double dl = fmax(dlo, nearp);
+    DI D = {dl, dhi};
+    DI ucx = di_add(di_add(di_mul(Ri[0], vs[0]), di_mul(Ri[3], vs[1])), di_mul(Ri[6], vs[2]));
+    DI ucy = di_add(di_add(di_mul(Ri[1], vs[0]), di_mul(Ri[4], vs[1])), di_mul(Ri[7], vs[2]));
+    const double fx = cc.fx, fy = cc.fy, cx = cc.cx, cy = cc.cy;
+    // D > 0, so min(u / D_lo, u / D_hi) is u / D_hi for u >= 0 and u / D_lo
+    // below (the same rounded quotient: division is monotone in D)
+    DI mux = {dadd(cx, dmul(fx, ucx.l / (ucx.l >= 0 ? D.u : D.l))), dadd(cx, dmul(fx, ucx.u / (ucx.u >= 0 ? D.l : D.u)))};
+    DI muy = {dadd(cy, dmul(fy, ucy.l / (ucy.l >= 0 ? D.u : D.l))), dadd(cy, dmul(fy, ucy.u / (ucy.u >= 0 ? D.l : D.u)))};
+    // frustum guard band (3DGS convention): a mean outside it at every pose
+    // of the cell drops the pair; outside it at some pose makes the lower
+    // alpha 0
+    {
+        const double gx = dmul(GUARD, (double)cc.W), gy = dmul(GUARD, (double)cc.H);
+        const double ml = dsub(mux.l, dmul(BOX_SLACK, dadd(1.0, fabs(mux.l))));
+        const double mh = dadd(mux.u, dmul(BOX_SLACK, dadd(1.0, fabs(mux.u))));
+        const double nl = dsub(muy.l, dmul(BOX_SLACK, dadd(1.0, fabs(muy.l))));
+        const double nh = dadd(muy.u, dmul(BOX_SLACK, dadd(1.0, fabs(muy.u))));
+        if (ml > dadd(cx, gx) || mh < dsub(cx, gx) || nl > dadd(cy, gy) || nh < dsub(cy, gy)) return SCREEN_DROP;
+        if (!(ml >= dsub(cx, gx) && mh <= dadd(cx, gx) && nl >= dsub(cy, gy) && nh <= dadd(cy, gy)))
+            straddle = true;
+    }
+    double X00 = 0, X11 = 0;
+    for (int c = 0; c < 3; ++c) {
+        DI m[3];
+        for (int a = 0; a < 3; ++a)
+            m[a] = di_add(di_add(di_scale(Ri[a], N[c]), di_scale(Ri[3 + a], N[3 + c])), di_scale(Ri[6 + a], N[6 + c]));
+        DI p0 = di_scale(di_add(di_mul_pos(D, m[0]), di_scale(di_mul(ucx, m[2]), -1.0)), fx);
+        DI p1 = di_scale(di_add(di_mul_pos(D, m[1]), di_scale(di_mul(ucy, m[2]), -1.0)), fy);
+        X00 = dadd(X00, di_sqmax(p0));
+        X11 = dadd(X11, di_sqmax(p1));
+    }
+    const double dl2 = dmul(dl, dl);
+    const double rx = sqrt(dmul(tau, X00)) / dl2, ry = sqrt(dmul(tau, X11)) / dl2;
+    double xl = dsub(mux.l, rx), xh = dadd(mux.u, rx), yl = dsub(muy.l, ry), yh = dadd(muy.u, ry);
+    xl = dsub(xl, dmul(BOX_SLACK, dadd(1.0, fabs(xl))));
+    xh = dadd(xh, dmul(BOX_SLACK, dadd(1.0, fabs(xh))));
+    yl = dsub(yl, dmul(BOX_SLACK, dadd(1.0, fabs(yl))));
+    yh = dadd(yh, dmul(BOX_SLACK, dadd(1.0, fabs(yh))));
+    if (!(xh >= xl) || !(yh >= yl)) return SCREEN_DROP;
+    double fx0 = ceil(dsub(xl, 0.5)), fx1 = floor(dsub(xh, 0.5));
+    double fy0 = ceil(dsub(yl, 0.5)), fy1 = floor(dsub(yh, 0.5));
+    fx0 = fmax(fx0, 0.0); fy0 = fmax(fy0, 0.0);
+    fx1 = fmin(fx1, (double)(cc.W - 1)); fy1 = fmin(fy1, (double)(cc.H - 1));
+    if (fx0 > fx1 || fy0 > fy1) return SCREEN_DROP;
+    box = PixBox{(int)fx0, (int)fx1, (int)fy0, (int)fy1};
+    mu_px[0] = floor(fmin(fmax(0.5 * (mux.l + mux.u), -1e6), 1e6)) + 0.5;
+    mu_px[1] = floor(fmin(fmax(0.5 * (muy.l + muy.u), -1e6), 1e6)) + 0.5;
+    return SCREEN_KEEP;
+}
+
+// The same decisions from FP32 enclosures (E32) of every FP64 value above,
+// step for step: where each comparison, ceil and floor of screen_fp64 is
+// settled by the enclosures, it has the same outcome as in FP64; otherwise
+// (or when a value leaves the checked range) SCREEN_UNDECIDED.  GB300's FP64
+// rate is about 1/64 of its FP32 rate, and the FP64 path is then taken by a
+// small fraction of the pairs.
+static __device__ __forceinline__ int screen_fp32(const double (*rd_int)[2], const double (*s_int)[2], const double *v,
+                                           const double *N, double dlo, double dhi, double tau, const CallConst &cc,
+                                           PixBox &box, double *mu_px, bool &straddle)
+{
+    bool ok = true;
+    const double nearp = (double)cc.near_plane;
+    EI Ri[9], vs[3];
+    for (int e = 0; e < 9; ++e) Ri[e] = EI{e_of(rd_int[e][0]), e_of(rd_int[e][1])};
+    for (int b = 0; b < 3; ++b) {
+        const E32 vb = e_of(v[b]);
+        vs[b] = EI{e_chk(e_sub(vb, e_of(s_int[b][1])), ok), e_chk(e_sub(vb, e_of(s_int[b][0])), ok)};
+    }
+    const double dl = fmax(dlo, nearp);
+    const EI D = {e_of(dl), e_of(dhi)};
+    const EI ucx = ei_add(ei_add(ei_mul(Ri[0], vs[0], ok), ei_mul(Ri[3], vs[1], ok), ok), ei_mul(Ri[6], vs[2], ok), ok);
+    const EI ucy = ei_add(ei_add(ei_mul(Ri[1], vs[0], ok), ei_mul(Ri[4], vs[1], ok), ok), ei_mul(Ri[7], vs[2], ok), ok);
+    const E32 fx = e_of((double)cc.fx), fy = e_of((double)cc.fy), cx = e_of((double)cc.cx), cy = e_of((double)cc.cy);
+    // u / D_hi or u / D_lo by the sign of u; where the sign is not settled,
+    // the enclosure of either quotient
+    auto qlo = [&](E32 u) {
+        const E32 a = e_div_pos(u, D.u), b = e_div_pos(u, D.l);
+        return u.lo >= 0.f ? a : (u.hi < 0.f ? b : e_hull(a, b));
+    };
+    auto qhi = [&](E32 u) {
+        const E32 a = e_div_pos(u, D.l), b = e_div_pos(u, D.u);
+        return u.lo >= 0.f ? a : (u.hi < 0.f ? b : e_hull(a, b));
+    };
+    const EI mux = {e_chk(e_add(cx, e_mul(fx, qlo(ucx.l))), ok), e_chk(e_add(cx, e_mul(fx, qhi(ucx.u))), ok)};
+    const EI muy = {e_chk(e_add(cy, e_mul(fy, qlo(ucy.l))), ok), e_chk(e_add(cy, e_mul(fy, qhi(ucy.u))), ok)};
+    if (!ok) return SCREEN_UNDECIDED;
+    const E32 one = {1.f, 1.f}, slack = e_of(BOX_SLACK);
+    auto widen_dn = [&](E32 x) { return e_sub(x, e_mul(slack, e_add(one, e_abs(x)))); };
+    auto widen_up = [&](E32 x) { return e_add(x, e_mul(slack, e_add(one, e_abs(x)))); };
+    {
+        const double gx = dmul(GUARD, (double)cc.W), gy = dmul(GUARD, (double)cc.H);
+        const E32 cxp = e_of(dadd((double)cc.cx, gx)), cxm = e_of(dsub((double)cc.cx, gx));
+        const E32 cyp = e_of(dadd((double)cc.cy, gy)), cym = e_of(dsub((double)cc.cy, gy));
+        const E32 ml = widen_dn(mux.l), mh = widen_up(mux.u), nl = widen_dn(muy.l), nh = widen_up(muy.u);
+        // drop: ml > cx + gx || mh < cx - gx || nl > cy + gy || nh < cy - gy
+        const int d0 = e_gt(ml, cxp), d1 = e_gt(cxm, mh), d2 = e_gt(nl, cyp), d3 = e_gt(cym, nh);
+        if (d0 == 1 || d1 == 1 || d2 == 1 || d3 == 1) return SCREEN_DROP;
+        if (d0 < 0 || d1 < 0 || d2 < 0 || d3 < 0) return SCREEN_UNDECIDED;
+        // inside: ml >= cx - gx && mh <= cx + gx && nl >= cy - gy && nh <= cy + gy
+        const int i0 = e_ge(ml, cxm), i1 = e_ge(cxp, mh), i2 = e_ge(nl, cym), i3 = e_ge(cyp, nh);
+        if (i0 < 0 || i1 < 0 || i2 < 0 || i3 < 0) return SCREEN_UNDECIDED;
+        if (!(i0 && i1 && i2 && i3)) straddle = true;
+    }
+    E32 X00 = {0.f, 0.f}, X11 = {0.f, 0.f};
+    for (int c = 0; c < 3; ++c) {
+        EI m[3];
+        for (int a = 0; a < 3; ++a)
+            m[a] = ei_add(ei_add(ei_scale(Ri[a], N[c], ok), ei_scale(Ri[3 + a], N[3 + c], ok), ok),
+                          ei_scale(Ri[6 + a], N[6 + c], ok), ok);
+        const EI p0 = ei_scale(ei_add(ei_mul_pos(D, m[0], ok), ei_neg(ei_mul(ucx, m[2], ok)), ok), cc.fx, ok);
+        const EI p1 = ei_scale(ei_add(ei_mul_pos(D, m[1], ok), ei_neg(ei_mul(ucy, m[2], ok)), ok), cc.fy, ok);
+        X00 = e_chk(e_add(X00, ei_sqmax(p0)), ok);
+        X11 = e_chk(e_add(X11, ei_sqmax(p1)), ok);
+    }
+    const E32 dl2 = e_mul(e_of(dl), e_of(dl)), t = e_of(tau);
+    const E32 rx = e_chk(e_div_pos(e_sqrt(e_mul(t, X00)), dl2), ok);
+    const E32 ry = e_chk(e_div_pos(e_sqrt(e_mul(t, X11)), dl2), ok);
+    if (!ok) return SCREEN_UNDECIDED;
+    const E32 xl = widen_dn(e_sub(mux.l, rx)), xh = widen_up(e_add(mux.u, rx));
+    const E32 yl = widen_dn(e_sub(muy.l, ry)), yh = widen_up(e_add(muy.u, ry));
+    // (xh >= xl and yh >= yl hold: the enclosures are finite and ordered)
+    if (e_ge(xh, xl) != 1 || e_ge(yh, yl) != 1) return SCREEN_UNDECIDED;
+    const E32 half = {0.5f, 0.5f};
+    const E32 ax = e_sub(xl, half), bx = e_sub(xh, half), ay = e_sub(yl, half), by = e_sub(yh, half);
+    float fx0 = ceilf(ax.lo), fx1 = floorf(bx.lo), fy0 = ceilf(ay.lo), fy1 = floorf(by.lo);
+    if (fx0 != ceilf(ax.hi) || fx1 != floorf(bx.hi) || fy0 != ceilf(ay.hi) || fy1 != floorf(by.hi))
+        return SCREEN_UNDECIDED;
+    fx0 = fmaxf(fx0, 0.f); fy0 = fmaxf(fy0, 0.f);
+    fx1 = fminf(fx1, (float)(cc.W - 1)); fy1 = fminf(fy1, (float)(cc.H - 1));
+    if (fx0 > fx1 || fy0 > fy1) return SCREEN_DROP;
+    // the midpoint of the mean's interval, clamped, floored (0.5 scales exactly)
+    float mp[2];
+    const EI mu2[2] = {mux, muy};
+    for (int k = 0; k < 2; ++k) {
+        const E32 sm = e_add(mu2[k].l, mu2[k].u);
+        const float a = floorf(fminf(fmaxf(0.5f * sm.lo, -1e6f), 1e6f)), b = floorf(fminf(fmaxf(0.5f * sm.hi, -1e6f), 1e6f));
+        if (a != b) return SCREEN_UNDECIDED;
+        mp[k] = a;
+    }
+    box = PixBox{(int)fx0, (int)fx1, (int)fy0, (int)fy1};
+    mu_px[0] = (double)mp[0] + 0.5;
+    mu_px[1] = (double)mp[1] + 0.5;
+    return SCREEN_KEEP;
+}
+
 // The decision part of one (Gaussian, cell) pair: depth forms, near-plane
 // class, depth key, pixel box and projected-mean interval, all in FP64.  It
 // writes the pair's key interval and box, and the scalar fields of its record
@@ -289,7 +453,6 @@ __device__ __forceinline__ int64_t record_decide(const double *__restrict__ vN, 
     // screen box, projected-mean pixel centre and guard band: decided from
     // FP32 enclosures of the FP64 values where they settle every decision,
     // else in FP64 (the same values either way)
-    PixBox box;
     double mu_px[2];
     int sr = screen_fp32(cd.rd_int, cd.s_int, v, N, dlo, dhi, tau, cc, box, mu_px, straddle);
     if (sr == SCREEN_UNDECIDED) sr = screen_fp64(cd.rd_int, cd.s_int, v, N, dlo, dhi, tau, cc, box, mu_px, straddle);
