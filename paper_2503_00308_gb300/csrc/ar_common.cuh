@@ -32,6 +32,18 @@ template <int M> struct CellData {
     double g[M];                              // depth-key offset (translation part of d)
     double rd_int[9][2];                      // concretised R_delta entries
     double s_int[3][2];                       // concretised s
+    // FP32 enclosures of FP64 constants of the screen-box filter
+    float rd_int32[9][2][2];                  // of rd_int[e][end]: [lo, hi]
+    float s_int32[3][2][2];                   // of s_int[a][end]
+    float guard32[4][2];                      // of cx + gx, cx - gx, cy + gy, cy - gy
+    float slack32[2];                         // of BOX_SLACK
+    // per-cell parts of the depth chain d = sum_b R_delta[b][2] (v_b - s_b):
+    // the interval [lo, hi] of each R_delta[b][2] and its midpoint, the
+    // translation-slot coefficients of d and of the depth-key form, and the
+    // slot ranges (translation slots [0, n_t), rotation slots [n_t, n_a))
+    double dx[3][3];
+    double dd_t[M], kd_t[M];
+    int n_t, n_a;
     SB<M, double> rd64[9];  // the same forms widened by a relative 1e-14 (sound in FP64)
     SB<M, double> s64[3];
 };
@@ -261,12 +273,12 @@ __device__ __forceinline__ EI ei_mul_pos(EI a, EI b, bool &ok)
     const E32 u = b.u.lo >= 0.f ? u1 : (b.u.hi < 0.f ? u2 : e_hull(u1, u2));
     return EI{e_chk(l, ok), e_chk(u, ok)};
 }
-// di_scale by an exact double s (the branch on its sign is exact)
-__device__ __forceinline__ EI ei_scale(EI a, double s, bool &ok)
+// di_scale by a double s given by its enclosure se (se = e_of(s)): s >= 0
+// exactly when se.lo >= 0 (rounding down keeps the sign, and -0 stays -0)
+__device__ __forceinline__ EI ei_scale(EI a, E32 se, bool &ok)
 {
-    const E32 se = e_of(s);
-    return s >= 0 ? EI{e_chk(e_mul(se, a.l), ok), e_chk(e_mul(se, a.u), ok)}
-                  : EI{e_chk(e_mul(se, a.u), ok), e_chk(e_mul(se, a.l), ok)};
+    return se.lo >= 0.f ? EI{e_chk(e_mul(se, a.l), ok), e_chk(e_mul(se, a.u), ok)}
+                        : EI{e_chk(e_mul(se, a.u), ok), e_chk(e_mul(se, a.l), ok)};
 }
 // di_scale by -1 (exact)
 __device__ __forceinline__ EI ei_neg(EI a) { return EI{e_neg(a.u), e_neg(a.l)}; }

@@ -129,6 +129,56 @@ __global__ void cell_prep_kernel(const double *__restrict__ cells_lo, const doub
         cd.s_int[a][0] = df_min(f);
         cd.s_int[a][1] = df_max(f);
     }
+    for (int e = 0; e < 9; ++e)
+        for (int t = 0; t < 2; ++t) {
+            cd.rd_int32[e][t][0] = __double2float_rd(cd.rd_int[e][t]);
+            cd.rd_int32[e][t][1] = __double2float_ru(cd.rd_int[e][t]);
+        }
+    for (int a = 0; a < 3; ++a)
+        for (int t = 0; t < 2; ++t) {
+            cd.s_int32[a][t][0] = __double2float_rd(cd.s_int[a][t]);
+            cd.s_int32[a][t][1] = __double2float_ru(cd.s_int[a][t]);
+        }
+    {
+        const double gx = dmul(GUARD, (double)cc.W), gy = dmul(GUARD, (double)cc.H);
+        const double gc[4] = {dadd((double)cc.cx, gx), dsub((double)cc.cx, gx), dadd((double)cc.cy, gy),
+                              dsub((double)cc.cy, gy)};
+        for (int i = 0; i < 4; ++i) {
+            cd.guard32[i][0] = __double2float_rd(gc[i]);
+            cd.guard32[i][1] = __double2float_ru(gc[i]);
+        }
+        cd.slack32[0] = __double2float_rd(BOX_SLACK);
+        cd.slack32[1] = __double2float_ru(BOX_SLACK);
+    }
+    // per-cell parts of the depth chain (see record_decide): R_delta[b][2]
+    // has coefficients on the rotation slots only and s_b on the translation
+    // slots only, so the products xm * (-s_b) and their sums over b are the
+    // same for every Gaussian of the cell
+    {
+        int nt = 0, na = 0;
+        for (int k = 0; k < MAXV; ++k) {
+            if (cc.m_slot[k] < 0) continue;
+            ++na;
+            if (k < 3) ++nt;
+        }
+        cd.n_t = nt;
+        cd.n_a = na;
+        for (int j = 0; j < M; ++j) cd.dd_t[j] = 0.0;
+        for (int b = 0; b < 3; ++b) {
+            const int e = 3 * b + 2;
+            DF<M> lo, hi;
+            for (int j = 0; j < M; ++j) { lo.c[j] = cd.rd_lo[e][j]; hi.c[j] = cd.rd_hi[e][j]; }
+            lo.k = cd.rd_lo[e][M]; hi.k = cd.rd_hi[e][M];
+            const double xl = df_min(lo), xh = df_max(hi);
+            const double xm = dmul(0.5, dadd(xl, xh));
+            cd.dx[b][0] = xl; cd.dx[b][1] = xh; cd.dx[b][2] = xm;
+            for (int j = 0; j < nt; ++j) {
+                const double t = dmul(xm, dsub(0.0, cd.s[b][j]));
+                cd.dd_t[j] = b == 0 ? t : dadd(cd.dd_t[j], t);
+            }
+        }
+        for (int j = 0; j < M; ++j) cd.kd_t[j] = dsub(cd.dd_t[j], cd.g[j]);
+    }
     // FP64 value-chain copies, widened to cover the rounding of sin, cos and
     // the Taylor terms (a relative 1e-14 is far above their few-ulp error);
     // the lower and upper forms share their coefficients
@@ -305,23 +355,29 @@ static __device__ __noinline__ int screen_fp64(const double (*rd_int)[2], const 
 // (or when a value leaves the checked range) SCREEN_UNDECIDED.  GB300's FP64
 // rate is about 1/64 of its FP32 rate, and the FP64 path is then taken by a
 // small fraction of the pairs.
-static __device__ __forceinline__ int screen_fp32(const double (*rd_int)[2], const double (*s_int)[2], const double *v,
-                                           const double *N, double dlo, double dhi, double tau, const CallConst &cc,
-                                           PixBox &box, double *mu_px, bool &straddle)
+template <int M>
+__device__ __forceinline__ int screen_fp32(const CellData<M> &cd, const double *v, const double *N, double dlo,
+                                           double dhi, double tau, const CallConst &cc, PixBox &box, double *mu_px,
+                                           bool &straddle)
 {
     bool ok = true;
     const double nearp = (double)cc.near_plane;
     EI Ri[9], vs[3];
-    for (int e = 0; e < 9; ++e) Ri[e] = EI{e_of(rd_int[e][0]), e_of(rd_int[e][1])};
+    for (int e = 0; e < 9; ++e)
+        Ri[e] = EI{E32{cd.rd_int32[e][0][0], cd.rd_int32[e][0][1]}, E32{cd.rd_int32[e][1][0], cd.rd_int32[e][1][1]}};
     for (int b = 0; b < 3; ++b) {
         const E32 vb = e_of(v[b]);
-        vs[b] = EI{e_chk(e_sub(vb, e_of(s_int[b][1])), ok), e_chk(e_sub(vb, e_of(s_int[b][0])), ok)};
+        vs[b] = EI{e_chk(e_sub(vb, E32{cd.s_int32[b][1][0], cd.s_int32[b][1][1]}), ok),
+                   e_chk(e_sub(vb, E32{cd.s_int32[b][0][0], cd.s_int32[b][0][1]}), ok)};
     }
+    E32 Ne[9];
+    for (int i = 0; i < 9; ++i) Ne[i] = e_of(N[i]);
     const double dl = fmax(dlo, nearp);
     const EI D = {e_of(dl), e_of(dhi)};
     const EI ucx = ei_add(ei_add(ei_mul(Ri[0], vs[0], ok), ei_mul(Ri[3], vs[1], ok), ok), ei_mul(Ri[6], vs[2], ok), ok);
     const EI ucy = ei_add(ei_add(ei_mul(Ri[1], vs[0], ok), ei_mul(Ri[4], vs[1], ok), ok), ei_mul(Ri[7], vs[2], ok), ok);
-    const E32 fx = e_of((double)cc.fx), fy = e_of((double)cc.fy), cx = e_of((double)cc.cx), cy = e_of((double)cc.cy);
+    // the intrinsics are floats: exact
+    const E32 fx = {cc.fx, cc.fx}, fy = {cc.fy, cc.fy}, cx = {cc.cx, cc.cx}, cy = {cc.cy, cc.cy};
     // u / D_hi or u / D_lo by the sign of u; where the sign is not settled,
     // the enclosure of either quotient
     auto qlo = [&](E32 u) {
@@ -335,13 +391,12 @@ static __device__ __forceinline__ int screen_fp32(const double (*rd_int)[2], con
     const EI mux = {e_chk(e_add(cx, e_mul(fx, qlo(ucx.l))), ok), e_chk(e_add(cx, e_mul(fx, qhi(ucx.u))), ok)};
     const EI muy = {e_chk(e_add(cy, e_mul(fy, qlo(ucy.l))), ok), e_chk(e_add(cy, e_mul(fy, qhi(ucy.u))), ok)};
     if (!ok) return SCREEN_UNDECIDED;
-    const E32 one = {1.f, 1.f}, slack = e_of(BOX_SLACK);
+    const E32 one = {1.f, 1.f}, slack = {cd.slack32[0], cd.slack32[1]};
     auto widen_dn = [&](E32 x) { return e_sub(x, e_mul(slack, e_add(one, e_abs(x)))); };
     auto widen_up = [&](E32 x) { return e_add(x, e_mul(slack, e_add(one, e_abs(x)))); };
     {
-        const double gx = dmul(GUARD, (double)cc.W), gy = dmul(GUARD, (double)cc.H);
-        const E32 cxp = e_of(dadd((double)cc.cx, gx)), cxm = e_of(dsub((double)cc.cx, gx));
-        const E32 cyp = e_of(dadd((double)cc.cy, gy)), cym = e_of(dsub((double)cc.cy, gy));
+        const E32 cxp = {cd.guard32[0][0], cd.guard32[0][1]}, cxm = {cd.guard32[1][0], cd.guard32[1][1]};
+        const E32 cyp = {cd.guard32[2][0], cd.guard32[2][1]}, cym = {cd.guard32[3][0], cd.guard32[3][1]};
         const E32 ml = widen_dn(mux.l), mh = widen_up(mux.u), nl = widen_dn(muy.l), nh = widen_up(muy.u);
         // drop: ml > cx + gx || mh < cx - gx || nl > cy + gy || nh < cy - gy
         const int d0 = e_gt(ml, cxp), d1 = e_gt(cxm, mh), d2 = e_gt(nl, cyp), d3 = e_gt(cym, nh);
@@ -356,10 +411,10 @@ static __device__ __forceinline__ int screen_fp32(const double (*rd_int)[2], con
     for (int c = 0; c < 3; ++c) {
         EI m[3];
         for (int a = 0; a < 3; ++a)
-            m[a] = ei_add(ei_add(ei_scale(Ri[a], N[c], ok), ei_scale(Ri[3 + a], N[3 + c], ok), ok),
-                          ei_scale(Ri[6 + a], N[6 + c], ok), ok);
-        const EI p0 = ei_scale(ei_add(ei_mul_pos(D, m[0], ok), ei_neg(ei_mul(ucx, m[2], ok)), ok), cc.fx, ok);
-        const EI p1 = ei_scale(ei_add(ei_mul_pos(D, m[1], ok), ei_neg(ei_mul(ucy, m[2], ok)), ok), cc.fy, ok);
+            m[a] = ei_add(ei_add(ei_scale(Ri[a], Ne[c], ok), ei_scale(Ri[3 + a], Ne[3 + c], ok), ok),
+                          ei_scale(Ri[6 + a], Ne[6 + c], ok), ok);
+        const EI p0 = ei_scale(ei_add(ei_mul_pos(D, m[0], ok), ei_neg(ei_mul(ucx, m[2], ok)), ok), fx, ok);
+        const EI p1 = ei_scale(ei_add(ei_mul_pos(D, m[1], ok), ei_neg(ei_mul(ucy, m[2], ok)), ok), fy, ok);
         X00 = e_chk(e_add(X00, ei_sqmax(p0)), ok);
         X11 = e_chk(e_add(X11, ei_sqmax(p1)), ok);
     }
@@ -418,34 +473,57 @@ __device__ __forceinline__ int64_t record_decide(const double *__restrict__ vN, 
     const double *v = vN + 12 * g;
     const double *N = v + 3;
 
-    // ---- FP64 decision chain: depth forms, near plane, depth key, pixel box
-    DB<M> Rd2[3], vms[3];
+    // ---- FP64 decision chain: depth d = sum_b R_delta[b][2] (v_b - s_b) by
+    // averaged McCormick products (db_mul, summed by db_add), its bounds, the
+    // near-plane class and the depth key.  These are the IEEE operations of
+    // db_mul, db_add and df_min / df_max on the full forms, in their order,
+    // less the ones whose operand is a coefficient that is zero by
+    // construction (R_delta[b][2] lives on the rotation slots, s_b on the
+    // translation slots; adding, subtracting or scaling zero changes no value
+    // but the sign of a zero, which the bounds never see) and less the
+    // per-cell parts the cell kernel computed.  So dlo, dhi, klo and khi are
+    // bit-identical to the plain statement.
+    const int n_t = cd.n_t, n_a = cd.n_a;
+    double ddr[M];  // rotation-slot coefficients of d
+    double dlk = 0.0, dhk = 0.0;  // constants of d's lower and upper forms
     for (int b = 0; b < 3; ++b) {
-        for (int j = 0; j < M; ++j) {
-            Rd2[b].lo.c[j] = cd.rd_lo[3 * b + 2][j];
-            Rd2[b].hi.c[j] = cd.rd_hi[3 * b + 2][j];
-            vms[b].lo.c[j] = dsub(0.0, cd.s[b][j]);
-            vms[b].hi.c[j] = vms[b].lo.c[j];
+        const int e = 3 * b + 2;
+        const double xl = cd.dx[b][0], xh = cd.dx[b][1], xm = cd.dx[b][2];
+        const double yk = dsub(v[b], cd.s[b][M]);  // v_b - s_b: constant
+        double yl = yk, yh = yk;
+        for (int j = 0; j < n_t; ++j) {
+            yl = dsub(yl, fabs(cd.s[b][j]));
+            yh = dadd(yh, fabs(cd.s[b][j]));
         }
-        Rd2[b].lo.k = cd.rd_lo[3 * b + 2][M];
-        Rd2[b].hi.k = cd.rd_hi[3 * b + 2][M];
-        vms[b].lo.k = dsub(v[b], cd.s[b][M]);
-        vms[b].hi.k = vms[b].lo.k;
+        const double ym = dmul(0.5, dadd(yl, yh));
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+            if (j < n_t || j >= n_a) continue;
+            const double t = dmul(ym, cd.rd_lo[e][j]);
+            ddr[j] = b == 0 ? t : dadd(ddr[j], t);
+        }
+        double lk = dadd(dmul(ym, ym >= 0 ? cd.rd_lo[e][M] : cd.rd_hi[e][M]), dmul(xm, yk));
+        lk = dsub(lk, dmul(0.5, dadd(dmul(xl, yl), dmul(xh, yh))));
+        double hk = dadd(dmul(ym, ym >= 0 ? cd.rd_hi[e][M] : cd.rd_lo[e][M]), dmul(xm, yk));
+        hk = dsub(hk, dmul(0.5, dadd(dmul(xh, yl), dmul(xl, yh))));
+        dlk = b == 0 ? lk : dadd(dlk, lk);
+        dhk = b == 0 ? hk : dadd(dhk, hk);
     }
-    DB<M> dd = db_mul<M>(Rd2[0], vms[0]);
-    dd = db_add<M>(dd, db_mul<M>(Rd2[1], vms[1]));
-    dd = db_add<M>(dd, db_mul<M>(Rd2[2], vms[2]));
-    const double dlo = df_min(dd.lo), dhi = df_max(dd.hi);
+    double dlo = dlk, dhi = dhk, klo = dlk, khi = dhk;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        if (j >= n_a) continue;
+        const double c = j < n_t ? cd.dd_t[j] : ddr[j];   // d's coefficient
+        const double ck = j < n_t ? cd.kd_t[j] : ddr[j];  // the key form's (d minus the shared term g)
+        dlo = dsub(dlo, fabs(c));
+        dhi = dadd(dhi, fabs(c));
+        klo = dsub(klo, fabs(ck));
+        khi = dadd(khi, fabs(ck));
+    }
     const double nearp = (double)cc.near_plane;
     if (!(dhi > nearp)) return -1;
     bool straddle = !(dlo > nearp);
-    double klo, khi;
     {
-        DF<M> gk;
-        for (int j = 0; j < M; ++j) gk.c[j] = cd.g[j];
-        gk.k = 0;
-        klo = df_min(df_sub(dd.lo, gk));
-        khi = df_max(df_sub(dd.hi, gk));
         double pad = dmul(KEY_SLACK, dadd(1.0, fmax(fabs(klo), fabs(khi))));
         klo = dsub(klo, pad);
         khi = dadd(khi, pad);
@@ -454,7 +532,7 @@ __device__ __forceinline__ int64_t record_decide(const double *__restrict__ vN, 
     // FP32 enclosures of the FP64 values where they settle every decision,
     // else in FP64 (the same values either way)
     double mu_px[2];
-    int sr = screen_fp32(cd.rd_int, cd.s_int, v, N, dlo, dhi, tau, cc, box, mu_px, straddle);
+    int sr = screen_fp32<M>(cd, v, N, dlo, dhi, tau, cc, box, mu_px, straddle);
     if (sr == SCREEN_UNDECIDED) sr = screen_fp64(cd.rd_int, cd.s_int, v, N, dlo, dhi, tau, cc, box, mu_px, straddle);
     if (sr == SCREEN_DROP) return -1;
     RO *rec = recs + ri * RL::WIDTH;
