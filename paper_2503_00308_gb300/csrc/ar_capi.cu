@@ -59,11 +59,11 @@ int launch_record_prep64_m4(const double *, const double *, const float *, const
 int launch_record_prep64_m6(const double *, const double *, const float *, const float *, const CallConst &,
                             const void *, int, double *, PixBox *, double *, unsigned long long *, cudaStream_t);
 int launch_record_build_m1(const double *, const CallConst &, const void *, int64_t, const uint32_t *,
-                           const uint32_t *, float *, unsigned long long *, cudaStream_t);
+                           const uint32_t *, float *, unsigned long long *, uint32_t *, uint32_t *, cudaStream_t);
 int launch_record_build_m4(const double *, const CallConst &, const void *, int64_t, const uint32_t *,
-                           const uint32_t *, float *, unsigned long long *, cudaStream_t);
+                           const uint32_t *, float *, unsigned long long *, uint32_t *, uint32_t *, cudaStream_t);
 int launch_record_build_m6(const double *, const CallConst &, const void *, int64_t, const uint32_t *,
-                           const uint32_t *, float *, unsigned long long *, cudaStream_t);
+                           const uint32_t *, float *, unsigned long long *, uint32_t *, uint32_t *, cudaStream_t);
 int launch_render_plain_m1(int, const RenderLaunch &, cudaStream_t);
 int launch_render_plain_m4(int, const RenderLaunch &, cudaStream_t);
 int launch_render_plain_m6(int, const RenderLaunch &, cudaStream_t);
@@ -105,11 +105,13 @@ int launch_record_prep64(int M, const double *vN, const double *tau, const float
 }
 int launch_record_build(int M, const double *vN, const CallConst &cc, const void *cells, int64_t n_gauss,
                         const uint32_t *work, const uint32_t *count, float *recs, unsigned long long *counters,
-                        cudaStream_t st)
+                        uint32_t *split_list, uint32_t *split_count, cudaStream_t st)
 {
-    if (M == 1) return launch_record_build_m1(vN, cc, cells, n_gauss, work, count, recs, counters, st);
-    if (M == 4) return launch_record_build_m4(vN, cc, cells, n_gauss, work, count, recs, counters, st);
-    return launch_record_build_m6(vN, cc, cells, n_gauss, work, count, recs, counters, st);
+    if (M == 1)
+        return launch_record_build_m1(vN, cc, cells, n_gauss, work, count, recs, counters, split_list, split_count, st);
+    if (M == 4)
+        return launch_record_build_m4(vN, cc, cells, n_gauss, work, count, recs, counters, split_list, split_count, st);
+    return launch_record_build_m6(vN, cc, cells, n_gauss, work, count, recs, counters, split_list, split_count, st);
 }
 int launch_render_plain(int M, int TS, const RenderLaunch &a, cudaStream_t st)
 {
@@ -181,7 +183,8 @@ void Workspace::release()
 {
     DevBuf *all[] = {&cells_lohi, &cells, &vN, &recs, &boxes, &keys, &counters, &evk0, &evk1, &evv0, &evv1,
                      &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege, &segk0,
-                     &segk1, &segv0, &segv1, &work, &state, &wlist, &act0, &act1, &words, &whist, &out_lo, &out_hi};
+                     &segk1, &segv0, &segv1, &work, &state, &wlist, &act0, &act1, &words, &slist, &whist, &out_lo,
+                     &out_hi};
     for (DevBuf *b : all) b->release();
     if (h_whist) cudaFreeHost(h_whist);
     h_whist = nullptr;
@@ -197,7 +200,7 @@ size_t Workspace::bytes() const
     const DevBuf *all[] = {&cells_lohi, &cells, &vN, &recs, &boxes, &keys, &counters, &evk0, &evk1, &evv0, &evv1,
                            &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege,
                            &segk0, &segk1, &segv0, &segv1, &work, &state, &wlist, &act0, &act1, &words,
-                           &whist, &out_lo, &out_hi};
+                           &slist, &whist, &out_lo, &out_hi};
     size_t s = 0;
     for (const DevBuf *b : all) s += b->cap;
     return s;
@@ -485,11 +488,12 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
         RK(ws.act0.ensure(sizeof(uint32_t) * n_seg));
         RK(ws.act1.ensure(sizeof(uint32_t) * n_seg));
         RK(ws.words.ensure(sizeof(uint32_t) * 4));
+        RK(ws.slist.ensure(sizeof(uint32_t) * n_pairs));
         rl.sweep_hist = ws.whist.as<uint32_t>();
         RK(run_windowed_render(M, TS, rl, cc, ws.cells.p, ws.vN.as<double>(), n_pairs, n_seg, ws.state.as<uint32_t>(),
                                ws.wlist.as<uint32_t>(), ws.act0.as<uint32_t>(), ws.act1.as<uint32_t>(),
                                ws.words.as<uint32_t>(), rl.counters + 2, st, &launches,
-                               profiling ? ev + 3 : nullptr, ws.w0));
+                               profiling ? ev + 3 : nullptr, ws.w0, ws.slist.as<uint32_t>()));
     }
     return AR_OK;
 }
@@ -515,7 +519,7 @@ uint32_t learned_window(const uint32_t *hist256)
 int run_windowed_render(int M, int TS, RenderLaunch rl, const CallConst &cc, const void *cells, const double *vN,
                         uint64_t n_pairs, uint64_t n_seg, uint32_t *state, uint32_t *wlist, uint32_t *act0,
                         uint32_t *act1, uint32_t *words, unsigned long long *build_counters, cudaStream_t st,
-                        int *launches, cudaEvent_t *ev, uint32_t w0)
+                        int *launches, cudaEvent_t *ev, uint32_t w0, uint32_t *split_list)
 {
     const uint32_t kWindow[3] = {w0, w0 < 8192u ? 8192u : 0xffffffffu, 0xffffffffu};
     uint32_t *act[2] = {act0, act1};
@@ -527,10 +531,13 @@ int run_windowed_render(int M, int TS, RenderLaunch rl, const CallConst &cc, con
         const uint32_t *cur = r == 0 ? rl.seg_order : act[(r - 1) & 1];
         CK(cudaMemsetAsync(words, 0, sizeof(uint32_t), st));
         CK(cudaMemsetAsync(nxt_n, 0, sizeof(uint32_t), st));
+        CK(cudaMemsetAsync(words + 3, 0, sizeof(uint32_t), st));
         launch_demand(cur, cur_n, (uint32_t)n_seg, rl.seg_start, rl.seg_end, rl.ent_ev, rl.ev_val, kWindow[r], state,
                       wlist, words, st);
-        if (launch_record_build(M, vN, cc, cells, rl.n_gauss, wlist, words, rl.recs, build_counters, st))
+        if (launch_record_build(M, vN, cc, cells, rl.n_gauss, wlist, words, rl.recs, build_counters, split_list,
+                                words + 3, st))
             return fail(AR_EDEVICE, "record build launch: %s", cudaGetErrorString(cudaGetLastError()));
+        ++*launches;
         if (ev) CK(cudaEventRecord(ev[2 * r], st));
         rl.active = cur;
         rl.n_active = cur_n;

@@ -27,7 +27,7 @@ struct Workspace {
     DevBuf cells_lohi, cells, vN, recs, boxes, keys, counters;
     DevBuf evk0, evk1, evv0, evv1, ents0, ents1, ente0, ente1;
     DevBuf ua, ub, uc, ud, hist, scan, segs, sege, segk0, segk1, segv0, segv1, work;
-    DevBuf state, wlist, act0, act1, words;  // windowed rounds: pair states, build list, active segments
+    DevBuf state, wlist, act0, act1, words, slist;  // windowed rounds: pair states, build list, active segments
     DevBuf whist;                            // [256] sweep-length histogram of the current render
     uint32_t *h_whist = nullptr;             // page-locked copy of the last render's histogram
     bool whist_pending = false;              // h_whist holds a render not yet learned from
@@ -55,11 +55,13 @@ struct TunedTile {
 // The FP32 render of one batch in windowed rounds (see render_kernel):
 // demand -> build -> render per round, windows w0, 8192, then unlimited.
 // state [n_pairs] (zeroed here), wlist [n_pairs], act0/act1 [n_seg], words [4];
-// build_counters: [0] fallbacks, [1] records built (optional).
+// build_counters: [0] fallbacks, [1] records built, [2] splits (optional);
+// split_list [n_pairs]: pairs whose MatrixInv needs input splitting, which a
+// second kernel finishes with a warp each.
 int run_windowed_render(int M, int TS, RenderLaunch rl, const CallConst &cc, const void *cells, const double *vN,
                         uint64_t n_pairs, uint64_t n_seg, uint32_t *state, uint32_t *wlist, uint32_t *act0,
                         uint32_t *act1, uint32_t *words, unsigned long long *build_counters, cudaStream_t st,
-                        int *launches, cudaEvent_t *ev = nullptr, uint32_t w0 = 512u);
+                        int *launches, cudaEvent_t *ev, uint32_t w0, uint32_t *split_list);
 // First window from the sweep histogram of an earlier render: the smallest
 // multiple of 32 entries that covers 99.5 % of its segments, in [128, 4096].
 uint32_t learned_window(const uint32_t *hist256);

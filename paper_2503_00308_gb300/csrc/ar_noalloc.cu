@@ -145,6 +145,7 @@ int ar_render_abstract_noalloc(ar_scene *s, const ar_intrinsics *in, const ar_no
     uint32_t *seg_v0 = A.take<uint32_t>(n_seg), *seg_v1 = A.take<uint32_t>(n_seg);
     unsigned int *work = A.take<unsigned int>(64);
     uint32_t *state = A.take<uint32_t>(n_pairs), *wlist = A.take<uint32_t>(n_pairs);
+    uint32_t *slist = A.take<uint32_t>(n_pairs);
     uint32_t *act0 = A.take<uint32_t>(n_seg), *act1 = A.take<uint32_t>(n_seg), *words = A.take<uint32_t>(4);
     if (A.over) return too_big("the per-(Gaussian, cell) records", A.used);
 
@@ -215,5 +216,5 @@ int ar_render_abstract_noalloc(ar_scene *s, const ar_intrinsics *in, const ar_no
     rl.out_hi = out_upper;
     rl.counters = nullptr;
     return run_windowed_render(M, TS, rl, cc, cellbuf, vN, n_pairs, n_seg, state, wlist, act0, act1, words, nullptr,
-                               st, &launches);
+                               st, &launches, nullptr, 512u, slist);
 }

@@ -89,7 +89,8 @@ static int launch_render_ts(const RenderLaunch &a, cudaStream_t st)
 
 int AR_CAT(launch_record_build_m, AR_M)(const double *vN, const CallConst &cc, const void *cells, int64_t n_gauss,
                                         const uint32_t *work, const uint32_t *count, float *recs,
-                                        unsigned long long *counters, cudaStream_t st)
+                                        unsigned long long *counters, uint32_t *split_list, uint32_t *split_count,
+                                        cudaStream_t st)
 {
     auto kern = record_build_kernel<AR_M>;
     int dev = 0, sms = 0, per_sm = 0;
@@ -97,7 +98,11 @@ int AR_CAT(launch_record_build_m, AR_M)(const double *vN, const CallConst &cc, c
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
     kern<<<sms * per_sm, 128, 0, st>>>(vN, cc.fx, cc.fy, cc.cx, cc.cy, (const CellData<AR_M> *)cells, n_gauss, work,
-                                       count, recs, counters);
+                                       count, recs, counters, split_list, split_count);
+    if (cudaGetLastError() != cudaSuccess) return 1;
+    // the deferred pairs: one warp each, grid-stride (the count stays on the device)
+    split_build_kernel<AR_M><<<sms, 128, 0, st>>>(vN, cc.fx, cc.fy, cc.cx, cc.cy, (const CellData<AR_M> *)cells,
+                                                 n_gauss, split_list, split_count, recs, counters);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 

@@ -742,16 +742,125 @@ __device__ __noinline__ int matinv_split(const SB<M, double> X[4], SB<M, RO> con
     return pieces;
 }
 
+// Split modes of record_value (see there).
+enum { SPLIT_INLINE = 0, SPLIT_DEFER = 1, SPLIT_WARP = 2 };
+
+// A piece of the pose cell for matinv_split_warp, packed in 64 bits: for each
+// slot j, bits 9j..9j+2 hold its bisection depth d_j and bits 9j+3..9j+8 its
+// index i_j, the piece being ctr_j = (2 i_j + 1) 2^-d_j - 1, h_j = 2^-d_j
+// (exact dyadic numbers, the same as repeated halving gives).
+__device__ __forceinline__ uint64_t piece_child(uint64_t pc, int js, int upper)
+{
+    const uint64_t f = (pc >> (9 * js)) & 511u;
+    const uint64_t d = f & 7u, i = f >> 3;
+    const uint64_t g = (d + 1) | (((2 * i + (uint64_t)upper)) << 3);
+    return (pc & ~((uint64_t)511u << (9 * js))) | (g << (9 * js));
+}
+template <int M>
+__device__ __forceinline__ void piece_box(uint64_t pc, double *ctr, double *h)
+{
+    for (int j = 0; j < M; ++j) {
+        const uint32_t f = (uint32_t)(pc >> (9 * j)) & 511u;
+        const int d = (int)(f & 7u), i = (int)(f >> 3);
+        h[j] = ldexp(1.0, -d);
+        ctr[j] = (double)(2 * i + 1) * h[j] - 1.0;
+    }
+}
+
+// matinv_split with the 32 lanes of a warp, for a pair on whose cell
+// MatrixInv failed: the same pieces (each failing piece bisected along its
+// own split_var, down to SPLIT_DEPTH), tried level by level with one piece
+// per lane; the hull and the outcome do not depend on the order.  Every lane
+// passes the same X and gets the same result; list is the warp's 2 x 64
+// shared-memory piece lists.  Returns the number of pieces, or 0 if a piece
+// at the depth limit still fails.
+template <int M, class RO>
+__device__ __noinline__ int matinv_split_warp(const SB<M, double> X[4], SB<M, RO> conic[4], uint64_t *list)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    RO lo[4], hi[4];
+    for (int e = 0; e < 4; ++e) {
+        lo[e] = Num<RO>::BIG;
+        hi[e] = -Num<RO>::BIG;
+    }
+    int pieces = 0;
+    bool failed = false;
+    {
+        const int js = split_var<M>(X);
+        if (lane == 0) {
+            list[0] = piece_child(0, js, 0);
+            list[1] = piece_child(0, js, 1);
+        }
+    }
+    __syncwarp();
+    int cnt = 2, cur = 0;
+    for (int depth = 1; depth <= SPLIT_DEPTH && cnt > 0; ++depth) {
+        int next = 0;
+        for (int base = 0; base < cnt; base += 32) {
+            const int i = base + lane;
+            bool need = false;
+            uint64_t pc = 0;
+            int js = 0;
+            if (i < cnt) {
+                pc = list[cur * 64 + i];
+                double ctr[M], h[M];
+                piece_box<M>(pc, ctr, h);
+                SB<M, double> Xr[4];
+                for (int e = 0; e < 4; ++e) Xr[e] = sb_restrict<M>(X[e], ctr, h);
+                SB<M, RO> C[4];
+                if (matinv_box<M, RO>(Xr, C)) {
+                    for (int e = 0; e < 4; ++e) {
+                        lo[e] = Num<RO>::min(lo[e], C[e].vlo);
+                        hi[e] = Num<RO>::max(hi[e], C[e].vhi);
+                    }
+                    ++pieces;
+                } else if (depth < SPLIT_DEPTH) {
+                    need = true;
+                    js = split_var<M>(Xr);
+                } else {
+                    failed = true;
+                }
+            }
+            const unsigned m = __ballot_sync(full, need);
+            if (need) {
+                const int at = next + 2 * __popc(m & ((1u << lane) - 1u));
+                list[(cur ^ 1) * 64 + at] = piece_child(pc, js, 0);
+                list[(cur ^ 1) * 64 + at + 1] = piece_child(pc, js, 1);
+            }
+            next += 2 * __popc(m);
+        }
+        __syncwarp();
+        if (__any_sync(full, failed)) return 0;
+        cnt = next;
+        cur ^= 1;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        pieces += __shfl_xor_sync(full, pieces, off);
+        for (int e = 0; e < 4; ++e) {
+            lo[e] = Num<RO>::min(lo[e], __shfl_xor_sync(full, lo[e], off));
+            hi[e] = Num<RO>::max(hi[e], __shfl_xor_sync(full, hi[e], off));
+        }
+    }
+    for (int e = 0; e < 4; ++e) conic[e] = sb_cst<M, RO>(lo[e], hi[e]);
+    return pieces;
+}
+
 // The value part of one (Gaussian, cell) pair: the forms the per-pixel stage
 // reads, S = d^2 and R = mu S - P (Algorithm 1 lines 2-8 with set-valued
 // variables), MatrixInv (Algorithm 3) and W = Conic Mp.  v points at the
 // Gaussian's v (3) and N (9); rec holds the scalar fields record_decide wrote,
 // mu_x / mu_y and flags are their values; fx, fy, cx, cy the intrinsics.  Writes the forms and the flags word
 // (with F_FALLBACK where the MatrixInv assertion fails or a form is not
-// finite) and returns that word.
-template <int M, class RO = float>
+// finite) and returns that word.  SPLIT: where MatrixInv fails on the cell,
+// SPLIT_INLINE splits it in this thread (matinv_split), SPLIT_DEFER returns
+// the flags with F_SPLIT_PENDING before writing W and the flags, and
+// SPLIT_WARP (all 32 lanes of a warp call it for one deferred pair, with the
+// warp's split_list) splits it with the warp (matinv_split_warp).
+template <int M, class RO = float, int SPLIT = SPLIT_INLINE>
 __device__ __forceinline__ uint32_t record_value(const double *__restrict__ v, float fx, float fy, float cx, float cy,
-                                                 const CellData<M> &cd, RO mux, RO muy, uint32_t flags, RO *rec)
+                                                 const CellData<M> &cd, RO mux, RO muy, uint32_t flags, RO *rec,
+                                                 uint64_t *split_list = nullptr)
 {
     using RL = Rec<M>;
     using NO = Num<RO>;
@@ -844,7 +953,12 @@ __device__ __forceinline__ uint32_t record_value(const double *__restrict__ v, f
             p.init(0.0, 0.0); p.mul(Mp64[0], Mp64[3]); p.mul(Mp64[1], Mp64[4]); p.mul(Mp64[2], Mp64[5]); X[1] = p.result();
             X[2] = X[1];
         }
-        if (!matinv_box<M, RO>(X, conic)) {
+        if (SPLIT == SPLIT_WARP) {
+            // a deferred pair (MatrixInv failed on its cell): the warp splits it
+            if (matinv_split_warp<M, RO>(X, conic, split_list) > 0) flags |= F_SPLIT;
+            else fallback = true;
+        } else if (!matinv_box<M, RO>(X, conic)) {
+            if (SPLIT == SPLIT_DEFER) return flags | F_SPLIT_PENDING;
             if (matinv_split<M, RO>(X, conic) > 0) flags |= F_SPLIT;
             else fallback = true;
         }
@@ -918,12 +1032,14 @@ __global__ void __launch_bounds__(128) record_prep_kernel(
 // record kernel wrote.  Grid-stride over the list; the grid is sized on the
 // host without knowing the count.
 // counters: [0] MatrixInv fallbacks among the records built, [1] records
-// built, [2] records whose MatrixInv needed input splitting.
+// built, [2] records whose MatrixInv needed input splitting.  A pair whose
+// MatrixInv fails on its cell is appended to split_list (split_count counts
+// them) and finished by split_build_kernel.
 template <int M>
 __global__ void __launch_bounds__(128) record_build_kernel(
     const double *__restrict__ vN, float fx, float fy, float cx, float cy, const CellData<M> *__restrict__ cells,
     int64_t n_gauss, const uint32_t *__restrict__ work, const uint32_t *__restrict__ count, float *__restrict__ recs,
-    unsigned long long *__restrict__ counters)
+    unsigned long long *__restrict__ counters, uint32_t *__restrict__ split_list, uint32_t *__restrict__ split_count)
 {
     using RL = Rec<M>;
     const uint32_t n = *count;
@@ -933,8 +1049,10 @@ __global__ void __launch_bounds__(128) record_build_kernel(
         const int cell = (int)(p / (uint64_t)n_gauss);
         const int64_t g = (int64_t)p - (int64_t)cell * n_gauss;
         float *rec = recs + (size_t)p * RL::WIDTH;
-        const uint32_t f = record_value<M, float>(vN + 12 * g, fx, fy, cx, cy, cells[cell], rec[RL::MU_X],
-                                                  rec[RL::MU_Y], __float_as_uint(rec[RL::FLAGS]), rec);
+        const uint32_t f = record_value<M, float, SPLIT_DEFER>(vN + 12 * g, fx, fy, cx, cy, cells[cell],
+                                                              rec[RL::MU_X], rec[RL::MU_Y],
+                                                              __float_as_uint(rec[RL::FLAGS]), rec);
+        if (f & F_SPLIT_PENDING) split_list[atomicAdd(split_count, 1u)] = p;
         ++built;
         if (f & F_FALLBACK) ++fb;
         if (f & F_SPLIT) ++sp;
@@ -948,6 +1066,42 @@ __global__ void __launch_bounds__(128) record_build_kernel(
             if (b) atomicAdd(&counters[1], (unsigned long long)b);
             if (c) atomicAdd(&counters[2], (unsigned long long)c);
         }
+    }
+}
+
+// Finishes the records of the pairs record_build_kernel deferred (list[0,
+// *count)): one warp per pair, every lane running the value chain of the pair
+// (the same values), the warp splitting its cell (SPLIT_WARP).  Grid-stride
+// over the list by warps.  counters as in record_build_kernel ([0] fallbacks,
+// [2] splits; the pairs were counted as built there).
+template <int M>
+__global__ void __launch_bounds__(128) split_build_kernel(
+    const double *__restrict__ vN, float fx, float fy, float cx, float cy, const CellData<M> *__restrict__ cells,
+    int64_t n_gauss, const uint32_t *__restrict__ list, const uint32_t *__restrict__ count, float *__restrict__ recs,
+    unsigned long long *__restrict__ counters)
+{
+    using RL = Rec<M>;
+    __shared__ uint64_t pieces[4][2 * 64];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t n = *count;
+    uint32_t fb = 0, sp = 0;
+    for (uint32_t i = blockIdx.x * 4 + w; i < n; i += gridDim.x * 4) {
+        const uint32_t p = list[i];
+        const int cell = (int)(p / (uint64_t)n_gauss);
+        const int64_t g = (int64_t)p - (int64_t)cell * n_gauss;
+        float *rec = recs + (size_t)p * RL::WIDTH;
+        const uint32_t f0 = __float_as_uint(rec[RL::FLAGS]);
+        __syncwarp();
+        const uint32_t f = record_value<M, float, SPLIT_WARP>(vN + 12 * g, fx, fy, cx, cy, cells[cell],
+                                                             rec[RL::MU_X], rec[RL::MU_Y], f0, rec, pieces[w]);
+        if (lane == 0) {
+            if (f & F_FALLBACK) ++fb;
+            if (f & F_SPLIT) ++sp;
+        }
+    }
+    if (counters && lane == 0) {
+        if (fb) atomicAdd(&counters[0], (unsigned long long)fb);
+        if (sp) atomicAdd(&counters[2], (unsigned long long)sp);
     }
 }
 
