@@ -59,11 +59,14 @@ int launch_record_prep64_m4(const double *, const double *, const float *, const
 int launch_record_prep64_m6(const double *, const double *, const float *, const float *, const CallConst &,
                             const void *, int, double *, PixBox *, double *, unsigned long long *, cudaStream_t);
 int launch_record_build_m1(const double *, const CallConst &, const void *, int64_t, const uint32_t *,
-                           const uint32_t *, float *, unsigned long long *, uint32_t *, uint32_t *, cudaStream_t);
+                           const uint32_t *, float *, unsigned long long *, uint32_t *, uint32_t *, uint32_t, uint32_t *,
+                           cudaStream_t);
 int launch_record_build_m4(const double *, const CallConst &, const void *, int64_t, const uint32_t *,
-                           const uint32_t *, float *, unsigned long long *, uint32_t *, uint32_t *, cudaStream_t);
+                           const uint32_t *, float *, unsigned long long *, uint32_t *, uint32_t *, uint32_t, uint32_t *,
+                           cudaStream_t);
 int launch_record_build_m6(const double *, const CallConst &, const void *, int64_t, const uint32_t *,
-                           const uint32_t *, float *, unsigned long long *, uint32_t *, uint32_t *, cudaStream_t);
+                           const uint32_t *, float *, unsigned long long *, uint32_t *, uint32_t *, uint32_t, uint32_t *,
+                           cudaStream_t);
 int launch_render_plain_m1(int, const RenderLaunch &, cudaStream_t);
 int launch_render_plain_m4(int, const RenderLaunch &, cudaStream_t);
 int launch_render_plain_m6(int, const RenderLaunch &, cudaStream_t);
@@ -105,13 +108,17 @@ int launch_record_prep64(int M, const double *vN, const double *tau, const float
 }
 int launch_record_build(int M, const double *vN, const CallConst &cc, const void *cells, int64_t n_gauss,
                         const uint32_t *work, const uint32_t *count, float *recs, unsigned long long *counters,
-                        uint32_t *split_list, uint32_t *split_count, cudaStream_t st)
+                        uint32_t *split_list, uint32_t *split_count, uint32_t list_cap, uint32_t *khigh_count,
+                        cudaStream_t st)
 {
     if (M == 1)
-        return launch_record_build_m1(vN, cc, cells, n_gauss, work, count, recs, counters, split_list, split_count, st);
+        return launch_record_build_m1(vN, cc, cells, n_gauss, work, count, recs, counters, split_list, split_count,
+                                      list_cap, khigh_count, st);
     if (M == 4)
-        return launch_record_build_m4(vN, cc, cells, n_gauss, work, count, recs, counters, split_list, split_count, st);
-    return launch_record_build_m6(vN, cc, cells, n_gauss, work, count, recs, counters, split_list, split_count, st);
+        return launch_record_build_m4(vN, cc, cells, n_gauss, work, count, recs, counters, split_list, split_count,
+                                      list_cap, khigh_count, st);
+    return launch_record_build_m6(vN, cc, cells, n_gauss, work, count, recs, counters, split_list, split_count,
+                                  list_cap, khigh_count, st);
 }
 int launch_render_plain(int M, int TS, const RenderLaunch &a, cudaStream_t st)
 {
@@ -487,7 +494,7 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
         RK(ws.wlist.ensure(sizeof(uint32_t) * n_pairs));
         RK(ws.act0.ensure(sizeof(uint32_t) * n_seg));
         RK(ws.act1.ensure(sizeof(uint32_t) * n_seg));
-        RK(ws.words.ensure(sizeof(uint32_t) * 4));
+        RK(ws.words.ensure(sizeof(uint32_t) * 8));
         RK(ws.slist.ensure(sizeof(uint32_t) * n_pairs));
         rl.sweep_hist = ws.whist.as<uint32_t>();
         RK(run_windowed_render(M, TS, rl, cc, ws.cells.p, ws.vN.as<double>(), n_pairs, n_seg, ws.state.as<uint32_t>(),
@@ -531,13 +538,13 @@ int run_windowed_render(int M, int TS, RenderLaunch rl, const CallConst &cc, con
         const uint32_t *cur = r == 0 ? rl.seg_order : act[(r - 1) & 1];
         CK(cudaMemsetAsync(words, 0, sizeof(uint32_t), st));
         CK(cudaMemsetAsync(nxt_n, 0, sizeof(uint32_t), st));
-        CK(cudaMemsetAsync(words + 3, 0, sizeof(uint32_t), st));
+        CK(cudaMemsetAsync(words + 3, 0, 2 * sizeof(uint32_t), st));
         launch_demand(cur, cur_n, (uint32_t)n_seg, rl.seg_start, rl.seg_end, rl.ent_ev, rl.ev_val, kWindow[r], state,
                       wlist, words, st);
         if (launch_record_build(M, vN, cc, cells, rl.n_gauss, wlist, words, rl.recs, build_counters, split_list,
-                                words + 3, st))
+                                words + 3, (uint32_t)n_pairs, words + 4, st))
             return fail(AR_EDEVICE, "record build launch: %s", cudaGetErrorString(cudaGetLastError()));
-        ++*launches;
+        *launches += 2;
         if (ev) CK(cudaEventRecord(ev[2 * r], st));
         rl.active = cur;
         rl.n_active = cur_n;

@@ -82,6 +82,7 @@ constexpr uint32_t F_STRADDLE = 2u;  // depth may cross the near plane: lower al
 constexpr uint32_t F_OPEN = 4u;      // depth-key interval has positive width
 constexpr uint32_t F_SPLIT = 8u;     // MatrixInv held only after splitting the cell (constant Conic)
 constexpr uint32_t F_SPLIT_PENDING = 16u;  // returned by a deferred record build, never stored
+constexpr uint32_t F_KHIGH_PENDING = 32u;  // likewise, for a Taylor order above the default
 
 // Pixel box of a (Gaussian, cell) pair: x0 < 0 marks "contributes nowhere".
 struct PixBox {

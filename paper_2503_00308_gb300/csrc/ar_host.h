@@ -54,7 +54,7 @@ struct TunedTile {
 };
 // The FP32 render of one batch in windowed rounds (see render_kernel):
 // demand -> build -> render per round, windows w0, 8192, then unlimited.
-// state [n_pairs] (zeroed here), wlist [n_pairs], act0/act1 [n_seg], words [4];
+// state [n_pairs] (zeroed here), wlist [n_pairs], act0/act1 [n_seg], words [8];
 // build_counters: [0] fallbacks, [1] records built, [2] splits (optional);
 // split_list [n_pairs]: pairs whose MatrixInv needs input splitting, which a
 // second kernel finishes with a warp each.

@@ -42,11 +42,13 @@ int launch_record_prep64(int M, const double *vN, const double *tau, const float
                          unsigned long long *counters, cudaStream_t st);
 int launch_render_plain(int M, int TS, const RenderLaunch &a, cudaStream_t st);
 // value parts of the records listed in work[0, *count); counters: [0] fallbacks, [1] built, [2] split.
-// split_list (room for *count entries) and split_count (zeroed by the caller): pairs whose MatrixInv
-// fails on the cell are split by a warp each in a second kernel.
+// split_list (list_cap >= *count entries), split_count and khigh_count (zeroed by the caller): pairs whose
+// MatrixInv fails on the cell are split by a warp each in a second kernel, pairs whose Taylor order exceeds
+// the default are finished in a third (listed from the back of split_list).
 int launch_record_build(int M, const double *vN, const CallConst &cc, const void *cells, int64_t n_gauss,
                         const uint32_t *work, const uint32_t *count, float *recs, unsigned long long *counters,
-                        uint32_t *split_list, uint32_t *split_count, cudaStream_t st);
+                        uint32_t *split_list, uint32_t *split_count, uint32_t list_cap, uint32_t *khigh_count,
+                        cudaStream_t st);
 // concrete render (k_concrete.cu)
 size_t concrete_pose_bytes();
 int concrete_rec_width();

@@ -90,7 +90,7 @@ static int launch_render_ts(const RenderLaunch &a, cudaStream_t st)
 int AR_CAT(launch_record_build_m, AR_M)(const double *vN, const CallConst &cc, const void *cells, int64_t n_gauss,
                                         const uint32_t *work, const uint32_t *count, float *recs,
                                         unsigned long long *counters, uint32_t *split_list, uint32_t *split_count,
-                                        cudaStream_t st)
+                                        uint32_t list_cap, uint32_t *khigh_count, cudaStream_t st)
 {
     auto kern = record_build_kernel<AR_M>;
     int dev = 0, sms = 0, per_sm = 0;
@@ -98,11 +98,17 @@ int AR_CAT(launch_record_build_m, AR_M)(const double *vN, const CallConst &cc, c
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
     kern<<<sms * per_sm, 128, 0, st>>>(vN, cc.fx, cc.fy, cc.cx, cc.cy, (const CellData<AR_M> *)cells, n_gauss, work,
-                                       count, recs, counters, split_list, split_count);
+                                       count, recs, counters, split_list, split_count, list_cap, khigh_count);
     if (cudaGetLastError() != cudaSuccess) return 1;
-    // the deferred pairs: one warp each, grid-stride (the count stays on the device)
+    // the deferred pairs (the counts stay on the device): splits one warp
+    // each, high orders one thread each, grid-stride
     split_build_kernel<AR_M><<<sms, 128, 0, st>>>(vN, cc.fx, cc.fy, cc.cx, cc.cy, (const CellData<AR_M> *)cells,
                                                  n_gauss, split_list, split_count, recs, counters);
+    if (cudaGetLastError() != cudaSuccess) return 1;
+    auto kh = khigh_build_kernel<AR_M>;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kh, 128, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    kh<<<sms * per_sm, 128, 0, st>>>(vN, cc.fx, cc.fy, cc.cx, cc.cy, (const CellData<AR_M> *)cells, n_gauss,
+                                     split_list, list_cap, khigh_count, recs, counters);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 

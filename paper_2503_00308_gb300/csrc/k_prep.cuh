@@ -560,10 +560,12 @@ __device__ __forceinline__ int64_t record_decide(const double *__restrict__ vN, 
 // sum; E = I - X X0 and its Frobenius norm bound rho are formed in FP64, the
 // series in the record precision.  The order starts at the default KTAYLOR
 // and grows while the remainder bound rho^(k+1) / (1 - rho) exceeds EPS_TOL
-// (relative to ||X0||_F), up to KMAX (adjustment (3)).  Returns false when
-// the centre matrix is not positive definite or rho >= RHO_MAX.
+// (relative to ||X0||_F), up to KMAX (adjustment (3)).  Returns MI_FAIL when
+// the centre matrix is not positive definite or rho >= RHO_MAX, MI_KHIGH
+// (without running the series) when the order would exceed kcap, else MI_OK.
+enum { MI_FAIL = 0, MI_OK = 1, MI_KHIGH = 2 };
 template <int M, class RO>
-__device__ __forceinline__ bool matinv_box(const SB<M, double> X[4], SB<M, RO> conic[4])
+__device__ __forceinline__ int matinv_box(const SB<M, double> X[4], SB<M, RO> conic[4], int kcap = KMAX)
 {
     using NO = Num<RO>;
     typedef SB<M, RO> B;
@@ -599,6 +601,7 @@ __device__ __forceinline__ bool matinv_box(const SB<M, double> X[4], SB<M, RO> c
             ++k;
         }
     }
+    if (k > kcap) return MI_KHIGH;
     RO rho;
     rec_up(rho64, rho);
     // T = sum_{i=1..k} (I - X X0)^i, so that Xp = X0 (I + T) = X0 + X0 T: the
@@ -726,7 +729,7 @@ __device__ __noinline__ int matinv_split(const SB<M, double> X[4], SB<M, RO> con
         SB<M, double> Xr[4];
         for (int e = 0; e < 4; ++e) Xr[e] = sb_restrict<M>(X[e], q.ctr, q.h);
         SB<M, RO> C[4];
-        if (matinv_box<M, RO>(Xr, C)) {
+        if (matinv_box<M, RO>(Xr, C) == MI_OK) {
             for (int e = 0; e < 4; ++e) {
                 lo[e] = Num<RO>::min(lo[e], C[e].vlo);
                 hi[e] = Num<RO>::max(hi[e], C[e].vhi);
@@ -809,7 +812,7 @@ __device__ __noinline__ int matinv_split_warp(const SB<M, double> X[4], SB<M, RO
                 SB<M, double> Xr[4];
                 for (int e = 0; e < 4; ++e) Xr[e] = sb_restrict<M>(X[e], ctr, h);
                 SB<M, RO> C[4];
-                if (matinv_box<M, RO>(Xr, C)) {
+                if (matinv_box<M, RO>(Xr, C) == MI_OK) {
                     for (int e = 0; e < 4; ++e) {
                         lo[e] = Num<RO>::min(lo[e], C[e].vlo);
                         hi[e] = Num<RO>::max(hi[e], C[e].vhi);
@@ -854,7 +857,8 @@ __device__ __noinline__ int matinv_split_warp(const SB<M, double> X[4], SB<M, RO
 // (with F_FALLBACK where the MatrixInv assertion fails or a form is not
 // finite) and returns that word.  SPLIT: where MatrixInv fails on the cell,
 // SPLIT_INLINE splits it in this thread (matinv_split), SPLIT_DEFER returns
-// the flags with F_SPLIT_PENDING before writing W and the flags, and
+// the flags with F_SPLIT_PENDING before writing W and the flags (and with
+// F_KHIGH_PENDING where the cell's Taylor order would exceed KTAYLOR), and
 // SPLIT_WARP (all 32 lanes of a warp call it for one deferred pair, with the
 // warp's split_list) splits it with the warp (matinv_split_warp).
 template <int M, class RO = float, int SPLIT = SPLIT_INLINE>
@@ -957,10 +961,16 @@ __device__ __forceinline__ uint32_t record_value(const double *__restrict__ v, f
             // a deferred pair (MatrixInv failed on its cell): the warp splits it
             if (matinv_split_warp<M, RO>(X, conic, split_list) > 0) flags |= F_SPLIT;
             else fallback = true;
-        } else if (!matinv_box<M, RO>(X, conic)) {
-            if (SPLIT == SPLIT_DEFER) return flags | F_SPLIT_PENDING;
-            if (matinv_split<M, RO>(X, conic) > 0) flags |= F_SPLIT;
-            else fallback = true;
+        } else {
+            // deferring: a pair whose order would exceed the default goes to a
+            // pass of its own, so that warps do not wait on a few long series
+            const int mi = matinv_box<M, RO>(X, conic, SPLIT == SPLIT_DEFER ? KTAYLOR : KMAX);
+            if (SPLIT == SPLIT_DEFER && mi == MI_KHIGH) return flags | F_KHIGH_PENDING;
+            if (mi == MI_FAIL) {
+                if (SPLIT == SPLIT_DEFER) return flags | F_SPLIT_PENDING;
+                if (matinv_split<M, RO>(X, conic) > 0) flags |= F_SPLIT;
+                else fallback = true;
+            }
         }
         if (!fallback)
             for (int e = 0; e < 4; ++e)
@@ -1033,13 +1043,16 @@ __global__ void __launch_bounds__(128) record_prep_kernel(
 // host without knowing the count.
 // counters: [0] MatrixInv fallbacks among the records built, [1] records
 // built, [2] records whose MatrixInv needed input splitting.  A pair whose
-// MatrixInv fails on its cell is appended to split_list (split_count counts
-// them) and finished by split_build_kernel.
+// MatrixInv fails on its cell is appended to the front of list (split_count
+// counts them) and finished by split_build_kernel; one whose Taylor order
+// exceeds the default is appended to the back (list_cap - 1 downwards;
+// khigh_count counts them) and finished by khigh_build_kernel.
 template <int M>
 __global__ void __launch_bounds__(128) record_build_kernel(
     const double *__restrict__ vN, float fx, float fy, float cx, float cy, const CellData<M> *__restrict__ cells,
     int64_t n_gauss, const uint32_t *__restrict__ work, const uint32_t *__restrict__ count, float *__restrict__ recs,
-    unsigned long long *__restrict__ counters, uint32_t *__restrict__ split_list, uint32_t *__restrict__ split_count)
+    unsigned long long *__restrict__ counters, uint32_t *__restrict__ split_list, uint32_t *__restrict__ split_count,
+    uint32_t list_cap, uint32_t *__restrict__ khigh_count)
 {
     using RL = Rec<M>;
     const uint32_t n = *count;
@@ -1053,6 +1066,7 @@ __global__ void __launch_bounds__(128) record_build_kernel(
                                                               rec[RL::MU_X], rec[RL::MU_Y],
                                                               __float_as_uint(rec[RL::FLAGS]), rec);
         if (f & F_SPLIT_PENDING) split_list[atomicAdd(split_count, 1u)] = p;
+        if (f & F_KHIGH_PENDING) split_list[list_cap - 1u - atomicAdd(khigh_count, 1u)] = p;
         ++built;
         if (f & F_FALLBACK) ++fb;
         if (f & F_SPLIT) ++sp;
@@ -1102,6 +1116,38 @@ __global__ void __launch_bounds__(128) split_build_kernel(
     if (counters && lane == 0) {
         if (fb) atomicAdd(&counters[0], (unsigned long long)fb);
         if (sp) atomicAdd(&counters[2], (unsigned long long)sp);
+    }
+}
+
+// Finishes the records of the pairs record_build_kernel deferred for their
+// Taylor order (list[list_cap - 1 - i], i < *count): one thread per pair, as
+// record_build_kernel without deferral.  counters as there ([0], [2]).
+template <int M>
+__global__ void __launch_bounds__(128) khigh_build_kernel(
+    const double *__restrict__ vN, float fx, float fy, float cx, float cy, const CellData<M> *__restrict__ cells,
+    int64_t n_gauss, const uint32_t *__restrict__ list, uint32_t list_cap, const uint32_t *__restrict__ count,
+    float *__restrict__ recs, unsigned long long *__restrict__ counters)
+{
+    using RL = Rec<M>;
+    const uint32_t n = *count;
+    uint32_t fb = 0, sp = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t p = list[list_cap - 1u - i];
+        const int cell = (int)(p / (uint64_t)n_gauss);
+        const int64_t g = (int64_t)p - (int64_t)cell * n_gauss;
+        float *rec = recs + (size_t)p * RL::WIDTH;
+        const uint32_t f = record_value<M, float>(vN + 12 * g, fx, fy, cx, cy, cells[cell], rec[RL::MU_X],
+                                                  rec[RL::MU_Y], __float_as_uint(rec[RL::FLAGS]), rec);
+        if (f & F_FALLBACK) ++fb;
+        if (f & F_SPLIT) ++sp;
+    }
+    if (counters) {
+        const uint32_t a = __reduce_add_sync(0xffffffffu, fb);
+        const uint32_t c = __reduce_add_sync(0xffffffffu, sp);
+        if ((threadIdx.x & 31) == 0) {
+            if (a) atomicAdd(&counters[0], (unsigned long long)a);
+            if (c) atomicAdd(&counters[2], (unsigned long long)c);
+        }
     }
 }
 
