@@ -562,10 +562,11 @@ __device__ __forceinline__ int64_t record_decide(const double *__restrict__ vN, 
 // and grows while the remainder bound rho^(k+1) / (1 - rho) exceeds EPS_TOL
 // (relative to ||X0||_F), up to KMAX (adjustment (3)).  Returns MI_FAIL when
 // the centre matrix is not positive definite or rho >= RHO_MAX, MI_KHIGH
-// (without running the series) when the order would exceed kcap, else MI_OK.
+// (without running the series) when the order would exceed KC, else MI_OK.
+// (KC = KTAYLOR fixes the series length at compile time.)
 enum { MI_FAIL = 0, MI_OK = 1, MI_KHIGH = 2 };
-template <int M, class RO>
-__device__ __forceinline__ int matinv_box(const SB<M, double> X[4], SB<M, RO> conic[4], int kcap = KMAX)
+template <int M, class RO, int KC = KMAX>
+__device__ __forceinline__ int matinv_box(const SB<M, double> X[4], SB<M, RO> conic[4])
 {
     using NO = Num<RO>;
     typedef SB<M, RO> B;
@@ -596,12 +597,15 @@ __device__ __forceinline__ int matinv_box(const SB<M, double> X[4], SB<M, RO> co
     {
         double rk = 1.0;  // rho^(k+1), for the adaptive order
         for (int i = 0; i <= KTAYLOR; ++i) rk *= rho64;
-        while (k < KMAX && rk / (1.0 - rho64) > EPS_TOL) {
+        // (only whether the order exceeds KC matters when KC < KMAX)
+        constexpr int kstop = KC < KMAX ? KC + 1 : KMAX;
+        while (k < kstop && rk / (1.0 - rho64) > EPS_TOL) {
             rk *= rho64;
             ++k;
         }
     }
-    if (k > kcap) return MI_KHIGH;
+    if (k > KC) return MI_KHIGH;
+    if (KC == KTAYLOR) k = KTAYLOR;
     RO rho;
     rec_up(rho64, rho);
     // T = sum_{i=1..k} (I - X X0)^i, so that Xp = X0 (I + T) = X0 + X0 T: the
@@ -964,7 +968,7 @@ __device__ __forceinline__ uint32_t record_value(const double *__restrict__ v, f
         } else {
             // deferring: a pair whose order would exceed the default goes to a
             // pass of its own, so that warps do not wait on a few long series
-            const int mi = matinv_box<M, RO>(X, conic, SPLIT == SPLIT_DEFER ? KTAYLOR : KMAX);
+            const int mi = matinv_box<M, RO, SPLIT == SPLIT_DEFER ? KTAYLOR : KMAX>(X, conic);
             if (SPLIT == SPLIT_DEFER && mi == MI_KHIGH) return flags | F_KHIGH_PENDING;
             if (mi == MI_FAIL) {
                 if (SPLIT == SPLIT_DEFER) return flags | F_SPLIT_PENDING;
