@@ -119,28 +119,33 @@ void exclusive_scan(const uint32_t *in, uint32_t *out, uint64_t n, uint32_t *tmp
 }
 
 // ------------------------------------------------------------ radix sort
-template <class K>
+// Digits of RB bits (NB = 2^RB buckets, RB <= 8).  A sort of `bits` key bits
+// takes ceil(bits / 8) passes of equal digits, so that no pass spends buckets
+// on bits beyond the key: fewer buckets give longer digit runs per block and
+// fuller store sectors in the scatter.
+template <class K, int RB>
 __global__ void __launch_bounds__(RS_THREADS) rs_hist_kernel(const K *__restrict__ keys, uint32_t n, int shift,
                                                              uint32_t *__restrict__ hist, uint32_t nblocks)
 {
-    __shared__ uint32_t h[256];
-    h[threadIdx.x] = 0;
+    constexpr uint32_t NB = 1u << RB;
+    __shared__ uint32_t h[NB];
+    if (threadIdx.x < NB) h[threadIdx.x] = 0;
     __syncthreads();
     const uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
 #pragma unroll
     for (int r = 0; r < RS_ROUNDS; ++r) {
         const uint64_t i = base + (uint64_t)r * RS_THREADS + threadIdx.x;
-        if (i < n) atomicAdd(&h[(uint32_t)(keys[i] >> shift) & 255u], 1u);
+        if (i < n) atomicAdd(&h[(uint32_t)(keys[i] >> shift) & (NB - 1u)], 1u);
     }
     __syncthreads();
-    hist[(uint64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+    if (threadIdx.x < NB) hist[(uint64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
 // Scatter of one radix pass.  Each block ranks its RS_TILE items by digit
 // (stable: warps in order, rounds in order, lanes in order), reorders them by
 // digit in shared memory, then writes every digit run to its global offset
 // with consecutive threads on consecutive addresses.
-template <class K>
+template <class K, int RB>
 __global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(const K *__restrict__ kin,
                                                                 const uint32_t *__restrict__ vin,
                                                                 K *__restrict__ kout, uint32_t *__restrict__ vout,
@@ -148,13 +153,15 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(const K *__restr
                                                                 const uint32_t *__restrict__ offs,
                                                                 uint32_t nblocks)
 {
-    __shared__ uint32_t wcnt[RS_WARPS][256];
-    __shared__ uint32_t dstart[256];   // block-local start of each digit run
-    __shared__ uint32_t gbase[256];    // global start of each digit run of this block
+    constexpr uint32_t NB = 1u << RB;
+    static_assert(NB <= RS_THREADS, "one thread per digit");
+    __shared__ uint32_t wcnt[RS_WARPS][NB];
+    __shared__ uint32_t dstart[NB];   // block-local start of each digit run
+    __shared__ uint32_t gbase[NB];    // global start of each digit run of this block
     __shared__ uint32_t s_warp[RS_WARPS];
     __shared__ K s_key[RS_TILE];
     __shared__ uint32_t s_val[RS_TILE];
-    for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < RS_WARPS * (int)NB; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t ltmask = (1u << lane) - 1u;
@@ -168,7 +175,7 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(const K *__restr
         const bool ok = i < n;
         key[r] = ok ? kin[i] : (K)0;
         val[r] = ok ? vin[i] : 0u;
-        dig[r] = ok ? ((uint32_t)(key[r] >> shift) & 255u) : 256u;
+        dig[r] = ok ? ((uint32_t)(key[r] >> shift) & (NB - 1u)) : NB;
         const uint32_t peers = __match_any_sync(0xffffffffu, dig[r]);
         uint32_t before = 0;
         if (ok) before = wcnt[warp][dig[r]];
@@ -179,16 +186,19 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(const K *__restr
     }
     __syncthreads();
     {
-        // per digit: warp prefix, block total, then the block-local start
-        const int d = threadIdx.x;  // 256 threads = 256 digits
+        // per digit (threads 0..NB-1): warp prefix, block total, then the
+        // block-local start
+        const int d = threadIdx.x;
         uint32_t run = 0;
+        if (d < (int)NB) {
 #pragma unroll
-        for (int w = 0; w < RS_WARPS; ++w) {
-            const uint32_t t = wcnt[w][d];
-            wcnt[w][d] = run;
-            run += t;
+            for (int w = 0; w < RS_WARPS; ++w) {
+                const uint32_t t = wcnt[w][d];
+                wcnt[w][d] = run;
+                run += t;
+            }
         }
-        uint32_t x = run;  // inclusive scan of the totals over the 256 digits
+        uint32_t x = run;  // inclusive scan of the totals over the digits
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -196,15 +206,17 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(const K *__restr
         }
         if (lane == 31) s_warp[warp] = x;
         __syncthreads();
-        uint32_t wpre = 0;
-        for (int w = 0; w < warp; ++w) wpre += s_warp[w];
-        dstart[d] = wpre + x - run;
-        gbase[d] = offs[(uint64_t)d * nblocks + blockIdx.x];
+        if (d < (int)NB) {
+            uint32_t wpre = 0;
+            for (int w = 0; w < warp; ++w) wpre += s_warp[w];
+            dstart[d] = wpre + x - run;
+            gbase[d] = offs[(uint64_t)d * nblocks + blockIdx.x];
+        }
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < RS_ROUNDS; ++r) {
-        if (dig[r] < 256u) {
+        if (dig[r] < NB) {
             const uint32_t lp = dstart[dig[r]] + wcnt[warp][dig[r]] + rank[r];
             s_key[lp] = key[r];
             s_val[lp] = val[r];
@@ -214,7 +226,7 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(const K *__restr
     const uint32_t cnt = n - blk0 < (uint64_t)RS_TILE ? (uint32_t)(n - blk0) : (uint32_t)RS_TILE;
     for (uint32_t j = threadIdx.x; j < cnt; j += RS_THREADS) {
         const K k = s_key[j];
-        const uint32_t d = (uint32_t)(k >> shift) & 255u;
+        const uint32_t d = (uint32_t)(k >> shift) & (NB - 1u);
         const uint32_t pos = gbase[d] + (j - dstart[d]);
         kout[pos] = k;
         vout[pos] = s_val[j];
@@ -227,23 +239,41 @@ size_t radix_hist_words(uint64_t n)
     return 256 * nb;
 }
 
-// Stable LSD sort of (keys, vals) on key bits [shift0, shift0 + bits).  Uses
-// the alt buffers; returns 1 if the result ended in the alt buffers.
+template <class K, int RB>
+static void radix_pass(const K *ka, const uint32_t *va, K *kb, uint32_t *vb, uint64_t n, int shift, uint32_t *hist,
+                       uint32_t *scan_tmp, cudaStream_t st, int *launches)
+{
+    const uint32_t nb = (uint32_t)((n + RS_TILE - 1) / RS_TILE);
+    rs_hist_kernel<K, RB><<<nb, RS_THREADS, 0, st>>>(ka, (uint32_t)n, shift, hist, nb);
+    ++*launches;
+    exclusive_scan(hist, hist, ((uint64_t)1 << RB) * nb, scan_tmp, st, launches);
+    rs_scatter_kernel<K, RB><<<nb, RS_THREADS, 0, st>>>(ka, va, kb, vb, (uint32_t)n, shift, hist, nb);
+    ++*launches;
+}
+
+// Stable LSD sort of (keys, vals) on key bits [shift0, shift0 + bits): the
+// fewest passes of at most 8 bits, with equal digits (at least 4 bits: the
+// key bits above shift0 + bits must then be zero, as they are for every
+// caller).  Uses the alt buffers; returns 1 if the result ended in the alt
+// buffers.
 template <class K>
 static int radix_sort(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt, uint64_t n, int bits,
                       uint32_t *hist, uint32_t *scan_tmp, cudaStream_t st, int *launches, int shift0 = 0)
 {
-    if (n == 0) return 0;
-    const uint32_t nb = (uint32_t)((n + RS_TILE - 1) / RS_TILE);
+    if (n == 0 || bits <= 0) return 0;
+    const int passes = (bits + 7) / 8;
+    const int rb = (bits + passes - 1) / passes;
     K *ka = keys, *kb = keys_alt;
     uint32_t *va = vals, *vb = vals_alt;
     int flips = 0;
-    for (int shift = shift0; shift < shift0 + bits; shift += 8) {
-        rs_hist_kernel<K><<<nb, RS_THREADS, 0, st>>>(ka, (uint32_t)n, shift, hist, nb);
-        ++*launches;
-        exclusive_scan(hist, hist, (uint64_t)256 * nb, scan_tmp, st, launches);
-        rs_scatter_kernel<K><<<nb, RS_THREADS, 0, st>>>(ka, va, kb, vb, (uint32_t)n, shift, hist, nb);
-        ++*launches;
+    for (int p = 0, shift = shift0; p < passes; ++p, shift += rb) {
+        switch (rb) {
+        case 1: case 2: case 3: case 4: radix_pass<K, 4>(ka, va, kb, vb, n, shift, hist, scan_tmp, st, launches); break;
+        case 5: radix_pass<K, 5>(ka, va, kb, vb, n, shift, hist, scan_tmp, st, launches); break;
+        case 6: radix_pass<K, 6>(ka, va, kb, vb, n, shift, hist, scan_tmp, st, launches); break;
+        case 7: radix_pass<K, 7>(ka, va, kb, vb, n, shift, hist, scan_tmp, st, launches); break;
+        default: radix_pass<K, 8>(ka, va, kb, vb, n, shift, hist, scan_tmp, st, launches); break;
+        }
         K *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
         flips ^= 1;
@@ -453,7 +483,7 @@ int run_binning(const BinArgs &a, BinOut &o, cudaStream_t st, int *launches)
         cell_keys_kernel<<<blocks_for(ne, T), T, 0, st>>>(evv, ne, a.n_gauss, a.u32_b);
         ++*launches;
         int bits = 0;
-        while ((1ull << bits) < (uint64_t)a.n_cells) bits += 8;
+        while ((1ull << bits) < (uint64_t)a.n_cells) ++bits;
         // carry the key bits along: sort (cell, position) then gather keys
         // through the permuted positions
         iota_kernel<<<blocks_for(ne, T), T, 0, st>>>(a.u32_a, ne);
@@ -487,7 +517,7 @@ int run_binning(const BinArgs &a, BinOut &o, cudaStream_t st, int *launches)
                                  a.scan_tmp, st, launches, cb);
     } else {
         int bits = 0;
-        while ((1ull << bits) < a.n_segments) bits += 8;
+        while ((1ull << bits) < a.n_segments) ++bits;
         h = radix_sort<uint32_t>(a.ent_seg[0], a.ent_ev[0], a.ent_seg[1], a.ent_ev[1], a.n_entries, bits, a.hist,
                                  a.scan_tmp, st, launches);
     }
