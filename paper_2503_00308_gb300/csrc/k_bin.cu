@@ -19,10 +19,8 @@ namespace ar {
 
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
-// items per thread: a block ranks and reorders RS_THREADS * rounds items in
-// shared memory (16 rounds for 32-bit keys, 8 for 64-bit keys: 40 KB either way)
-template <class K> struct RsRounds { static constexpr int R = sizeof(K) == 4 ? 16 : 8; };
-constexpr int RS_MIN_TILE = RS_THREADS * 8;  // the smallest block tile (sizes the histogram)
+constexpr int RS_ROUNDS = 8;
+constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;  // items per block
 
 // ------------------------------------------------------------------ scan
 constexpr int SC_THREADS = 256;
@@ -129,7 +127,6 @@ template <class K, int RB>
 __global__ void __launch_bounds__(RS_THREADS) rs_hist_kernel(const K *__restrict__ keys, uint32_t n, int shift,
                                                              uint32_t *__restrict__ hist, uint32_t nblocks)
 {
-    constexpr int RS_ROUNDS = RsRounds<K>::R, RS_TILE = RS_THREADS * RS_ROUNDS;
     constexpr uint32_t NB = 1u << RB;
     __shared__ uint32_t h[NB];
     if (threadIdx.x < NB) h[threadIdx.x] = 0;
@@ -156,7 +153,6 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(const K *__restr
                                                                 const uint32_t *__restrict__ offs,
                                                                 uint32_t nblocks)
 {
-    constexpr int RS_ROUNDS = RsRounds<K>::R, RS_TILE = RS_THREADS * RS_ROUNDS;
     constexpr uint32_t NB = 1u << RB;
     static_assert(NB <= RS_THREADS, "one thread per digit");
     __shared__ uint32_t wcnt[RS_WARPS][NB];
@@ -239,7 +235,7 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(const K *__restr
 
 size_t radix_hist_words(uint64_t n)
 {
-    const uint64_t nb = (n + RS_MIN_TILE - 1) / RS_MIN_TILE;
+    const uint64_t nb = (n + RS_TILE - 1) / RS_TILE;
     return 256 * nb;
 }
 
@@ -247,7 +243,6 @@ template <class K, int RB>
 static void radix_pass(const K *ka, const uint32_t *va, K *kb, uint32_t *vb, uint64_t n, int shift, uint32_t *hist,
                        uint32_t *scan_tmp, cudaStream_t st, int *launches)
 {
-    constexpr int RS_TILE = RS_THREADS * RsRounds<K>::R;
     const uint32_t nb = (uint32_t)((n + RS_TILE - 1) / RS_TILE);
     rs_hist_kernel<K, RB><<<nb, RS_THREADS, 0, st>>>(ka, (uint32_t)n, shift, hist, nb);
     ++*launches;
