@@ -136,17 +136,6 @@ __device__ __forceinline__ void pixel_alpha(const R *__restrict__ r, R ux, R uy,
     }
     const B m = pm.result();
     const R mlo = m.vlo, mhi = m.vhi;
-    // Beyond the cutoff at every pose of the cell (m >= tau + 1/2 > tau):
-    // a = 0, and the steps below give the zero forms (psi2 = 1 because the
-    // ramp is at most CUT_RAMP; the lower form stays below 1/255 by a margin
-    // of (1 - e^-1/4)/255), except for the TINY slack of the upper constant.
-    if (mlo >= r[RL::TAU_UP] + R(CUT_RAMP)) {
-#pragma unroll
-        for (int j = 0; j < M; ++j) { out.L.c[j] = 0; out.U.c[j] = 0; }
-        out.L.k = 0; out.U.k = 0; out.rL = 0; out.rU = 0;
-        out.alo = 0; out.ahi = 0;
-        return;
-    }
     // Exp on x = -m/2 in [xl, xu], xu clipped at 0 because m >= 0
     const R xl = R(-0.5) * mhi;
     R xu = N::min(R(-0.5) * mlo, R(0));
@@ -538,15 +527,10 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
                 }
                 c_rec = ev.rec;
                 const float col[3] = {r[RL::COL], r[RL::COL + 1], r[RL::COL + 2]};
-                // a Gaussian with a_hi = 0 (beyond the cutoff; its forms are
-                // zero) changes neither sum nor product: the steps are skipped
-                const bool live = cache.ahi > 0.f;
                 if (lower) {
-                    if (live) {
-                        hi.add(PB, col, cache.U, cache.rU);
-                        PAp = __fmul_rd(PAp, __fsub_rd(1.f, cache.ahi));
-                        open_w = __fadd_ru(open_w, open_ratio_up(cache.ahi));
-                    }
+                    hi.add(PB, col, cache.U, cache.rU);
+                    PAp = __fmul_rd(PAp, __fsub_rd(1.f, cache.ahi));
+                    open_w = __fadd_ru(open_w, open_ratio_up(cache.ahi));
                     const int k = (int)(head % RING);
                     ++head;
                     s_rid[k * NT + tid] = ev.rec;
@@ -557,7 +541,7 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
                     pp[3 * NT] = cache.L.k;
 #pragma unroll
                     for (int j = 0; j < M; ++j) pp[(4 + j) * NT] = cache.L.c[j];
-                } else if (live) {
+                } else {
                     open_w = fmaxf(0.f, __fsub_ru(open_w, open_ratio_up(cache.ahi)));
                     const uint32_t flags = __float_as_uint(r[RL::FLAGS]);
                     float T = PA;
