@@ -43,12 +43,12 @@ def flops_per_triple(M: int) -> int:
 
 # DRAM bytes of the render kernel per opacity evaluation, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the first 4 cells of the
-# 300k-Gaussian workload: 62.5 MB over 102.0M evaluations.  Valid only for the
+# 300k-Gaussian workload: 62.6 MB over 102.0M evaluations.  Valid only for the
 # kernel sources it was taken from (their SHA-256 below); otherwise the
 # roofline's traffic is reported as null.
-RENDER_TRAFFIC = {"bytes_per_evaluation": (43775232 + 18682368) / 101959073,
+RENDER_TRAFFIC = {"bytes_per_evaluation": (43892992 + 18751232) / 101964693,
                   "sources": ["k_render.cuh", "ar_num.cuh", "ar_common.cuh", "k_inst.cuh"],
-                  "sha256": "04e746fa92b13294c1124e2869bfbcb00ce3d59b4b6fc682261cb5563aafcdb5"}
+                  "sha256": "045a1e4469cc79270963a4754087887ad72cc605e3f158945e7f25ba2238ad89"}
 
 
 def render_traffic(n_evaluated: int):
