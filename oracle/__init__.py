@@ -68,6 +68,8 @@ def _load():
         lib.orc_pixel_trace.restype = I
         lib.orc_record_trace.argtypes = [P, P, P, P, P, I64, P, P, P, P, P, I64, P]
         lib.orc_record_trace.restype = I
+        lib.orc_set_boxes.argtypes = [P, I64]
+        lib.orc_set_boxes.restype = I
         lib.orc_set_threads.argtypes = [I]
         lib.orc_set_threads.restype = I
         _lib = lib
@@ -109,6 +111,19 @@ def render_concrete(scene, cam, delta, blend: str = "ind") -> np.ndarray:
     if st:
         raise RuntimeError("oracle concrete render failed")
     return out
+
+
+def set_boxes(boxes):
+    """Scene-parameter boxes (Sec. 4.5) for the abstract calls that follow:
+    an [n, 14] array per Gaussian (mean lo[3], hi[3]; opacity lo, hi; colour
+    lo[3], hi[3]), or None to clear them."""
+    lib = _load()
+    if boxes is None:
+        lib.orc_set_boxes(None, 0)
+        return
+    b = _d(boxes).reshape(-1, 14)
+    if lib.orc_set_boxes(_p(b), b.shape[0]):
+        raise MemoryError("oracle boxes")
 
 
 def render_abstract(scene, cam, cell_lo, cell_hi, window=None, with_cond=False):

@@ -622,7 +622,9 @@ typedef struct {
     int px0, px1, py0, py1;  /* pixel box whose centres may see the Gaussian */
     bs S, Px, Py;       /* S = d^2, P = d * up */
     bs W[6];            /* W = Conic * Mp, row-major 2x3 */
-    double o, tau, c[3];
+    /* scene parameters as boxes (Sec. 4.5; lo = hi without boxes): opacity,
+     * its cutoff exponent tau = 2 ln(255 o) at both ends, colour */
+    double o_lo, o_hi, tau_lo, tau_hi, c_lo[3], c_hi[3];
 } grec;
 
 /* Interval helpers for the screen box (sound enclosures, no correlation). */
@@ -638,27 +640,69 @@ static ival iv_scale(ival a, double s) { ival r = s >= 0 ? (ival){s * a.l, s * a
 static ival iv_add(ival a, ival b) { ival r = {a.l + b.l, a.u + b.u}; return r; }
 static double iv_sqmax(ival a) { return fmax(a.l * a.l, a.u * a.u); }
 
+/* Scene-parameter boxes for the abstract render (Sec. 4.5): per Gaussian 14
+ * doubles, mean lo[3], hi[3] (world frame), opacity lo, hi, colour lo[3],
+ * hi[3]; each Gaussian's parameters range over their boxes independently.
+ * Set for the calls that follow (NULL clears them). */
+static double *g_boxes = NULL;
+static int64_t g_boxes_n = 0;
+
+int orc_set_boxes(const double *boxes, int64_t n)
+{
+    free(g_boxes);
+    g_boxes = NULL;
+    g_boxes_n = 0;
+    if (!boxes || n <= 0) return 0;
+    g_boxes = (double *)malloc(sizeof(double) * 14 * (size_t)n);
+    if (!g_boxes) return 1;
+    memcpy(g_boxes, boxes, sizeof(double) * 14 * (size_t)n);
+    g_boxes_n = n;
+    return 0;
+}
+
+static const double *box_of(int64_t i) { return (g_boxes && i < g_boxes_n) ? g_boxes + 14 * i : NULL; }
+
 static void gaussian_record(const camera *cam, const cellforms *cf, const double *uw, const double *ls,
-                            const double *q, double o, const double *rgb, grec *g)
+                            const double *q, double o, const double *rgb, const double *pb, grec *g)
 {
     memset(g, 0, sizeof *g);
-    g->o = o;
-    g->tau = (o > 0) ? 2.0 * log(255.0 * o) : -INFINITY;
-    for (int k = 0; k < 3; ++k) g->c[k] = rgb[k];
+    /* the parameters, as boxes (lo = hi = the nominal value without one) */
+    double uwl[3], uwh[3];
+    for (int k = 0; k < 3; ++k) {
+        uwl[k] = pb ? pb[k] : uw[k];
+        uwh[k] = pb ? pb[3 + k] : uw[k];
+        g->c_lo[k] = pb ? pb[8 + k] : rgb[k];
+        g->c_hi[k] = pb ? pb[11 + k] : rgb[k];
+    }
+    g->o_lo = pb ? pb[6] : o;
+    g->o_hi = pb ? pb[7] : o;
+    g->tau_lo = (g->o_lo > 0) ? 2.0 * log(255.0 * g->o_lo) : -INFINITY;
+    g->tau_hi = (g->o_hi > 0) ? 2.0 * log(255.0 * g->o_hi) : -INFINITY;
     g->rho = INFINITY;
-    if (!(g->tau >= 0)) return;   /* o < 1/255: never reaches the cutoff */
+    if (!(g->tau_hi >= 0)) return;   /* o < 1/255: never reaches the cutoff */
 
-    /* a1: nominal camera-frame mean v = R0 (uw - t0) and N = R0 Mw */
-    double Mw[9], N[9], v[3];
+    /* a1: camera-frame mean v = R0 (uw - t0), an interval over the mean's box
+     * (each product taken at the end of the box its sign selects), and N = R0 Mw */
+    double Mw[9], N[9], vl[3], vh[3];
     cov_factor(ls, q, Mw);
     mat3_mul(cam->R0, Mw, N);
     for (int a = 0; a < 3; ++a) {
-        v[a] = 0;
-        for (int b = 0; b < 3; ++b) v[a] += cam->R0[3 * a + b] * (uw[b] - cam->t0[b]);
+        vl[a] = 0;
+        vh[a] = 0;
+        for (int b = 0; b < 3; ++b) {
+            const double r = cam->R0[3 * a + b], dl = uwl[b] - cam->t0[b], dh = uwh[b] - cam->t0[b];
+            vl[a] += r >= 0 ? r * dl : r * dh;
+            vh[a] += r >= 0 ? r * dh : r * dl;
+        }
     }
     /* Algorithm 1, line 2: uc = R_delta^T (v - s) */
     bs vms[3], uc[3];
-    for (int b = 0; b < 3; ++b) vms[b] = bs_sub(bs_cst(v[b]), cf->s[b]);
+    for (int b = 0; b < 3; ++b) {
+        bs vb;
+        vb.lo = lf_cst(vl[b]);
+        vb.hi = lf_cst(vh[b]);
+        vms[b] = bs_sub(vb, cf->s[b]);
+    }
     for (int a = 0; a < 3; ++a) {
         uc[a] = bs_mul(cf->Rd[a], vms[0]);   /* R_delta[0][a] */
         uc[a] = bs_add(uc[a], bs_mul(cf->Rd[3 + a], vms[1]));
@@ -701,7 +745,7 @@ static void gaussian_record(const camera *cam, const cellforms *cf, const double
     {
         ival Ri[9], vs[3];
         for (int e = 0; e < 9; ++e) { Ri[e].l = bs_min(&cf->Rd[e]); Ri[e].u = bs_max(&cf->Rd[e]); }
-        for (int b = 0; b < 3; ++b) { vs[b].l = v[b] - bs_max(&cf->s[b]); vs[b].u = v[b] - bs_min(&cf->s[b]); }
+        for (int b = 0; b < 3; ++b) { vs[b].l = vl[b] - bs_max(&cf->s[b]); vs[b].u = vh[b] - bs_min(&cf->s[b]); }
         double dl = fmax(dlo, cam->near_plane);
         ival D = {dl, dhi};
         ival ucx = iv_add(iv_add(iv_mul(Ri[0], vs[0]), iv_mul(Ri[3], vs[1])), iv_mul(Ri[6], vs[2]));
@@ -727,7 +771,7 @@ static void gaussian_record(const camera *cam, const cellforms *cf, const double
             ival p1 = iv_scale(iv_add(iv_mul(D, m[1]), iv_scale(iv_mul(ucy, m[2]), -1.0)), cam->fy);
             X00 += iv_sqmax(p0); X11 += iv_sqmax(p1);
         }
-        double rx = sqrt(g->tau * X00) / (dl * dl), ry = sqrt(g->tau * X11) / (dl * dl);
+        double rx = sqrt(g->tau_hi * X00) / (dl * dl), ry = sqrt(g->tau_hi * X11) / (dl * dl);
         double xl = mux.l - rx, xh = mux.u + rx, yl = muy.l - ry, yh = muy.u + ry;
         xl -= BOX_SLACK * (1 + fabs(xl)); xh += BOX_SLACK * (1 + fabs(xh));
         yl -= BOX_SLACK * (1 + fabs(yl)); yh += BOX_SLACK * (1 + fabs(yh));
@@ -777,7 +821,7 @@ typedef struct { lf L, U; double alo, ahi; double mlo, mhi, ramp; } galpha;
 static void gaussian_alpha(const grec *g, double ux, double uy, galpha *r)
 {
     if (g->fallback) {
-        r->L = lf_cst(0); r->U = lf_cst(g->o); r->alo = 0; r->ahi = g->o;
+        r->L = lf_cst(0); r->U = lf_cst(g->o_hi); r->alo = 0; r->ahi = g->o_hi;
         r->mlo = -INFINITY; r->mhi = INFINITY; r->ramp = 0;
         return;
     }
@@ -800,17 +844,21 @@ static void gaussian_alpha(const grec *g, double ux, double uy, galpha *r)
     /* lower: El (1 + x - xl) with x >= -m.hi/2 ; upper: El + slope (x - xl) with x <= -m.lo/2 */
     lf Le = lf_scale(&m.hi, -0.5 * El); Le.k += El * (1.0 - xl);
     lf Ue = lf_scale(&m.lo, -0.5 * slope); Ue.k += El - slope * xl;
-    lf La = lf_scale(&Le, g->o), Ua = lf_scale(&Ue, g->o);
+    /* a = o e with o in [o_lo, o_hi] and e >= 0: o_lo below, o_hi above */
+    lf La = lf_scale(&Le, g->o_lo), Ua = lf_scale(&Ue, g->o_hi);
     /* upper side: blend toward the constant o when the form's maximum exceeds o */
     double amax = lf_max(&Ua);
-    double lam = clamp01((g->o * (1.0 + CLIP_RAMP) - amax) / (g->o * CLIP_RAMP));
-    lf U1 = lf_scale(&Ua, lam); U1.k += (1.0 - lam) * g->o;
+    double lam = clamp01((g->o_hi * (1.0 + CLIP_RAMP) - amax) / (g->o_hi * CLIP_RAMP));
+    lf U1 = lf_scale(&Ua, lam); U1.k += (1.0 - lam) * g->o_hi;
     /* cutoff ramps: width shrinks with the m interval, zero on a point cell */
     double ramp = fmin(CUT_RAMP, mhi - mlo);
     if (!(ramp > 0)) ramp = 0;
     r->ramp = ramp;
-    double psi2 = (mlo <= g->tau) ? 0.0 : (ramp > 0 ? clamp01((mlo - g->tau) / ramp) : 1.0);
-    double psi = (mhi > g->tau) ? 1.0 : (ramp > 0 ? clamp01((mhi - g->tau + ramp) / ramp) : 0.0);
+    /* the upper form is cut where m > tau(o_hi) for every pose (no opacity in
+     * the box is then visible); the lower one keeps a margin of 1/255 unless
+     * m <= tau(o_lo) at every pose (no opacity in the box is then cut) */
+    double psi2 = (mlo <= g->tau_hi) ? 0.0 : (ramp > 0 ? clamp01((mlo - g->tau_hi) / ramp) : 1.0);
+    double psi = (mhi > g->tau_lo) ? 1.0 : (ramp > 0 ? clamp01((mhi - g->tau_lo + ramp) / ramp) : 0.0);
     r->U = lf_scale(&U1, 1.0 - psi2);
     lf L2 = La; L2.k -= psi * ALPHA_MIN;
     double l2min = lf_min(&L2), l2max = lf_max(&L2);
@@ -818,7 +866,7 @@ static void gaussian_alpha(const grec *g, double ux, double uy, galpha *r)
     r->L = lf_scale(&L2, mu);
     if (g->straddle) r->L = lf_cst(0);
     r->alo = fmax(0.0, lf_min(&r->L));
-    r->ahi = fmin(g->o, lf_max(&r->U));
+    r->ahi = fmin(g->o_hi, lf_max(&r->U));
 }
 
 /* Abstract render of one cell over the pixel window [px0,px1] x [py0,py1].
@@ -846,7 +894,7 @@ int orc_render_abstract(const double *uw, const double *ls, const double *quat, 
     if (!G) return 1;
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t i = 0; i < n; ++i)
-        gaussian_record(&cam, &cf, uw + 3 * i, ls + 3 * i, quat + 4 * i, opac[i], rgb + 3 * i, &G[i]);
+        gaussian_record(&cam, &cf, uw + 3 * i, ls + 3 * i, quat + 4 * i, opac[i], rgb + 3 * i, box_of(i), &G[i]);
 
     int npx = px1 - px0 + 1, npy = py1 - py0 + 1;
     int status = 0;
@@ -875,9 +923,9 @@ int orc_render_abstract(const double *uw, const double *ls, const double *quat, 
             if (g->rho_margin < 1e-6) frag = 1;
             if (!g->fallback && A[K].ramp < 0.05) {
                 /* a narrow ramp makes the cutoff nearly a step in m */
-                double tol = 1e-3 * fmax(1.0, g->tau), rp = A[K].ramp;
-                if (A[K].mhi > g->tau - rp - tol && A[K].mhi < g->tau + tol) frag = 1;
-                if (A[K].mlo > g->tau - tol && A[K].mlo < g->tau + rp + tol) frag = 1;
+                double tol = 1e-3 * fmax(1.0, g->tau_hi), rp = A[K].ramp;
+                if (A[K].mhi > g->tau_lo - rp - tol && A[K].mhi < g->tau_lo + tol) frag = 1;
+                if (A[K].mlo > g->tau_hi - tol && A[K].mlo < g->tau_hi + rp + tol) frag = 1;
             }
             ++K;
         }
@@ -908,9 +956,10 @@ int orc_render_abstract(const double *uw, const double *ls, const double *quat, 
                 est += 2.0 * Thi * da;
             }
             for (int ch = 0; ch < 3; ++ch) {
-                lf t = lf_scale(&A[a].L, Tlo * gi->c[ch]);
+                /* colour in [c_lo, c_hi] and L', U' >= 0 over the cell */
+                lf t = lf_scale(&A[a].L, Tlo * gi->c_lo[ch]);
                 lo[ch] = lf_add(&lo[ch], &t);
-                t = lf_scale(&A[a].U, Thi * gi->c[ch]);
+                t = lf_scale(&A[a].U, Thi * gi->c_hi[ch]);
                 hi[ch] = lf_add(&hi[ch], &t);
             }
         }
@@ -940,7 +989,7 @@ int orc_records(const double *uw, const double *ls, const double *quat, const do
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t i = 0; i < n; ++i) {
         grec g;
-        gaussian_record(&cam, &cf, uw + 3 * i, ls + 3 * i, quat + 4 * i, opac[i], rgb + 3 * i, &g);
+        gaussian_record(&cam, &cf, uw + 3 * i, ls + 3 * i, quat + 4 * i, opac[i], rgb + 3 * i, box_of(i), &g);
         double *o = out + 13 * i;
         o[0] = g.valid; o[1] = g.straddle; o[2] = g.fallback; o[3] = g.klo; o[4] = g.khi;
         o[5] = g.px0; o[6] = g.px1; o[7] = g.py0; o[8] = g.py1; o[9] = g.rho;
@@ -1044,7 +1093,7 @@ int orc_pixel_detail(const double *uw, const double *ls, const double *quat, con
     int k = 0;
     for (int64_t i = 0; i < n && k < cap; ++i) {
         grec g;
-        gaussian_record(&cam, &cf, uw + 3 * i, ls + 3 * i, quat + 4 * i, opac[i], rgb + 3 * i, &g);
+        gaussian_record(&cam, &cf, uw + 3 * i, ls + 3 * i, quat + 4 * i, opac[i], rgb + 3 * i, box_of(i), &g);
         if (!g.valid || px < g.px0 || px > g.px1 || py < g.py0 || py > g.py1) continue;
         galpha a;
         gaussian_alpha(&g, px + 0.5, py + 0.5, &a);
@@ -1068,7 +1117,7 @@ int orc_pixel_trace(const double *uw, const double *ls, const double *quat, cons
     cell_setup(&cam, cell_lo, cell_hi, &cf);
     if (gi < 0 || gi >= n) return 1;
     grec g;
-    gaussian_record(&cam, &cf, uw + 3 * gi, ls + 3 * gi, quat + 4 * gi, opac[gi], rgb + 3 * gi, &g);
+    gaussian_record(&cam, &cf, uw + 3 * gi, ls + 3 * gi, quat + 4 * gi, opac[gi], rgb + 3 * gi, box_of(gi), &g);
     if (!g.valid || g.fallback) return 1;
     double ux = px + 0.5, uy = py + 0.5;
     bs Dx = bs_sub(bs_scale(g.S, ux), g.Px);

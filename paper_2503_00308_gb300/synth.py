@@ -131,6 +131,31 @@ def box_scene(n: int, seed: int, extent=(20.0, 5.0, 20.0), logscale_mu: float = 
                  o.astype(np.float32), c.astype(np.float32))
 
 
+def scene_boxes(sc: Scene, seed: int, frac: float = 0.3, mean_d=(0.0, 0.0, 0.0), opacity_scale: float = 1.0,
+                opacity_add: float = 0.0, red_add: float = 0.0) -> dict:
+    """Scene-parameter boxes in the manner of the paper's Sec. 4.5 experiments,
+    on a seeded fraction of the Gaussians: the mean moved by 0..mean_d (world
+    frame), the opacity scaled by opacity_scale and raised by up to
+    opacity_add (capped below 1), the red channel raised by up to red_add
+    (capped at 1).  Returns float32 arrays uw_lo, uw_hi (n, 3), o_lo, o_hi
+    (n,), c_lo, c_hi (n, 3); the other Gaussians keep lo = hi = nominal."""
+    rng = np.random.default_rng(seed)
+    sel = rng.uniform(size=sc.n) < frac
+    d = np.asarray(mean_d, dtype=np.float64)
+    uw = sc.uw.astype(np.float64)
+    uw_lo = np.where(sel[:, None], uw + np.minimum(d, 0.0), uw)
+    uw_hi = np.where(sel[:, None], uw + np.maximum(d, 0.0), uw)
+    o = sc.opacity.astype(np.float64)
+    o_lo = np.where(sel, np.minimum(o * opacity_scale, 0.99), o)
+    o_hi = np.where(sel, np.minimum(o * opacity_scale + opacity_add, 0.99), o)
+    c = sc.rgb.astype(np.float64)
+    c_lo = c.copy()
+    c_hi = c.copy()
+    c_hi[:, 0] = np.where(sel, np.minimum(c[:, 0] + red_add, 1.0), c[:, 0])
+    f = lambda a: np.ascontiguousarray(a, dtype=np.float32)
+    return {"uw_lo": f(uw_lo), "uw_hi": f(uw_hi), "o_lo": f(o_lo), "o_hi": f(o_hi), "c_lo": f(c_lo), "c_hi": f(c_hi)}
+
+
 def look_camera(width: int, height: int, f: float, centre=(0.0, 0.0, -4.0), near: float = 0.2) -> Camera:
     """Pinhole camera with identity orientation (looking along +z) at `centre`.
     Intrinsics are rounded to float32 so every consumer sees the same values."""

@@ -542,3 +542,94 @@ def test_guard_band_crossing_is_sound(orc):
     worst, nv = orc.check_samples(sc, cam, poses, lo, hi, tol=1e-12)
     assert nv == 0, worst
     assert np.all(lo == 0.0) and hi[8, 15, 0] > 0.2
+
+
+# ------------------------------------------------ scene-parameter boxes (Sec. 4.5)
+
+def _box_array(b):
+    return np.concatenate([b["uw_lo"], b["uw_hi"], b["o_lo"][:, None], b["o_hi"][:, None], b["c_lo"], b["c_hi"]],
+                          axis=1).astype(np.float64)
+
+
+def _sample_scene(sc, b, rng):
+    u = lambda shape: rng.uniform(size=shape)
+    lo, hi = b["uw_lo"].astype(np.float64), b["uw_hi"].astype(np.float64)
+    uw = lo + (hi - lo) * u(lo.shape)
+    o = b["o_lo"] + (b["o_hi"].astype(np.float64) - b["o_lo"]) * u(sc.n)
+    c = b["c_lo"] + (b["c_hi"].astype(np.float64) - b["c_lo"]) * u((sc.n, 3))
+    return synth.Scene(uw, sc.logscale.astype(np.float64), sc.quat.astype(np.float64), o, c)
+
+
+def test_boxes_point_cell_closed_form(orc):
+    # one Gaussian seen from a fixed pose, with opacity in [o/2, o] and red in
+    # [c - 0.2, c]: at a pixel where no opacity of the box is cut, a = o e^-m/2
+    # is exact at a point cell and T = 1, so the bounds are c_lo o_lo e and
+    # c_hi o_hi e (e from the textbook EWA formula)
+    sc = synth.object_scene(1, 7, mean_sd=0.0, logscale_mu=-1.6)
+    sc.opacity[:] = 0.9
+    sc.rgb[:] = np.array([0.7, 0.4, 0.2], dtype=np.float32)
+    cam = synth.look_camera(24, 24, 30.0, centre=(0, 0, -3))
+    b = {"uw_lo": sc.uw.copy(), "uw_hi": sc.uw.copy(), "o_lo": np.float32([0.45]), "o_hi": np.float32([0.9]),
+         "c_lo": np.float32([[0.5, 0.4, 0.2]]), "c_hi": np.float32([[0.7, 0.4, 0.2]])}
+    d = np.zeros(6)
+    orc.set_boxes(_box_array(b))
+    try:
+        lo, hi, _ = orc.render_abstract(sc, cam, d, d)
+    finally:
+        orc.set_boxes(None)
+    n_checked = 0
+    for py in range(8, 16):
+        for px in range(8, 16):
+            e = _ewa_alpha(sc.uw[0].astype(np.float64), sc.logscale[0].astype(np.float64),
+                           sc.quat[0].astype(np.float64), 1.0, cam, d, px + 0.5, py + 0.5)
+            if 0.45 * e < 1.5 / 255:
+                continue
+            # (the box ends are float32 values)
+            exp_lo = b["c_lo"][0].astype(np.float64) * float(b["o_lo"][0]) * e
+            exp_hi = b["c_hi"][0].astype(np.float64) * float(b["o_hi"][0]) * e
+            np.testing.assert_allclose(lo[py, px], exp_lo, rtol=1e-9, atol=1e-12)
+            np.testing.assert_allclose(hi[py, px], exp_hi, rtol=1e-9, atol=1e-12)
+            n_checked += 1
+    assert n_checked > 20
+
+
+def test_boxes_equal_to_nominal_change_nothing(orc):
+    w = synth.tiny64()
+    b = synth.scene_boxes(w.scene, 3, frac=0.0)
+    lo0, hi0, _ = orc.render_abstract(w.scene, w.camera, w.cells_lo[0], w.cells_hi[0])
+    orc.set_boxes(_box_array(b))
+    try:
+        lo1, hi1, _ = orc.render_abstract(w.scene, w.camera, w.cells_lo[0], w.cells_hi[0])
+    finally:
+        orc.set_boxes(None)
+    assert np.array_equal(lo0, lo1) and np.array_equal(hi0, hi1)
+
+
+@pytest.mark.parametrize("kind", ["colour", "mean", "opacity", "all"])
+def test_boxes_sound_sampled(orc, kind):
+    # Theorem 1 over the product of the pose cell and the parameter boxes:
+    # concrete renders at sampled (pose, scene) pairs lie inside the bounds
+    sc = synth.object_scene(300, 11, logscale_mu=-3.0)
+    cam = synth.look_camera(36, 32, 44.0, centre=(0, 0, -3))
+    clo = np.array([-0.01, -0.01, -0.01, 0.0, -0.003, 0.0])
+    args = {"colour": dict(red_add=0.5), "mean": dict(mean_d=(0.0, 0.08, 0.0)),
+            "opacity": dict(opacity_scale=0.5, opacity_add=0.1),
+            "all": dict(red_add=0.3, mean_d=(0.03, 0.03, 0.0), opacity_scale=0.8, opacity_add=0.1)}[kind]
+    b = synth.scene_boxes(sc, 5, frac=0.4, **args)
+    orc.set_boxes(_box_array(b))
+    try:
+        lo, hi, _ = orc.render_abstract(sc, cam, clo, -clo)
+    finally:
+        orc.set_boxes(None)
+    base_lo, base_hi, _ = orc.render_abstract(sc, cam, clo, -clo)
+    assert np.all(lo <= hi)
+    if kind in ("colour", "mean"):
+        # boxes that hold the nominal scene widen the bounds
+        assert (hi - lo).sum() > (base_hi - base_lo).sum()
+    rng = np.random.default_rng(2)
+    corners = _corners(clo, -clo)
+    for k in range(60):
+        s2 = _sample_scene(sc, b, rng)
+        pose = corners[k] if k < 8 else synth.sample_poses(rng, clo, -clo, 1)[0]
+        img = orc.render_concrete(s2, cam, pose, "ind")
+        assert np.all(img >= lo - 1e-12) and np.all(img <= hi + 1e-12), (kind, k)
