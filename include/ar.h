@@ -191,6 +191,23 @@ int ar_render_abstract_plain_fp64(ar_scene *scene, const ar_intrinsics *intr,
 int ar_render_concrete(ar_scene *scene, const ar_intrinsics *intr, const ar_nominal_pose *pose,
                        const double *deltas, int32_t n_poses, float *out, void *cuda_stream);
 
+/* Scene-parameter boxes (Sec. 4.5, abstract rendering of sets of scenes):
+ * per Gaussian, an interval for its mean (uw_lo3/uw_hi3, [n][3], world
+ * frame), its opacity (opacity_lo/hi, [n], 0 <= lo <= hi < 1) and its colour
+ * (rgb_lo3/rgb_hi3, [n][3], 0 <= lo <= hi <= 1).  Host arrays, copied.  A
+ * NULL pair keeps that parameter at the scene's nominal value (all NULL:
+ * back to the nominal scene).  The boxes need not contain the nominal values.
+ * Later abstract renders bound GSplat over every pose of each cell and every
+ * scene whose Gaussians take any parameters in their boxes, independently of
+ * one another.  The mean's box enters the projection as an interval; the
+ * opacity box as o_lo in the lower opacity forms and cutoff and o_hi in the
+ * upper ones; the colour box as c_lo in the lower colour sum and c_hi in the
+ * upper one.  (ar_render_concrete keeps rendering the nominal scene.)
+ * Synchronous; must not overlap a render of the scene.  AR_EINVAL for a half
+ * given pair, a non-finite value or lo > hi. */
+int ar_scene_set_boxes(ar_scene *scene, const float *uw_lo3, const float *uw_hi3, const float *opacity_lo,
+                       const float *opacity_hi, const float *rgb_lo3, const float *rgb_hi3);
+
 /* Test and diagnosis hook: the decision part of every (Gaussian, cell)
  * record of one pose cell, as the batched renderer computes it (Algorithm 1
  * lines 2-7 with set-valued variables: depth, near-plane class, depth key,

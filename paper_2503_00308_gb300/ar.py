@@ -70,6 +70,7 @@ def lib():
             "ar_render_abstract_noalloc": ([P, P, P, P, c_int32, c_int32, P, P, P], ctypes.c_int),
             "ar_render_concrete": ([P, P, P, P, c_int32, P, P], ctypes.c_int),
             "ar_debug_records": ([P, P, P, P, P], ctypes.c_int),
+            "ar_scene_set_boxes": ([P, P, P, P, P, P, P], ctypes.c_int),
             "ar_set_profiling": ([P, ctypes.c_int], ctypes.c_int),
             "ar_set_workspace_limit": ([P, c_int64], ctypes.c_int),
             "ar_last_render_stats": ([P, P], ctypes.c_int),
@@ -260,6 +261,22 @@ class Scene:
         """Concrete renders at the poses deltas ([n][6]) into out ([n][H][W][3], device)."""
         d = np.ascontiguousarray(np.asarray(deltas, dtype=np.float64).reshape(-1, 6))
         ar_render_concrete(self.handle, make_intrinsics(cam), make_pose(cam), d, d.shape[0], out, stream)
+
+    def set_boxes(self, boxes=None):
+        """Scene-parameter boxes (a dict of float32 arrays uw_lo, uw_hi, o_lo,
+        o_hi, c_lo, c_hi, any pair may be missing), or None for the nominal scene."""
+        b = boxes or {}
+        keep = []
+
+        def arr(k):
+            if k not in b:
+                return None
+            a = np.ascontiguousarray(b[k], dtype=np.float32)
+            keep.append(a)
+            return a.ctypes.data
+
+        check(lib().ar_scene_set_boxes(self.handle, arr("uw_lo"), arr("uw_hi"), arr("o_lo"), arr("o_hi"),
+                                       arr("c_lo"), arr("c_hi")))
 
     def debug_records(self, cam, cell_lo, cell_hi) -> np.ndarray:
         cells = make_cells(np.reshape(cell_lo, (1, 6)), np.reshape(cell_hi, (1, 6)))

@@ -43,20 +43,20 @@ int rec_scalar_offset_m6();
 int launch_cell_prep_m1(const double *, const double *, const CallConst &, void *, cudaStream_t);
 int launch_cell_prep_m4(const double *, const double *, const CallConst &, void *, cudaStream_t);
 int launch_cell_prep_m6(const double *, const double *, const CallConst &, void *, cudaStream_t);
-int launch_record_prep_m1(const double *, const double *, const float *, const float *, const CallConst &,
+int launch_record_prep_m1(const double *, const void *, const CallConst &,
                           const void *, int, float *, PixBox *, double *, unsigned long long *, cudaStream_t);
-int launch_record_prep_m4(const double *, const double *, const float *, const float *, const CallConst &,
+int launch_record_prep_m4(const double *, const void *, const CallConst &,
                           const void *, int, float *, PixBox *, double *, unsigned long long *, cudaStream_t);
-int launch_record_prep_m6(const double *, const double *, const float *, const float *, const CallConst &,
+int launch_record_prep_m6(const double *, const void *, const CallConst &,
                           const void *, int, float *, PixBox *, double *, unsigned long long *, cudaStream_t);
 int launch_render_m1(int, const RenderLaunch &, cudaStream_t);
 int launch_render_m4(int, const RenderLaunch &, cudaStream_t);
 int launch_render_m6(int, const RenderLaunch &, cudaStream_t);
-int launch_record_prep64_m1(const double *, const double *, const float *, const float *, const CallConst &,
+int launch_record_prep64_m1(const double *, const void *, const CallConst &,
                             const void *, int, double *, PixBox *, double *, unsigned long long *, cudaStream_t);
-int launch_record_prep64_m4(const double *, const double *, const float *, const float *, const CallConst &,
+int launch_record_prep64_m4(const double *, const void *, const CallConst &,
                             const void *, int, double *, PixBox *, double *, unsigned long long *, cudaStream_t);
-int launch_record_prep64_m6(const double *, const double *, const float *, const float *, const CallConst &,
+int launch_record_prep64_m6(const double *, const void *, const CallConst &,
                             const void *, int, double *, PixBox *, double *, unsigned long long *, cudaStream_t);
 int launch_record_build_m1(const double *, const CallConst &, const void *, int64_t, const uint32_t *,
                            const uint32_t *, float *, unsigned long long *, uint32_t *, uint32_t *, uint32_t, uint32_t *,
@@ -86,25 +86,25 @@ int launch_cell_prep(int M, const double *lo, const double *hi, const CallConst 
     return M == 1 ? launch_cell_prep_m1(lo, hi, cc, cells, st)
                   : (M == 4 ? launch_cell_prep_m4(lo, hi, cc, cells, st) : launch_cell_prep_m6(lo, hi, cc, cells, st));
 }
-int launch_record_prep(int M, const double *vN, const double *tau, const float *opac, const float *rgb,
+int launch_record_prep(int M, const double *vN, const void *gp,
                        const CallConst &cc, const void *cells, int TS, float *recs, PixBox *boxes, double *keys,
                        unsigned long long *counters, cudaStream_t st)
 {
-    if (M == 1) return launch_record_prep_m1(vN, tau, opac, rgb, cc, cells, TS, recs, boxes, keys, counters, st);
-    if (M == 4) return launch_record_prep_m4(vN, tau, opac, rgb, cc, cells, TS, recs, boxes, keys, counters, st);
-    return launch_record_prep_m6(vN, tau, opac, rgb, cc, cells, TS, recs, boxes, keys, counters, st);
+    if (M == 1) return launch_record_prep_m1(vN, gp, cc, cells, TS, recs, boxes, keys, counters, st);
+    if (M == 4) return launch_record_prep_m4(vN, gp, cc, cells, TS, recs, boxes, keys, counters, st);
+    return launch_record_prep_m6(vN, gp, cc, cells, TS, recs, boxes, keys, counters, st);
 }
 int launch_render(int M, int TS, const RenderLaunch &a, cudaStream_t st)
 {
     return M == 1 ? launch_render_m1(TS, a, st) : (M == 4 ? launch_render_m4(TS, a, st) : launch_render_m6(TS, a, st));
 }
-int launch_record_prep64(int M, const double *vN, const double *tau, const float *opac, const float *rgb,
+int launch_record_prep64(int M, const double *vN, const void *gp,
                          const CallConst &cc, const void *cells, int TS, double *recs, PixBox *boxes, double *keys,
                          unsigned long long *counters, cudaStream_t st)
 {
-    if (M == 1) return launch_record_prep64_m1(vN, tau, opac, rgb, cc, cells, TS, recs, boxes, keys, counters, st);
-    if (M == 4) return launch_record_prep64_m4(vN, tau, opac, rgb, cc, cells, TS, recs, boxes, keys, counters, st);
-    return launch_record_prep64_m6(vN, tau, opac, rgb, cc, cells, TS, recs, boxes, keys, counters, st);
+    if (M == 1) return launch_record_prep64_m1(vN, gp, cc, cells, TS, recs, boxes, keys, counters, st);
+    if (M == 4) return launch_record_prep64_m4(vN, gp, cc, cells, TS, recs, boxes, keys, counters, st);
+    return launch_record_prep64_m6(vN, gp, cc, cells, TS, recs, boxes, keys, counters, st);
 }
 int launch_record_build(int M, const double *vN, const CallConst &cc, const void *cells, int64_t n_gauss,
                         const uint32_t *work, const uint32_t *count, float *recs, unsigned long long *counters,
@@ -283,7 +283,15 @@ int ar_scene_create(const float *uw3, const float *logscale3, const float *quat4
             ar_scene_destroy(s);
             return fail(AR_ENOMEM, "scene allocation failed");
         }
-        if (launch_scene_prep(s->ls, s->quat, s->opac, n, s->Mw, s->tau, 0) || cudaDeviceSynchronize() != cudaSuccess) {
+        if (cudaMalloc(&s->gp, sizeof(GParam) * n) != cudaSuccess) {
+            cudaGetLastError();
+            ar_scene_destroy(s);
+            return fail(AR_ENOMEM, "scene allocation failed");
+        }
+        s->uw_lo = s->uw;
+        s->uw_hi = s->uw;
+        if (launch_scene_prep(s->ls, s->quat, s->opac, n, s->Mw, s->tau, 0) ||
+            launch_gparam(s->opac, s->opac, s->rgb, s->rgb, n, s->gp, 0) || cudaDeviceSynchronize() != cudaSuccess) {
             const char *m = cudaGetErrorString(cudaGetLastError());
             ar_scene_destroy(s);
             return fail(AR_EDEVICE, "scene preprocessing failed: %s", m);
@@ -293,12 +301,67 @@ int ar_scene_create(const float *uw3, const float *logscale3, const float *quat4
     return AR_OK;
 }
 
+int ar_scene_set_boxes(ar_scene *s, const float *uw_lo3, const float *uw_hi3, const float *opacity_lo,
+                       const float *opacity_hi, const float *rgb_lo3, const float *rgb_hi3)
+{
+    if (!s) return fail(AR_EINVAL, "scene is null");
+    if (!uw_lo3 != !uw_hi3 || !opacity_lo != !opacity_hi || !rgb_lo3 != !rgb_hi3)
+        return fail(AR_EINVAL, "a box needs both its lower and its upper array");
+    const int64_t n = s->n;
+    if (n == 0) return AR_OK;
+    CK(cudaSetDevice(s->device));
+    // host copies of the nominal values fill the parameters without a box
+    std::vector<float> nom_uw((size_t)3 * n), nom_o((size_t)n), nom_c((size_t)3 * n);
+    CK(cudaMemcpy(nom_uw.data(), s->uw, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(nom_o.data(), s->opac, sizeof(float) * n, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(nom_c.data(), s->rgb, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost));
+    // layout of the box buffer: uw_lo 3n, uw_hi 3n, o_lo n, o_hi n, c_lo 3n, c_hi 3n
+    std::vector<float> h((size_t)14 * n);
+    float *ul = h.data(), *uh = ul + 3 * n, *ol = uh + 3 * n, *oh = ol + n, *cl = oh + n, *ch = cl + 3 * n;
+    for (int64_t i = 0; i < 3 * n; ++i) {
+        ul[i] = uw_lo3 ? uw_lo3[i] : nom_uw[i];
+        uh[i] = uw_hi3 ? uw_hi3[i] : nom_uw[i];
+        cl[i] = rgb_lo3 ? rgb_lo3[i] : nom_c[i];
+        ch[i] = rgb_hi3 ? rgb_hi3[i] : nom_c[i];
+        if (!std::isfinite(ul[i]) || !std::isfinite(uh[i]) || !(ul[i] <= uh[i]))
+            return fail(AR_EINVAL, "mean box %lld: not finite or lo > hi", (long long)(i / 3));
+        if (!(cl[i] >= 0.f && cl[i] <= ch[i] && ch[i] <= 1.f))
+            return fail(AR_EINVAL, "colour box %lld outside 0 <= lo <= hi <= 1", (long long)(i / 3));
+    }
+    double omax = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        ol[i] = opacity_lo ? opacity_lo[i] : nom_o[i];
+        oh[i] = opacity_hi ? opacity_hi[i] : nom_o[i];
+        if (!(ol[i] >= 0.f && ol[i] <= oh[i] && oh[i] < 1.f))
+            return fail(AR_EINVAL, "opacity box %lld outside 0 <= lo <= hi < 1", (long long)i);
+        omax = std::fmax(omax, (double)oh[i]);
+    }
+    float *buf = nullptr;
+    if (cudaMalloc(&buf, sizeof(float) * h.size()) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(AR_ENOMEM, "box allocation failed");
+    }
+    if (cudaMemcpy(buf, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        launch_gparam(buf + 6 * n, buf + 7 * n, buf + 8 * n, buf + 11 * n, n, s->gp, 0) ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+        const char *m = cudaGetErrorString(cudaGetLastError());
+        cudaFree(buf);
+        return fail(AR_EDEVICE, "box upload failed: %s", m);
+    }
+    if (s->boxbuf) cudaFree(s->boxbuf);
+    s->boxbuf = buf;
+    s->uw_lo = buf;
+    s->uw_hi = buf + 3 * n;
+    s->k_open = (float)(1.0 / (1.0 - omax)) * 1.0001f + 1e-6f;
+    return AR_OK;
+}
+
 int ar_scene_destroy(ar_scene *s)
 {
     if (!s) return fail(AR_EINVAL, "scene is null");
     cudaSetDevice(s->device);
     cudaDeviceSynchronize();
-    void *ptrs[] = {s->uw, s->ls, s->quat, s->opac, s->rgb, s->Mw, s->tau};
+    void *ptrs[] = {s->uw, s->ls, s->quat, s->opac, s->rgb, s->Mw, s->tau, s->gp, s->boxbuf};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     s->ws.release();
@@ -435,10 +498,10 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
     if (profiling) CK(cudaEventRecord(ev[0], st));
     CK(cudaMemsetAsync(ws.counters.p, 0, sizeof(unsigned long long) * 8, st));
     if (launch_cell_prep(M, d_lo, d_hi, cc, ws.cells.p, st)) return fail(AR_EDEVICE, "cell_prep launch");
-    const int rp = plain ? launch_record_prep64(M, ws.vN.as<double>(), s->tau, s->opac, s->rgb, cc, ws.cells.p, TS,
+    const int rp = plain ? launch_record_prep64(M, ws.vN.as<double>(), s->gp, cc, ws.cells.p, TS,
                                                 ws.recs.as<double>(), ws.boxes.as<PixBox>(), ws.keys.as<double>(),
                                                 ws.counters.as<unsigned long long>(), st)
-                         : launch_record_prep(M, ws.vN.as<double>(), s->tau, s->opac, s->rgb, cc, ws.cells.p, TS,
+                         : launch_record_prep(M, ws.vN.as<double>(), s->gp, cc, ws.cells.p, TS,
                                               ws.recs.as<float>(), ws.boxes.as<PixBox>(), ws.keys.as<double>(),
                                               ws.counters.as<unsigned long long>(), st);
     if (rp) return fail(AR_EDEVICE, "record_prep launch: %s", cudaGetErrorString(cudaGetLastError()));
@@ -681,7 +744,7 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
         ws.evs.push_back(e);
     }
     RK(ws.cells_lohi.ensure(sizeof(double) * 12 * n_cells));
-    RK(ws.vN.ensure(sizeof(double) * 12 * s->n));
+    RK(ws.vN.ensure(sizeof(double) * VN_STRIDE * s->n));
     RK(ws.counters.ensure(sizeof(unsigned long long) * (8 + kCountersPerBatch * n_batches)));
     {
         std::vector<double> lohi((size_t)12 * n_cells);
@@ -699,7 +762,7 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
     CK(cudaMemsetAsync(ws.whist.p, 0, sizeof(uint32_t) * 256, st));
     CK(cudaMemsetAsync(ws.counters.as<unsigned long long>() + 8, 0, sizeof(unsigned long long) * kCountersPerBatch * n_batches, st));
     int launches = 0;
-    if (launch_pose_prep(s->uw, s->Mw, s->n, cc, ws.vN.as<double>(), st)) return fail(AR_EDEVICE, "pose_prep launch");
+    if (launch_pose_prep(s->uw_lo, s->uw_hi, s->Mw, s->n, cc, ws.vN.as<double>(), st)) return fail(AR_EDEVICE, "pose_prep launch");
     ++launches;
     for (int b = 0; b < n_batches; ++b) {
         const int c0 = (int)(b * per_batch);
@@ -895,7 +958,7 @@ int ar_debug_records(ar_scene *s, const ar_intrinsics *in, const ar_nominal_pose
     const int64_t n = s->n;
     cudaStream_t st = 0;
     RK(ws.cells_lohi.ensure(sizeof(double) * 2 * MAXV));
-    RK(ws.vN.ensure(sizeof(double) * 12 * n));
+    RK(ws.vN.ensure(sizeof(double) * VN_STRIDE * n));
     RK(ws.cells.ensure(cell_data_bytes(M)));
     RK(ws.recs.ensure(sizeof(float) * rec_width(M) * n));
     RK(ws.boxes.ensure(sizeof(PixBox) * n));
@@ -906,9 +969,9 @@ int ar_debug_records(ar_scene *s, const ar_intrinsics *in, const ar_nominal_pose
     CK(cudaMemcpy(ws.cells_lohi.p, lohi, sizeof lohi, cudaMemcpyHostToDevice));
     CK(cudaMemset(ws.counters.p, 0, sizeof(unsigned long long) * 8));
     const double *d_lo = ws.cells_lohi.as<double>(), *d_hi = d_lo + MAXV;
-    if (launch_pose_prep(s->uw, s->Mw, s->n, cc, ws.vN.as<double>(), st) ||
+    if (launch_pose_prep(s->uw_lo, s->uw_hi, s->Mw, s->n, cc, ws.vN.as<double>(), st) ||
         launch_cell_prep(M, d_lo, d_hi, cc, ws.cells.p, st) ||
-        launch_record_prep(M, ws.vN.as<double>(), s->tau, s->opac, s->rgb, cc, ws.cells.p, 16, ws.recs.as<float>(),
+        launch_record_prep(M, ws.vN.as<double>(), s->gp, cc, ws.cells.p, 16, ws.recs.as<float>(),
                            ws.boxes.as<PixBox>(), ws.keys.as<double>(), ws.counters.as<unsigned long long>(), st))
         return fail(AR_EDEVICE, "record prep launch: %s", cudaGetErrorString(cudaGetLastError()));
     const int w = rec_width(M);

@@ -69,10 +69,12 @@ template <int M> struct Rec {
     static constexpr int S = 0, RX = SBW, RY = 2 * SBW;
     static constexpr int WS = (M + 5 + 3) / 4 * 4;   // c[M], klo, khi, vlo, vhi, r (padded)
     static constexpr int W0 = 3 * SBW;               // W_rc at W0 + (3 r + c) WS
-    static constexpr int SC = W0 + 6 * WS;           // o, tau_dn, tau_up, c0, c1, c2, flags, mu_x, mu_y, gap_s
+    // scalars: o_hi, tau_dn, tau_up, c_lo[3], flags, mu_x, mu_y, gap_s, o_lo, c_hi[3]
+    // (the opacity and colour boxes of the scene parameters; lo = hi without boxes)
+    static constexpr int SC = W0 + 6 * WS;
     static constexpr int O = SC, TAU_DN = SC + 1, TAU_UP = SC + 2, COL = SC + 3, FLAGS = SC + 6;
-    static constexpr int MU_X = SC + 7, MU_Y = SC + 8, GAP_S = SC + 9;
-    static constexpr int SCW = 12;
+    static constexpr int MU_X = SC + 7, MU_Y = SC + 8, GAP_S = SC + 9, O_LO = SC + 10, COL_HI = SC + 11;
+    static constexpr int SCW = 16;
     static constexpr int WIDTH = SC + SCW;            // a multiple of 4 elements
 };
 
@@ -83,6 +85,20 @@ constexpr uint32_t F_OPEN = 4u;      // depth-key interval has positive width
 constexpr uint32_t F_SPLIT = 8u;     // MatrixInv held only after splitting the cell (constant Conic)
 constexpr uint32_t F_SPLIT_PENDING = 16u;  // returned by a deferred record build, never stored
 constexpr uint32_t F_KHIGH_PENDING = 32u;  // likewise, for a Taylor order above the default
+
+// doubles per Gaussian of the per-call array vN: v = R_wc (uw - t) as an
+// interval over the mean's box (lower ends 3, upper ends 3), then N = R_wc Mw
+constexpr int VN_STRIDE = 15;
+
+// Per-Gaussian scene parameters of the abstract render as boxes (Sec. 4.5):
+// opacity o in [o_lo, o_hi], the cutoff exponent tau = 2 ln(255 o) at both
+// ends (-inf below 1/255), and each colour channel in [c_lo, c_hi]; lo = hi
+// without boxes.  (The mean's box enters through v; see pose_prep_kernel.)
+struct GParam {
+    double tau_lo, tau_hi;
+    float o_lo, o_hi;
+    float c_lo[3], c_hi[3];
+};
 
 // Pixel box of a (Gaussian, cell) pair: x0 < 0 marks "contributes nowhere".
 struct PixBox {

@@ -78,7 +78,13 @@ struct ar_scene {
     int64_t n = 0;
     float *uw = nullptr, *ls = nullptr, *quat = nullptr, *opac = nullptr, *rgb = nullptr;
     double *Mw = nullptr, *tau = nullptr;
-    float k_open = 1.f;  // 1 / (1 - largest opacity), rounded up (bounds skipped lower-sum terms)
+    // scene-parameter boxes (Sec. 4.5) of the abstract render: the mean's box
+    // (both pointers at uw without boxes) and the opacity and colour boxes as
+    // GParam; boxbuf owns the box arrays once they are set
+    const float *uw_lo = nullptr, *uw_hi = nullptr;
+    void *gp = nullptr;
+    float *boxbuf = nullptr;
+    float k_open = 1.f;  // 1 / (1 - largest upper opacity), rounded up (bounds skipped lower-sum terms)
     int64_t ws_limit = int64_t(64) << 30;  // workspace limit that sizes the cell batches
     ar::Workspace ws;
     bool profiling = false;

@@ -33,11 +33,11 @@ struct RenderLaunch {
 size_t cell_data_bytes(int M);
 int rec_width(int M);
 int launch_cell_prep(int M, const double *lo, const double *hi, const CallConst &cc, void *cells, cudaStream_t st);
-int launch_record_prep(int M, const double *vN, const double *tau, const float *opac, const float *rgb,
+int launch_record_prep(int M, const double *vN, const void *gp,
                        const CallConst &cc, const void *cells, int TS, float *recs, PixBox *boxes, double *keys,
                        unsigned long long *counters, cudaStream_t st);
 int launch_render(int M, int TS, const RenderLaunch &a, cudaStream_t st);
-int launch_record_prep64(int M, const double *vN, const double *tau, const float *opac, const float *rgb,
+int launch_record_prep64(int M, const double *vN, const void *gp,
                          const CallConst &cc, const void *cells, int TS, double *recs, PixBox *boxes, double *keys,
                          unsigned long long *counters, cudaStream_t st);
 int launch_render_plain(int M, int TS, const RenderLaunch &a, cudaStream_t st);
@@ -61,7 +61,9 @@ int launch_concrete_render(const double *recs, const PixBox *boxes, const uint32
                            int ntx, int n_tiles, float *out, cudaStream_t st);
 int launch_scene_prep(const float *logscale, const float *quat, const float *opacity, int64_t n, double *Mw,
                       double *tau, cudaStream_t st);
-int launch_pose_prep(const float *uw, const double *Mw, int64_t n, const CallConst &cc, double *vN,
-                     cudaStream_t st);
+int launch_pose_prep(const float *uw_lo, const float *uw_hi, const double *Mw, int64_t n, const CallConst &cc,
+                     double *vN, cudaStream_t st);
+int launch_gparam(const float *o_lo, const float *o_hi, const float *c_lo, const float *c_hi, int64_t n, void *gp,
+                  cudaStream_t st);
 
 }  // namespace ar

@@ -135,7 +135,7 @@ int ar_render_abstract_noalloc(ar_scene *s, const ar_intrinsics *in, const ar_no
     Arena A{base};
     double *d_lo = A.take<double>((size_t)MAXV * n_cells), *d_hi = A.take<double>((size_t)MAXV * n_cells);
     void *cellbuf = A.take<unsigned char>(cell_data_bytes(M) * n_cells);
-    double *vN = A.take<double>(12 * (size_t)s->n);
+    double *vN = A.take<double>((size_t)VN_STRIDE * s->n);
     float *recs = A.take<float>((size_t)rec_width(M) * n_pairs);
     PixBox *boxes = A.take<PixBox>(n_pairs);
     double *keys = A.take<double>(2 * n_pairs);
@@ -156,8 +156,8 @@ int ar_render_abstract_noalloc(ar_scene *s, const ar_intrinsics *in, const ar_no
                             n_cells, cudaMemcpyHostToDevice, st));
     // the counters keep the previous call's values: clear them
     NA_CK(cudaMemsetAsync(counters, 0, 8 * sizeof(unsigned long long), st));
-    if (launch_pose_prep(s->uw, s->Mw, s->n, cc, vN, st) || launch_cell_prep(M, d_lo, d_hi, cc, cellbuf, st) ||
-        launch_record_prep(M, vN, s->tau, s->opac, s->rgb, cc, cellbuf, TS, recs, boxes, keys, counters, st))
+    if (launch_pose_prep(s->uw_lo, s->uw_hi, s->Mw, s->n, cc, vN, st) || launch_cell_prep(M, d_lo, d_hi, cc, cellbuf, st) ||
+        launch_record_prep(M, vN, s->gp, cc, cellbuf, TS, recs, boxes, keys, counters, st))
         return set_last_error(AR_EDEVICE, cudaGetErrorString(cudaGetLastError()));
     unsigned long long hc[4] = {0, 0, 0, 0};
     NA_CK(cudaMemcpyAsync(hc, counters, sizeof hc, cudaMemcpyDeviceToHost, st));

@@ -21,7 +21,7 @@ int AR_CAT(launch_cell_prep_m, AR_M)(const double *lo, const double *hi, const C
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 
-int AR_CAT(launch_record_prep_m, AR_M)(const double *vN, const double *tau, const float *opac, const float *rgb,
+int AR_CAT(launch_record_prep_m, AR_M)(const double *vN, const void *gp,
                                        const CallConst &cc, const void *cells, int TS, float *recs,
                                        PixBox *boxes, double *keys, unsigned long long *counters,
                                        cudaStream_t st)
@@ -29,19 +29,19 @@ int AR_CAT(launch_record_prep_m, AR_M)(const double *vN, const double *tau, cons
     const int T = 128;
     dim3 grid((unsigned)((cc.n_gauss + T - 1) / T), (unsigned)cc.n_cells);
     // decision part only: the value parts are built by the renderer on demand
-    record_prep_kernel<AR_M, float, false><<<grid, T, 0, st>>>(vN, tau, opac, rgb, cc, (const CellData<AR_M> *)cells,
+    record_prep_kernel<AR_M, float, false><<<grid, T, 0, st>>>(vN, (const GParam *)gp, cc, (const CellData<AR_M> *)cells,
                                                                TS, recs, boxes, keys, counters);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 
-int AR_CAT(launch_record_prep64_m, AR_M)(const double *vN, const double *tau, const float *opac, const float *rgb,
+int AR_CAT(launch_record_prep64_m, AR_M)(const double *vN, const void *gp,
                                          const CallConst &cc, const void *cells, int TS, double *recs,
                                          PixBox *boxes, double *keys, unsigned long long *counters,
                                          cudaStream_t st)
 {
     const int T = 128;
     dim3 grid((unsigned)((cc.n_gauss + T - 1) / T), (unsigned)cc.n_cells);
-    record_prep_kernel<AR_M, double><<<grid, T, 0, st>>>(vN, tau, opac, rgb, cc, (const CellData<AR_M> *)cells,
+    record_prep_kernel<AR_M, double><<<grid, T, 0, st>>>(vN, (const GParam *)gp, cc, (const CellData<AR_M> *)cells,
                                                          TS, recs, boxes, keys, counters);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }

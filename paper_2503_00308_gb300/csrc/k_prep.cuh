@@ -290,14 +290,14 @@ struct PrepCount {
 enum { SCREEN_DROP = 0, SCREEN_KEEP = 1, SCREEN_UNDECIDED = 2 };
 
 // The definition, in FP64 with round-to-nearest steps in a fixed order.
-static __device__ __noinline__ int screen_fp64(const double (*rd_int)[2], const double (*s_int)[2], const double *v,
-                                        const double *N, double dlo, double dhi, double tau, const CallConst &cc,
-                                        PixBox &box, double *mu_px, bool &straddle)
+static __device__ __noinline__ int screen_fp64(const double (*rd_int)[2], const double (*s_int)[2], const double *vl,
+                                               const double *vh, const double *N, double dlo, double dhi, double tau,
+                                               const CallConst &cc, PixBox &box, double *mu_px, bool &straddle)
 {
     const double nearp = (double)cc.near_plane;
     DI Ri[9], vs[3];
     for (int e = 0; e < 9; ++e) Ri[e] = DI{rd_int[e][0], rd_int[e][1]};
-    for (int b = 0; b < 3; ++b) vs[b] = DI{dsub(v[b], s_int[b][1]), dsub(v[b], s_int[b][0])};
+    for (int b = 0; b < 3; ++b) vs[b] = DI{dsub(vl[b], s_int[b][1]), dsub(vh[b], s_int[b][0])};
     const double dl = fmax(dlo, nearp);
     DI D = {dl, dhi};
     DI ucx = di_add(di_add(di_mul(Ri[0], vs[0]), di_mul(Ri[3], vs[1])), di_mul(Ri[6], vs[2]));
@@ -356,9 +356,9 @@ static __device__ __noinline__ int screen_fp64(const double (*rd_int)[2], const 
 // rate is about 1/64 of its FP32 rate, and the FP64 path is then taken by a
 // small fraction of the pairs.
 template <int M>
-__device__ __forceinline__ int screen_fp32(const CellData<M> &cd, const double *v, const double *N, double dlo,
-                                           double dhi, double tau, const CallConst &cc, PixBox &box, double *mu_px,
-                                           bool &straddle)
+__device__ __forceinline__ int screen_fp32(const CellData<M> &cd, const double *vl, const double *vh,
+                                           const double *N, double dlo, double dhi, double tau, const CallConst &cc,
+                                           PixBox &box, double *mu_px, bool &straddle)
 {
     bool ok = true;
     const double nearp = (double)cc.near_plane;
@@ -366,9 +366,8 @@ __device__ __forceinline__ int screen_fp32(const CellData<M> &cd, const double *
     for (int e = 0; e < 9; ++e)
         Ri[e] = EI{E32{cd.rd_int32[e][0][0], cd.rd_int32[e][0][1]}, E32{cd.rd_int32[e][1][0], cd.rd_int32[e][1][1]}};
     for (int b = 0; b < 3; ++b) {
-        const E32 vb = e_of(v[b]);
-        vs[b] = EI{e_chk(e_sub(vb, E32{cd.s_int32[b][1][0], cd.s_int32[b][1][1]}), ok),
-                   e_chk(e_sub(vb, E32{cd.s_int32[b][0][0], cd.s_int32[b][0][1]}), ok)};
+        vs[b] = EI{e_chk(e_sub(e_of(vl[b]), E32{cd.s_int32[b][1][0], cd.s_int32[b][1][1]}), ok),
+                   e_chk(e_sub(e_of(vh[b]), E32{cd.s_int32[b][0][0], cd.s_int32[b][0][1]}), ok)};
     }
     E32 Ne[9];
     for (int i = 0; i < 9; ++i) Ne[i] = e_of(N[i]);
@@ -458,8 +457,7 @@ __device__ __forceinline__ int screen_fp32(const CellData<M> &cd, const double *
 // chain with outward rounding), double for the plain FP64 renderer, where
 // the same steps run with every value kept in FP64.
 template <int M, class RO = float>
-__device__ __forceinline__ int64_t record_decide(const double *__restrict__ vN, const double *__restrict__ tau_g,
-                                                 const float *__restrict__ opacity, const float *__restrict__ rgb,
+__device__ __forceinline__ int64_t record_decide(const double *__restrict__ vN, const GParam *__restrict__ gp,
                                                  const CallConst &cc, const CellData<M> &cd, int cell, int64_t g,
                                                  int TS, RO *__restrict__ recs, PixBox *__restrict__ boxes,
                                                  double *__restrict__ keys, PrepCount &pc)
@@ -468,10 +466,11 @@ __device__ __forceinline__ int64_t record_decide(const double *__restrict__ vN, 
     const int64_t ri = (int64_t)cell * cc.n_gauss + g;
     PixBox box = {-1, -1, -1, -1};
     boxes[ri] = box;
-    const double tau = tau_g[g];
-    if (!(tau >= 0)) return -1;  // o < 1/255: never above the cutoff
-    const double *v = vN + 12 * g;
-    const double *N = v + 3;
+    const GParam P = gp[g];
+    const double tau = P.tau_hi;  // the largest cutoff exponent of the opacity box
+    if (!(tau >= 0)) return -1;   // o < 1/255: never above the cutoff
+    // v as an interval over the mean's box (lo = hi without one), then N
+    const double *vl = vN + VN_STRIDE * g, *vh = vl + 3, *N = vl + 6;
 
     // ---- FP64 decision chain: depth d = sum_b R_delta[b][2] (v_b - s_b) by
     // averaged McCormick products (db_mul, summed by db_add), its bounds, the
@@ -489,8 +488,9 @@ __device__ __forceinline__ int64_t record_decide(const double *__restrict__ vN, 
     for (int b = 0; b < 3; ++b) {
         const int e = 3 * b + 2;
         const double xl = cd.dx[b][0], xh = cd.dx[b][1], xm = cd.dx[b][2];
-        const double yk = dsub(v[b], cd.s[b][M]);  // v_b - s_b: constant
-        double yl = yk, yh = yk;
+        // v_b - s_b: constants of its lower and upper forms
+        const double ylk = dsub(vl[b], cd.s[b][M]), yhk = dsub(vh[b], cd.s[b][M]);
+        double yl = ylk, yh = yhk;
         for (int j = 0; j < n_t; ++j) {
             yl = dsub(yl, fabs(cd.s[b][j]));
             yh = dadd(yh, fabs(cd.s[b][j]));
@@ -502,9 +502,9 @@ __device__ __forceinline__ int64_t record_decide(const double *__restrict__ vN, 
             const double t = dmul(ym, cd.rd_lo[e][j]);
             ddr[j] = b == 0 ? t : dadd(ddr[j], t);
         }
-        double lk = dadd(dmul(ym, ym >= 0 ? cd.rd_lo[e][M] : cd.rd_hi[e][M]), dmul(xm, yk));
+        double lk = dadd(dmul(ym, ym >= 0 ? cd.rd_lo[e][M] : cd.rd_hi[e][M]), dmul(xm, xm >= 0 ? ylk : yhk));
         lk = dsub(lk, dmul(0.5, dadd(dmul(xl, yl), dmul(xh, yh))));
-        double hk = dadd(dmul(ym, ym >= 0 ? cd.rd_hi[e][M] : cd.rd_lo[e][M]), dmul(xm, yk));
+        double hk = dadd(dmul(ym, ym >= 0 ? cd.rd_hi[e][M] : cd.rd_lo[e][M]), dmul(xm, xm >= 0 ? yhk : ylk));
         hk = dsub(hk, dmul(0.5, dadd(dmul(xh, yl), dmul(xl, yh))));
         dlk = b == 0 ? lk : dadd(dlk, lk);
         dhk = b == 0 ? hk : dadd(dhk, hk);
@@ -532,15 +532,22 @@ __device__ __forceinline__ int64_t record_decide(const double *__restrict__ vN, 
     // FP32 enclosures of the FP64 values where they settle every decision,
     // else in FP64 (the same values either way)
     double mu_px[2];
-    int sr = screen_fp32<M>(cd, v, N, dlo, dhi, tau, cc, box, mu_px, straddle);
-    if (sr == SCREEN_UNDECIDED) sr = screen_fp64(cd.rd_int, cd.s_int, v, N, dlo, dhi, tau, cc, box, mu_px, straddle);
+    int sr = screen_fp32<M>(cd, vl, vh, N, dlo, dhi, tau, cc, box, mu_px, straddle);
+    if (sr == SCREEN_UNDECIDED)
+        sr = screen_fp64(cd.rd_int, cd.s_int, vl, vh, N, dlo, dhi, tau, cc, box, mu_px, straddle);
     if (sr == SCREEN_DROP) return -1;
     RO *rec = recs + ri * RL::WIDTH;
     const uint32_t flags = (straddle ? F_STRADDLE : 0u) | (klo < khi ? F_OPEN : 0u);
-    rec[RL::O] = opacity[g];
-    rec_dn(tau, rec[RL::TAU_DN]);
-    rec_up(tau, rec[RL::TAU_UP]);
-    for (int k = 0; k < 3; ++k) rec[RL::COL + k] = rgb[3 * g + k];
+    // the opacity box: the lower forms are cut from tau(o_lo), the upper ones
+    // from tau(o_hi); the colour box: c_lo for the lower sum, c_hi the upper
+    rec[RL::O] = P.o_hi;
+    rec[RL::O_LO] = P.o_lo;
+    rec_dn(P.tau_lo, rec[RL::TAU_DN]);
+    rec_up(P.tau_hi, rec[RL::TAU_UP]);
+    for (int k = 0; k < 3; ++k) {
+        rec[RL::COL + k] = P.c_lo[k];
+        rec[RL::COL_HI + k] = P.c_hi[k];
+    }
     // pixel centre near the projected mean, the expansion point of R = mu S - P
     rec[RL::MU_X] = (RO)mu_px[0];
     rec[RL::MU_Y] = (RO)mu_px[1];
@@ -875,7 +882,8 @@ __device__ __forceinline__ uint32_t record_value(const double *__restrict__ v, f
     typedef SB<M, RO> B;
     typedef SB<M, double> BD;
     typedef SAcc<M, double> AD;
-    const double *N = v + 3;
+    // v: lower ends (3), upper ends (3) over the mean's box, then N (9)
+    const double *N = v + 6;
     bool ok = true;
     // ---- FP64 value chain (directed rounding): uc, S, P, Mc, J, Mp, X, E.
     // These are differences of large, nearly equal terms (S u - P, I - X X0,
@@ -883,12 +891,12 @@ __device__ __forceinline__ uint32_t record_value(const double *__restrict__ v, f
     BD uc64[3];
     {
         double vabs = 1.0;
-        for (int b = 0; b < 3; ++b) vabs += fabs(v[b]);
+        for (int b = 0; b < 3; ++b) vabs += fmax(fabs(v[b]), fabs(v[3 + b]));
         const double ev = __dmul_ru(1e-14, vabs);
         BD vm[3];
         for (int b = 0; b < 3; ++b) {
             AD p;
-            p.init(__dsub_rd(v[b], ev), __dadd_ru(v[b], ev));
+            p.init(__dsub_rd(v[b], ev), __dadd_ru(v[3 + b], ev));
             p.term(-1.0, cd.s64[b]);
             vm[b] = p.result();
         }
@@ -1008,8 +1016,8 @@ __device__ __forceinline__ uint32_t record_value(const double *__restrict__ v, f
 // MatrixInv needed input splitting.
 template <int M, class RO = float, bool VALUE = true>
 __global__ void __launch_bounds__(128) record_prep_kernel(
-    const double *__restrict__ vN, const double *__restrict__ tau_g, const float *__restrict__ opacity,
-    const float *__restrict__ rgb, CallConst cc, const CellData<M> *__restrict__ cells, int TS,
+    const double *__restrict__ vN, const GParam *__restrict__ gp, CallConst cc,
+    const CellData<M> *__restrict__ cells, int TS,
     RO *__restrict__ recs, PixBox *__restrict__ boxes, double *__restrict__ keys,
     unsigned long long *__restrict__ counters)
 {
@@ -1017,11 +1025,10 @@ __global__ void __launch_bounds__(128) record_prep_kernel(
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     PrepCount pc = {0, 0, 0, 0, 0};
     if (g < cc.n_gauss) {
-        const int64_t fl = record_decide<M, RO>(vN, tau_g, opacity, rgb, cc, cells[cell], cell, g, TS, recs, boxes,
-                                                keys, pc);
+        const int64_t fl = record_decide<M, RO>(vN, gp, cc, cells[cell], cell, g, TS, recs, boxes, keys, pc);
         if (VALUE && fl >= 0) {
             RO *rec = recs + ((int64_t)cell * cc.n_gauss + g) * Rec<M>::WIDTH;
-            const uint32_t f = record_value<M, RO>(vN + 12 * g, cc.fx, cc.fy, cc.cx, cc.cy, cells[cell], rec[Rec<M>::MU_X],
+            const uint32_t f = record_value<M, RO>(vN + VN_STRIDE * g, cc.fx, cc.fy, cc.cx, cc.cy, cells[cell], rec[Rec<M>::MU_X],
                                                    rec[Rec<M>::MU_Y], (uint32_t)fl, rec);
             pc.fallback = (f & F_FALLBACK) ? 1u : 0u;
             pc.split = (f & F_SPLIT) ? 1u : 0u;
@@ -1066,7 +1073,7 @@ __global__ void __launch_bounds__(128) record_build_kernel(
         const int cell = (int)(p / (uint64_t)n_gauss);
         const int64_t g = (int64_t)p - (int64_t)cell * n_gauss;
         float *rec = recs + (size_t)p * RL::WIDTH;
-        const uint32_t f = record_value<M, float, SPLIT_DEFER>(vN + 12 * g, fx, fy, cx, cy, cells[cell],
+        const uint32_t f = record_value<M, float, SPLIT_DEFER>(vN + VN_STRIDE * g, fx, fy, cx, cy, cells[cell],
                                                               rec[RL::MU_X], rec[RL::MU_Y],
                                                               __float_as_uint(rec[RL::FLAGS]), rec);
         if (f & F_SPLIT_PENDING) split_list[atomicAdd(split_count, 1u)] = p;
@@ -1110,7 +1117,7 @@ __global__ void __launch_bounds__(128) split_build_kernel(
         float *rec = recs + (size_t)p * RL::WIDTH;
         const uint32_t f0 = __float_as_uint(rec[RL::FLAGS]);
         __syncwarp();
-        const uint32_t f = record_value<M, float, SPLIT_WARP>(vN + 12 * g, fx, fy, cx, cy, cells[cell],
+        const uint32_t f = record_value<M, float, SPLIT_WARP>(vN + VN_STRIDE * g, fx, fy, cx, cy, cells[cell],
                                                              rec[RL::MU_X], rec[RL::MU_Y], f0, rec, pieces[w]);
         if (lane == 0) {
             if (f & F_FALLBACK) ++fb;
@@ -1140,7 +1147,7 @@ __global__ void __launch_bounds__(128) khigh_build_kernel(
         const int cell = (int)(p / (uint64_t)n_gauss);
         const int64_t g = (int64_t)p - (int64_t)cell * n_gauss;
         float *rec = recs + (size_t)p * RL::WIDTH;
-        const uint32_t f = record_value<M, float>(vN + 12 * g, fx, fy, cx, cy, cells[cell], rec[RL::MU_X],
+        const uint32_t f = record_value<M, float>(vN + VN_STRIDE * g, fx, fy, cx, cy, cells[cell], rec[RL::MU_X],
                                                   rec[RL::MU_Y], __float_as_uint(rec[RL::FLAGS]), rec);
         if (f & F_FALLBACK) ++fb;
         if (f & F_SPLIT) ++sp;

@@ -86,7 +86,8 @@ __device__ __forceinline__ void pixel_alpha(const R *__restrict__ r, R ux, R uy,
 {
     using RL = Rec<M>;
     using N = Num<R>;
-    const R o = r[RL::O];
+    // opacity box [o_lo, o]: o_lo scales the lower forms, o the upper ones
+    const R o = r[RL::O], o_lo = r[RL::O_LO];
     const uint32_t flags = rec_flags(r, RL::FLAGS);
     if (flags & F_FALLBACK) {
 #pragma unroll
@@ -143,7 +144,7 @@ __device__ __forceinline__ void pixel_alpha(const R *__restrict__ r, R ux, R uy,
     const R el_dn = N::exp_dn(xl), el_up = N::exp_up(xl), eu_up = N::exp_up(xu);
     // lower: o e(xl) (1 + x - xl) with x >= -m.hi/2
     Acc<M, R, true> la;
-    const R e1 = N::mul_rd(o, el_dn);
+    const R e1 = N::mul_rd(o_lo, el_dn);
     la.init(N::mul_rd(e1, N::sub_rd(R(1), xl)));
     la.term_ck(R(-0.5) * e1, m.c, m.khi, m.r);
     LF<M, R> La = la.result();
@@ -526,9 +527,11 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
                     }
                 }
                 c_rec = ev.rec;
+                // colour box: c_lo in the lower sum, c_hi in the upper one
                 const float col[3] = {r[RL::COL], r[RL::COL + 1], r[RL::COL + 2]};
+                const float colh[3] = {r[RL::COL_HI], r[RL::COL_HI + 1], r[RL::COL_HI + 2]};
                 if (lower) {
-                    hi.add(PB, col, cache.U, cache.rU);
+                    hi.add(PB, colh, cache.U, cache.rU);
                     PAp = __fmul_rd(PAp, __fsub_rd(1.f, cache.ahi));
                     open_w = __fadd_ru(open_w, open_ratio_up(cache.ahi));
                     const int k = (int)(head % RING);
@@ -652,8 +655,9 @@ __global__ void __launch_bounds__(TS *TS) render_plain_kernel(
                 const double *r = s_rec[e];
                 pixel_alpha<M, double>(r, ux, uy, a);
                 const double col[3] = {r[RL::COL], r[RL::COL + 1], r[RL::COL + 2]};
+                const double colh[3] = {r[RL::COL_HI], r[RL::COL_HI + 1], r[RL::COL_HI + 2]};
                 if (!(ev.bits & 1u)) {
-                    hi.add(PB, col, a.U, a.rU);
+                    hi.add(PB, colh, a.U, a.rU);
                     PAp = N::mul_rd(PAp, N::sub_rd(1.0, a.ahi));
                 } else {
                     double T = PA;

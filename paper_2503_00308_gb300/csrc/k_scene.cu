@@ -21,19 +21,47 @@ __global__ void scene_prep_kernel(const float *__restrict__ logscale, const floa
     tau[i] = (o > 0) ? dmul(2.0, log(dmul(255.0, o))) : -INFINITY;
 }
 
-// v = R_wc (uw - t), N = R_wc Mw for the call's nominal camera.
-__global__ void pose_prep_kernel(const float *__restrict__ uw, const double *__restrict__ Mw, int64_t n,
-                                 CallConst cc, double *__restrict__ vN)
+// v = R_wc (uw - t) as an interval over the mean's box [uw_lo, uw_hi] (each
+// product at the end of the box its sign selects; lo = hi without a box),
+// and N = R_wc Mw, for the call's nominal camera: VN_STRIDE doubles each.
+__global__ void pose_prep_kernel(const float *__restrict__ uw_lo, const float *__restrict__ uw_hi,
+                                 const double *__restrict__ Mw, int64_t n, CallConst cc, double *__restrict__ vN)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double *o = vN + 12 * i;
+    double *o = vN + VN_STRIDE * i;
     for (int a = 0; a < 3; ++a) {
-        double s = 0;
-        for (int b = 0; b < 3; ++b) s = dadd(s, dmul(cc.R0[3 * a + b], dsub((double)uw[3 * i + b], cc.t0[b])));
-        o[a] = s;
+        double sl = 0, sh = 0;
+        for (int b = 0; b < 3; ++b) {
+            const double r = cc.R0[3 * a + b];
+            const double dl = dsub((double)uw_lo[3 * i + b], cc.t0[b]), dh = dsub((double)uw_hi[3 * i + b], cc.t0[b]);
+            sl = dadd(sl, dmul(r, r >= 0 ? dl : dh));
+            sh = dadd(sh, dmul(r, r >= 0 ? dh : dl));
+        }
+        o[a] = sl;
+        o[3 + a] = sh;
     }
-    mat3(cc.R0, Mw + 9 * i, o + 3);
+    mat3(cc.R0, Mw + 9 * i, o + 6);
+}
+
+// The GParam of every Gaussian from its opacity and colour boxes.
+__global__ void gparam_kernel(const float *__restrict__ o_lo, const float *__restrict__ o_hi,
+                              const float *__restrict__ c_lo, const float *__restrict__ c_hi, int64_t n,
+                              GParam *__restrict__ gp)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    GParam P;
+    P.o_lo = o_lo[i];
+    P.o_hi = o_hi[i];
+    const double a = P.o_lo, b = P.o_hi;
+    P.tau_lo = (a > 0) ? dmul(2.0, log(dmul(255.0, a))) : -INFINITY;
+    P.tau_hi = (b > 0) ? dmul(2.0, log(dmul(255.0, b))) : -INFINITY;
+    for (int k = 0; k < 3; ++k) {
+        P.c_lo[k] = c_lo[3 * i + k];
+        P.c_hi[k] = c_hi[3 * i + k];
+    }
+    gp[i] = P;
 }
 
 int launch_scene_prep(const float *logscale, const float *quat, const float *opacity, int64_t n, double *Mw,
@@ -45,11 +73,21 @@ int launch_scene_prep(const float *logscale, const float *quat, const float *opa
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 
-int launch_pose_prep(const float *uw, const double *Mw, int64_t n, const CallConst &cc, double *vN, cudaStream_t st)
+int launch_pose_prep(const float *uw_lo, const float *uw_hi, const double *Mw, int64_t n, const CallConst &cc,
+                     double *vN, cudaStream_t st)
 {
     if (n <= 0) return 0;
     const int T = 128;
-    pose_prep_kernel<<<(unsigned)((n + T - 1) / T), T, 0, st>>>(uw, Mw, n, cc, vN);
+    pose_prep_kernel<<<(unsigned)((n + T - 1) / T), T, 0, st>>>(uw_lo, uw_hi, Mw, n, cc, vN);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+int launch_gparam(const float *o_lo, const float *o_hi, const float *c_lo, const float *c_hi, int64_t n, void *gp,
+                  cudaStream_t st)
+{
+    if (n <= 0) return 0;
+    const int T = 128;
+    gparam_kernel<<<(unsigned)((n + T - 1) / T), T, 0, st>>>(o_lo, o_hi, c_lo, c_hi, n, (GParam *)gp);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 
