@@ -48,6 +48,8 @@ def _load():
         lib.orc_render_concrete.restype = I
         lib.orc_render_abstract.argtypes = [P, P, P, P, P, I64, P, P, P, P, P, I, I, I, I, P, P, P, P]
         lib.orc_render_abstract.restype = I
+        lib.orc_render_abstract_sort.argtypes = [P, P, P, P, P, I64, P, P, P, P, P, I, I, I, I, P, P]
+        lib.orc_render_abstract_sort.restype = I
         lib.orc_records.argtypes = [P, P, P, P, P, I64, P, P, P, P, P, P]
         lib.orc_records.restype = I
         lib.orc_matrixinv_interval.argtypes = [P, P, I, I, P, P, P]
@@ -151,6 +153,26 @@ def render_abstract(scene, cam, cell_lo, cell_hi, window=None, with_cond=False):
     if st:
         raise RuntimeError("oracle abstract render failed")
     return (lo, hi, frag, cond) if with_cond else (lo, hi, frag)
+
+
+def render_abstract_sort(scene, cam, cell_lo, cell_hi, window=None):
+    """Bounds of one pose cell with the abstract BlendSort of Example 2 (rank
+    ranges from the depth-key intervals, interval hulls per rank) in place of
+    BlendInd.  Returns (lo, hi), [H, W, 3] (NaN outside window)."""
+    lib = _load()
+    s = _scene_args(scene)
+    intr, R0, t0 = _cam_args(cam)
+    lo = np.full((cam.height, cam.width, 3), np.nan)
+    hi = np.full((cam.height, cam.width, 3), np.nan)
+    if window is None:
+        window = (0, cam.width - 1, 0, cam.height - 1)
+    px0, px1, py0, py1 = (int(v) for v in window)
+    st = lib.orc_render_abstract_sort(*[_p(a) for a in s], scene.n, _p(intr), _p(R0), _p(t0),
+                                      _p(_d(cell_lo).reshape(6)), _p(_d(cell_hi).reshape(6)),
+                                      px0, px1, py0, py1, _p(lo), _p(hi))
+    if st:
+        raise RuntimeError("oracle abstract render failed")
+    return lo, hi
 
 
 def records(scene, cam, cell_lo, cell_hi) -> dict:

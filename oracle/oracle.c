@@ -881,11 +881,63 @@ static void gaussian_alpha(const grec *g, double ux, double uy, galpha *r)
  * its opacity bounds by half of that times a (a_hi only while m_lo > 0: below
  * that the upper secant ends at x = 0 and a_hi = o), and the pixel colour by
  * at most 2 T_hi times that (d colour / d a_i is at most 2 T_i). */
-int orc_render_abstract(const double *uw, const double *ls, const double *quat, const double *opac,
-                        const double *rgb, int64_t n, const double *intr, const double *R0,
-                        const double *t0, const double *cell_lo, const double *cell_hi,
-                        int px0, int px1, int py0, int py1, double *out_lo, double *out_hi,
-                        uint8_t *fragile, double *cond)
+/* Abstract BlendSort (Algorithm 2 with an abstract Sort), the comparison of
+ * Example 2.  Sort is abstracted by rank ranges: Gaussian i of the pixel has
+ * rank at least the number of Gaussians certainly in front of it (k_hi(j) <
+ * k_lo(i)) and at most the number possibly in front (k_lo(j) < k_hi(i)), so
+ * the Gaussian at rank r is one of those whose range holds r, and a, c a at
+ * rank r lie in the hull of theirs.  Algorithm 2's sum over ranks then takes
+ * the hulls: lower sum of min c_lo a_lo times the product of (1 - max a_hi)
+ * before it, upper sum of max c_hi a_hi times the product of (1 - min a_lo).
+ * Sound for distinct depths (a Gaussian may enter several ranks' hulls: the
+ * index uncertainty Sec. 3.2 removes with BlendInd).  Interval bounds. */
+static void blend_sort_abstract(const grec *G, const int64_t *idx, const galpha *A, int64_t K, double out_lo[3],
+                                double out_hi[3])
+{
+    int64_t *rmin = (int64_t *)malloc(sizeof(int64_t) * (size_t)(K > 0 ? K : 1));
+    int64_t *rmax = (int64_t *)malloc(sizeof(int64_t) * (size_t)(K > 0 ? K : 1));
+    for (int ch = 0; ch < 3; ++ch) { out_lo[ch] = 0; out_hi[ch] = 0; }
+    if (!rmin || !rmax) { free(rmin); free(rmax); for (int ch = 0; ch < 3; ++ch) out_hi[ch] = 1; return; }
+    for (int64_t a = 0; a < K; ++a) {
+        const grec *gi = &G[idx[a]];
+        rmin[a] = 0;
+        rmax[a] = 0;
+        for (int64_t b = 0; b < K; ++b) {
+            if (b == a) continue;
+            const grec *gj = &G[idx[b]];
+            if (gj->khi < gi->klo) ++rmin[a];
+            if (gj->klo < gi->khi) ++rmax[a];
+        }
+    }
+    for (int ch = 0; ch < 3; ++ch) {
+        double Tlo = 1.0, Thi = 1.0, slo = 0.0, shi = 0.0;
+        for (int64_t r = 0; r < K; ++r) {
+            double amin = INFINITY, amax = -INFINITY, calo = INFINITY, cahi = -INFINITY;
+            for (int64_t a = 0; a < K; ++a) {
+                if (r < rmin[a] || r > rmax[a]) continue;
+                const grec *gi = &G[idx[a]];
+                amin = fmin(amin, A[a].alo);
+                amax = fmax(amax, A[a].ahi);
+                calo = fmin(calo, gi->c_lo[ch] * A[a].alo);
+                cahi = fmax(cahi, gi->c_hi[ch] * A[a].ahi);
+            }
+            slo += calo * Tlo;
+            shi += cahi * Thi;
+            Tlo *= 1.0 - amax;
+            Thi *= 1.0 - amin;
+        }
+        out_lo[ch] = clamp01(slo);
+        out_hi[ch] = clamp01(shi);
+    }
+    free(rmin);
+    free(rmax);
+}
+
+static int render_abstract_impl(const double *uw, const double *ls, const double *quat, const double *opac,
+                                const double *rgb, int64_t n, const double *intr, const double *R0,
+                                const double *t0, const double *cell_lo, const double *cell_hi,
+                                int px0, int px1, int py0, int py1, double *out_lo, double *out_hi,
+                                uint8_t *fragile, double *cond, int sort_blend)
 {
     camera cam = make_camera(intr, R0, t0);
     cellforms cf;
@@ -930,6 +982,16 @@ int orc_render_abstract(const double *uw, const double *ls, const double *quat, 
             ++K;
         }
         if (!idx || !A) { free(idx); free(A); continue; }
+        if (sort_blend) {
+            double bl[3], bh[3];
+            blend_sort_abstract(G, idx, A, K, bl, bh);
+            size_t o = 3 * ((size_t)py * cam.W + px);
+            for (int ch = 0; ch < 3; ++ch) { out_lo[o + ch] = bl[ch]; out_hi[o + ch] = bh[ch]; }
+            if (fragile) fragile[(size_t)py * cam.W + px] = (uint8_t)frag;
+            if (cond) cond[(size_t)py * cam.W + px] = 0.0;
+            free(idx); free(A);
+            continue;
+        }
         /* BlendInd with interval Prod: for each i, T_lo over j that may be in
          * front (not certainly behind), T_hi over j certainly in front */
         lf lo[3], hi[3];
@@ -974,6 +1036,26 @@ int orc_render_abstract(const double *uw, const double *ls, const double *quat, 
     }
     free(G);
     return status;
+}
+
+int orc_render_abstract(const double *uw, const double *ls, const double *quat, const double *opac,
+                        const double *rgb, int64_t n, const double *intr, const double *R0,
+                        const double *t0, const double *cell_lo, const double *cell_hi,
+                        int px0, int px1, int py0, int py1, double *out_lo, double *out_hi,
+                        uint8_t *fragile, double *cond)
+{
+    return render_abstract_impl(uw, ls, quat, opac, rgb, n, intr, R0, t0, cell_lo, cell_hi, px0, px1, py0, py1,
+                                out_lo, out_hi, fragile, cond, 0);
+}
+
+/* The same with the abstract BlendSort of blend_sort_abstract (Example 2). */
+int orc_render_abstract_sort(const double *uw, const double *ls, const double *quat, const double *opac,
+                             const double *rgb, int64_t n, const double *intr, const double *R0,
+                             const double *t0, const double *cell_lo, const double *cell_hi,
+                             int px0, int px1, int py0, int py1, double *out_lo, double *out_hi)
+{
+    return render_abstract_impl(uw, ls, quat, opac, rgb, n, intr, R0, t0, cell_lo, cell_hi, px0, px1, py0, py1,
+                                out_lo, out_hi, NULL, NULL, 1);
 }
 
 /* Per-Gaussian record summary for one cell (for tests): valid, straddle,

@@ -633,3 +633,46 @@ def test_boxes_sound_sampled(orc, kind):
         pose = corners[k] if k < 8 else synth.sample_poses(rng, clo, -clo, 1)[0]
         img = orc.render_concrete(s2, cam, pose, "ind")
         assert np.all(img >= lo - 1e-12) and np.all(img <= hi + 1e-12), (kind, k)
+
+
+# ------------------------------------------------ abstract BlendSort (Example 2)
+
+def _three_gaussians():
+    # three Gaussians (red, green, blue) at increasing depths in front of a
+    # camera at the origin, in the manner of Example 2 (its scene is not printed)
+    uw = np.array([[-0.35, 0.1, 3.0], [0.0, -0.1, 3.6], [0.35, 0.05, 4.2]], dtype=np.float32)
+    ls = np.log(np.array([[0.45, 0.35, 0.3], [0.4, 0.5, 0.3], [0.5, 0.4, 0.35]], dtype=np.float32))
+    q = np.array([[1, 0, 0, 0], [0.96, 0.2, 0.1, 0.1], [0.9, -0.1, 0.3, 0.2]], dtype=np.float32)
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    sc = synth.Scene(uw, ls, q, np.array([0.8, 0.75, 0.85], dtype=np.float32), np.eye(3, dtype=np.float32))
+    return sc, synth.look_camera(20, 20, 16.0, centre=(0, 0, 0))
+
+
+def test_abstract_blendsort_point_cell_is_concrete(orc):
+    # at a point cell every rank is exact and every opacity interval a point:
+    # the abstract BlendSort is Algorithm 2 itself
+    sc, cam = _three_gaussians()
+    d = np.array([0.02, -0.01, 0.05, 0.0, 0.0, 0.0])
+    lo, hi = orc.render_abstract_sort(sc, cam, d, d)
+    img = orc.render_concrete(sc, cam, d, "sort")
+    assert np.abs(lo - img).max() < 1e-10 and np.abs(hi - img).max() < 1e-10
+
+
+@pytest.mark.parametrize("h", [0.1, 0.3])
+def test_abstract_blendsort_sound(orc, h):
+    sc, cam = _three_gaussians()
+    clo = np.array([-h, -h, -h, 0.0, 0.0, 0.0])
+    lo, hi = orc.render_abstract_sort(sc, cam, clo, -clo)
+    rng = np.random.default_rng(4)
+    poses = np.concatenate([synth.sample_poses(rng, clo, -clo, 400), _corners(clo, -clo)])
+    for p in poses:
+        img = orc.render_concrete(sc, cam, p, "sort")
+        assert np.all(img >= lo - 1e-12) and np.all(img <= hi + 1e-12)
+    # the same cell with BlendInd is sound too, and both are wider than the samples
+    li, hi2, _ = orc.render_abstract(sc, cam, clo, -clo)
+    assert np.all(li >= 0) and np.all(hi2 <= 1)
+    w = synth.tiny64()
+    slo, shi = orc.render_abstract_sort(w.scene, w.camera, w.cells_lo[0], w.cells_hi[0])
+    worst, nv = orc.check_samples(w.scene, w.camera, synth.sample_poses(rng, w.cells_lo[0], w.cells_hi[0], 2000),
+                                  slo, shi, tol=1e-12)
+    assert nv == 0, worst
