@@ -176,7 +176,15 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(const K *__restr
         key[r] = ok ? kin[i] : (K)0;
         val[r] = ok ? vin[i] : 0u;
         dig[r] = ok ? ((uint32_t)(key[r] >> shift) & (NB - 1u)) : NB;
-        const uint32_t peers = __match_any_sync(0xffffffffu, dig[r]);
+        // lanes with the same digit, by one ballot per digit bit (bit RB marks
+        // the lanes past the end, so that they match only one another)
+        uint32_t peers = 0xffffffffu;
+#pragma unroll
+        for (int b = 0; b <= RB; ++b) {
+            const bool bit = (dig[r] >> b) & 1u;
+            const uint32_t m = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? m : ~m;
+        }
         uint32_t before = 0;
         if (ok) before = wcnt[warp][dig[r]];
         rank[r] = before + __popc(peers & ltmask);
