@@ -132,10 +132,23 @@ __global__ void __launch_bounds__(RS_THREADS) rs_hist_kernel(const K *__restrict
     if (threadIdx.x < NB) h[threadIdx.x] = 0;
     __syncthreads();
     const uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
+    // the counts do not depend on which thread reads which item: each thread
+    // reads RS_ROUNDS consecutive keys with 16-byte loads where the tile is
+    // whole (the arrays are 16-byte aligned), else one by one
+    constexpr int PER16 = 16 / (int)sizeof(K);
+    static_assert(RS_ROUNDS % PER16 == 0, "whole vectors per thread");
+    const uint64_t i0 = base + (uint64_t)threadIdx.x * RS_ROUNDS;
+    K v[RS_ROUNDS];
+    if (base + RS_TILE <= n) {
 #pragma unroll
-    for (int r = 0; r < RS_ROUNDS; ++r) {
-        const uint64_t i = base + (uint64_t)r * RS_THREADS + threadIdx.x;
-        if (i < n) atomicAdd(&h[(uint32_t)(keys[i] >> shift) & (NB - 1u)], 1u);
+        for (int q = 0; q < RS_ROUNDS / PER16; ++q)
+            reinterpret_cast<uint4 *>(v)[q] = reinterpret_cast<const uint4 *>(keys + i0)[q];
+#pragma unroll
+        for (int r = 0; r < RS_ROUNDS; ++r) atomicAdd(&h[(uint32_t)(v[r] >> shift) & (NB - 1u)], 1u);
+    } else {
+#pragma unroll
+        for (int r = 0; r < RS_ROUNDS; ++r)
+            if (i0 + r < n) atomicAdd(&h[(uint32_t)(keys[i0 + r] >> shift) & (NB - 1u)], 1u);
     }
     __syncthreads();
     if (threadIdx.x < NB) hist[(uint64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
