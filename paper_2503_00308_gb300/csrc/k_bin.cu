@@ -182,6 +182,7 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(const K *__restr
     const uint64_t base = blk0 + (uint64_t)warp * (RS_ROUNDS * 32);
     K key[RS_ROUNDS];
     uint32_t val[RS_ROUNDS], dig[RS_ROUNDS], rank[RS_ROUNDS];
+    // all loads first, so that they are in flight together
 #pragma unroll
     for (int r = 0; r < RS_ROUNDS; ++r) {
         const uint64_t i = base + (uint64_t)r * 32 + lane;
@@ -189,6 +190,10 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(const K *__restr
         key[r] = ok ? kin[i] : (K)0;
         val[r] = ok ? vin[i] : 0u;
         dig[r] = ok ? ((uint32_t)(key[r] >> shift) & (NB - 1u)) : NB;
+    }
+#pragma unroll
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        const bool ok = dig[r] < NB;
         // lanes with the same digit, by one ballot per digit bit (bit RB marks
         // the lanes past the end, so that they match only one another)
         uint32_t peers = 0xffffffffu;
