@@ -123,8 +123,20 @@ void exclusive_scan(const uint32_t *in, uint32_t *out, uint64_t n, uint32_t *tmp
 // takes ceil(bits / 8) passes of equal digits, so that no pass spends buckets
 // on bits beyond the key: fewer buckets give longer digit runs per block and
 // fuller store sectors in the scatter.
-template <class K, int RB>
-__global__ void __launch_bounds__(RS_THREADS) rs_hist_kernel(const K *__restrict__ keys, uint32_t n, int shift,
+// digit of an item: key bits [shift, shift + RB), or, with CELL, bits of the
+// cell of the event's pair (val = 2 pair + end, pair = cell n_gauss + g)
+template <class K, int RB, bool CELL>
+__device__ __forceinline__ uint32_t rs_digit(K key, uint32_t val, int shift, uint64_t n_gauss)
+{
+    constexpr uint32_t NB = 1u << RB;
+    if (CELL) return (uint32_t)(((uint64_t)(val >> 1) / n_gauss) >> shift) & (NB - 1u);
+    return (uint32_t)(key >> shift) & (NB - 1u);
+}
+
+template <class K, int RB, bool CELL>
+__global__ void __launch_bounds__(RS_THREADS) rs_hist_kernel(const K *__restrict__ keys,
+                                                             const uint32_t *__restrict__ vals, uint32_t n,
+                                                             int shift, uint64_t n_gauss,
                                                              uint32_t *__restrict__ hist, uint32_t nblocks)
 {
     constexpr uint32_t NB = 1u << RB;
@@ -133,22 +145,38 @@ __global__ void __launch_bounds__(RS_THREADS) rs_hist_kernel(const K *__restrict
     __syncthreads();
     const uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
     // the counts do not depend on which thread reads which item: each thread
-    // reads RS_ROUNDS consecutive keys with 16-byte loads where the tile is
+    // reads RS_ROUNDS consecutive items with 16-byte loads where the tile is
     // whole (the arrays are 16-byte aligned), else one by one
-    constexpr int PER16 = 16 / (int)sizeof(K);
-    static_assert(RS_ROUNDS % PER16 == 0, "whole vectors per thread");
     const uint64_t i0 = base + (uint64_t)threadIdx.x * RS_ROUNDS;
-    K v[RS_ROUNDS];
-    if (base + RS_TILE <= n) {
+    if (CELL) {
+        static_assert(RS_ROUNDS % 4 == 0, "whole vectors per thread");
+        uint32_t v[RS_ROUNDS];
+        if (base + RS_TILE <= n) {
 #pragma unroll
-        for (int q = 0; q < RS_ROUNDS / PER16; ++q)
-            reinterpret_cast<uint4 *>(v)[q] = reinterpret_cast<const uint4 *>(keys + i0)[q];
+            for (int q = 0; q < RS_ROUNDS / 4; ++q)
+                reinterpret_cast<uint4 *>(v)[q] = reinterpret_cast<const uint4 *>(vals + i0)[q];
 #pragma unroll
-        for (int r = 0; r < RS_ROUNDS; ++r) atomicAdd(&h[(uint32_t)(v[r] >> shift) & (NB - 1u)], 1u);
+            for (int r = 0; r < RS_ROUNDS; ++r) atomicAdd(&h[rs_digit<K, RB, true>(0, v[r], shift, n_gauss)], 1u);
+        } else {
+#pragma unroll
+            for (int r = 0; r < RS_ROUNDS; ++r)
+                if (i0 + r < n) atomicAdd(&h[rs_digit<K, RB, true>(0, vals[i0 + r], shift, n_gauss)], 1u);
+        }
     } else {
+        constexpr int PER16 = 16 / (int)sizeof(K);
+        static_assert(RS_ROUNDS % PER16 == 0, "whole vectors per thread");
+        K v[RS_ROUNDS];
+        if (base + RS_TILE <= n) {
 #pragma unroll
-        for (int r = 0; r < RS_ROUNDS; ++r)
-            if (i0 + r < n) atomicAdd(&h[(uint32_t)(keys[i0 + r] >> shift) & (NB - 1u)], 1u);
+            for (int q = 0; q < RS_ROUNDS / PER16; ++q)
+                reinterpret_cast<uint4 *>(v)[q] = reinterpret_cast<const uint4 *>(keys + i0)[q];
+#pragma unroll
+            for (int r = 0; r < RS_ROUNDS; ++r) atomicAdd(&h[rs_digit<K, RB, false>(v[r], 0, shift, 0)], 1u);
+        } else {
+#pragma unroll
+            for (int r = 0; r < RS_ROUNDS; ++r)
+                if (i0 + r < n) atomicAdd(&h[rs_digit<K, RB, false>(keys[i0 + r], 0, shift, 0)], 1u);
+        }
     }
     __syncthreads();
     if (threadIdx.x < NB) hist[(uint64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
@@ -158,11 +186,11 @@ __global__ void __launch_bounds__(RS_THREADS) rs_hist_kernel(const K *__restrict
 // (stable: warps in order, rounds in order, lanes in order), reorders them by
 // digit in shared memory, then writes every digit run to its global offset
 // with consecutive threads on consecutive addresses.
-template <class K, int RB>
+template <class K, int RB, bool CELL>
 __global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(const K *__restrict__ kin,
                                                                 const uint32_t *__restrict__ vin,
                                                                 K *__restrict__ kout, uint32_t *__restrict__ vout,
-                                                                uint32_t n, int shift,
+                                                                uint32_t n, int shift, uint64_t n_gauss,
                                                                 const uint32_t *__restrict__ offs,
                                                                 uint32_t nblocks)
 {
@@ -189,7 +217,7 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(const K *__restr
         const bool ok = i < n;
         key[r] = ok ? kin[i] : (K)0;
         val[r] = ok ? vin[i] : 0u;
-        dig[r] = ok ? ((uint32_t)(key[r] >> shift) & (NB - 1u)) : NB;
+        dig[r] = ok ? rs_digit<K, RB, CELL>(key[r], val[r], shift, n_gauss) : NB;
     }
 #pragma unroll
     for (int r = 0; r < RS_ROUNDS; ++r) {
@@ -252,10 +280,11 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(const K *__restr
     const uint32_t cnt = n - blk0 < (uint64_t)RS_TILE ? (uint32_t)(n - blk0) : (uint32_t)RS_TILE;
     for (uint32_t j = threadIdx.x; j < cnt; j += RS_THREADS) {
         const K k = s_key[j];
-        const uint32_t d = (uint32_t)(k >> shift) & (NB - 1u);
+        const uint32_t v = s_val[j];
+        const uint32_t d = rs_digit<K, RB, CELL>(k, v, shift, n_gauss);
         const uint32_t pos = gbase[d] + (j - dstart[d]);
         kout[pos] = k;
-        vout[pos] = s_val[j];
+        vout[pos] = v;
     }
 }
 
@@ -265,16 +294,45 @@ size_t radix_hist_words(uint64_t n)
     return 256 * nb;
 }
 
-template <class K, int RB>
+template <class K, int RB, bool CELL = false>
 static void radix_pass(const K *ka, const uint32_t *va, K *kb, uint32_t *vb, uint64_t n, int shift, uint32_t *hist,
-                       uint32_t *scan_tmp, cudaStream_t st, int *launches)
+                       uint32_t *scan_tmp, cudaStream_t st, int *launches, uint64_t n_gauss = 0)
 {
     const uint32_t nb = (uint32_t)((n + RS_TILE - 1) / RS_TILE);
-    rs_hist_kernel<K, RB><<<nb, RS_THREADS, 0, st>>>(ka, (uint32_t)n, shift, hist, nb);
+    rs_hist_kernel<K, RB, CELL><<<nb, RS_THREADS, 0, st>>>(ka, va, (uint32_t)n, shift, n_gauss, hist, nb);
     ++*launches;
     exclusive_scan(hist, hist, ((uint64_t)1 << RB) * nb, scan_tmp, st, launches);
-    rs_scatter_kernel<K, RB><<<nb, RS_THREADS, 0, st>>>(ka, va, kb, vb, (uint32_t)n, shift, hist, nb);
+    rs_scatter_kernel<K, RB, CELL><<<nb, RS_THREADS, 0, st>>>(ka, va, kb, vb, (uint32_t)n, shift, n_gauss, hist, nb);
     ++*launches;
+}
+
+// Stable sort of the events (keys, vals) by the cell of their pair, bits
+// [0, bits) of it, in passes of at most 8 bits; returns 1 if the result
+// ended in the alt buffers.
+static int radix_sort_cells(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint64_t n,
+                            int bits, uint64_t n_gauss, uint32_t *hist, uint32_t *scan_tmp, cudaStream_t st,
+                            int *launches)
+{
+    if (n == 0 || bits <= 0) return 0;
+    const int passes = (bits + 7) / 8;
+    const int rb = (bits + passes - 1) / passes;
+    uint64_t *ka = keys, *kb = keys_alt;
+    uint32_t *va = vals, *vb = vals_alt;
+    int flips = 0;
+    for (int p = 0, shift = 0; p < passes; ++p, shift += rb) {
+        switch (rb) {
+        case 1: case 2: case 3: case 4:
+            radix_pass<uint64_t, 4, true>(ka, va, kb, vb, n, shift, hist, scan_tmp, st, launches, n_gauss); break;
+        case 5: radix_pass<uint64_t, 5, true>(ka, va, kb, vb, n, shift, hist, scan_tmp, st, launches, n_gauss); break;
+        case 6: radix_pass<uint64_t, 6, true>(ka, va, kb, vb, n, shift, hist, scan_tmp, st, launches, n_gauss); break;
+        case 7: radix_pass<uint64_t, 7, true>(ka, va, kb, vb, n, shift, hist, scan_tmp, st, launches, n_gauss); break;
+        default: radix_pass<uint64_t, 8, true>(ka, va, kb, vb, n, shift, hist, scan_tmp, st, launches, n_gauss); break;
+        }
+        uint64_t *tk = ka; ka = kb; kb = tk;
+        uint32_t *tv = va; va = vb; vb = tv;
+        flips ^= 1;
+    }
+    return flips;
 }
 
 // Stable LSD sort of (keys, vals) on key bits [shift0, shift0 + bits): the
@@ -325,13 +383,6 @@ __global__ void emit_events_kernel(const PixBox *__restrict__ boxes, const doubl
     ev_key[2 * p + 1] = key_bits(keys[2 * i + 1]);
     ev_val[2 * p] = (uint32_t)(2 * i);
     ev_val[2 * p + 1] = (uint32_t)(2 * i + 1);
-}
-
-__global__ void cell_keys_kernel(const uint32_t *__restrict__ ev_val, uint64_t ne, uint64_t n_gauss,
-                                 uint32_t *__restrict__ ck)
-{
-    const uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    if (e < ne) ck[e] = (uint32_t)((ev_val[e] >> 1) / n_gauss);
 }
 
 __device__ __forceinline__ void tile_rect(const PixBox &b, int TS, int &tx0, int &tx1, int &ty0, int &ty1)
@@ -463,17 +514,6 @@ __global__ void iota_kernel(uint32_t *__restrict__ p, uint64_t n)
     if (i < n) p[i] = (uint32_t)i;
 }
 
-__global__ void gather_events_kernel(const uint32_t *__restrict__ perm, const uint64_t *__restrict__ kin,
-                                     const uint32_t *__restrict__ vin, uint64_t n, uint64_t *__restrict__ kout,
-                                     uint32_t *__restrict__ vout)
-{
-    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint32_t p = perm[i];
-    kout[i] = kin[p];
-    vout[i] = vin[p];
-}
-
 static inline unsigned blocks_for(uint64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 int run_binning(const BinArgs &a, BinOut &o, cudaStream_t st, int *launches)
@@ -506,20 +546,13 @@ int run_binning(const BinArgs &a, BinOut &o, cudaStream_t st, int *launches)
     uint64_t *evk = a.ev_key[f];
     uint32_t *evv = a.ev_val[f];
     if (a.n_cells > 1) {
-        cell_keys_kernel<<<blocks_for(ne, T), T, 0, st>>>(evv, ne, a.n_gauss, a.u32_b);
-        ++*launches;
+        // stably by cell, the digits taken from the pair index in the value
         int bits = 0;
         while ((1ull << bits) < (uint64_t)a.n_cells) ++bits;
-        // carry the key bits along: sort (cell, position) then gather keys
-        // through the permuted positions
-        iota_kernel<<<blocks_for(ne, T), T, 0, st>>>(a.u32_a, ne);
-        ++*launches;
-        int g = radix_sort<uint32_t>(a.u32_b, a.u32_a, a.u32_c, a.u32_d, ne, bits, a.hist, a.scan_tmp, st, launches);
-        const uint32_t *perm = g ? a.u32_d : a.u32_a;
-        gather_events_kernel<<<blocks_for(ne, T), T, 0, st>>>(perm, evk, evv, ne, a.ev_key[f ^ 1], a.ev_val[f ^ 1]);
-        ++*launches;
-        evk = a.ev_key[f ^ 1];
-        evv = a.ev_val[f ^ 1];
+        const int g = radix_sort_cells(evk, evv, a.ev_key[f ^ 1], a.ev_val[f ^ 1], ne, bits, a.n_gauss, a.hist,
+                                       a.scan_tmp, st, launches);
+        evk = a.ev_key[f ^ g];
+        evv = a.ev_val[f ^ g];
     }
     o.ev_key = evk;
     o.ev_val = evv;
