@@ -111,9 +111,6 @@ template <int M> struct DF {
     double c[M];
     double k;
 };
-template <int M> struct DB {
-    DF<M> lo, hi;
-};
 
 __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
@@ -133,63 +130,6 @@ template <int M> __device__ __forceinline__ double df_max(const DF<M> &f)
     for (int j = 0; j < M; ++j) s = dadd(s, fabs(f.c[j]));
     return s;
 }
-template <int M> __device__ __forceinline__ DF<M> df_scale(const DF<M> &a, double s)
-{
-    DF<M> r;
-#pragma unroll
-    for (int j = 0; j < M; ++j) r.c[j] = dmul(s, a.c[j]);
-    r.k = dmul(s, a.k);
-    return r;
-}
-template <int M> __device__ __forceinline__ DF<M> df_add(const DF<M> &a, const DF<M> &b)
-{
-    DF<M> r;
-#pragma unroll
-    for (int j = 0; j < M; ++j) r.c[j] = dadd(a.c[j], b.c[j]);
-    r.k = dadd(a.k, b.k);
-    return r;
-}
-template <int M> __device__ __forceinline__ DF<M> df_sub(const DF<M> &a, const DF<M> &b)
-{
-    DF<M> r;
-#pragma unroll
-    for (int j = 0; j < M; ++j) r.c[j] = dsub(a.c[j], b.c[j]);
-    r.k = dsub(a.k, b.k);
-    return r;
-}
-template <int M> __device__ __forceinline__ DB<M> db_add(const DB<M> &a, const DB<M> &b)
-{
-    DB<M> r;  // shared coefficients (see db_mul)
-#pragma unroll
-    for (int j = 0; j < M; ++j) {
-        r.lo.c[j] = dadd(a.lo.c[j], b.lo.c[j]);
-        r.hi.c[j] = r.lo.c[j];
-    }
-    r.lo.k = dadd(a.lo.k, b.lo.k);
-    r.hi.k = dadd(a.hi.k, b.hi.k);
-    return r;
-}
-// averaged McCormick planes (same statement as the single-precision Mul).
-// The lower and upper forms of every operand here share their coefficients
-// (the pose forms differ only in their constants), so the coefficients of the
-// product are computed once; each is the same IEEE expression either way.
-template <int M> __device__ __forceinline__ DB<M> db_mul(const DB<M> &x, const DB<M> &y)
-{
-    double xl = df_min(x.lo), xh = df_max(x.hi), yl = df_min(y.lo), yh = df_max(y.hi);
-    double xm = dmul(0.5, dadd(xl, xh)), ym = dmul(0.5, dadd(yl, yh));
-    DB<M> r;
-#pragma unroll
-    for (int j = 0; j < M; ++j) {
-        r.lo.c[j] = dadd(dmul(ym, x.lo.c[j]), dmul(xm, y.lo.c[j]));
-        r.hi.c[j] = r.lo.c[j];
-    }
-    r.lo.k = dadd(dmul(ym, (ym >= 0 ? x.lo : x.hi).k), dmul(xm, (xm >= 0 ? y.lo : y.hi).k));
-    r.lo.k = dsub(r.lo.k, dmul(0.5, dadd(dmul(xl, yl), dmul(xh, yh))));
-    r.hi.k = dadd(dmul(ym, (ym >= 0 ? x.hi : x.lo).k), dmul(xm, (xm >= 0 ? y.hi : y.lo).k));
-    r.hi.k = dsub(r.hi.k, dmul(0.5, dadd(dmul(xh, yl), dmul(xl, yh))));
-    return r;
-}
-
 // intervals for the screen box
 struct DI {
     double l, u;

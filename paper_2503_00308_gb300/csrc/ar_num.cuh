@@ -1,10 +1,10 @@
 // ar_num.cuh -- sound linear bounds over a pose cell, in directed rounding.
 //
 // A pose cell is a box; every pose variable is normalised to p in [-1, 1]^M.
-// A bounded scalar BS holds two affine forms lo(p) <= v <= hi(p) (the
+// A bounded scalar holds two affine forms lo(p) <= v <= hi(p) (the
 // piecewise-linear relations of Sec. 2.1 with one piece) plus their
-// concretisation over the box: vlo = min lo, vhi = max hi, and the radii
-// rlo = sum |lo.c|, rhi = sum |hi.c|.
+// concretisation over the box.  Here the two forms share their coefficients
+// (SB below); LF is a single form.
 //
 // Soundness in floating point: coefficients are computed round-to-nearest and
 // the worst-case rounding error of every coefficient, summed over the box
@@ -123,39 +123,6 @@ template <int M, class R> struct LF {
     R k;
 };
 
-template <int M, class R> struct BS {
-    LF<M, R> lo, hi;
-    R vlo, vhi;  // concretised bounds over the box
-    R rlo, rhi;  // radii of lo and hi (sum of |coefficients|, rounded up)
-};
-
-template <int M, class R>
-__device__ __forceinline__ void finish(BS<M, R> &b)
-{
-    using N = Num<R>;
-    R rl = 0, rh = 0;
-#pragma unroll
-    for (int j = 0; j < M; ++j) {
-        rl = N::add_ru(rl, N::abs(b.lo.c[j]));
-        rh = N::add_ru(rh, N::abs(b.hi.c[j]));
-    }
-    b.rlo = rl;
-    b.rhi = rh;
-    b.vlo = N::sub_rd(b.lo.k, rl);
-    b.vhi = N::add_ru(b.hi.k, rh);
-}
-
-template <int M, class R>
-__device__ __forceinline__ BS<M, R> cst(R lo, R hi)
-{
-    BS<M, R> b;
-#pragma unroll
-    for (int j = 0; j < M; ++j) { b.lo.c[j] = 0; b.hi.c[j] = 0; }
-    b.lo.k = lo; b.hi.k = hi;
-    b.vlo = lo; b.vhi = hi; b.rlo = 0; b.rhi = 0;
-    return b;
-}
-
 // Accumulator of a sound form  sum_t a_t F_t + b  (one side).  DN = true for
 // a lower form (constant rounded down, slack subtracted), false for upper.
 template <int M, class R, bool DN> struct Acc {
@@ -216,56 +183,6 @@ template <int M, class R, bool DN> struct Acc {
         LF<M, R> out = f;
         out.k = DN ? N::sub_rd(f.k, s) : N::add_ru(f.k, s);
         return out;
-    }
-};
-
-template <int M, class R> struct Pair {
-    Acc<M, R, true> lo;
-    Acc<M, R, false> hi;
-    __device__ __forceinline__ void init(R blo, R bhi) { lo.init(blo); hi.init(bhi); }
-    __device__ __forceinline__ BS<M, R> result() const
-    {
-        BS<M, R> b;
-        b.lo = lo.result();
-        b.hi = hi.result();
-        finish(b);
-        return b;
-    }
-    // + a * x   (a exact)
-    __device__ __forceinline__ void lin(R a, const BS<M, R> &x)
-    {
-        if (a >= 0) { lo.term(a, x.lo, x.rlo); hi.term(a, x.hi, x.rhi); }
-        else        { lo.term(a, x.hi, x.rhi); hi.term(a, x.lo, x.rlo); }
-    }
-    // + x * y  (averaged McCormick planes)
-    __device__ __forceinline__ void mul(const BS<M, R> &x, const BS<M, R> &y)
-    {
-        using N = Num<R>;
-        const R xl = x.vlo, xh = x.vhi, yl = y.vlo, yh = y.vhi;
-        const R xm = N::mul_rn(xl + xh, (R)0.5), ym = N::mul_rn(yl + yh, (R)0.5);
-        lin(ym, x);
-        lin(xm, y);
-        // constants: -(xl yl + xh yh)/2 below, -(xh yl + xl yh)/2 above
-        lo.add_const(-N::mul_ru(N::fma_ru(xl, yl, N::mul_ru(xh, yh)), (R)0.5));
-        hi.add_const(-N::mul_rd(N::fma_rd(xh, yl, N::mul_rd(xl, yh)), (R)0.5));
-        // the slopes are the rounded midpoints: cover |ym - y_mid| max|x| + ...
-        const R xa = N::max(N::abs(xl), N::abs(xh)), ya = N::max(N::abs(yl), N::abs(yh));
-        const R mid = N::mul_ru(N::fma_ru(N::abs(ym), xa, N::mul_ru(N::abs(xm), ya)), N::mul_ru(N::U, (R)1.001));
-        lo.add_slack(mid);
-        hi.add_slack(mid);
-    }
-    // + x^2  (tangent at the midpoint below, secant above)
-    __device__ __forceinline__ void sqr(const BS<M, R> &x)
-    {
-        using N = Num<R>;
-        const R xl = x.vlo, xh = x.vhi;
-        const R c = N::mul_rn(xl + xh, (R)0.5);
-        const R c2 = c + c;
-        if (c2 >= 0) lo.term(c2, x.lo, x.rlo); else lo.term(c2, x.hi, x.rhi);
-        lo.add_const(-N::mul_ru(c, c));
-        const R s = xl + xh;
-        if (s >= 0) hi.term(s, x.hi, x.rhi); else hi.term(s, x.lo, x.rlo);
-        hi.add_const(N::max(N::fma_ru(xl, xl, N::mul_ru(-s, xl)), N::fma_ru(xh, xh, N::mul_ru(-s, xh))));
     }
 };
 
@@ -416,38 +333,6 @@ template <int M, class R>
 __device__ __forceinline__ SB<M, R> sb_add(const SB<M, R> &x, const SB<M, R> &y)
 {
     SAcc<M, R> p; p.init(0, 0); p.term((R)1, x); p.term((R)1, y); return p.result();
-}
-
-template <int M, class R>
-__device__ __forceinline__ BS<M, R> b_mul(const BS<M, R> &x, const BS<M, R> &y)
-{
-    Pair<M, R> p; p.init(0, 0); p.mul(x, y); return p.result();
-}
-template <int M, class R>
-__device__ __forceinline__ BS<M, R> b_sqr(const BS<M, R> &x)
-{
-    Pair<M, R> p; p.init(0, 0); p.sqr(x); return p.result();
-}
-// a*x + b*y + c
-template <int M, class R>
-__device__ __forceinline__ BS<M, R> b_lin2(R a, const BS<M, R> &x, R b, const BS<M, R> &y, R c)
-{
-    Pair<M, R> p; p.init(c, c); p.lin(a, x); p.lin(b, y); return p.result();
-}
-template <int M, class R>
-__device__ __forceinline__ BS<M, R> b_add(const BS<M, R> &x, const BS<M, R> &y)
-{
-    return b_lin2<M, R>((R)1, x, (R)1, y, (R)0);
-}
-// x widened by e >= 0 on both sides
-template <int M, class R>
-__device__ __forceinline__ BS<M, R> b_widen(BS<M, R> x, R e)
-{
-    using N = Num<R>;
-    x.lo.k = N::sub_rd(x.lo.k, e);
-    x.hi.k = N::add_ru(x.hi.k, e);
-    finish(x);
-    return x;
 }
 
 }  // namespace ar

@@ -473,15 +473,17 @@ __device__ __forceinline__ int64_t record_decide(const double *__restrict__ vN, 
     const double *vl = vN + VN_STRIDE * g, *vh = vl + 3, *N = vl + 6;
 
     // ---- FP64 decision chain: depth d = sum_b R_delta[b][2] (v_b - s_b) by
-    // averaged McCormick products (db_mul, summed by db_add), its bounds, the
-    // near-plane class and the depth key.  These are the IEEE operations of
-    // db_mul, db_add and df_min / df_max on the full forms, in their order,
-    // less the ones whose operand is a coefficient that is zero by
-    // construction (R_delta[b][2] lives on the rotation slots, s_b on the
-    // translation slots; adding, subtracting or scaling zero changes no value
-    // but the sign of a zero, which the bounds never see) and less the
-    // per-cell parts the cell kernel computed.  So dlo, dhi, klo and khi are
-    // bit-identical to the plain statement.
+    // averaged McCormick products (the lower form of x y is y_m x + x_m y -
+    // (x_lo y_lo + x_hi y_hi)/2 with each operand's side chosen by the sign of
+    // the other's midpoint, the upper one likewise), summed, then its bounds,
+    // the near-plane class and the depth key.  These are the round-to-nearest
+    // IEEE operations of that statement on the full forms, in its order, less
+    // the ones whose operand is a coefficient that is zero by construction
+    // (R_delta[b][2] lives on the rotation slots, s_b on the translation
+    // slots; adding, subtracting or scaling zero changes no value but the sign
+    // of a zero, which the bounds never see) and less the per-cell parts the
+    // cell kernel computed.  So dlo, dhi, klo and khi are bit-identical to the
+    // plain statement.
     const int n_t = cd.n_t, n_a = cd.n_a;
     double ddr[M];  // rotation-slot coefficients of d
     double dlk = 0.0, dhk = 0.0;  // constants of d's lower and upper forms

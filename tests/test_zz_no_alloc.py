@@ -48,6 +48,12 @@ def test_noalloc_matches_allocating_entry_point_twice():
     b_lo, b_hi = _render(ar, ar.ar_render_abstract_noalloc, t, w.camera, w.cells_lo, w.cells_hi)
     assert np.abs(a_lo - b_lo).max() <= TOL and np.abs(a_hi - b_hi).max() <= TOL
     t.close()
+    # with scene-parameter boxes (the decision and value chains read them the same way)
+    s.set_boxes(synth.scene_boxes(sc, 3, frac=0.4, red_add=0.3, mean_d=(0.02, 0.0, 0.0), opacity_scale=0.8,
+                                  opacity_add=0.1))
+    ref_lo, ref_hi = _render(ar, ar.ar_render_abstract, s, cam, lo, hi)
+    n_lo, n_hi = _render(ar, ar.ar_render_abstract_noalloc, s, cam, lo, hi)
+    assert np.abs(n_lo - ref_lo).max() <= TOL and np.abs(n_hi - ref_hi).max() <= TOL
     s.close()
 
 
