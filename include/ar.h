@@ -122,8 +122,8 @@ int ar_scene_destroy(ar_scene *scene);
  * lower and upper bounds.
  *   cells[n_cells] (host memory), n_cells >= 1.
  *   tile: 0 = choose, else 8 or 16 (screen tile edge of the binning; the
- *   bounds do not depend on it beyond 1e-7: a pixel stops sweeping once what
- *   is left of its tile's list can move its bounds by less than 5e-8, and
+ *   bounds do not depend on it beyond 2e-5: a pixel stops sweeping once what
+ *   is left of its tile's list can move its bounds by less than 1e-5, and
  *   widens them by that much).  With 0, the first call for a given image
  *   size and number of pose variables times the pipeline with both edges on
  *   its first two cells and keeps the faster for the scene (autotuner).

@@ -10,7 +10,7 @@ plain 1e-4.  Pixels where a threshold decision taken in single precision lies
 within its rounding band are "fragile": both outcomes are sound there, and
 they are checked for soundness instead.  Soundness: concrete FP64 renders at
 sampled poses lie inside the GPU bounds.  Invariances: cell batching is
-bit-exact; the tile size moves the bounds by at most 1e-7 (early stopping).
+bit-exact; the tile size moves the bounds by at most 2e-5 (early stopping).
 """
 import numpy as np
 import pytest
@@ -106,8 +106,8 @@ def test_tile_and_batch_invariance(arlib):
     lo, hi = synth.cell_grid([0.03, 0.0, 0.03, 0.0, 0.01, 0.0], [2, 1, 2, 1, 1, 1])
     a_lo, a_hi = gpu_render(arlib, sc, cam, lo, hi, tile=16)
     b_lo, b_hi = gpu_render(arlib, sc, cam, lo, hi, tile=8)
-    # tiles differ only in where a pixel may stop early (each stop widens by < 5e-8)
-    assert np.abs(a_lo - b_lo).max() <= 1e-7 and np.abs(a_hi - b_hi).max() <= 1e-7
+    # tiles differ only in where a pixel may stop early (each stop widens by <= 1e-5)
+    assert np.abs(a_lo - b_lo).max() <= 2e-5 and np.abs(a_hi - b_hi).max() <= 2e-5
     for c in [0, 3]:
         c_lo, c_hi = gpu_render(arlib, sc, cam, lo[c:c + 1], hi[c:c + 1], tile=16)
         assert np.array_equal(c_lo[0], a_lo[c]) and np.array_equal(c_hi[0], a_hi[c])
