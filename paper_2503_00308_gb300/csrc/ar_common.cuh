@@ -88,7 +88,10 @@ constexpr uint32_t F_KHIGH_PENDING = 32u;  // likewise, for a Taylor order above
 
 // doubles per Gaussian of the per-call array vN: v = R_wc (uw - t) as an
 // interval over the mean's box (lower ends 3, upper ends 3), then N = R_wc Mw
-constexpr int VN_STRIDE = 15;
+// (9), then, in the storage of VN_ENC_DOUBLES doubles, 30 floats: the FP32
+// enclosures (lo, hi) of those 15 values, for the screen-box filter
+constexpr int VN_ENC = 15, VN_ENC_DOUBLES = 15;
+constexpr int VN_STRIDE = VN_ENC + VN_ENC_DOUBLES;
 
 // Per-Gaussian scene parameters of the abstract render as boxes (Sec. 4.5):
 // opacity o in [o_lo, o_hi], the cutoff exponent tau = 2 ln(255 o) at both

@@ -356,9 +356,9 @@ static __device__ __noinline__ int screen_fp64(const double (*rd_int)[2], const 
 // rate is about 1/64 of its FP32 rate, and the FP64 path is then taken by a
 // small fraction of the pairs.
 template <int M>
-__device__ __forceinline__ int screen_fp32(const CellData<M> &cd, const double *vl, const double *vh,
-                                           const double *N, double dlo, double dhi, double tau, const CallConst &cc,
-                                           PixBox &box, double *mu_px, bool &straddle)
+__device__ __forceinline__ int screen_fp32(const CellData<M> &cd, const float *enc, double dlo, double dhi,
+                                           double tau, const CallConst &cc, PixBox &box, double *mu_px,
+                                           bool &straddle)
 {
     bool ok = true;
     const double nearp = (double)cc.near_plane;
@@ -366,11 +366,13 @@ __device__ __forceinline__ int screen_fp32(const CellData<M> &cd, const double *
     for (int e = 0; e < 9; ++e)
         Ri[e] = EI{E32{cd.rd_int32[e][0][0], cd.rd_int32[e][0][1]}, E32{cd.rd_int32[e][1][0], cd.rd_int32[e][1][1]}};
     for (int b = 0; b < 3; ++b) {
-        vs[b] = EI{e_chk(e_sub(e_of(vl[b]), E32{cd.s_int32[b][1][0], cd.s_int32[b][1][1]}), ok),
-                   e_chk(e_sub(e_of(vh[b]), E32{cd.s_int32[b][0][0], cd.s_int32[b][0][1]}), ok)};
+        // enc: the enclosures of v_lo, v_hi, N that pose_prep_kernel stored
+        vs[b] = EI{e_chk(e_sub(E32{enc[2 * b], enc[2 * b + 1]}, E32{cd.s_int32[b][1][0], cd.s_int32[b][1][1]}), ok),
+                   e_chk(e_sub(E32{enc[6 + 2 * b], enc[7 + 2 * b]}, E32{cd.s_int32[b][0][0], cd.s_int32[b][0][1]}),
+                         ok)};
     }
     E32 Ne[9];
-    for (int i = 0; i < 9; ++i) Ne[i] = e_of(N[i]);
+    for (int i = 0; i < 9; ++i) Ne[i] = E32{enc[12 + 2 * i], enc[13 + 2 * i]};
     const double dl = fmax(dlo, nearp);
     const EI D = {e_of(dl), e_of(dhi)};
     const EI ucx = ei_add(ei_add(ei_mul(Ri[0], vs[0], ok), ei_mul(Ri[3], vs[1], ok), ok), ei_mul(Ri[6], vs[2], ok), ok);
@@ -534,7 +536,8 @@ __device__ __forceinline__ int64_t record_decide(const double *__restrict__ vN, 
     // FP32 enclosures of the FP64 values where they settle every decision,
     // else in FP64 (the same values either way)
     double mu_px[2];
-    int sr = screen_fp32<M>(cd, vl, vh, N, dlo, dhi, tau, cc, box, mu_px, straddle);
+    int sr = screen_fp32<M>(cd, reinterpret_cast<const float *>(vl + VN_ENC), dlo, dhi, tau, cc, box, mu_px,
+                            straddle);
     if (sr == SCREEN_UNDECIDED)
         sr = screen_fp64(cd.rd_int, cd.s_int, vl, vh, N, dlo, dhi, tau, cc, box, mu_px, straddle);
     if (sr == SCREEN_DROP) return -1;

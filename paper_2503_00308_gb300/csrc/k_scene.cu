@@ -42,6 +42,11 @@ __global__ void pose_prep_kernel(const float *__restrict__ uw_lo, const float *_
         o[3 + a] = sh;
     }
     mat3(cc.R0, Mw + 9 * i, o + 6);
+    float *enc = reinterpret_cast<float *>(o + VN_ENC);
+    for (int k = 0; k < VN_ENC; ++k) {
+        enc[2 * k] = __double2float_rd(o[k]);
+        enc[2 * k + 1] = __double2float_ru(o[k]);
+    }
 }
 
 // The GParam of every Gaussian from its opacity and colour boxes.
