@@ -64,9 +64,10 @@ int AR_CAT(launch_render_plain_m, AR_M)(int TS, const RenderLaunch &a, cudaStrea
 template <int TS>
 static int launch_render_ts(const RenderLaunch &a, cudaStream_t st)
 {
-    // double-buffered chunks and a ring of 6 keep two 256-thread CTAs within
-    // the shared memory of an SM
-    constexpr int CH = 32, RING = 6;
+    // double-buffered chunks of 16 events and a ring of 4 (measured best of
+    // chunks 8-64 and rings 3-8: the exit vote, taken once per chunk, stops a
+    // tile sooner with short chunks; the ring's shared memory stays small)
+    constexpr int CH = 16, RING = 4;
     typedef RenderSmem<AR_M, TS, CH, RING> SM;
     auto kern = render_kernel<AR_M, TS, CH, RING>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::BYTES) != cudaSuccess)

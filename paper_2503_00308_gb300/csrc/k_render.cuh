@@ -312,8 +312,8 @@ __device__ __forceinline__ float open_ratio_up(float a)
     return den > 0.f ? __fmul_ru(__fdividef(a, den), 1.000000477f) : 3.0e38f;
 }
 
-// Shared-memory layout of the render kernel (dynamic; about 100 KB at six
-// pose variables, tile 16 and a ring of 6, so two CTAs fit on an SM):
+// Shared-memory layout of the render kernel (dynamic; about 60 KB at six
+// pose variables, tile 16, chunks of 16 and a ring of 4, so two CTAs fit on an SM):
 //   two buffers, each with the records staged for a chunk of CH events, their
 //   event info and pixel boxes (the next chunk is copied in while the current
 //   one is swept),
