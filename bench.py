@@ -43,12 +43,12 @@ def flops_per_triple(M: int) -> int:
 
 # DRAM bytes of the render kernel per opacity evaluation, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the first 4 cells of the
-# 300k-Gaussian workload: 53.3 MB over 80.1M evaluations.  Valid only for the
+# 300k-Gaussian workload: 44.2 MB over 73.0M evaluations.  Valid only for the
 # kernel sources it was taken from (their SHA-256 below); otherwise the
 # roofline's traffic is reported as null.
-RENDER_TRAFFIC = {"bytes_per_evaluation": (37127936 + 16136192) / 80127389,
+RENDER_TRAFFIC = {"bytes_per_evaluation": (30953472 + 13228800) / 73014342,
                   "sources": ["k_render.cuh", "ar_num.cuh", "ar_common.cuh", "k_inst.cuh"],
-                  "sha256": "749b9c426ddc8e3420ab2eb3b1704dbd9d8745ecb1b6497d7d030eb8dc2187c9"}
+                  "sha256": "f055e330a68e09e9b9110b26b7556321ef1d63cbcc92fded137b1eed2c06501d"}
 
 
 def render_traffic(n_evaluated: int):
