@@ -137,10 +137,15 @@ int ar_render_abstract(ar_scene *scene, const ar_intrinsics *intr, const ar_nomi
                        const ar_pose_box *cells, int32_t n_cells, int32_t tile,
                        float *out_lower, float *out_upper, void *cuda_stream);
 
-/* Same as ar_render_abstract with HOST output buffers: the bounds are
- * computed into scene-owned device memory and copied to host_lower /
- * host_upper ([n_cells][H][W][3] float32 each, page-locked memory is
- * fastest).  Returns after the copies complete. */
+/* Same as ar_render_abstract with HOST output buffers host_lower /
+ * host_upper ([n_cells][H][W][3] float32 each).  When both are page-locked
+ * host memory mapped into the device (cudaHostAlloc, or cudaHostRegister on a
+ * unified-addressing system), the render kernel stores the bounds into them
+ * directly, so the device-to-host transfer overlaps the render.  Any other
+ * host memory gets the bounds computed into scene-owned device memory and
+ * copied after the render.  The results are identical either way.  Returns
+ * after the bounds are in host memory; on an error the buffers' contents are
+ * undefined. */
 int ar_render_abstract_host(ar_scene *scene, const ar_intrinsics *intr, const ar_nominal_pose *pose,
                             const ar_pose_box *cells, int32_t n_cells, int32_t tile,
                             float *host_lower, float *host_upper, void *cuda_stream);

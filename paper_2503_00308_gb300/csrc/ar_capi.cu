@@ -9,6 +9,7 @@
 // all enqueued on the caller's stream.
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -838,6 +839,26 @@ int ar_render_abstract(ar_scene *s, const ar_intrinsics *in, const ar_nominal_po
     return r;
 }
 
+// Device address of a host buffer of `bytes` bytes when its first and last
+// byte are page-locked host memory mapped into `device`'s address space (one
+// contiguous mapping), else null.  Pageable memory and device memory give null.
+static float *mapped_host(float *p, size_t bytes, int device)
+{
+    if (!p || bytes == 0) return nullptr;
+    cudaPointerAttributes a, b;
+    char *last = (char *)p + (bytes - 1);
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess || cudaPointerGetAttributes(&b, last) != cudaSuccess) {
+        cudaGetLastError();  // not a CUDA-known pointer: clear the error, use the copy path
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer || !b.devicePointer)
+        return nullptr;
+    if ((char *)b.devicePointer - (char *)a.devicePointer != (ptrdiff_t)(bytes - 1)) return nullptr;
+    int dev_ok = 0;
+    if (cudaDeviceGetAttribute(&dev_ok, cudaDevAttrCanMapHostMemory, device) != cudaSuccess || !dev_ok) return nullptr;
+    return (float *)a.devicePointer;
+}
+
 int ar_render_abstract_host(ar_scene *s, const ar_intrinsics *in, const ar_nominal_pose *pose,
                             const ar_pose_box *cells, int32_t n_cells, int32_t tile, float *host_lower,
                             float *host_upper, void *stream)
@@ -848,6 +869,17 @@ int ar_render_abstract_host(ar_scene *s, const ar_intrinsics *in, const ar_nomin
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = sizeof(float) * 3 * (size_t)in->width * in->height * n_cells;
     CK(cudaSetDevice(s->device));
+    // Page-locked, mapped buffers are written by the render kernel itself:
+    // it only stores to its outputs, once per finished (cell, tile) segment,
+    // so the transfer to the host runs while the render does instead of after
+    // it.  Both ends of both buffers must lie in mapped host memory.
+    float *map_lo = mapped_host(host_lower, bytes, s->device), *map_hi = mapped_host(host_upper, bytes, s->device);
+    if (map_lo && map_hi && s->n > 0) {
+        RK(render_core(s, s->ws, in, pose, cells, n_cells, tile, map_lo, map_hi, st, s->profiling, &s->stats));
+        s->stats_stream = st;
+        CK(cudaStreamSynchronize(st));
+        return AR_OK;
+    }
     RK(s->ws.out_lo.ensure(bytes));
     RK(s->ws.out_hi.ensure(bytes));
     RK(render_core(s, s->ws, in, pose, cells, n_cells, tile, s->ws.out_lo.as<float>(), s->ws.out_hi.as<float>(), st,

@@ -213,6 +213,40 @@ def test_cell_batches_are_bit_identical(arlib):
     s.close()
 
 
+def test_host_outputs_match_device_outputs(arlib):
+    """ar_render_abstract_host: page-locked buffers (written by the render
+    kernel itself), pageable buffers (staged and copied), one of each (copied),
+    and an empty scene all give the device call's bounds bit for bit."""
+    ar = arlib
+    sc = synth.object_scene(2500, 4)
+    cam = synth.look_camera(72, 56, 80.0, centre=(0, 0, -4))
+    lo, hi = synth.cell_grid([0.03, 0.0, 0.03, 0.0, 0.01, 0.0], [2, 1, 2, 1, 1, 1])
+    nc = lo.shape[0]
+    ref_lo, ref_hi = gpu_render(ar, sc, cam, lo, hi)
+    s = ar.Scene(sc)
+    intr, pose, cells = ar.make_intrinsics(cam), ar.make_pose(cam), ar.make_cells(lo, hi)
+    shape = (nc, cam.height, cam.width, 3)
+    p_lo = torch.full(shape, -7.0, dtype=torch.float32).pin_memory()
+    p_hi = torch.full(shape, -7.0, dtype=torch.float32).pin_memory()
+    ar.ar_render_abstract_host(s.handle, intr, pose, cells, nc, 0, p_lo, p_hi)
+    assert np.array_equal(p_lo.double().numpy(), ref_lo) and np.array_equal(p_hi.double().numpy(), ref_hi)
+    n_lo, n_hi = np.full(shape, -7.0, np.float32), np.full(shape, -7.0, np.float32)
+    ar.ar_render_abstract_host(s.handle, intr, pose, cells, nc, 0, n_lo, n_hi)
+    assert np.array_equal(n_lo.astype(np.float64), ref_lo) and np.array_equal(n_hi.astype(np.float64), ref_hi)
+    # one page-locked and one pageable buffer: the staged copy path
+    mixed_hi = np.full(shape, -7.0, np.float32)
+    p_lo.fill_(-7.0)
+    ar.ar_render_abstract_host(s.handle, intr, pose, cells, nc, 0, p_lo, mixed_hi)
+    assert np.array_equal(p_lo.double().numpy(), ref_lo) and np.array_equal(mixed_hi.astype(np.float64), ref_hi)
+    s.close()
+    e = ar.Scene(synth.cube_scene(0, 0))
+    p_lo.fill_(-7.0)
+    p_hi.fill_(-7.0)
+    ar.ar_render_abstract_host(e.handle, intr, pose, cells, nc, 0, p_lo, p_hi)
+    assert float(p_lo.abs().max()) == 0.0 and float(p_hi.abs().max()) == 0.0
+    e.close()
+
+
 def test_windowed_rounds_restart(arlib, orc):
     """Faint, dense scenes: tiles never stop early, so sweeps outgrow the first
     (512-entry) and second (8192-entry) windows of built records and are swept
