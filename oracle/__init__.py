@@ -48,6 +48,10 @@ def _load():
         lib.orc_render_concrete.restype = I
         lib.orc_render_abstract.argtypes = [P, P, P, P, P, I64, P, P, P, P, P, I, I, I, I, P, P, P, P]
         lib.orc_render_abstract.restype = I
+        lib.orc_render_abstract_tight.argtypes = [P, P, P, P, P, I64, P, P, P, P, P, I, I, I, I, P, P, P, P]
+        lib.orc_render_abstract_tight.restype = I
+        lib.orc_transmittance_chain.argtypes = [P, P, P, I, P, P]
+        lib.orc_transmittance_chain.restype = I
         lib.orc_render_abstract_sort.argtypes = [P, P, P, P, P, I64, P, P, P, P, P, I, I, I, I, P, P]
         lib.orc_render_abstract_sort.restype = I
         lib.orc_records.argtypes = [P, P, P, P, P, I64, P, P, P, P, P, P]
@@ -128,7 +132,7 @@ def set_boxes(boxes):
         raise MemoryError("oracle boxes")
 
 
-def render_abstract(scene, cam, cell_lo, cell_hi, window=None, with_cond=False):
+def render_abstract(scene, cam, cell_lo, cell_hi, window=None, with_cond=False, tight=False):
     """AbstractSplat bounds of one pose cell.
 
     Returns (lo, hi, fragile) -- and cond if with_cond: lo/hi are [H, W, 3]
@@ -136,7 +140,8 @@ def render_abstract(scene, cam, cell_lo, cell_hi, window=None, with_cond=False):
     rest stays NaN), fragile [H, W] uint8 marks pixels where a threshold
     decision that the single-precision path takes lies within its rounding
     band, and cond [H, W] estimates how far FP32 evaluation can move the
-    bounds."""
+    bounds.  tight=True: the upper bound uses the relational transmittance
+    of orc_render_abstract_tight (never above the interval one)."""
     lib = _load()
     s = _scene_args(scene)
     intr, R0, t0 = _cam_args(cam)
@@ -147,12 +152,28 @@ def render_abstract(scene, cam, cell_lo, cell_hi, window=None, with_cond=False):
     if window is None:
         window = (0, cam.width - 1, 0, cam.height - 1)
     px0, px1, py0, py1 = (int(v) for v in window)
-    st = lib.orc_render_abstract(*[_p(a) for a in s], scene.n, _p(intr), _p(R0), _p(t0),
-                                 _p(_d(cell_lo).reshape(6)), _p(_d(cell_hi).reshape(6)),
-                                 px0, px1, py0, py1, _p(lo), _p(hi), _p(frag), _p(cond))
+    fn = lib.orc_render_abstract_tight if tight else lib.orc_render_abstract
+    st = fn(*[_p(a) for a in s], scene.n, _p(intr), _p(R0), _p(t0),
+            _p(_d(cell_lo).reshape(6)), _p(_d(cell_hi).reshape(6)),
+            px0, px1, py0, py1, _p(lo), _p(hi), _p(frag), _p(cond))
     if st:
         raise RuntimeError("oracle abstract render failed")
     return (lo, hi, frag, cond) if with_cond else (lo, hi, frag)
+
+
+def transmittance_chain(L, alo, ahi):
+    """Relational upper transmittance of a chain of factors (1 - a_j), taken
+    in the given order: L [K, 7] lower opacity forms (six coefficients, then
+    the constant), alo / ahi [K].  Returns (F [7], y_hi): F(p) >= prod (1 - a_j)
+    for every p in [-1, 1]^6 and every a_j in [max(alo_j, L_j(p)), ahi_j]."""
+    lib = _load()
+    L = np.ascontiguousarray(L, dtype=np.float64).reshape(-1, 7)
+    alo = np.ascontiguousarray(alo, dtype=np.float64).reshape(-1)
+    ahi = np.ascontiguousarray(ahi, dtype=np.float64).reshape(-1)
+    F = np.zeros(7)
+    yhi = np.zeros(1)
+    lib.orc_transmittance_chain(_p(L), _p(alo), _p(ahi), int(L.shape[0]), _p(F), _p(yhi))
+    return F, float(yhi[0])
 
 
 def render_abstract_sort(scene, cam, cell_lo, cell_hi, window=None):

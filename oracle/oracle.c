@@ -933,12 +933,92 @@ static void blend_sort_abstract(const grec *G, const int64_t *idx, const galpha 
     free(rmax);
 }
 
+/* Upper transmittance of the a-th Gaussian of a pixel as an affine form
+ * (transmittance kept relational in the pose, upper side):
+ * T(i) = prod over j certainly in front of i (k_hi(j) < k_lo(i)) of (1 - a_j),
+ * the factors taken in increasing k_hi(j) (ties by Gaussian index), which is
+ * the order in which a depth sweep meets their upper endpoints; `order` lists
+ * the pixel's Gaussians in that order.  With the running product y <= y_hi
+ * bounded above by the form F and the next factor x = 1 - a_j in
+ * [1 - a_hi(j), 1 - a_lo(j)] bounded above by the form X_j, the McCormick
+ * plane (y_hi - y)(x - x_lo) >= 0 gives
+ *   y x <= y_hi X_j + x_lo (F - y_hi),
+ * sound because y_hi >= 0 and x_lo >= 0 weight upper bounds.  y_hi is the
+ * interval product, updated alongside.  X_j = 1 - L_j where a_lo(j) > 0 (there
+ * L_j >= a_lo(j) on the whole cell, so X_j <= 1 - a_lo(j)), else the constant
+ * 1; then F <= y_hi at every pose, step by step, and the term the colour sum
+ * gains from F is never positive.  Returns F and y_hi. */
+/* One factor of the chain below: F <- y_hi X + x_lo (F - y_hi), then
+ * y_hi <- y_hi (1 - a_lo), with x_lo = 1 - a_hi and X = 1 - L where a_lo > 0,
+ * else 1. */
+static void transmittance_step(lf *F, double *yhi, const lf *L, double alo, double ahi)
+{
+    const double xlo = 1.0 - ahi;
+    lf X = lf_cst(1.0);
+    if (alo > 0.0) {
+        X = lf_scale(L, -1.0);
+        X.k += 1.0;
+    }
+    lf t1 = lf_scale(&X, *yhi);
+    F->k -= *yhi;
+    lf t2 = lf_scale(F, xlo);
+    *F = lf_add(&t1, &t2);
+    *yhi *= 1.0 - alo;
+}
+
+static void upper_transmittance(const grec *G, const int64_t *idx, const galpha *A, const int64_t *order, int64_t K,
+                                int64_t a, lf *F_out, double *yhi_out)
+{
+    const grec *gi = &G[idx[a]];
+    lf F = lf_cst(1.0);
+    double yhi = 1.0;
+    for (int64_t u = 0; u < K && G[idx[order[u]]].khi < gi->klo; ++u) {
+        const galpha *Aj = &A[order[u]];
+        transmittance_step(&F, &yhi, &Aj->L, Aj->alo, Aj->ahi);
+    }
+    *F_out = F;
+    *yhi_out = yhi;
+}
+
+/* The chain of upper_transmittance on given factors (for tests): K factors
+ * with lower opacity forms L (K x 7: six coefficients, then the constant)
+ * and opacity bounds [alo, ahi]; F (7 doubles) and y_hi out. */
+int orc_transmittance_chain(const double *L, const double *alo, const double *ahi, int K, double *F_out,
+                            double *yhi_out)
+{
+    lf F = lf_cst(1.0);
+    double yhi = 1.0;
+    for (int j = 0; j < K; ++j) {
+        lf Lj;
+        for (int v = 0; v < NV; ++v) Lj.c[v] = L[7 * j + v];
+        Lj.k = L[7 * j + 6];
+        transmittance_step(&F, &yhi, &Lj, alo[j], ahi[j]);
+    }
+    for (int v = 0; v < NV; ++v) F_out[v] = F.c[v];
+    F_out[6] = F.k;
+    *yhi_out = yhi;
+    return 0;
+}
+
+/* the pixel's Gaussians by increasing (k_hi, Gaussian index) */
+static const grec *g_sort_G;
+static const int64_t *g_sort_idx;
+#pragma omp threadprivate(g_sort_G, g_sort_idx)
+static int by_khi(const void *x, const void *y)
+{
+    const int64_t a = *(const int64_t *)x, b = *(const int64_t *)y;
+    const double ka = g_sort_G[g_sort_idx[a]].khi, kb = g_sort_G[g_sort_idx[b]].khi;
+    if (ka != kb) return ka < kb ? -1 : 1;
+    return g_sort_idx[a] < g_sort_idx[b] ? -1 : (g_sort_idx[a] > g_sort_idx[b]);
+}
+
 static int render_abstract_impl(const double *uw, const double *ls, const double *quat, const double *opac,
                                 const double *rgb, int64_t n, const double *intr, const double *R0,
                                 const double *t0, const double *cell_lo, const double *cell_hi,
                                 int px0, int px1, int py0, int py1, double *out_lo, double *out_hi,
-                                uint8_t *fragile, double *cond, int sort_blend)
+                                uint8_t *fragile, double *cond, int blend_mode)
 {
+    const int sort_blend = blend_mode == 1, tight = blend_mode == 2;
     camera cam = make_camera(intr, R0, t0);
     cellforms cf;
     cell_setup(&cam, cell_lo, cell_hi, &cf);
@@ -996,6 +1076,15 @@ static int render_abstract_impl(const double *uw, const double *ls, const double
          * front (not certainly behind), T_hi over j certainly in front */
         lf lo[3], hi[3];
         double est = 0.0;
+        int64_t *order = NULL;
+        if (tight) {
+            order = (int64_t *)malloc(sizeof(int64_t) * (size_t)(K > 0 ? K : 1));
+            if (!order) { status = 1; free(idx); free(A); continue; }
+            for (int64_t u = 0; u < K; ++u) order[u] = u;
+            g_sort_G = G;
+            g_sort_idx = idx;
+            qsort(order, (size_t)K, sizeof(int64_t), by_khi);
+        }
         for (int ch = 0; ch < 3; ++ch) { lo[ch] = lf_cst(0); hi[ch] = lf_cst(0); }
         for (int64_t a = 0; a < K; ++a) {
             const grec *gi = &G[idx[a]];
@@ -1017,11 +1106,26 @@ static int render_abstract_impl(const double *uw, const double *ls, const double
                 double da = 0.5 * em * ((A[a].mlo > 0 ? A[a].ahi : 0.0) + A[a].alo);
                 est += 2.0 * Thi * da;
             }
+            /* relational upper transmittance: FU(p) >= T(i) at every pose */
+            lf dU = lf_cst(0.0);
+            if (tight) {
+                lf FU;
+                double PB;
+                upper_transmittance(G, idx, A, order, K, a, &FU, &PB);
+                /* McCormick upper plane of T a: T_hi U + a_lo (FU - T_hi) */
+                FU.k -= PB;
+                dU = lf_scale(&FU, A[a].alo);
+                Thi = PB;
+            }
             for (int ch = 0; ch < 3; ++ch) {
                 /* colour in [c_lo, c_hi] and L', U' >= 0 over the cell */
                 lf t = lf_scale(&A[a].L, Tlo * gi->c_lo[ch]);
                 lo[ch] = lf_add(&lo[ch], &t);
                 t = lf_scale(&A[a].U, Thi * gi->c_hi[ch]);
+                if (tight) {
+                    lf t2 = lf_scale(&dU, gi->c_hi[ch]);
+                    t = lf_add(&t, &t2);
+                }
                 hi[ch] = lf_add(&hi[ch], &t);
             }
         }
@@ -1032,6 +1136,7 @@ static int render_abstract_impl(const double *uw, const double *ls, const double
         }
         if (fragile) fragile[(size_t)py * cam.W + px] = (uint8_t)frag;
         if (cond) cond[(size_t)py * cam.W + px] = est;
+        free(order);
         free(idx); free(A);
     }
     free(G);
@@ -1046,6 +1151,17 @@ int orc_render_abstract(const double *uw, const double *ls, const double *quat, 
 {
     return render_abstract_impl(uw, ls, quat, opac, rgb, n, intr, R0, t0, cell_lo, cell_hi, px0, px1, py0, py1,
                                 out_lo, out_hi, fragile, cond, 0);
+}
+
+/* The same with the relational upper transmittance of upper_transmittance. */
+int orc_render_abstract_tight(const double *uw, const double *ls, const double *quat, const double *opac,
+                              const double *rgb, int64_t n, const double *intr, const double *R0,
+                              const double *t0, const double *cell_lo, const double *cell_hi,
+                              int px0, int px1, int py0, int py1, double *out_lo, double *out_hi,
+                              uint8_t *fragile, double *cond)
+{
+    return render_abstract_impl(uw, ls, quat, opac, rgb, n, intr, R0, t0, cell_lo, cell_hi, px0, px1, py0, py1,
+                                out_lo, out_hi, fragile, cond, 2);
 }
 
 /* The same with the abstract BlendSort of blend_sort_abstract (Example 2). */

@@ -676,3 +676,76 @@ def test_abstract_blendsort_sound(orc, h):
     worst, nv = orc.check_samples(w.scene, w.camera, synth.sample_poses(rng, w.cells_lo[0], w.cells_hi[0], 2000),
                                   slo, shi, tol=1e-12)
     assert nv == 0, worst
+
+
+# ------------------------------------- relational upper transmittance (tight)
+
+def test_transmittance_chain_closed_forms(orc):
+    # one factor: F = 1 - L where a_lo > 0, else the constant 1
+    F, y = orc.transmittance_chain([_form([0.1], 0.3)], [0.2], [0.4])
+    assert np.allclose(F, _form([-0.1], 0.7), atol=1e-15) and y == pytest.approx(0.8)
+    F, y = orc.transmittance_chain([_form([0.3], 0.1)], [0.0], [0.4])
+    assert np.allclose(F, _form([], 1.0), atol=1e-15) and y == 1.0
+    # two factors, worked by hand: L1 = 0.1 p0 + 0.3 on [0.2, 0.4],
+    # L2 = -0.05 p1 + 0.5 on [0.45, 0.6].  After the first, F = 0.7 - 0.1 p0 and
+    # y = 0.8; then F = 0.8 (0.5 + 0.05 p1) + 0.4 (0.7 - 0.1 p0 - 0.8)
+    #                = 0.36 - 0.04 p0 + 0.04 p1, y = 0.8 * 0.55 = 0.44
+    F, y = orc.transmittance_chain([_form([0.1], 0.3), _form([0, -0.05], 0.5)], [0.2, 0.45], [0.4, 0.6])
+    assert np.allclose(F, _form([-0.04, 0.04], 0.36), atol=1e-15) and y == pytest.approx(0.44)
+    # at p = (1, -1) the product is at most 0.6 * 0.45 = 0.27: F gives 0.28,
+    # the interval product 0.44
+    assert _eval(F, np.array([1, -1, 0, 0, 0, 0])) == pytest.approx(0.28)
+
+
+def test_transmittance_chain_point_forms_are_the_interval_product(orc):
+    # constant forms (a point cell): the chain is the interval product
+    rng = np.random.default_rng(11)
+    a = rng.uniform(0.05, 0.6, 8)
+    L = np.stack([_form([], v) for v in a])
+    F, y = orc.transmittance_chain(L, a, a)
+    assert np.allclose(F[:6], 0.0) and F[6] == pytest.approx(np.prod(1 - a), rel=1e-12)
+    assert y == pytest.approx(np.prod(1 - a), rel=1e-12)
+
+
+def test_transmittance_chain_sound_and_below_interval_product(orc):
+    # brute force: random chains of lower forms over three active variables;
+    # the product is largest where every a_j takes its least consistent value
+    rng = np.random.default_rng(12)
+    for trial in range(40):
+        K = int(rng.integers(1, 9))
+        L, alo, ahi = [], [], []
+        for _ in range(K):
+            c = rng.uniform(-0.08, 0.08, 3)
+            k = rng.uniform(0.0, 0.5)
+            lo_v = k - np.abs(c).sum()
+            L.append(_form(c, k))
+            alo.append(max(0.0, lo_v))
+            ahi.append(min(0.95, k + np.abs(c).sum() + rng.uniform(0, 0.2)))
+        F, y = orc.transmittance_chain(np.stack(L), alo, ahi)
+        assert F[6] + np.abs(F[:6]).sum() <= y + 1e-12          # never above the interval product
+        P = rng.uniform(-1, 1, (300, 6))
+        P[:, 3:] = 0.0
+        P[:8, :3] = np.array([[sx, sy, sz] for sx in (-1, 1) for sy in (-1, 1) for sz in (-1, 1)])
+        for p in P:
+            amin = np.array([max(alo[j], _eval(L[j], p)) for j in range(K)])
+            assert np.prod(1 - amin) <= _eval(F, p) + 1e-12
+
+
+def test_tight_blend_never_looser_and_sound(orc):
+    # the relational upper transmittance only lowers the upper bound, and the
+    # bounds stay sound at sampled poses
+    w = synth.tiny64()
+    lo, hi, _ = orc.render_abstract(w.scene, w.camera, w.cells_lo[0], w.cells_hi[0])
+    tlo, thi, _ = orc.render_abstract(w.scene, w.camera, w.cells_lo[0], w.cells_hi[0], tight=True)
+    assert np.array_equal(lo, tlo)
+    assert np.all(thi <= hi + 1e-12)
+    assert (thi - tlo).mean() < 0.9 * (hi - lo).mean()
+    rng = np.random.default_rng(13)
+    worst, nv = orc.check_samples(w.scene, w.camera, synth.sample_poses(rng, w.cells_lo[0], w.cells_hi[0], 2000),
+                                  tlo, thi, tol=1e-12)
+    assert nv == 0, worst
+    # a point cell: every form is constant and both blends agree
+    d = np.array([0.004, -0.003, 0.01, 0.002, -0.004, 0.003])
+    lo, hi, _ = orc.render_abstract(w.scene, w.camera, d, d)
+    tlo, thi, _ = orc.render_abstract(w.scene, w.camera, d, d, tight=True)
+    assert np.array_equal(lo, tlo) and np.abs(hi - thi).max() < 1e-12
