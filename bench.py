@@ -46,9 +46,9 @@ def flops_per_triple(M: int) -> int:
 # 300k-Gaussian workload: 44.2 MB over 73.0M evaluations.  Valid only for the
 # kernel sources it was taken from (their SHA-256 below); otherwise the
 # roofline's traffic is reported as null.
-RENDER_TRAFFIC = {"bytes_per_evaluation": (30953472 + 13228800) / 73014342,
+RENDER_TRAFFIC = {"bytes_per_evaluation": (30877184 + 13303552) / 73014342,
                   "sources": ["k_render.cuh", "ar_num.cuh", "ar_common.cuh", "k_inst.cuh"],
-                  "sha256": "f055e330a68e09e9b9110b26b7556321ef1d63cbcc92fded137b1eed2c06501d"}
+                  "sha256": "3ddccd08301b56bbb0c4608b5b55c1370b731bf9b79b96ad6c728a0dc5894746"}
 
 
 def render_traffic(n_evaluated: int):
@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-window", type=int, default=16, help="edge of the oracle's pixel sample")
     ap.add_argument("--cells", type=int, default=0, help="use only the first N cells (profiling slices)")
+    ap.add_argument("--relational-steps", type=int, default=2,
+                    help="timed steps of the relational-transmittance blend (0: skip)")
     ap.add_argument("--serve-requests", type=int, default=32, help="requests in the serving mix (0: skip)")
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-budget-gb", type=float, default=96.0)
@@ -210,6 +212,53 @@ def plain_path(ar, s, w, intr, pose, args, sp, value):
     return {"value": pv, "unit": UNIT, "cells": k, "ms": ms, "dtype": "f64", "warmup": 1, "steps": 1,
             "stages_ms": {"prep": st["ms_prep"], "bin": st["ms_bin"], "render": st["ms_render"]},
             "speedup": value / pv}
+
+
+def relational(ar, s, w, intr, pose, cells, nc, args, sp, out_lo, out_hi, value):
+    """The relational upper transmittance (AR_BLEND_RELATIONAL) on the same
+    workload: W warm-up and K timed steps with CUDA events, the mean bounds of
+    both blends (out_lo / out_hi hold the interval blend's last step), and the
+    same on the first cell shrunk to a twentieth of its widths, where the bounds
+    are no longer saturated."""
+    import numpy as np
+    import torch
+    stream = torch.cuda.current_stream()
+    mean_int = (float(out_lo.double().mean()), float(out_hi.double().mean()))
+    ar.ar_scene_set_blend(s.handle, ar.AR_BLEND_RELATIONAL)
+    try:
+        for _ in range(args.warmup):
+            ar.ar_render_abstract(s.handle, intr, pose, cells, nc, args.tile, out_lo, out_hi, sp)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.relational_steps):
+            ar.ar_render_abstract(s.handle, intr, pose, cells, nc, args.tile, out_lo, out_hi, sp)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / args.relational_steps
+        st = ar.ar_last_render_stats(s.handle)
+        mean_rel = (float(out_lo.double().mean()), float(out_hi.double().mean()))
+        # one small cell: the first cell's centre with a twentieth of its widths
+        c = 0.5 * (w.cells_lo[0] + w.cells_hi[0])
+        h = 0.025 * (w.cells_hi[0] - w.cells_lo[0])
+        small = ar.make_cells((c - h)[None], (c + h)[None])
+        cam = w.camera
+        o_lo = torch.empty((1, cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
+        o_hi = torch.empty_like(o_lo)
+        widths = {}
+        for name, mode in (("interval", ar.AR_BLEND_INTERVAL), ("relational", ar.AR_BLEND_RELATIONAL)):
+            ar.ar_scene_set_blend(s.handle, mode)
+            ar.ar_render_abstract(s.handle, intr, pose, small, 1, args.tile, o_lo, o_hi, sp)
+            torch.cuda.synchronize()
+            widths[name] = float((o_hi - o_lo).double().mean())
+    finally:
+        ar.ar_scene_set_blend(s.handle, ar.AR_BLEND_INTERVAL)
+    pv = w.pixel_cells() / (ms / 1e3)
+    return {"value": pv, "unit": UNIT, "ms_per_step": ms, "warmup": args.warmup, "steps": args.relational_steps,
+            "vs_interval": pv / value, "render_ms": st["ms_render"], "evaluated": st["n_evaluated"],
+            "mean_lower": {"interval": mean_int[0], "relational": mean_rel[0]},
+            "mean_upper": {"interval": mean_int[1], "relational": mean_rel[1]},
+            "small_cell_mean_width": widths}
 
 
 def serving(ar, args, sp):
@@ -395,6 +444,8 @@ def run_ours(args, rank, world, local, pg):
                    "evaluated": stats["n_evaluated"], "reevaluated": stats["n_reevaluated"],
                    "fallback": stats["n_fallback"], "split": stats["n_split"], "built": stats["n_built"], "restarted": stats["n_restarted"]},
     }
+    if args.relational_steps > 0:
+        line["relational"] = relational(ar, s, w, intr, pose, cells, nc, args, sp, out_lo, out_hi, value)
     if args.plain_cells > 0:
         line["plain_path"] = plain_path(ar, s, w, intr, pose, args, sp, value)
     if args.serve_requests > 0:

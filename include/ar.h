@@ -236,6 +236,26 @@ int ar_set_workspace_limit(ar_scene *scene, int64_t bytes);
 /* Stage timing with CUDA events on the render stream (on = 1) or off (0). */
 int ar_set_profiling(ar_scene *scene, int on);
 
+/* Blend of the scene's abstract renders (ar_render_abstract, _host, _noalloc
+ * and serving; the plain FP64 path always uses AR_BLEND_INTERVAL):
+ *   AR_BLEND_INTERVAL (default): BlendInd of Algorithm 4 with Prod bounded by
+ *     interval products.
+ *   AR_BLEND_RELATIONAL: the same, except that the transmittance of the upper
+ *     bound is kept as an affine form in the pose, a McCormick product of the
+ *     front Gaussians' opacity forms taken in depth order.  The extra term it
+ *     adds is never positive, so every upper bound is at most the interval
+ *     one (tighter where the cell is small enough that the bounds are not
+ *     saturated); the lower bounds are the same.  Where the constants of
+ *     the interval blend's upper terms alone reach 1 in every channel, the
+ *     upper bound is 1 in both modes (the sweep stops there).  A Gaussian
+ *     whose lower depth key equals the upper key of one absorbed earlier in
+ *     its group of equal keys takes the interval term.
+ * The mode applies to renders issued after the call.  AR_EINVAL for a null
+ * scene or an unknown mode. */
+#define AR_BLEND_INTERVAL 0
+#define AR_BLEND_RELATIONAL 1
+int ar_scene_set_blend(ar_scene *scene, int32_t mode);
+
 /* Counters and stage times of the scene's last render (synchronises its stream). */
 int ar_last_render_stats(ar_scene *scene, ar_render_stats *stats);
 

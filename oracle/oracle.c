@@ -1075,7 +1075,7 @@ static int render_abstract_impl(const double *uw, const double *ls, const double
         /* BlendInd with interval Prod: for each i, T_lo over j that may be in
          * front (not certainly behind), T_hi over j certainly in front */
         lf lo[3], hi[3];
-        double est = 0.0;
+        double est = 0.0, kplain[3] = {0.0, 0.0, 0.0};
         int64_t *order = NULL;
         if (tight) {
             order = (int64_t *)malloc(sizeof(int64_t) * (size_t)(K > 0 ? K : 1));
@@ -1122,6 +1122,7 @@ static int render_abstract_impl(const double *uw, const double *ls, const double
                 lf t = lf_scale(&A[a].L, Tlo * gi->c_lo[ch]);
                 lo[ch] = lf_add(&lo[ch], &t);
                 t = lf_scale(&A[a].U, Thi * gi->c_hi[ch]);
+                kplain[ch] += t.k;
                 if (tight) {
                     lf t2 = lf_scale(&dU, gi->c_hi[ch]);
                     t = lf_add(&t, &t2);
@@ -1133,6 +1134,17 @@ static int render_abstract_impl(const double *uw, const double *ls, const double
         for (int ch = 0; ch < 3; ++ch) {
             out_lo[o + ch] = clamp01(lf_min(&lo[ch]));
             out_hi[o + ch] = clamp01(lf_max(&hi[ch]));
+        }
+        if (tight) {
+            /* saturation: where the constants of the interval terms alone sum
+             * to 1 or more in every channel, the interval blend's upper bound
+             * is 1 and the relational one is taken as 1 too (a sweep can stop
+             * there, as it does for the interval blend).  Near the threshold
+             * the single-precision sums may decide the other way: fragile. */
+            const double kmin = fmin(kplain[0], fmin(kplain[1], kplain[2]));
+            if (kmin >= 1.0)
+                for (int ch = 0; ch < 3; ++ch) out_hi[o + ch] = 1.0;
+            if (fabs(kmin - 1.0) < 1e-3) frag = 1;
         }
         if (fragile) fragile[(size_t)py * cam.W + px] = (uint8_t)frag;
         if (cond) cond[(size_t)py * cam.W + px] = est;

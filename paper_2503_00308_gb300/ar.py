@@ -72,6 +72,7 @@ def lib():
             "ar_debug_records": ([P, P, P, P, P], ctypes.c_int),
             "ar_scene_set_boxes": ([P, P, P, P, P, P, P], ctypes.c_int),
             "ar_set_profiling": ([P, ctypes.c_int], ctypes.c_int),
+            "ar_scene_set_blend": ([P, ctypes.c_int32], ctypes.c_int),
             "ar_set_workspace_limit": ([P, c_int64], ctypes.c_int),
             "ar_last_render_stats": ([P, P], ctypes.c_int),
             "ar_serve_create": ([c_int64, c_int32, P], ctypes.c_int),
@@ -193,6 +194,13 @@ def ar_set_workspace_limit(scene, nbytes: int):
 
 def ar_set_profiling(scene, on: bool):
     return check(lib().ar_set_profiling(scene, 1 if on else 0))
+
+
+AR_BLEND_INTERVAL, AR_BLEND_RELATIONAL = 0, 1
+
+
+def ar_scene_set_blend(scene, mode: int):
+    return check(lib().ar_scene_set_blend(scene, int(mode)))
 
 
 def ar_last_render_stats(scene) -> dict:

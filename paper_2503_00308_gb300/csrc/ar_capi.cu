@@ -385,6 +385,14 @@ int ar_set_profiling(ar_scene *s, int on)
     return AR_OK;
 }
 
+int ar_scene_set_blend(ar_scene *s, int32_t mode)
+{
+    if (!s) return fail(AR_EINVAL, "scene is null");
+    if (mode != AR_BLEND_INTERVAL && mode != AR_BLEND_RELATIONAL) return fail(AR_EINVAL, "unknown blend mode %d", mode);
+    s->blend = mode;
+    return AR_OK;
+}
+
 // ---------------------------------------------------------------- render
 namespace ar {
 
@@ -543,6 +551,7 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
     rl.W = W; rl.H = H; rl.ntx = ntx; rl.n_tiles = n_tiles; rl.n_cells = n_cells;
     rl.n_gauss = s->n;
     rl.k_open = s->k_open;
+    rl.rel = s->blend == AR_BLEND_RELATIONAL;
     rl.out_lo = out_lo;
     rl.out_hi = out_hi;
     rl.counters = ws.counters.as<unsigned long long>() + 8 + kCountersPerBatch * batch;

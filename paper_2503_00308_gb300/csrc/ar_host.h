@@ -88,6 +88,7 @@ struct ar_scene {
     int64_t ws_limit = int64_t(64) << 30;  // workspace limit that sizes the cell batches
     ar::Workspace ws;
     bool profiling = false;
+    int blend = AR_BLEND_INTERVAL;  // blend of the abstract renders (ar_scene_set_blend)
     ar_render_stats stats;
     cudaStream_t stats_stream = nullptr;
     // tile edges chosen by the autotuner, per (width, height, pose variables)

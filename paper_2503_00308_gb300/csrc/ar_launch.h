@@ -28,6 +28,7 @@ struct RenderLaunch {
     unsigned long long *counters;     // optional: [0] opacity evaluations, [1] re-evaluations,
                                       // [5] segments abandoned for a wider window ([2]-[4]: record build)
     unsigned int *work;               // segment counter of the persistent grid (zeroed by the launcher)
+    int rel = 0;                      // 1: relational upper transmittance (AR_BLEND_RELATIONAL)
 };
 
 size_t cell_data_bytes(int M);

@@ -212,6 +212,7 @@ int ar_render_abstract_noalloc(ar_scene *s, const ar_intrinsics *in, const ar_no
     rl.W = W; rl.H = H; rl.ntx = ntx; rl.n_tiles = n_tiles; rl.n_cells = n_cells;
     rl.n_gauss = s->n;
     rl.k_open = s->k_open;
+    rl.rel = s->blend == AR_BLEND_RELATIONAL;
     rl.out_lo = out_lower;
     rl.out_hi = out_upper;
     rl.counters = nullptr;

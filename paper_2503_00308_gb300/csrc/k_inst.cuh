@@ -61,7 +61,7 @@ int AR_CAT(launch_render_plain_m, AR_M)(int TS, const RenderLaunch &a, cudaStrea
     return TS == 16 ? launch_render_plain_ts<16>(a, st) : launch_render_plain_ts<8>(a, st);
 }
 
-template <int TS>
+template <int TS, bool REL>
 static int launch_render_ts(const RenderLaunch &a, cudaStream_t st)
 {
     // double-buffered chunks of 16 events and a ring of 4 (measured best of
@@ -69,7 +69,7 @@ static int launch_render_ts(const RenderLaunch &a, cudaStream_t st)
     // tile sooner with short chunks; the ring's shared memory stays small)
     constexpr int CH = 16, RING = 4;
     typedef RenderSmem<AR_M, TS, CH, RING> SM;
-    auto kern = render_kernel<AR_M, TS, CH, RING>;
+    auto kern = render_kernel<AR_M, TS, CH, RING, REL>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::BYTES) != cudaSuccess)
         return 1;
     int dev = 0, sms = 0, per_sm = 0;
@@ -115,7 +115,8 @@ int AR_CAT(launch_record_build_m, AR_M)(const double *vN, const CallConst &cc, c
 
 int AR_CAT(launch_render_m, AR_M)(int TS, const RenderLaunch &a, cudaStream_t st)
 {
-    return TS == 16 ? launch_render_ts<16>(a, st) : launch_render_ts<8>(a, st);
+    if (a.rel) return TS == 16 ? launch_render_ts<16, true>(a, st) : launch_render_ts<8, true>(a, st);
+    return TS == 16 ? launch_render_ts<16, false>(a, st) : launch_render_ts<8, false>(a, st);
 }
 
 }  // namespace ar

@@ -16,7 +16,8 @@
 //                         colour form gains T_lo(i) c_i L_i.
 //
 // This is BlendInd (Algorithm 4) with Ind(d_i - d_j) three-valued from the
-// depth-key intervals and Prod bounded by interval products.  Products over
+// depth-key intervals and Prod bounded by interval products (REL = true adds
+// the relational upper transmittance of RelT below).  Products over
 // keys strictly below a value are running products over the sorted list;
 // endpoints with equal keys are handled as a group (queries before
 // absorptions) so strictness matches the pairwise definition.
@@ -267,6 +268,51 @@ template <int M, bool DN, class R = float> struct ColourAcc {
     }
 };
 
+// Relational upper transmittance (the AR_BLEND_RELATIONAL mode; a tighter
+// blend than the interval Prod of Algorithm 4).  F is an affine upper form of
+// the running product over the Gaussians already certainly in front, y its
+// interval bound (rounded up).  Each factor x = 1 - a_j, with x >= x_lo =
+// 1 - a_hi(j) and x <= X(p) (X = 1 - L_j where a_lo(j) > 0, so that X stays
+// below 1 - a_lo(j); else the constant 1), enters through the McCormick plane
+//   (y - prod)(x - x_lo) >= 0  =>  prod x <= y X + x_lo (F - y),
+// which is sound because y >= 0 and x_lo >= 0 weight upper bounds; step by
+// step F <= y at every pose of the cell.  The coefficients are rounded to
+// nearest: each is within 2u (1 + u) of |y L_j.c| + |x_lo F.c| (plus an
+// underflow term), so 2.01 u r2 + TINY bounds their total error, which the
+// constant takes; rF bounds sum |F.c|.
+template <int M> struct RelT {
+    LF<M, float> F;
+    float rF, y;
+    __device__ __forceinline__ void init()
+    {
+#pragma unroll
+        for (int j = 0; j < M; ++j) F.c[j] = 0.f;
+        F.k = 1.f;
+        rF = 0.f;
+        y = 1.f;
+    }
+    __device__ __forceinline__ void absorb(const LF<M, float> &L, float rL, float alo, float ahi)
+    {
+        const float xlo = __fsub_rd(1.f, ahi);
+        float k2 = __fmul_ru(xlo, __fsub_ru(F.k, y));
+        float r2 = __fmul_ru(xlo, rF);
+        if (alo > 0.f) {
+#pragma unroll
+            for (int j = 0; j < M; ++j) F.c[j] = __fmaf_rn(-y, L.c[j], __fmul_rn(xlo, F.c[j]));
+            k2 = __fadd_ru(k2, __fmul_ru(y, __fsub_ru(1.f, L.k)));
+            r2 = __fadd_ru(r2, __fmul_ru(y, rL));
+        } else {
+#pragma unroll
+            for (int j = 0; j < M; ++j) F.c[j] = __fmul_rn(xlo, F.c[j]);
+            k2 = __fadd_ru(k2, y);
+        }
+        const float e = __fmaf_ru(r2, 2.01f * Num<float>::U, Num<float>::TINY);
+        F.k = __fadd_ru(k2, e);
+        rF = __fadd_ru(r2, e);
+        y = __fmul_ru(y, __fsub_ru(1.f, alo));
+    }
+};
+
 struct EvInfo {
     uint32_t rec;   // record index within the cell
     uint32_t bits;  // bit 0: upper endpoint, bit 1: key equals the previous entry's key
@@ -359,7 +405,7 @@ template <int TS> struct RenderOcc {
 // the next round builds the records of a wider window and sweeps it again
 // from its start.  The sweep is deterministic, so the restarted segment
 // gives the same bounds it would have given in one pass.
-template <int M, int TS, int CH, int RING>
+template <int M, int TS, int CH, int RING, bool REL>
 __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kernel(
     const float *__restrict__ recs, const PixBox *__restrict__ boxes, const uint32_t *__restrict__ seg_start,
     const uint32_t *__restrict__ seg_end, const uint32_t *__restrict__ active, const uint32_t *__restrict__ n_active,
@@ -410,6 +456,17 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
         lo.init();
         hi.init();
         float PA = 1.f, PB = 1.f, PAp = 1.f, PBp = 1.f;
+        // relational mode: F of the Gaussians absorbed so far; rel_tie once
+        // one has been absorbed in the current group of equal keys (a query
+        // later in that group takes the interval term: the group's absorptions
+        // are not certainly in front of it)
+        RelT<M> rel;
+        bool rel_tie = false;
+        // relational mode: the constants of the interval terms alone (the
+        // upper sum of the interval blend); where they reach 1 in every
+        // channel the upper bound is taken as 1, as the interval blend's is
+        float hk[3] = {0.f, 0.f, 0.f};
+        if (REL) rel.init();
         int n_open = 0;      // Gaussians of this pixel between their two endpoints
         float open_w = 0.f;  // sum over them of a_hi / (1 - a_hi), rounded up
         uint32_t c_rec = 0xffffffffu;  // register copy of the latest evaluation
@@ -467,7 +524,7 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch) {
                     lo_zero = lo_zero && __fadd_ru(lo.upper_min(ch), elo2) <= 0.f;
-                    hi_one = hi_one && hi.k[ch] >= 1.f;
+                    hi_one = hi_one && (REL ? hk[ch] : hi.k[ch]) >= 1.f;
                 }
                 const bool lo_dec = lo_zero || elo2 <= EXIT_EPS;
                 const bool hi_dec = hi_one || ehi2 <= EXIT_EPS;
@@ -500,6 +557,7 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
                     PB = __fmul_ru(PB, PBp);
                     PAp = 1.f;
                     PBp = 1.f;
+                    rel_tie = false;
                 }
                 const PixBox bx = s_box[e];
                 if (px < bx.x0 || px > bx.x1 || py < bx.y0 || py > bx.y1) continue;
@@ -535,6 +593,16 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
                 const float colh[3] = {r[RL::COL_HI], r[RL::COL_HI + 1], r[RL::COL_HI + 2]};
                 if (lower) {
                     hi.add(PB, colh, cache.U, cache.rU);
+                    if (REL) {
+#pragma unroll
+                        for (int ch = 0; ch < 3; ++ch) hk[ch] = __fmaf_ru(__fmul_ru(PB, colh[ch]), cache.U.k, hk[ch]);
+                    }
+                    if (REL && !rel_tie && cache.alo > 0.f) {
+                        // McCormick plane of T a: PB U + a_lo (F - PB), F <= PB
+                        LF<M, float> D = rel.F;
+                        D.k = __fsub_ru(rel.F.k, PB);
+                        hi.add(cache.alo, colh, D, rel.rF);
+                    }
                     PAp = __fmul_rd(PAp, __fsub_rd(1.f, cache.ahi));
                     open_w = __fadd_ru(open_w, open_ratio_up(cache.ahi));
                     const int k = (int)(head % RING);
@@ -557,6 +625,10 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
                     }
                     lo.add(T, col, cache.L, cache.rL);
                     PBp = __fmul_ru(PBp, __fsub_ru(1.f, cache.alo));
+                    if (REL) {
+                        rel.absorb(cache.L, cache.rL, cache.alo, cache.ahi);
+                        rel_tie = true;
+                    }
                 }
             }
         }
@@ -570,6 +642,7 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
         if (sweep_hist && tid == 0) atomicAdd(&sweep_hist[min(swept / 32u, 255u)], 1u);
         evals += seg_evals;
         recomp += seg_recomp;
+        if (REL && hk[0] >= 1.f && hk[1] >= 1.f && hk[2] >= 1.f) hi_adj = -1.f;
         if (inside) {
             const size_t o = ((size_t)cell * H * W + (size_t)py * W + px) * 3;
 #pragma unroll

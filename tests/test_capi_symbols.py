@@ -40,3 +40,6 @@ def test_last_error_without_gpu_calls():
     with pytest.raises(ar.ArError) as e:
         ar.ar_scene_create(None, None, None, None, None, -1, 0)
     assert e.value.code == ar.AR_EINVAL
+    with pytest.raises(ar.ArError) as e:
+        ar.ar_scene_set_blend(None, ar.AR_BLEND_RELATIONAL)
+    assert e.value.code == ar.AR_EINVAL

@@ -1,0 +1,121 @@
+"""The relational upper transmittance (AR_BLEND_RELATIONAL) on the GPU:
+parity with the oracle's tight blend, never looser than the interval blend,
+and sound at sampled poses.
+
+Tolerance as in test_gpu_parity: |gpu - oracle| <= 1e-4 + cond per channel,
+at most 0.1 % of the compared pixels above the plain 1e-4, fragile pixels
+checked for soundness only.  Against the interval blend on the GPU the upper
+bound may exceed it only by the early-exit widening (each side stops within
+1e-5 of its full sweep, and the two modes may stop at different events)."""
+import numpy as np
+import pytest
+
+from paper_2503_00308_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+EXIT = 2e-5
+
+
+@pytest.fixture(scope="module")
+def arlib():
+    from paper_2503_00308_gb300 import _build, ar
+    _build.build()
+    assert torch.cuda.is_available()
+    return ar
+
+
+def render(ar, scene, cam, lo, hi, mode, tile=16):
+    lo = np.asarray(lo, dtype=np.float64).reshape(-1, 6)
+    hi = np.asarray(hi, dtype=np.float64).reshape(-1, 6)
+    s = ar.Scene(scene)
+    ar.ar_scene_set_blend(s.handle, mode)
+    out_lo = torch.full((lo.shape[0], cam.height, cam.width, 3), -7.0, dtype=torch.float32, device="cuda")
+    out_hi = torch.full_like(out_lo, -7.0)
+    s.render(cam, lo, hi, out_lo, out_hi, tile=tile)
+    torch.cuda.synchronize()
+    r = out_lo.double().cpu().numpy(), out_hi.double().cpu().numpy()
+    s.close()
+    return r
+
+
+def compare_tight(orc, scene, cam, lo_c, hi_c, glo, ghi):
+    olo, ohi, frag, cond = orc.render_abstract(scene, cam, lo_c, hi_c, with_cond=True, tight=True)
+    m = ~np.isnan(olo[..., 0])
+    ok = m & (frag == 0)
+    e = np.maximum(np.abs(glo - olo), np.abs(ghi - ohi)).max(axis=-1)
+    assert np.all(e[ok] <= TOL + cond[ok]), (e[ok] - cond[ok]).max()
+    assert (e[ok] > TOL).sum() / max(1, ok.sum()) <= 1e-3
+    return olo, ohi
+
+
+CASES = [
+    ("tiny64", lambda: (synth.tiny64().scene, synth.tiny64().camera, synth.tiny64().cells_lo, synth.tiny64().cells_hi)),
+    ("object2500_small_cells", lambda: (synth.object_scene(2500, 4), synth.look_camera(72, 56, 80.0, centre=(0, 0, -4)))
+     + synth.cell_grid([0.005, 0.0, 0.005, 0.0, 0.002, 0.0], [2, 1, 1, 1, 2, 1])),
+]
+
+
+@pytest.mark.parametrize("name,make", CASES)
+def test_relational_parity_and_never_looser(arlib, orc, name, make):
+    sc, cam, lo, hi = make()
+    ilo, ihi = render(arlib, sc, cam, lo, hi, arlib.AR_BLEND_INTERVAL)
+    rlo, rhi = render(arlib, sc, cam, lo, hi, arlib.AR_BLEND_RELATIONAL)
+    assert np.all(rlo >= 0) and np.all(rhi <= 1) and np.all(rlo <= rhi)
+    # the lower bounds are the interval blend's; the upper ones never above them
+    assert np.abs(rlo - ilo).max() <= EXIT
+    assert np.all(rhi <= ihi + EXIT)
+    for c in range(lo.shape[0]):
+        compare_tight(orc, sc, cam, lo[c], hi[c], rlo[c], rhi[c])
+    rng = np.random.default_rng(21)
+    c = lo.shape[0] - 1
+    worst, nv = orc.check_samples(sc, cam, synth.sample_poses(rng, lo[c], hi[c], 500), rlo[c], rhi[c])
+    assert nv == 0, worst
+
+
+def test_relational_tightens_tiny64(arlib, orc):
+    w = synth.tiny64()
+    ilo, ihi = render(arlib, w.scene, w.camera, w.cells_lo, w.cells_hi, arlib.AR_BLEND_INTERVAL)
+    rlo, rhi = render(arlib, w.scene, w.camera, w.cells_lo, w.cells_hi, arlib.AR_BLEND_RELATIONAL)
+    # measured on the oracle: the mean width falls by about 18 %
+    assert (rhi - rlo).mean() < 0.9 * (ihi - ilo).mean()
+    rng = np.random.default_rng(22)
+    poses = synth.sample_poses(rng, w.cells_lo[0], w.cells_hi[0], 4000)
+    worst, nv = orc.check_samples(w.scene, w.camera, poses, rlo[0], rhi[0], tol=0.0)
+    assert nv == 0, worst
+
+
+def test_relational_point_cell_matches_interval(arlib):
+    # at a point cell the forms are constants and the two blends agree
+    w = synth.tiny64()
+    d = np.array([0.004, -0.003, 0.01, 0.002, -0.004, 0.003])
+    ilo, ihi = render(arlib, w.scene, w.camera, d, d, arlib.AR_BLEND_INTERVAL)
+    rlo, rhi = render(arlib, w.scene, w.camera, d, d, arlib.AR_BLEND_RELATIONAL)
+    assert np.abs(rlo - ilo).max() <= EXIT and np.abs(rhi - ihi).max() <= EXIT
+
+
+def test_relational_other_entry_points(arlib):
+    # the host-buffer and no-allocation entry points honour the mode
+    ar = arlib
+    sc = synth.object_scene(1500, 6)
+    cam = synth.look_camera(50, 38, 60.0, centre=(0, 0, -4))
+    lo, hi = synth.cell_grid([0.005, 0.0, 0.005, 0.0, 0.002, 0.0], [2, 1, 1, 1, 1, 1])
+    ref_lo, ref_hi = render(ar, sc, cam, lo, hi, ar.AR_BLEND_RELATIONAL)
+    s = ar.Scene(sc)
+    ar.ar_scene_set_blend(s.handle, ar.AR_BLEND_RELATIONAL)
+    intr, pose, cells = ar.make_intrinsics(cam), ar.make_pose(cam), ar.make_cells(lo, hi)
+    shape = (lo.shape[0], cam.height, cam.width, 3)
+    h_lo = torch.empty(shape, dtype=torch.float32).pin_memory()
+    h_hi = torch.empty(shape, dtype=torch.float32).pin_memory()
+    ar.ar_render_abstract_host(s.handle, intr, pose, cells, lo.shape[0], 16, h_lo, h_hi)
+    assert np.array_equal(h_lo.double().numpy(), ref_lo) and np.array_equal(h_hi.double().numpy(), ref_hi)
+    d_lo = torch.empty(shape, dtype=torch.float32, device="cuda")
+    d_hi = torch.empty_like(d_lo)
+    ar.ar_render_abstract_noalloc(s.handle, intr, pose, cells, lo.shape[0], 16, d_lo, d_hi)
+    torch.cuda.synchronize()
+    assert np.array_equal(d_lo.double().cpu().numpy(), ref_lo) and np.array_equal(d_hi.double().cpu().numpy(), ref_hi)
+    with pytest.raises(ar.ArError):
+        ar.ar_scene_set_blend(s.handle, 7)
+    s.close()
