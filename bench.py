@@ -261,6 +261,42 @@ def relational(ar, s, w, intr, pose, cells, nc, args, sp, out_lo, out_hi, value)
             "small_cell_mean_width": widths}
 
 
+def hbm_peak():
+    """Measured HBM copy bandwidth (GB/s) of this machine's GPUs, else the fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def union_leg(ar, w, nc, args, sp, out_lo, out_hi):
+    """ar_bounds_union over the workload's cells (the bounds of the whole pose
+    box): W warm-ups and K timed launches with CUDA events.  The inputs (both
+    bound images of every cell) are far larger than L2."""
+    import torch
+    cam = w.camera
+    stream = torch.cuda.current_stream()
+    u_lo = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
+    u_hi = torch.empty_like(u_lo)
+    for _ in range(args.warmup):
+        ar.ar_bounds_union(out_lo, out_hi, nc, cam.width, cam.height, u_lo, u_hi, sp)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        ar.ar_bounds_union(out_lo, out_hi, nc, cam.width, cam.height, u_lo, u_hi, sp)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    n = cam.height * cam.width * 3
+    nbytes = 4 * (2 * nc * n + 2 * n)
+    peak, src = hbm_peak()
+    gbs = nbytes / (ms / 1e3) / 1e9
+    return {"ms": ms, "bytes_per_launch": nbytes, "achieved_gbs": gbs, "peak_gbs": peak, "peak_source": src,
+            "frac": gbs / peak, "launches": args.steps, "mean_width": float((u_hi - u_lo).double().mean())}
+
+
 def serving(ar, args, sp):
     """The serving mix: a seeded Poisson stream of requests over resident
     10k / 300k / 750k-Gaussian scenes (200x200 to 1280x720, 1 to 256 cells).
@@ -444,6 +480,7 @@ def run_ours(args, rank, world, local, pg):
                    "evaluated": stats["n_evaluated"], "reevaluated": stats["n_reevaluated"],
                    "fallback": stats["n_fallback"], "split": stats["n_split"], "built": stats["n_built"], "restarted": stats["n_restarted"]},
     }
+    line["union"] = union_leg(ar, w, nc, args, sp, out_lo, out_hi)
     if args.relational_steps > 0:
         line["relational"] = relational(ar, s, w, intr, pose, cells, nc, args, sp, out_lo, out_hi, value)
     if args.plain_cells > 0:

@@ -174,6 +174,39 @@ int ar_render_abstract_noalloc(ar_scene *scene, const ar_intrinsics *intr, const
                                const ar_pose_box *cells, int32_t n_cells, int32_t tile,
                                float *out_lower, float *out_upper, void *cuda_stream);
 
+/* Union of the bounds of several pose cells (Sec. 5: the bounds of a camera
+ * set partitioned into subsets are the subsets' bounds, joined).
+ *   in_lower, in_upper: DEVICE [n_cells][height][width][3] float32, as
+ *     ar_render_abstract writes them.
+ *   out_lower, out_upper: DEVICE [height][width][3] float32; out_lower gets
+ *     the elementwise minimum of in_lower over the cells, out_upper the
+ *     maximum of in_upper.  The outputs must not overlap the inputs or each
+ *     other.
+ * Enqueued on cuda_stream (no synchronisation).  One kernel launch, bound by
+ * HBM bandwidth.  Errors: AR_EINVAL (null pointers, n_cells < 1, sizes out of
+ * range, overlapping buffers), AR_EDEVICE. */
+int ar_bounds_union(const float *in_lower, const float *in_upper, int32_t n_cells, int32_t width, int32_t height,
+                    float *out_lower, float *out_upper, void *cuda_stream);
+
+/* Bounds of one pose box over all its poses, from a partition of the box
+ * (Sec. 5): the box is cut into parts[k] equal pieces along pose dimension k
+ * (dimension 0 varying fastest), the pieces are rendered as cells, in chunks
+ * of at most 64, and their bounds are joined as by ar_bounds_union.  Finer
+ * partitions give tighter bounds (Sec. 5) at proportional cost.
+ *   box: one pose box (the checks of ar_render_abstract's cells apply).
+ *   parts: 6 entries >= 1 whose product is at most 2^24; a dimension with
+ *     lo = hi takes 1.
+ *   out_lower, out_upper: DEVICE [height][width][3] float32.
+ * Piece k of n along a dimension is [lo + w k / n, lo + w (k + 1) / n], with
+ * w = hi - lo, and the last piece ends at hi exactly, so the pieces cover the
+ * box.  The scene's blend mode applies.  Chunk buffers come from the scene's
+ * workspace.  Synchronises with cuda_stream once per chunk (as
+ * ar_render_abstract does); the stats of ar_last_render_stats describe the
+ * last chunk.  Errors as for ar_render_abstract, and AR_EINVAL for bad parts. */
+int ar_render_abstract_partitioned(ar_scene *scene, const ar_intrinsics *intr, const ar_nominal_pose *pose,
+                                   const ar_pose_box *box, const int32_t *parts, int32_t tile, float *out_lower,
+                                   float *out_upper, void *cuda_stream);
+
 /* Plain comparison path: the same bounds computed one cell per launch
  * sequence in FP64 with directed rounding, without cell batching.  Same
  * arguments and output layout as ar_render_abstract. */

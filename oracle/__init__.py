@@ -161,6 +161,43 @@ def render_abstract(scene, cam, cell_lo, cell_hi, window=None, with_cond=False, 
     return (lo, hi, frag, cond) if with_cond else (lo, hi, frag)
 
 
+def partition_cells(box_lo, box_hi, parts):
+    """The pieces of a pose box cut into parts[k] equal pieces along dimension k
+    (dimension 0 varying fastest): piece i of n is [lo + w i / n, lo + w (i+1) / n]
+    with w = hi - lo, the last ending at hi.  Returns (lo [N, 6], hi [N, 6])."""
+    box_lo = _d(box_lo).reshape(6)
+    box_hi = _d(box_hi).reshape(6)
+    parts = [int(p) for p in parts]
+    n = int(np.prod(parts))
+    lo = np.empty((n, 6))
+    hi = np.empty((n, 6))
+    for r0 in range(n):
+        r = r0
+        for k in range(6):
+            P = parts[k]
+            i = r % P
+            r //= P
+            w = box_hi[k] - box_lo[k]
+            lo[r0, k] = box_lo[k] if i == 0 else box_lo[k] + w * float(i) / float(P)
+            hi[r0, k] = box_hi[k] if i + 1 == P else box_lo[k] + w * float(i + 1) / float(P)
+    return lo, hi
+
+
+def render_abstract_partitioned(scene, cam, box_lo, box_hi, parts, window=None, tight=False):
+    """Bounds of a pose box as the union of the bounds of its pieces (Sec. 5):
+    the elementwise minimum of the pieces' lower bounds and maximum of their
+    upper bounds.  Returns (lo, hi, fragile) like render_abstract; fragile marks
+    a pixel fragile in any piece."""
+    lo_c, hi_c = partition_cells(box_lo, box_hi, parts)
+    lo = hi = frag = None
+    for c in range(lo_c.shape[0]):
+        a, b, f = render_abstract(scene, cam, lo_c[c], hi_c[c], window=window, tight=tight)
+        lo = a if lo is None else np.minimum(lo, a)
+        hi = b if hi is None else np.maximum(hi, b)
+        frag = f if frag is None else np.maximum(frag, f)
+    return lo, hi, frag
+
+
 def transmittance_chain(L, alo, ahi):
     """Relational upper transmittance of a chain of factors (1 - a_j), taken
     in the given order: L [K, 7] lower opacity forms (six coefficients, then

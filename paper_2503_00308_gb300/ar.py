@@ -73,6 +73,8 @@ def lib():
             "ar_scene_set_boxes": ([P, P, P, P, P, P, P], ctypes.c_int),
             "ar_set_profiling": ([P, ctypes.c_int], ctypes.c_int),
             "ar_scene_set_blend": ([P, ctypes.c_int32], ctypes.c_int),
+            "ar_bounds_union": ([P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P], ctypes.c_int),
+            "ar_render_abstract_partitioned": ([P, P, P, P, P, ctypes.c_int32, P, P, P], ctypes.c_int),
             "ar_set_workspace_limit": ([P, c_int64], ctypes.c_int),
             "ar_last_render_stats": ([P, P], ctypes.c_int),
             "ar_serve_create": ([c_int64, c_int32, P], ctypes.c_int),
@@ -172,6 +174,20 @@ def ar_render_abstract_noalloc(scene, intr, pose, cells, n_cells, tile, out_lowe
     return check(lib().ar_render_abstract_noalloc(scene, ctypes.byref(intr), ctypes.byref(pose), cells,
                                                   int(n_cells), int(tile), _ptr(out_lower), _ptr(out_upper),
                                                   _ptr(stream)))
+
+
+def ar_bounds_union(in_lower, in_upper, n_cells, width, height, out_lower, out_upper, stream=0):
+    """Elementwise min / max over cells of device bounds [n_cells, H, W, 3] into [H, W, 3]."""
+    return check(lib().ar_bounds_union(_ptr(in_lower), _ptr(in_upper), int(n_cells), int(width), int(height),
+                                       _ptr(out_lower), _ptr(out_upper), _ptr(stream)))
+
+
+def ar_render_abstract_partitioned(scene, intr, pose, box, parts, tile, out_lower, out_upper, stream=0):
+    """Bounds of one pose box (an ar_pose_box) from parts[k] pieces along each
+    pose dimension, joined into device [H, W, 3] outputs."""
+    p = (ctypes.c_int32 * 6)(*[int(v) for v in parts])
+    return check(lib().ar_render_abstract_partitioned(scene, ctypes.byref(intr), ctypes.byref(pose), ctypes.byref(box),
+                                                      p, int(tile), _ptr(out_lower), _ptr(out_upper), _ptr(stream)))
 
 
 def ar_render_concrete(scene, intr, pose, deltas, n_poses, out, stream=0):

@@ -192,7 +192,7 @@ void Workspace::release()
     DevBuf *all[] = {&cells_lohi, &cells, &vN, &recs, &boxes, &keys, &counters, &evk0, &evk1, &evv0, &evv1,
                      &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege, &segk0,
                      &segk1, &segv0, &segv1, &work, &state, &wlist, &act0, &act1, &words, &slist, &whist, &out_lo,
-                     &out_hi};
+                     &out_hi, &part_lo, &part_hi};
     for (DevBuf *b : all) b->release();
     if (h_whist) cudaFreeHost(h_whist);
     h_whist = nullptr;
@@ -208,7 +208,7 @@ size_t Workspace::bytes() const
     const DevBuf *all[] = {&cells_lohi, &cells, &vN, &recs, &boxes, &keys, &counters, &evk0, &evk1, &evv0, &evv1,
                            &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege,
                            &segk0, &segk1, &segv0, &segv1, &work, &state, &wlist, &act0, &act1, &words,
-                           &slist, &whist, &out_lo, &out_hi};
+                           &slist, &whist, &out_lo, &out_hi, &part_lo, &part_hi};
     size_t s = 0;
     for (const DevBuf *b : all) s += b->cap;
     return s;
@@ -897,6 +897,78 @@ int ar_render_abstract_host(ar_scene *s, const ar_intrinsics *in, const ar_nomin
     CK(cudaMemcpyAsync(host_lower, s->ws.out_lo.p, bytes, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(host_upper, s->ws.out_hi.p, bytes, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    return AR_OK;
+}
+
+// true if [a, a + na) and [b, b + nb) (in floats) overlap
+static bool overlaps(const float *a, size_t na, const float *b, size_t nb)
+{
+    const uintptr_t a0 = (uintptr_t)a, a1 = a0 + na * sizeof(float);
+    const uintptr_t b0 = (uintptr_t)b, b1 = b0 + nb * sizeof(float);
+    return a0 < b1 && b0 < a1;
+}
+
+int ar_bounds_union(const float *in_lower, const float *in_upper, int32_t n_cells, int32_t width, int32_t height,
+                    float *out_lower, float *out_upper, void *stream)
+{
+    if (!in_lower || !in_upper || !out_lower || !out_upper) return fail(AR_EINVAL, "null argument");
+    if (n_cells < 1) return fail(AR_EINVAL, "n_cells must be >= 1");
+    if (width < 1 || height < 1 || width > 16384 || height > 16384) return fail(AR_EINVAL, "image size out of range");
+    const size_t n = (size_t)3 * width * height, nin = n * (size_t)n_cells;
+    if (overlaps(out_lower, n, in_lower, nin) || overlaps(out_lower, n, in_upper, nin) ||
+        overlaps(out_upper, n, in_lower, nin) || overlaps(out_upper, n, in_upper, nin) ||
+        overlaps(out_lower, n, out_upper, n))
+        return fail(AR_EINVAL, "overlapping buffers");
+    if (launch_bounds_union(in_lower, in_upper, n_cells, n, out_lower, out_upper, false, (cudaStream_t)stream))
+        return fail(AR_EDEVICE, "bounds_union launch: %s", cudaGetErrorString(cudaGetLastError()));
+    return AR_OK;
+}
+
+int ar_render_abstract_partitioned(ar_scene *s, const ar_intrinsics *in, const ar_nominal_pose *pose,
+                                   const ar_pose_box *box, const int32_t *parts, int32_t tile, float *out_lower,
+                                   float *out_upper, void *stream)
+{
+    if (!s || !parts) return fail(AR_EINVAL, "null argument");
+    if (!out_lower || !out_upper) return fail(AR_EINVAL, "null output");
+    RK(validate_call(in, pose, box, 1, tile));
+    int64_t total = 1;
+    for (int k = 0; k < MAXV; ++k) {
+        if (parts[k] < 1) return fail(AR_EINVAL, "parts[%d] must be >= 1", k);
+        if (parts[k] > 1 && !(box->hi[k] > box->lo[k])) return fail(AR_EINVAL, "parts[%d] > 1 on a point dimension", k);
+        total *= parts[k];
+        if (total > (int64_t)1 << 24) return fail(AR_EINVAL, "more than 2^24 pieces");
+    }
+    const size_t n = (size_t)3 * in->width * in->height;
+    if (overlaps(out_lower, n, out_upper, n)) return fail(AR_EINVAL, "overlapping outputs");
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(s->device));
+    // chunks of at most 64 pieces, and at most 2 GiB of chunk images
+    int64_t chunk = 64;
+    while (chunk > 1 && (size_t)chunk * n * sizeof(float) > ((size_t)1 << 30)) chunk /= 2;
+    if (chunk > total) chunk = total;
+    RK(s->ws.part_lo.ensure(sizeof(float) * n * (size_t)chunk));
+    RK(s->ws.part_hi.ensure(sizeof(float) * n * (size_t)chunk));
+    std::vector<ar_pose_box> cells((size_t)chunk);
+    for (int64_t c0 = 0; c0 < total; c0 += chunk) {
+        const int64_t nb = c0 + chunk <= total ? chunk : total - c0;
+        for (int64_t q = 0; q < nb; ++q) {
+            int64_t r = c0 + q;  // multi-index, dimension 0 fastest
+            ar_pose_box &b = cells[(size_t)q];
+            for (int k = 0; k < MAXV; ++k) {
+                const int64_t P = parts[k], i = r % P;
+                r /= P;
+                const double lo = box->lo[k], hi = box->hi[k], w = hi - lo;
+                b.lo[k] = i == 0 ? lo : lo + w * (double)i / (double)P;
+                b.hi[k] = i + 1 == P ? hi : lo + w * (double)(i + 1) / (double)P;
+            }
+        }
+        RK(render_core(s, s->ws, in, pose, cells.data(), (int32_t)nb, tile, s->ws.part_lo.as<float>(),
+                       s->ws.part_hi.as<float>(), st, s->profiling, &s->stats));
+        s->stats_stream = st;
+        if (launch_bounds_union(s->ws.part_lo.as<float>(), s->ws.part_hi.as<float>(), (int)nb, n, out_lower, out_upper,
+                                c0 > 0, st))
+            return fail(AR_EDEVICE, "bounds_union launch: %s", cudaGetErrorString(cudaGetLastError()));
+    }
     return AR_OK;
 }
 

@@ -32,7 +32,8 @@ struct Workspace {
     uint32_t *h_whist = nullptr;             // page-locked copy of the last render's histogram
     bool whist_pending = false;              // h_whist holds a render not yet learned from
     uint32_t w0 = 512;                       // first window of the windowed rounds
-    DevBuf out_lo, out_hi;
+    DevBuf out_lo, out_hi;      // staged outputs of ar_render_abstract_host
+    DevBuf part_lo, part_hi;    // chunk outputs of ar_render_abstract_partitioned
     unsigned long long *h_counters = nullptr;  // page-locked
     std::vector<cudaEvent_t> evs;              // 9 per cell batch (stage timing)
     int n_batches = 0;                         // cell batches of the last render

@@ -42,6 +42,10 @@ int launch_record_prep64(int M, const double *vN, const void *gp,
                          const CallConst &cc, const void *cells, int TS, double *recs, PixBox *boxes, double *keys,
                          unsigned long long *counters, cudaStream_t st);
 int launch_render_plain(int M, int TS, const RenderLaunch &a, cudaStream_t st);
+// union of the bounds of n_cells cells of n floats each (k_union.cu); acc: fold
+// the current outputs in too
+int launch_bounds_union(const float *lo, const float *hi, int n_cells, size_t n, float *out_lo, float *out_hi,
+                        bool acc, cudaStream_t st);
 // value parts of the records listed in work[0, *count); counters: [0] fallbacks, [1] built, [2] split.
 // split_list (list_cap >= *count entries), split_count and khigh_count (zeroed by the caller): pairs whose
 // MatrixInv fails on the cell are split by a warp each in a second kernel, pairs whose Taylor order exceeds

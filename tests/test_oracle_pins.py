@@ -749,3 +749,38 @@ def test_tight_blend_never_looser_and_sound(orc):
     lo, hi, _ = orc.render_abstract(w.scene, w.camera, d, d)
     tlo, thi, _ = orc.render_abstract(w.scene, w.camera, d, d, tight=True)
     assert np.array_equal(lo, tlo) and np.abs(hi - thi).max() < 1e-12
+
+
+# ------------------------------------------------------- partition and union
+
+def test_partition_pieces_cover_the_box(orc):
+    box_lo = np.array([-0.03, 0.0, -0.01, 0.0, -0.02, 0.0])
+    box_hi = np.array([0.03, 0.0, 0.05, 0.0, 0.02, 0.0])
+    lo, hi = orc.partition_cells(box_lo, box_hi, [3, 1, 2, 1, 4, 1])
+    assert lo.shape == (24, 6)
+    # per dimension the pieces tile [lo, hi] end to end, with equal widths
+    for k, P in enumerate([3, 1, 2, 1, 4, 1]):
+        edges = sorted(set(lo[:, k]) | set(hi[:, k]))
+        assert len(edges) == P + 1 or box_lo[k] == box_hi[k]
+        assert edges[0] == box_lo[k] and edges[-1] == box_hi[k]
+        assert np.allclose(np.diff(edges), (box_hi[k] - box_lo[k]) / P)
+    # dimension 0 varies fastest
+    assert lo[1, 0] > lo[0, 0] and lo[1, 2] == lo[0, 2]
+
+
+def test_partition_union_is_sound_and_tighter(orc):
+    # Sec. 5: bounds of the pieces, joined, bound the whole box, and finer
+    # partitions tighten them
+    w = synth.tiny64()
+    blo, bhi = w.cells_lo[0], w.cells_hi[0]
+    act = [int(v) for v in (bhi > blo)]
+    parts = [2 if a else 1 for a in act]
+    lo1, hi1, _ = orc.render_abstract(w.scene, w.camera, blo, bhi)
+    lo2, hi2, _ = orc.render_abstract_partitioned(w.scene, w.camera, blo, bhi, parts)
+    assert (hi2 - lo2).mean() < 0.9 * (hi1 - lo1).mean()
+    rng = np.random.default_rng(31)
+    worst, nv = orc.check_samples(w.scene, w.camera, synth.sample_poses(rng, blo, bhi, 2000), lo2, hi2, tol=1e-12)
+    assert nv == 0, worst
+    # one piece is the box itself
+    lo3, hi3, _ = orc.render_abstract_partitioned(w.scene, w.camera, blo, bhi, [1] * 6)
+    assert np.array_equal(lo3, lo1) and np.array_equal(hi3, hi1)
