@@ -123,6 +123,29 @@ template <int M, class R> struct LF {
     R k;
 };
 
+// c[j] = fma_rn(a, x[j], c[j]) for j < M.  For float, pairs of coefficients
+// go through the packed FMA of sm_100 and later (__ffma2_rn: per element the
+// same result as __fmaf_rn, two elements per instruction), which halves the
+// issue slots of the coefficient updates without changing a bit.
+template <int M, class R>
+__device__ __forceinline__ void axpy_rn(R a, const R *x, R *c)
+{
+#pragma unroll
+    for (int j = 0; j < M; ++j) c[j] = Num<R>::fma_rn(a, x[j], c[j]);
+}
+template <int M>
+__device__ __forceinline__ void axpy_rn(float a, const float *x, float *c)
+{
+    const float2 aa = make_float2(a, a);
+#pragma unroll
+    for (int j = 0; j + 1 < M; j += 2) {
+        const float2 r = __ffma2_rn(aa, make_float2(x[j], x[j + 1]), make_float2(c[j], c[j + 1]));
+        c[j] = r.x;
+        c[j + 1] = r.y;
+    }
+    if (M & 1) c[M - 1] = __fmaf_rn(a, x[M - 1], c[M - 1]);
+}
+
 // Accumulator of a sound form  sum_t a_t F_t + b  (one side).  DN = true for
 // a lower form (constant rounded down, slack subtracted), false for upper.
 template <int M, class R, bool DN> struct Acc {
@@ -148,8 +171,7 @@ template <int M, class R, bool DN> struct Acc {
     __device__ __forceinline__ void term_ck(R a, const R *Fc, R Fk, R r)
     {
         using N = Num<R>;
-#pragma unroll
-        for (int j = 0; j < M; ++j) f.c[j] = N::fma_rn(a, Fc[j], f.c[j]);
+        axpy_rn<M>(a, Fc, f.c);
         f.k = DN ? N::fma_rd(a, Fk, f.k) : N::fma_ru(a, Fk, f.k);
         rs = N::fma_ru(N::abs(a), r, rs);
         ++n;
@@ -158,8 +180,7 @@ template <int M, class R, bool DN> struct Acc {
     __device__ __forceinline__ void term(R a, const LF<M, R> &F, R r)
     {
         using N = Num<R>;
-#pragma unroll
-        for (int j = 0; j < M; ++j) f.c[j] = N::fma_rn(a, F.c[j], f.c[j]);
+        axpy_rn<M>(a, F.c, f.c);
         f.k = DN ? N::fma_rd(a, F.k, f.k) : N::fma_ru(a, F.k, f.k);
         rs = N::fma_ru(N::abs(a), r, rs);
         ++n;
@@ -252,8 +273,7 @@ template <int M, class R> struct SAcc {
     __device__ __forceinline__ void term(R a, const SB<M, R> &x)
     {
         using N = Num<R>;
-#pragma unroll
-        for (int j = 0; j < M; ++j) c[j] = N::fma_rn(a, x.c[j], c[j]);
+        axpy_rn<M>(a, x.c, c);
         if (a >= 0) {
             klo = N::fma_rd(a, x.klo, klo);
             khi = N::fma_ru(a, x.khi, khi);
@@ -270,8 +290,7 @@ template <int M, class R> struct SAcc {
     __device__ __forceinline__ void term_same_side(R a, const SB<M, R> &x)
     {
         using N = Num<R>;
-#pragma unroll
-        for (int j = 0; j < M; ++j) c[j] = N::fma_rn(a, x.c[j], c[j]);
+        axpy_rn<M>(a, x.c, c);
         klo = N::fma_rd(a, x.klo, klo);
         khi = N::fma_ru(a, x.khi, khi);
         rs = N::fma_ru(N::abs(a), x.r, rs);

@@ -236,8 +236,7 @@ template <int M, bool DN, class R = float> struct ColourAcc {
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
             const R w = DN ? N::mul_rd(T, col[ch]) : N::mul_ru(T, col[ch]);
-#pragma unroll
-            for (int j = 0; j < M; ++j) c[ch][j] = N::fma_rn(w, F.c[j], c[ch][j]);
+            axpy_rn<M>(w, F.c, c[ch]);
             k[ch] = DN ? N::fma_rd(w, F.k, k[ch]) : N::fma_ru(w, F.k, k[ch]);
         }
         const R t = N::mul_ru(T, rF);
