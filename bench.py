@@ -43,12 +43,12 @@ def flops_per_triple(M: int) -> int:
 
 # DRAM bytes of the render kernel per opacity evaluation, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the first 4 cells of the
-# 300k-Gaussian workload: 44.2 MB over 73.0M evaluations.  Valid only for the
+# 300k-Gaussian workload: 43.8 MB over 73.0M evaluations.  Valid only for the
 # kernel sources it was taken from (their SHA-256 below); otherwise the
 # roofline's traffic is reported as null.
-RENDER_TRAFFIC = {"bytes_per_evaluation": (30877184 + 13303552) / 73014342,
+RENDER_TRAFFIC = {"bytes_per_evaluation": (30896896 + 12922112) / 73014342,
                   "sources": ["k_render.cuh", "ar_num.cuh", "ar_common.cuh", "k_inst.cuh"],
-                  "sha256": "3ddccd08301b56bbb0c4608b5b55c1370b731bf9b79b96ad6c728a0dc5894746"}
+                  "sha256": "756d67ef4afa7d5f0c442fae7aaba8f751e2b434b7dae497b72e7dbb2d16afdf"}
 
 
 def render_traffic(n_evaluated: int):
@@ -259,6 +259,14 @@ def relational(ar, s, w, intr, pose, cells, nc, args, sp, out_lo, out_hi, value)
             "mean_lower": {"interval": mean_int[0], "relational": mean_rel[0]},
             "mean_upper": {"interval": mean_int[1], "relational": mean_rel[1]},
             "small_cell_mean_width": widths}
+
+
+def fma_probe(ar, sp):
+    """Measured FP32 FMA rate, scalar and packed (best of 3 each), beside the nominal peak."""
+    out = {}
+    for name, packed in (("scalar", False), ("packed", True)):
+        out[name] = max(ar.ar_fp32_fma_rate(packed, 16384, sp) for _ in range(3))
+    return out
 
 
 def hbm_peak():
@@ -473,7 +481,8 @@ def run_ours(args, rank, world, local, pg):
                      "kernel": "render_kernel", "kernel_ms": r_ms,
                      "flops_per_triple": flops_per_triple(M), "triples_evaluated": stats["n_evaluated"],
                      "triples_in_boxes": stats["n_triples"],
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal, no measured FP32 peak)"},
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal: MEASURED_PEAKS.json has no FP32 figure)",
+                     "fp32_fma_probe_tflops": fma_probe(ar, sp)},
         "stages_ms": {"prep": stats["ms_prep"], "bin": stats["ms_bin"], "build": stats["ms_build"],
                       "render": stats["ms_render"], "total": stats["ms_total"]},
         "counts": {"records": stats["n_records"], "entries": stats["n_entries"], "triples": stats["n_triples"],

@@ -74,6 +74,7 @@ def lib():
             "ar_set_profiling": ([P, ctypes.c_int], ctypes.c_int),
             "ar_scene_set_blend": ([P, ctypes.c_int32], ctypes.c_int),
             "ar_bounds_union": ([P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P], ctypes.c_int),
+            "ar_fp32_fma_rate": ([ctypes.c_int32, ctypes.c_int32, P, P], ctypes.c_int),
             "ar_render_abstract_partitioned": ([P, P, P, P, P, ctypes.c_int32, P, P, P], ctypes.c_int),
             "ar_set_workspace_limit": ([P, c_int64], ctypes.c_int),
             "ar_last_render_stats": ([P, P], ctypes.c_int),
@@ -188,6 +189,13 @@ def ar_render_abstract_partitioned(scene, intr, pose, box, parts, tile, out_lowe
     p = (ctypes.c_int32 * 6)(*[int(v) for v in parts])
     return check(lib().ar_render_abstract_partitioned(scene, ctypes.byref(intr), ctypes.byref(pose), ctypes.byref(box),
                                                       p, int(tile), _ptr(out_lower), _ptr(out_upper), _ptr(stream)))
+
+
+def ar_fp32_fma_rate(packed: bool, iters: int = 16384, stream=0) -> float:
+    """Measured FP32 FMA throughput of the current device in TFLOP/s."""
+    v = ctypes.c_double(0.0)
+    check(lib().ar_fp32_fma_rate(1 if packed else 0, int(iters), ctypes.byref(v), _ptr(stream)))
+    return v.value
 
 
 def ar_render_concrete(scene, intr, pose, deltas, n_poses, out, stream=0):

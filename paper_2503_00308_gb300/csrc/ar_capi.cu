@@ -972,6 +972,14 @@ int ar_render_abstract_partitioned(ar_scene *s, const ar_intrinsics *in, const a
     return AR_OK;
 }
 
+int ar_fp32_fma_rate(int32_t packed, int32_t iters, double *tflops, void *stream)
+{
+    if (!tflops || iters < 1) return fail(AR_EINVAL, "need tflops and iters >= 1");
+    if (fma_rate(packed, iters, tflops, (cudaStream_t)stream))
+        return fail(AR_EDEVICE, "fma rate probe: %s", cudaGetErrorString(cudaGetLastError()));
+    return AR_OK;
+}
+
 int ar_last_render_stats(ar_scene *s, ar_render_stats *out)
 {
     if (!s || !out) return fail(AR_EINVAL, "null argument");

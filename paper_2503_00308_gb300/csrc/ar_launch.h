@@ -46,6 +46,9 @@ int launch_render_plain(int M, int TS, const RenderLaunch &a, cudaStream_t st);
 // the current outputs in too
 int launch_bounds_union(const float *lo, const float *hi, int n_cells, size_t n, float *out_lo, float *out_hi,
                         bool acc, cudaStream_t st);
+// FP32 FMA throughput (TFLOP/s) of the current device (k_probe.cu); packed:
+// through __ffma2_rn.  Synchronises with st.
+int fma_rate(int packed, int iters, double *tflops, cudaStream_t st);
 // value parts of the records listed in work[0, *count); counters: [0] fallbacks, [1] built, [2] split.
 // split_list (list_cap >= *count entries), split_count and khigh_count (zeroed by the caller): pairs whose
 // MatrixInv fails on the cell are split by a warp each in a second kernel, pairs whose Taylor order exceeds
