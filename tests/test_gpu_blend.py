@@ -119,3 +119,25 @@ def test_relational_other_entry_points(arlib):
     with pytest.raises(ar.ArError):
         ar.ar_scene_set_blend(s.handle, 7)
     s.close()
+
+
+def test_relational_object300k_small_cell(arlib, orc):
+    """The 300k-Gaussian, 800x800 scene at a small cell (the centre of the
+    first benchmark cell, a twentieth of its widths), where the bounds are not
+    saturated: parity with the oracle's tight blend on a pixel window at the
+    image centre, never looser than the interval blend over the whole image,
+    and a clearly narrower mean width."""
+    w = synth.object300k()
+    c = 0.5 * (w.cells_lo[0] + w.cells_hi[0])
+    h = 0.025 * (w.cells_hi[0] - w.cells_lo[0])
+    lo, hi = (c - h)[None], (c + h)[None]
+    ilo, ihi = render(arlib, w.scene, w.camera, lo, hi, arlib.AR_BLEND_INTERVAL)
+    rlo, rhi = render(arlib, w.scene, w.camera, lo, hi, arlib.AR_BLEND_RELATIONAL)
+    assert np.abs(rlo - ilo).max() <= EXIT and np.all(rhi <= ihi + EXIT)
+    assert (rhi - rlo).mean() < 0.85 * (ihi - ilo).mean()
+    olo, ohi, frag, cond = orc.render_abstract(w.scene, w.camera, lo[0], hi[0], window=(396, 403, 396, 403),
+                                               with_cond=True, tight=True)
+    m = ~np.isnan(olo[..., 0])
+    ok = m & (frag == 0)
+    e = np.maximum(np.abs(rlo[0] - olo), np.abs(rhi[0] - ohi)).max(axis=-1)
+    assert ok.sum() > 0 and np.all(e[ok] <= TOL + cond[ok]), (e[ok] - cond[ok]).max()
