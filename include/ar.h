@@ -207,6 +207,30 @@ int ar_render_abstract_partitioned(ar_scene *scene, const ar_intrinsics *intr, c
                                    const ar_pose_box *box, const int32_t *parts, int32_t tile, float *out_lower,
                                    float *out_upper, void *cuda_stream);
 
+/* Bounds of one pose box from an adaptive partition (Sec. 5 partitions the
+ * camera set to tighten the bounds; here the pieces whose bounds stay loose
+ * are the ones cut further).  Round 0 renders the box.  Each of the next
+ * `rounds` rounds cuts the looser half of the current pieces, ranked by the
+ * mean width of their bounds (sum over pixels and channels of upper - lower,
+ * ties by index), each into two halves along the pose dimension where the
+ * piece is widest relative to the box, and renders the new set of pieces.
+ * The outputs are the intersection over the rounds of each round's union of
+ * its pieces' bounds: sound, because every round's union bounds every pose of
+ * the box, and never looser than the box's own bounds.
+ *   box: one pose box (the checks of ar_render_abstract's cells apply).
+ *   rounds: 0..12.  Pieces per round: 1, 2, 3, 5, 8, 12, ... (n + ceil(n/2)).
+ *   out_lower, out_upper: DEVICE [height][width][3] float32.
+ *   leaves (optional, host, leaves_cap entries): the last round's pieces, in
+ *     order; n_leaves (optional) gets their number.
+ * Rendering goes through ar_render_abstract in chunks of at most 64 pieces;
+ * the scene's blend mode applies.  Synchronises with cuda_stream once per
+ * chunk.  Errors as for ar_render_abstract, and AR_EINVAL for bad rounds or
+ * leaves arguments. */
+int ar_render_abstract_refined(ar_scene *scene, const ar_intrinsics *intr, const ar_nominal_pose *pose,
+                               const ar_pose_box *box, int32_t rounds, int32_t tile, float *out_lower,
+                               float *out_upper, ar_pose_box *leaves, int32_t leaves_cap, int32_t *n_leaves,
+                               void *cuda_stream);
+
 /* FP32 FMA throughput of the current device, in TFLOP/s (an FMA counts as 2
  * flops): 16 independent FMA chains per thread over 8 blocks of 256 threads
  * per SM, `iters` steps each, timed with CUDA events on cuda_stream.  packed =

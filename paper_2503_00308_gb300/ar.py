@@ -75,6 +75,8 @@ def lib():
             "ar_scene_set_blend": ([P, ctypes.c_int32], ctypes.c_int),
             "ar_bounds_union": ([P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P], ctypes.c_int),
             "ar_fp32_fma_rate": ([ctypes.c_int32, ctypes.c_int32, P, P], ctypes.c_int),
+            "ar_render_abstract_refined": ([P, P, P, P, ctypes.c_int32, ctypes.c_int32, P, P, P, ctypes.c_int32, P, P],
+                                           ctypes.c_int),
             "ar_render_abstract_partitioned": ([P, P, P, P, P, ctypes.c_int32, P, P, P], ctypes.c_int),
             "ar_set_workspace_limit": ([P, c_int64], ctypes.c_int),
             "ar_last_render_stats": ([P, P], ctypes.c_int),
@@ -189,6 +191,22 @@ def ar_render_abstract_partitioned(scene, intr, pose, box, parts, tile, out_lowe
     p = (ctypes.c_int32 * 6)(*[int(v) for v in parts])
     return check(lib().ar_render_abstract_partitioned(scene, ctypes.byref(intr), ctypes.byref(pose), ctypes.byref(box),
                                                       p, int(tile), _ptr(out_lower), _ptr(out_upper), _ptr(stream)))
+
+
+def ar_render_abstract_refined(scene, intr, pose, box, rounds, tile, out_lower, out_upper, stream=0,
+                               leaves_cap: int = 4096):
+    """Bounds of one pose box (an ar_pose_box) from an adaptive partition
+    into device [H, W, 3] outputs; returns the last round's pieces as
+    (lo [n, 6], hi [n, 6]) arrays."""
+    buf = (ar_pose_box * leaves_cap)()
+    n = ctypes.c_int32(0)
+    check(lib().ar_render_abstract_refined(scene, ctypes.byref(intr), ctypes.byref(pose), ctypes.byref(box),
+                                           int(rounds), int(tile), _ptr(out_lower), _ptr(out_upper), buf,
+                                           int(leaves_cap), ctypes.byref(n), _ptr(stream)))
+    k = min(n.value, leaves_cap)
+    lo = np.array([[buf[i].lo[j] for j in range(6)] for i in range(k)]).reshape(k, 6)
+    hi = np.array([[buf[i].hi[j] for j in range(6)] for i in range(k)]).reshape(k, 6)
+    return lo, hi
 
 
 def ar_fp32_fma_rate(packed: bool, iters: int = 16384, stream=0) -> float:

@@ -7,6 +7,7 @@
 //   pose prep -> cell prep -> record prep -> (one counter read-back) ->
 //   binning (radix sorts) -> per-pixel render,
 // all enqueued on the caller's stream.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstddef>
@@ -192,7 +193,7 @@ void Workspace::release()
     DevBuf *all[] = {&cells_lohi, &cells, &vN, &recs, &boxes, &keys, &counters, &evk0, &evk1, &evv0, &evv1,
                      &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege, &segk0,
                      &segk1, &segv0, &segv1, &work, &state, &wlist, &act0, &act1, &words, &slist, &whist, &out_lo,
-                     &out_hi, &part_lo, &part_hi};
+                     &out_hi, &part_lo, &part_hi, &lvl_lo, &lvl_hi, &wpart};
     for (DevBuf *b : all) b->release();
     if (h_whist) cudaFreeHost(h_whist);
     h_whist = nullptr;
@@ -208,7 +209,7 @@ size_t Workspace::bytes() const
     const DevBuf *all[] = {&cells_lohi, &cells, &vN, &recs, &boxes, &keys, &counters, &evk0, &evk1, &evv0, &evv1,
                            &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege,
                            &segk0, &segk1, &segv0, &segv1, &work, &state, &wlist, &act0, &act1, &words,
-                           &slist, &whist, &out_lo, &out_hi, &part_lo, &part_hi};
+                           &slist, &whist, &out_lo, &out_hi, &part_lo, &part_hi, &lvl_lo, &lvl_hi, &wpart};
     size_t s = 0;
     for (const DevBuf *b : all) s += b->cap;
     return s;
@@ -969,6 +970,97 @@ int ar_render_abstract_partitioned(ar_scene *s, const ar_intrinsics *in, const a
                                 c0 > 0, st))
             return fail(AR_EDEVICE, "bounds_union launch: %s", cudaGetErrorString(cudaGetLastError()));
     }
+    return AR_OK;
+}
+
+int ar_render_abstract_refined(ar_scene *s, const ar_intrinsics *in, const ar_nominal_pose *pose,
+                               const ar_pose_box *box, int32_t rounds, int32_t tile, float *out_lower,
+                               float *out_upper, ar_pose_box *leaves, int32_t leaves_cap, int32_t *n_leaves,
+                               void *stream)
+{
+    if (!s) return fail(AR_EINVAL, "scene is null");
+    if (!out_lower || !out_upper) return fail(AR_EINVAL, "null output");
+    if (leaves_cap < 0 || (leaves_cap > 0 && !leaves)) return fail(AR_EINVAL, "bad leaves buffer");
+    if (rounds < 0 || rounds > 12) return fail(AR_EINVAL, "rounds must be in [0, 12]");
+    RK(validate_call(in, pose, box, 1, tile));
+    const size_t n = (size_t)3 * in->width * in->height;
+    if (overlaps(out_lower, n, out_upper, n)) return fail(AR_EINVAL, "overlapping outputs");
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(s->device));
+    int64_t chunk = 64;
+    while (chunk > 1 && (size_t)chunk * n * sizeof(float) > ((size_t)1 << 30)) chunk /= 2;
+    const int PB = 64;  // partial sums per piece
+    RK(s->ws.part_lo.ensure(sizeof(float) * n * (size_t)chunk));
+    RK(s->ws.part_hi.ensure(sizeof(float) * n * (size_t)chunk));
+    RK(s->ws.lvl_lo.ensure(sizeof(float) * n));
+    RK(s->ws.lvl_hi.ensure(sizeof(float) * n));
+    RK(s->ws.wpart.ensure(sizeof(double) * (size_t)chunk * PB));
+    float *plo = s->ws.part_lo.as<float>(), *phi = s->ws.part_hi.as<float>();
+    float *llo = s->ws.lvl_lo.as<float>(), *lhi = s->ws.lvl_hi.as<float>();
+    std::vector<ar_pose_box> cur(1, *box);
+    std::vector<double> width, part((size_t)chunk * PB);
+    for (int r = 0; r <= rounds; ++r) {
+        const int64_t L = (int64_t)cur.size();
+        width.assign((size_t)L, 0.0);
+        for (int64_t c0 = 0; c0 < L; c0 += chunk) {
+            const int64_t nb = c0 + chunk <= L ? chunk : L - c0;
+            RK(render_core(s, s->ws, in, pose, &cur[(size_t)c0], (int32_t)nb, tile, plo, phi, st, s->profiling,
+                           &s->stats));
+            s->stats_stream = st;
+            if (launch_bounds_union(plo, phi, (int)nb, n, llo, lhi, c0 > 0, st))
+                return fail(AR_EDEVICE, "bounds_union launch: %s", cudaGetErrorString(cudaGetLastError()));
+            if (r < rounds) {  // the pieces' mean widths choose the next splits
+                if (launch_width_partials(plo, phi, (int)nb, n, PB, s->ws.wpart.as<double>(), st))
+                    return fail(AR_EDEVICE, "width launch: %s", cudaGetErrorString(cudaGetLastError()));
+                CK(cudaMemcpyAsync(part.data(), s->ws.wpart.p, sizeof(double) * (size_t)nb * PB,
+                                   cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                for (int64_t q = 0; q < nb; ++q) {
+                    double w = 0.0;
+                    for (int b = 0; b < PB; ++b) w += part[(size_t)q * PB + b];
+                    width[(size_t)(c0 + q)] = w;
+                }
+            }
+        }
+        if (r == 0) {
+            CK(cudaMemcpyAsync(out_lower, llo, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(out_upper, lhi, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+        } else if (launch_bounds_intersect(llo, lhi, n, out_lower, out_upper, st)) {
+            return fail(AR_EDEVICE, "intersect launch: %s", cudaGetErrorString(cudaGetLastError()));
+        }
+        if (r == rounds) break;
+        // split the looser half of the pieces (ties by index), each in two
+        // halves along its widest pose dimension relative to the box
+        std::vector<int64_t> order((size_t)L);
+        for (int64_t i = 0; i < L; ++i) order[(size_t)i] = i;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int64_t a, int64_t b) { return width[(size_t)a] > width[(size_t)b]; });
+        std::vector<char> split((size_t)L, 0);
+        for (int64_t i = 0; i < (L + 1) / 2; ++i) split[(size_t)order[(size_t)i]] = 1;
+        std::vector<ar_pose_box> next;
+        next.reserve((size_t)(L + (L + 1) / 2));
+        for (int64_t i = 0; i < L; ++i) {
+            const ar_pose_box &c = cur[(size_t)i];
+            int kbest = -1;
+            double best = 0.0;
+            for (int k = 0; k < MAXV; ++k) {
+                const double bw = box->hi[k] - box->lo[k];
+                if (!(bw > 0.0)) continue;
+                const double rel = (c.hi[k] - c.lo[k]) / bw;
+                if (rel > best) { best = rel; kbest = k; }
+            }
+            if (!split[(size_t)i] || kbest < 0) { next.push_back(c); continue; }
+            const double mid = c.lo[kbest] + (c.hi[kbest] - c.lo[kbest]) / 2.0;
+            ar_pose_box a = c, b = c;
+            a.hi[kbest] = mid;
+            b.lo[kbest] = mid;
+            next.push_back(a);
+            next.push_back(b);
+        }
+        cur.swap(next);
+    }
+    if (n_leaves) *n_leaves = (int32_t)cur.size();
+    for (int64_t i = 0; i < (int64_t)cur.size() && i < leaves_cap; ++i) leaves[i] = cur[(size_t)i];
     return AR_OK;
 }
 

@@ -33,7 +33,9 @@ struct Workspace {
     bool whist_pending = false;              // h_whist holds a render not yet learned from
     uint32_t w0 = 512;                       // first window of the windowed rounds
     DevBuf out_lo, out_hi;      // staged outputs of ar_render_abstract_host
-    DevBuf part_lo, part_hi;    // chunk outputs of ar_render_abstract_partitioned
+    DevBuf part_lo, part_hi;    // chunk outputs of ar_render_abstract_partitioned / _refined
+    DevBuf lvl_lo, lvl_hi;      // one refinement round's union (ar_render_abstract_refined)
+    DevBuf wpart;               // partial width sums of the refinement's pieces
     unsigned long long *h_counters = nullptr;  // page-locked
     std::vector<cudaEvent_t> evs;              // 9 per cell batch (stage timing)
     int n_batches = 0;                         // cell batches of the last render

@@ -46,6 +46,12 @@ int launch_render_plain(int M, int TS, const RenderLaunch &a, cudaStream_t st);
 // the current outputs in too
 int launch_bounds_union(const float *lo, const float *hi, int n_cells, size_t n, float *out_lo, float *out_hi,
                         bool acc, cudaStream_t st);
+// out = out intersected with [lo, hi] elementwise (k_union.cu)
+int launch_bounds_intersect(const float *lo, const float *hi, size_t n, float *out_lo, float *out_hi, cudaStream_t st);
+// part[c * blocks + b] = partial sum of (hi - lo) over cell c (k_union.cu); the
+// host adds the partials in order, so the sums are deterministic
+int launch_width_partials(const float *lo, const float *hi, int n_cells, size_t n, int blocks, double *part,
+                          cudaStream_t st);
 // FP32 FMA throughput (TFLOP/s) of the current device (k_probe.cu); packed:
 // through __ffma2_rn.  Synchronises with st.
 int fma_rate(int packed, int iters, double *tflops, cudaStream_t st);

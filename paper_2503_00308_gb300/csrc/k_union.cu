@@ -80,4 +80,57 @@ int launch_bounds_union(const float *lo, const float *hi, int n_cells, size_t n,
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 
+// out = out intersected with [lo, hi]: the larger lower and the smaller upper bound
+__global__ void __launch_bounds__(256) bounds_intersect_kernel(const float *__restrict__ lo,
+                                                               const float *__restrict__ hi, size_t n,
+                                                               float *__restrict__ out_lo, float *__restrict__ out_hi)
+{
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < n; j += stride) {
+        out_lo[j] = fmaxf(out_lo[j], lo[j]);
+        out_hi[j] = fminf(out_hi[j], hi[j]);
+    }
+}
+
+// partial sums of (hi - lo) over each cell's n floats: block (b, c) sums the
+// elements b, b + B, ... of cell c (B = gridDim.x blocks) into part[c B + b]
+__global__ void __launch_bounds__(256) width_partials_kernel(const float *__restrict__ lo,
+                                                             const float *__restrict__ hi, size_t n,
+                                                             double *__restrict__ part)
+{
+    __shared__ double s_sum[256];
+    const size_t c = blockIdx.y;
+    const float *l = lo + c * n, *h = hi + c * n;
+    double acc = 0.0;
+    for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < n; j += (size_t)gridDim.x * blockDim.x)
+        acc += (double)h[j] - (double)l[j];
+    s_sum[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) s_sum[threadIdx.x] += s_sum[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[c * gridDim.x + blockIdx.x] = s_sum[0];
+}
+
+int launch_bounds_intersect(const float *lo, const float *hi, size_t n, float *out_lo, float *out_hi, cudaStream_t st)
+{
+    if (n == 0) return 0;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms < 1) sms = 1;
+    const size_t want = (n + 255) / 256, cap = (size_t)sms * 8;
+    bounds_intersect_kernel<<<(unsigned)(want < cap ? want : cap), 256, 0, st>>>(lo, hi, n, out_lo, out_hi);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+int launch_width_partials(const float *lo, const float *hi, int n_cells, size_t n, int blocks, double *part,
+                          cudaStream_t st)
+{
+    if (n_cells < 1 || blocks < 1) return 0;
+    width_partials_kernel<<<dim3((unsigned)blocks, (unsigned)n_cells), 256, 0, st>>>(lo, hi, n, part);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
 }  // namespace ar

@@ -107,3 +107,49 @@ def test_partitioned_parity_and_soundness(arlib, orc):
     rng = np.random.default_rng(32)
     worst, nv = orc.check_samples(sc, cam, synth.sample_poses(rng, box_lo, box_hi, 400), glo, ghi)
     assert nv == 0, worst
+
+
+def test_refined_render(arlib, orc):
+    """Adaptive refinement: the pieces cover the box; the bounds are never
+    looser than the box's own, at least as tight as the union of the last
+    round's pieces, deterministic, and sound at sampled poses."""
+    ar = arlib
+    sc, cam, box_lo, box_hi = _scene()
+    s = ar.Scene(sc)
+    intr, pose = ar.make_intrinsics(cam), ar.make_pose(cam)
+    box = ar.make_cells(box_lo, box_hi)[0]
+    shape = (cam.height, cam.width, 3)
+    rlo = torch.full(shape, -7.0, device="cuda")
+    rhi = torch.full_like(rlo, -7.0)
+    llo, lhi = ar.ar_render_abstract_refined(s.handle, intr, pose, box, 3, 16, rlo, rhi)
+    assert llo.shape == (5, 6)                      # 1 -> 2 -> 3 -> 5 pieces
+    act = box_hi > box_lo
+    assert np.all(llo >= box_lo) and np.all(lhi <= box_hi) and np.all(llo <= lhi)
+    vol = np.prod((lhi - llo)[:, act], axis=1).sum() / np.prod((box_hi - box_lo)[act])
+    assert abs(vol - 1.0) < 1e-12
+    one_lo = torch.empty((1,) + shape, device="cuda")
+    one_hi = torch.empty_like(one_lo)
+    ar.ar_render_abstract(s.handle, intr, pose, ar.make_cells(box_lo, box_hi), 1, 16, one_lo, one_hi)
+    p_lo = torch.empty((5,) + shape, device="cuda")
+    p_hi = torch.empty_like(p_lo)
+    ar.ar_render_abstract(s.handle, intr, pose, ar.make_cells(llo, lhi), 5, 16, p_lo, p_hi)
+    ulo = torch.empty(shape, device="cuda")
+    uhi = torch.empty_like(ulo)
+    ar.ar_bounds_union(p_lo, p_hi, 5, cam.width, cam.height, ulo, uhi)
+    torch.cuda.synchronize()
+    assert torch.all(rlo >= one_lo[0]) and torch.all(rhi <= one_hi[0])
+    assert torch.all(rlo >= ulo) and torch.all(rhi <= uhi)
+    assert float((rhi - rlo).mean()) < float((one_hi - one_lo).mean())
+    r2lo = torch.empty_like(rlo)
+    r2hi = torch.empty_like(rlo)
+    l2lo, l2hi = ar.ar_render_abstract_refined(s.handle, intr, pose, box, 3, 16, r2lo, r2hi)
+    torch.cuda.synchronize()
+    assert np.array_equal(l2lo, llo) and np.array_equal(l2hi, lhi)
+    assert torch.equal(r2lo, rlo) and torch.equal(r2hi, rhi)
+    with pytest.raises(ar.ArError):
+        ar.ar_render_abstract_refined(s.handle, intr, pose, box, 13, 16, r2lo, r2hi)
+    glo, ghi = rlo.double().cpu().numpy(), rhi.double().cpu().numpy()
+    s.close()
+    rng = np.random.default_rng(33)
+    worst, nv = orc.check_samples(sc, cam, synth.sample_poses(rng, box_lo, box_hi, 400), glo, ghi)
+    assert nv == 0, worst
