@@ -202,7 +202,8 @@ int ar_bounds_union(const float *in_lower, const float *in_upper, int32_t n_cell
  * box.  The scene's blend mode applies.  Chunk buffers come from the scene's
  * workspace.  Synchronises with cuda_stream once per chunk (as
  * ar_render_abstract does); the stats of ar_last_render_stats describe the
- * last chunk.  Errors as for ar_render_abstract, and AR_EINVAL for bad parts. */
+ * last chunk.  Errors as for ar_render_abstract, and AR_EINVAL for bad parts;
+ * after an error the outputs' contents are undefined. */
 int ar_render_abstract_partitioned(ar_scene *scene, const ar_intrinsics *intr, const ar_nominal_pose *pose,
                                    const ar_pose_box *box, const int32_t *parts, int32_t tile, float *out_lower,
                                    float *out_upper, void *cuda_stream);
@@ -225,7 +226,7 @@ int ar_render_abstract_partitioned(ar_scene *scene, const ar_intrinsics *intr, c
  * Rendering goes through ar_render_abstract in chunks of at most 64 pieces;
  * the scene's blend mode applies.  Synchronises with cuda_stream once per
  * chunk.  Errors as for ar_render_abstract, and AR_EINVAL for bad rounds or
- * leaves arguments. */
+ * leaves arguments; after an error the outputs' contents are undefined. */
 int ar_render_abstract_refined(ar_scene *scene, const ar_intrinsics *intr, const ar_nominal_pose *pose,
                                const ar_pose_box *box, int32_t rounds, int32_t tile, float *out_lower,
                                float *out_upper, ar_pose_box *leaves, int32_t leaves_cap, int32_t *n_leaves,
