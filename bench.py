@@ -72,7 +72,8 @@ def parse():
     ap.add_argument("--tile", type=int, default=0, help="0: the library's autotuner picks the tile edge")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-window", type=int, default=16, help="edge of the oracle's pixel sample")
+    ap.add_argument("--cpu-window", type=int, default=32,
+                    help="edge of the oracle's pixel sample (32: about 15 s of oracle work on 16 cores)")
     ap.add_argument("--cells", type=int, default=0, help="use only the first N cells (profiling slices)")
     ap.add_argument("--relational-steps", type=int, default=2,
                     help="timed steps of the relational-transmittance blend (0: skip)")
