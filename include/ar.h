@@ -208,6 +208,12 @@ int ar_render_abstract_partitioned(ar_scene *scene, const ar_intrinsics *intr, c
                                    const ar_pose_box *box, const int32_t *parts, int32_t tile, float *out_lower,
                                    float *out_upper, void *cuda_stream);
 
+/* Piece `index` of the partition used by ar_render_abstract_partitioned
+ * (dimension 0 varying fastest), written to *out.  Host only: no CUDA call.
+ * Errors: AR_EINVAL (null pointers, parts < 1 or more than 2^24 pieces,
+ * index outside [0, prod parts)). */
+int ar_partition_piece(const ar_pose_box *box, const int32_t *parts, int64_t index, ar_pose_box *out);
+
 /* Bounds of one pose box from an adaptive partition (Sec. 5 partitions the
  * camera set to tighten the bounds; here the pieces whose bounds stay loose
  * are the ones cut further).  Round 0 renders the box.  Each of the next

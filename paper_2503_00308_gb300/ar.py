@@ -75,6 +75,7 @@ def lib():
             "ar_scene_set_blend": ([P, ctypes.c_int32], ctypes.c_int),
             "ar_bounds_union": ([P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P], ctypes.c_int),
             "ar_fp32_fma_rate": ([ctypes.c_int32, ctypes.c_int32, P, P], ctypes.c_int),
+            "ar_partition_piece": ([P, P, c_int64, P], ctypes.c_int),
             "ar_render_abstract_refined": ([P, P, P, P, ctypes.c_int32, ctypes.c_int32, P, P, P, ctypes.c_int32, P, P],
                                            ctypes.c_int),
             "ar_render_abstract_partitioned": ([P, P, P, P, P, ctypes.c_int32, P, P, P], ctypes.c_int),
@@ -191,6 +192,15 @@ def ar_render_abstract_partitioned(scene, intr, pose, box, parts, tile, out_lowe
     p = (ctypes.c_int32 * 6)(*[int(v) for v in parts])
     return check(lib().ar_render_abstract_partitioned(scene, ctypes.byref(intr), ctypes.byref(pose), ctypes.byref(box),
                                                       p, int(tile), _ptr(out_lower), _ptr(out_upper), _ptr(stream)))
+
+
+def ar_partition_piece(box, parts, index: int):
+    """Piece `index` of the partition of an ar_pose_box into parts[k] pieces per
+    dimension: returns (lo [6], hi [6]).  Host only."""
+    p = (ctypes.c_int32 * 6)(*[int(v) for v in parts])
+    out = ar_pose_box()
+    check(lib().ar_partition_piece(ctypes.byref(box), p, int(index), ctypes.byref(out)))
+    return np.array(list(out.lo)), np.array(list(out.hi))
 
 
 def ar_render_abstract_refined(scene, intr, pose, box, rounds, tile, out_lower, out_upper, stream=0,

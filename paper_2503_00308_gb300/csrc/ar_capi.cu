@@ -925,6 +925,27 @@ int ar_bounds_union(const float *in_lower, const float *in_upper, int32_t n_cell
     return AR_OK;
 }
 
+int ar_partition_piece(const ar_pose_box *box, const int32_t *parts, int64_t index, ar_pose_box *out)
+{
+    if (!box || !parts || !out) return fail(AR_EINVAL, "null argument");
+    int64_t total = 1;
+    for (int k = 0; k < MAXV; ++k) {
+        if (parts[k] < 1) return fail(AR_EINVAL, "parts[%d] must be >= 1", k);
+        total *= parts[k];
+        if (total > (int64_t)1 << 24) return fail(AR_EINVAL, "more than 2^24 pieces");
+    }
+    if (index < 0 || index >= total) return fail(AR_EINVAL, "piece index out of range");
+    int64_t r = index;  // multi-index, dimension 0 fastest
+    for (int k = 0; k < MAXV; ++k) {
+        const int64_t P = parts[k], i = r % P;
+        r /= P;
+        const double lo = box->lo[k], hi = box->hi[k], w = hi - lo;
+        out->lo[k] = i == 0 ? lo : lo + w * (double)i / (double)P;
+        out->hi[k] = i + 1 == P ? hi : lo + w * (double)(i + 1) / (double)P;
+    }
+    return AR_OK;
+}
+
 int ar_render_abstract_partitioned(ar_scene *s, const ar_intrinsics *in, const ar_nominal_pose *pose,
                                    const ar_pose_box *box, const int32_t *parts, int32_t tile, float *out_lower,
                                    float *out_upper, void *stream)
@@ -952,17 +973,7 @@ int ar_render_abstract_partitioned(ar_scene *s, const ar_intrinsics *in, const a
     std::vector<ar_pose_box> cells((size_t)chunk);
     for (int64_t c0 = 0; c0 < total; c0 += chunk) {
         const int64_t nb = c0 + chunk <= total ? chunk : total - c0;
-        for (int64_t q = 0; q < nb; ++q) {
-            int64_t r = c0 + q;  // multi-index, dimension 0 fastest
-            ar_pose_box &b = cells[(size_t)q];
-            for (int k = 0; k < MAXV; ++k) {
-                const int64_t P = parts[k], i = r % P;
-                r /= P;
-                const double lo = box->lo[k], hi = box->hi[k], w = hi - lo;
-                b.lo[k] = i == 0 ? lo : lo + w * (double)i / (double)P;
-                b.hi[k] = i + 1 == P ? hi : lo + w * (double)(i + 1) / (double)P;
-            }
-        }
+        for (int64_t q = 0; q < nb; ++q) RK(ar_partition_piece(box, parts, c0 + q, &cells[(size_t)q]));
         RK(render_core(s, s->ws, in, pose, cells.data(), (int32_t)nb, tile, s->ws.part_lo.as<float>(),
                        s->ws.part_hi.as<float>(), st, s->profiling, &s->stats));
         s->stats_stream = st;

@@ -35,11 +35,11 @@ def test_library_exports_every_symbol():
 def test_last_error_without_gpu_calls():
     from paper_2503_00308_gb300 import _build, ar
     _build.build()
-    assert ar.ar_last_error() == ""
-    # argument validation happens before any CUDA call
+    # argument validation happens before any CUDA call, and sets the thread's message
     with pytest.raises(ar.ArError) as e:
         ar.ar_scene_create(None, None, None, None, None, -1, 0)
     assert e.value.code == ar.AR_EINVAL
+    assert ar.ar_last_error() != ""
     with pytest.raises(ar.ArError) as e:
         ar.ar_scene_set_blend(None, ar.AR_BLEND_RELATIONAL)
     assert e.value.code == ar.AR_EINVAL
