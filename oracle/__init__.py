@@ -62,6 +62,10 @@ def _load():
         lib.orc_matrixinv_cell.restype = I
         lib.orc_relax_mul.argtypes = [P, P, P]
         lib.orc_relax_sq.argtypes = [P, P]
+        lib.orc_relax_exp.argtypes = [P, P]
+        lib.orc_alpha_from_m.argtypes = [P, D, D, D, D, I, P]
+        lib.orc_pixel_alpha.argtypes = [P, P, P, P, P, I64, P, P, P, P, P, I64, I, I, P]
+        lib.orc_pixel_alpha.restype = I
         lib.orc_rot_forms.argtypes = [P, P, P]
         lib.orc_concrete_alpha.argtypes = [P, P, P, D, P, P, P, P, D, D]
         lib.orc_concrete_alpha.restype = D
@@ -300,6 +304,43 @@ def relax_sq(x) -> np.ndarray:
     out = np.zeros(14)
     lib.orc_relax_sq(_p(_d(x)), _p(out))
     return out
+
+
+def relax_exp(x) -> np.ndarray:
+    """Table 2's Exp relaxation on x <= 0 (x_hi clipped at 0): tangent at x_lo
+    below, secant above.  x and the result are packed bounded scalars (14)."""
+    out = np.zeros(14)
+    _load().orc_relax_exp(_p(_d(x).reshape(14)), _p(out))
+    return out
+
+
+def alpha_from_m(m, o_lo, o_hi, tau_lo, tau_hi, straddle=False) -> dict:
+    """The opacity stage a = o Exp(-m/2) with the clip to o and the cutoff
+    ramps, from a packed bounded scalar m (14)."""
+    out = np.zeros(19)
+    _load().orc_alpha_from_m(_p(_d(m).reshape(14)), float(o_lo), float(o_hi), float(tau_lo), float(tau_hi),
+                             int(bool(straddle)), _p(out))
+    return {"L": out[0:7], "U": out[7:14], "alo": out[14], "ahi": out[15], "mlo": out[16], "mhi": out[17],
+            "ramp": out[18]}
+
+
+def pixel_alpha(scene, cam, cell_lo, cell_hi, gi, px, py):
+    """The relaxed effective opacity of Gaussian gi at pixel (px, py) over one
+    cell: its Mahalanobis term m (packed bounded scalar), the opacity forms L,
+    U (7 each), alo, ahi, mlo, mhi, ramp and the record's opacity box and
+    cutoff exponents.  None if the pair is not valid."""
+    lib = _load()
+    s = _scene_args(scene)
+    intr, R0, t0 = _cam_args(cam)
+    out = np.zeros(39)
+    st = lib.orc_pixel_alpha(*[_p(a) for a in s], scene.n, _p(intr), _p(R0), _p(t0),
+                             _p(_d(cell_lo).reshape(6)), _p(_d(cell_hi).reshape(6)), int(gi), int(px), int(py),
+                             _p(out))
+    if st:
+        return None
+    return {"m": out[0:14], "L": out[14:21], "U": out[21:28], "alo": out[28], "ahi": out[29], "mlo": out[30],
+            "mhi": out[31], "ramp": out[32], "o_lo": out[33], "o_hi": out[34], "tau_lo": out[35],
+            "tau_hi": out[36], "fallback": bool(out[37]), "straddle": bool(out[38])}
 
 
 def rot_forms(lo, hi) -> np.ndarray:

@@ -39,7 +39,11 @@
  *
  * Parity of the "tightness" of these choices against the paper's CROWN numbers
  * is unpinned (the paper's scenes are not available); their soundness and their
- * exactness on point cells are pinned by the test-suite.
+ * exactness on point cells are pinned by the test-suite.  The values of each
+ * relaxation are pinned by hand-worked closed forms: Mul, Square and Exp one
+ * by one (bs_mul, bs_sq, bs_exp), the opacity stage with its clip and cutoff
+ * ramps (alpha_from_m) in every branch, and one Gaussian's whole pixel chain
+ * on a case whose Mahalanobis term has a closed form.
  */
 #include <math.h>
 #include <stdint.h>
@@ -607,6 +611,8 @@ static void pack_bs(const bs *b, double *v)
 }
 void orc_relax_mul(const double *x, const double *y, double *out) { bs r = bs_mul(unpack_bs(x), unpack_bs(y)); pack_bs(&r, out); }
 void orc_relax_sq(const double *x, double *out) { bs r = bs_sq(unpack_bs(x)); pack_bs(&r, out); }
+static bs bs_exp(bs x);
+void orc_relax_exp(const double *x, double *out) { bs r = bs_exp(unpack_bs(x)); pack_bs(&r, out); }
 
 /* Per-(Gaussian, cell) record of the abstract pipeline (steps of Algorithm 1
  * up to W = Conic * Mp). */
@@ -814,42 +820,49 @@ static void gaussian_record(const camera *cam, const cellforms *cf, const double
 
 static double clamp01(double x) { return x < 0 ? 0 : (x > 1 ? 1 : x); }
 
-/* Effective-opacity bounds of one Gaussian at one pixel (Algorithm 1 lines
- * 9-10 relaxed).  Produces lower/upper forms and their scalar enclosure. */
-typedef struct { lf L, U; double alo, ahi; double mlo, mhi, ramp; } galpha;
-
-static void gaussian_alpha(const grec *g, double ux, double uy, galpha *r)
+/* Exp relaxation of Table 2 on x <= 0.  x is a bounded scalar; its range
+ * [x_lo, x_hi] is concretised from its forms and x_hi is clipped at 0 (the
+ * argument is x = -m/2 and m >= 0, so no pose reaches x > 0).  With
+ * E = exp(x_lo):
+ *   lower: the tangent at x_lo,  E (1 + x - x_lo),  applied to the lower form;
+ *   upper: the secant over [x_lo, x_hi],  E + s (x - x_lo),
+ *          s = (exp(x_hi) - E) / (x_hi - x_lo)  (s = E on a point interval),
+ *          applied to the upper form.
+ * Both slopes are positive, so each side takes its own side's form. */
+static bs bs_exp(bs x)
 {
-    if (g->fallback) {
-        r->L = lf_cst(0); r->U = lf_cst(g->o_hi); r->alo = 0; r->ahi = g->o_hi;
-        r->mlo = -INFINITY; r->mhi = INFINITY; r->ramp = 0;
-        return;
-    }
-    /* Delta = d^2 u - d up = S u - P (u constant) */
-    bs Dx = bs_sub(bs_scale(g->S, ux), g->Px);
-    bs Dy = bs_sub(bs_scale(g->S, uy), g->Py);
-    /* q = Delta^T W ; m = q q^T */
-    bs m = bs_cst(0);
-    for (int c = 0; c < 3; ++c) {
-        bs qc = bs_add(bs_mul(Dx, g->W[c]), bs_mul(Dy, g->W[3 + c]));
-        m = bs_add(m, bs_sq(qc));
-    }
-    double mlo = bs_min(&m), mhi = bs_max(&m);
-    r->mlo = mlo; r->mhi = mhi;
-    /* Exp on x = -m/2 in [xl, xu], xu clipped at 0 since m >= 0 */
-    double xl = -0.5 * mhi, xu = fmin(-0.5 * mlo, 0.0);
+    double xl = bs_min(&x), xu = fmin(bs_max(&x), 0.0);
     if (xu < xl) xu = xl;
     double El = exp(xl);
     double slope = (xu > xl) ? (exp(xu) - El) / (xu - xl) : El;
-    /* lower: El (1 + x - xl) with x >= -m.hi/2 ; upper: El + slope (x - xl) with x <= -m.lo/2 */
-    lf Le = lf_scale(&m.hi, -0.5 * El); Le.k += El * (1.0 - xl);
-    lf Ue = lf_scale(&m.lo, -0.5 * slope); Ue.k += El - slope * xl;
+    bs e;
+    e.lo = lf_scale(&x.lo, El); e.lo.k += El * (1.0 - xl);
+    e.hi = lf_scale(&x.hi, slope); e.hi.k += El - slope * xl;
+    return e;
+}
+
+/* Effective-opacity bounds of one Gaussian at one pixel from its Mahalanobis
+ * term m (Algorithm 1 line 10 relaxed): a = o Exp(-m/2), then the upper clip
+ * to o and the two 1/255 cutoff ramps.  Produces lower/upper forms and their
+ * scalar enclosure. */
+typedef struct { lf L, U; double alo, ahi; double mlo, mhi, ramp; } galpha;
+
+static void alpha_from_m(const bs *m, double o_lo, double o_hi, double tau_lo, double tau_hi, int straddle,
+                         galpha *r)
+{
+    double mlo = bs_min(m), mhi = bs_max(m);
+    r->mlo = mlo; r->mhi = mhi;
+    /* Exp on x = -m/2 (x.lo = -m.hi/2, x.hi = -m.lo/2) */
+    bs x;
+    x.lo = lf_scale(&m->hi, -0.5);
+    x.hi = lf_scale(&m->lo, -0.5);
+    bs e = bs_exp(x);
     /* a = o e with o in [o_lo, o_hi] and e >= 0: o_lo below, o_hi above */
-    lf La = lf_scale(&Le, g->o_lo), Ua = lf_scale(&Ue, g->o_hi);
+    lf La = lf_scale(&e.lo, o_lo), Ua = lf_scale(&e.hi, o_hi);
     /* upper side: blend toward the constant o when the form's maximum exceeds o */
     double amax = lf_max(&Ua);
-    double lam = clamp01((g->o_hi * (1.0 + CLIP_RAMP) - amax) / (g->o_hi * CLIP_RAMP));
-    lf U1 = lf_scale(&Ua, lam); U1.k += (1.0 - lam) * g->o_hi;
+    double lam = clamp01((o_hi * (1.0 + CLIP_RAMP) - amax) / (o_hi * CLIP_RAMP));
+    lf U1 = lf_scale(&Ua, lam); U1.k += (1.0 - lam) * o_hi;
     /* cutoff ramps: width shrinks with the m interval, zero on a point cell */
     double ramp = fmin(CUT_RAMP, mhi - mlo);
     if (!(ramp > 0)) ramp = 0;
@@ -857,16 +870,43 @@ static void gaussian_alpha(const grec *g, double ux, double uy, galpha *r)
     /* the upper form is cut where m > tau(o_hi) for every pose (no opacity in
      * the box is then visible); the lower one keeps a margin of 1/255 unless
      * m <= tau(o_lo) at every pose (no opacity in the box is then cut) */
-    double psi2 = (mlo <= g->tau_hi) ? 0.0 : (ramp > 0 ? clamp01((mlo - g->tau_hi) / ramp) : 1.0);
-    double psi = (mhi > g->tau_lo) ? 1.0 : (ramp > 0 ? clamp01((mhi - g->tau_lo + ramp) / ramp) : 0.0);
+    double psi2 = (mlo <= tau_hi) ? 0.0 : (ramp > 0 ? clamp01((mlo - tau_hi) / ramp) : 1.0);
+    double psi = (mhi > tau_lo) ? 1.0 : (ramp > 0 ? clamp01((mhi - tau_lo + ramp) / ramp) : 0.0);
     r->U = lf_scale(&U1, 1.0 - psi2);
     lf L2 = La; L2.k -= psi * ALPHA_MIN;
     double l2min = lf_min(&L2), l2max = lf_max(&L2);
     double mu = (l2min >= 0) ? 1.0 : ((l2max <= 0) ? 0.0 : l2max / (l2max - l2min));
     r->L = lf_scale(&L2, mu);
-    if (g->straddle) r->L = lf_cst(0);
+    if (straddle) r->L = lf_cst(0);
     r->alo = fmax(0.0, lf_min(&r->L));
-    r->ahi = fmin(g->o_hi, lf_max(&r->U));
+    r->ahi = fmin(o_hi, lf_max(&r->U));
+}
+
+/* The Mahalanobis term of one Gaussian at pixel u (Algorithm 1 line 9):
+ * Delta = d^2 u - d up = S u - P (u constant), q = Delta^T W, m = q q^T. */
+static bs gaussian_m(const grec *g, double ux, double uy)
+{
+    bs Dx = bs_sub(bs_scale(g->S, ux), g->Px);
+    bs Dy = bs_sub(bs_scale(g->S, uy), g->Py);
+    bs m = bs_cst(0);
+    for (int c = 0; c < 3; ++c) {
+        bs qc = bs_add(bs_mul(Dx, g->W[c]), bs_mul(Dy, g->W[3 + c]));
+        m = bs_add(m, bs_sq(qc));
+    }
+    return m;
+}
+
+/* Effective-opacity bounds of one Gaussian at one pixel (Algorithm 1 lines
+ * 9-10 relaxed). */
+static void gaussian_alpha(const grec *g, double ux, double uy, galpha *r)
+{
+    if (g->fallback) {
+        r->L = lf_cst(0); r->U = lf_cst(g->o_hi); r->alo = 0; r->ahi = g->o_hi;
+        r->mlo = -INFINITY; r->mhi = INFINITY; r->ramp = 0;
+        return;
+    }
+    bs m = gaussian_m(g, ux, uy);
+    alpha_from_m(&m, g->o_lo, g->o_hi, g->tau_lo, g->tau_hi, g->straddle, r);
 }
 
 /* Abstract render of one cell over the pixel window [px0,px1] x [py0,py1].
@@ -1313,6 +1353,51 @@ int orc_pixel_detail(const double *uw, const double *ls, const double *quat, con
         ++k;
     }
     return k;
+}
+
+/* The opacity stage alone, for the pins: m as a packed bounded scalar (14
+ * doubles: lower coefficients, lower constant, upper coefficients, upper
+ * constant), the opacity box, the two cutoff exponents tau = 2 ln(255 o) and
+ * the near-plane straddle flag.  out: L (7), U (7), alo, ahi, mlo, mhi, ramp. */
+void orc_alpha_from_m(const double *m, double o_lo, double o_hi, double tau_lo, double tau_hi, int straddle,
+                      double *out)
+{
+    bs mm = unpack_bs(m);
+    galpha a;
+    alpha_from_m(&mm, o_lo, o_hi, tau_lo, tau_hi, straddle, &a);
+    for (int i = 0; i < NV; ++i) { out[i] = a.L.c[i]; out[7 + i] = a.U.c[i]; }
+    out[6] = a.L.k; out[13] = a.U.k;
+    out[14] = a.alo; out[15] = a.ahi; out[16] = a.mlo; out[17] = a.mhi; out[18] = a.ramp;
+}
+
+/* gaussian_alpha of one (Gaussian, cell) pair at one pixel, for the pins:
+ * out = m (14, packed as above), L (7), U (7), alo, ahi, mlo, mhi, ramp,
+ * then the record's o_lo, o_hi, tau_lo, tau_hi, fallback, straddle (39
+ * doubles).  Returns 0 if the pair is valid. */
+int orc_pixel_alpha(const double *uw, const double *ls, const double *quat, const double *opac,
+                    const double *rgb, int64_t n, const double *intr, const double *R0, const double *t0,
+                    const double *cell_lo, const double *cell_hi, int64_t gi, int px, int py, double *out)
+{
+    camera cam = make_camera(intr, R0, t0);
+    cellforms cf;
+    cell_setup(&cam, cell_lo, cell_hi, &cf);
+    if (gi < 0 || gi >= n) return 1;
+    grec g;
+    gaussian_record(&cam, &cf, uw + 3 * gi, ls + 3 * gi, quat + 4 * gi, opac[gi], rgb + 3 * gi, box_of(gi), &g);
+    if (!g.valid) return 1;
+    galpha a;
+    gaussian_alpha(&g, px + 0.5, py + 0.5, &a);
+    memset(out, 0, 14 * sizeof(double));
+    if (!g.fallback) {
+        bs m = gaussian_m(&g, px + 0.5, py + 0.5);
+        pack_bs(&m, out);
+    }
+    for (int i = 0; i < NV; ++i) { out[14 + i] = a.L.c[i]; out[21 + i] = a.U.c[i]; }
+    out[20] = a.L.k; out[27] = a.U.k;
+    out[28] = a.alo; out[29] = a.ahi; out[30] = a.mlo; out[31] = a.mhi; out[32] = a.ramp;
+    out[33] = g.o_lo; out[34] = g.o_hi; out[35] = g.tau_lo; out[36] = g.tau_hi;
+    out[37] = g.fallback; out[38] = g.straddle;
+    return 0;
 }
 
 /* Intermediate intervals of one (Gaussian, cell) pair at one pixel (for

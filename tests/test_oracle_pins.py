@@ -55,6 +55,203 @@ def test_square_closed_form(orc):
     np.testing.assert_allclose(r[7:], _form([4], 5), atol=1e-14)
 
 
+def _bs(lo, hi):
+    return np.concatenate([lo, hi])
+
+
+def test_exp_closed_form(orc):
+    """Table 2's Exp: tangent at the lower end below, secant above (worked by hand)."""
+    e2, e1, e3 = math.exp(-2), math.exp(-1), math.exp(-3)
+    # x in [-2, 0] = -1 + p0: lower e^-2 (1 + x + 2) = e^-2 (p0 + 2);
+    # upper e^-2 + s (x + 2) with s = (1 - e^-2) / 2, i.e. s p0 + (e^-2 + s)
+    x = _bs(_form([1], -1), _form([1], -1))
+    r = orc.relax_exp(x)
+    s = (1 - e2) / 2
+    np.testing.assert_allclose(r[:7], _form([e2], 2 * e2), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(r[7:], _form([s], e2 + s), rtol=0, atol=1e-15)
+    # distinct lower and upper forms: x.lo = -2.5 + 0.5 p0 (min -3), x.hi = -1.5 + 0.5 p0 (max -1):
+    # lower e^-3 (1 + x.lo + 3) = e^-3 (1.5 + 0.5 p0);
+    # upper e^-3 + s (x.hi + 3) = e^-3 + s (1.5 + 0.5 p0), s = (e^-1 - e^-3) / 2
+    x = _bs(_form([0.5], -2.5), _form([0.5], -1.5))
+    r = orc.relax_exp(x)
+    s = (e1 - e3) / 2
+    np.testing.assert_allclose(r[:7], _form([0.5 * e3], 1.5 * e3), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(r[7:], _form([0.5 * s], e3 + 1.5 * s), rtol=0, atol=1e-15)
+    # x in [-1, 1] = p0: the argument is -m/2 <= 0, so the secant ends at 0:
+    # lower e^-1 (p0 + 2); upper e^-1 + (1 - e^-1)(p0 + 1)
+    x = _bs(_form([1], 0), _form([1], 0))
+    r = orc.relax_exp(x)
+    np.testing.assert_allclose(r[:7], _form([e1], 2 * e1), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(r[7:], _form([1 - e1], 1.0), rtol=0, atol=1e-15)
+    # a point: both sides are the constant e^-0.7
+    x = _bs(_form([], -0.7), _form([], -0.7))
+    r = orc.relax_exp(x)
+    np.testing.assert_allclose(r, _bs(_form([], math.exp(-0.7)), _form([], math.exp(-0.7))), rtol=0, atol=1e-15)
+
+
+def test_exp_relaxation_sound_and_tight_at_ends(orc):
+    """Soundness on random forms with x <= 0, and the closed form's own
+    property: the lower form touches exp at the lower end of the interval,
+    the upper one at both ends."""
+    rng = np.random.default_rng(11)
+    for _ in range(300):
+        c = rng.normal(size=6) * rng.uniform(0, 1, size=6)
+        lo = _form(c, -np.sum(np.abs(c)) - rng.uniform(0, 4))
+        hi = lo.copy()
+        hi[6] += rng.uniform(0, 0.5)
+        hi[6] = min(hi[6], -np.sum(np.abs(c)))          # x_hi <= 0 at every p
+        r = orc.relax_exp(_bs(lo, hi))
+        for _ in range(30):
+            p = rng.uniform(-1, 1, size=6)
+            xv = _eval(lo, p) + rng.uniform() * (_eval(hi, p) - _eval(lo, p))
+            v = math.exp(xv)
+            assert _eval(r[:7], p) <= v + 1e-12 and v <= _eval(r[7:], p) + 1e-12
+        xl, xu = lo[6] - np.sum(np.abs(lo[:6])), hi[6] + np.sum(np.abs(hi[:6]))
+        # concretised lower bound = exp(x_lo); upper bound = exp(x_hi)
+        assert abs((r[6] - np.sum(np.abs(r[:6]))) - math.exp(xl)) < 1e-12
+        assert abs((r[13] + np.sum(np.abs(r[7:13]))) - math.exp(xu)) < 1e-12
+
+
+TAU = lambda o: 2 * math.log(255 * o)   # noqa: E731  (cutoff: o exp(-m/2) >= 1/255 iff m <= tau)
+
+
+def test_alpha_stage_closed_form(orc):
+    """a = o Exp(-m/2) with m in [2, 6] = 4 + 2 p0 and o = 0.8, far from the
+    cutoff and the clip: x = -m/2 in [-3, -1], x.lo = x.hi = -2 - p0, so
+    lower 0.8 e^-3 (1 + x + 3) = 0.8 e^-3 (2 - p0) and upper
+    0.8 (e^-3 + s (x + 3)) = 0.8 (e^-3 + s (1 - p0)), s = (e^-1 - e^-3) / 2."""
+    e1, e3 = math.exp(-1), math.exp(-3)
+    s = (e1 - e3) / 2
+    m = _bs(_form([2], 4), _form([2], 4))
+    r = orc.alpha_from_m(m, 0.8, 0.8, TAU(0.8), TAU(0.8))
+    np.testing.assert_allclose(r["L"], _form([-0.8 * e3], 1.6 * e3), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(r["U"], _form([-0.8 * s], 0.8 * (e3 + s)), rtol=0, atol=1e-15)
+    assert abs(r["alo"] - 0.8 * e3) < 1e-15 and abs(r["ahi"] - 0.8 * e1) < 1e-15
+    assert r["ramp"] == 0.5
+    # a near-plane straddle keeps the upper side and drops the lower one
+    r = orc.alpha_from_m(m, 0.8, 0.8, TAU(0.8), TAU(0.8), straddle=True)
+    np.testing.assert_allclose(r["L"], _form([], 0.0), rtol=0, atol=0)
+    np.testing.assert_allclose(r["U"], _form([-0.8 * s], 0.8 * (e3 + s)), rtol=0, atol=1e-15)
+    assert r["alo"] == 0.0
+
+
+def test_alpha_lower_cutoff_ramp_closed_form(orc):
+    """m in [8, 10.5] = 9.25 + 1.25 p0, o = 0.8, tau = 2 ln 204 = 10.636...:
+    m_hi < tau, within the ramp of width 0.5 below it, so the lower form loses
+    psi/255 with psi = (10.5 - tau + 0.5) / 0.5 = 2 (11 - tau); the upper form
+    is untouched.  x.lo = x.hi = -4.625 - 0.625 p0, x in [-5.25, -4]."""
+    tau = TAU(0.8)
+    psi = 2 * (11 - tau)
+    assert 0.7275 < psi < 0.7276
+    e525, e4 = math.exp(-5.25), math.exp(-4)
+    s = (e4 - e525) / 1.25
+    m = _bs(_form([1.25], 9.25), _form([1.25], 9.25))
+    r = orc.alpha_from_m(m, 0.8, 0.8, tau, tau)
+    # lower: 0.8 e^-5.25 (1 + x + 5.25) - psi/255 = 0.8 e^-5.25 (1.625 - 0.625 p0) - psi/255 (> 0 on the cell)
+    np.testing.assert_allclose(r["L"], _form([-0.5 * e525], 1.3 * e525 - psi / 255), rtol=0, atol=1e-15)
+    assert abs(r["alo"] - (0.8 * e525 - psi / 255)) < 1e-15
+    # upper: 0.8 (e^-5.25 + s (x + 5.25)) = 0.8 (e^-5.25 + s (0.625 - 0.625 p0))
+    np.testing.assert_allclose(r["U"], _form([-0.5 * s], 0.8 * (e525 + 0.625 * s)), rtol=0, atol=1e-15)
+
+
+def test_alpha_upper_cutoff_ramp_closed_form(orc):
+    """m in [11, 12] = 11.5 + 0.5 p0, o = 0.8 (tau = 10.636...): m_lo > tau, so
+    the upper form is scaled by 1 - psi2, psi2 = (11 - tau) / 0.5; m_hi > tau,
+    so the lower form loses 1/255, and since 0.8 e^-6 (1 + x + 6) <= 1.2 e^-6
+    < 1/255 on the cell, it is replaced by 0.  x = -5.75 - 0.25 p0."""
+    tau = TAU(0.8)
+    psi2 = 2 * (11 - tau)
+    e6, e55 = math.exp(-6), math.exp(-5.5)
+    s = (e55 - e6) / 0.5
+    m = _bs(_form([0.5], 11.5), _form([0.5], 11.5))
+    r = orc.alpha_from_m(m, 0.8, 0.8, tau, tau)
+    keep = 1 - psi2
+    # upper: keep * 0.8 (e^-6 + s (x + 6)) = keep * 0.8 (e^-6 + s (0.25 - 0.25 p0))
+    np.testing.assert_allclose(r["U"], _form([-keep * 0.2 * s], keep * 0.8 * (e6 + 0.25 * s)), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(r["L"], _form([], 0.0), rtol=0, atol=0)
+    assert r["alo"] == 0.0 and abs(r["ahi"] - keep * 0.8 * e55) < 1e-15
+
+
+def test_alpha_clip_ramp_closed_form(orc):
+    """A lower m form that dips below 0 (m.lo = 1 + 2 p0, min -1; m.hi = 5 + 2 p0,
+    max 7) with o = 0.6: x_lo = -3.5 and the secant ends at x = 0, so the upper
+    form 0.6 (e^-3.5 + s (x.hi + 3.5)), s = (1 - e^-3.5) / 3.5, x.hi = -0.5 - p0,
+    peaks at 0.6 (e^-3.5 + 4 s) > 0.6.  It is blended toward the constant 0.6
+    with lam = (1.25 - (e^-3.5 + 4 s)) / 0.25."""
+    e35 = math.exp(-3.5)
+    s = (1 - e35) / 3.5
+    lam = (1.25 - (e35 + 4 * s)) / 0.25
+    assert 0.44 < lam < 0.45
+    m = _bs(_form([2], 1), _form([2], 5))
+    r = orc.alpha_from_m(m, 0.6, 0.6, TAU(0.6), TAU(0.6))
+    np.testing.assert_allclose(r["U"], _form([-0.6 * lam * s], lam * 0.6 * (e35 + 3 * s) + (1 - lam) * 0.6),
+                               rtol=0, atol=1e-15)
+    assert r["ahi"] == 0.6
+    # lower: 0.6 e^-3.5 (1 + x.lo + 3.5), x.lo = -2.5 - p0, i.e. 0.6 e^-3.5 (2 - p0) (m_hi = 7 is far below tau)
+    np.testing.assert_allclose(r["L"], _form([-0.6 * e35], 1.2 * e35), rtol=0, atol=1e-15)
+
+
+def test_alpha_negative_lower_blend_closed_form(orc):
+    """m in [7, 9] = 8 + p0 with o = 0.3 (tau = 2 ln 76.5 = 8.67...): m_hi > tau
+    takes 1/255 off the lower form 0.3 e^-4.5 (1.5 - 0.5 p0), which then spans
+    [0.3 e^-4.5 - 1/255, 0.6 e^-4.5 - 1/255] across 0, so it is scaled by
+    mu = max / (max - min) = (0.6 e^-4.5 - 1/255) / (0.3 e^-4.5)."""
+    e45 = math.exp(-4.5)
+    lmax, lmin = 0.6 * e45 - 1 / 255, 0.3 * e45 - 1 / 255
+    assert lmin < 0 < lmax
+    mu = lmax / (lmax - lmin)
+    m = _bs(_form([1], 8), _form([1], 8))
+    r = orc.alpha_from_m(m, 0.3, 0.3, TAU(0.3), TAU(0.3))
+    np.testing.assert_allclose(r["L"], _form([-0.15 * e45 * mu], mu * (0.45 * e45 - 1 / 255)), rtol=0, atol=1e-15)
+    assert r["alo"] == 0.0
+
+
+def test_pixel_alpha_closed_form_flat_gaussian(orc):
+    """One Gaussian through the whole record chain with a Mahalanobis term
+    known in closed form.  Camera at (0, 0, -3) looking down +z (R0 = I),
+    fx = fy = 32, principal point (16, 16); the Gaussian at (a, b, 0) has
+    identity rotation, scales (sx, sy, e^-30): flat along the view axis, so
+    Mp = J Mc = diag(3 fx sx, 3 fy sy) up to terms of order e^-30, X and Conic
+    are constant and W = diag(1 / (3 fx sx), 1 / (3 fy sy)).  On a cell
+    tx = h p0, Delta_x = 9 (u - cx) - 3 fx (a - h p0) and Delta_y is constant,
+    so q0 = alpha + beta p0 with alpha = (3 (ux - cx) - fx a) / (fx sx),
+    beta = h / sx, and q1 = gamma = (3 (uy - cy) - fy b) / (fy sy).  The square
+    relaxation then gives m.lo = alpha^2 + gamma^2 + 2 alpha beta p0 (tangent at
+    alpha) and m.hi = m.lo + beta^2 (secant), and Table 2's Exp on
+    x = -m/2 gives a's forms."""
+    a, b, h, o = 0.05, -0.03, 0.01, 0.7
+    ls = -2.5
+    sc = synth.Scene(np.array([[a, b, 0.0]], np.float32), np.array([[ls, ls, -30.0]], np.float32),
+                     np.array([[1, 0, 0, 0]], np.float32), np.array([o], np.float32),
+                     np.array([[0.2, 0.5, 0.9]], np.float32))
+    cam = synth.look_camera(32, 32, 32.0, centre=(0, 0, -3))
+    assert np.array_equal(cam.R_wc, np.eye(3)) and cam.cx == 16 and cam.fx == 32
+    a, b, o = float(sc.uw[0, 0]), float(sc.uw[0, 1]), float(sc.opacity[0])
+    sx = math.exp(float(sc.logscale[0, 0]))
+    lo = np.array([-h, 0, 0, 0, 0, 0])
+    px, py = 16, 15
+    r = orc.pixel_alpha(sc, cam, lo, -lo, 0, px, py)
+    assert r is not None and not r["fallback"] and not r["straddle"]
+    al = (3 * (px + 0.5 - 16) - 32 * a) / (32 * sx)
+    be = h / sx
+    ga = (3 * (py + 0.5 - 16) - 32 * b) / (32 * sx)
+    mlo_form = _form([2 * al * be], al * al + ga * ga)
+    mhi_form = _form([2 * al * be], al * al + be * be + ga * ga)
+    np.testing.assert_allclose(r["m"], _bs(mlo_form, mhi_form), rtol=0, atol=1e-11)
+    mlo = al * al + ga * ga - 2 * abs(al * be)
+    mhi = al * al + be * be + ga * ga + 2 * abs(al * be)
+    assert 0 < mlo < mhi < 0.1
+    # x = -m/2 in [-mhi/2, -mlo/2]; lower o E (1 + x.lo - xl), upper o (E + s (x.hi - xl))
+    xl, xu = -mhi / 2, -mlo / 2
+    E = math.exp(xl)
+    s = (math.exp(xu) - E) / (xu - xl)
+    L = _form([-o * E * al * be], o * E * (1 - xl - (al * al + be * be + ga * ga) / 2))
+    U = _form([-o * s * al * be], o * (E - s * xl - s * (al * al + ga * ga) / 2))
+    np.testing.assert_allclose(r["L"], L, rtol=0, atol=1e-11)
+    np.testing.assert_allclose(r["U"], U, rtol=0, atol=1e-11)
+    assert abs(r["alo"] - o * math.exp(-mhi / 2)) < 1e-11 and abs(r["ahi"] - o * math.exp(-mlo / 2)) < 1e-11
+
+
 def _random_bs(rng, scale=1.0):
     lo = _form(rng.normal(size=6) * scale * rng.uniform(0, 1, size=6), rng.normal() * 2 * scale)
     hi = lo.copy()
