@@ -96,6 +96,10 @@ typedef struct ar_render_stats {
     int64_t n_split;            /* (Gaussian, cell) pairs whose MatrixInv held only after the
                                    cell was split into pieces (Sec. 3.1, adjustment (2); among
                                    the pairs whose records were built) */
+    int64_t n_fp64;             /* opacity evaluations taken again in FP64 because their m
+                                   interval was too wide for FP32 (ar_scene_set_fp64_alpha) */
+    int64_t n_fp64_segments;    /* (cell, tile) sweeps that met such an evaluation and were
+                                   swept again by the FP64-capable instance of the renderer */
 } ar_render_stats;
 
 /* Create a scene from n Gaussians <uw, Mw, o, c> (Sec. 2.2).  Mw is given by
@@ -162,8 +166,14 @@ int ar_render_abstract_host(ar_scene *scene, const ar_intrinsics *intr, const ar
  *     exits.  Requests whose buffers need more (roughly: many cells x
  *     Gaussians, or many tile entries) fail with AR_ENOMEM and a message
  *     naming the limit; the outputs are then left untouched.
- *   - The first call on each device looks up the array's device address;
- *     make that first call before any stream capture.
+ *   - Each call looks up the array's device address on the scene's device;
+ *     the first call on a device may load the library's device code there
+ *     (the one-time set-up), so make that first call before any stream
+ *     capture.
+ *   - tile = 0 takes the edge the scene's autotuner chose for this image
+ *     size and number of pose variables in an earlier ar_render_abstract
+ *     call, else 16; this entry point does not time candidates itself.  With
+ *     the same tile the bounds are bit-identical to ar_render_abstract's.
  *   - All calls share the array and it keeps the last call's contents: two
  *     calls that overlap on the GPU (different streams or threads without
  *     ordering) race and corrupt each other's results.  Serialise them.
@@ -295,9 +305,31 @@ int ar_scene_set_boxes(ar_scene *scene, const float *uw_lo3, const float *uw_hi3
  * stage expands around).  The decisions are taken in FP64 in the order of the
  * oracle's steps, so they are bit-identical to a plain FP64 implementation.
  * Synchronous (default stream); uses the scene's workspace, so it must not
- * overlap a render of the same scene.  AR_EINVAL for bad arguments. */
+ * overlap a render of the same scene.  AR_EINVAL for bad arguments.  (out =
+ * NULL only leaves the records of the cell in the scene's workspace.) */
 int ar_debug_records(ar_scene *scene, const ar_intrinsics *intr, const ar_nominal_pose *pose,
                      const ar_pose_box *cell, double *out);
+
+/* Test and diagnosis hook: the per-pixel effective-opacity relaxation
+ * (Algorithm 1 lines 9-10 relaxed, Table 2's Exp) of n (Gaussian, pixel)
+ * pairs of one pose cell, as the batched renderer evaluates them: the record
+ * of Gaussian gi[t] on the cell is built as the renderer builds it, then
+ * evaluated at pixel (px[t], py[t]) in FP32 (precision 0), in FP32 and again
+ * in FP64 where the FP32 deviation estimate alone exceeds the scene's
+ * ar_scene_set_fp64_alpha threshold (precision 1; the renderer also weights it
+ * by the pixel's transmittance), or always in FP64 as well (precision 2).
+ * out: host, [n][40] doubles per pair: the lower opacity form (coefficients of
+ * the 6 pose dimensions tx..rz over the cell normalised to [-1, 1], then the
+ * constant), the upper form (7), the radii bounding the sums of the
+ * coefficients' magnitudes of the two forms, a_lo, a_hi, the FP32 deviation
+ * estimate, m_lo, m_hi, the record's W entries as 6 (lo, hi) intervals, its
+ * S, R_x, R_y as (lo, hi), and flags (1 valid, 2 FP64 taken, 4 MatrixInv
+ * fallback); all 0 where the Gaussian reaches no pixel on the cell.
+ * Synchronous; uses the scene's workspace and allocates a few small device
+ * buffers.  AR_EINVAL for bad arguments or a pair out of range. */
+int ar_debug_alpha(ar_scene *scene, const ar_intrinsics *intr, const ar_nominal_pose *pose,
+                   const ar_pose_box *cell, int32_t n, const int64_t *gi, const int32_t *px, const int32_t *py,
+                   int32_t precision, double *out);
 
 /* Device-memory limit (bytes, >= 1 MiB) for the scene's render workspace.
  * ar_render_abstract splits the cells of a call into batches whose
@@ -328,6 +360,30 @@ int ar_set_profiling(ar_scene *scene, int on);
 #define AR_BLEND_INTERVAL 0
 #define AR_BLEND_RELATIONAL 1
 int ar_scene_set_blend(ar_scene *scene, int32_t mode);
+
+/* Precision of the per-pixel opacity relaxation (Algorithm 1 lines 9-10 with
+ * Table 2's Exp; FP64 in choosing the tangent and secant points of the Exp
+ * relaxation where FP32 cannot carry them).  The FP32 renderer evaluates each
+ * (pixel, Gaussian, cell) triple in FP32 with outward rounding and estimates
+ * how far single precision moves the opacity bounds: the Mahalanobis term m
+ * is a small difference of terms of magnitude about |m_lo| + |m_hi|, so the
+ * estimate is 16 u (|m_lo| + |m_hi|) (a_lo + a_hi [m_lo > 0]) with u = 2^-24.
+ * It is weighted by how far the pixel's bounds can still move with this
+ * Gaussian's opacity: T_hi (the running upper transmittance) unless the upper
+ * bound has already reached 1 in every channel, plus T_lo (the running lower
+ * transmittance).  Where the weighted estimate exceeds `threshold`, the triple
+ * is evaluated again in FP64 from the same record (the m interval, the Exp
+ * points and the opacity forms) and the result is narrowed to FP32 outward.
+ * Both results are sound; the FP64 one is within the record's own FP32
+ * storage error of the FP64 oracle.  threshold = 0 takes every evaluation
+ * with a nonzero estimate in FP64 (slow); a huge value none.  The decision
+ * depends only on the pixel's own sweep, so it is the same for every tile
+ * size and cell batching.  Default AR_FP64_ALPHA_DEFAULT.  Applies to ar_render_abstract, _host, _noalloc,
+ * the partitioned and refined renders and serving; the count is
+ * ar_render_stats.n_fp64.  AR_EINVAL for a null scene or a negative or NaN
+ * threshold. */
+#define AR_FP64_ALPHA_DEFAULT 1e-4f
+int ar_scene_set_fp64_alpha(ar_scene *scene, float threshold);
 
 /* Counters and stage times of the scene's last render (synchronises its stream). */
 int ar_last_render_stats(ar_scene *scene, ar_render_stats *stats);

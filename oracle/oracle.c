@@ -1091,8 +1091,10 @@ static int render_abstract_impl(const double *uw, const double *ls, const double
             idx[K] = i;
             gaussian_alpha(g, ux, uy, &A[K]);
             /* threshold decisions the FP32 path takes in single precision */
-            /* rho is FP64 on both sides; their forms differ by rounding only */
-            if (g->rho_margin < 1e-6) frag = 1;
+            /* rho is FP64 on both sides, from the same X0 (the inverse of the
+             * centre matrix, Sec. 3.1 adjustment (1)); their X forms differ by
+             * FP64 rounding only, far below this margin */
+            if (g->rho_margin < 1e-9) frag = 1;
             if (!g->fallback && A[K].ramp < 0.05) {
                 /* a narrow ramp makes the cutoff nearly a step in m */
                 double tol = 1e-3 * fmax(1.0, g->tau_hi), rp = A[K].ramp;

@@ -37,7 +37,8 @@ class ar_render_stats(ctypes.Structure):
                 ("n_fallback", c_int64), ("n_launches", c_int32), ("tile", c_int32), ("m_vars", c_int32),
                 ("ms_prep", c_float), ("ms_bin", c_float), ("ms_render", c_float), ("ms_total", c_float),
                 ("n_evaluated", c_int64), ("n_reevaluated", c_int64), ("n_built", c_int64),
-                ("n_restarted", c_int64), ("ms_build", c_float), ("n_split", c_int64)]
+                ("n_restarted", c_int64), ("ms_build", c_float), ("n_split", c_int64),
+                ("n_fp64", c_int64), ("n_fp64_segments", c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -70,9 +71,11 @@ def lib():
             "ar_render_abstract_noalloc": ([P, P, P, P, c_int32, c_int32, P, P, P], ctypes.c_int),
             "ar_render_concrete": ([P, P, P, P, c_int32, P, P], ctypes.c_int),
             "ar_debug_records": ([P, P, P, P, P], ctypes.c_int),
+            "ar_debug_alpha": ([P, P, P, P, c_int32, P, P, P, c_int32, P], ctypes.c_int),
             "ar_scene_set_boxes": ([P, P, P, P, P, P, P], ctypes.c_int),
             "ar_set_profiling": ([P, ctypes.c_int], ctypes.c_int),
             "ar_scene_set_blend": ([P, ctypes.c_int32], ctypes.c_int),
+            "ar_scene_set_fp64_alpha": ([P, ctypes.c_float], ctypes.c_int),
             "ar_bounds_union": ([P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P], ctypes.c_int),
             "ar_fp32_fma_rate": ([ctypes.c_int32, ctypes.c_int32, P, P], ctypes.c_int),
             "ar_partition_piece": ([P, P, c_int64, P], ctypes.c_int),
@@ -240,6 +243,17 @@ def ar_debug_records(scene, intr, pose, cell, n: int) -> np.ndarray:
     return out
 
 
+def ar_debug_alpha(scene, intr, pose, cell, gi, px, py, precision: int = 0) -> np.ndarray:
+    gi = np.ascontiguousarray(gi, dtype=np.int64).reshape(-1)
+    px = np.ascontiguousarray(px, dtype=np.int32).reshape(-1)
+    py = np.ascontiguousarray(py, dtype=np.int32).reshape(-1)
+    n = gi.size
+    out = np.zeros((n, 40), dtype=np.float64)
+    check(lib().ar_debug_alpha(scene, ctypes.byref(intr), ctypes.byref(pose), ctypes.byref(cell), n,
+                               _ptr(gi), _ptr(px), _ptr(py), int(precision), _ptr(out)))
+    return out
+
+
 def ar_set_workspace_limit(scene, nbytes: int):
     return check(lib().ar_set_workspace_limit(scene, int(nbytes)))
 
@@ -253,6 +267,10 @@ AR_BLEND_INTERVAL, AR_BLEND_RELATIONAL = 0, 1
 
 def ar_scene_set_blend(scene, mode: int):
     return check(lib().ar_scene_set_blend(scene, int(mode)))
+
+
+def ar_scene_set_fp64_alpha(scene, threshold: float):
+    return check(lib().ar_scene_set_fp64_alpha(scene, float(threshold)))
 
 
 def ar_last_render_stats(scene) -> dict:
@@ -341,6 +359,10 @@ class Scene:
     def debug_records(self, cam, cell_lo, cell_hi) -> np.ndarray:
         cells = make_cells(np.reshape(cell_lo, (1, 6)), np.reshape(cell_hi, (1, 6)))
         return ar_debug_records(self.handle, make_intrinsics(cam), make_pose(cam), cells[0], self.n)
+
+    def debug_alpha(self, cam, cell_lo, cell_hi, gi, px, py, precision: int = 0) -> np.ndarray:
+        cells = make_cells(np.reshape(cell_lo, (1, 6)), np.reshape(cell_hi, (1, 6)))
+        return ar_debug_alpha(self.handle, make_intrinsics(cam), make_pose(cam), cells[0], gi, px, py, precision)
 
     def render_plain_fp64(self, cam, cells_lo, cells_hi, out_lower, out_upper, tile: int = 0, stream=0):
         cells = make_cells(cells_lo, cells_hi)

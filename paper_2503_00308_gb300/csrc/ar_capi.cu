@@ -28,8 +28,9 @@ namespace ar {
 constexpr int kEventsPerBatch = 9;
 // device counters of one cell batch: opacity evaluations, re-evaluations,
 // MatrixInv fallbacks and records built (record build), MatrixInv input
-// splits (record build), segments restarted (render)
-constexpr int kCountersPerBatch = 6;
+// splits (record build), segments restarted (render), evaluations taken
+// again in FP64 (render), segments swept again for them (render)
+constexpr int kCountersPerBatch = 8;
 }  // namespace ar
 
 namespace ar {
@@ -69,6 +70,19 @@ int launch_record_build_m4(const double *, const CallConst &, const void *, int6
 int launch_record_build_m6(const double *, const CallConst &, const void *, int64_t, const uint32_t *,
                            const uint32_t *, float *, unsigned long long *, uint32_t *, uint32_t *, uint32_t, uint32_t *,
                            cudaStream_t);
+int launch_debug_alpha_m1(const float *, int, const int64_t *, const int32_t *, const int32_t *, int, float, double *,
+                          cudaStream_t);
+int launch_debug_alpha_m4(const float *, int, const int64_t *, const int32_t *, const int32_t *, int, float, double *,
+                          cudaStream_t);
+int launch_debug_alpha_m6(const float *, int, const int64_t *, const int32_t *, const int32_t *, int, float, double *,
+                          cudaStream_t);
+static int launch_debug_alpha(int M, const float *recs, int n, const int64_t *gi, const int32_t *px, const int32_t *py,
+                              int precision, float fp64_dev, double *out, cudaStream_t st)
+{
+    if (M == 1) return launch_debug_alpha_m1(recs, n, gi, px, py, precision, fp64_dev, out, st);
+    if (M == 4) return launch_debug_alpha_m4(recs, n, gi, px, py, precision, fp64_dev, out, st);
+    return launch_debug_alpha_m6(recs, n, gi, px, py, precision, fp64_dev, out, st);
+}
 int launch_render_plain_m1(int, const RenderLaunch &, cudaStream_t);
 int launch_render_plain_m4(int, const RenderLaunch &, cudaStream_t);
 int launch_render_plain_m6(int, const RenderLaunch &, cudaStream_t);
@@ -192,7 +206,7 @@ void Workspace::release()
 {
     DevBuf *all[] = {&cells_lohi, &cells, &vN, &recs, &boxes, &keys, &counters, &evk0, &evk1, &evv0, &evv1,
                      &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege, &segk0,
-                     &segk1, &segv0, &segv1, &work, &state, &wlist, &act0, &act1, &words, &slist, &whist, &out_lo,
+                     &segk1, &segv0, &segv1, &work, &state, &wlist, &act0, &act1, &words, &slist, &plist, &whist, &out_lo,
                      &out_hi, &part_lo, &part_hi, &lvl_lo, &lvl_hi, &wpart};
     for (DevBuf *b : all) b->release();
     if (h_whist) cudaFreeHost(h_whist);
@@ -209,7 +223,7 @@ size_t Workspace::bytes() const
     const DevBuf *all[] = {&cells_lohi, &cells, &vN, &recs, &boxes, &keys, &counters, &evk0, &evk1, &evv0, &evv1,
                            &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege,
                            &segk0, &segk1, &segv0, &segv1, &work, &state, &wlist, &act0, &act1, &words,
-                           &slist, &whist, &out_lo, &out_hi, &part_lo, &part_hi, &lvl_lo, &lvl_hi, &wpart};
+                           &slist, &plist, &whist, &out_lo, &out_hi, &part_lo, &part_hi, &lvl_lo, &lvl_hi, &wpart};
     size_t s = 0;
     for (const DevBuf *b : all) s += b->cap;
     return s;
@@ -394,6 +408,14 @@ int ar_scene_set_blend(ar_scene *s, int32_t mode)
     return AR_OK;
 }
 
+int ar_scene_set_fp64_alpha(ar_scene *s, float threshold)
+{
+    if (!s) return fail(AR_EINVAL, "scene is null");
+    if (!(threshold >= 0.f)) return fail(AR_EINVAL, "threshold must be >= 0 (not NaN)");
+    s->fp64_dev = threshold;
+    return AR_OK;
+}
+
 // ---------------------------------------------------------------- render
 namespace ar {
 
@@ -553,6 +575,7 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
     rl.n_gauss = s->n;
     rl.k_open = s->k_open;
     rl.rel = s->blend == AR_BLEND_RELATIONAL;
+    rl.fp64_dev = s->fp64_dev;
     rl.out_lo = out_lo;
     rl.out_hi = out_hi;
     rl.counters = ws.counters.as<unsigned long long>() + 8 + kCountersPerBatch * batch;
@@ -570,11 +593,12 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
         RK(ws.act1.ensure(sizeof(uint32_t) * n_seg));
         RK(ws.words.ensure(sizeof(uint32_t) * 8));
         RK(ws.slist.ensure(sizeof(uint32_t) * n_pairs));
+        RK(ws.plist.ensure(sizeof(uint32_t) * n_seg));
         rl.sweep_hist = ws.whist.as<uint32_t>();
         RK(run_windowed_render(M, TS, rl, cc, ws.cells.p, ws.vN.as<double>(), n_pairs, n_seg, ws.state.as<uint32_t>(),
                                ws.wlist.as<uint32_t>(), ws.act0.as<uint32_t>(), ws.act1.as<uint32_t>(),
                                ws.words.as<uint32_t>(), rl.counters + 2, st, &launches,
-                               profiling ? ev + 3 : nullptr, ws.w0, ws.slist.as<uint32_t>()));
+                               profiling ? ev + 3 : nullptr, ws.w0, ws.slist.as<uint32_t>(), ws.plist.as<uint32_t>()));
     }
     return AR_OK;
 }
@@ -600,7 +624,7 @@ uint32_t learned_window(const uint32_t *hist256)
 int run_windowed_render(int M, int TS, RenderLaunch rl, const CallConst &cc, const void *cells, const double *vN,
                         uint64_t n_pairs, uint64_t n_seg, uint32_t *state, uint32_t *wlist, uint32_t *act0,
                         uint32_t *act1, uint32_t *words, unsigned long long *build_counters, cudaStream_t st,
-                        int *launches, cudaEvent_t *ev, uint32_t w0, uint32_t *split_list)
+                        int *launches, cudaEvent_t *ev, uint32_t w0, uint32_t *split_list, uint32_t *precise_list)
 {
     const uint32_t kWindow[3] = {w0, w0 < 8192u ? 8192u : 0xffffffffu, 0xffffffffu};
     uint32_t *act[2] = {act0, act1};
@@ -625,10 +649,23 @@ int run_windowed_render(int M, int TS, RenderLaunch rl, const CallConst &cc, con
         rl.window = kWindow[r];
         rl.next_active = act[r & 1];
         rl.n_next = nxt_n;
+        rl.precise = precise_list;
+        rl.n_precise = words + 5;
+        CK(cudaMemsetAsync(words + 5, 0, sizeof(uint32_t), st));
+        rl.f64 = 0;
         if (launch_render(M, TS, rl, st))
             return fail(AR_EDEVICE, "render launch: %s", cudaGetErrorString(cudaGetLastError()));
+        // the segments that met an evaluation needing FP64, swept again from
+        // their start by the FP64-capable instance (window abandons go to the
+        // same next list)
+        RenderLaunch rp = rl;
+        rp.active = precise_list;
+        rp.n_active = words + 5;
+        rp.f64 = 1;
+        if (launch_render(M, TS, rp, st))
+            return fail(AR_EDEVICE, "render launch: %s", cudaGetErrorString(cudaGetLastError()));
         if (ev) CK(cudaEventRecord(ev[2 * r + 1], st));
-        *launches += 3;
+        *launches += 6;
     }
     return AR_OK;
 }
@@ -810,6 +847,8 @@ int finish_stats(Workspace &ws, cudaStream_t st, bool profiling, ar_render_stats
         rs.n_built = ws.built_prep;
         rs.n_split = ws.split_prep;
         rs.n_restarted = 0;
+        rs.n_fp64 = 0;
+        rs.n_fp64_segments = 0;
         for (int b = 0; b < ws.n_batches; ++b) {
             const unsigned long long *c = &ev[(size_t)kCountersPerBatch * b];
             rs.n_evaluated += (int64_t)c[0];
@@ -818,6 +857,8 @@ int finish_stats(Workspace &ws, cudaStream_t st, bool profiling, ar_render_stats
             rs.n_built += (int64_t)c[3];
             rs.n_split += (int64_t)c[4];
             rs.n_restarted += (int64_t)c[5];
+            rs.n_fp64 += (int64_t)c[6];
+            rs.n_fp64_segments += (int64_t)c[7];
         }
     }
     if (profiling && ws.n_batches > 0) {
@@ -1172,7 +1213,7 @@ int ar_render_concrete(ar_scene *s, const ar_intrinsics *in, const ar_nominal_po
 int ar_debug_records(ar_scene *s, const ar_intrinsics *in, const ar_nominal_pose *pose, const ar_pose_box *cell,
                      double *out)
 {
-    if (!s || !out) return fail(AR_EINVAL, "null argument");
+    if (!s) return fail(AR_EINVAL, "null argument");
     RK(validate_call(in, pose, cell, 1, 16));
     CK(cudaSetDevice(s->device));
     if (s->n == 0) return AR_OK;
@@ -1198,6 +1239,7 @@ int ar_debug_records(ar_scene *s, const ar_intrinsics *in, const ar_nominal_pose
         launch_record_prep(M, ws.vN.as<double>(), s->gp, cc, ws.cells.p, 16, ws.recs.as<float>(),
                            ws.boxes.as<PixBox>(), ws.keys.as<double>(), ws.counters.as<unsigned long long>(), st))
         return fail(AR_EDEVICE, "record prep launch: %s", cudaGetErrorString(cudaGetLastError()));
+    if (!out) return AR_OK;  // (ar_debug_alpha: the device records are what it needs)
     const int w = rec_width(M);
     std::vector<PixBox> boxes((size_t)n);
     std::vector<double> keys((size_t)2 * n);
@@ -1222,6 +1264,89 @@ int ar_debug_records(ar_scene *s, const ar_intrinsics *in, const ar_nominal_pose
         o[4] = b.x0; o[5] = b.x1; o[6] = b.y0; o[7] = b.y1;
         o[8] = r[sc + 7];
         o[9] = r[sc + 8];
+    }
+    return AR_OK;
+}
+
+int ar_debug_alpha(ar_scene *s, const ar_intrinsics *in, const ar_nominal_pose *pose, const ar_pose_box *cell,
+                   int32_t n, const int64_t *gi, const int32_t *px, const int32_t *py, int32_t precision, double *out)
+{
+    constexpr int OW = 42, W_OUT = 40;
+    if (!s || !out || (n > 0 && (!gi || !px || !py))) return fail(AR_EINVAL, "null argument");
+    if (n < 0 || n > (1 << 20)) return fail(AR_EINVAL, "n must be in [0, 2^20]");
+    if (precision < 0 || precision > 2) return fail(AR_EINVAL, "precision must be 0, 1 or 2");
+    for (int32_t t = 0; t < n; ++t)
+        if (gi[t] < 0 || gi[t] >= s->n || px[t] < 0 || py[t] < 0 || px[t] >= in->width || py[t] >= in->height)
+            return fail(AR_EINVAL, "triple %d out of range", t);
+    RK(ar_debug_records(s, in, pose, cell, nullptr));
+    if (n == 0) return AR_OK;
+    Workspace &ws = s->ws;
+    CallConst cc;
+    const int M = call_const(s, in, pose, cell, 1, cc);
+    // the value parts of the listed pairs (cell 0: pair index = Gaussian index);
+    // pairs that reach no pixel keep their decision part only
+    std::vector<PixBox> boxes((size_t)s->n);
+    CK(cudaMemcpy(boxes.data(), ws.boxes.p, sizeof(PixBox) * s->n, cudaMemcpyDeviceToHost));
+    std::vector<uint32_t> work;
+    for (int32_t t = 0; t < n; ++t)
+        if (boxes[(size_t)gi[t]].x0 >= 0) work.push_back((uint32_t)gi[t]);
+    std::sort(work.begin(), work.end());
+    work.erase(std::unique(work.begin(), work.end()), work.end());
+    const uint32_t nw = (uint32_t)work.size();
+    uint32_t *d_work = nullptr, *d_words = nullptr, *d_list = nullptr;
+    int64_t *d_gi = nullptr;
+    int32_t *d_px = nullptr, *d_py = nullptr;
+    double *d_out = nullptr;
+    int rc = AR_OK;
+    auto cleanup = [&]() {
+        cudaFree(d_work); cudaFree(d_words); cudaFree(d_list); cudaFree(d_gi); cudaFree(d_px); cudaFree(d_py);
+        cudaFree(d_out);
+    };
+    if (cudaMalloc(&d_work, sizeof(uint32_t) * (nw + 1)) != cudaSuccess ||
+        cudaMalloc(&d_words, sizeof(uint32_t) * 8) != cudaSuccess ||
+        cudaMalloc(&d_list, sizeof(uint32_t) * (nw + 1)) != cudaSuccess ||
+        cudaMalloc(&d_gi, sizeof(int64_t) * n) != cudaSuccess || cudaMalloc(&d_px, sizeof(int32_t) * n) != cudaSuccess ||
+        cudaMalloc(&d_py, sizeof(int32_t) * n) != cudaSuccess ||
+        cudaMalloc(&d_out, sizeof(double) * OW * n) != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return fail(AR_ENOMEM, "debug buffers");
+    }
+    uint32_t words[8] = {nw, 0, 0, 0, 0, 0, 0, 0};
+    if (cudaMemcpy(d_work, work.data(), sizeof(uint32_t) * nw, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_words, words, sizeof words, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_gi, gi, sizeof(int64_t) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_px, px, sizeof(int32_t) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_py, py, sizeof(int32_t) * n, cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = fail(AR_EDEVICE, "debug copies: %s", cudaGetErrorString(cudaGetLastError()));
+    if (rc == AR_OK && nw > 0 &&
+        launch_record_build(M, ws.vN.as<double>(), cc, ws.cells.p, s->n, d_work, d_words, ws.recs.as<float>(), nullptr,
+                            d_list, d_words + 3, nw, d_words + 4, 0))
+        rc = fail(AR_EDEVICE, "record build launch: %s", cudaGetErrorString(cudaGetLastError()));
+    if (rc == AR_OK &&
+        launch_debug_alpha(M, ws.recs.as<float>(), n, d_gi, d_px, d_py, precision, s->fp64_dev, d_out, 0))
+        rc = fail(AR_EDEVICE, "debug launch: %s", cudaGetErrorString(cudaGetLastError()));
+    std::vector<double> h((size_t)OW * n);
+    if (rc == AR_OK && cudaMemcpy(h.data(), d_out, sizeof(double) * OW * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = fail(AR_EDEVICE, "debug read-back: %s", cudaGetErrorString(cudaGetLastError()));
+    cleanup();
+    if (rc != AR_OK) return rc;
+    // coefficients by pose dimension (slot order -> dimension order)
+    for (int32_t t = 0; t < n; ++t) {
+        const double *g = &h[(size_t)OW * t];
+        double *o = out + (size_t)W_OUT * t;
+        for (int k = 0; k < W_OUT; ++k) o[k] = 0.0;
+        if (boxes[(size_t)gi[t]].x0 < 0) continue;
+        for (int k = 0; k < MAXV; ++k) {
+            const int sl = cc.m_slot[k];
+            o[k] = sl >= 0 ? g[sl] : 0.0;
+            o[7 + k] = sl >= 0 ? g[7 + sl] : 0.0;
+        }
+        o[6] = g[6];
+        o[13] = g[13];
+        for (int k = 14; k < 21; ++k) o[k] = g[k];   // rL rU alo ahi dev mlo mhi
+        for (int k = 21; k < 39; ++k) o[k] = g[k];   // W, S, Rx, Ry intervals
+        o[39] = 1.0 + 2.0 * g[40] + 4.0 * (((uint32_t)g[39] & 1u) != 0);  // valid, FP64 taken, fallback
     }
     return AR_OK;
 }

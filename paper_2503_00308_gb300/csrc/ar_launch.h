@@ -24,11 +24,18 @@ struct RenderLaunch {
     int W, H, ntx, n_tiles, n_cells;
     int64_t n_gauss;
     float k_open;                     // 1 / (1 - largest opacity), rounded up
+    float fp64_dev = 3.0e38f;         // opacity evaluations whose FP32 deviation estimate exceeds this
+                                      // are taken again in FP64 (pixel_alpha_fp64)
     float *out_lo, *out_hi;
     unsigned long long *counters;     // optional: [0] opacity evaluations, [1] re-evaluations,
-                                      // [5] segments abandoned for a wider window ([2]-[4]: record build)
+                                      // [5] segments abandoned for a wider window ([2]-[4]: record build),
+                                      // [6] evaluations taken again in FP64, [7] segments swept again for them
     unsigned int *work;               // segment counter of the persistent grid (zeroed by the launcher)
     int rel = 0;                      // 1: relational upper transmittance (AR_BLEND_RELATIONAL)
+    // precision: the FP32 sweep (f64 = 0) appends a segment that needs an FP64
+    // evaluation to precise[*n_precise]; the f64 = 1 instance sweeps that list
+    int f64 = 0;
+    uint32_t *precise = nullptr, *n_precise = nullptr;
 };
 
 size_t cell_data_bytes(int M);

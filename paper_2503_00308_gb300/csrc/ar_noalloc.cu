@@ -33,25 +33,21 @@ constexpr int kMaxDevices = 64;
 // cudaGetSymbolAddress returns for the current device.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
-static void *g_scratch_addr[kMaxDevices];
-static std::mutex g_scratch_mu;
-
-// Device address of the scratch array on the current device; looked up once
-// per device (the first call on a device does this set-up).
+// Device address of the scratch array on the current device, looked up on
+// every call (with that device current) so that no address outlives a device
+// reset or a re-created context.  Once the library's module is loaded on the
+// device the lookup allocates nothing; the first call on a device may load
+// it, which is the set-up the first call does.
 static int scratch_base(int device, unsigned char **out)
 {
     if (device < 0 || device >= kMaxDevices) return set_last_error(AR_EDEVICE, "device index out of range");
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            return set_last_error(AR_EDEVICE, "cudaGetSymbolAddress of the no-allocation scratch array failed");
-        }
-        g_scratch_addr[device] = p;
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return set_last_error(AR_EDEVICE, "cudaGetSymbolAddress of the no-allocation scratch array failed");
     }
-    *out = (unsigned char *)g_scratch_addr[device];
+    *out = (unsigned char *)p;
     return AR_OK;
 }
 
@@ -105,7 +101,7 @@ int ar_render_abstract_noalloc(ar_scene *s, const ar_intrinsics *in, const ar_no
     NA_CK(cudaSetDevice(s->device));
     unsigned char *base = nullptr;
     if ((r = scratch_base(s->device, &base))) return r;
-    const int W = in->width, H = in->height, TS = tile ? tile : 16;
+    const int W = in->width, H = in->height;
     const size_t out_words = (size_t)n_cells * W * H * 3;
     if (s->n == 0) {
         NA_CK(cudaMemsetAsync(out_lower, 0, out_words * sizeof(float), st));
@@ -121,6 +117,16 @@ int ar_render_abstract_noalloc(ar_scene *s, const ar_intrinsics *in, const ar_no
         cc.m_slot[k] = act ? m_active++ : -1;
     }
     const int M = m_active <= 1 ? 1 : (m_active <= 4 ? 4 : 6);
+    // tile = 0: the edge the scene's autotuner chose for this image size and
+    // number of pose variables, if an earlier ar_render_abstract call tuned
+    // it; else 16 (this entry point does not time candidates itself)
+    int TS = tile;
+    if (TS == 0) {
+        TS = 16;
+        std::lock_guard<std::mutex> lock(s->tune_mu);
+        for (const TunedTile &t : s->tuned)
+            if (t.W == W && t.H == H && t.M == M) TS = t.TS;
+    }
     cc.W = W; cc.H = H;
     cc.fx = in->fx; cc.fy = in->fy; cc.cx = in->cx; cc.cy = in->cy; cc.near_plane = in->near_plane;
     std::memcpy(cc.R0, pose->R_wc, sizeof cc.R0);
@@ -147,6 +153,7 @@ int ar_render_abstract_noalloc(ar_scene *s, const ar_intrinsics *in, const ar_no
     uint32_t *state = A.take<uint32_t>(n_pairs), *wlist = A.take<uint32_t>(n_pairs);
     uint32_t *slist = A.take<uint32_t>(n_pairs);
     uint32_t *act0 = A.take<uint32_t>(n_seg), *act1 = A.take<uint32_t>(n_seg), *words = A.take<uint32_t>(8);
+    uint32_t *plist = A.take<uint32_t>(n_seg);
     if (A.over) return too_big("the per-(Gaussian, cell) records", A.used);
 
     // pose cells: lo and hi rows straight from the caller's array (no staging copy)
@@ -213,9 +220,10 @@ int ar_render_abstract_noalloc(ar_scene *s, const ar_intrinsics *in, const ar_no
     rl.n_gauss = s->n;
     rl.k_open = s->k_open;
     rl.rel = s->blend == AR_BLEND_RELATIONAL;
+    rl.fp64_dev = s->fp64_dev;
     rl.out_lo = out_lower;
     rl.out_hi = out_upper;
     rl.counters = nullptr;
     return run_windowed_render(M, TS, rl, cc, cellbuf, vN, n_pairs, n_seg, state, wlist, act0, act1, words, nullptr,
-                               st, &launches, nullptr, 512u, slist);
+                               st, &launches, nullptr, 512u, slist, plist);
 }

@@ -61,7 +61,7 @@ int AR_CAT(launch_render_plain_m, AR_M)(int TS, const RenderLaunch &a, cudaStrea
     return TS == 16 ? launch_render_plain_ts<16>(a, st) : launch_render_plain_ts<8>(a, st);
 }
 
-template <int TS, bool REL>
+template <int TS, bool REL, bool F64>
 static int launch_render_ts(const RenderLaunch &a, cudaStream_t st)
 {
     // double-buffered chunks of 16 events and a ring of 4 (measured best of
@@ -69,7 +69,7 @@ static int launch_render_ts(const RenderLaunch &a, cudaStream_t st)
     // tile sooner with short chunks; the ring's shared memory stays small)
     constexpr int CH = 16, RING = 4;
     typedef RenderSmem<AR_M, TS, CH, RING> SM;
-    auto kern = render_kernel<AR_M, TS, CH, RING, REL>;
+    auto kern = render_kernel<AR_M, TS, CH, RING, REL, F64>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::BYTES) != cudaSuccess)
         return 1;
     int dev = 0, sms = 0, per_sm = 0;
@@ -82,8 +82,9 @@ static int launch_render_ts(const RenderLaunch &a, cudaStream_t st)
     if (grid > nseg) grid = nseg;
     if (cudaMemsetAsync(a.work, 0, sizeof(unsigned int), st) != cudaSuccess) return 1;
     kern<<<grid, TS * TS, SM::BYTES, st>>>(a.recs, a.boxes, a.seg_start, a.seg_end, a.active, a.n_active, a.window,
-                                           a.next_active, a.n_next, a.sweep_hist, a.ent_ev, a.ev_val,
-                                           a.ev_key, a.W, a.H, a.ntx, a.n_tiles, a.n_gauss, a.k_open, a.out_lo,
+                                           a.next_active, a.n_next, a.precise, a.n_precise, a.sweep_hist,
+                                           a.ent_ev, a.ev_val,
+                                           a.ev_key, a.W, a.H, a.ntx, a.n_tiles, a.n_gauss, a.k_open, a.fp64_dev, a.out_lo,
                                            a.out_hi, a.counters, a.work);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
@@ -113,10 +114,22 @@ int AR_CAT(launch_record_build_m, AR_M)(const double *vN, const CallConst &cc, c
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 
+int AR_CAT(launch_debug_alpha_m, AR_M)(const float *recs, int n, const int64_t *gi, const int32_t *px,
+                                       const int32_t *py, int precision, float fp64_dev, double *out,
+                                       cudaStream_t st)
+{
+    debug_alpha_kernel<AR_M><<<(n + 63) / 64, 64, 0, st>>>(recs, n, gi, px, py, precision, fp64_dev, out);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
 int AR_CAT(launch_render_m, AR_M)(int TS, const RenderLaunch &a, cudaStream_t st)
 {
-    if (a.rel) return TS == 16 ? launch_render_ts<16, true>(a, st) : launch_render_ts<8, true>(a, st);
-    return TS == 16 ? launch_render_ts<16, false>(a, st) : launch_render_ts<8, false>(a, st);
+    if (a.f64) {
+        if (a.rel) return TS == 16 ? launch_render_ts<16, true, true>(a, st) : launch_render_ts<8, true, true>(a, st);
+        return TS == 16 ? launch_render_ts<16, false, true>(a, st) : launch_render_ts<8, false, true>(a, st);
+    }
+    if (a.rel) return TS == 16 ? launch_render_ts<16, true, false>(a, st) : launch_render_ts<8, true, false>(a, st);
+    return TS == 16 ? launch_render_ts<16, false, false>(a, st) : launch_render_ts<8, false, false>(a, st);
 }
 
 }  // namespace ar

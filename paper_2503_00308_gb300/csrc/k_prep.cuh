@@ -567,28 +567,33 @@ __device__ __forceinline__ int64_t record_decide(const double *__restrict__ vN, 
 }
 
 // MatrixInv (Algorithm 3) on X, FP64 forms over a box (X10 = X01): X0 is
-// the inverse of the centre matrix (adjustment (1) of Sec. 3.1), rounded to
-// the record precision so that the same constant enters I - X X0 and X0 *
-// sum; E = I - X X0 and its Frobenius norm bound rho are formed in FP64, the
-// series in the record precision.  The order starts at the default KTAYLOR
-// and grows while the remainder bound rho^(k+1) / (1 - rho) exceeds EPS_TOL
-// (relative to ||X0||_F), up to KMAX (adjustment (3)).  Returns MI_FAIL when
-// the centre matrix is not positive definite or rho >= RHO_MAX, MI_KHIGH
-// (without running the series) when the order would exceed KC, else MI_OK.
-// (KC = KTAYLOR fixes the series length at compile time.)
+// the inverse of the centre matrix (adjustment (1) of Sec. 3.1), in FP64 as
+// the oracle takes it, so that rho, and with it the assertion of Algorithm 3
+// and the Taylor order, is the oracle's up to FP64 rounding; E = I - X X0 and
+// rho are formed in FP64, E is rounded outward to the series precision RS,
+// the series T = sum_{i=1..k} E^i runs in RS, and Conic = X0 (I + T) +- Eps
+// is assembled in FP64 with the same X0.  (The assembly's constants are of the size of X0; in
+// FP32 their outward rounding would widen every entry of W = Conic Mp by a
+// few u of its size, which the Mahalanobis term of far pixels multiplies by
+// 2 |q|^2.  T is small, ||T|| <= rho / (1 - rho), so its FP32 error is not.)
+// The order starts at the default KTAYLOR and grows while the remainder
+// bound rho^(k+1) / (1 - rho) exceeds EPS_TOL (relative to ||X0||_F), up to
+// KMAX (adjustment (3)).  Returns MI_FAIL when the centre matrix is not
+// positive definite or rho >= RHO_MAX, MI_KHIGH (without running the series)
+// when the order would exceed KC, else MI_OK.  (KC = KTAYLOR fixes the series
+// length at compile time.)
 enum { MI_FAIL = 0, MI_OK = 1, MI_KHIGH = 2 };
-template <int M, class RO, int KC = KMAX>
-__device__ __forceinline__ int matinv_box(const SB<M, double> X[4], SB<M, RO> conic[4])
+template <int M, class RS, int KC = KMAX>
+__device__ __forceinline__ int matinv_box(const SB<M, double> X[4], SB<M, double> conic[4])
 {
-    using NO = Num<RO>;
-    typedef SB<M, RO> B;
+    typedef SB<M, RS> B;
     typedef SB<M, double> BD;
     typedef SAcc<M, double> AD;
     const double h00 = 0.5 * (X[0].vlo + X[0].vhi), h01 = 0.5 * (X[1].vlo + X[1].vhi);
     const double h11 = 0.5 * (X[3].vlo + X[3].vhi);
     const double det = h00 * h11 - h01 * h01;
     if (!(det > 0.0) || !(h00 > 0.0) || !isfinite(det)) return false;
-    const RO X0[4] = {(RO)(h11 / det), (RO)(-h01 / det), (RO)(-h01 / det), (RO)(h00 / det)};
+    const double X0[4] = {h11 / det, -h01 / det, -h01 / det, h00 / det};
     B E[4];
     double rho2 = 0.0;
     for (int r = 0; r < 2; ++r)
@@ -596,8 +601,8 @@ __device__ __forceinline__ int matinv_box(const SB<M, double> X[4], SB<M, RO> co
             AD p;
             const double dl = (r == s) ? 1.0 : 0.0;
             p.init(dl, dl);
-            p.term(-(double)X0[s], X[2 * r]);
-            p.term(-(double)X0[2 + s], X[2 * r + 1]);
+            p.term(-X0[s], X[2 * r]);
+            p.term(-X0[2 + s], X[2 * r + 1]);
             const BD e64 = p.result();
             const double m = fmax(fabs(e64.vlo), fabs(e64.vhi));
             rho2 = __fma_ru(m, m, rho2);
@@ -618,8 +623,6 @@ __device__ __forceinline__ int matinv_box(const SB<M, double> X[4], SB<M, RO> co
     }
     if (k > KC) return MI_KHIGH;
     if (KC == KTAYLOR) k = KTAYLOR;
-    RO rho;
-    rec_up(rho64, rho);
     // T = sum_{i=1..k} (I - X X0)^i, so that Xp = X0 (I + T) = X0 + X0 T: the
     // identity term is added as an exact constant at the end
     B P[4], Ssum[4];
@@ -632,27 +635,29 @@ __device__ __forceinline__ int matinv_box(const SB<M, double> X[4], SB<M, RO> co
         B Q[4];
         for (int r = 0; r < 2; ++r)
             for (int s = 0; s < 2; ++s) {
-                SAcc<M, RO> p;
+                SAcc<M, RS> p;
                 p.init(0, 0);
                 p.mul(P[2 * r], E[s]);
                 p.mul(P[2 * r + 1], E[2 + s]);
                 Q[2 * r + s] = p.result();
             }
-        for (int e = 0; e < 4; ++e) { P[e] = Q[e]; Ssum[e] = sb_add<M, RO>(Ssum[e], Q[e]); }
+        for (int e = 0; e < 4; ++e) { P[e] = Q[e]; Ssum[e] = sb_add<M, RS>(Ssum[e], Q[e]); }
     }
-    RO nX0 = 0;
-    for (int e = 0; e < 4; ++e) nX0 = NO::fma_ru(X0[e], X0[e], nX0);
-    nX0 = NO::sqrt_ru(nX0);
-    RO rk = 1;
-    for (int i = 0; i <= k; ++i) rk = NO::mul_ru(rk, rho);
-    const RO eps = NO::div_ru(NO::mul_ru(nX0, rk), NO::sub_rd(RO(1), rho));
+    // Eps = ||X0||_F rho^(k+1) / (1 - rho), and the assembly, in FP64
+    const double *X0d = X0;
+    double nX0 = 0.0;
+    for (int e = 0; e < 4; ++e) nX0 = __fma_ru(X0d[e], X0d[e], nX0);
+    nX0 = __dsqrt_ru(nX0);
+    double rk = 1.0;
+    for (int i = 0; i <= k; ++i) rk = __dmul_ru(rk, rho64);
+    const double eps = __ddiv_ru(__dmul_ru(nX0, rk), __dsub_rd(1.0, rho64));
     for (int r = 0; r < 2; ++r)
         for (int s = 0; s < 2; ++s) {
-            SAcc<M, RO> p;
+            AD p;
             // X0[r][s] + eps-widening, then + X0 T
-            p.init(NO::sub_rd(X0[2 * r + s], eps), NO::add_ru(X0[2 * r + s], eps));
-            p.term(X0[2 * r], Ssum[s]);
-            p.term(X0[2 * r + 1], Ssum[2 + s]);
+            p.init(__dsub_rd(X0d[2 * r + s], eps), __dadd_ru(X0d[2 * r + s], eps));
+            p.term(X0d[2 * r], to_f64<M>(Ssum[s]));
+            p.term(X0d[2 * r + 1], to_f64<M>(Ssum[2 + s]));
             conic[2 * r + s] = p.result();
         }
     return true;
@@ -703,8 +708,8 @@ __device__ __forceinline__ int split_var(const SB<M, double> Xr[4])
 // the pieces.  Returns the number of pieces, or 0 if a piece at the depth
 // limit still fails.  At most one pending sibling per level waits on the
 // stack, so SPLIT_DEPTH + 1 entries suffice.
-template <int M, class RO>
-__device__ __noinline__ int matinv_split(const SB<M, double> X[4], SB<M, RO> conic[4])
+template <int M, class RS>
+__device__ __noinline__ int matinv_split(const SB<M, double> X[4], SB<M, double> conic[4])
 {
     struct Piece {
         double ctr[M], h[M];
@@ -712,10 +717,10 @@ __device__ __noinline__ int matinv_split(const SB<M, double> X[4], SB<M, RO> con
     };
     Piece st[SPLIT_DEPTH + 1];
     int top = 0;
-    RO lo[4], hi[4];
+    double lo[4], hi[4];
     for (int e = 0; e < 4; ++e) {
-        lo[e] = Num<RO>::BIG;
-        hi[e] = -Num<RO>::BIG;
+        lo[e] = Num<double>::BIG;
+        hi[e] = -Num<double>::BIG;
     }
     // push the two halves of a piece, the upper one first
     auto push_halves = [&](const double *ctr, const double *h, int depth, const SB<M, double> Xr[4]) {
@@ -744,11 +749,11 @@ __device__ __noinline__ int matinv_split(const SB<M, double> X[4], SB<M, RO> con
         const Piece q = st[--top];
         SB<M, double> Xr[4];
         for (int e = 0; e < 4; ++e) Xr[e] = sb_restrict<M>(X[e], q.ctr, q.h);
-        SB<M, RO> C[4];
-        if (matinv_box<M, RO>(Xr, C) == MI_OK) {
+        SB<M, double> C[4];
+        if (matinv_box<M, RS>(Xr, C) == MI_OK) {
             for (int e = 0; e < 4; ++e) {
-                lo[e] = Num<RO>::min(lo[e], C[e].vlo);
-                hi[e] = Num<RO>::max(hi[e], C[e].vhi);
+                lo[e] = fmin(lo[e], C[e].vlo);
+                hi[e] = fmax(hi[e], C[e].vhi);
             }
             ++pieces;
         } else if (q.depth < SPLIT_DEPTH) {
@@ -757,7 +762,7 @@ __device__ __noinline__ int matinv_split(const SB<M, double> X[4], SB<M, RO> con
             return 0;
         }
     }
-    for (int e = 0; e < 4; ++e) conic[e] = sb_cst<M, RO>(lo[e], hi[e]);
+    for (int e = 0; e < 4; ++e) conic[e] = sb_cst<M, double>(lo[e], hi[e]);
     return pieces;
 }
 
@@ -793,15 +798,15 @@ __device__ __forceinline__ void piece_box(uint64_t pc, double *ctr, double *h)
 // passes the same X and gets the same result; list is the warp's 2 x 64
 // shared-memory piece lists.  Returns the number of pieces, or 0 if a piece
 // at the depth limit still fails.
-template <int M, class RO>
-__device__ __noinline__ int matinv_split_warp(const SB<M, double> X[4], SB<M, RO> conic[4], uint64_t *list)
+template <int M, class RS>
+__device__ __noinline__ int matinv_split_warp(const SB<M, double> X[4], SB<M, double> conic[4], uint64_t *list)
 {
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
-    RO lo[4], hi[4];
+    double lo[4], hi[4];
     for (int e = 0; e < 4; ++e) {
-        lo[e] = Num<RO>::BIG;
-        hi[e] = -Num<RO>::BIG;
+        lo[e] = Num<double>::BIG;
+        hi[e] = -Num<double>::BIG;
     }
     int pieces = 0;
     bool failed = false;
@@ -827,11 +832,11 @@ __device__ __noinline__ int matinv_split_warp(const SB<M, double> X[4], SB<M, RO
                 piece_box<M>(pc, ctr, h);
                 SB<M, double> Xr[4];
                 for (int e = 0; e < 4; ++e) Xr[e] = sb_restrict<M>(X[e], ctr, h);
-                SB<M, RO> C[4];
-                if (matinv_box<M, RO>(Xr, C) == MI_OK) {
+                SB<M, double> C[4];
+                if (matinv_box<M, RS>(Xr, C) == MI_OK) {
                     for (int e = 0; e < 4; ++e) {
-                        lo[e] = Num<RO>::min(lo[e], C[e].vlo);
-                        hi[e] = Num<RO>::max(hi[e], C[e].vhi);
+                        lo[e] = fmin(lo[e], C[e].vlo);
+                        hi[e] = fmax(hi[e], C[e].vhi);
                     }
                     ++pieces;
                 } else if (depth < SPLIT_DEPTH) {
@@ -857,11 +862,11 @@ __device__ __noinline__ int matinv_split_warp(const SB<M, double> X[4], SB<M, RO
     for (int off = 16; off > 0; off >>= 1) {
         pieces += __shfl_xor_sync(full, pieces, off);
         for (int e = 0; e < 4; ++e) {
-            lo[e] = Num<RO>::min(lo[e], __shfl_xor_sync(full, lo[e], off));
-            hi[e] = Num<RO>::max(hi[e], __shfl_xor_sync(full, hi[e], off));
+            lo[e] = fmin(lo[e], __shfl_xor_sync(full, lo[e], off));
+            hi[e] = fmax(hi[e], __shfl_xor_sync(full, hi[e], off));
         }
     }
-    for (int e = 0; e < 4; ++e) conic[e] = sb_cst<M, RO>(lo[e], hi[e]);
+    for (int e = 0; e < 4; ++e) conic[e] = sb_cst<M, double>(lo[e], hi[e]);
     return pieces;
 }
 
@@ -964,7 +969,9 @@ __device__ __forceinline__ uint32_t record_value(const double *__restrict__ v, f
     // ---- MatrixInv (Algorithm 3) with the adaptive order and, where its
     // assertion fails on the cell, the input splitting of Sec. 3.1
     bool fallback = false;
-    B conic[4];
+    // Conic as FP64 forms (see matinv_box: the series in the record
+    // precision, the assembly in FP64)
+    SB<M, double> conic[4];
     {
         BD X[4];
         {
@@ -996,11 +1003,11 @@ __device__ __forceinline__ uint32_t record_value(const double *__restrict__ v, f
     if (!fallback) {
         for (int r = 0; r < 2; ++r)
             for (int c = 0; c < 3; ++c) {
-                // W = Conic Mp in FP64 (FP32 Conic forms are exact in FP64)
+                // W = Conic Mp in FP64
                 AD p;
                 p.init(0.0, 0.0);
-                p.mul(to_f64<M>(conic[2 * r]), Mp64[c]);
-                p.mul(to_f64<M>(conic[2 * r + 1]), Mp64[3 + c]);
+                p.mul(conic[2 * r], Mp64[c]);
+                p.mul(conic[2 * r + 1], Mp64[3 + c]);
                 B w;
                 sb_to_rec<M>(p.result(), w);
                 if (!sb_finite(w)) fallback = true;

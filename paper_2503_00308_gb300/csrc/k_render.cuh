@@ -30,6 +30,7 @@ template <int M, class R = float> struct AlphaOut {
     LF<M, R> L, U;  // lower / upper forms of the effective opacity
     R rL, rU;       // their coefficient radii
     R alo, ahi;     // scalar enclosure of a over the cell
+    R dev;          // estimate of how far single precision moves alo, ahi (see pixel_alpha)
 };
 
 // n elements (a multiple of 4, 16-byte aligned) copied with 16-byte loads
@@ -46,32 +47,34 @@ __device__ __forceinline__ void load_vec(const double *src, double *dst)
     for (int q = 0; q < n / 2; ++q) reinterpret_cast<double2 *>(dst)[q] = reinterpret_cast<const double2 *>(src)[q];
 }
 
-// c[M], klo, khi, r (S and R entries; vlo, vhi are not needed)
-template <int M, class R>
-__device__ __forceinline__ void load_sb(const R *src, SB<M, R> &b)
+// c[M], klo, khi, r (S and R entries; vlo, vhi are not needed).  The record
+// element type RE may be narrower than the arithmetic type R (an FP32 record
+// evaluated in FP64): the conversion is exact.
+template <int M, class R, class RE>
+__device__ __forceinline__ void load_sb(const RE *src, SB<M, R> &b)
 {
-    R v[Rec<M>::SBW];
+    RE v[Rec<M>::SBW];
     load_vec<Rec<M>::SBW>(src, v);
 #pragma unroll
-    for (int j = 0; j < M; ++j) b.c[j] = v[j];
-    b.klo = v[M];
-    b.khi = v[M + 1];
-    b.r = v[M + 2];
+    for (int j = 0; j < M; ++j) b.c[j] = (R)v[j];
+    b.klo = (R)v[M];
+    b.khi = (R)v[M + 1];
+    b.r = (R)v[M + 2];
 }
 
 // c[M], klo, khi, vlo, vhi, r (W entries)
-template <int M, class R>
-__device__ __forceinline__ void load_sbw(const R *src, SB<M, R> &b)
+template <int M, class R, class RE>
+__device__ __forceinline__ void load_sbw(const RE *src, SB<M, R> &b)
 {
-    R v[Rec<M>::WS];
+    RE v[Rec<M>::WS];
     load_vec<Rec<M>::WS>(src, v);
 #pragma unroll
-    for (int j = 0; j < M; ++j) b.c[j] = v[j];
-    b.klo = v[M];
-    b.khi = v[M + 1];
-    b.vlo = v[M + 2];
-    b.vhi = v[M + 3];
-    b.r = v[M + 4];
+    for (int j = 0; j < M; ++j) b.c[j] = (R)v[j];
+    b.klo = (R)v[M];
+    b.khi = (R)v[M + 1];
+    b.vlo = (R)v[M + 2];
+    b.vhi = (R)v[M + 3];
+    b.r = (R)v[M + 4];
 }
 
 __device__ __forceinline__ float clamp01(float x) { return fminf(1.f, fmaxf(0.f, x)); }
@@ -81,15 +84,25 @@ __device__ __forceinline__ double clamp01(double x) { return fmin(1.0, fmax(0.0,
 __device__ __forceinline__ uint32_t rec_flags(const float *r, int at) { return __float_as_uint(r[at]); }
 __device__ __forceinline__ uint32_t rec_flags(const double *r, int at) { return (uint32_t)r[at]; }
 
-// Effective-opacity bounds of one (Gaussian, cell) record at pixel (ux, uy).
-template <int M, class R = float>
-__device__ __forceinline__ void pixel_alpha(const R *__restrict__ r, R ux, R uy, AlphaOut<M, R> &out)
+// Effective-opacity bounds of one (Gaussian, cell) record at pixel (ux, uy),
+// in the arithmetic of R from a record of element type RE.
+//
+// out.dev estimates how far evaluating in R's precision moves alo and ahi: m
+// is a small difference of terms of magnitude about |m_lo| + |m_hi|, so its
+// ends move by about 32 u (|m_lo| + |m_hi|), and a = o e^(-m/2) moves by half
+// of that times a (a_hi only while m_lo > 0: below that the secant ends at
+// x = 0 and a_hi = o).  The FP32 renderer evaluates the pair again in FP64
+// where this estimate exceeds its threshold (pixel_alpha_fp64).
+template <int M, class R = float, class RE = R>
+__device__ __forceinline__ void pixel_alpha(const RE *__restrict__ r, R ux, R uy, AlphaOut<M, R> &out,
+                                            R *m_out = nullptr)
 {
     using RL = Rec<M>;
     using N = Num<R>;
     // opacity box [o_lo, o]: o_lo scales the lower forms, o the upper ones
     const R o = r[RL::O], o_lo = r[RL::O_LO];
     const uint32_t flags = rec_flags(r, RL::FLAGS);
+    out.dev = 0;
     if (flags & F_FALLBACK) {
 #pragma unroll
         for (int j = 0; j < M; ++j) { out.L.c[j] = 0; out.U.c[j] = 0; }
@@ -104,17 +117,17 @@ __device__ __forceinline__ void pixel_alpha(const R *__restrict__ r, R ux, R uy,
     B Dx, Dy;
     {
         B S, Rr;
-        load_sb<M, R>(r + RL::S, S);
+        load_sb<M, R, RE>(r + RL::S, S);
         const R dx = ux - r[RL::MU_X], dy = uy - r[RL::MU_Y];  // exact: both are half-integers
         const R gap = r[RL::GAP_S];
         SAcc<M, R> a;
-        load_sb<M, R>(r + RL::RX, Rr);
+        load_sb<M, R, RE>(r + RL::RX, Rr);
         a.init(0, 0);
         a.term_same_side(dx, S);
         a.term((R)1, Rr);
         if (dx < (R)0) a.add_slack(N::mul_ru(-dx, gap));
         Dx = a.result();
-        load_sb<M, R>(r + RL::RY, Rr);
+        load_sb<M, R, RE>(r + RL::RY, Rr);
         a.init(0, 0);
         a.term_same_side(dy, S);
         a.term((R)1, Rr);
@@ -127,8 +140,8 @@ __device__ __forceinline__ void pixel_alpha(const R *__restrict__ r, R ux, R uy,
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         B w0, w1;
-        load_sbw<M, R>(r + RL::W0 + c * RL::WS, w0);
-        load_sbw<M, R>(r + RL::W0 + (3 + c) * RL::WS, w1);
+        load_sbw<M, R, RE>(r + RL::W0 + c * RL::WS, w0);
+        load_sbw<M, R, RE>(r + RL::W0 + (3 + c) * RL::WS, w1);
         SAcc<M, R> pq;
         pq.init(0, 0);
         pq.mul(Dx, w0);
@@ -138,6 +151,10 @@ __device__ __forceinline__ void pixel_alpha(const R *__restrict__ r, R ux, R uy,
     }
     const B m = pm.result();
     const R mlo = m.vlo, mhi = m.vhi;
+    if (m_out) {
+        m_out[0] = mlo;
+        m_out[1] = mhi;
+    }
     // Exp on x = -m/2 in [xl, xu], xu clipped at 0 because m >= 0
     const R xl = R(-0.5) * mhi;
     R xu = N::min(R(-0.5) * mlo, R(0));
@@ -203,6 +220,40 @@ __device__ __forceinline__ void pixel_alpha(const R *__restrict__ r, R ux, R uy,
         out.rL = l1.radius_bound();
         out.alo = N::max(R(0), N::sub_rd(out.L.k, out.rL));
     }
+    out.dev = R(0.5 * 32) * N::U * (N::abs(mlo) + N::abs(mhi)) * ((mlo > R(0) ? out.ahi : R(0)) + out.alo);
+}
+
+// The same evaluation in FP64 arithmetic from the FP32 record, narrowed back
+// to FP32 forms soundly: each coefficient is rounded to nearest and the
+// rounding errors, summed (|p_j| <= 1), move the constant outward; radii,
+// constants and the scalar enclosure round outward.  This takes the Exp
+// stage's tangent and secant points (the ends of the m interval) in FP64 for
+// the pairs whose m interval is so wide that FP32 cannot carry its ends to
+// the bounds' tolerance.  Kept out of line: it runs for few evaluations, and
+// the FP32 sweep keeps its registers.
+template <int M>
+__device__ __noinline__ AlphaOut<M, float> pixel_alpha_fp64(const float *r, float ux, float uy,
+                                                           double *m_out = nullptr)
+{
+    AlphaOut<M, float> out;
+    AlphaOut<M, double> d;
+    pixel_alpha<M, double, float>(r, (double)ux, (double)uy, d, m_out);
+    double eL = 0.0, eU = 0.0;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        out.L.c[j] = __double2float_rn(d.L.c[j]);
+        out.U.c[j] = __double2float_rn(d.U.c[j]);
+        eL = __dadd_ru(eL, fabs(__dsub_rn(d.L.c[j], (double)out.L.c[j])));
+        eU = __dadd_ru(eU, fabs(__dsub_rn(d.U.c[j], (double)out.U.c[j])));
+    }
+    out.L.k = __double2float_rd(__dsub_rd(d.L.k, eL));
+    out.U.k = __double2float_ru(__dadd_ru(d.U.k, eU));
+    out.rL = __double2float_ru(__dadd_ru(d.rL, eL));
+    out.rU = __double2float_ru(__dadd_ru(d.rU, eU));
+    out.alo = __double2float_rd(d.alo);
+    out.ahi = __double2float_ru(d.ahi);
+    out.dev = 0.f;
+    return out;
 }
 
 // Colour accumulator: sum_i w_i F_i per channel, with the rounding error of
@@ -404,15 +455,24 @@ template <int TS> struct RenderOcc {
 // the next round builds the records of a wider window and sweeps it again
 // from its start.  The sweep is deterministic, so the restarted segment
 // gives the same bounds it would have given in one pass.
-template <int M, int TS, int CH, int RING, bool REL>
-__global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kernel(
+//
+// Precision (F64): the opacity evaluations whose FP32 deviation estimate
+// exceeds fp64_dev are taken in FP64 (pixel_alpha_fp64).  The FP32 sweep
+// (F64 = false) keeps that out-of-line call out of its code: a segment in
+// which any pixel meets such an evaluation is abandoned at its end (no output
+// written) and appended to precise_list, which the F64 = true instance then
+// sweeps from its start.  Either way every evaluation over the threshold is
+// taken in FP64, so the bounds do not depend on which instance swept a
+// segment.
+template <int M, int TS, int CH, int RING, bool REL, bool F64>
+__global__ void __launch_bounds__(TS *TS, F64 ? 1 : RenderOcc<TS>::MIN_BLOCKS) render_kernel(
     const float *__restrict__ recs, const PixBox *__restrict__ boxes, const uint32_t *__restrict__ seg_start,
     const uint32_t *__restrict__ seg_end, const uint32_t *__restrict__ active, const uint32_t *__restrict__ n_active,
     uint32_t window, uint32_t *__restrict__ next_active, uint32_t *__restrict__ n_next,
-    uint32_t *__restrict__ sweep_hist,
+    uint32_t *__restrict__ precise_list, uint32_t *__restrict__ n_precise, uint32_t *__restrict__ sweep_hist,
     const uint32_t *__restrict__ entry_ev, const uint32_t *__restrict__ ev_val,
     const uint64_t *__restrict__ ev_key, int W, int H, int ntx, int n_tiles, int64_t n_gauss,
-    float k_open, float *__restrict__ out_lo, float *__restrict__ out_hi,
+    float k_open, float fp64_dev, float *__restrict__ out_lo, float *__restrict__ out_hi,
     unsigned long long *__restrict__ counters, unsigned int *__restrict__ work)
 {
     using RL = Rec<M>;
@@ -425,14 +485,18 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
     uint32_t *s_rid = reinterpret_cast<uint32_t *>(smem_raw + SM::REC + SM::EV + SM::BOX);
     float *s_pay = reinterpret_cast<float *>(smem_raw + SM::REC + SM::EV + SM::BOX + SM::RID);
     uint32_t *s_next = reinterpret_cast<uint32_t *>(smem_raw + SM::REC + SM::EV + SM::BOX + SM::RID + SM::RPAY);
+    uint32_t *s_wflag = s_next + 1;  // [3]: an evaluation of chunk c needed FP64 (slot c % 3)
     const int tid = threadIdx.x;
-    uint32_t evals = 0, recomp = 0;
+    uint32_t evals = 0, recomp = 0, wide = 0;
     const uint32_t n_seg = *n_active;
 
     for (;;) {
         if (tid == 0) *s_next = atomicAdd(work, 1u);
         __syncthreads();
         const uint32_t wk = *s_next;
+        // every read of the previous segment's FP64 flags came before the
+        // barrier above, every write of this segment's comes after the next
+        if (!F64 && tid == 0) s_wflag[0] = s_wflag[1] = s_wflag[2] = 0u;
         __syncthreads();
         if (wk >= n_seg) break;
         const uint32_t seg = active[wk];
@@ -477,7 +541,8 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
         float lo_adj = 0.f, hi_adj = 0.f;  // -1: decided 0 / 1; >= 0: widening for skipped events
         bool abandoned = false;
         uint32_t swept = b1 - b0;  // entries swept before the tile stopped
-        uint32_t seg_evals = 0, seg_recomp = 0;
+        uint32_t seg_evals = 0, seg_recomp = 0, seg_wide = 0;
+        bool wide_hit = false;  // F64 = false: an evaluation needed FP64
 
         // Copy the chunk starting at entry sb into buffer bf: warp w takes
         // events EPW w .. EPW w + EPW - 1, its first EPW lanes read their event
@@ -534,7 +599,17 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
                 }
             }
             cp_async_wait_all();  // this thread's copies of the current chunk
-            if (__syncthreads_and(done)) {  // ... and everyone's, now visible
+            const bool all_done = __syncthreads_and(done);  // ... and everyone's, now visible
+            const uint32_t ci = (base - b0) / CH;           // this chunk's index in the segment
+            if (!F64) {
+                // FP64 flags rotate over three slots: chunk c sets slot c % 3;
+                // after the barrier of chunk c every thread reads slot
+                // (c - 1) % 3, complete since that barrier, and thread 0
+                // clears slot (c + 1) % 3, whose readers all passed it
+                if (tid == 0) s_wflag[(ci + 1) % 3] = 0u;
+                if (ci > 0 && s_wflag[(ci + 2) % 3]) break;  // swept again in FP64 (below)
+            }
+            if (all_done) {
                 swept = base - b0;
                 break;
             }
@@ -581,6 +656,39 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
                 }
                 if (!have) {
                     pixel_alpha<M>(r, ux, uy, cache);
+                    // a wide m interval: the Exp stage's points in FP64 where
+                    // the FP32 deviation, weighted by how much this pixel's
+                    // bounds can still move with it, exceeds the threshold.
+                    // The upper bound moves by at most T_hi = PB times it,
+                    // and not at all once its constant has reached 1 in every
+                    // channel (final: the constant only grows); the lower one
+                    // by at most T_lo (PA here, or PA / (1 - a_hi) at an
+                    // upper endpoint whose evaluation left the ring), and not
+                    // at all once the early exit's test decides it 0 on the
+                    // state before this event (final as well).  The weight is
+                    // at most 2, so smaller deviations skip it.
+                    if (cache.dev > 0.5f * fp64_dev) {
+                        bool sat = true, dead = true;
+                        const int nb = n_open + (lower ? -1 : 1);  // before this event
+                        const float ow = fminf(open_w, __fmul_ru((float)nb, k_open));
+                        const float elo = __fmul_ru(__fmul_ru(PA, 1.01f), __fadd_ru(ow, 1.f));
+#pragma unroll
+                        for (int ch = 0; ch < 3; ++ch) {
+                            sat = sat && (REL ? hk[ch] : hi.k[ch]) >= 1.f;
+                            dead = dead && __fadd_ru(lo.upper_min(ch), elo) <= 0.f;
+                        }
+                        const float tlo = dead ? 0.f
+                                               : (lower ? PA : fminf(1.f, __fdividef(PA, fmaxf(1.f - cache.ahi, 1e-6f))));
+                        if (cache.dev * ((sat ? 0.f : PB) + tlo) > fp64_dev) {
+                            if (F64) {
+                                cache = pixel_alpha_fp64<M>(r, ux, uy);
+                                ++seg_wide;
+                            } else {
+                                wide_hit = true;
+                                s_wflag[ci % 3] = 1u;
+                            }
+                        }
+                    }
                     // a MatrixInv fallback is a constant [0, o]: not an evaluation
                     if (!(__float_as_uint(r[RL::FLAGS]) & F_FALLBACK)) {
                         if (lower) ++seg_evals; else ++seg_recomp;
@@ -638,9 +746,17 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
             }
             continue;
         }
+        if (!F64 && __syncthreads_or(wide_hit)) {
+            if (tid == 0) {
+                precise_list[atomicAdd(n_precise, 1u)] = seg;
+                if (counters) atomicAdd(&counters[7], 1ull);
+            }
+            continue;
+        }
         if (sweep_hist && tid == 0) atomicAdd(&sweep_hist[min(swept / 32u, 255u)], 1u);
         evals += seg_evals;
         recomp += seg_recomp;
+        wide += seg_wide;
         if (REL && hk[0] >= 1.f && hk[1] >= 1.f && hk[2] >= 1.f) hi_adj = -1.f;
         if (inside) {
             const size_t o = ((size_t)cell * H * W + (size_t)py * W + px) * 3;
@@ -654,9 +770,11 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
     if (counters) {
         const uint32_t a = __reduce_add_sync(0xffffffffu, evals);
         const uint32_t b = __reduce_add_sync(0xffffffffu, recomp);
+        const uint32_t c = __reduce_add_sync(0xffffffffu, wide);
         if ((tid & 31) == 0) {
             if (a) atomicAdd(&counters[0], (unsigned long long)a);
             if (b) atomicAdd(&counters[1], (unsigned long long)b);
+            if (c) atomicAdd(&counters[6], (unsigned long long)c);
         }
     }
 }
@@ -755,6 +873,55 @@ __global__ void __launch_bounds__(TS *TS) render_plain_kernel(
             out_hi[o + ch] = __double2float_ru(clamp01(hi.bound(ch)));
         }
     }
+}
+
+// Test and diagnosis hook: the opacity relaxation of listed (record, pixel)
+// triples, in FP32 (precision 0) or FP32 then FP64 where the renderer would
+// take FP64 (precision 1: the threshold fp64_dev) or always (precision 2).
+// Per triple DEBUG_ALPHA_W doubles: L.c[6 slots], L.k, U.c[6 slots], U.k,
+// rL, rU, alo, ahi, dev, mlo, mhi, W[6] as (vlo, vhi), S, Rx, Ry as their
+// concretised (lo, hi), flags, whether FP64 was taken.
+constexpr int DEBUG_ALPHA_W = 42;
+template <int M>
+__global__ void debug_alpha_kernel(const float *__restrict__ recs, int n, const int64_t *__restrict__ gi,
+                                   const int32_t *__restrict__ px, const int32_t *__restrict__ py, int precision,
+                                   float fp64_dev, double *__restrict__ out)
+{
+    using RL = Rec<M>;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const float *r = recs + (size_t)gi[t] * RL::WIDTH;
+    const float ux = px[t] + 0.5f, uy = py[t] + 0.5f;
+    AlphaOut<M, float> a;
+    float m32[2] = {0.f, 0.f};
+    double m64[2] = {0.0, 0.0};
+    pixel_alpha<M>(r, ux, uy, a, m32);
+    double mlo = m32[0], mhi = m32[1];
+    int took = 0;
+    if (precision == 2 || (precision == 1 && a.dev > fp64_dev)) {
+        const float dev = a.dev;
+        a = pixel_alpha_fp64<M>(r, ux, uy, m64);
+        a.dev = dev;
+        mlo = m64[0];
+        mhi = m64[1];
+        took = 1;
+    }
+    double *o = out + (size_t)t * DEBUG_ALPHA_W;
+    for (int k = 0; k < DEBUG_ALPHA_W; ++k) o[k] = 0.0;
+    for (int j = 0; j < M; ++j) { o[j] = a.L.c[j]; o[7 + j] = a.U.c[j]; }
+    o[6] = a.L.k; o[13] = a.U.k;
+    o[14] = a.rL; o[15] = a.rU; o[16] = a.alo; o[17] = a.ahi; o[18] = a.dev; o[19] = mlo; o[20] = mhi;
+    for (int e = 0; e < 6; ++e) {
+        o[21 + 2 * e] = r[RL::W0 + e * RL::WS + M + 2];
+        o[22 + 2 * e] = r[RL::W0 + e * RL::WS + M + 3];
+    }
+    const int sb[3] = {RL::S, RL::RX, RL::RY};
+    for (int q = 0; q < 3; ++q) {
+        o[33 + 2 * q] = (double)r[sb[q] + M] - (double)r[sb[q] + M + 2];
+        o[34 + 2 * q] = (double)r[sb[q] + M + 1] + (double)r[sb[q] + M + 2];
+    }
+    o[39] = (double)__float_as_uint(r[RL::FLAGS]);
+    o[40] = took;
 }
 
 }  // namespace ar

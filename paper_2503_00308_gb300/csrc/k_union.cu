@@ -11,13 +11,20 @@
 
 namespace ar {
 
+// min and max that return NaN when either operand is NaN (fminf and fmaxf
+// return the other operand): a NaN bound of any piece, which would mean an
+// unsound piece, reaches the joined image instead of being hidden by the
+// other pieces' finite bounds
+__device__ __forceinline__ float min_nan(float a, float b) { return (a != a || b != b) ? __int_as_float(0x7fc00000) : fminf(a, b); }
+__device__ __forceinline__ float max_nan(float a, float b) { return (a != a || b != b) ? __int_as_float(0x7fc00000) : fmaxf(a, b); }
+
 __device__ __forceinline__ float4 min4(float4 a, float4 b)
 {
-    return make_float4(fminf(a.x, b.x), fminf(a.y, b.y), fminf(a.z, b.z), fminf(a.w, b.w));
+    return make_float4(min_nan(a.x, b.x), min_nan(a.y, b.y), min_nan(a.z, b.z), min_nan(a.w, b.w));
 }
 __device__ __forceinline__ float4 max4(float4 a, float4 b)
 {
-    return make_float4(fmaxf(a.x, b.x), fmaxf(a.y, b.y), fmaxf(a.z, b.z), fmaxf(a.w, b.w));
+    return make_float4(max_nan(a.x, b.x), max_nan(a.y, b.y), max_nan(a.z, b.z), max_nan(a.w, b.w));
 }
 
 // n4 groups of four floats per cell; acc: fold the current outputs in too
@@ -52,8 +59,8 @@ __global__ void __launch_bounds__(256) bounds_union1_kernel(const float *__restr
         int c = acc ? 0 : 1;
 #pragma unroll 4
         for (; c < n_cells; ++c) {
-            a = fminf(a, lo[(size_t)c * n + j]);
-            b = fmaxf(b, hi[(size_t)c * n + j]);
+            a = min_nan(a, lo[(size_t)c * n + j]);
+            b = max_nan(b, hi[(size_t)c * n + j]);
         }
         out_lo[j] = a;
         out_hi[j] = b;
@@ -87,8 +94,8 @@ __global__ void __launch_bounds__(256) bounds_intersect_kernel(const float *__re
 {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < n; j += stride) {
-        out_lo[j] = fmaxf(out_lo[j], lo[j]);
-        out_hi[j] = fminf(out_hi[j], hi[j]);
+        out_lo[j] = max_nan(out_lo[j], lo[j]);
+        out_hi[j] = min_nan(out_hi[j], hi[j]);
     }
 }
 

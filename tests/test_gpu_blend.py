@@ -2,9 +2,9 @@
 parity with the oracle's tight blend, never looser than the interval blend,
 and sound at sampled poses.
 
-Tolerance as in test_gpu_parity: |gpu - oracle| <= 1e-4 + cond per channel,
-at most 0.1 % of the compared pixels above the plain 1e-4, fragile pixels
-checked for soundness only.  Against the interval blend on the GPU the upper
+Tolerance as in test_gpu_parity: |gpu - oracle| <= 1e-4 per channel at every
+pixel that is not fragile, at most 1 % of the pixels fragile (checked for
+soundness only).  Against the interval blend on the GPU the upper
 bound may exceed it only by the early-exit widening (each side stops within
 1e-5 of its full sweep, and the two modes may stop at different events)."""
 import numpy as np
@@ -41,13 +41,15 @@ def render(ar, scene, cam, lo, hi, mode, tile=16):
     return r
 
 
-def compare_tight(orc, scene, cam, lo_c, hi_c, glo, ghi):
-    olo, ohi, frag, cond = orc.render_abstract(scene, cam, lo_c, hi_c, with_cond=True, tight=True)
+def compare_tight(orc, scene, cam, lo_c, hi_c, glo, ghi, window=None):
+    olo, ohi, frag = orc.render_abstract(scene, cam, lo_c, hi_c, window=window, tight=True)
     m = ~np.isnan(olo[..., 0])
     ok = m & (frag == 0)
     e = np.maximum(np.abs(glo - olo), np.abs(ghi - ohi)).max(axis=-1)
-    assert np.all(e[ok] <= TOL + cond[ok]), (e[ok] - cond[ok]).max()
-    assert (e[ok] > TOL).sum() / max(1, ok.sum()) <= 1e-3
+    fr = float((m & (frag != 0)).sum()) / max(1, int(m.sum()))
+    print("tight parity: max |gpu - oracle| = %.3g over %d pixels, fragile %.4f" % (e[ok].max(initial=0), ok.sum(), fr))
+    assert ok.sum() > 0 and np.all(e[ok] <= TOL), e[ok].max()
+    assert fr <= 0.01, fr
     return olo, ohi
 
 
@@ -135,9 +137,4 @@ def test_relational_object300k_small_cell(arlib, orc):
     rlo, rhi = render(arlib, w.scene, w.camera, lo, hi, arlib.AR_BLEND_RELATIONAL)
     assert np.abs(rlo - ilo).max() <= EXIT and np.all(rhi <= ihi + EXIT)
     assert (rhi - rlo).mean() < 0.85 * (ihi - ilo).mean()
-    olo, ohi, frag, cond = orc.render_abstract(w.scene, w.camera, lo[0], hi[0], window=(396, 403, 396, 403),
-                                               with_cond=True, tight=True)
-    m = ~np.isnan(olo[..., 0])
-    ok = m & (frag == 0)
-    e = np.maximum(np.abs(rlo[0] - olo), np.abs(rhi[0] - ohi)).max(axis=-1)
-    assert ok.sum() > 0 and np.all(e[ok] <= TOL + cond[ok]), (e[ok] - cond[ok]).max()
+    compare_tight(orc, w.scene, w.camera, lo[0], hi[0], rlo[0], rhi[0], window=(384, 415, 384, 415))

@@ -1,16 +1,15 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle, and its soundness.
 
-Tolerance, per colour channel, against the oracle's bounds:
-  |gpu - oracle| <= 1e-4 + cond
-where cond is the oracle's own estimate of how far single-precision
-evaluation of the same relaxation can move that pixel's bounds (it is zero
-unless some Gaussian's Mahalanobis interval is so wide that FP32 cannot carry
-its ends to 1e-4), and at most 0.1 % of the compared pixels may exceed the
-plain 1e-4.  Pixels where a threshold decision taken in single precision lies
-within its rounding band are "fragile": both outcomes are sound there, and
-they are checked for soundness instead.  Soundness: concrete FP64 renders at
-sampled poses lie inside the GPU bounds.  Invariances: cell batching is
-bit-exact; the tile size moves the bounds by at most 2e-5 (early stopping).
+Tolerance, per colour channel, against the oracle's bounds: |gpu - oracle| <=
+1e-4 at every pixel that is not fragile.  A pixel is fragile where a threshold
+decision that the GPU takes in single precision (MatrixInv's assertion on a
+cell or a split piece, a cutoff ramp narrower than 0.05) lies within its
+rounding band, so that both outcomes are sound; fragile pixels are checked for
+soundness instead, and at most 1 % of the compared pixels may be fragile.
+Every comparison prints its largest error and its fragile fraction.
+Soundness: concrete FP64 renders at sampled poses lie inside the GPU bounds.
+Invariances: cell batching is bit-exact; the tile size moves the bounds by at
+most 2e-5 (early stopping).
 """
 import numpy as np
 import pytest
@@ -47,18 +46,22 @@ def gpu_render(ar, scene, cam, lo, hi, tile=0, return_stats=False):
     return (r + (stats,)) if return_stats else r
 
 
-def compare(orc, scene, cam, lo_c, hi_c, glo, ghi, window=None, frag_max=0.03):
+FRAG_MAX = 0.01
+
+
+def compare(orc, scene, cam, lo_c, hi_c, glo, ghi, window=None, label=""):
     """Oracle bounds of one cell vs the GPU's; returns (max err, fragile fraction)."""
-    olo, ohi, frag, cond = orc.render_abstract(scene, cam, lo_c, hi_c, window=window, with_cond=True)
+    olo, ohi, frag = orc.render_abstract(scene, cam, lo_c, hi_c, window=window)
     m = ~np.isnan(olo[..., 0])
     ok = m & (frag == 0)
     e = np.maximum(np.abs(glo - olo), np.abs(ghi - ohi)).max(axis=-1)
-    assert np.all(e[ok] <= TOL + cond[ok]), (e[ok] - cond[ok]).max()
-    over = (e[ok] > TOL).sum() / max(1, ok.sum())
-    assert over <= 1e-3, over
-    fr = (m & (frag != 0)).sum() / max(1, m.sum())
-    assert fr <= frag_max, fr
-    return e[ok].max(initial=0), fr
+    fr = float((m & (frag != 0)).sum()) / max(1, int(m.sum()))
+    err = float(e[ok].max(initial=0.0))
+    print("parity %s: max |gpu - oracle| = %.3g over %d pixels, fragile %.4f" % (label, err, int(ok.sum()), fr))
+    assert np.all(e[ok] <= TOL), (err, np.argwhere(e > TOL)[:5])
+    assert fr <= FRAG_MAX, fr
+    assert np.all(glo[m] <= ghi[m])
+    return err, fr
 
 
 def test_tiny64_parity_and_soundness(arlib, orc):
@@ -166,14 +169,17 @@ def test_bad_arguments_rejected(arlib):
     s.close()
 
 
-def test_object10k_cells_sampled(arlib, orc):
-    """The 10k-Gaussian, 200x200, 16-cell workload in one launch; two cells
-    checked against the oracle on pixel windows, one for soundness."""
+def test_object10k_all_cells(arlib, orc):
+    """The 10k-Gaussian, 200x200, 16-cell workload in one launch, every pixel
+    of every cell against the oracle (the wide Mahalanobis intervals of this
+    workload are where the FP64 re-evaluation of the opacity stage is
+    needed), one cell also for soundness."""
     w = synth.object10k()
     glo, ghi, st = gpu_render(arlib, w.scene, w.camera, w.cells_lo, w.cells_hi, return_stats=True)
     assert st["n_records"] > 0 and st["m_vars"] == 4
-    for c, win in [(0, (88, 111, 90, 113)), (11, (60, 83, 120, 135))]:
-        compare(orc, w.scene, w.camera, w.cells_lo[c], w.cells_hi[c], glo[c], ghi[c], window=win)
+    assert st["n_fp64"] > 0 and st["n_fp64_segments"] > 0
+    for c in range(w.n_cells):
+        compare(orc, w.scene, w.camera, w.cells_lo[c], w.cells_hi[c], glo[c], ghi[c], label="object10k cell %d" % c)
     rng = np.random.default_rng(5)
     c = 7
     worst, nv = orc.check_samples(w.scene, w.camera, synth.sample_poses(rng, w.cells_lo[c], w.cells_hi[c], 64),
@@ -183,13 +189,34 @@ def test_object10k_cells_sampled(arlib, orc):
 
 def test_object300k_full_size_sampled(arlib, orc):
     """The 300k-Gaussian, 800x800, 64-cell workload in the launch configuration
-    the benchmark times; oracle on small pixel windows of two cells."""
+    the benchmark times (tile chosen by the autotuner); the oracle on eight
+    seeded 32x32 windows of eight cells, one at the image centre."""
     w = synth.object300k()
     glo, ghi, st = gpu_render(arlib, w.scene, w.camera, w.cells_lo, w.cells_hi, return_stats=True)
     assert st["m_vars"] == 6 and st["n_fallback"] < st["n_records"] // 100
-    for c, win in [(0, (396, 403, 396, 403)), (45, (300, 305, 480, 485))]:
-        compare(orc, w.scene, w.camera, w.cells_lo[c], w.cells_hi[c], glo[c], ghi[c], window=win, frag_max=0.2)
+    rng = np.random.default_rng(1)
+    cells = rng.choice(64, size=8, replace=False)
+    xs, ys = rng.integers(250, 520, size=8), rng.integers(250, 520, size=8)
+    xs[0] = ys[0] = 384
+    for c, x, y in zip(cells, xs, ys):
+        compare(orc, w.scene, w.camera, w.cells_lo[c], w.cells_hi[c], glo[c], ghi[c],
+                window=(int(x), int(x) + 31, int(y), int(y) + 31), label="object300k cell %d at (%d, %d)" % (c, x, y))
     assert np.all(glo <= ghi)
+
+
+def test_unbounded750k_slice(arlib, orc):
+    """750k Gaussians in a 20 x 5 x 20 m box around the camera, 1280x720, four
+    of the 256 cells of the +-10 cm / +-2 deg box rendered in one launch; the
+    oracle on a 24x24 window of each."""
+    w = synth.unbounded750k()
+    rng = np.random.default_rng(2)
+    cells = np.sort(rng.choice(w.n_cells, size=4, replace=False))
+    glo, ghi, st = gpu_render(arlib, w.scene, w.camera, w.cells_lo[cells], w.cells_hi[cells], return_stats=True)
+    assert st["m_vars"] == 6
+    xs, ys = rng.integers(100, 1150, size=4), rng.integers(100, 590, size=4)
+    for i, (c, x, y) in enumerate(zip(cells, xs, ys)):
+        compare(orc, w.scene, w.camera, w.cells_lo[c], w.cells_hi[c], glo[i], ghi[i],
+                window=(int(x), int(x) + 23, int(y), int(y) + 23), label="unbounded750k cell %d at (%d, %d)" % (c, x, y))
 
 
 def test_cell_batches_are_bit_identical(arlib):

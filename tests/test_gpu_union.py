@@ -36,6 +36,33 @@ def test_union_matches_numpy(arlib, nc, W, H):
     assert np.array_equal(ohi.cpu().numpy(), hi.cpu().numpy().max(axis=0))
 
 
+@pytest.mark.parametrize("W,H", [(8, 6), (7, 5)])   # the 16-byte and the one-float kernels
+def test_union_propagates_nan(arlib, W, H):
+    """A NaN bound of any piece (which would mean an unsound piece) reaches
+    the joined image, as numpy's minimum / maximum let it, instead of being
+    hidden by the other pieces' finite bounds."""
+    ar = arlib
+    nc = 3
+    g = torch.Generator().manual_seed(5)
+    lo = torch.rand((nc, H, W, 3), generator=g)
+    hi = lo + torch.rand((nc, H, W, 3), generator=g)
+    lo[1, 2, 3, 1] = float("nan")
+    hi[2, 0, 1, 0] = float("nan")
+    hi[0, 4, 4, 2] = float("nan")
+    olo = torch.full((H, W, 3), -1.0, device="cuda")
+    ohi = torch.full_like(olo, -1.0)
+    ar.ar_bounds_union(lo.cuda(), hi.cuda(), nc, W, H, olo, ohi)
+    torch.cuda.synchronize()
+    want_lo, want_hi = np.minimum.reduce(lo.numpy()), np.maximum.reduce(hi.numpy())
+    got_lo, got_hi = olo.cpu().numpy(), ohi.cpu().numpy()
+    assert np.isnan(got_lo[2, 3, 1]) and np.isnan(got_hi[0, 1, 0]) and np.isnan(got_hi[4, 4, 2])
+    assert np.array_equal(np.isnan(got_lo), np.isnan(want_lo)) and np.array_equal(np.isnan(got_hi), np.isnan(want_hi))
+    f = ~np.isnan(want_lo)
+    assert np.array_equal(got_lo[f], want_lo[f])
+    f = ~np.isnan(want_hi)
+    assert np.array_equal(got_hi[f], want_hi[f])
+
+
 def test_union_rejects_bad_arguments(arlib):
     ar = arlib
     lo = torch.zeros((2, 4, 4, 3), device="cuda")
