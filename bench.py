@@ -84,6 +84,12 @@ def parse():
                     help="offered load of the Poisson stream, as a fraction of the one-at-a-time capacity")
     ap.add_argument("--plain-cells", type=int, default=1,
                     help="cells timed through the plain FP64 one-cell-per-launch path (0: skip)")
+    ap.add_argument("--workloads", default="object10k,unbounded750k",
+                    help="further workloads timed beside the main one ('' to skip)")
+    ap.add_argument("--workload-steps", type=int, default=2)
+    ap.add_argument("--sound-poses", type=int, default=16,
+                    help="concrete renders of cell 0 checked against the timed bounds (0: skip)")
+    ap.add_argument("--no-small-cells", action="store_true")
     return ap.parse_args()
 
 
@@ -148,21 +154,75 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(w, window_edge: int, cell: int = 0):
-    """Time the FP64 oracle (as it stands) on a pixel window of one cell."""
+def centre_window(w, window_edge: int):
+    cx, cy = w.camera.width // 2, w.camera.height // 2
+    h = window_edge // 2
+    return (cx - h, cx - h + window_edge - 1, cy - h, cy - h + window_edge - 1)
+
+
+def cpu_baseline(w, window_edge: int, cell: int = 0, keep=None):
+    """Time the FP64 oracle (as it stands) on a pixel window of one cell.  With
+    keep (a dict), the oracle's bounds of the window are left in it, for the
+    accuracy of the GPU's bounds there."""
     import oracle
     oracle.build()
     cores = oracle.set_threads(os.cpu_count() or 1)
-    cx, cy = w.camera.width // 2, w.camera.height // 2
-    h = window_edge // 2
-    win = (cx - h, cx - h + window_edge - 1, cy - h, cy - h + window_edge - 1)
+    win = centre_window(w, window_edge)
     t0 = time.perf_counter()
-    oracle.render_abstract(w.scene, w.camera, w.cells_lo[cell], w.cells_hi[cell], window=win)
+    r = oracle.render_abstract(w.scene, w.camera, w.cells_lo[cell], w.cells_hi[cell], window=win)
     dt = time.perf_counter() - t0
+    if keep is not None:
+        keep.update(cell=cell, window=win, lo=r[0], hi=r[1], frag=r[2])
     units = window_edge * window_edge
     return {"value": units / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%dx%d pixels at the image centre (densest region) of cell %d of %s; %.1f s" %
                       (window_edge, window_edge, cell, w.name, dt)}
+
+
+def accuracy(orc_out, glo, ghi):
+    """GPU bounds of one cell against the oracle's on its window: the largest
+    |gpu - oracle| over channels at non-fragile pixels, how many pixels exceed
+    the 1e-4 contract, the fragile fraction."""
+    import numpy as np
+    olo, ohi, frag = orc_out["lo"], orc_out["hi"], orc_out["frag"]
+    m = ~np.isnan(olo[..., 0])
+    ok = m & (frag == 0)
+    e = np.maximum(np.abs(glo - olo), np.abs(ghi - ohi)).max(axis=-1)
+    x0, x1, y0, y1 = orc_out["window"]
+    return {"cell": int(orc_out["cell"]), "window": "%dx%d at (%d, %d)" % (x1 - x0 + 1, y1 - y0 + 1, x0, y0),
+            "pixels": int(ok.sum()), "max_abs_err": float(e[ok].max(initial=0.0)),
+            "n_over_1e-4": int((e[ok] > 1e-4).sum()),
+            "fragile_frac": float((m & (frag != 0)).sum()) / max(1, int(m.sum()))}
+
+
+def gap_metrics(lo, hi):
+    """MPG and XPG of the paper's evaluation: the mean and the largest over
+    pixels of the RGB norm of upper - lower (per cell, then averaged over the
+    cells for MPG and maximised for XPG); device tensors [n][H][W][3]."""
+    g = (hi.double() - lo.double()).norm(dim=-1)
+    return {"mpg": float(g.mean()), "xpg": float(g.max())}
+
+
+def soundness(ar, s, w, out_lo, out_hi, n_poses, sp, cell=0):
+    """Concrete FP64 renders on the device (ar_render_concrete) at the cell's
+    two extreme corners and n_poses - 2 seeded random poses of the cell: the
+    number of (pose, pixel, channel) values outside the GPU bounds of the
+    timed step, with no tolerance."""
+    import numpy as np
+    import torch
+
+    from paper_2503_00308_gb300 import synth
+    lo, hi = w.cells_lo[cell], w.cells_hi[cell]
+    poses = np.concatenate([lo[None], hi[None],
+                            synth.sample_poses(np.random.default_rng(7), lo, hi, max(0, n_poses - 2))])
+    cam = w.camera
+    img = torch.empty((1, cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
+    bad = 0
+    for p in poses:
+        s.render_concrete(cam, p[None], img, sp)
+        torch.cuda.synchronize()
+        bad += int(((img[0] < out_lo[cell]) | (img[0] > out_hi[cell])).sum())
+    return {"cell": cell, "poses": int(len(poses)), "violations": bad, "values_checked": int(len(poses)) * img.numel()}
 
 
 def run_reference(args, rank):
@@ -260,6 +320,94 @@ def relational(ar, s, w, intr, pose, cells, nc, args, sp, out_lo, out_hi, value)
             "mean_lower": {"interval": mean_int[0], "relational": mean_rel[0]},
             "mean_upper": {"interval": mean_int[1], "relational": mean_rel[1]},
             "small_cell_mean_width": widths}
+
+
+def timed_render(ar, s, intr, pose, cells, nc, tile, out_lo, out_hi, sp, warmup, steps):
+    """W untimed and K timed renders (CUDA events on the stream); ms per step and the last stats."""
+    import torch
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        ar.ar_render_abstract(s.handle, intr, pose, cells, nc, tile, out_lo, out_hi, sp)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    render_ms = []
+    for _ in range(steps):
+        ar.ar_render_abstract(s.handle, intr, pose, cells, nc, tile, out_lo, out_hi, sp)
+        render_ms.append(ar.ar_last_render_stats(s.handle)["ms_render"])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / steps, ar.ar_last_render_stats(s.handle), statistics.mean(render_ms)
+
+
+def roofline_of(stats, r_ms):
+    M = stats["m_vars"]
+    flops = flops_per_triple(M) * stats["n_evaluated"]
+    achieved = flops / (r_ms / 1e3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_TFLOPS, "kernel": "render_kernel", "kernel_ms": r_ms,
+            "flops_per_triple": flops_per_triple(M), "triples_evaluated": stats["n_evaluated"]}
+
+
+def stage_dict(st):
+    return {"prep": st["ms_prep"], "bin": st["ms_bin"], "build": st["ms_build"], "render": st["ms_render"],
+            "total": st["ms_total"]}
+
+
+def count_dict(st):
+    return {"records": st["n_records"], "entries": st["n_entries"], "triples": st["n_triples"],
+            "evaluated": st["n_evaluated"], "reevaluated": st["n_reevaluated"], "fallback": st["n_fallback"],
+            "split": st["n_split"], "built": st["n_built"], "restarted": st["n_restarted"],
+            "fp64_evaluations": st["n_fp64"], "fp64_segments": st["n_fp64_segments"]}
+
+
+def workload_leg(ar, name, args, sp, warmup, steps, window_edge):
+    """Another workload of the paper's shapes through the same call: throughput,
+    stages, counts, the render kernel's roofline, MPG/XPG and the accuracy
+    against the oracle on a window of cell 0 at the image centre."""
+    import torch
+
+    from paper_2503_00308_gb300 import synth
+    w = synth.WORKLOADS[name]()
+    cam, nc = w.camera, w.n_cells
+    s = ar.Scene(w.scene)
+    ar.ar_set_profiling(s.handle, True)
+    intr, pose, cells = ar.make_intrinsics(cam), ar.make_pose(cam), ar.make_cells(w.cells_lo, w.cells_hi)
+    out_lo = torch.empty((nc, cam.height, cam.width, 3), dtype=torch.float32, device="cuda")
+    out_hi = torch.empty_like(out_lo)
+    ms, st, r_ms = timed_render(ar, s, intr, pose, cells, nc, args.tile, out_lo, out_hi, sp, warmup, steps)
+    keep = {}
+    cpu = cpu_baseline(w, window_edge, keep=keep)
+    glo = out_lo[0].double().cpu().numpy()
+    ghi = out_hi[0].double().cpu().numpy()
+    acc = accuracy(keep, glo, ghi)
+    out = {"value": w.pixel_cells() / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "warmup": warmup, "steps": steps,
+           "config": {"workload": w.name, "gaussians": w.scene.n, "image": "%dx%d" % (cam.width, cam.height),
+                      "cells": nc, "pose_vars": st["m_vars"], "tile": st["tile"]},
+           "stages_ms": stage_dict(st), "counts": count_dict(st), "roofline": roofline_of(st, r_ms),
+           "gaps": gap_metrics(out_lo, out_hi), "accuracy": acc, "oracle_sample": cpu["sample"]}
+    s.close()
+    return out
+
+
+def small_cells_leg(ar, s, w, intr, pose, args, sp, out_lo, out_hi):
+    """The benchmark workload with every cell shrunk about its centre to a
+    twentieth of its widths, so that the bounds are informative instead of
+    saturated: throughput, evaluations per in-box triple, the render kernel's
+    roofline and MPG/XPG."""
+    import numpy as np
+    c = 0.5 * (w.cells_lo + w.cells_hi)
+    h = 0.025 * (w.cells_hi - w.cells_lo)
+    nc = w.n_cells
+    cells = ar.make_cells(c - h, c + h)
+    ms, st, r_ms = timed_render(ar, s, intr, pose, cells, nc, args.tile, out_lo, out_hi, sp, args.warmup,
+                                max(1, min(args.steps, 3)))
+    return {"value": w.pixel_cells() / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "cells": "the %d benchmark cells, each shrunk about its centre to 1/20 of its widths" % nc,
+            "stages_ms": stage_dict(st), "counts": count_dict(st),
+            "evaluations_per_triple": st["n_evaluated"] / max(1, st["n_triples"]),
+            "roofline": roofline_of(st, r_ms), "gaps": gap_metrics(out_lo, out_hi),
+            "mean_width": float((out_hi - out_lo).double().mean())}
 
 
 def fma_probe(ar, sp):
@@ -486,21 +634,32 @@ def run_ours(args, rank, world, local, pg):
                      "fp32_fma_probe_tflops": fma_probe(ar, sp)},
         "stages_ms": {"prep": stats["ms_prep"], "bin": stats["ms_bin"], "build": stats["ms_build"],
                       "render": stats["ms_render"], "total": stats["ms_total"]},
-        "counts": {"records": stats["n_records"], "entries": stats["n_entries"], "triples": stats["n_triples"],
-                   "evaluated": stats["n_evaluated"], "reevaluated": stats["n_reevaluated"],
-                   "fallback": stats["n_fallback"], "split": stats["n_split"], "built": stats["n_built"], "restarted": stats["n_restarted"]},
+        "counts": count_dict(stats),
+        "gaps": gap_metrics(out_lo, out_hi),
     }
+    if args.sound_poses > 0:
+        line["soundness"] = soundness(ar, s, w, out_lo, out_hi, args.sound_poses, sp)
+    keep = {}
+    if not args.no_cpu and world == 1:
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_window, keep=keep)
+        line["accuracy"] = accuracy(keep, out_lo[keep["cell"]].double().cpu().numpy(),
+                                    out_hi[keep["cell"]].double().cpu().numpy())
     line["union"] = union_leg(ar, w, nc, args, sp, out_lo, out_hi)
     if args.relational_steps > 0:
         line["relational"] = relational(ar, s, w, intr, pose, cells, nc, args, sp, out_lo, out_hi, value)
     if args.plain_cells > 0:
         line["plain_path"] = plain_path(ar, s, w, intr, pose, args, sp, value)
+    if not args.no_small_cells:
+        line["small_cells"] = small_cells_leg(ar, s, w, intr, pose, args, sp, out_lo, out_hi)
+    s.close()
     if args.serve_requests > 0:
         line["serving"] = serving(ar, args, sp)
-    if not args.no_cpu and world == 1:
-        line["cpu_baseline"] = cpu_baseline(w, args.cpu_window)
+    if args.workloads and world == 1:
+        line["workloads"] = {}
+        for name in [x for x in args.workloads.split(",") if x and x != args.workload]:
+            line["workloads"][name] = workload_leg(ar, name, args, sp, max(1, min(args.warmup, 2)),
+                                                   args.workload_steps, 32 if name == "object10k" else 16)
     print(json.dumps(line), flush=True)
-    s.close()
 
 
 def main():
