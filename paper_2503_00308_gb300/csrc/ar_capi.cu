@@ -206,7 +206,7 @@ void Workspace::release()
 {
     DevBuf *all[] = {&cells_lohi, &cells, &vN, &recs, &boxes, &keys, &counters, &evk0, &evk1, &evv0, &evv1,
                      &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege, &segk0,
-                     &segk1, &segv0, &segv1, &work, &state, &wlist, &act0, &act1, &words, &slist, &plist, &whist, &out_lo,
+                     &segk1, &segv0, &segv1, &work, &state, &wlist, &act0, &act1, &words, &slist, &plist, &pmask, &whist, &out_lo,
                      &out_hi, &part_lo, &part_hi, &lvl_lo, &lvl_hi, &wpart};
     for (DevBuf *b : all) b->release();
     if (h_whist) cudaFreeHost(h_whist);
@@ -223,7 +223,7 @@ size_t Workspace::bytes() const
     const DevBuf *all[] = {&cells_lohi, &cells, &vN, &recs, &boxes, &keys, &counters, &evk0, &evk1, &evv0, &evv1,
                            &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege,
                            &segk0, &segk1, &segv0, &segv1, &work, &state, &wlist, &act0, &act1, &words,
-                           &slist, &plist, &whist, &out_lo, &out_hi, &part_lo, &part_hi, &lvl_lo, &lvl_hi, &wpart};
+                           &slist, &plist, &pmask, &whist, &out_lo, &out_hi, &part_lo, &part_hi, &lvl_lo, &lvl_hi, &wpart};
     size_t s = 0;
     for (const DevBuf *b : all) s += b->cap;
     return s;
@@ -594,11 +594,13 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
         RK(ws.words.ensure(sizeof(uint32_t) * 8));
         RK(ws.slist.ensure(sizeof(uint32_t) * n_pairs));
         RK(ws.plist.ensure(sizeof(uint32_t) * n_seg));
+        RK(ws.pmask.ensure(sizeof(uint32_t) * n_seg * (TS * TS / 32)));
         rl.sweep_hist = ws.whist.as<uint32_t>();
         RK(run_windowed_render(M, TS, rl, cc, ws.cells.p, ws.vN.as<double>(), n_pairs, n_seg, ws.state.as<uint32_t>(),
                                ws.wlist.as<uint32_t>(), ws.act0.as<uint32_t>(), ws.act1.as<uint32_t>(),
                                ws.words.as<uint32_t>(), rl.counters + 2, st, &launches,
-                               profiling ? ev + 3 : nullptr, ws.w0, ws.slist.as<uint32_t>(), ws.plist.as<uint32_t>()));
+                               profiling ? ev + 3 : nullptr, ws.w0, ws.slist.as<uint32_t>(), ws.plist.as<uint32_t>(),
+                               ws.pmask.as<uint32_t>()));
     }
     return AR_OK;
 }
@@ -624,7 +626,8 @@ uint32_t learned_window(const uint32_t *hist256)
 int run_windowed_render(int M, int TS, RenderLaunch rl, const CallConst &cc, const void *cells, const double *vN,
                         uint64_t n_pairs, uint64_t n_seg, uint32_t *state, uint32_t *wlist, uint32_t *act0,
                         uint32_t *act1, uint32_t *words, unsigned long long *build_counters, cudaStream_t st,
-                        int *launches, cudaEvent_t *ev, uint32_t w0, uint32_t *split_list, uint32_t *precise_list)
+                        int *launches, cudaEvent_t *ev, uint32_t w0, uint32_t *split_list, uint32_t *precise_list,
+                        uint32_t *precise_mask)
 {
     const uint32_t kWindow[3] = {w0, w0 < 8192u ? 8192u : 0xffffffffu, 0xffffffffu};
     uint32_t *act[2] = {act0, act1};
@@ -651,13 +654,14 @@ int run_windowed_render(int M, int TS, RenderLaunch rl, const CallConst &cc, con
         rl.n_next = nxt_n;
         rl.precise = precise_list;
         rl.n_precise = words + 5;
+        rl.precise_mask = precise_mask;
         CK(cudaMemsetAsync(words + 5, 0, sizeof(uint32_t), st));
         rl.f64 = 0;
         if (launch_render(M, TS, rl, st))
             return fail(AR_EDEVICE, "render launch: %s", cudaGetErrorString(cudaGetLastError()));
-        // the segments that met an evaluation needing FP64, swept again from
-        // their start by the FP64-capable instance (window abandons go to the
-        // same next list)
+        // the segments where some pixel met an evaluation needing FP64, swept
+        // again from their start for those pixels by the FP64-capable
+        // instance (window abandons go to the same next list)
         RenderLaunch rp = rl;
         rp.active = precise_list;
         rp.n_active = words + 5;

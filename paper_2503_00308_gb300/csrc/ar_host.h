@@ -28,7 +28,7 @@ struct Workspace {
     DevBuf evk0, evk1, evv0, evv1, ents0, ents1, ente0, ente1;
     DevBuf ua, ub, uc, ud, hist, scan, segs, sege, segk0, segk1, segv0, segv1, work;
     DevBuf state, wlist, act0, act1, words, slist;  // windowed rounds: pair states, build list, active segments
-    DevBuf plist;                            // segments swept again with FP64 evaluations (per round)
+    DevBuf plist, pmask;                     // segments swept again with FP64 evaluations, their pixel masks
     DevBuf whist;                            // [256] sweep-length histogram of the current render
     uint32_t *h_whist = nullptr;             // page-locked copy of the last render's histogram
     bool whist_pending = false;              // h_whist holds a render not yet learned from
@@ -63,11 +63,13 @@ struct TunedTile {
 // split_list [n_pairs]: pairs whose MatrixInv needs input splitting, which a
 // second kernel finishes with a warp each; precise_list [n_seg]: segments that
 // meet an opacity evaluation needing FP64, swept again by the FP64-capable
-// render instance in the same round.
+// render instance in the same round, and precise_mask [n_seg * TS * TS / 32]
+// the pixels of each that do.
 int run_windowed_render(int M, int TS, RenderLaunch rl, const CallConst &cc, const void *cells, const double *vN,
                         uint64_t n_pairs, uint64_t n_seg, uint32_t *state, uint32_t *wlist, uint32_t *act0,
                         uint32_t *act1, uint32_t *words, unsigned long long *build_counters, cudaStream_t st,
-                        int *launches, cudaEvent_t *ev, uint32_t w0, uint32_t *split_list, uint32_t *precise_list);
+                        int *launches, cudaEvent_t *ev, uint32_t w0, uint32_t *split_list, uint32_t *precise_list,
+                        uint32_t *precise_mask);
 // First window from the sweep histogram of an earlier render: the smallest
 // multiple of 32 entries that covers 99.5 % of its segments, in [128, 4096].
 uint32_t learned_window(const uint32_t *hist256);

@@ -33,9 +33,10 @@ struct RenderLaunch {
     unsigned int *work;               // segment counter of the persistent grid (zeroed by the launcher)
     int rel = 0;                      // 1: relational upper transmittance (AR_BLEND_RELATIONAL)
     // precision: the FP32 sweep (f64 = 0) appends a segment that needs an FP64
-    // evaluation to precise[*n_precise]; the f64 = 1 instance sweeps that list
+    // evaluation to precise[*n_precise], with the mask of the pixels that do in
+    // precise_mask[slot * TS * TS / 32 ...]; the f64 = 1 instance sweeps them
     int f64 = 0;
-    uint32_t *precise = nullptr, *n_precise = nullptr;
+    uint32_t *precise = nullptr, *n_precise = nullptr, *precise_mask = nullptr;
 };
 
 size_t cell_data_bytes(int M);

@@ -153,7 +153,7 @@ int ar_render_abstract_noalloc(ar_scene *s, const ar_intrinsics *in, const ar_no
     uint32_t *state = A.take<uint32_t>(n_pairs), *wlist = A.take<uint32_t>(n_pairs);
     uint32_t *slist = A.take<uint32_t>(n_pairs);
     uint32_t *act0 = A.take<uint32_t>(n_seg), *act1 = A.take<uint32_t>(n_seg), *words = A.take<uint32_t>(8);
-    uint32_t *plist = A.take<uint32_t>(n_seg);
+    uint32_t *plist = A.take<uint32_t>(n_seg), *pmask = A.take<uint32_t>(n_seg * (TS * TS / 32));
     if (A.over) return too_big("the per-(Gaussian, cell) records", A.used);
 
     // pose cells: lo and hi rows straight from the caller's array (no staging copy)
@@ -225,5 +225,5 @@ int ar_render_abstract_noalloc(ar_scene *s, const ar_intrinsics *in, const ar_no
     rl.out_hi = out_upper;
     rl.counters = nullptr;
     return run_windowed_render(M, TS, rl, cc, cellbuf, vN, n_pairs, n_seg, state, wlist, act0, act1, words, nullptr,
-                               st, &launches, nullptr, 512u, slist, plist);
+                               st, &launches, nullptr, 512u, slist, plist, pmask);
 }

@@ -456,20 +456,23 @@ template <int TS> struct RenderOcc {
 // from its start.  The sweep is deterministic, so the restarted segment
 // gives the same bounds it would have given in one pass.
 //
-// Precision (F64): the opacity evaluations whose FP32 deviation estimate
-// exceeds fp64_dev are taken in FP64 (pixel_alpha_fp64).  The FP32 sweep
-// (F64 = false) keeps that out-of-line call out of its code: a segment in
-// which any pixel meets such an evaluation is abandoned at its end (no output
-// written) and appended to precise_list, which the F64 = true instance then
-// sweeps from its start.  Either way every evaluation over the threshold is
-// taken in FP64, so the bounds do not depend on which instance swept a
-// segment.
+// Precision (F64): the opacity evaluations whose weighted FP32 deviation
+// estimate exceeds fp64_dev are taken in FP64 (pixel_alpha_fp64).  The FP32
+// sweep (F64 = false) keeps that out-of-line call out of its code: it sweeps
+// every segment in FP32, writes the bounds of the pixels that met no such
+// evaluation, and appends a segment where some pixel did to precise_list,
+// with the mask of those pixels (one word per warp) in precise_mask.  The
+// F64 = true instance sweeps the listed segments again from their start for
+// the masked pixels alone (the others start as stopped and write nothing).
+// The decision is per pixel, taken from the pixel's own sweep, so every pixel
+// gets the bounds one FP64-capable sweep would give it.
 template <int M, int TS, int CH, int RING, bool REL, bool F64>
-__global__ void __launch_bounds__(TS *TS, F64 ? 1 : RenderOcc<TS>::MIN_BLOCKS) render_kernel(
+__global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kernel(
     const float *__restrict__ recs, const PixBox *__restrict__ boxes, const uint32_t *__restrict__ seg_start,
     const uint32_t *__restrict__ seg_end, const uint32_t *__restrict__ active, const uint32_t *__restrict__ n_active,
     uint32_t window, uint32_t *__restrict__ next_active, uint32_t *__restrict__ n_next,
-    uint32_t *__restrict__ precise_list, uint32_t *__restrict__ n_precise, uint32_t *__restrict__ sweep_hist,
+    uint32_t *__restrict__ precise_list, uint32_t *__restrict__ n_precise, uint32_t *__restrict__ precise_mask,
+    uint32_t *__restrict__ sweep_hist,
     const uint32_t *__restrict__ entry_ev, const uint32_t *__restrict__ ev_val,
     const uint64_t *__restrict__ ev_key, int W, int H, int ntx, int n_tiles, int64_t n_gauss,
     float k_open, float fp64_dev, float *__restrict__ out_lo, float *__restrict__ out_hi,
@@ -485,7 +488,6 @@ __global__ void __launch_bounds__(TS *TS, F64 ? 1 : RenderOcc<TS>::MIN_BLOCKS) r
     uint32_t *s_rid = reinterpret_cast<uint32_t *>(smem_raw + SM::REC + SM::EV + SM::BOX);
     float *s_pay = reinterpret_cast<float *>(smem_raw + SM::REC + SM::EV + SM::BOX + SM::RID);
     uint32_t *s_next = reinterpret_cast<uint32_t *>(smem_raw + SM::REC + SM::EV + SM::BOX + SM::RID + SM::RPAY);
-    uint32_t *s_wflag = s_next + 1;  // [3]: an evaluation of chunk c needed FP64 (slot c % 3)
     const int tid = threadIdx.x;
     uint32_t evals = 0, recomp = 0, wide = 0;
     const uint32_t n_seg = *n_active;
@@ -494,9 +496,6 @@ __global__ void __launch_bounds__(TS *TS, F64 ? 1 : RenderOcc<TS>::MIN_BLOCKS) r
         if (tid == 0) *s_next = atomicAdd(work, 1u);
         __syncthreads();
         const uint32_t wk = *s_next;
-        // every read of the previous segment's FP64 flags came before the
-        // barrier above, every write of this segment's comes after the next
-        if (!F64 && tid == 0) s_wflag[0] = s_wflag[1] = s_wflag[2] = 0u;
         __syncthreads();
         if (wk >= n_seg) break;
         const uint32_t seg = active[wk];
@@ -537,7 +536,10 @@ __global__ void __launch_bounds__(TS *TS, F64 ? 1 : RenderOcc<TS>::MIN_BLOCKS) r
 #pragma unroll
         for (int k = 0; k < RING; ++k) s_rid[k * NT + tid] = 0xffffffffu;
         uint32_t head = 0;
-        bool done = !inside;
+        // the FP64 instance sweeps only the pixels the FP32 sweep listed
+        const bool active = F64 ? ((precise_mask[(size_t)wk * (NT / 32) + (tid >> 5)] >> (tid & 31)) & 1u) != 0u
+                                : true;
+        bool done = !inside || !active;
         float lo_adj = 0.f, hi_adj = 0.f;  // -1: decided 0 / 1; >= 0: widening for skipped events
         bool abandoned = false;
         uint32_t swept = b1 - b0;  // entries swept before the tile stopped
@@ -599,17 +601,7 @@ __global__ void __launch_bounds__(TS *TS, F64 ? 1 : RenderOcc<TS>::MIN_BLOCKS) r
                 }
             }
             cp_async_wait_all();  // this thread's copies of the current chunk
-            const bool all_done = __syncthreads_and(done);  // ... and everyone's, now visible
-            const uint32_t ci = (base - b0) / CH;           // this chunk's index in the segment
-            if (!F64) {
-                // FP64 flags rotate over three slots: chunk c sets slot c % 3;
-                // after the barrier of chunk c every thread reads slot
-                // (c - 1) % 3, complete since that barrier, and thread 0
-                // clears slot (c + 1) % 3, whose readers all passed it
-                if (tid == 0) s_wflag[(ci + 1) % 3] = 0u;
-                if (ci > 0 && s_wflag[(ci + 2) % 3]) break;  // swept again in FP64 (below)
-            }
-            if (all_done) {
+            if (__syncthreads_and(done)) {  // ... and everyone's, now visible
                 swept = base - b0;
                 break;
             }
@@ -685,7 +677,6 @@ __global__ void __launch_bounds__(TS *TS, F64 ? 1 : RenderOcc<TS>::MIN_BLOCKS) r
                                 ++seg_wide;
                             } else {
                                 wide_hit = true;
-                                s_wflag[ci % 3] = 1u;
                             }
                         }
                     }
@@ -747,18 +738,27 @@ __global__ void __launch_bounds__(TS *TS, F64 ? 1 : RenderOcc<TS>::MIN_BLOCKS) r
             continue;
         }
         if (!F64 && __syncthreads_or(wide_hit)) {
+            // list the segment with the mask of its pixels that need FP64
+            // (the slot goes through s_next[1]: s_next[0], the work index, is
+            // rewritten at the next segment's start while others may read this)
             if (tid == 0) {
-                precise_list[atomicAdd(n_precise, 1u)] = seg;
+                const uint32_t slot = atomicAdd(n_precise, 1u);
+                precise_list[slot] = seg;
+                s_next[1] = slot;
                 if (counters) atomicAdd(&counters[7], 1ull);
             }
-            continue;
+            __syncthreads();
+            const uint32_t m = __ballot_sync(0xffffffffu, wide_hit);
+            if ((tid & 31) == 0) precise_mask[(size_t)s_next[1] * (NT / 32) + (tid >> 5)] = m;
         }
-        if (sweep_hist && tid == 0) atomicAdd(&sweep_hist[min(swept / 32u, 255u)], 1u);
+        if (!F64 && sweep_hist && tid == 0) atomicAdd(&sweep_hist[min(swept / 32u, 255u)], 1u);
         evals += seg_evals;
         recomp += seg_recomp;
         wide += seg_wide;
         if (REL && hk[0] >= 1.f && hk[1] >= 1.f && hk[2] >= 1.f) hi_adj = -1.f;
-        if (inside) {
+        // pixels listed for the FP64 sweep, and in it the pixels not listed,
+        // leave their outputs to the other instance
+        if (inside && active && (F64 || !wide_hit)) {
             const size_t o = ((size_t)cell * H * W + (size_t)py * W + px) * 3;
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
