@@ -410,11 +410,13 @@ def small_cells_leg(ar, s, w, intr, pose, args, sp, out_lo, out_hi):
             "mean_width": float((out_hi - out_lo).double().mean())}
 
 
-def fma_probe(ar, sp):
-    """Measured FP32 FMA rate, scalar and packed (best of 3 each), beside the nominal peak."""
+def fma_probe(sp):
+    """Measured FP32 FMA rate, scalar and packed (best of 3 each), beside the nominal peak
+    (the benchmark's own helper library, not libar)."""
+    from paper_2503_00308_gb300 import probe
     out = {}
     for name, packed in (("scalar", False), ("packed", True)):
-        out[name] = max(ar.ar_fp32_fma_rate(packed, 16384, sp) for _ in range(3))
+        out[name] = max(probe.fp32_fma_rate(packed, 16384, sp) for _ in range(3))
     return out
 
 
@@ -631,7 +633,7 @@ def run_ours(args, rank, world, local, pg):
                      "flops_per_triple": flops_per_triple(M), "triples_evaluated": stats["n_evaluated"],
                      "triples_in_boxes": stats["n_triples"],
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal: MEASURED_PEAKS.json has no FP32 figure)",
-                     "fp32_fma_probe_tflops": fma_probe(ar, sp)},
+                     "fp32_fma_probe_tflops": fma_probe(sp)},
         "stages_ms": {"prep": stats["ms_prep"], "bin": stats["ms_bin"], "build": stats["ms_build"],
                       "render": stats["ms_render"], "total": stats["ms_total"]},
         "counts": count_dict(stats),

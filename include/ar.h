@@ -248,15 +248,6 @@ int ar_render_abstract_refined(ar_scene *scene, const ar_intrinsics *intr, const
                                float *out_upper, ar_pose_box *leaves, int32_t leaves_cap, int32_t *n_leaves,
                                void *cuda_stream);
 
-/* FP32 FMA throughput of the current device, in TFLOP/s (an FMA counts as 2
- * flops): 16 independent FMA chains per thread over 8 blocks of 256 threads
- * per SM, `iters` steps each, timed with CUDA events on cuda_stream.  packed =
- * 1 issues the FMAs in pairs (the two-lane FP32 FMA of sm_100 and later).  A
- * measurement utility for the roofline of the render kernel, not part of the
- * rendering path.  Synchronises with cuda_stream; allocates and frees a small
- * device buffer.  Errors: AR_EINVAL (null tflops, iters < 1), AR_EDEVICE. */
-int ar_fp32_fma_rate(int32_t packed, int32_t iters, double *tflops, void *cuda_stream);
-
 /* Plain comparison path: the same bounds computed one cell per launch
  * sequence in FP64 with directed rounding, without cell batching.  Same
  * arguments and output layout as ar_render_abstract. */

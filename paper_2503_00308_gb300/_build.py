@@ -18,6 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libar.so")
+PROBE_SRC = os.path.join(HERE, "probe", "fma_probe.cu")
+PROBE_LIB = os.path.join(LIBDIR, "libarprobe.so")   # the benchmark's FP32 FMA-rate helper (not libar)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -44,8 +46,24 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
+def build_probe(force: bool = False) -> str:
+    """Compile the benchmark's FP32 FMA-rate helper into libarprobe.so; returns its path."""
+    if not force and os.path.exists(PROBE_LIB) and os.path.getmtime(PROBE_LIB) >= os.path.getmtime(PROBE_SRC):
+        return PROBE_LIB
+    os.makedirs(LIBDIR, exist_ok=True)
+    tmp = PROBE_LIB + ".tmp"
+    cmd = [nvcc()] + ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-shared", PROBE_SRC, "-o", tmp,
+                             "-lcudart"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc failed on %s:\n%s%s" % (PROBE_SRC, r.stdout, r.stderr))
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link libar.so; returns its path."""
+    """Compile and link libar.so (and the benchmark's probe library); returns libar's path."""
+    build_probe(force)
     if not force and up_to_date():
         return LIB
     os.makedirs(LIBDIR, exist_ok=True)

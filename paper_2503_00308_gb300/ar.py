@@ -77,7 +77,6 @@ def lib():
             "ar_scene_set_blend": ([P, ctypes.c_int32], ctypes.c_int),
             "ar_scene_set_fp64_alpha": ([P, ctypes.c_float], ctypes.c_int),
             "ar_bounds_union": ([P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P], ctypes.c_int),
-            "ar_fp32_fma_rate": ([ctypes.c_int32, ctypes.c_int32, P, P], ctypes.c_int),
             "ar_partition_piece": ([P, P, c_int64, P], ctypes.c_int),
             "ar_render_abstract_refined": ([P, P, P, P, ctypes.c_int32, ctypes.c_int32, P, P, P, ctypes.c_int32, P, P],
                                            ctypes.c_int),
@@ -220,13 +219,6 @@ def ar_render_abstract_refined(scene, intr, pose, box, rounds, tile, out_lower, 
     lo = np.array([[buf[i].lo[j] for j in range(6)] for i in range(k)]).reshape(k, 6)
     hi = np.array([[buf[i].hi[j] for j in range(6)] for i in range(k)]).reshape(k, 6)
     return lo, hi
-
-
-def ar_fp32_fma_rate(packed: bool, iters: int = 16384, stream=0) -> float:
-    """Measured FP32 FMA throughput of the current device in TFLOP/s."""
-    v = ctypes.c_double(0.0)
-    check(lib().ar_fp32_fma_rate(1 if packed else 0, int(iters), ctypes.byref(v), _ptr(stream)))
-    return v.value
 
 
 def ar_render_concrete(scene, intr, pose, deltas, n_poses, out, stream=0):

@@ -16,6 +16,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ar.h"
 #include "ar_bin.h"
 #include "ar_common.cuh"
@@ -23,6 +25,21 @@
 #include "ar_host.h"
 
 namespace ar {
+// NVTX range over a host scope (the enqueue of a render stage; a profiler's
+// CUDA trace lines the kernels up under it).  Header-only NVTX 3: no library
+// is linked, and the calls cost nothing without a tool attached.
+struct NvtxRange {
+    bool open = true;
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    void end()
+    {
+        if (open) nvtxRangePop();
+        open = false;
+    }
+    ~NvtxRange() { end(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 // stage events of one cell batch: start, after prep, after binning, then per
 // windowed round: after the record build, after the render
 constexpr int kEventsPerBatch = 9;
@@ -527,8 +544,10 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
     RK(ws.keys.ensure(sizeof(double) * 2 * n_pairs));
 
     cudaEvent_t *ev = &ws.evs[kEventsPerBatch * batch];
+    NvtxRange batch_range("ar.cell_batch");
     if (profiling) CK(cudaEventRecord(ev[0], st));
     CK(cudaMemsetAsync(ws.counters.p, 0, sizeof(unsigned long long) * 8, st));
+    NvtxRange prep_range("ar.prep: cells and (Gaussian, cell) decisions");
     if (launch_cell_prep(M, d_lo, d_hi, cc, ws.cells.p, st)) return fail(AR_EDEVICE, "cell_prep launch");
     const int rp = plain ? launch_record_prep64(M, ws.vN.as<double>(), s->gp, cc, ws.cells.p, TS,
                                                 ws.recs.as<double>(), ws.boxes.as<PixBox>(), ws.keys.as<double>(),
@@ -541,6 +560,7 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
     if (profiling) CK(cudaEventRecord(ev[1], st));
     CK(cudaMemcpyAsync(ws.h_counters, ws.counters.p, sizeof(unsigned long long) * 5, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    prep_range.end();
     if (ws.whist_pending) {
         // the previous render's histogram arrived with this synchronisation
         ws.w0 = learned_window(ws.h_whist);
@@ -557,8 +577,11 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
         return fail(AR_ENOMEM, "%llu bin entries exceed the 32-bit index range; lower the workspace limit",
                     (unsigned long long)nent);
     BinOut bo;
-    RK(bin_pairs(ws, ws.boxes.as<PixBox>(), ws.keys.as<double>(), n_pairs, (uint64_t)s->n, n_cells, ne, nent, TS, ntx,
-                 n_tiles, st, bo, launches));
+    {
+        NvtxRange r("ar.bin: depth-sorted tile bins");
+        RK(bin_pairs(ws, ws.boxes.as<PixBox>(), ws.keys.as<double>(), n_pairs, (uint64_t)s->n, n_cells, ne, nent, TS,
+                     ntx, n_tiles, st, bo, launches));
+    }
     if (profiling) CK(cudaEventRecord(ev[2], st));
     RenderLaunch rl;
     rl.recs = ws.recs.as<float>();
@@ -634,7 +657,10 @@ int run_windowed_render(int M, int TS, RenderLaunch rl, const CallConst &cc, con
     CK(cudaMemsetAsync(state, 0, sizeof(uint32_t) * n_pairs, st));
     launch_set_u32(words + 1, (uint32_t)n_seg, st);
     ++*launches;
+    static const char *kRoundName[3] = {"ar.round 0: build + render", "ar.round 1: build + render",
+                                        "ar.round 2: build + render"};
     for (int r = 0; r < 3; ++r) {
+        NvtxRange round_range(kRoundName[r]);
         uint32_t *cur_n = words + 1 + (r & 1), *nxt_n = words + 1 + ((r + 1) & 1);
         const uint32_t *cur = r == 0 ? rl.seg_order : act[(r - 1) & 1];
         CK(cudaMemsetAsync(words, 0, sizeof(uint32_t), st));
@@ -814,6 +840,7 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
     CK(cudaMemsetAsync(ws.whist.p, 0, sizeof(uint32_t) * 256, st));
     CK(cudaMemsetAsync(ws.counters.as<unsigned long long>() + 8, 0, sizeof(unsigned long long) * kCountersPerBatch * n_batches, st));
     int launches = 0;
+    NvtxRange call_range(plain ? "ar.render_abstract_plain_fp64" : "ar.render_abstract");
     if (launch_pose_prep(s->uw_lo, s->uw_hi, s->Mw, s->n, cc, ws.vN.as<double>(), st)) return fail(AR_EDEVICE, "pose_prep launch");
     ++launches;
     for (int b = 0; b < n_batches; ++b) {
@@ -1117,14 +1144,6 @@ int ar_render_abstract_refined(ar_scene *s, const ar_intrinsics *in, const ar_no
     }
     if (n_leaves) *n_leaves = (int32_t)cur.size();
     for (int64_t i = 0; i < (int64_t)cur.size() && i < leaves_cap; ++i) leaves[i] = cur[(size_t)i];
-    return AR_OK;
-}
-
-int ar_fp32_fma_rate(int32_t packed, int32_t iters, double *tflops, void *stream)
-{
-    if (!tflops || iters < 1) return fail(AR_EINVAL, "need tflops and iters >= 1");
-    if (fma_rate(packed, iters, tflops, (cudaStream_t)stream))
-        return fail(AR_EDEVICE, "fma rate probe: %s", cudaGetErrorString(cudaGetLastError()));
     return AR_OK;
 }
 

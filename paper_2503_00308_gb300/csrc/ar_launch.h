@@ -60,9 +60,6 @@ int launch_bounds_intersect(const float *lo, const float *hi, size_t n, float *o
 // host adds the partials in order, so the sums are deterministic
 int launch_width_partials(const float *lo, const float *hi, int n_cells, size_t n, int blocks, double *part,
                           cudaStream_t st);
-// FP32 FMA throughput (TFLOP/s) of the current device (k_probe.cu); packed:
-// through __ffma2_rn.  Synchronises with st.
-int fma_rate(int packed, int iters, double *tflops, cudaStream_t st);
 // value parts of the records listed in work[0, *count); counters: [0] fallbacks, [1] built, [2] split.
 // split_list (list_cap >= *count entries), split_count and khigh_count (zeroed by the caller): pairs whose
 // MatrixInv fails on the cell are split by a warp each in a second kernel, pairs whose Taylor order exceeds

@@ -1,17 +1,17 @@
-// k_probe.cu -- FP32 FMA throughput of the current device, the measured
+// fma_probe.cu -- FP32 FMA throughput of the current device, the measured
 // companion of the nominal FP32 peak (SMs x 128 lanes x 2 flops x clock) that
-// the render kernel's roofline is quoted against.  Not part of the rendering
-// path.
+// the render kernel's roofline is quoted against.  A benchmark helper built as
+// its own library (libarprobe.so): it is not part of libar or of the
+// rendering path.
 //
 // Every thread runs 16 independent FMA chains (scalar __fmaf_rn, or pairs
 // through the packed __ffma2_rn of sm_100 and later), so the FMA pipe, not a
 // dependency, sets the rate; a grid of 8 blocks of 256 threads per SM keeps
 // every scheduler busy.
 #include <cuda_runtime.h>
+#include <stdint.h>
 
-#include "ar_launch.h"
-
-namespace ar {
+namespace arprobe {
 
 template <bool PACKED>
 __global__ void __launch_bounds__(256) fma_rate_kernel(float *out, float b, float c, int iters)
@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(256) fma_rate_kernel(float *out, float b, floa
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
-int fma_rate(int packed, int iters, double *tflops, cudaStream_t st)
+static int fma_rate(int packed, int iters, double *tflops, cudaStream_t st)
 {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 1;
@@ -67,4 +67,15 @@ int fma_rate(int packed, int iters, double *tflops, cudaStream_t st)
     return r;
 }
 
-}  // namespace ar
+}  // namespace arprobe
+
+// TFLOP/s (an FMA counts as 2 flops) of 16 independent FMA chains per thread
+// over 8 blocks of 256 threads per SM, iters steps each, timed with CUDA
+// events on stream; packed = 1 issues them in pairs.  Returns 0, or 1 for bad
+// arguments or a CUDA error.  Synchronises with stream; allocates and frees a
+// small device buffer.
+extern "C" int arprobe_fp32_fma_rate(int32_t packed, int32_t iters, double *tflops, void *stream)
+{
+    if (!tflops || iters < 1) return 1;
+    return arprobe::fma_rate(packed, iters, tflops, (cudaStream_t)stream);
+}

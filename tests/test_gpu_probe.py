@@ -1,6 +1,6 @@
-"""The FP32 FMA rate probe (ar_fp32_fma_rate): a plausible rate for one GB300
-(nominal 152 SMs x 128 lanes x 2 flops x 2.07 GHz = 80.5 TFLOP/s), scalar and
-packed, and argument checks."""
+"""The benchmark's FP32 FMA rate probe (libarprobe.so, not part of libar): a
+plausible rate for one GB300 (nominal 152 SMs x 128 lanes x 2 flops x 2.07
+GHz = 80.5 TFLOP/s), scalar and packed, and argument checks."""
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -8,11 +8,11 @@ pytestmark = pytest.mark.gpu
 
 
 def test_fma_rate():
-    from paper_2503_00308_gb300 import _build, ar
+    from paper_2503_00308_gb300 import _build, probe
     _build.build()
     assert torch.cuda.is_available()
     for packed in (False, True):
-        r = ar.ar_fp32_fma_rate(packed, 4096)
+        r = probe.fp32_fma_rate(packed, 4096)
         assert 20.0 < r < 120.0, r
-    with pytest.raises(ar.ArError):
-        ar.ar_fp32_fma_rate(False, 0)
+    with pytest.raises(RuntimeError):
+        probe.fp32_fma_rate(False, 0)
