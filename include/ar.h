@@ -100,6 +100,8 @@ typedef struct ar_render_stats {
                                    interval was too wide for FP32 (ar_scene_set_fp64_alpha) */
     int64_t n_fp64_segments;    /* (cell, tile) sweeps that met such an evaluation and were
                                    swept again by the FP64-capable instance of the renderer */
+    int64_t n_graph_replays;    /* cell batches whose binning and render were replayed from a
+                                   captured CUDA graph (ar_scene_set_graphs) */
 } ar_render_stats;
 
 /* Create a scene from n Gaussians <uw, Mw, o, c> (Sec. 2.2).  Mw is given by
@@ -375,6 +377,24 @@ int ar_scene_set_blend(ar_scene *scene, int32_t mode);
  * threshold. */
 #define AR_FP64_ALPHA_DEFAULT 1e-4f
 int ar_scene_set_fp64_alpha(ar_scene *scene, float threshold);
+
+/* CUDA graphs for repeated renders (on = 1, the default; 0 = off).  After the
+ * one host synchronisation of a cell batch (which reads how many pairs and
+ * tile entries it has, to size its buffers), everything else the batch
+ * enqueues -- the binning and the windowed rounds of record build and render,
+ * some forty kernels and memsets -- depends on the host only through those
+ * sizes, the workspace's buffers and the call's parameters.  With graphs on,
+ * that phase is captured once per such key (on a private stream, then
+ * launched on cuda_stream) and later batches with the same key replay the
+ * graph instead of enqueueing it again; up to 32 graphs are kept per
+ * workspace.  The key includes the output buffers' addresses, the first
+ * window the workspace has learned and the stage-timing switch, so renders
+ * that reuse their output buffers replay from the second or third call on.  The bounds are bit-identical either way.  If a capture fails,
+ * the scene falls back to enqueueing and turns graphs off.  Applies to
+ * ar_render_abstract, _host, the partitioned and refined renders and serving
+ * (not to the plain FP64 path or the no-allocation entry point, which
+ * allocate nothing for graphs).  AR_EINVAL for a null scene or on not 0/1. */
+int ar_scene_set_graphs(ar_scene *scene, int32_t on);
 
 /* Counters and stage times of the scene's last render (synchronises its stream). */
 int ar_last_render_stats(ar_scene *scene, ar_render_stats *stats);

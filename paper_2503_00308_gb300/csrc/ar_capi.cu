@@ -219,8 +219,21 @@ void DevBuf::release()
     cap = 0;
 }
 
+void Workspace::append_pointers(std::vector<uint64_t> &key) const
+{
+    const DevBuf *all[] = {&cells_lohi, &cells, &vN, &recs, &boxes, &keys, &counters, &evk0, &evk1, &evv0, &evv1,
+                           &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege,
+                           &segk0, &segk1, &segv0, &segv1, &work, &state, &wlist, &act0, &act1, &words,
+                           &slist, &plist, &pmask, &whist};
+    for (const DevBuf *b : all) key.push_back((uint64_t)(uintptr_t)b->p);
+}
+
 void Workspace::release()
 {
+    for (GraphEntry &g : graphs) cudaGraphExecDestroy(g.exec);
+    graphs.clear();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    cap_stream = nullptr;
     DevBuf *all[] = {&cells_lohi, &cells, &vN, &recs, &boxes, &keys, &counters, &evk0, &evk1, &evv0, &evv1,
                      &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege, &segk0,
                      &segk1, &segv0, &segv1, &work, &state, &wlist, &act0, &act1, &words, &slist, &plist, &pmask, &whist, &out_lo,
@@ -425,6 +438,14 @@ int ar_scene_set_blend(ar_scene *s, int32_t mode)
     return AR_OK;
 }
 
+int ar_scene_set_graphs(ar_scene *s, int32_t on)
+{
+    if (!s) return fail(AR_EINVAL, "scene is null");
+    if (on != 0 && on != 1) return fail(AR_EINVAL, "on must be 0 or 1");
+    s->graphs = on != 0;
+    return AR_OK;
+}
+
 int ar_scene_set_fp64_alpha(ar_scene *s, float threshold)
 {
     if (!s) return fail(AR_EINVAL, "scene is null");
@@ -468,11 +489,11 @@ int validate_call(const ar_intrinsics *in, const ar_nominal_pose *pose, const ar
         if (r_) return r_;         \
     } while (0)
 
-// Sizes the binning buffers of the workspace and runs the binning of n_pairs
-// (cell, Gaussian) pairs with ne events and nent (event, tile) entries.
+// Sizes the binning buffers of the workspace and (run) runs the binning of
+// n_pairs (cell, Gaussian) pairs with ne events and nent (event, tile) entries.
 static int bin_pairs(Workspace &ws, const PixBox *boxes, const double *keys, uint64_t n_pairs, uint64_t n_gauss,
                      int n_cells, uint64_t ne, uint64_t nent, int TS, int ntx, int n_tiles, cudaStream_t st,
-                     BinOut &bo, int &launches)
+                     BinOut &bo, int &launches, bool run = true)
 {
     const uint64_t n_seg = (uint64_t)n_cells * n_tiles;
     const uint64_t nsc = n_pairs > ne ? n_pairs : ne;
@@ -500,6 +521,7 @@ static int bin_pairs(Workspace &ws, const PixBox *boxes, const double *keys, uin
     RK(ws.segv0.ensure(sizeof(uint32_t) * n_seg));
     RK(ws.segv1.ensure(sizeof(uint32_t) * n_seg));
     RK(ws.work.ensure(256));
+    if (!run) return AR_OK;
     BinArgs ba;
     ba.boxes = boxes;
     ba.keys = keys;
@@ -526,6 +548,34 @@ static int bin_pairs(Workspace &ws, const PixBox *boxes, const double *keys, uin
         return fail(AR_EDEVICE, "binning: %s", cudaGetErrorString(cudaGetLastError()));
     return AR_OK;
 }
+
+static uint32_t float_bits(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, sizeof u);
+    return u;
+}
+static uint64_t double_bits(double d)
+{
+    uint64_t u;
+    std::memcpy(&u, &d, sizeof u);
+    return u;
+}
+
+// A stage-timing event on q.  While q is being captured, the record becomes an
+// external event node of the graph, so that every replay records the event
+// (an ordinary record during capture would only order the graph's nodes).
+static cudaError_t record_stage(cudaEvent_t e, cudaStream_t q)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(q, &cs) != cudaSuccess) return cudaGetLastError();
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e, q, cudaEventRecordExternal)
+                                               : cudaEventRecord(e, q);
+}
+
+static int enqueue_rest(ar_scene *s, Workspace &ws, const CallConst &cc, int M, int TS, float *out_lo, float *out_hi,
+                        cudaStream_t q, bool profiling, int batch, cudaEvent_t *ev, uint64_t n_pairs, uint64_t n_seg,
+                        uint64_t ne, uint64_t nent, int ntx, int n_tiles, bool plain, int &launches);
 
 // One batch of cells through the whole pipeline.  cc describes the batch
 // (n_cells = cells in the batch, slots shared by every batch of the call).
@@ -576,13 +626,110 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
     if (nent >= (1ull << 32) - (1ull << 20))
         return fail(AR_ENOMEM, "%llu bin entries exceed the 32-bit index range; lower the workspace limit",
                     (unsigned long long)nent);
+    // every buffer of the rest of the batch, sized before any of it is enqueued
+    BinOut bo;
+    RK(bin_pairs(ws, ws.boxes.as<PixBox>(), ws.keys.as<double>(), n_pairs, (uint64_t)s->n, n_cells, ne, nent, TS, ntx,
+                 n_tiles, st, bo, launches, false));
+    if (!plain) {
+        RK(ws.state.ensure(sizeof(uint32_t) * n_pairs));
+        RK(ws.wlist.ensure(sizeof(uint32_t) * n_pairs));
+        RK(ws.act0.ensure(sizeof(uint32_t) * n_seg));
+        RK(ws.act1.ensure(sizeof(uint32_t) * n_seg));
+        RK(ws.words.ensure(sizeof(uint32_t) * 8));
+        RK(ws.slist.ensure(sizeof(uint32_t) * n_pairs));
+        RK(ws.plist.ensure(sizeof(uint32_t) * n_seg));
+        RK(ws.pmask.ensure(sizeof(uint32_t) * n_seg * (TS * TS / 32)));
+    }
+    // The rest of the batch (binning, then the windowed rounds of build and
+    // render) depends on the host only through the sizes read above, so with
+    // graphs on it is captured once per sizes, buffers and parameters and
+    // replayed as one CUDA graph: a repeated render of the same shape
+    // launches one graph instead of some forty kernels and memsets.
+    std::vector<uint64_t> key;
+    if (s->graphs && !plain) {
+        const uint64_t head[] = {(uint64_t)M, (uint64_t)TS, (uint64_t)n_cells, n_pairs, ne, nent, (uint64_t)n_tiles,
+                                 (uint64_t)ntx, (uint64_t)W, (uint64_t)H, (uint64_t)s->n, ws.w0,
+                                 (uint64_t)s->blend, (uint64_t)float_bits(s->fp64_dev), (uint64_t)float_bits(s->k_open),
+                                 (uint64_t)profiling, (uint64_t)batch, (uint64_t)(uintptr_t)out_lo,
+                                 (uint64_t)(uintptr_t)out_hi, (uint64_t)(uintptr_t)d_lo};
+        key.assign(head, head + sizeof head / sizeof head[0]);
+        ws.append_pointers(key);
+        for (int k = 0; k < kEventsPerBatch; ++k) key.push_back((uint64_t)(uintptr_t)ev[k]);
+        // the call constants the launches take by value (named fields: no padding bytes)
+        const float fc[5] = {cc.fx, cc.fy, cc.cx, cc.cy, cc.near_plane};
+        for (float f : fc) key.push_back(float_bits(f));
+        for (int i = 0; i < 9; ++i) key.push_back(double_bits(cc.R0[i]));
+        for (int i = 0; i < 3; ++i) key.push_back(double_bits(cc.t0[i]));
+        for (int k = 0; k < MAXV; ++k) key.push_back((uint64_t)(int64_t)cc.m_slot[k]);
+        key.push_back((uint64_t)cc.n_gauss);
+        for (GraphEntry &g : ws.graphs)
+            if (g.key == key) {
+                CK(cudaGraphLaunch(g.exec, st));
+                g.last_use = ++ws.graph_clock;
+                launches += g.launches;
+                ++ws.graph_hits;
+                ++rs.n_graph_replays;
+                return AR_OK;
+            }
+    }
+    cudaStream_t q = st;  // the stream the rest is enqueued on (the capture stream while capturing)
+    bool capturing = false;
+    if (!key.empty()) {
+        if (!ws.cap_stream) CK(cudaStreamCreateWithFlags(&ws.cap_stream, cudaStreamNonBlocking));
+        if (cudaStreamBeginCapture(ws.cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            q = ws.cap_stream;
+            capturing = true;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    const int launches0 = launches;
+    const int rc = enqueue_rest(s, ws, cc, M, TS, out_lo, out_hi, q, profiling, batch, ev, n_pairs, n_seg, ne, nent,
+                                ntx, n_tiles, plain, launches);
+    if (capturing) {
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(ws.cap_stream, &graph);
+        cudaGraphExec_t exec = nullptr;
+        if (rc == AR_OK && e == cudaSuccess && graph &&
+            cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess && exec) {
+            cudaGraphDestroy(graph);
+            if (ws.graphs.size() >= kMaxGraphs) {
+                size_t old = 0;
+                for (size_t i = 1; i < ws.graphs.size(); ++i)
+                    if (ws.graphs[i].last_use < ws.graphs[old].last_use) old = i;
+                cudaGraphExecDestroy(ws.graphs[old].exec);
+                ws.graphs.erase(ws.graphs.begin() + (long)old);
+            }
+            ws.graphs.push_back(GraphEntry{key, exec, launches - launches0, ++ws.graph_clock});
+            CK(cudaGraphLaunch(exec, st));
+            return AR_OK;
+        }
+        // capture failed (a call that cannot be captured): run uncaptured from now on
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        s->graphs = false;
+        RK(rc);
+        launches = launches0;
+        return enqueue_rest(s, ws, cc, M, TS, out_lo, out_hi, st, profiling, batch, ev, n_pairs, n_seg, ne, nent, ntx,
+                            n_tiles, plain, launches);
+    }
+    return rc;
+}
+
+// The part of a batch after the host has read its sizes: binning, then the
+// render (windowed rounds, or the plain FP64 renderer), enqueued on q.
+static int enqueue_rest(ar_scene *s, Workspace &ws, const CallConst &cc, int M, int TS, float *out_lo, float *out_hi,
+                        cudaStream_t q, bool profiling, int batch, cudaEvent_t *ev, uint64_t n_pairs, uint64_t n_seg,
+                        uint64_t ne, uint64_t nent, int ntx, int n_tiles, bool plain, int &launches)
+{
+    const int W = cc.W, H = cc.H, n_cells = cc.n_cells;
     BinOut bo;
     {
         NvtxRange r("ar.bin: depth-sorted tile bins");
         RK(bin_pairs(ws, ws.boxes.as<PixBox>(), ws.keys.as<double>(), n_pairs, (uint64_t)s->n, n_cells, ne, nent, TS,
-                     ntx, n_tiles, st, bo, launches));
+                     ntx, n_tiles, q, bo, launches));
     }
-    if (profiling) CK(cudaEventRecord(ev[2], st));
+    if (profiling) CK(record_stage(ev[2], q));
     RenderLaunch rl;
     rl.recs = ws.recs.as<float>();
     rl.recs64 = ws.recs.as<double>();
@@ -603,25 +750,17 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
     rl.out_hi = out_hi;
     rl.counters = ws.counters.as<unsigned long long>() + 8 + kCountersPerBatch * batch;
     if (plain) {
-        if (profiling) CK(cudaEventRecord(ev[3], st));
-        if (launch_render_plain(M, TS, rl, st))
+        if (profiling) CK(record_stage(ev[3], q));
+        if (launch_render_plain(M, TS, rl, q))
             return fail(AR_EDEVICE, "render launch: %s", cudaGetErrorString(cudaGetLastError()));
         ++launches;
         if (profiling)
-            for (int k = 4; k < kEventsPerBatch; ++k) CK(cudaEventRecord(ev[k], st));
+            for (int k = 4; k < kEventsPerBatch; ++k) CK(record_stage(ev[k], q));
     } else {
-        RK(ws.state.ensure(sizeof(uint32_t) * n_pairs));
-        RK(ws.wlist.ensure(sizeof(uint32_t) * n_pairs));
-        RK(ws.act0.ensure(sizeof(uint32_t) * n_seg));
-        RK(ws.act1.ensure(sizeof(uint32_t) * n_seg));
-        RK(ws.words.ensure(sizeof(uint32_t) * 8));
-        RK(ws.slist.ensure(sizeof(uint32_t) * n_pairs));
-        RK(ws.plist.ensure(sizeof(uint32_t) * n_seg));
-        RK(ws.pmask.ensure(sizeof(uint32_t) * n_seg * (TS * TS / 32)));
         rl.sweep_hist = ws.whist.as<uint32_t>();
         RK(run_windowed_render(M, TS, rl, cc, ws.cells.p, ws.vN.as<double>(), n_pairs, n_seg, ws.state.as<uint32_t>(),
                                ws.wlist.as<uint32_t>(), ws.act0.as<uint32_t>(), ws.act1.as<uint32_t>(),
-                               ws.words.as<uint32_t>(), rl.counters + 2, st, &launches,
+                               ws.words.as<uint32_t>(), rl.counters + 2, q, &launches,
                                profiling ? ev + 3 : nullptr, ws.w0, ws.slist.as<uint32_t>(), ws.plist.as<uint32_t>(),
                                ws.pmask.as<uint32_t>()));
     }
@@ -672,7 +811,7 @@ int run_windowed_render(int M, int TS, RenderLaunch rl, const CallConst &cc, con
                                 words + 3, (uint32_t)n_pairs, words + 4, st))
             return fail(AR_EDEVICE, "record build launch: %s", cudaGetErrorString(cudaGetLastError()));
         *launches += 2;
-        if (ev) CK(cudaEventRecord(ev[2 * r], st));
+        if (ev) CK(record_stage(ev[2 * r], st));
         rl.active = cur;
         rl.n_active = cur_n;
         rl.window = kWindow[r];
@@ -694,7 +833,7 @@ int run_windowed_render(int M, int TS, RenderLaunch rl, const CallConst &cc, con
         rp.f64 = 1;
         if (launch_render(M, TS, rp, st))
             return fail(AR_EDEVICE, "render launch: %s", cudaGetErrorString(cudaGetLastError()));
-        if (ev) CK(cudaEventRecord(ev[2 * r + 1], st));
+        if (ev) CK(record_stage(ev[2 * r + 1], st));
         *launches += 6;
     }
     return AR_OK;

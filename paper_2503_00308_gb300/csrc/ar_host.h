@@ -20,6 +20,16 @@ struct DevBuf {
     template <class T> T *as() const { return (T *)p; }
 };
 
+// A captured post-sync phase of a cell batch (binning and the windowed
+// rounds), keyed by everything its launches depend on.
+struct GraphEntry {
+    std::vector<uint64_t> key;
+    cudaGraphExec_t exec;
+    int launches;        // kernels it launches
+    uint64_t last_use;
+};
+constexpr size_t kMaxGraphs = 32;  // cached graphs per workspace (least recently used goes)
+
 // Everything one render needs besides the scene itself.  A scene owns one
 // workspace; a server owns one per slot so that concurrent requests never
 // share buffers.
@@ -43,8 +53,12 @@ struct Workspace {
     int64_t fallback_prep = 0;                 // MatrixInv fallbacks counted by the record kernel
     int64_t split_prep = 0;                    // MatrixInv input splits counted by the record kernel
     int64_t built_prep = 0;                    // records built completely by the record kernel
+    std::vector<GraphEntry> graphs;            // captured batch phases (see render_batch)
+    uint64_t graph_clock = 0, graph_hits = 0;
+    cudaStream_t cap_stream = nullptr;         // private stream the captures are taken on
     void release();
     size_t bytes() const;
+    void append_pointers(std::vector<uint64_t> &key) const;  // every buffer's address, for graph keys
 };
 
 int set_last_error(int code, const char *msg);  // sets ar_last_error() for this thread
@@ -97,6 +111,7 @@ struct ar_scene {
     ar::Workspace ws;
     bool profiling = false;
     int blend = AR_BLEND_INTERVAL;  // blend of the abstract renders (ar_scene_set_blend)
+    bool graphs = true;             // replay repeated batch phases as CUDA graphs (ar_scene_set_graphs)
     float fp64_dev = AR_FP64_ALPHA_DEFAULT;  // FP64 re-evaluation threshold (ar_scene_set_fp64_alpha)
     ar_render_stats stats;
     cudaStream_t stats_stream = nullptr;
