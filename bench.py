@@ -383,7 +383,7 @@ def workload_leg(ar, name, args, sp, warmup, steps, window_edge):
     acc = accuracy(keep, glo, ghi)
     out = {"value": w.pixel_cells() / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "warmup": warmup, "steps": steps,
            "config": {"workload": w.name, "gaussians": w.scene.n, "image": "%dx%d" % (cam.width, cam.height),
-                      "cells": nc, "pose_vars": st["m_vars"], "tile": st["tile"]},
+                      "cells": nc, "pose_vars": st["m_vars"], "tile": st["tile"], "chunk": st["chunk"]},
            "stages_ms": stage_dict(st), "counts": count_dict(st), "roofline": roofline_of(st, r_ms),
            "gaps": gap_metrics(out_lo, out_hi), "accuracy": acc, "oracle_sample": cpu["sample"]}
     s.close()
@@ -620,8 +620,9 @@ def run_ours(args, rank, world, local, pg):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name, "gaussians": w.scene.n, "image": "%dx%d" % (cam.width, cam.height),
-                   "cells": nc, "pose_vars": M, "tile": stats["tile"],
-                   "tile_choice": "autotuned" if args.tile == 0 else "fixed",
+                   "cells": nc, "pose_vars": M, "tile": stats["tile"], "chunk": stats["chunk"],
+                   "tile_choice": ("autotuned over (tile, chunk) in (16, 16), (16, 8), (16, 32), (8, 16)"
+                                   if args.tile == 0 else "fixed"),
                    "l2": "working set (records + bins, tens of GB) far larger than L2; no flush needed"},
         "clocks": clk,
         "e2e": e2e,

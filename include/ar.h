@@ -102,6 +102,8 @@ typedef struct ar_render_stats {
                                    swept again by the FP64-capable instance of the renderer */
     int64_t n_graph_replays;    /* cell batches whose binning and render were replayed from a
                                    captured CUDA graph (ar_scene_set_graphs) */
+    int32_t chunk;              /* events per staged chunk of the per-pixel sweep (autotuned
+                                   with tile = 0, else 16) */
 } ar_render_stats;
 
 /* Create a scene from n Gaussians <uw, Mw, o, c> (Sec. 2.2).  Mw is given by
@@ -131,8 +133,11 @@ int ar_scene_destroy(ar_scene *scene);
  *   bounds do not depend on it beyond 2e-5: a pixel stops sweeping once what
  *   is left of its tile's list can move its bounds by less than 1e-5, and
  *   widens them by that much).  With 0, the first call for a given image
- *   size and number of pose variables times the pipeline with both edges on
- *   its first two cells and keeps the faster for the scene (autotuner).
+ *   size and number of pose variables times the pipeline on its first eight
+ *   cells for each (tile edge, events per staged chunk of the sweep) of
+ *   (16, 16), (16, 8), (16, 32), (8, 16) and keeps the fastest for the scene
+ *   (autotuner; ar_render_stats.tile and .chunk report the choice).  An
+ *   explicit tile sweeps in chunks of 16.
  *   out_lower, out_upper: device pointers, float32 [n_cells][H][W][3] each,
  *   owned by the caller.
  * Work is enqueued on cuda_stream; the call returns after the last launch is
@@ -172,10 +177,11 @@ int ar_render_abstract_host(ar_scene *scene, const ar_intrinsics *intr, const ar
  *     the first call on a device may load the library's device code there
  *     (the one-time set-up), so make that first call before any stream
  *     capture.
- *   - tile = 0 takes the edge the scene's autotuner chose for this image
- *     size and number of pose variables in an earlier ar_render_abstract
- *     call, else 16; this entry point does not time candidates itself.  With
- *     the same tile the bounds are bit-identical to ar_render_abstract's.
+ *   - tile = 0 takes the tile edge and sweep chunk the scene's autotuner
+ *     chose for this image size and number of pose variables in an earlier
+ *     ar_render_abstract call, else 16 and 16; this entry point does not time
+ *     candidates itself.  With the same tile argument, after the same tuning,
+ *     the bounds are bit-identical to ar_render_abstract's.
  *   - All calls share the array and it keeps the last call's contents: two
  *     calls that overlap on the GPU (different streams or threads without
  *     ordering) race and corrupt each other's results.  Serialise them.
@@ -323,6 +329,19 @@ int ar_debug_records(ar_scene *scene, const ar_intrinsics *intr, const ar_nomina
 int ar_debug_alpha(ar_scene *scene, const ar_intrinsics *intr, const ar_nominal_pose *pose,
                    const ar_pose_box *cell, int32_t n, const int64_t *gi, const int32_t *px, const int32_t *py,
                    int32_t precision, double *out);
+
+/* Test hook: the events per staged chunk (8, 16 or 32) of the FP32 sweep at
+ * tile 16 for the scene's renders with an explicit tile (0: back to 16), so
+ * that the autotuner's other candidates can be checked for parity.
+ * AR_EINVAL for a null scene or another value. */
+int ar_debug_set_chunk(ar_scene *scene, int32_t chunk);
+
+/* Test hook: a cell batch whose (Gaussian, cell, tile) entries reach `cap`
+ * is split into two halves and rendered again (the bins index entries with
+ * 32 bits, so the library's own cap is 2^32 - 2^20, which cap = 0 restores);
+ * a lower cap exercises the split.  The bounds do not change.  AR_EINVAL for
+ * a null scene or a cap outside [0, 2^32 - 2^20]. */
+int ar_debug_set_entry_cap(ar_scene *scene, int64_t cap);
 
 /* Device-memory limit (bytes, >= 1 MiB) for the scene's render workspace.
  * ar_render_abstract splits the cells of a call into batches whose

@@ -38,7 +38,8 @@ class ar_render_stats(ctypes.Structure):
                 ("ms_prep", c_float), ("ms_bin", c_float), ("ms_render", c_float), ("ms_total", c_float),
                 ("n_evaluated", c_int64), ("n_reevaluated", c_int64), ("n_built", c_int64),
                 ("n_restarted", c_int64), ("ms_build", c_float), ("n_split", c_int64),
-                ("n_fp64", c_int64), ("n_fp64_segments", c_int64), ("n_graph_replays", c_int64)]
+                ("n_fp64", c_int64), ("n_fp64_segments", c_int64), ("n_graph_replays", c_int64),
+                ("chunk", c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -77,6 +78,8 @@ def lib():
             "ar_scene_set_blend": ([P, ctypes.c_int32], ctypes.c_int),
             "ar_scene_set_fp64_alpha": ([P, ctypes.c_float], ctypes.c_int),
             "ar_scene_set_graphs": ([P, ctypes.c_int32], ctypes.c_int),
+            "ar_debug_set_chunk": ([P, ctypes.c_int32], ctypes.c_int),
+            "ar_debug_set_entry_cap": ([P, c_int64], ctypes.c_int),
             "ar_bounds_union": ([P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P], ctypes.c_int),
             "ar_partition_piece": ([P, P, c_int64, P], ctypes.c_int),
             "ar_render_abstract_refined": ([P, P, P, P, ctypes.c_int32, ctypes.c_int32, P, P, P, ctypes.c_int32, P, P],
@@ -268,6 +271,14 @@ def ar_scene_set_fp64_alpha(scene, threshold: float):
 
 def ar_scene_set_graphs(scene, on: bool):
     return check(lib().ar_scene_set_graphs(scene, 1 if on else 0))
+
+
+def ar_debug_set_chunk(scene, chunk: int):
+    return check(lib().ar_debug_set_chunk(scene, int(chunk)))
+
+
+def ar_debug_set_entry_cap(scene, cap: int):
+    return check(lib().ar_debug_set_entry_cap(scene, int(cap)))
 
 
 def ar_last_render_stats(scene) -> dict:

@@ -48,6 +48,9 @@ constexpr int kEventsPerBatch = 9;
 // splits (record build), segments restarted (render), evaluations taken
 // again in FP64 (render), segments swept again for them (render)
 constexpr int kCountersPerBatch = 8;
+// render_batch's answer for a batch with more tile entries than 32-bit
+// indices reach (not an AR_ code: render_core splits the batch)
+constexpr int kSplitBatch = 1000;
 }  // namespace ar
 
 namespace ar {
@@ -438,6 +441,23 @@ int ar_scene_set_blend(ar_scene *s, int32_t mode)
     return AR_OK;
 }
 
+int ar_debug_set_entry_cap(ar_scene *s, int64_t cap)
+{
+    if (!s) return fail(AR_EINVAL, "scene is null");
+    const int64_t top = (int64_t)((1ull << 32) - (1ull << 20));
+    if (cap < 0 || cap > top) return fail(AR_EINVAL, "cap must be in [0, 2^32 - 2^20]");
+    s->entry_cap = cap ? (uint64_t)cap : (uint64_t)top;
+    return AR_OK;
+}
+
+int ar_debug_set_chunk(ar_scene *s, int32_t chunk)
+{
+    if (!s) return fail(AR_EINVAL, "scene is null");
+    if (chunk != 0 && chunk != 8 && chunk != 16 && chunk != 32) return fail(AR_EINVAL, "chunk must be 0, 8, 16 or 32");
+    s->chunk = chunk;
+    return AR_OK;
+}
+
 int ar_scene_set_graphs(ar_scene *s, int32_t on)
 {
     if (!s) return fail(AR_EINVAL, "scene is null");
@@ -573,14 +593,14 @@ static cudaError_t record_stage(cudaEvent_t e, cudaStream_t q)
                                                : cudaEventRecord(e, q);
 }
 
-static int enqueue_rest(ar_scene *s, Workspace &ws, const CallConst &cc, int M, int TS, float *out_lo, float *out_hi,
+static int enqueue_rest(ar_scene *s, Workspace &ws, const CallConst &cc, int M, int TS, int CH, float *out_lo, float *out_hi,
                         cudaStream_t q, bool profiling, int batch, cudaEvent_t *ev, uint64_t n_pairs, uint64_t n_seg,
                         uint64_t ne, uint64_t nent, int ntx, int n_tiles, bool plain, int &launches);
 
 // One batch of cells through the whole pipeline.  cc describes the batch
 // (n_cells = cells in the batch, slots shared by every batch of the call).
 // plain: FP64 records and the plain FP64 renderer instead of the FP32 ones.
-static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, int TS, const double *d_lo,
+static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, int TS, int CH, const double *d_lo,
                         const double *d_hi, float *out_lo, float *out_hi, cudaStream_t st, bool profiling,
                         int batch, ar_render_stats &rs, int &launches, bool plain)
 {
@@ -617,15 +637,13 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
         ws.whist_pending = false;
     }
     const unsigned long long n_valid = ws.h_counters[2];
+    const uint64_t ne = 2 * n_valid, nent = 2 * ws.h_counters[3];
+    if (nent >= s->entry_cap) return kSplitBatch;  // the caller splits the batch
     rs.n_records += (int64_t)n_valid;
     rs.n_triples += (int64_t)ws.h_counters[0];
     rs.n_fallback += (int64_t)ws.h_counters[1];
     rs.n_split += (int64_t)ws.h_counters[4];
-    const uint64_t ne = 2 * n_valid, nent = 2 * ws.h_counters[3];
     rs.n_entries += (int64_t)(nent / 2);
-    if (nent >= (1ull << 32) - (1ull << 20))
-        return fail(AR_ENOMEM, "%llu bin entries exceed the 32-bit index range; lower the workspace limit",
-                    (unsigned long long)nent);
     // every buffer of the rest of the batch, sized before any of it is enqueued
     BinOut bo;
     RK(bin_pairs(ws, ws.boxes.as<PixBox>(), ws.keys.as<double>(), n_pairs, (uint64_t)s->n, n_cells, ne, nent, TS, ntx,
@@ -647,7 +665,7 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
     // launches one graph instead of some forty kernels and memsets.
     std::vector<uint64_t> key;
     if (s->graphs && !plain) {
-        const uint64_t head[] = {(uint64_t)M, (uint64_t)TS, (uint64_t)n_cells, n_pairs, ne, nent, (uint64_t)n_tiles,
+        const uint64_t head[] = {(uint64_t)M, (uint64_t)TS, (uint64_t)CH, (uint64_t)n_cells, n_pairs, ne, nent, (uint64_t)n_tiles,
                                  (uint64_t)ntx, (uint64_t)W, (uint64_t)H, (uint64_t)s->n, ws.w0,
                                  (uint64_t)s->blend, (uint64_t)float_bits(s->fp64_dev), (uint64_t)float_bits(s->k_open),
                                  (uint64_t)profiling, (uint64_t)batch, (uint64_t)(uintptr_t)out_lo,
@@ -684,7 +702,7 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
         }
     }
     const int launches0 = launches;
-    const int rc = enqueue_rest(s, ws, cc, M, TS, out_lo, out_hi, q, profiling, batch, ev, n_pairs, n_seg, ne, nent,
+    const int rc = enqueue_rest(s, ws, cc, M, TS, CH, out_lo, out_hi, q, profiling, batch, ev, n_pairs, n_seg, ne, nent,
                                 ntx, n_tiles, plain, launches);
     if (capturing) {
         cudaGraph_t graph = nullptr;
@@ -710,7 +728,7 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
         s->graphs = false;
         RK(rc);
         launches = launches0;
-        return enqueue_rest(s, ws, cc, M, TS, out_lo, out_hi, st, profiling, batch, ev, n_pairs, n_seg, ne, nent, ntx,
+        return enqueue_rest(s, ws, cc, M, TS, CH, out_lo, out_hi, st, profiling, batch, ev, n_pairs, n_seg, ne, nent, ntx,
                             n_tiles, plain, launches);
     }
     return rc;
@@ -718,7 +736,7 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
 
 // The part of a batch after the host has read its sizes: binning, then the
 // render (windowed rounds, or the plain FP64 renderer), enqueued on q.
-static int enqueue_rest(ar_scene *s, Workspace &ws, const CallConst &cc, int M, int TS, float *out_lo, float *out_hi,
+static int enqueue_rest(ar_scene *s, Workspace &ws, const CallConst &cc, int M, int TS, int CH, float *out_lo, float *out_hi,
                         cudaStream_t q, bool profiling, int batch, cudaEvent_t *ev, uint64_t n_pairs, uint64_t n_seg,
                         uint64_t ne, uint64_t nent, int ntx, int n_tiles, bool plain, int &launches)
 {
@@ -746,6 +764,7 @@ static int enqueue_rest(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
     rl.k_open = s->k_open;
     rl.rel = s->blend == AR_BLEND_RELATIONAL;
     rl.fp64_dev = s->fp64_dev;
+    rl.ch = CH;
     rl.out_lo = out_lo;
     rl.out_hi = out_hi;
     rl.counters = ws.counters.as<unsigned long long>() + 8 + kCountersPerBatch * batch;
@@ -839,15 +858,18 @@ int run_windowed_render(int M, int TS, RenderLaunch rl, const CallConst &cc, con
     return AR_OK;
 }
 
-// The tile autotuner: for tile = 0, the first render of a scene at a given
-// image size and number of pose variables times the whole pipeline with tile
-// edges 16 and 8 on the first two cells of the call (each twice, keeping the
-// second timing, so that workspace growth is not counted), and keeps the
-// faster for every later render with the same key.  The bounds do not depend
-// on the tile beyond 1e-7.
+// The autotuner: for tile = 0, the first render of a scene at a given image
+// size and number of pose variables times the whole pipeline on the first
+// eight cells of the call for each candidate (tile edge, events per staged
+// chunk): (16, 16), (16, 8), (16, 32), (8, 16).  Each candidate runs three
+// times and keeps the faster of the last two, so that workspace growth and
+// graph capture are not counted; the fastest is kept for every later render
+// with the same key.
+// Other tile edges and chunks move the bounds only by the early stop's 2e-5.
+static const int kTuneCand[4][2] = {{16, 16}, {16, 8}, {16, 32}, {8, 16}};
 static int tuned_tile(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_nominal_pose *pose,
                       const ar_pose_box *cells, int32_t n_cells, float *out_lo, float *out_hi, cudaStream_t st,
-                      int64_t ws_limit, int *TS)
+                      int64_t ws_limit, int *TS, int *CH)
 {
     int m_active = 0;
     for (int k = 0; k < MAXV; ++k) {
@@ -860,34 +882,40 @@ static int tuned_tile(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const
     for (const TunedTile &t : s->tuned)
         if (t.W == in->width && t.H == in->height && t.M == M) {
             *TS = t.TS;
+            *CH = t.CH;
             return AR_OK;
         }
-    const int32_t k = n_cells < 2 ? n_cells : 2;
-    const int cand[2] = {16, 8};
+    const int32_t k = n_cells < 8 ? n_cells : 8;
     float best = 0.f;
-    int best_ts = 16;
+    int bi = 0;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     int r = AR_OK;
-    for (int i = 0; i < 4 && r == AR_OK; ++i) {
-        const int ts = cand[i % 2];
-        CK(cudaEventRecord(e0, st));
-        r = render_core(s, ws, in, pose, cells, k, ts, out_lo, out_hi, st, false, nullptr, false, ws_limit);
-        CK(cudaEventRecord(e1, st));
-        CK(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, e0, e1));
-        if (i >= 2 && (i == 2 || ms < best)) {
-            best = ms;
-            best_ts = ts;
+    for (int c = 0; c < 4 && r == AR_OK; ++c)
+        for (int rep = 0; rep < 3 && r == AR_OK; ++rep) {
+            CK(cudaEventRecord(e0, st));
+            r = render_core(s, ws, in, pose, cells, k, kTuneCand[c][0], out_lo, out_hi, st, false, nullptr, false,
+                            ws_limit, kTuneCand[c][1]);
+            CK(cudaEventRecord(e1, st));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (r == AR_ENOMEM && c > 0) {  // a candidate that does not fit is not chosen
+                r = AR_OK;
+                break;
+            }
+            if (rep >= 1 && ((c == 0 && rep == 1) || ms < best)) {
+                best = ms;
+                bi = c;
+            }
         }
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     RK(r);
-    s->tuned.push_back(TunedTile{in->width, in->height, M, best_ts});
-    *TS = best_ts;
+    s->tuned.push_back(TunedTile{in->width, in->height, M, kTuneCand[bi][0], kTuneCand[bi][1]});
+    *TS = kTuneCand[bi][0];
+    *CH = kTuneCand[bi][1];
     return AR_OK;
 }
 
@@ -915,19 +943,24 @@ static int call_const(const ar_scene *s, const ar_intrinsics *in, const ar_nomin
 
 int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_nominal_pose *pose,
                 const ar_pose_box *cells, int32_t n_cells, int32_t tile, float *out_lo, float *out_hi,
-                cudaStream_t st, bool profiling, ar_render_stats *stats, bool plain, int64_t ws_limit)
+                cudaStream_t st, bool profiling, ar_render_stats *stats, bool plain, int64_t ws_limit, int chunk)
 {
     RK(validate_call(in, pose, cells, n_cells, tile));
     if (!out_lo || !out_hi) return fail(AR_EINVAL, "null output");
     CK(cudaSetDevice(s->device));
+    int tuned_ch = (tile != 0 && s->chunk) ? s->chunk : 16;
     if (tile == 0 && !plain && s->n > 0)
-        RK(tuned_tile(s, ws, in, pose, cells, n_cells, out_lo, out_hi, st, ws_limit, &tile));
+        RK(tuned_tile(s, ws, in, pose, cells, n_cells, out_lo, out_hi, st, ws_limit, &tile, &tuned_ch));
     const int W = in->width, H = in->height;
     const int TS = tile ? tile : 16;
+    // events per staged chunk of the FP32 sweep: the tuner's choice with tile
+    // = 0, else 16 (the FP64 instance always stages 16)
+    const int CH = plain ? 16 : (chunk ? chunk : (TS == 16 ? tuned_ch : 16));
     const size_t out_words = (size_t)n_cells * W * H * 3;
     ar_render_stats rs;
     std::memset(&rs, 0, sizeof rs);
     rs.tile = TS;
+    rs.chunk = CH;
     rs.ms_prep = rs.ms_bin = rs.ms_render = rs.ms_total = rs.ms_build = -1.f;
     CallConst cc;
     const int M = call_const(s, in, pose, cells, n_cells, cc);
@@ -951,18 +984,21 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
     if (per_batch > n_cells) per_batch = n_cells;
     if (plain) per_batch = 1;  // the plain path: one cell per launch sequence
     const int n_batches = (int)((n_cells + per_batch - 1) / per_batch);
+    // a batch whose tile entries would not fit 32-bit indices is split in two
+    // (see below): room for that many more batches' counters and events
+    const int max_batches = 2 * n_batches + 16;
     const int ntx = (W + TS - 1) / TS, nty = (H + TS - 1) / TS;
     if ((uint64_t)per_batch * (uint64_t)ntx * (uint64_t)nty >= (1ull << 31))
         return fail(AR_EINVAL, "too many (cell, tile) segments");
     if (!ws.h_counters) CK(cudaMallocHost(&ws.h_counters, 8 * sizeof(unsigned long long)));
-    while ((int)ws.evs.size() < kEventsPerBatch * n_batches) {
+    while ((int)ws.evs.size() < kEventsPerBatch * max_batches) {
         cudaEvent_t e;
         CK(cudaEventCreate(&e));
         ws.evs.push_back(e);
     }
     RK(ws.cells_lohi.ensure(sizeof(double) * 12 * n_cells));
     RK(ws.vN.ensure(sizeof(double) * VN_STRIDE * s->n));
-    RK(ws.counters.ensure(sizeof(unsigned long long) * (8 + kCountersPerBatch * n_batches)));
+    RK(ws.counters.ensure(sizeof(unsigned long long) * (8 + kCountersPerBatch * max_batches)));
     {
         std::vector<double> lohi((size_t)12 * n_cells);
         for (int c = 0; c < n_cells; ++c)
@@ -977,26 +1013,39 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
     RK(ws.whist.ensure(sizeof(uint32_t) * 256));
     if (!ws.h_whist) CK(cudaMallocHost(&ws.h_whist, sizeof(uint32_t) * 256));
     CK(cudaMemsetAsync(ws.whist.p, 0, sizeof(uint32_t) * 256, st));
-    CK(cudaMemsetAsync(ws.counters.as<unsigned long long>() + 8, 0, sizeof(unsigned long long) * kCountersPerBatch * n_batches, st));
+    CK(cudaMemsetAsync(ws.counters.as<unsigned long long>() + 8, 0, sizeof(unsigned long long) * kCountersPerBatch * max_batches, st));
     int launches = 0;
     NvtxRange call_range(plain ? "ar.render_abstract_plain_fp64" : "ar.render_abstract");
     if (launch_pose_prep(s->uw_lo, s->uw_hi, s->Mw, s->n, cc, ws.vN.as<double>(), st)) return fail(AR_EDEVICE, "pose_prep launch");
     ++launches;
-    for (int b = 0; b < n_batches; ++b) {
-        const int c0 = (int)(b * per_batch);
-        const int nb = (int)(c0 + per_batch <= n_cells ? per_batch : n_cells - c0);
+    std::vector<std::pair<int, int>> batches;  // (first cell, cells)
+    for (int c0 = 0; c0 < n_cells; c0 += (int)per_batch)
+        batches.push_back({c0, (int)(c0 + per_batch <= n_cells ? per_batch : n_cells - c0)});
+    for (size_t b = 0; b < batches.size(); ++b) {
+        const int c0 = batches[b].first, nb = batches[b].second;
         CallConst cb = cc;
         cb.n_cells = nb;
         const size_t off = (size_t)c0 * W * H * 3;
-        RK(render_batch(s, ws, cb, M, TS, d_lo + (size_t)MAXV * c0, d_hi + (size_t)MAXV * c0, out_lo + off,
-                        out_hi + off, st, profiling, b, rs, launches, plain));
+        const int r = render_batch(s, ws, cb, M, TS, CH, d_lo + (size_t)MAXV * c0, d_hi + (size_t)MAXV * c0,
+                                   out_lo + off, out_hi + off, st, profiling, (int)b, rs, launches, plain);
+        if (r == kSplitBatch) {
+            // more tile entries than 32-bit indices reach (its record prep ran,
+            // nothing else was enqueued): the batch goes again as two halves
+            if (nb == 1 || (int)batches.size() >= max_batches)
+                return fail(AR_ENOMEM, "a cell's tile entries exceed the 32-bit index range");
+            batches[b].second = nb / 2;
+            batches.insert(batches.begin() + (long)b + 1, {c0 + nb / 2, nb - nb / 2});
+            --b;
+            continue;
+        }
+        RK(r);
     }
     if (!plain) {
         // for the next render's first window (read after its first synchronisation)
         CK(cudaMemcpyAsync(ws.h_whist, ws.whist.p, sizeof(uint32_t) * 256, cudaMemcpyDeviceToHost, st));
         ws.whist_pending = true;
     }
-    ws.n_batches = n_batches;
+    ws.n_batches = (int)batches.size();
     ws.fallback_prep = rs.n_fallback;
     ws.split_prep = rs.n_split;
     ws.built_prep = plain ? rs.n_records : 0;

@@ -68,7 +68,7 @@ int validate_call(const ar_intrinsics *in, const ar_nominal_pose *pose, const ar
 struct RenderLaunch;
 struct CallConst;
 struct TunedTile {
-    int W, H, M, TS;
+    int W, H, M, TS, CH;  // key (image size, pose variables) -> tile edge, events per staged chunk
 };
 // The FP32 render of one batch in windowed rounds (see render_kernel):
 // demand -> build -> render per round, windows w0, 8192, then unlimited.
@@ -90,7 +90,7 @@ uint32_t learned_window(const uint32_t *hist256);
 int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_nominal_pose *pose,
                 const ar_pose_box *cells, int32_t n_cells, int32_t tile, float *out_lo, float *out_hi,
                 cudaStream_t st, bool profiling, ar_render_stats *stats, bool plain = false,
-                int64_t ws_limit = 0);
+                int64_t ws_limit = 0, int chunk = 0);
 
 }  // namespace ar
 
@@ -112,6 +112,10 @@ struct ar_scene {
     bool profiling = false;
     int blend = AR_BLEND_INTERVAL;  // blend of the abstract renders (ar_scene_set_blend)
     bool graphs = true;             // replay repeated batch phases as CUDA graphs (ar_scene_set_graphs)
+    int chunk = 0;                  // sweep chunk for explicit tiles (0: 16; ar_debug_set_chunk)
+    // a cell batch with this many tile entries or more is split in two (the
+    // 32-bit entry indices; lowered by ar_debug_set_entry_cap for tests)
+    uint64_t entry_cap = (1ull << 32) - (1ull << 20);
     float fp64_dev = AR_FP64_ALPHA_DEFAULT;  // FP64 re-evaluation threshold (ar_scene_set_fp64_alpha)
     ar_render_stats stats;
     cudaStream_t stats_stream = nullptr;

@@ -117,15 +117,19 @@ int ar_render_abstract_noalloc(ar_scene *s, const ar_intrinsics *in, const ar_no
         cc.m_slot[k] = act ? m_active++ : -1;
     }
     const int M = m_active <= 1 ? 1 : (m_active <= 4 ? 4 : 6);
-    // tile = 0: the edge the scene's autotuner chose for this image size and
-    // number of pose variables, if an earlier ar_render_abstract call tuned
-    // it; else 16 (this entry point does not time candidates itself)
-    int TS = tile;
+    // tile = 0: the tile edge and chunk the scene's autotuner chose for this
+    // image size and number of pose variables, if an earlier
+    // ar_render_abstract call tuned them; else 16 and 16 (this entry point
+    // does not time candidates itself)
+    int TS = tile, CH = 16;
     if (TS == 0) {
         TS = 16;
         std::lock_guard<std::mutex> lock(s->tune_mu);
         for (const TunedTile &t : s->tuned)
-            if (t.W == W && t.H == H && t.M == M) TS = t.TS;
+            if (t.W == W && t.H == H && t.M == M) {
+                TS = t.TS;
+                CH = t.CH;
+            }
     }
     cc.W = W; cc.H = H;
     cc.fx = in->fx; cc.fy = in->fy; cc.cx = in->cx; cc.cy = in->cy; cc.near_plane = in->near_plane;
@@ -221,6 +225,7 @@ int ar_render_abstract_noalloc(ar_scene *s, const ar_intrinsics *in, const ar_no
     rl.k_open = s->k_open;
     rl.rel = s->blend == AR_BLEND_RELATIONAL;
     rl.fp64_dev = s->fp64_dev;
+    rl.ch = CH;
     rl.out_lo = out_lower;
     rl.out_hi = out_upper;
     rl.counters = nullptr;

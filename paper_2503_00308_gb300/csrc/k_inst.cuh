@@ -61,13 +61,15 @@ int AR_CAT(launch_render_plain_m, AR_M)(int TS, const RenderLaunch &a, cudaStrea
     return TS == 16 ? launch_render_plain_ts<16>(a, st) : launch_render_plain_ts<8>(a, st);
 }
 
-template <int TS, bool REL, bool F64>
+template <int TS, bool REL, bool F64, int CH = 16>
 static int launch_render_ts(const RenderLaunch &a, cudaStream_t st)
 {
-    // double-buffered chunks of 16 events and a ring of 4 (measured best of
-    // chunks 8-64 and rings 3-8: the exit vote, taken once per chunk, stops a
-    // tile sooner with short chunks; the ring's shared memory stays small)
-    constexpr int CH = 16, RING = 4;
+    // double-buffered chunks of CH events (16 unless the autotuner picks 8 or
+    // 32 for the FP32 sweep at tile 16: the exit vote, taken once per chunk,
+    // stops a tile sooner with short chunks, while long chunks take fewer
+    // barriers) and a ring of 4 (rings of 3-8 measured: 4 keeps the ring's
+    // shared memory small)
+    constexpr int RING = 4;
     typedef RenderSmem<AR_M, TS, CH, RING> SM;
     auto kern = render_kernel<AR_M, TS, CH, RING, REL, F64>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::BYTES) != cudaSuccess)
@@ -128,8 +130,11 @@ int AR_CAT(launch_render_m, AR_M)(int TS, const RenderLaunch &a, cudaStream_t st
         if (a.rel) return TS == 16 ? launch_render_ts<16, true, true>(a, st) : launch_render_ts<8, true, true>(a, st);
         return TS == 16 ? launch_render_ts<16, false, true>(a, st) : launch_render_ts<8, false, true>(a, st);
     }
-    if (a.rel) return TS == 16 ? launch_render_ts<16, true, false>(a, st) : launch_render_ts<8, true, false>(a, st);
-    return TS == 16 ? launch_render_ts<16, false, false>(a, st) : launch_render_ts<8, false, false>(a, st);
+    if (TS == 8) return a.rel ? launch_render_ts<8, true, false>(a, st) : launch_render_ts<8, false, false>(a, st);
+    if (a.ch == 8) return a.rel ? launch_render_ts<16, true, false, 8>(a, st) : launch_render_ts<16, false, false, 8>(a, st);
+    if (a.ch == 32)
+        return a.rel ? launch_render_ts<16, true, false, 32>(a, st) : launch_render_ts<16, false, false, 32>(a, st);
+    return a.rel ? launch_render_ts<16, true, false>(a, st) : launch_render_ts<16, false, false>(a, st);
 }
 
 }  // namespace ar

@@ -240,6 +240,35 @@ def test_cell_batches_are_bit_identical(arlib):
     s.close()
 
 
+def test_batches_split_on_entry_overflow(arlib):
+    """A cell batch whose tile entries would overflow the bins' 32-bit indices
+    is split in halves and rendered again: with a low cap every batch splits
+    down to one cell, with bounds bit-identical to one batch; a single cell
+    over the cap is refused with AR_ENOMEM."""
+    ar = arlib
+    sc = synth.object_scene(3000, 12)
+    cam = synth.look_camera(60, 44, 70.0, centre=(0, 0, -4))
+    lo, hi = synth.cell_grid([0.03, 0.0, 0.03, 0.01, 0.0, 0.0], [2, 1, 2, 2, 1, 1])
+    ref_lo, ref_hi, ref_st = gpu_render(ar, sc, cam, lo, hi, tile=16, return_stats=True)
+    s = ar.Scene(sc)
+    per_cell = ref_st["n_entries"] * 2 // lo.shape[0]
+    ar.ar_debug_set_entry_cap(s.handle, int(1.9 * per_cell))     # two cells' entries do not fit
+    out_lo = torch.empty((lo.shape[0], cam.height, cam.width, 3), device="cuda")
+    out_hi = torch.empty_like(out_lo)
+    ar.ar_set_profiling(s.handle, True)
+    s.render(cam, lo, hi, out_lo, out_hi, tile=16)
+    st = ar.ar_last_render_stats(s.handle)
+    torch.cuda.synchronize()
+    assert np.array_equal(out_lo.double().cpu().numpy(), ref_lo)
+    assert np.array_equal(out_hi.double().cpu().numpy(), ref_hi)
+    assert st["n_entries"] == ref_st["n_entries"] and st["n_evaluated"] == ref_st["n_evaluated"]
+    ar.ar_debug_set_entry_cap(s.handle, 10)
+    with pytest.raises(ar.ArError) as e:
+        s.render(cam, lo, hi, out_lo, out_hi, tile=16)
+    assert e.value.code == ar.AR_ENOMEM
+    s.close()
+
+
 def test_host_outputs_match_device_outputs(arlib):
     """ar_render_abstract_host: page-locked buffers (written by the render
     kernel itself), pageable buffers (staged and copied), one of each (copied),
@@ -316,8 +345,9 @@ def test_guard_band_parity(arlib, orc):
 
 
 def test_autotuned_tile(arlib):
-    """tile = 0: the autotuner picks 8 or 16 once per (size, pose variables)
-    and the bounds equal those of that tile edge."""
+    """tile = 0: the autotuner picks a (tile edge, chunk) once per (size, pose
+    variables), the same on later calls with bit-identical bounds, and those
+    bounds are within the early stop's 2e-5 of an explicit tile's."""
     sc = synth.object_scene(1500, 6)
     cam = synth.look_camera(50, 38, 60.0, centre=(0, 0, -4))
     lo, hi = synth.cell_grid([0.03, 0.0, 0.03, 0.0, 0.01, 0.0], [2, 1, 2, 1, 1, 1])
@@ -328,11 +358,40 @@ def test_autotuned_tile(arlib):
         a = torch.empty((lo.shape[0], cam.height, cam.width, 3), device="cuda")
         b = torch.empty_like(a)
         s.render(cam, lo, hi, a, b, tile=tile)
-        outs.append((a, b, arlib.ar_last_render_stats(s.handle)["tile"]))
-    assert outs[0][2] in (8, 16) and outs[1][2] == outs[0][2]
+        st = arlib.ar_last_render_stats(s.handle)
+        outs.append((a, b, st["tile"], st["chunk"]))
+    assert (outs[0][2], outs[0][3]) in ((16, 16), (16, 8), (16, 32), (8, 16))
+    assert outs[1][2:] == outs[0][2:]
+    torch.cuda.synchronize()
+    assert torch.equal(outs[1][0], outs[0][0]) and torch.equal(outs[1][1], outs[0][1])
     a = torch.empty_like(outs[0][0])
     b = torch.empty_like(a)
     s.render(cam, lo, hi, a, b, tile=outs[0][2])
+    st = arlib.ar_last_render_stats(s.handle)
     torch.cuda.synchronize()
-    assert torch.equal(a, outs[0][0]) and torch.equal(b, outs[0][1]) and torch.equal(a, outs[1][0])
+    assert st["chunk"] == 16
+    assert float((a - outs[0][0]).abs().max()) <= 2e-5 and float((b - outs[0][1]).abs().max()) <= 2e-5
     s.close()
+
+
+@pytest.mark.parametrize("chunk", [8, 32])
+def test_chunk_sizes_parity(arlib, orc, chunk):
+    """The sweep's other chunk sizes (which the autotuner may pick) keep parity
+    with the oracle and stay within 2e-5 of chunks of 16."""
+    sc = synth.object_scene(2500, 4)
+    cam = synth.look_camera(72, 56, 80.0, centre=(0, 0, -4))
+    lo, hi = synth.cell_grid([0.02, 0.02, 0.02, 0.0087, 0.0087, 0.0087], [1, 2, 1, 1, 1, 2])
+    ref_lo, ref_hi = gpu_render(arlib, sc, cam, lo, hi, tile=16)
+    s = arlib.Scene(sc)
+    out_lo = torch.empty((lo.shape[0], cam.height, cam.width, 3), device="cuda")
+    out_hi = torch.empty_like(out_lo)
+    assert arlib.lib().ar_debug_set_chunk(s.handle, chunk) == 0
+    s.render(cam, lo, hi, out_lo, out_hi, tile=16)
+    st = arlib.ar_last_render_stats(s.handle)
+    torch.cuda.synchronize()
+    assert st["chunk"] == chunk
+    glo, ghi = out_lo.double().cpu().numpy(), out_hi.double().cpu().numpy()
+    s.close()
+    assert np.abs(glo - ref_lo).max() <= 2e-5 and np.abs(ghi - ref_hi).max() <= 2e-5
+    for c in range(lo.shape[0]):
+        compare(orc, sc, cam, lo[c], hi[c], glo[c], ghi[c], label="chunk %d cell %d" % (chunk, c))
