@@ -518,8 +518,17 @@ def serving(ar, args, sp):
             time.sleep(0.0002)
         srv.close()
         span = max(end)
-        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "mean_ms": float(np.mean(lat)), "bounds_per_s": total / span, "makespan_s": span}
+        out = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+               "mean_ms": float(np.mean(lat)), "bounds_per_s": total / span, "makespan_s": span}
+        # latency per request-size class: at most 4 cells (high priority in
+        # the server) and more
+        for name, sel in (("small", [q.cells_lo.shape[0] <= 4 for q in reqs]),
+                          ("large", [q.cells_lo.shape[0] > 4 for q in reqs])):
+            ls = [x for x, k in zip(lat, sel) if k]
+            if ls:
+                out[name] = {"requests": len(ls), "p50_ms": float(np.percentile(ls, 50)),
+                             "p99_ms": float(np.percentile(ls, 99))}
+        return out
 
     one = stream(1)
     many = stream(args.serve_slots)

@@ -49,6 +49,7 @@ extern "C" {
 #define AR_EAGAIN 3    /* serving: request queue full, try again */
 #define AR_ETIMEOUT 4  /* serving: a bounded wait ran out */
 #define AR_EDEVICE 5   /* CUDA error (message from the runtime) */
+#define AR_ECANCELED 6 /* serving: the request was cancelled */
 
 typedef struct ar_intrinsics {
     int32_t width, height;      /* image size in pixels, 1..16384 each */
@@ -427,6 +428,11 @@ int ar_last_render_stats(ar_scene *scene, ar_render_stats *stats);
  * workspace estimate fits the budget next to what the other slots hold, or a
  * later one that fits while leaving room for the oldest (backfilling).
  * Idle slots' workspaces are released when the oldest request does not fit.
+ * Every slot has a high- and a low-priority CUDA stream: requests of at most 4
+ * cells run on the high-priority one, larger ones on the other, and the
+ * slots launch each batch's first per-pixel sweep as one CTA per (cell, tile)
+ * segment, so that a small request's work is scheduled on the SMs a large
+ * request's CTAs free as they finish, instead of after the large request.
  * Results are bit-identical to ar_render_abstract of the same request. */
 
 /* hbm_budget_bytes: workspace budget (>= 1 MiB) shared by the slots, beside
@@ -449,6 +455,23 @@ int ar_serve_destroy(ar_server *server);
 int ar_serve_submit(ar_server *server, ar_scene *scene, const ar_intrinsics *intr,
                     const ar_nominal_pose *pose, const ar_pose_box *cells, int32_t n_cells,
                     float *out_lower, float *out_upper, uint64_t *ticket);
+
+/* Timeout of the server's requests in ms, measured from submission (0: none,
+ * the default).  A request still queued when it expires is completed with
+ * AR_ETIMEOUT without running.  A running one whose GPU work has not finished
+ * when it expires (a host watchdog polls the slot's stream) is completed with
+ * AR_ETIMEOUT at once; its outputs are then undefined, and the slot waits for
+ * that work to drain before it admits another request.  Applies to requests
+ * admitted or polled after the call.  AR_EINVAL for a null server or a
+ * negative or NaN timeout. */
+int ar_serve_set_timeout(ar_server *server, double timeout_ms);
+
+/* Cancel a ticket.  A queued request leaves the queue at once and completes
+ * with AR_ECANCELED (its outputs untouched); a running one completes with
+ * AR_ECANCELED when its GPU work ends (its outputs may have been written); a
+ * completed one keeps its status.  The ticket is retired by ar_serve_poll as
+ * usual.  AR_EINVAL for a null server or an unknown or retired ticket. */
+int ar_serve_cancel(ar_server *server, uint64_t ticket);
 
 /* Poll a ticket: *done = 1 once its outputs are complete; then *latency_ms is
  * the submit-to-completion wall time, the ticket is retired, and the return

@@ -13,7 +13,7 @@ import numpy as np
 
 from . import _build
 
-AR_OK, AR_EINVAL, AR_ENOMEM, AR_EAGAIN, AR_ETIMEOUT, AR_EDEVICE = range(6)
+AR_OK, AR_EINVAL, AR_ENOMEM, AR_EAGAIN, AR_ETIMEOUT, AR_EDEVICE, AR_ECANCELED = range(7)
 
 c_int32, c_int64, c_float, c_double, c_void_p = (ctypes.c_int32, ctypes.c_int64, ctypes.c_float,
                                                  ctypes.c_double, ctypes.c_void_p)
@@ -91,6 +91,8 @@ def lib():
             "ar_serve_destroy": ([P], ctypes.c_int),
             "ar_serve_submit": ([P, P, P, P, P, c_int32, P, P, P], ctypes.c_int),
             "ar_serve_poll": ([P, ctypes.c_uint64, P, P], ctypes.c_int),
+            "ar_serve_set_timeout": ([P, c_double], ctypes.c_int),
+            "ar_serve_cancel": ([P, ctypes.c_uint64], ctypes.c_int),
             "ar_last_error": ([], ctypes.c_char_p),
         }
         for name, (args, res) in sig.items():
@@ -316,6 +318,14 @@ def ar_serve_poll(server, ticket: int):
     return bool(done.value), float(lat.value)
 
 
+def ar_serve_set_timeout(server, timeout_ms: float):
+    return check(lib().ar_serve_set_timeout(server, float(timeout_ms)))
+
+
+def ar_serve_cancel(server, ticket: int):
+    return check(lib().ar_serve_cancel(server, ctypes.c_uint64(ticket)))
+
+
 # ------------------------------------------------------------ conveniences
 
 class Scene:
@@ -391,6 +401,12 @@ class Server:
 
     def poll(self, ticket: int):
         return ar_serve_poll(self.handle, ticket)
+
+    def set_timeout(self, timeout_ms: float):
+        return ar_serve_set_timeout(self.handle, timeout_ms)
+
+    def cancel(self, ticket: int):
+        return ar_serve_cancel(self.handle, ticket)
 
     def close(self):
         if self.handle is not None:

@@ -668,7 +668,7 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
         const uint64_t head[] = {(uint64_t)M, (uint64_t)TS, (uint64_t)CH, (uint64_t)n_cells, n_pairs, ne, nent, (uint64_t)n_tiles,
                                  (uint64_t)ntx, (uint64_t)W, (uint64_t)H, (uint64_t)s->n, ws.w0,
                                  (uint64_t)s->blend, (uint64_t)float_bits(s->fp64_dev), (uint64_t)float_bits(s->k_open),
-                                 (uint64_t)profiling, (uint64_t)batch, (uint64_t)(uintptr_t)out_lo,
+                                 (uint64_t)profiling, (uint64_t)ws.interleave, (uint64_t)batch, (uint64_t)(uintptr_t)out_lo,
                                  (uint64_t)(uintptr_t)out_hi, (uint64_t)(uintptr_t)d_lo};
         key.assign(head, head + sizeof head / sizeof head[0]);
         ws.append_pointers(key);
@@ -765,6 +765,7 @@ static int enqueue_rest(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
     rl.rel = s->blend == AR_BLEND_RELATIONAL;
     rl.fp64_dev = s->fp64_dev;
     rl.ch = CH;
+    rl.interleave = ws.interleave ? 1 : 0;
     rl.out_lo = out_lo;
     rl.out_hi = out_hi;
     rl.counters = ws.counters.as<unsigned long long>() + 8 + kCountersPerBatch * batch;
@@ -841,6 +842,7 @@ int run_windowed_render(int M, int TS, RenderLaunch rl, const CallConst &cc, con
         rl.precise_mask = precise_mask;
         CK(cudaMemsetAsync(words + 5, 0, sizeof(uint32_t), st));
         rl.f64 = 0;
+        rl.direct = rl.interleave && r == 0;
         if (launch_render(M, TS, rl, st))
             return fail(AR_EDEVICE, "render launch: %s", cudaGetErrorString(cudaGetLastError()));
         // the segments where some pixel met an evaluation needing FP64, swept
@@ -850,6 +852,7 @@ int run_windowed_render(int M, int TS, RenderLaunch rl, const CallConst &cc, con
         rp.active = precise_list;
         rp.n_active = words + 5;
         rp.f64 = 1;
+        rp.direct = 0;
         if (launch_render(M, TS, rp, st))
             return fail(AR_EDEVICE, "render launch: %s", cudaGetErrorString(cudaGetLastError()));
         if (ev) CK(record_stage(ev[2 * r + 1], st));

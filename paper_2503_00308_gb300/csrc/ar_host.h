@@ -56,6 +56,7 @@ struct Workspace {
     std::vector<GraphEntry> graphs;            // captured batch phases (see render_batch)
     uint64_t graph_clock = 0, graph_hits = 0;
     cudaStream_t cap_stream = nullptr;         // private stream the captures are taken on
+    bool interleave = false;                   // server slots: the first sweep in one CTA per segment
     void release();
     size_t bytes() const;
     void append_pointers(std::vector<uint64_t> &key) const;  // every buffer's address, for graph keys

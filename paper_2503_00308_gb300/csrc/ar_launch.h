@@ -33,6 +33,10 @@ struct RenderLaunch {
     unsigned int *work;               // segment counter of the persistent grid (zeroed by the launcher)
     int rel = 0;                      // 1: relational upper transmittance (AR_BLEND_RELATIONAL)
     int ch = 16;                      // events per staged chunk of the FP32 sweep (8, 16 or 32 at tile 16)
+    // interleave: the first round's FP32 sweep (whose active list is all n_seg
+    // segments) launches one CTA per segment (direct) instead of persistent
+    // CTAs, so that work on a higher-priority stream can take SMs as they free
+    int interleave = 0, direct = 0;
     // precision: the FP32 sweep (f64 = 0) appends a segment that needs an FP64
     // evaluation to precise[*n_precise], with the mask of the pixels that do in
     // precise_mask[slot * TS * TS / 32 ...]; the f64 = 1 instance sweeps them

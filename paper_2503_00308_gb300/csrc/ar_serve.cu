@@ -15,6 +15,21 @@
 // its cell batches (records are about a third of it; the batch size follows
 // from the per-request limit), capped at the budget.  When a request does not
 // fit and idle slots keep large workspaces, those are released first.
+//
+// Overlap on the device: every slot has a high- and a low-priority stream.  A
+// request of at most kSmallCells cells runs on the high-priority one, a larger
+// one on the low-priority one, and the slots' workspaces launch the first
+// per-pixel sweep of a batch as one CTA per segment (Workspace::interleave),
+// so that a large request's CTAs finish one by one and the blocks of a small
+// request that arrives meanwhile are scheduled as SMs free up, instead of
+// waiting for the large request's persistent sweep to end.
+//
+// Timeouts and cancellation: with a timeout set, a request still queued when
+// it expires is completed with AR_ETIMEOUT without running, and one whose GPU
+// work has not finished by then (a host watchdog polls its stream) is
+// completed with AR_ETIMEOUT while the slot waits for that work to drain
+// before it admits another request.  A cancelled request leaves the queue at
+// once; a running one is completed with AR_ECANCELED when its work ends.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -45,18 +60,21 @@ struct ServeRequest {
     int64_t limit = 0;   // workspace limit the request renders under
     Clock::time_point t_submit, t_done;
     bool done = false;
+    bool cancel = false;  // cancelled while running: completed as AR_ECANCELED
     int status = AR_OK;
     std::string error;
 };
 
 struct ServeSlot {
     std::thread worker;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;       // low priority: large requests
+    cudaStream_t stream_hi = nullptr;    // high priority: small requests
     Workspace ws;
     ServeRequest *running = nullptr;
 };
 
 constexpr size_t kQueueCap = 1024;
+constexpr size_t kSmallCells = 4;  // requests of at most this many cells run at high priority
 
 // Workspace estimate of one request: the records, keys and boxes of one cell
 // batch times three (bins and sort buffers take about two thirds), capped by
@@ -93,6 +111,7 @@ struct ar_server {
     std::unordered_map<uint64_t, ServeRequest *> tickets;
     uint64_t next_ticket = 1;
     bool stop = false;
+    double timeout_ms = 0.0;  // 0: none
 };
 
 namespace ar {
@@ -104,9 +123,30 @@ static int64_t held_by(const ServeSlot &sl)
     return h;
 }
 
+static double ms_since(Clock::time_point t) { return std::chrono::duration<double, std::milli>(Clock::now() - t).count(); }
+
+// Under the lock: complete the queued requests whose timeout has passed.
+static void expire_queued(ar_server *sv)
+{
+    if (!(sv->timeout_ms > 0.0)) return;
+    for (auto it = sv->pending.begin(); it != sv->pending.end();) {
+        ServeRequest *r = *it;
+        if (ms_since(r->t_submit) > sv->timeout_ms) {
+            r->t_done = Clock::now();
+            r->status = AR_ETIMEOUT;
+            r->error = "request timed out in the queue";
+            r->done = true;
+            it = sv->pending.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
 // Under the lock: pick the request slot k admits next, or null.
 static ServeRequest *pick(ar_server *sv, int k)
 {
+    expire_queued(sv);
     if (sv->pending.empty()) return nullptr;
     int64_t others = 0;
     for (int j = 0; j < (int)sv->slots.size(); ++j)
@@ -128,6 +168,7 @@ static ServeRequest *pick(ar_server *sv, int k)
         ServeSlot &o = sv->slots[j];
         if (!o.running && o.ws.bytes() > 0) {
             cudaStreamSynchronize(o.stream);
+            cudaStreamSynchronize(o.stream_hi);
             o.ws.release();
             trimmed = true;
         }
@@ -153,30 +194,61 @@ static ServeRequest *pick(ar_server *sv, int k)
     return nullptr;
 }
 
+static void complete(ar_server *sv, ServeRequest *r, int code, const std::string &err)
+{
+    r->t_done = Clock::now();
+    r->status = r->cancel ? AR_ECANCELED : code;
+    r->error = r->cancel ? std::string("request cancelled") : err;
+    r->done = true;
+}
+
 static void worker_main(ar_server *sv, int k)
 {
     cudaSetDevice(sv->device);
     ServeSlot &sl = sv->slots[k];
+    sl.ws.interleave = true;
     std::unique_lock<std::mutex> lock(sv->mu);
     for (;;) {
         ServeRequest *r = nullptr;
-        sv->cv.wait(lock, [&] { return sv->stop || (r = pick(sv, k)) != nullptr; });
+        // wake now and then to expire queued requests under a timeout
+        while (!sv->stop && (r = pick(sv, k)) == nullptr) sv->cv.wait_for(lock, std::chrono::milliseconds(5));
         if (!r) break;  // stopping and nothing admitted
         sl.running = r;
+        const double timeout = sv->timeout_ms;
         lock.unlock();
-        ar_render_stats st;
+        cudaStream_t st = r->cells.size() <= kSmallCells ? sl.stream_hi : sl.stream;
+        ar_render_stats stats;
         int code = render_core(r->scene, sl.ws, &r->intr, &r->pose, r->cells.data(), (int32_t)r->cells.size(), 0,
-                               r->out_lo, r->out_hi, sl.stream, false, &st, false, r->limit);
+                               r->out_lo, r->out_hi, st, false, &stats, false, r->limit);
         std::string err = code ? ar_last_error() : std::string();
-        if (cudaStreamSynchronize(sl.stream) != cudaSuccess && code == AR_OK) {
-            code = AR_EDEVICE;
-            err = cudaGetErrorString(cudaGetLastError());
+        // watchdog: poll the stream until its work is done or the timeout passes
+        bool timed_out = false;
+        for (;;) {
+            const cudaError_t q = cudaStreamQuery(st);
+            if (q == cudaSuccess) break;
+            if (q != cudaErrorNotReady) {
+                if (code == AR_OK) {
+                    code = AR_EDEVICE;
+                    err = cudaGetErrorString(q);
+                }
+                cudaGetLastError();
+                break;
+            }
+            if (!timed_out && timeout > 0.0 && ms_since(r->t_submit) > timeout) {
+                // report the timeout now; the slot keeps waiting for its work
+                timed_out = true;
+                lock.lock();
+                complete(sv, r, AR_ETIMEOUT, "request did not finish within the server's timeout");
+                lock.unlock();
+            }
+            std::this_thread::sleep_for(std::chrono::microseconds(100));
+        }
+        if (!timed_out && code == AR_OK && timeout > 0.0 && ms_since(r->t_submit) > timeout) {
+            code = AR_ETIMEOUT;
+            err = "request did not finish within the server's timeout";
         }
         lock.lock();
-        r->t_done = Clock::now();
-        r->status = code;
-        r->error = err;
-        r->done = true;
+        if (!timed_out) complete(sv, r, code, err);
         sl.running = nullptr;
         sv->cv.notify_all();  // memory freed: other slots may admit now
     }
@@ -196,11 +268,16 @@ int ar_serve_create(int64_t hbm_budget_bytes, int32_t n_slots, ar_server **out)
     cudaGetDevice(&sv->device);
     sv->budget = hbm_budget_bytes;
     sv->slots.resize(n_slots);
+    int prio_lo = 0, prio_hi = 0;  // numerically lower is higher priority
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     for (auto &sl : sv->slots) {
-        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess) {
+        if (cudaStreamCreateWithPriority(&sl.stream, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&sl.stream_hi, cudaStreamNonBlocking, prio_hi) != cudaSuccess) {
             cudaGetLastError();
-            for (auto &o : sv->slots)
+            for (auto &o : sv->slots) {
                 if (o.stream) cudaStreamDestroy(o.stream);
+                if (o.stream_hi) cudaStreamDestroy(o.stream_hi);
+            }
             delete sv;
             return serve_fail(AR_EDEVICE, "stream creation failed");
         }
@@ -229,8 +306,10 @@ int ar_serve_destroy(ar_server *sv)
     cudaSetDevice(sv->device);
     for (auto &sl : sv->slots) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);
+        if (sl.stream_hi) cudaStreamSynchronize(sl.stream_hi);
         sl.ws.release();
         if (sl.stream) cudaStreamDestroy(sl.stream);
+        if (sl.stream_hi) cudaStreamDestroy(sl.stream_hi);
     }
     for (auto &kv : sv->tickets) delete kv.second;
     delete sv;
@@ -274,10 +353,39 @@ int ar_serve_submit(ar_server *sv, ar_scene *scene, const ar_intrinsics *intr, c
     return AR_OK;
 }
 
+int ar_serve_set_timeout(ar_server *sv, double timeout_ms)
+{
+    if (!sv) return serve_fail(AR_EINVAL, "server is null");
+    if (!(timeout_ms >= 0.0)) return serve_fail(AR_EINVAL, "timeout must be >= 0 (0: none)");
+    std::lock_guard<std::mutex> lock(sv->mu);
+    sv->timeout_ms = timeout_ms;
+    return AR_OK;
+}
+
+int ar_serve_cancel(ar_server *sv, uint64_t ticket)
+{
+    if (!sv) return serve_fail(AR_EINVAL, "server is null");
+    std::lock_guard<std::mutex> lock(sv->mu);
+    auto it = sv->tickets.find(ticket);
+    if (it == sv->tickets.end()) return serve_fail(AR_EINVAL, "unknown or retired ticket");
+    ServeRequest *q = it->second;
+    if (q->done) return AR_OK;
+    for (auto p = sv->pending.begin(); p != sv->pending.end(); ++p)
+        if (*p == q) {
+            sv->pending.erase(p);
+            q->cancel = true;
+            complete(sv, q, AR_ECANCELED, "");
+            return AR_OK;
+        }
+    q->cancel = true;  // running: completed as cancelled when its work ends
+    return AR_OK;
+}
+
 int ar_serve_poll(ar_server *sv, uint64_t ticket, int *done, double *latency_ms)
 {
     if (!sv || !done) return serve_fail(AR_EINVAL, "null argument");
     std::lock_guard<std::mutex> lock(sv->mu);
+    expire_queued(sv);
     auto it = sv->tickets.find(ticket);
     if (it == sv->tickets.end()) return serve_fail(AR_EINVAL, "unknown or retired ticket");
     ServeRequest *q = it->second;

@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
     const uint32_t *__restrict__ entry_ev, const uint32_t *__restrict__ ev_val,
     const uint64_t *__restrict__ ev_key, int W, int H, int ntx, int n_tiles, int64_t n_gauss,
     float k_open, float fp64_dev, float *__restrict__ out_lo, float *__restrict__ out_hi,
-    unsigned long long *__restrict__ counters, unsigned int *__restrict__ work)
+    unsigned long long *__restrict__ counters, unsigned int *__restrict__ work, int direct)
 {
     using RL = Rec<M>;
     using SM = RenderSmem<M, TS, CH, RING>;
@@ -492,8 +492,11 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
     uint32_t evals = 0, recomp = 0, wide = 0;
     const uint32_t n_seg = *n_active;
 
-    for (;;) {
-        if (tid == 0) *s_next = atomicAdd(work, 1u);
+    // direct: one CTA per active segment (the grid covers them all), so that
+    // CTAs finish one by one and a higher-priority stream's work can take
+    // their SMs; else persistent CTAs take segments from the work counter
+    for (uint32_t round = 0;; ++round) {
+        if (tid == 0) *s_next = direct ? (round == 0 ? blockIdx.x : 0xffffffffu) : atomicAdd(work, 1u);
         __syncthreads();
         const uint32_t wk = *s_next;
         __syncthreads();

@@ -128,3 +128,84 @@ def test_serve_arguments(arlib):
         srv.poll(t)   # retired
     srv.close()
     sc.close()
+
+
+def _wait(srv, t, limit_s=60):
+    t_end = time.time() + limit_s
+    while True:
+        done, ms = srv.poll(t)
+        if done:
+            return ms
+        assert time.time() < t_end, "request did not complete"
+        time.sleep(0.001)
+
+
+def test_cancel_queued_and_running(arlib):
+    """One slot busy with a long request: a request cancelled while queued
+    completes with AR_ECANCELED and its outputs are untouched; the long one,
+    cancelled while running, completes with AR_ECANCELED too; the server then
+    serves a new request normally."""
+    ar = arlib
+    big = ar.Scene(synth.object_scene(100_000, 4))
+    cam = synth.look_camera(400, 400, 440.0, centre=(0, 0, -4))
+    lo, hi = synth.cell_grid([0.02, 0.02, 0.02, 0.0087, 0.0087, 0.0087], [2, 2, 2, 1, 1, 2])   # 16 cells
+    w = synth.tiny64()
+    small = ar.Scene(w.scene)
+    srv = ar.Server(8 << 30, 1)
+    a, b = alloc(cam, lo.shape[0])
+    t_big = srv.submit(big, cam, lo, hi, a, b)
+    sa, sb = alloc(w.camera, 1)
+    t_small = srv.submit(small, w.camera, w.cells_lo, w.cells_hi, sa, sb)
+    srv.cancel(t_small)
+    srv.cancel(t_big)
+    for t in (t_small, t_big):
+        with pytest.raises(ar.ArError) as e:
+            _wait(srv, t)
+        assert e.value.code == ar.AR_ECANCELED
+    torch.cuda.synchronize()
+    assert torch.all(sa == -3.0) and torch.all(sb == -3.0)
+    ca, cb = alloc(w.camera, 1)
+    t = srv.submit(small, w.camera, w.cells_lo, w.cells_hi, ca, cb)
+    assert _wait(srv, t) >= 0
+    ref_a, ref_b = alloc(w.camera, 1)
+    small.render(w.camera, w.cells_lo, w.cells_hi, ref_a, ref_b)
+    torch.cuda.synchronize()
+    assert torch.equal(ca, ref_a) and torch.equal(cb, ref_b)
+    with pytest.raises(ar.ArError):
+        srv.cancel(t)            # retired by the poll
+    srv.close()
+    big.close()
+    small.close()
+
+
+def test_timeout(arlib):
+    """With a timeout shorter than any request, every request completes with
+    AR_ETIMEOUT (in the queue or by the watchdog); with the timeout off again
+    the server serves requests normally."""
+    ar = arlib
+    scenes, reqs = requests()
+    handles = [ar.Scene(s) for s in scenes]
+    srv = ar.Server(4 << 30, 2)
+    srv.set_timeout(1e-3)
+    tickets = []
+    for si, cam, lo, hi in reqs[:6]:
+        a, b = alloc(cam, lo.shape[0])
+        tickets.append((srv.submit(handles[si], cam, lo, hi, a, b), a, b))
+    for t, _, _ in tickets:
+        with pytest.raises(ar.ArError) as e:
+            _wait(srv, t)
+        assert e.value.code == ar.AR_ETIMEOUT
+    srv.set_timeout(0.0)
+    si, cam, lo, hi = reqs[0]
+    a, b = alloc(cam, lo.shape[0])
+    t = srv.submit(handles[si], cam, lo, hi, a, b)
+    assert _wait(srv, t) >= 0
+    ra, rb = alloc(cam, lo.shape[0])
+    handles[si].render(cam, lo, hi, ra, rb)
+    torch.cuda.synchronize()
+    assert torch.equal(a, ra) and torch.equal(b, rb)
+    with pytest.raises(ar.ArError):
+        srv.set_timeout(-1.0)
+    with pytest.raises(ar.ArError):
+        srv.cancel(987654)
+    srv.close()
