@@ -31,14 +31,24 @@ UNIT = "pixel-cells/s"
 SMS, FP32_LANES, MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_MHZ * 1e6 / 1e12   # FMA = 2 flops
 
-# FP32 operations of the per-(pixel, Gaussian, cell) relaxation, counted once
-# per triple inside a screen box (FMA = 2 flops; an IEEE divide or expf = 10):
-# Delta (2 forms), q (3 x two averaged-McCormick products), m (3 squares),
-# the Exp/cutoff/clip stage and both colour accumulations, including the
-# rounding-error terms that keep FP32 bounds sound.  With M pose variables
-# this is 49 M + 132 FMAs and 15 M + 340 other operations: 113 M + 604 flops.
+# FP32 operations of the relaxation itself per evaluated (pixel, Gaussian,
+# cell) triple, with M pose variables (an FMA = 2 flops, any other FP32
+# operation = 1, expf = 2: a multiply and the SFU exponential):
+#   Delta_x, Delta_y = (u - mu) S + R          4 M + 8
+#   concretising Delta_x, Delta_y, q0..q2, m   6 M + 12   (k -+ sum |c|)
+#   q_c: 6 averaged-McCormick products        24 M + 132
+#   m = sum q_c^2: 3 tangent/secant squares    6 M + 45
+#   Exp (Table 2), opacity, clip and cutoff    6 M + 60
+#   both colour sums (lower and upper endpoint) and the transmittances
+#                                             12 M + 26
+# = 58 M + 283 (631 at M = 6).  The rounding-error bookkeeping that keeps the
+# FP32 bounds sound (the gamma_n sum |a| r terms, midpoint slacks, widened
+# exps, the colour sums' error bounds) is about 156 more and is not counted.
 def flops_per_triple(M: int) -> int:
-    return 113 * M + 604
+    return 58 * M + 283
+
+
+BOOKKEEPING_FLOPS_PER_TRIPLE = 156
 
 
 # DRAM bytes of the render kernel per opacity evaluation, from an ncu capture
@@ -640,7 +650,12 @@ def run_ours(args, rank, world, local, pg):
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": render_traffic(stats["n_evaluated"]),
                      "traffic_unit": "DRAM bytes per render step (all render_kernel launches of the step)",
                      "kernel": "render_kernel", "kernel_ms": r_ms,
-                     "flops_per_triple": flops_per_triple(M), "triples_evaluated": stats["n_evaluated"],
+                     "flops_per_triple": flops_per_triple(M),
+                     "flops_note": "the relaxation's own FP32 arithmetic (FMA = 2, other ops = 1, expf = 2); "
+                                   "%d more of rounding-error bookkeeping per triple not counted; kernel_ms "
+                                   "is both render instances (FP32 sweep and FP64 re-sweep)"
+                                   % BOOKKEEPING_FLOPS_PER_TRIPLE,
+                     "triples_evaluated": stats["n_evaluated"],
                      "triples_in_boxes": stats["n_triples"],
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal: MEASURED_PEAKS.json has no FP32 figure)",
                      "fp32_fma_probe_tflops": fma_probe(sp)},
