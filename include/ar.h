@@ -344,6 +344,16 @@ int ar_debug_set_chunk(ar_scene *scene, int32_t chunk);
  * a null scene or a cap outside [0, 2^32 - 2^20]. */
 int ar_debug_set_entry_cap(ar_scene *scene, int64_t cap);
 
+/* Test hook: the depth prefix of the binning's first phase for the scene's
+ * renders.  Each (cell, tile) list first holds only the entries of the cell's
+ * first ceil(E / 2^shift) depth-sorted endpoint events (E: the cell's
+ * events); a segment whose sweep needs more is binned again with its full
+ * list before the second windowed round.  shift = 0 bins every list in full
+ * in one phase, shift = -1 (the default) learns the shift per workspace from
+ * where the previous render's segments stopped.  The bounds do not depend on
+ * it.  AR_EINVAL for a null scene or a shift outside [-1, 8]. */
+int ar_debug_set_prefix(ar_scene *scene, int32_t shift);
+
 /* Device-memory limit (bytes, >= 1 MiB) for the scene's render workspace.
  * ar_render_abstract splits the cells of a call into batches whose
  * per-(Gaussian, cell) records take about a third of this limit, and runs the

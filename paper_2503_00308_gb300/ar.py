@@ -80,6 +80,7 @@ def lib():
             "ar_scene_set_graphs": ([P, ctypes.c_int32], ctypes.c_int),
             "ar_debug_set_chunk": ([P, ctypes.c_int32], ctypes.c_int),
             "ar_debug_set_entry_cap": ([P, c_int64], ctypes.c_int),
+            "ar_debug_set_prefix": ([P, c_int32], ctypes.c_int),
             "ar_bounds_union": ([P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P], ctypes.c_int),
             "ar_partition_piece": ([P, P, c_int64, P], ctypes.c_int),
             "ar_render_abstract_refined": ([P, P, P, P, ctypes.c_int32, ctypes.c_int32, P, P, P, ctypes.c_int32, P, P],
@@ -281,6 +282,10 @@ def ar_debug_set_chunk(scene, chunk: int):
 
 def ar_debug_set_entry_cap(scene, cap: int):
     return check(lib().ar_debug_set_entry_cap(scene, int(cap)))
+
+
+def ar_debug_set_prefix(scene, shift: int):
+    return check(lib().ar_debug_set_prefix(scene, int(shift)))
 
 
 def ar_last_render_stats(scene) -> dict:

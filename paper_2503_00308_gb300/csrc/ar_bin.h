@@ -26,6 +26,16 @@ struct BinArgs {
     uint32_t *scan_tmp;      // >= scan_temp_words(largest scanned length)
     uint32_t *seg_start, *seg_end;  // [n_segments]
     uint32_t *seg_k[2], *seg_v[2];  // [n_segments] x2 each: segment order by length
+    // Two-phase binning (prefix_shift > 0): the first phase bins only each
+    // cell's first ceil(E / 2^prefix_shift) depth-sorted events (E: the
+    // cell's events), and seg_total receives the lengths of the full lists;
+    // run_rebin bins the full lists of the segments that need them.
+    int prefix_shift = 0;
+    uint32_t *cell_ev = nullptr;    // [n_cells + 1] first sorted event of each cell
+    uint32_t *seg_total = nullptr;  // [n_segments]
+    uint32_t *words = nullptr;      // [2] entry counts known on the device only
+    uint32_t *mask = nullptr;       // [(n_segments + 31) / 32] active segments of the second phase
+    uint32_t *sat = nullptr;        // [n_cells][(nty + 1) (ntx + 1)] their summed-area tables
 };
 
 struct BinOut {
@@ -34,12 +44,19 @@ struct BinOut {
     const uint32_t *ent_seg; // entries sorted by segment
     const uint32_t *ent_ev;  // entry -> sorted event index
     const uint32_t *seg_order;  // segments, longest first
+    const uint32_t *seg_total;  // full-list lengths, or null: the lists are complete (seg_end - seg_start)
 };
 
 size_t scan_temp_words(uint64_t n);
 size_t radix_hist_words(uint64_t n);
 void exclusive_scan(const uint32_t *in, uint32_t *out, uint64_t n, uint32_t *tmp, cudaStream_t st, int *launches);
 int run_binning(const BinArgs &a, BinOut &o, cudaStream_t st, int *launches);
+// The second phase: complete lists for the segments active[0, *n_active)
+// (a device count), sorted as run_binning sorts them, in place of the first
+// phase's lists (the other segments' bounds become empty); o.seg_order lists
+// the active segments again, longest first.
+int run_rebin(const BinArgs &a, const BinOut &first, const uint32_t *active, const uint32_t *n_active, BinOut &o,
+              cudaStream_t st, int *launches);
 
 // Windowed rounds of the renderer.  launch_demand claims (state 0 -> 1) the
 // pairs whose lower endpoints lie in the first `window` entries of the

@@ -42,7 +42,10 @@ struct NvtxRange {
 };
 // stage events of one cell batch: start, after prep, after binning, then per
 // windowed round: after the record build, after the render
-constexpr int kEventsPerBatch = 9;
+constexpr int kEventsPerBatch = 10;
+// the renderer's histograms: 256 sweep lengths, then 64 64-bit stop depths
+// weighted by full-list length, then 64 stop depths by segment count
+constexpr int kHistWords = 256 + 2 * 64 + 64;
 // device counters of one cell batch: opacity evaluations, re-evaluations,
 // MatrixInv fallbacks and records built (record build), MatrixInv input
 // splits (record build), segments restarted (render), evaluations taken
@@ -225,7 +228,7 @@ void DevBuf::release()
 void Workspace::append_pointers(std::vector<uint64_t> &key) const
 {
     const DevBuf *all[] = {&cells_lohi, &cells, &vN, &recs, &boxes, &keys, &counters, &evk0, &evk1, &evv0, &evv1,
-                           &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege,
+                           &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege, &segt, &cellev, &bwords, &smask, &ssat,
                            &segk0, &segk1, &segv0, &segv1, &work, &state, &wlist, &act0, &act1, &words,
                            &slist, &plist, &pmask, &whist};
     for (const DevBuf *b : all) key.push_back((uint64_t)(uintptr_t)b->p);
@@ -238,7 +241,7 @@ void Workspace::release()
     if (cap_stream) cudaStreamDestroy(cap_stream);
     cap_stream = nullptr;
     DevBuf *all[] = {&cells_lohi, &cells, &vN, &recs, &boxes, &keys, &counters, &evk0, &evk1, &evv0, &evv1,
-                     &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege, &segk0,
+                     &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege, &segt, &cellev, &bwords, &smask, &ssat, &segk0,
                      &segk1, &segv0, &segv1, &work, &state, &wlist, &act0, &act1, &words, &slist, &plist, &pmask, &whist, &out_lo,
                      &out_hi, &part_lo, &part_hi, &lvl_lo, &lvl_hi, &wpart};
     for (DevBuf *b : all) b->release();
@@ -254,7 +257,7 @@ void Workspace::release()
 size_t Workspace::bytes() const
 {
     const DevBuf *all[] = {&cells_lohi, &cells, &vN, &recs, &boxes, &keys, &counters, &evk0, &evk1, &evv0, &evv1,
-                           &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege,
+                           &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege, &segt, &cellev, &bwords, &smask, &ssat,
                            &segk0, &segk1, &segv0, &segv1, &work, &state, &wlist, &act0, &act1, &words,
                            &slist, &plist, &pmask, &whist, &out_lo, &out_hi, &part_lo, &part_hi, &lvl_lo, &lvl_hi, &wpart};
     size_t s = 0;
@@ -441,6 +444,14 @@ int ar_scene_set_blend(ar_scene *s, int32_t mode)
     return AR_OK;
 }
 
+int ar_debug_set_prefix(ar_scene *s, int32_t shift)
+{
+    if (!s) return fail(AR_EINVAL, "scene is null");
+    if (shift < -1 || shift > 8) return fail(AR_EINVAL, "shift must be -1 or in [0, 8]");
+    s->prefix_force = shift;
+    return AR_OK;
+}
+
 int ar_debug_set_entry_cap(ar_scene *s, int64_t cap)
 {
     if (!s) return fail(AR_EINVAL, "scene is null");
@@ -511,9 +522,12 @@ int validate_call(const ar_intrinsics *in, const ar_nominal_pose *pose, const ar
 
 // Sizes the binning buffers of the workspace and (run) runs the binning of
 // n_pairs (cell, Gaussian) pairs with ne events and nent (event, tile) entries.
+// shift > 0: the first phase of a two-phase binning (BinArgs), whose
+// arguments ba_out receives for the second; the renderer's own binning
+// (cell_ev) also passes a non-null ba_out with shift 0.
 static int bin_pairs(Workspace &ws, const PixBox *boxes, const double *keys, uint64_t n_pairs, uint64_t n_gauss,
                      int n_cells, uint64_t ne, uint64_t nent, int TS, int ntx, int n_tiles, cudaStream_t st,
-                     BinOut &bo, int &launches, bool run = true)
+                     BinOut &bo, int &launches, bool run = true, int shift = 0, BinArgs *ba_out = nullptr)
 {
     const uint64_t n_seg = (uint64_t)n_cells * n_tiles;
     const uint64_t nsc = n_pairs > ne ? n_pairs : ne;
@@ -541,6 +555,15 @@ static int bin_pairs(Workspace &ws, const PixBox *boxes, const double *keys, uin
     RK(ws.segv0.ensure(sizeof(uint32_t) * n_seg));
     RK(ws.segv1.ensure(sizeof(uint32_t) * n_seg));
     RK(ws.work.ensure(256));
+    if (ba_out) {
+        RK(ws.cellev.ensure(sizeof(uint32_t) * (n_cells + 1)));
+        RK(ws.bwords.ensure(sizeof(uint32_t) * 4));
+    }
+    if (shift > 0) {
+        RK(ws.segt.ensure(sizeof(uint32_t) * n_seg));
+        RK(ws.smask.ensure(sizeof(uint32_t) * ((n_seg + 31) / 32 + 1)));
+        RK(ws.ssat.ensure(sizeof(uint32_t) * (uint64_t)n_cells * (ntx + 1) * (n_tiles / ntx + 1)));
+    }
     if (!run) return AR_OK;
     BinArgs ba;
     ba.boxes = boxes;
@@ -564,6 +587,17 @@ static int bin_pairs(Workspace &ws, const PixBox *boxes, const double *keys, uin
     ba.seg_end = ws.sege.as<uint32_t>();
     ba.seg_k[0] = ws.segk0.as<uint32_t>(); ba.seg_k[1] = ws.segk1.as<uint32_t>();
     ba.seg_v[0] = ws.segv0.as<uint32_t>(); ba.seg_v[1] = ws.segv1.as<uint32_t>();
+    if (ba_out) {
+        ba.cell_ev = ws.cellev.as<uint32_t>();
+        ba.words = ws.bwords.as<uint32_t>();
+    }
+    if (shift > 0) {
+        ba.prefix_shift = shift;
+        ba.seg_total = ws.segt.as<uint32_t>();
+        ba.mask = ws.smask.as<uint32_t>();
+        ba.sat = ws.ssat.as<uint32_t>();
+    }
+    if (ba_out) *ba_out = ba;
     if (run_binning(ba, bo, st, &launches))
         return fail(AR_EDEVICE, "binning: %s", cudaGetErrorString(cudaGetLastError()));
     return AR_OK;
@@ -595,7 +629,7 @@ static cudaError_t record_stage(cudaEvent_t e, cudaStream_t q)
 
 static int enqueue_rest(ar_scene *s, Workspace &ws, const CallConst &cc, int M, int TS, int CH, float *out_lo, float *out_hi,
                         cudaStream_t q, bool profiling, int batch, cudaEvent_t *ev, uint64_t n_pairs, uint64_t n_seg,
-                        uint64_t ne, uint64_t nent, int ntx, int n_tiles, bool plain, int &launches);
+                        uint64_t ne, uint64_t nent, int ntx, int n_tiles, bool plain, int shift, int &launches);
 
 // One batch of cells through the whole pipeline.  cc describes the batch
 // (n_cells = cells in the batch, slots shared by every batch of the call).
@@ -631,13 +665,17 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
     CK(cudaMemcpyAsync(ws.h_counters, ws.counters.p, sizeof(unsigned long long) * 5, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     prep_range.end();
-    if (ws.whist_pending) {
-        // the previous render's histogram arrived with this synchronisation
-        ws.w0 = learned_window(ws.h_whist);
-        ws.whist_pending = false;
-    }
     const unsigned long long n_valid = ws.h_counters[2];
     const uint64_t ne = 2 * n_valid, nent = 2 * ws.h_counters[3];
+    if (ws.whist_pending) {
+        // the previous render's histograms arrived with this synchronisation
+        ws.w0 = learned_window(ws.h_whist);
+        ws.prefix_shift = learned_prefix_shift(reinterpret_cast<const unsigned long long *>(ws.h_whist + 256),
+                                               ws.h_whist + 384, nent, ne);
+        ws.whist_pending = false;
+    }
+    // the depth prefix of the first binning phase (0: one phase)
+    const int shift = plain ? 0 : (s->prefix_force >= 0 ? s->prefix_force : ws.prefix_shift);
     if (nent >= s->entry_cap) return kSplitBatch;  // the caller splits the batch
     rs.n_records += (int64_t)n_valid;
     rs.n_triples += (int64_t)ws.h_counters[0];
@@ -646,8 +684,9 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
     rs.n_entries += (int64_t)(nent / 2);
     // every buffer of the rest of the batch, sized before any of it is enqueued
     BinOut bo;
+    BinArgs sized;
     RK(bin_pairs(ws, ws.boxes.as<PixBox>(), ws.keys.as<double>(), n_pairs, (uint64_t)s->n, n_cells, ne, nent, TS, ntx,
-                 n_tiles, st, bo, launches, false));
+                 n_tiles, st, bo, launches, false, shift, plain ? nullptr : &sized));
     if (!plain) {
         RK(ws.state.ensure(sizeof(uint32_t) * n_pairs));
         RK(ws.wlist.ensure(sizeof(uint32_t) * n_pairs));
@@ -669,7 +708,7 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
                                  (uint64_t)ntx, (uint64_t)W, (uint64_t)H, (uint64_t)s->n, ws.w0,
                                  (uint64_t)s->blend, (uint64_t)float_bits(s->fp64_dev), (uint64_t)float_bits(s->k_open),
                                  (uint64_t)profiling, (uint64_t)ws.interleave, (uint64_t)batch, (uint64_t)(uintptr_t)out_lo,
-                                 (uint64_t)(uintptr_t)out_hi, (uint64_t)(uintptr_t)d_lo};
+                                 (uint64_t)(uintptr_t)out_hi, (uint64_t)(uintptr_t)d_lo, (uint64_t)shift};
         key.assign(head, head + sizeof head / sizeof head[0]);
         ws.append_pointers(key);
         for (int k = 0; k < kEventsPerBatch; ++k) key.push_back((uint64_t)(uintptr_t)ev[k]);
@@ -703,7 +742,7 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
     }
     const int launches0 = launches;
     const int rc = enqueue_rest(s, ws, cc, M, TS, CH, out_lo, out_hi, q, profiling, batch, ev, n_pairs, n_seg, ne, nent,
-                                ntx, n_tiles, plain, launches);
+                                ntx, n_tiles, plain, shift, launches);
     if (capturing) {
         cudaGraph_t graph = nullptr;
         const cudaError_t e = cudaStreamEndCapture(ws.cap_stream, &graph);
@@ -729,7 +768,7 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
         RK(rc);
         launches = launches0;
         return enqueue_rest(s, ws, cc, M, TS, CH, out_lo, out_hi, st, profiling, batch, ev, n_pairs, n_seg, ne, nent, ntx,
-                            n_tiles, plain, launches);
+                            n_tiles, plain, shift, launches);
     }
     return rc;
 }
@@ -738,14 +777,15 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
 // render (windowed rounds, or the plain FP64 renderer), enqueued on q.
 static int enqueue_rest(ar_scene *s, Workspace &ws, const CallConst &cc, int M, int TS, int CH, float *out_lo, float *out_hi,
                         cudaStream_t q, bool profiling, int batch, cudaEvent_t *ev, uint64_t n_pairs, uint64_t n_seg,
-                        uint64_t ne, uint64_t nent, int ntx, int n_tiles, bool plain, int &launches)
+                        uint64_t ne, uint64_t nent, int ntx, int n_tiles, bool plain, int shift, int &launches)
 {
     const int W = cc.W, H = cc.H, n_cells = cc.n_cells;
     BinOut bo;
+    BinArgs ba;
     {
         NvtxRange r("ar.bin: depth-sorted tile bins");
         RK(bin_pairs(ws, ws.boxes.as<PixBox>(), ws.keys.as<double>(), n_pairs, (uint64_t)s->n, n_cells, ne, nent, TS,
-                     ntx, n_tiles, q, bo, launches));
+                     ntx, n_tiles, q, bo, launches, true, shift, plain ? nullptr : &ba));
     }
     if (profiling) CK(record_stage(ev[2], q));
     RenderLaunch rl;
@@ -759,6 +799,8 @@ static int enqueue_rest(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
     rl.ent_ev = bo.ent_ev;
     rl.ev_val = bo.ev_val;
     rl.ev_key = bo.ev_key;
+    rl.seg_total = bo.seg_total;
+    rl.cell_ev = plain ? nullptr : ba.cell_ev;
     rl.W = W; rl.H = H; rl.ntx = ntx; rl.n_tiles = n_tiles; rl.n_cells = n_cells;
     rl.n_gauss = s->n;
     rl.k_open = s->k_open;
@@ -782,9 +824,41 @@ static int enqueue_rest(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
                                ws.wlist.as<uint32_t>(), ws.act0.as<uint32_t>(), ws.act1.as<uint32_t>(),
                                ws.words.as<uint32_t>(), rl.counters + 2, q, &launches,
                                profiling ? ev + 3 : nullptr, ws.w0, ws.slist.as<uint32_t>(), ws.plist.as<uint32_t>(),
-                               ws.pmask.as<uint32_t>()));
+                               ws.pmask.as<uint32_t>(), bo.seg_total ? &ba : nullptr, &bo));
     }
     return AR_OK;
+}
+
+// the cost of a segment's restart (its prefix swept twice) in sorted
+// entries: on object300k a restart cost about 183 ns of render time and the
+// tile binning about 14 ps per entry
+constexpr double kRestartEntries = 12000.0;
+
+int learned_prefix_shift(const unsigned long long *h, const uint32_t *hc, uint64_t n_entries, uint64_t n_events)
+{
+    unsigned long long tot = 0, segs = 0;
+    for (int b = 0; b < 64; ++b) {
+        tot += h[b];
+        segs += hc[b];
+    }
+    if (tot == 0 || segs == 0) return 3;
+    int best = 0;
+    double best_cost = (double)n_entries;
+    for (int sh = 1; sh <= 6; ++sh) {
+        unsigned long long beyond = 0, beyond_n = 0;  // buckets at or past the prefix, 2^-sh of the events
+        for (int b = 64 >> sh; b < 64; ++b) {
+            beyond += h[b];
+            beyond_n += hc[b];
+        }
+        const double scale = (double)n_entries / (double)tot;  // the earlier render's lengths to this one's
+        const double cost = (double)n_entries * std::ldexp(1.0, -sh) + scale * (double)beyond +
+                            (beyond_n ? (double)n_events : 0.0) + kRestartEntries * scale * (double)beyond_n;
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = sh;
+        }
+    }
+    return best;
 }
 
 uint32_t learned_window(const uint32_t *hist256)
@@ -809,9 +883,13 @@ int run_windowed_render(int M, int TS, RenderLaunch rl, const CallConst &cc, con
                         uint64_t n_pairs, uint64_t n_seg, uint32_t *state, uint32_t *wlist, uint32_t *act0,
                         uint32_t *act1, uint32_t *words, unsigned long long *build_counters, cudaStream_t st,
                         int *launches, cudaEvent_t *ev, uint32_t w0, uint32_t *split_list, uint32_t *precise_list,
-                        uint32_t *precise_mask)
+                        uint32_t *precise_mask, const BinArgs *rebin, const BinOut *first)
 {
-    const uint32_t kWindow[3] = {w0, w0 < 8192u ? 8192u : 0xffffffffu, 0xffffffffu};
+    // two phases: a segment restarts in the second round mostly because its
+    // depth prefix ran out, so that round keeps the first window
+    const bool two = rebin && first && first->seg_total;
+    const uint32_t kWindow[3] = {w0, two ? w0 : (w0 < 8192u ? 8192u : 0xffffffffu), 0xffffffffu};
+    const uint32_t *round1_order = nullptr;
     uint32_t *act[2] = {act0, act1};
     CK(cudaMemsetAsync(state, 0, sizeof(uint32_t) * n_pairs, st));
     launch_set_u32(words + 1, (uint32_t)n_seg, st);
@@ -821,7 +899,7 @@ int run_windowed_render(int M, int TS, RenderLaunch rl, const CallConst &cc, con
     for (int r = 0; r < 3; ++r) {
         NvtxRange round_range(kRoundName[r]);
         uint32_t *cur_n = words + 1 + (r & 1), *nxt_n = words + 1 + ((r + 1) & 1);
-        const uint32_t *cur = r == 0 ? rl.seg_order : act[(r - 1) & 1];
+        const uint32_t *cur = r == 0 ? rl.seg_order : (r == 1 && round1_order ? round1_order : act[(r - 1) & 1]);
         CK(cudaMemsetAsync(words, 0, sizeof(uint32_t), st));
         CK(cudaMemsetAsync(nxt_n, 0, sizeof(uint32_t), st));
         CK(cudaMemsetAsync(words + 3, 0, 2 * sizeof(uint32_t), st));
@@ -857,6 +935,19 @@ int run_windowed_render(int M, int TS, RenderLaunch rl, const CallConst &cc, con
             return fail(AR_EDEVICE, "render launch: %s", cudaGetErrorString(cudaGetLastError()));
         if (ev) CK(record_stage(ev[2 * r + 1], st));
         *launches += 6;
+        if (r == 0) {
+            // the second binning phase: full lists for the segments that
+            // left the first round (a window or their depth prefix ran out)
+            if (two) {
+                NvtxRange rebin_range("ar.bin: full lists of the segments left");
+                BinOut full;
+                if (run_rebin(*rebin, *first, act[0], words + 2, full, st, launches))
+                    return fail(AR_EDEVICE, "second binning phase: %s", cudaGetErrorString(cudaGetLastError()));
+                rl.ent_ev = full.ent_ev;
+                round1_order = full.seg_order;
+            }
+            if (ev) CK(record_stage(ev[6], st));
+        }
     }
     return AR_OK;
 }
@@ -1013,9 +1104,9 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
         CK(cudaStreamSynchronize(st));  // the host vector is released on return
     }
     const double *d_lo = ws.cells_lohi.as<double>(), *d_hi = d_lo + (size_t)MAXV * n_cells;
-    RK(ws.whist.ensure(sizeof(uint32_t) * 256));
-    if (!ws.h_whist) CK(cudaMallocHost(&ws.h_whist, sizeof(uint32_t) * 256));
-    CK(cudaMemsetAsync(ws.whist.p, 0, sizeof(uint32_t) * 256, st));
+    RK(ws.whist.ensure(sizeof(uint32_t) * kHistWords));
+    if (!ws.h_whist) CK(cudaMallocHost(&ws.h_whist, sizeof(uint32_t) * kHistWords));
+    CK(cudaMemsetAsync(ws.whist.p, 0, sizeof(uint32_t) * kHistWords, st));
     CK(cudaMemsetAsync(ws.counters.as<unsigned long long>() + 8, 0, sizeof(unsigned long long) * kCountersPerBatch * max_batches, st));
     int launches = 0;
     NvtxRange call_range(plain ? "ar.render_abstract_plain_fp64" : "ar.render_abstract");
@@ -1045,7 +1136,7 @@ int render_core(ar_scene *s, Workspace &ws, const ar_intrinsics *in, const ar_no
     }
     if (!plain) {
         // for the next render's first window (read after its first synchronisation)
-        CK(cudaMemcpyAsync(ws.h_whist, ws.whist.p, sizeof(uint32_t) * 256, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(ws.h_whist, ws.whist.p, sizeof(uint32_t) * kHistWords, cudaMemcpyDeviceToHost, st));
         ws.whist_pending = true;
     }
     ws.n_batches = (int)batches.size();
@@ -1090,12 +1181,14 @@ int finish_stats(Workspace &ws, cudaStream_t st, bool profiling, ar_render_stats
             const cudaEvent_t *e = &ws.evs[kEventsPerBatch * b];
             CK(cudaEventElapsedTime(&t, e[0], e[1])); rs.ms_prep += t;
             CK(cudaEventElapsedTime(&t, e[1], e[2])); rs.ms_bin += t;
+            // e[9]: the end of the second binning phase, after round 0
+            CK(cudaEventElapsedTime(&t, e[4], e[9])); rs.ms_bin += t;
             for (int r = 0; r < 3; ++r) {
-                CK(cudaEventElapsedTime(&t, e[2 + 2 * r], e[3 + 2 * r])); rs.ms_build += t;
+                CK(cudaEventElapsedTime(&t, r == 1 ? e[9] : e[2 + 2 * r], e[3 + 2 * r])); rs.ms_build += t;
                 CK(cudaEventElapsedTime(&t, e[3 + 2 * r], e[4 + 2 * r])); rs.ms_render += t;
             }
         }
-        CK(cudaEventElapsedTime(&rs.ms_total, ws.evs[0], ws.evs[kEventsPerBatch * ws.n_batches - 1]));
+        CK(cudaEventElapsedTime(&rs.ms_total, ws.evs[0], ws.evs[kEventsPerBatch * (ws.n_batches - 1) + 8]));
     }
     return AR_OK;
 }

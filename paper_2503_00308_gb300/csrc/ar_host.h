@@ -37,12 +37,16 @@ struct Workspace {
     DevBuf cells_lohi, cells, vN, recs, boxes, keys, counters;
     DevBuf evk0, evk1, evv0, evv1, ents0, ents1, ente0, ente1;
     DevBuf ua, ub, uc, ud, hist, scan, segs, sege, segk0, segk1, segv0, segv1, work;
+    DevBuf segt, cellev, bwords, smask, ssat;  // two-phase binning: full-list lengths, cell event ranges,
+                                               // counts, active mask and its summed-area tables
     DevBuf state, wlist, act0, act1, words, slist;  // windowed rounds: pair states, build list, active segments
     DevBuf plist, pmask;                     // segments swept again with FP64 evaluations, their pixel masks
-    DevBuf whist;                            // [256] sweep-length histogram of the current render
+    DevBuf whist;                            // [256] sweep-length histogram of the current render, then
+                                             // [64] 64-bit: full-list entries by where the segments stopped
     uint32_t *h_whist = nullptr;             // page-locked copy of the last render's histogram
     bool whist_pending = false;              // h_whist holds a render not yet learned from
     uint32_t w0 = 512;                       // first window of the windowed rounds
+    int prefix_shift = 3;                    // depth prefix of the first binning phase: 1 / 2^shift of the events
     DevBuf out_lo, out_hi;      // staged outputs of ar_render_abstract_host
     DevBuf part_lo, part_hi;    // chunk outputs of ar_render_abstract_partitioned / _refined
     DevBuf lvl_lo, lvl_hi;      // one refinement round's union (ar_render_abstract_refined)
@@ -80,11 +84,24 @@ struct TunedTile {
 // meet an opacity evaluation needing FP64, swept again by the FP64-capable
 // render instance in the same round, and precise_mask [n_seg * TS * TS / 32]
 // the pixels of each that do.
+// rebin / first: the binning of a two-phase render, whose second phase runs
+// between the first and the second round (null: one phase, lists complete)
+struct BinArgs;
+struct BinOut;
 int run_windowed_render(int M, int TS, RenderLaunch rl, const CallConst &cc, const void *cells, const double *vN,
                         uint64_t n_pairs, uint64_t n_seg, uint32_t *state, uint32_t *wlist, uint32_t *act0,
                         uint32_t *act1, uint32_t *words, unsigned long long *build_counters, cudaStream_t st,
                         int *launches, cudaEvent_t *ev, uint32_t w0, uint32_t *split_list, uint32_t *precise_list,
-                        uint32_t *precise_mask);
+                        uint32_t *precise_mask, const BinArgs *rebin = nullptr, const BinOut *first = nullptr);
+// Depth prefix of the next render's first binning phase, from the stop
+// histograms of an earlier render (64 buckets of full-list entries, and of
+// segments, by where in its cell's depth order a segment stopped): the shift
+// s in [0, 6] that minimises the entries sorted, n_entries / 2^s plus the
+// entries of the segments that stop beyond the prefix, plus n_events for the
+// second phase's pass over the events if any does, plus a fixed cost per
+// restarted segment.
+int learned_prefix_shift(const unsigned long long *hist64, const uint32_t *count64, uint64_t n_entries,
+                         uint64_t n_events);
 // First window from the sweep histogram of an earlier render: the smallest
 // multiple of 32 entries that covers 99.5 % of its segments, in [128, 4096].
 uint32_t learned_window(const uint32_t *hist256);
@@ -117,6 +134,9 @@ struct ar_scene {
     // a cell batch with this many tile entries or more is split in two (the
     // 32-bit entry indices; lowered by ar_debug_set_entry_cap for tests)
     uint64_t entry_cap = (1ull << 32) - (1ull << 20);
+    // depth prefix of the first binning phase: -1 learned per workspace, else
+    // the shift (0: one phase); set by ar_debug_set_prefix for tests
+    int prefix_force = -1;
     float fp64_dev = AR_FP64_ALPHA_DEFAULT;  // FP64 re-evaluation threshold (ar_scene_set_fp64_alpha)
     ar_render_stats stats;
     cudaStream_t stats_stream = nullptr;

@@ -14,12 +14,19 @@ struct RenderLaunch {
     const double *recs64 = nullptr;   // FP64 records (plain renderer only)
     const PixBox *boxes;
     const uint32_t *seg_start, *seg_end, *seg_order, *ent_ev, *ev_val;
+    // full-list lengths where the lists are depth prefixes (the first binning
+    // phase), else null; a segment whose sweep needs more than its prefix is
+    // abandoned like one that leaves its window
+    const uint32_t *seg_total = nullptr;
+    const uint32_t *cell_ev = nullptr;  // [n_cells + 1] first sorted event of each cell (for sweep_hist's depth part)
     // windowed rounds (FP32 renderer): segments active[0, *n_active) are swept;
     // one that needs entries beyond `window` is appended to next_active
     const uint32_t *active = nullptr, *n_active = nullptr;
     uint32_t *next_active = nullptr, *n_next = nullptr;
     uint32_t window = 0xffffffffu;
-    uint32_t *sweep_hist = nullptr;   // optional [256]: completed segments by entries swept / 32
+    uint32_t *sweep_hist = nullptr;   // optional [256]: completed segments by entries swept / 32, then (with
+                                      // cell_ev) [64] 64-bit: their full lengths by where in the cell's
+                                      // depth order they stopped, and [64] their counts
     const uint64_t *ev_key;
     int W, H, ntx, n_tiles, n_cells;
     int64_t n_gauss;

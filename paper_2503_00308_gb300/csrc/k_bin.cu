@@ -21,6 +21,7 @@ constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_ROUNDS = 8;
 constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;  // items per block
+constexpr uint32_t kDevGrid = 152u * 8u;          // blocks of a pass whose count is on the device
 
 // ------------------------------------------------------------------ scan
 constexpr int SC_THREADS = 256;
@@ -133,53 +134,62 @@ __device__ __forceinline__ uint32_t rs_digit(K key, uint32_t val, int shift, uin
     return (uint32_t)(key >> shift) & (NB - 1u);
 }
 
+// Both kernels of a pass take the item count n from the host, or (n_dev
+// non-null) the smaller of n and *n_dev, a count known only on the device
+// (the grid is then sized for n and each block loops over tiles).
 template <class K, int RB, bool CELL>
 __global__ void __launch_bounds__(RS_THREADS) rs_hist_kernel(const K *__restrict__ keys,
                                                              const uint32_t *__restrict__ vals, uint32_t n,
                                                              int shift, uint64_t n_gauss,
-                                                             uint32_t *__restrict__ hist, uint32_t nblocks)
+                                                             uint32_t *__restrict__ hist, uint32_t nblocks,
+                                                             const uint32_t *__restrict__ n_dev)
 {
     constexpr uint32_t NB = 1u << RB;
     __shared__ uint32_t h[NB];
-    if (threadIdx.x < NB) h[threadIdx.x] = 0;
-    __syncthreads();
-    const uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
-    // the counts do not depend on which thread reads which item: each thread
-    // reads RS_ROUNDS consecutive items with 16-byte loads where the tile is
-    // whole (the arrays are 16-byte aligned), else one by one
-    const uint64_t i0 = base + (uint64_t)threadIdx.x * RS_ROUNDS;
-    if (CELL) {
-        static_assert(RS_ROUNDS % 4 == 0, "whole vectors per thread");
-        uint32_t v[RS_ROUNDS];
-        if (base + RS_TILE <= n) {
+    if (n_dev) n = min(n, *n_dev);
+    for (uint32_t blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
+        if (threadIdx.x < NB) h[threadIdx.x] = 0;
+        __syncthreads();
+        const uint64_t base = (uint64_t)blk * RS_TILE;
+        // the counts do not depend on which thread reads which item: each thread
+        // reads RS_ROUNDS consecutive items with 16-byte loads where the tile is
+        // whole (the arrays are 16-byte aligned), else one by one
+        const uint64_t i0 = base + (uint64_t)threadIdx.x * RS_ROUNDS;
+        if (CELL) {
+            static_assert(RS_ROUNDS % 4 == 0, "whole vectors per thread");
+            uint32_t v[RS_ROUNDS];
+            if (base + RS_TILE <= n) {
 #pragma unroll
-            for (int q = 0; q < RS_ROUNDS / 4; ++q)
-                reinterpret_cast<uint4 *>(v)[q] = reinterpret_cast<const uint4 *>(vals + i0)[q];
+                for (int q = 0; q < RS_ROUNDS / 4; ++q)
+                    reinterpret_cast<uint4 *>(v)[q] = reinterpret_cast<const uint4 *>(vals + i0)[q];
 #pragma unroll
-            for (int r = 0; r < RS_ROUNDS; ++r) atomicAdd(&h[rs_digit<K, RB, true>(0, v[r], shift, n_gauss)], 1u);
+                for (int r = 0; r < RS_ROUNDS; ++r)
+                    atomicAdd(&h[rs_digit<K, RB, true>(0, v[r], shift, n_gauss)], 1u);
+            } else {
+#pragma unroll
+                for (int r = 0; r < RS_ROUNDS; ++r)
+                    if (i0 + r < n) atomicAdd(&h[rs_digit<K, RB, true>(0, vals[i0 + r], shift, n_gauss)], 1u);
+            }
         } else {
+            constexpr int PER16 = 16 / (int)sizeof(K);
+            static_assert(RS_ROUNDS % PER16 == 0, "whole vectors per thread");
+            K v[RS_ROUNDS];
+            if (base + RS_TILE <= n) {
 #pragma unroll
-            for (int r = 0; r < RS_ROUNDS; ++r)
-                if (i0 + r < n) atomicAdd(&h[rs_digit<K, RB, true>(0, vals[i0 + r], shift, n_gauss)], 1u);
+                for (int q = 0; q < RS_ROUNDS / PER16; ++q)
+                    reinterpret_cast<uint4 *>(v)[q] = reinterpret_cast<const uint4 *>(keys + i0)[q];
+#pragma unroll
+                for (int r = 0; r < RS_ROUNDS; ++r) atomicAdd(&h[rs_digit<K, RB, false>(v[r], 0, shift, 0)], 1u);
+            } else {
+#pragma unroll
+                for (int r = 0; r < RS_ROUNDS; ++r)
+                    if (i0 + r < n) atomicAdd(&h[rs_digit<K, RB, false>(keys[i0 + r], 0, shift, 0)], 1u);
+            }
         }
-    } else {
-        constexpr int PER16 = 16 / (int)sizeof(K);
-        static_assert(RS_ROUNDS % PER16 == 0, "whole vectors per thread");
-        K v[RS_ROUNDS];
-        if (base + RS_TILE <= n) {
-#pragma unroll
-            for (int q = 0; q < RS_ROUNDS / PER16; ++q)
-                reinterpret_cast<uint4 *>(v)[q] = reinterpret_cast<const uint4 *>(keys + i0)[q];
-#pragma unroll
-            for (int r = 0; r < RS_ROUNDS; ++r) atomicAdd(&h[rs_digit<K, RB, false>(v[r], 0, shift, 0)], 1u);
-        } else {
-#pragma unroll
-            for (int r = 0; r < RS_ROUNDS; ++r)
-                if (i0 + r < n) atomicAdd(&h[rs_digit<K, RB, false>(keys[i0 + r], 0, shift, 0)], 1u);
-        }
+        __syncthreads();
+        if (threadIdx.x < NB) hist[(uint64_t)threadIdx.x * nblocks + blk] = h[threadIdx.x];
+        __syncthreads();  // h is cleared for the next tile
     }
-    __syncthreads();
-    if (threadIdx.x < NB) hist[(uint64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
 // Scatter of one radix pass.  Each block ranks its RS_TILE items by digit
@@ -192,7 +202,7 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(const K *__restr
                                                                 K *__restrict__ kout, uint32_t *__restrict__ vout,
                                                                 uint32_t n, int shift, uint64_t n_gauss,
                                                                 const uint32_t *__restrict__ offs,
-                                                                uint32_t nblocks)
+                                                                uint32_t nblocks, const uint32_t *__restrict__ n_dev)
 {
     constexpr uint32_t NB = 1u << RB;
     static_assert(NB <= RS_THREADS, "one thread per digit");
@@ -202,89 +212,94 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(const K *__restr
     __shared__ uint32_t s_warp[RS_WARPS];
     __shared__ K s_key[RS_TILE];
     __shared__ uint32_t s_val[RS_TILE];
-    for (int i = threadIdx.x; i < RS_WARPS * (int)NB; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
-    __syncthreads();
+    if (n_dev) n = min(n, *n_dev);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t ltmask = (1u << lane) - 1u;
-    const uint64_t blk0 = (uint64_t)blockIdx.x * RS_TILE;
-    const uint64_t base = blk0 + (uint64_t)warp * (RS_ROUNDS * 32);
-    K key[RS_ROUNDS];
-    uint32_t val[RS_ROUNDS], dig[RS_ROUNDS], rank[RS_ROUNDS];
-    // all loads first, so that they are in flight together
+    for (uint32_t blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
+        const uint64_t blk0 = (uint64_t)blk * RS_TILE;
+        if (blk0 >= n) break;  // uniform over the block; later tiles are empty too
+        for (int i = threadIdx.x; i < RS_WARPS * (int)NB; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
+        __syncthreads();
+        const uint64_t base = blk0 + (uint64_t)warp * (RS_ROUNDS * 32);
+        K key[RS_ROUNDS];
+        uint32_t val[RS_ROUNDS], dig[RS_ROUNDS], rank[RS_ROUNDS];
+        // all loads first, so that they are in flight together
 #pragma unroll
-    for (int r = 0; r < RS_ROUNDS; ++r) {
-        const uint64_t i = base + (uint64_t)r * 32 + lane;
-        const bool ok = i < n;
-        key[r] = ok ? kin[i] : (K)0;
-        val[r] = ok ? vin[i] : 0u;
-        dig[r] = ok ? rs_digit<K, RB, CELL>(key[r], val[r], shift, n_gauss) : NB;
-    }
-#pragma unroll
-    for (int r = 0; r < RS_ROUNDS; ++r) {
-        const bool ok = dig[r] < NB;
-        // lanes with the same digit, by one ballot per digit bit (bit RB marks
-        // the lanes past the end, so that they match only one another)
-        uint32_t peers = 0xffffffffu;
-#pragma unroll
-        for (int b = 0; b <= RB; ++b) {
-            const bool bit = (dig[r] >> b) & 1u;
-            const uint32_t m = __ballot_sync(0xffffffffu, bit);
-            peers &= bit ? m : ~m;
+        for (int r = 0; r < RS_ROUNDS; ++r) {
+            const uint64_t i = base + (uint64_t)r * 32 + lane;
+            const bool ok = i < n;
+            key[r] = ok ? kin[i] : (K)0;
+            val[r] = ok ? vin[i] : 0u;
+            dig[r] = ok ? rs_digit<K, RB, CELL>(key[r], val[r], shift, n_gauss) : NB;
         }
-        uint32_t before = 0;
-        if (ok) before = wcnt[warp][dig[r]];
-        rank[r] = before + __popc(peers & ltmask);
-        __syncwarp();
-        if (ok && lane == __ffs(peers) - 1) wcnt[warp][dig[r]] = before + __popc(peers);
-        __syncwarp();
-    }
-    __syncthreads();
-    {
-        // per digit (threads 0..NB-1): warp prefix, block total, then the
-        // block-local start
-        const int d = threadIdx.x;
-        uint32_t run = 0;
-        if (d < (int)NB) {
 #pragma unroll
-            for (int w = 0; w < RS_WARPS; ++w) {
-                const uint32_t t = wcnt[w][d];
-                wcnt[w][d] = run;
-                run += t;
+        for (int r = 0; r < RS_ROUNDS; ++r) {
+            const bool ok = dig[r] < NB;
+            // lanes with the same digit, by one ballot per digit bit (bit RB marks
+            // the lanes past the end, so that they match only one another)
+            uint32_t peers = 0xffffffffu;
+#pragma unroll
+            for (int b = 0; b <= RB; ++b) {
+                const bool bit = (dig[r] >> b) & 1u;
+                const uint32_t m = __ballot_sync(0xffffffffu, bit);
+                peers &= bit ? m : ~m;
+            }
+            uint32_t before = 0;
+            if (ok) before = wcnt[warp][dig[r]];
+            rank[r] = before + __popc(peers & ltmask);
+            __syncwarp();
+            if (ok && lane == __ffs(peers) - 1) wcnt[warp][dig[r]] = before + __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        {
+            // per digit (threads 0..NB-1): warp prefix, block total, then the
+            // block-local start
+            const int d = threadIdx.x;
+            uint32_t run = 0;
+            if (d < (int)NB) {
+#pragma unroll
+                for (int w = 0; w < RS_WARPS; ++w) {
+                    const uint32_t t = wcnt[w][d];
+                    wcnt[w][d] = run;
+                    run += t;
+                }
+            }
+            uint32_t x = run;  // inclusive scan of the totals over the digits
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) s_warp[warp] = x;
+            __syncthreads();
+            if (d < (int)NB) {
+                uint32_t wpre = 0;
+                for (int w = 0; w < warp; ++w) wpre += s_warp[w];
+                dstart[d] = wpre + x - run;
+                gbase[d] = offs[(uint64_t)d * nblocks + blk];
             }
         }
-        uint32_t x = run;  // inclusive scan of the totals over the digits
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) s_warp[warp] = x;
         __syncthreads();
-        if (d < (int)NB) {
-            uint32_t wpre = 0;
-            for (int w = 0; w < warp; ++w) wpre += s_warp[w];
-            dstart[d] = wpre + x - run;
-            gbase[d] = offs[(uint64_t)d * nblocks + blockIdx.x];
-        }
-    }
-    __syncthreads();
 #pragma unroll
-    for (int r = 0; r < RS_ROUNDS; ++r) {
-        if (dig[r] < NB) {
-            const uint32_t lp = dstart[dig[r]] + wcnt[warp][dig[r]] + rank[r];
-            s_key[lp] = key[r];
-            s_val[lp] = val[r];
+        for (int r = 0; r < RS_ROUNDS; ++r) {
+            if (dig[r] < NB) {
+                const uint32_t lp = dstart[dig[r]] + wcnt[warp][dig[r]] + rank[r];
+                s_key[lp] = key[r];
+                s_val[lp] = val[r];
+            }
         }
-    }
-    __syncthreads();
-    const uint32_t cnt = n - blk0 < (uint64_t)RS_TILE ? (uint32_t)(n - blk0) : (uint32_t)RS_TILE;
-    for (uint32_t j = threadIdx.x; j < cnt; j += RS_THREADS) {
-        const K k = s_key[j];
-        const uint32_t v = s_val[j];
-        const uint32_t d = rs_digit<K, RB, CELL>(k, v, shift, n_gauss);
-        const uint32_t pos = gbase[d] + (j - dstart[d]);
-        kout[pos] = k;
-        vout[pos] = v;
+        __syncthreads();
+        const uint32_t cnt = n - blk0 < (uint64_t)RS_TILE ? (uint32_t)(n - blk0) : (uint32_t)RS_TILE;
+        for (uint32_t j = threadIdx.x; j < cnt; j += RS_THREADS) {
+            const K k = s_key[j];
+            const uint32_t v = s_val[j];
+            const uint32_t d = rs_digit<K, RB, CELL>(k, v, shift, n_gauss);
+            const uint32_t pos = gbase[d] + (j - dstart[d]);
+            kout[pos] = k;
+            vout[pos] = v;
+        }
+        __syncthreads();  // the shared arrays are rewritten for the next tile
     }
 }
 
@@ -294,15 +309,20 @@ size_t radix_hist_words(uint64_t n)
     return 256 * nb;
 }
 
+// n_dev: see rs_hist_kernel; n is then an upper bound, and the grid is at
+// most a few blocks per SM
 template <class K, int RB, bool CELL = false>
 static void radix_pass(const K *ka, const uint32_t *va, K *kb, uint32_t *vb, uint64_t n, int shift, uint32_t *hist,
-                       uint32_t *scan_tmp, cudaStream_t st, int *launches, uint64_t n_gauss = 0)
+                       uint32_t *scan_tmp, cudaStream_t st, int *launches, uint64_t n_gauss = 0,
+                       const uint32_t *n_dev = nullptr)
 {
     const uint32_t nb = (uint32_t)((n + RS_TILE - 1) / RS_TILE);
-    rs_hist_kernel<K, RB, CELL><<<nb, RS_THREADS, 0, st>>>(ka, va, (uint32_t)n, shift, n_gauss, hist, nb);
+    const uint32_t grid = n_dev ? (nb < kDevGrid ? nb : kDevGrid) : nb;
+    rs_hist_kernel<K, RB, CELL><<<grid, RS_THREADS, 0, st>>>(ka, va, (uint32_t)n, shift, n_gauss, hist, nb, n_dev);
     ++*launches;
     exclusive_scan(hist, hist, ((uint64_t)1 << RB) * nb, scan_tmp, st, launches);
-    rs_scatter_kernel<K, RB, CELL><<<nb, RS_THREADS, 0, st>>>(ka, va, kb, vb, (uint32_t)n, shift, n_gauss, hist, nb);
+    rs_scatter_kernel<K, RB, CELL><<<grid, RS_THREADS, 0, st>>>(ka, va, kb, vb, (uint32_t)n, shift, n_gauss, hist, nb,
+                                                                n_dev);
     ++*launches;
 }
 
@@ -339,10 +359,11 @@ static int radix_sort_cells(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, 
 // fewest passes of at most 8 bits, with equal digits (at least 4 bits: the
 // key bits above shift0 + bits must then be zero, as they are for every
 // caller).  Uses the alt buffers; returns 1 if the result ended in the alt
-// buffers.
+// buffers.  n_dev: the count on the device, n its upper bound (radix_pass).
 template <class K>
 static int radix_sort(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt, uint64_t n, int bits,
-                      uint32_t *hist, uint32_t *scan_tmp, cudaStream_t st, int *launches, int shift0 = 0)
+                      uint32_t *hist, uint32_t *scan_tmp, cudaStream_t st, int *launches, int shift0 = 0,
+                      const uint32_t *n_dev = nullptr)
 {
     if (n == 0 || bits <= 0) return 0;
     const int passes = (bits + 7) / 8;
@@ -352,11 +373,11 @@ static int radix_sort(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt, 
     int flips = 0;
     for (int p = 0, shift = shift0; p < passes; ++p, shift += rb) {
         switch (rb) {
-        case 1: case 2: case 3: case 4: radix_pass<K, 4>(ka, va, kb, vb, n, shift, hist, scan_tmp, st, launches); break;
-        case 5: radix_pass<K, 5>(ka, va, kb, vb, n, shift, hist, scan_tmp, st, launches); break;
-        case 6: radix_pass<K, 6>(ka, va, kb, vb, n, shift, hist, scan_tmp, st, launches); break;
-        case 7: radix_pass<K, 7>(ka, va, kb, vb, n, shift, hist, scan_tmp, st, launches); break;
-        default: radix_pass<K, 8>(ka, va, kb, vb, n, shift, hist, scan_tmp, st, launches); break;
+        case 1: case 2: case 3: case 4: radix_pass<K, 4>(ka, va, kb, vb, n, shift, hist, scan_tmp, st, launches, 0, n_dev); break;
+        case 5: radix_pass<K, 5>(ka, va, kb, vb, n, shift, hist, scan_tmp, st, launches, 0, n_dev); break;
+        case 6: radix_pass<K, 6>(ka, va, kb, vb, n, shift, hist, scan_tmp, st, launches, 0, n_dev); break;
+        case 7: radix_pass<K, 7>(ka, va, kb, vb, n, shift, hist, scan_tmp, st, launches, 0, n_dev); break;
+        default: radix_pass<K, 8>(ka, va, kb, vb, n, shift, hist, scan_tmp, st, launches, 0, n_dev); break;
         }
         K *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
@@ -390,14 +411,160 @@ __device__ __forceinline__ void tile_rect(const PixBox &b, int TS, int &tx0, int
     tx0 = b.x0 / TS; tx1 = b.x1 / TS; ty0 = b.y0 / TS; ty1 = b.y1 / TS;
 }
 
+// First sorted event of every cell (cell c holds [cell_ev[c], cell_ev[c + 1])):
+// from the exclusive scan pos of the pairs' presence flags, cell c's events
+// start at 2 pos[c n_gauss].
+__global__ void cell_events_kernel(const uint32_t *__restrict__ pos, uint64_t n_gauss, int n_cells, uint32_t ne,
+                                   uint32_t *__restrict__ cell_ev)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > n_cells) return;
+    cell_ev[c] = c < n_cells ? 2u * pos[(uint64_t)c * n_gauss] : ne;
+}
+
+// The depth prefix of a cell: its first ceil(E / 2^shift) sorted events, E
+// the cell's events (shift = 0: all of them).  Sorted event e of cell `cell`
+// lies in it when this holds.
+__device__ __forceinline__ bool in_prefix(uint64_t e, uint32_t cell, const uint32_t *__restrict__ cell_ev, int shift)
+{
+    if (!shift) return true;
+    const uint32_t c0 = cell_ev[cell], ec = cell_ev[cell + 1] - c0;
+    return e - c0 < (((uint64_t)ec + (1u << shift) - 1u) >> shift);
+}
+
 __global__ void tile_counts_kernel(const uint32_t *__restrict__ ev_val, uint64_t ne,
-                                   const PixBox *__restrict__ boxes, int TS, uint32_t *__restrict__ cnt)
+                                   const PixBox *__restrict__ boxes, int TS, uint64_t n_gauss,
+                                   const uint32_t *__restrict__ cell_ev, int shift, uint32_t *__restrict__ cnt)
 {
     const uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     if (e >= ne) return;
+    const uint32_t ri = ev_val[e] >> 1;
     int tx0, tx1, ty0, ty1;
-    tile_rect(boxes[ev_val[e] >> 1], TS, tx0, tx1, ty0, ty1);
-    cnt[e] = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+    tile_rect(boxes[ri], TS, tx0, tx1, ty0, ty1);
+    cnt[e] = in_prefix(e, (uint32_t)(ri / n_gauss), cell_ev, shift) ? (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1))
+                                                                      : 0u;
+}
+
+// *word = cnt[n - 1] before an in-place exclusive scan of cnt, then (add)
+// the scan's last value: the total
+__global__ void scan_last_kernel(const uint32_t *__restrict__ v, uint64_t n, uint32_t *__restrict__ word, int add)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *word = (add ? *word : 0u) + (n ? v[n - 1] : 0u);
+}
+
+// Entry counts of the segments' full lists, as 2D difference marks per cell:
+// each present pair adds 2 (its two events) at the corner of its tile
+// rectangle and subtracts it past the right and the bottom edge (adding it
+// back past both); marks past the grid's last column or row are dropped, as
+// no prefix sum reaches them.  tot: [n_cells][n_tiles], zeroed first.  One
+// block takes MARK_PAIRS pairs of one cell (blockIdx.y) and gathers their
+// marks in shared memory (SMEM; else straight into tot).
+constexpr int MARK_PAIRS = 16384;
+constexpr int kMarkSmemTiles = 12288;  // 48 KB of shared marks
+template <bool SMEM>
+__global__ void __launch_bounds__(256) seg_marks_kernel(const PixBox *__restrict__ boxes, uint64_t n_gauss, int TS,
+                                                        int ntx, int nty, uint32_t *__restrict__ tot)
+{
+    extern __shared__ uint32_t s_m[];
+    const int n_tiles = ntx * nty;
+    const uint64_t c = blockIdx.y, g0 = (uint64_t)blockIdx.x * MARK_PAIRS;
+    const uint64_t g1 = min(g0 + (uint64_t)MARK_PAIRS, n_gauss);
+    uint32_t *t = tot + c * (uint64_t)n_tiles;
+    uint32_t *m = SMEM ? s_m : t;
+    if (SMEM) {
+        for (int i = threadIdx.x; i < n_tiles; i += blockDim.x) s_m[i] = 0u;
+        __syncthreads();
+    }
+    const PixBox *bc = boxes + c * n_gauss;
+    for (uint64_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+        const PixBox b = bc[g];
+        if (b.x0 < 0) continue;
+        int tx0, tx1, ty0, ty1;
+        tile_rect(b, TS, tx0, tx1, ty0, ty1);
+        const bool right = tx1 + 1 < ntx, below = ty1 + 1 < nty;
+        atomicAdd(&m[ty0 * ntx + tx0], 2u);
+        if (right) atomicAdd(&m[ty0 * ntx + tx1 + 1], 0u - 2u);
+        if (below) {
+            atomicAdd(&m[(ty1 + 1) * ntx + tx0], 0u - 2u);
+            if (right) atomicAdd(&m[(ty1 + 1) * ntx + tx1 + 1], 2u);
+        }
+    }
+    if (SMEM) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < n_tiles; i += blockDim.x)
+            if (s_m[i]) atomicAdd(&t[i], s_m[i]);
+    }
+}
+
+// prefix sums of the marks (modulo 2^32) along each row (cols = 0: one
+// thread per (cell, row)) or each column (cols = 1: per (cell, column))
+__global__ void seg_prefix_kernel(uint32_t *__restrict__ tot, int n_cells, int ntx, int nty, int cols)
+{
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const int lines = cols ? ntx : nty, len = cols ? nty : ntx;
+    if (i >= (uint64_t)n_cells * (uint64_t)lines) return;
+    const uint64_t c = i / (uint64_t)lines;
+    const int l = (int)(i % (uint64_t)lines);
+    uint32_t *t = tot + c * (uint64_t)ntx * (uint64_t)nty;
+    const int step = cols ? ntx : 1;
+    uint32_t *p = t + (cols ? l : l * ntx);
+    uint32_t run = 0;
+    for (int k = 0; k < len; ++k, p += step) {
+        run += *p;
+        *p = run;
+    }
+}
+
+// The second binning phase's input: the active segments as a bit mask
+// (zeroed first), and per event the tiles of its box whose segment is active.
+__global__ void active_mask_kernel(const uint32_t *__restrict__ active, const uint32_t *__restrict__ n_active,
+                                   uint32_t *__restrict__ mask)
+{
+    const uint32_t na = *n_active;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < na; i += gridDim.x * blockDim.x)
+        atomicOr(&mask[active[i] >> 5], 1u << (active[i] & 31u));
+}
+
+__device__ __forceinline__ bool seg_active(const uint32_t *__restrict__ mask, uint64_t seg)
+{
+    return (mask[seg >> 5] >> (seg & 31u)) & 1u;
+}
+
+// Per cell, a summed-area table of the active tiles ([n_cells][(nty + 1) x
+// (ntx + 1)], the first row and column 0; sat zeroed first, then prefix sums
+// along its rows and columns): the active tiles of any tile rectangle in four
+// lookups.
+__global__ void sat_fill_kernel(const uint32_t *__restrict__ mask, int n_cells, int ntx, int nty,
+                                uint32_t *__restrict__ sat)
+{
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t n_tiles = (uint64_t)ntx * (uint64_t)nty;
+    if (i >= (uint64_t)n_cells * n_tiles) return;
+    const uint64_t c = i / n_tiles;
+    const int t = (int)(i % n_tiles), y = t / ntx, x = t % ntx;
+    if (seg_active(mask, i)) sat[c * (uint64_t)(ntx + 1) * (nty + 1) + (uint64_t)(y + 1) * (ntx + 1) + (x + 1)] = 1u;
+}
+
+__device__ __forceinline__ uint32_t sat_rect(const uint32_t *__restrict__ s, int w, int tx0, int tx1, int ty0, int ty1)
+{
+    return s[(ty1 + 1) * w + tx1 + 1] - s[ty0 * w + tx1 + 1] - s[(ty1 + 1) * w + tx0] + s[ty0 * w + tx0];
+}
+
+__global__ void masked_counts_kernel(const uint32_t *__restrict__ ev_val, uint64_t ne,
+                                     const PixBox *__restrict__ boxes, int TS, int ntx, int nty, uint64_t n_gauss,
+                                     const uint32_t *__restrict__ sat, const uint32_t *__restrict__ n_active,
+                                     uint32_t *__restrict__ cnt)
+{
+    const uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    uint32_t n = 0;
+    if (*n_active) {
+        const uint32_t ri = ev_val[e] >> 1;
+        int tx0, tx1, ty0, ty1;
+        tile_rect(boxes[ri], TS, tx0, tx1, ty0, ty1);
+        n = sat_rect(sat + (ri / n_gauss) * (uint64_t)(ntx + 1) * (nty + 1), ntx + 1, tx0, tx1, ty0, ty1);
+    }
+    cnt[e] = n;
 }
 
 // Entry keys: (tile << cb) | cell when cb >= 0 (the entries of one cell are
@@ -418,10 +585,13 @@ __device__ __forceinline__ uint32_t entry_segment(uint32_t key, int cb, int n_ti
 // that range, so every store instruction writes 32 consecutive words; each
 // lane finds the event of its entry by a binary search over the warp's 32
 // offsets (shuffles).  Launch with a multiple of 32 threads per block.
+// Events outside their cell's depth prefix (cell_ev, shift: in_prefix) give
+// no entries.
 __global__ void emit_entries_kernel(const uint32_t *__restrict__ ev_val, uint64_t ne,
                                     const PixBox *__restrict__ boxes, int TS, int ntx, int n_tiles, int cb,
-                                    uint64_t n_gauss, const uint32_t *__restrict__ off,
-                                    uint32_t *__restrict__ ent_seg, uint32_t *__restrict__ ent_ev)
+                                    uint64_t n_gauss, const uint32_t *__restrict__ cell_ev, int shift,
+                                    const uint32_t *__restrict__ off, uint32_t *__restrict__ ent_seg,
+                                    uint32_t *__restrict__ ent_ev)
 {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -437,7 +607,7 @@ __global__ void emit_entries_kernel(const uint32_t *__restrict__ ev_val, uint64_
         tile_rect(boxes[ri], TS, tx0, tx1, ty0, ty1);
         tw = tx1 - tx0 + 1;
         myoff = off[e];
-        myend = myoff + (uint32_t)(tw * (ty1 - ty0 + 1));
+        myend = myoff + (in_prefix(e, cell, cell_ev, shift) ? (uint32_t)(tw * (ty1 - ty0 + 1)) : 0u);
     }
     const uint32_t start = __shfl_sync(full, myoff, 0);
     uint32_t end = myend;
@@ -464,6 +634,36 @@ __global__ void emit_entries_kernel(const uint32_t *__restrict__ ev_val, uint64_
     }
 }
 
+// The second phase's entries: each event writes, one thread per event, its
+// tiles whose segment is active, from off[e] on (off: the exclusive scan of
+// masked_counts_kernel's counts).
+__global__ void masked_emit_kernel(const uint32_t *__restrict__ ev_val, uint64_t ne, const PixBox *__restrict__ boxes,
+                                   int TS, int ntx, int nty, int cb, uint64_t n_gauss,
+                                   const uint32_t *__restrict__ mask, const uint32_t *__restrict__ sat,
+                                   const uint32_t *__restrict__ n_active, const uint32_t *__restrict__ off,
+                                   uint32_t *__restrict__ ent_seg, uint32_t *__restrict__ ent_ev)
+{
+    const uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (e >= ne || *n_active == 0) return;
+    const int n_tiles = ntx * nty;
+    const uint32_t ri = ev_val[e] >> 1;
+    const uint32_t cell = (uint32_t)(ri / n_gauss);
+    const uint64_t s0 = (uint64_t)cell * (uint64_t)n_tiles;
+    int tx0, tx1, ty0, ty1;
+    tile_rect(boxes[ri], TS, tx0, tx1, ty0, ty1);
+    if (!sat_rect(sat + cell * (uint64_t)(ntx + 1) * (nty + 1), ntx + 1, tx0, tx1, ty0, ty1)) return;
+    uint32_t j = off[e];
+    for (int ty = ty0; ty <= ty1; ++ty)
+        for (int tx = tx0; tx <= tx1; ++tx) {
+            const uint32_t tile = (uint32_t)(ty * ntx + tx);
+            if (seg_active(mask, s0 + tile)) {
+                ent_seg[j] = entry_key(cell, tile, cb, n_tiles);
+                ent_ev[j] = (uint32_t)e;
+                ++j;
+            }
+        }
+}
+
 // key = ~length so that an ascending stable sort puts the longest first
 __global__ void seg_len_kernel(const uint32_t *__restrict__ start, const uint32_t *__restrict__ end, uint64_t n,
                                uint32_t *__restrict__ key, uint32_t *__restrict__ val)
@@ -475,9 +675,11 @@ __global__ void seg_len_kernel(const uint32_t *__restrict__ start, const uint32_
 }
 
 __global__ void seg_bounds_kernel(const uint32_t *__restrict__ key, uint64_t n, int cb, int n_tiles,
-                                  uint32_t *__restrict__ start, uint32_t *__restrict__ end)
+                                  uint32_t *__restrict__ start, uint32_t *__restrict__ end,
+                                  const uint32_t *__restrict__ n_dev)
 {
     const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (n_dev && *n_dev < n) n = *n_dev;
     if (i >= n) return;
     const uint32_t k = key[i];
     const uint32_t s = entry_segment(k, cb, n_tiles);
@@ -497,9 +699,11 @@ __device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t *__restrict__
     return lo;
 }
 __global__ void seg_bounds_search_kernel(const uint32_t *__restrict__ key, uint32_t n, int cb, int n_cells,
-                                         int n_tiles, uint32_t *__restrict__ start, uint32_t *__restrict__ end)
+                                         int n_tiles, uint32_t *__restrict__ start, uint32_t *__restrict__ end,
+                                         const uint32_t *__restrict__ n_dev)
 {
     const uint64_t sg = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (n_dev && *n_dev < n) n = *n_dev;
     if (sg >= (uint64_t)n_cells * (uint64_t)n_tiles) return;
     const uint32_t cell = (uint32_t)(sg / (uint64_t)n_tiles), tile = (uint32_t)(sg % (uint64_t)n_tiles);
     const uint32_t k = (tile << cb) | cell;
@@ -516,6 +720,41 @@ __global__ void iota_kernel(uint32_t *__restrict__ p, uint64_t n)
 
 static inline unsigned blocks_for(uint64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// The entries' stable sort by tile (packed keys: the tile bits above cb) or
+// by segment, then the segment bounds; n_dev: the entries' count when it is
+// known on the device only (n_entries bounds it).  Returns the buffer
+// holding the result.
+static int sort_entries(const BinArgs &a, bool packed, int cb, int tb, const uint32_t *n_dev, cudaStream_t st,
+                        int *launches)
+{
+    const int T = 256;
+    int h;
+    if (packed) {
+        h = radix_sort<uint32_t>(a.ent_seg[0], a.ent_ev[0], a.ent_seg[1], a.ent_ev[1], a.n_entries, tb, a.hist,
+                                 a.scan_tmp, st, launches, cb, n_dev);
+    } else {
+        int bits = 0;
+        while ((1ull << bits) < a.n_segments) ++bits;
+        h = radix_sort<uint32_t>(a.ent_seg[0], a.ent_ev[0], a.ent_seg[1], a.ent_ev[1], a.n_entries, bits, a.hist,
+                                 a.scan_tmp, st, launches, 0, n_dev);
+    }
+    const uint32_t *keys = a.ent_seg[h];
+    if (packed) {
+        seg_bounds_search_kernel<<<blocks_for(a.n_segments, T), T, 0, st>>>(keys, (uint32_t)a.n_entries, cb, a.n_cells,
+                                                                            a.n_tiles, a.seg_start, a.seg_end, n_dev);
+        ++*launches;
+    } else {
+        cudaMemsetAsync(a.seg_start, 0, sizeof(uint32_t) * a.n_segments, st);
+        cudaMemsetAsync(a.seg_end, 0, sizeof(uint32_t) * a.n_segments, st);
+        if (a.n_entries) {
+            seg_bounds_kernel<<<blocks_for(a.n_entries, T), T, 0, st>>>(keys, a.n_entries, -1, a.n_tiles, a.seg_start,
+                                                                         a.seg_end, n_dev);
+            ++*launches;
+        }
+    }
+    return h;
+}
+
 int run_binning(const BinArgs &a, BinOut &o, cudaStream_t st, int *launches)
 {
     const int T = 256;
@@ -528,6 +767,7 @@ int run_binning(const BinArgs &a, BinOut &o, cudaStream_t st, int *launches)
                                                                  a.ev_val[0]);
     ++*launches;
     const uint64_t ne = a.n_events;
+    o.seg_total = nullptr;
     if (ne == 0) {
         o.ev_key = a.ev_key[0];
         o.ev_val = a.ev_val[0];
@@ -539,6 +779,15 @@ int run_binning(const BinArgs &a, BinOut &o, cudaStream_t st, int *launches)
         ++*launches;
         o.seg_order = a.seg_v[0];
         return cudaGetLastError() == cudaSuccess ? 0 : 1;
+    }
+    // the first phase bins only each cell's depth prefix (see in_prefix): the
+    // cells' event ranges, while the presence scan is at hand (also wanted by
+    // the renderer's stop histogram when there is one phase)
+    const bool prefix = a.prefix_shift > 0 && a.cell_ev;
+    if (a.cell_ev) {
+        cell_events_kernel<<<blocks_for((uint64_t)a.n_cells + 1, T), T, 0, st>>>(a.u32_a, a.n_gauss, a.n_cells,
+                                                                                  (uint32_t)ne, a.cell_ev);
+        ++*launches;
     }
     // 3. sort by key bits, then stably by cell
     int f = radix_sort<uint64_t>(a.ev_key[0], a.ev_val[0], a.ev_key[1], a.ev_val[1], ne, 64, a.hist, a.scan_tmp,
@@ -556,10 +805,37 @@ int run_binning(const BinArgs &a, BinOut &o, cudaStream_t st, int *launches)
     }
     o.ev_key = evk;
     o.ev_val = evv;
-    // 4. entries per tile
-    tile_counts_kernel<<<blocks_for(ne, T), T, 0, st>>>(evv, ne, a.boxes, a.TS, a.u32_a);
+    const int nty = a.n_tiles / a.ntx;
+    if (prefix) {
+        // the lengths of the segments' full lists
+        cudaMemsetAsync(a.seg_total, 0, sizeof(uint32_t) * a.n_segments, st);
+        const dim3 mg((unsigned)((a.n_gauss + MARK_PAIRS - 1) / MARK_PAIRS), (unsigned)a.n_cells);
+        if (a.n_tiles <= kMarkSmemTiles)
+            seg_marks_kernel<true><<<mg, T, sizeof(uint32_t) * a.n_tiles, st>>>(a.boxes, a.n_gauss, a.TS, a.ntx, nty,
+                                                                                 a.seg_total);
+        else
+            seg_marks_kernel<false><<<mg, T, 0, st>>>(a.boxes, a.n_gauss, a.TS, a.ntx, nty, a.seg_total);
+        seg_prefix_kernel<<<blocks_for((uint64_t)a.n_cells * nty, T), T, 0, st>>>(a.seg_total, a.n_cells, a.ntx, nty, 0);
+        seg_prefix_kernel<<<blocks_for((uint64_t)a.n_cells * a.ntx, T), T, 0, st>>>(a.seg_total, a.n_cells, a.ntx, nty,
+                                                                                    1);
+        *launches += 3;
+        o.seg_total = a.seg_total;
+    }
+    // 4. entries per tile (of the prefix: their count is then known on the device only)
+    tile_counts_kernel<<<blocks_for(ne, T), T, 0, st>>>(evv, ne, a.boxes, a.TS, a.n_gauss, a.cell_ev,
+                                                         a.prefix_shift, a.u32_a);
     ++*launches;
+    const uint32_t *n_dev = nullptr;
+    if (prefix) {
+        scan_last_kernel<<<1, 32, 0, st>>>(a.u32_a, ne, a.words, 0);
+        ++*launches;
+    }
     exclusive_scan(a.u32_a, a.u32_a, ne, a.scan_tmp, st, launches);
+    if (prefix) {
+        scan_last_kernel<<<1, 32, 0, st>>>(a.u32_a, ne, a.words, 1);
+        ++*launches;
+        n_dev = a.words;
+    }
     // entry keys: tile bits above cell bits when both fit in 32 bits
     int cb = 0, tb = 0;
     while ((1ull << cb) < (uint64_t)a.n_cells) ++cb;
@@ -567,42 +843,78 @@ int run_binning(const BinArgs &a, BinOut &o, cudaStream_t st, int *launches)
     if (tb == 0) tb = 1;
     const bool packed = cb + tb <= 32;
     emit_entries_kernel<<<blocks_for(ne, T), T, 0, st>>>(evv, ne, a.boxes, a.TS, a.ntx, a.n_tiles, packed ? cb : -1,
-                                                          a.n_gauss, a.u32_a, a.ent_seg[0], a.ent_ev[0]);
+                                                          a.n_gauss, a.cell_ev, a.prefix_shift, a.u32_a, a.ent_seg[0],
+                                                          a.ent_ev[0]);
     ++*launches;
-    // 5. stable sort by tile (packed keys) or by segment
-    int h;
-    if (packed) {
-        h = radix_sort<uint32_t>(a.ent_seg[0], a.ent_ev[0], a.ent_seg[1], a.ent_ev[1], a.n_entries, tb, a.hist,
-                                 a.scan_tmp, st, launches, cb);
-    } else {
-        int bits = 0;
-        while ((1ull << bits) < a.n_segments) ++bits;
-        h = radix_sort<uint32_t>(a.ent_seg[0], a.ent_ev[0], a.ent_seg[1], a.ent_ev[1], a.n_entries, bits, a.hist,
-                                 a.scan_tmp, st, launches);
-    }
+    // 5-6. stable sort by tile, segment bounds
+    const int h = sort_entries(a, packed, cb, tb, n_dev, st, launches);
     o.ent_seg = a.ent_seg[h];
     o.ent_ev = a.ent_ev[h];
-    // 6. segment bounds
-    if (packed) {
-        seg_bounds_search_kernel<<<blocks_for(a.n_segments, T), T, 0, st>>>(o.ent_seg, (uint32_t)a.n_entries, cb,
-                                                                            a.n_cells, a.n_tiles, a.seg_start,
-                                                                            a.seg_end);
-        ++*launches;
-    } else {
-        cudaMemsetAsync(a.seg_start, 0, sizeof(uint32_t) * a.n_segments, st);
-        cudaMemsetAsync(a.seg_end, 0, sizeof(uint32_t) * a.n_segments, st);
-        if (a.n_entries) {
-            seg_bounds_kernel<<<blocks_for(a.n_entries, T), T, 0, st>>>(o.ent_seg, a.n_entries, -1, a.n_tiles,
-                                                                         a.seg_start, a.seg_end);
-            ++*launches;
-        }
-    }
     // 7. schedule: segments by decreasing length (load balance of the render)
     seg_len_kernel<<<blocks_for(a.n_segments, T), T, 0, st>>>(a.seg_start, a.seg_end, a.n_segments, a.seg_k[0],
                                                                a.seg_v[0]);
     ++*launches;
     int q = radix_sort<uint32_t>(a.seg_k[0], a.seg_v[0], a.seg_k[1], a.seg_v[1], a.n_segments, 32, a.hist,
                                  a.scan_tmp, st, launches);
+    o.seg_order = a.seg_v[q];
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+// keys ~len[seg] of the listed segments, so that an ascending sort puts the
+// longest first
+__global__ void active_keys_kernel(const uint32_t *__restrict__ active, const uint32_t *__restrict__ n_active,
+                                   const uint32_t *__restrict__ len, uint32_t *__restrict__ key,
+                                   uint32_t *__restrict__ val)
+{
+    const uint32_t na = *n_active;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < na; i += gridDim.x * blockDim.x) {
+        key[i] = ~len[active[i]];
+        val[i] = active[i];
+    }
+}
+
+int run_rebin(const BinArgs &a, const BinOut &first, const uint32_t *active, const uint32_t *n_active, BinOut &o,
+              cudaStream_t st, int *launches)
+{
+    const int T = 256;
+    const uint64_t ne = a.n_events;
+    o = first;
+    if (ne == 0) return 0;
+    const int nty = a.n_tiles / a.ntx;
+    cudaMemsetAsync(a.mask, 0, sizeof(uint32_t) * ((a.n_segments + 31) / 32), st);
+    cudaMemsetAsync(a.sat, 0, sizeof(uint32_t) * (size_t)a.n_cells * (a.ntx + 1) * (nty + 1), st);
+    const uint64_t mg = blocks_for(a.n_segments, T);
+    active_mask_kernel<<<(unsigned)(mg < kDevGrid ? mg : kDevGrid), T, 0, st>>>(active, n_active, a.mask);
+    sat_fill_kernel<<<blocks_for(a.n_segments, T), T, 0, st>>>(a.mask, a.n_cells, a.ntx, nty, a.sat);
+    seg_prefix_kernel<<<blocks_for((uint64_t)a.n_cells * (nty + 1), T), T, 0, st>>>(a.sat, a.n_cells, a.ntx + 1,
+                                                                                    nty + 1, 0);
+    seg_prefix_kernel<<<blocks_for((uint64_t)a.n_cells * (a.ntx + 1), T), T, 0, st>>>(a.sat, a.n_cells, a.ntx + 1,
+                                                                                      nty + 1, 1);
+    masked_counts_kernel<<<blocks_for(ne, T), T, 0, st>>>(first.ev_val, ne, a.boxes, a.TS, a.ntx, nty, a.n_gauss,
+                                                           a.sat, n_active, a.u32_a);
+    scan_last_kernel<<<1, 32, 0, st>>>(a.u32_a, ne, a.words + 1, 0);
+    *launches += 6;
+    exclusive_scan(a.u32_a, a.u32_a, ne, a.scan_tmp, st, launches);
+    scan_last_kernel<<<1, 32, 0, st>>>(a.u32_a, ne, a.words + 1, 1);
+    int cb = 0, tb = 0;
+    while ((1ull << cb) < (uint64_t)a.n_cells) ++cb;
+    while ((1ull << tb) < (uint64_t)a.n_tiles) ++tb;
+    if (tb == 0) tb = 1;
+    const bool packed = cb + tb <= 32;
+    masked_emit_kernel<<<blocks_for(ne, T), T, 0, st>>>(first.ev_val, ne, a.boxes, a.TS, a.ntx, nty, packed ? cb : -1,
+                                                         a.n_gauss, a.mask, a.sat, n_active, a.u32_a, a.ent_seg[0],
+                                                         a.ent_ev[0]);
+    *launches += 2;
+    const int h = sort_entries(a, packed, cb, tb, a.words + 1, st, launches);
+    o.ent_seg = a.ent_seg[h];
+    o.ent_ev = a.ent_ev[h];
+    // the active segments, longest full list first (the first phase's order
+    // is no longer needed: its buffers are reused)
+    active_keys_kernel<<<(unsigned)(mg < kDevGrid ? mg : kDevGrid), T, 0, st>>>(active, n_active, a.seg_total,
+                                                                               a.seg_k[0], a.seg_v[0]);
+    ++*launches;
+    const int q = radix_sort<uint32_t>(a.seg_k[0], a.seg_v[0], a.seg_k[1], a.seg_v[1], a.n_segments, 32, a.hist,
+                                       a.scan_tmp, st, launches, 0, n_active);
     o.seg_order = a.seg_v[q];
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }

@@ -86,7 +86,9 @@ static int launch_render_ts(const RenderLaunch &a, cudaStream_t st)
     // one CTA per segment
     if (a.direct) grid = nseg;
     if (cudaMemsetAsync(a.work, 0, sizeof(unsigned int), st) != cudaSuccess) return 1;
-    kern<<<grid, TS * TS, SM::BYTES, st>>>(a.recs, a.boxes, a.seg_start, a.seg_end, a.active, a.n_active, a.window,
+    kern<<<grid, TS * TS, SM::BYTES, st>>>(a.recs, a.boxes, a.seg_start, a.seg_end, a.seg_total, a.cell_ev,
+                                           a.active, a.n_active,
+                                           a.window,
                                            a.next_active, a.n_next, a.precise, a.n_precise, a.precise_mask, a.sweep_hist,
                                            a.ent_ev, a.ev_val,
                                            a.ev_key, a.W, a.H, a.ntx, a.n_tiles, a.n_gauss, a.k_open, a.fp64_dev, a.out_lo,

@@ -469,7 +469,8 @@ template <int TS> struct RenderOcc {
 template <int M, int TS, int CH, int RING, bool REL, bool F64>
 __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kernel(
     const float *__restrict__ recs, const PixBox *__restrict__ boxes, const uint32_t *__restrict__ seg_start,
-    const uint32_t *__restrict__ seg_end, const uint32_t *__restrict__ active, const uint32_t *__restrict__ n_active,
+    const uint32_t *__restrict__ seg_end, const uint32_t *__restrict__ seg_total,
+    const uint32_t *__restrict__ cell_ev, const uint32_t *__restrict__ active, const uint32_t *__restrict__ n_active,
     uint32_t window, uint32_t *__restrict__ next_active, uint32_t *__restrict__ n_next,
     uint32_t *__restrict__ precise_list, uint32_t *__restrict__ n_precise, uint32_t *__restrict__ precise_mask,
     uint32_t *__restrict__ sweep_hist,
@@ -513,6 +514,10 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
         const bool inside = px < W && py < H;
         const float ux = px + 0.5f, uy = py + 0.5f;
         const uint32_t b0 = seg_start[seg], b1 = seg_end[seg];
+        // entries of the segment's full list; the list at hand may be a
+        // prefix of it (the first binning phase)
+        const uint32_t total = seg_total ? seg_total[seg] : b1 - b0;
+        const bool incomplete = total > b1 - b0;
         const float *rec_cell = recs + (size_t)cell * n_gauss * RL::WIDTH;
         const PixBox *box_cell = boxes + (size_t)cell * n_gauss;
 
@@ -581,10 +586,14 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
         };
         int buf = 0;
         if (b0 < b1) stage(0, b0);
-        for (uint32_t base = b0; base < b1; base += CH, buf ^= 1) {
-            const int cnt = (int)min((uint32_t)CH, b1 - base);
+        // a complete list ends the sweep when it runs out; a prefix only when
+        // every pixel has stopped, or by abandoning the segment at the first
+        // chunk it does not hold in full (the next binning phase gives the
+        // segment its full list, and the sweep starts again: the exit tests
+        // fall at the same entries, so the bounds are those of one sweep)
+        for (uint32_t base = b0; base < b1 || incomplete; base += CH, buf ^= 1) {
             if (!done) {
-                const float left = (float)(b1 - base);
+                const float left = (float)(total - (base - b0));
                 // PA is rounded down; 1.01 covers its relative error for < 10^5 factors
                 const float ow = fminf(open_w, __fmul_ru((float)n_open, k_open));
                 const float elo2 = __fmul_ru(__fmul_ru(PA, 1.01f), __fadd_ru(ow, 1.f));
@@ -608,6 +617,11 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
                 swept = base - b0;
                 break;
             }
+            if (incomplete && base + CH > b1) {  // the chunk reaches beyond the prefix
+                abandoned = true;
+                break;
+            }
+            const int cnt = (int)min((uint32_t)CH, b1 - base);
             if (base + (uint32_t)cnt - b0 > window) {  // records beyond the window are not built
                 abandoned = true;
                 break;
@@ -755,6 +769,16 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
             if ((tid & 31) == 0) precise_mask[(size_t)s_next[1] * (NT / 32) + (tid >> 5)] = m;
         }
         if (!F64 && sweep_hist && tid == 0) atomicAdd(&sweep_hist[min(swept / 32u, 255u)], 1u);
+        // where in its cell's depth order the segment stopped (64 buckets of
+        // the cell's sorted events), weighted by its full length and counted:
+        // the host sizes the next render's depth prefix from them
+        if (!F64 && sweep_hist && cell_ev && tid == 0 && b1 > b0) {
+            const uint32_t c0 = cell_ev[cell], ec = cell_ev[cell + 1] - c0;
+            const uint32_t stop = entry_ev[b0 + (swept ? swept : 1u) - 1u];
+            const uint32_t bkt = ec ? (uint32_t)min((uint64_t)(stop - c0) * 64u / ec, (uint64_t)63) : 0u;
+            atomicAdd(reinterpret_cast<unsigned long long *>(sweep_hist + 256) + bkt, (unsigned long long)total);
+            atomicAdd(sweep_hist + 384 + bkt, 1u);
+        }
         evals += seg_evals;
         recomp += seg_recomp;
         wide += seg_wide;

@@ -395,3 +395,59 @@ def test_chunk_sizes_parity(arlib, orc, chunk):
     assert np.abs(glo - ref_lo).max() <= 2e-5 and np.abs(ghi - ref_hi).max() <= 2e-5
     for c in range(lo.shape[0]):
         compare(orc, sc, cam, lo[c], hi[c], glo[c], ghi[c], label="chunk %d cell %d" % (chunk, c))
+
+
+def test_depth_prefix_phases_are_bit_identical(arlib):
+    """Two-phase binning: the first phase bins each cell's first 1/2^s of its
+    depth-sorted events, segments that need more restart with full lists.
+    Every prefix (and the learned one) gives bounds bit-identical to one
+    phase, and a small prefix does restart segments."""
+    ar = arlib
+    w = synth.object10k()
+    lo, hi = w.cells_lo[:6], w.cells_hi[:6]
+    outs = {}
+    for shift in (0, 1, 3, 6, -1):
+        s = ar.Scene(w.scene)
+        ar.ar_set_profiling(s.handle, True)
+        ar.ar_debug_set_prefix(s.handle, shift)
+        out_lo = torch.full((len(lo), w.camera.height, w.camera.width, 3), -7.0, device="cuda")
+        out_hi = torch.full_like(out_lo, -7.0)
+        for _ in range(2):                     # the second render uses the learned prefix (shift -1)
+            s.render(w.camera, lo, hi, out_lo, out_hi, tile=16)
+        st = ar.ar_last_render_stats(s.handle)
+        torch.cuda.synchronize()
+        outs[shift] = (out_lo.cpu().numpy(), out_hi.cpu().numpy(), st)
+        s.close()
+    ref_lo, ref_hi, ref_st = outs[0]
+    assert ref_st["n_restarted"] <= 2
+    for shift, (o_lo, o_hi, st) in outs.items():
+        assert np.array_equal(o_lo, ref_lo) and np.array_equal(o_hi, ref_hi), shift
+        assert st["n_evaluated"] == ref_st["n_evaluated"], shift
+    assert outs[6][2]["n_restarted"] > 100      # the second phase did run
+    with pytest.raises(ar.ArError):
+        ar.ar_debug_set_prefix(None, 3)
+
+
+def test_depth_prefix_with_batches_and_scene_boxes(arlib):
+    """The prefix is per cell, so batch splits (a small workspace limit) and
+    scene-parameter boxes keep the bounds bit-identical too."""
+    ar = arlib
+    sc = synth.object_scene(3000, 12)
+    cam = synth.look_camera(60, 44, 70.0, centre=(0, 0, -4))
+    lo, hi = synth.cell_grid([0.03, 0.0, 0.03, 0.01, 0.0, 0.0], [2, 1, 2, 2, 1, 1])
+    res = []
+    for shift, limit in ((0, 0), (4, 0), (4, 4 << 20)):
+        s = ar.Scene(sc)
+        s.set_boxes(synth.scene_boxes(sc, 5, frac=0.3, red_add=0.2, mean_d=(0.01, 0.0, 0.0), opacity_scale=0.9,
+                                      opacity_add=0.05))
+        ar.ar_debug_set_prefix(s.handle, shift)
+        if limit:
+            ar.ar_set_workspace_limit(s.handle, limit)
+        out_lo = torch.empty((lo.shape[0], cam.height, cam.width, 3), device="cuda")
+        out_hi = torch.empty_like(out_lo)
+        s.render(cam, lo, hi, out_lo, out_hi, tile=16)
+        torch.cuda.synchronize()
+        res.append((out_lo.cpu().numpy(), out_hi.cpu().numpy()))
+        s.close()
+    for r in res[1:]:
+        assert np.array_equal(r[0], res[0][0]) and np.array_equal(r[1], res[0][1])
