@@ -354,6 +354,17 @@ int ar_debug_set_entry_cap(ar_scene *scene, int64_t cap);
  * it.  AR_EINVAL for a null scene or a shift outside [-1, 8]. */
 int ar_debug_set_prefix(ar_scene *scene, int32_t shift);
 
+/* Test hook: the cull before the FP64 decision part of the (Gaussian, cell)
+ * records.  With it on, a first pass drops, from FP32 enclosures of the
+ * FP64 values, the pairs certainly behind the near plane or outside the
+ * frustum guard band (the outcome the FP64 chain reaches for them) and lists
+ * the others, over which the FP64 chain then runs.  mode 1: always, 0: never,
+ * -1 (the default): while the previous render of the workspace found fewer
+ * than 3/4 of its pairs reaching a pixel.  ar_debug_records culls unless
+ * mode is 0.  The records do not depend on it.  AR_EINVAL for a null scene
+ * or another mode. */
+int ar_debug_set_cull(ar_scene *scene, int32_t mode);
+
 /* Device-memory limit (bytes, >= 1 MiB) for the scene's render workspace.
  * ar_render_abstract splits the cells of a call into batches whose
  * per-(Gaussian, cell) records take about a third of this limit, and runs the

@@ -81,6 +81,7 @@ def lib():
             "ar_debug_set_chunk": ([P, ctypes.c_int32], ctypes.c_int),
             "ar_debug_set_entry_cap": ([P, c_int64], ctypes.c_int),
             "ar_debug_set_prefix": ([P, c_int32], ctypes.c_int),
+            "ar_debug_set_cull": ([P, c_int32], ctypes.c_int),
             "ar_bounds_union": ([P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P], ctypes.c_int),
             "ar_partition_piece": ([P, P, c_int64, P], ctypes.c_int),
             "ar_render_abstract_refined": ([P, P, P, P, ctypes.c_int32, ctypes.c_int32, P, P, P, ctypes.c_int32, P, P],
@@ -286,6 +287,10 @@ def ar_debug_set_entry_cap(scene, cap: int):
 
 def ar_debug_set_prefix(scene, shift: int):
     return check(lib().ar_debug_set_prefix(scene, int(shift)))
+
+
+def ar_debug_set_cull(scene, mode: int):
+    return check(lib().ar_debug_set_cull(scene, int(mode)))
 
 
 def ar_last_render_stats(scene) -> dict:

@@ -69,12 +69,12 @@ int rec_scalar_offset_m6();
 int launch_cell_prep_m1(const double *, const double *, const CallConst &, void *, cudaStream_t);
 int launch_cell_prep_m4(const double *, const double *, const CallConst &, void *, cudaStream_t);
 int launch_cell_prep_m6(const double *, const double *, const CallConst &, void *, cudaStream_t);
-int launch_record_prep_m1(const double *, const void *, const CallConst &,
-                          const void *, int, float *, PixBox *, double *, unsigned long long *, cudaStream_t);
-int launch_record_prep_m4(const double *, const void *, const CallConst &,
-                          const void *, int, float *, PixBox *, double *, unsigned long long *, cudaStream_t);
-int launch_record_prep_m6(const double *, const void *, const CallConst &,
-                          const void *, int, float *, PixBox *, double *, unsigned long long *, cudaStream_t);
+int launch_record_prep_m1(const double *, const void *, const CallConst &, const void *, int, float *, PixBox *,
+                          double *, unsigned long long *, cudaStream_t, uint32_t *, uint32_t *);
+int launch_record_prep_m4(const double *, const void *, const CallConst &, const void *, int, float *, PixBox *,
+                          double *, unsigned long long *, cudaStream_t, uint32_t *, uint32_t *);
+int launch_record_prep_m6(const double *, const void *, const CallConst &, const void *, int, float *, PixBox *,
+                          double *, unsigned long long *, cudaStream_t, uint32_t *, uint32_t *);
 int launch_render_m1(int, const RenderLaunch &, cudaStream_t);
 int launch_render_m4(int, const RenderLaunch &, cudaStream_t);
 int launch_render_m6(int, const RenderLaunch &, cudaStream_t);
@@ -127,11 +127,11 @@ int launch_cell_prep(int M, const double *lo, const double *hi, const CallConst 
 }
 int launch_record_prep(int M, const double *vN, const void *gp,
                        const CallConst &cc, const void *cells, int TS, float *recs, PixBox *boxes, double *keys,
-                       unsigned long long *counters, cudaStream_t st)
+                       unsigned long long *counters, cudaStream_t st, uint32_t *list, uint32_t *count)
 {
-    if (M == 1) return launch_record_prep_m1(vN, gp, cc, cells, TS, recs, boxes, keys, counters, st);
-    if (M == 4) return launch_record_prep_m4(vN, gp, cc, cells, TS, recs, boxes, keys, counters, st);
-    return launch_record_prep_m6(vN, gp, cc, cells, TS, recs, boxes, keys, counters, st);
+    if (M == 1) return launch_record_prep_m1(vN, gp, cc, cells, TS, recs, boxes, keys, counters, st, list, count);
+    if (M == 4) return launch_record_prep_m4(vN, gp, cc, cells, TS, recs, boxes, keys, counters, st, list, count);
+    return launch_record_prep_m6(vN, gp, cc, cells, TS, recs, boxes, keys, counters, st, list, count);
 }
 int launch_render(int M, int TS, const RenderLaunch &a, cudaStream_t st)
 {
@@ -228,7 +228,7 @@ void DevBuf::release()
 void Workspace::append_pointers(std::vector<uint64_t> &key) const
 {
     const DevBuf *all[] = {&cells_lohi, &cells, &vN, &recs, &boxes, &keys, &counters, &evk0, &evk1, &evv0, &evv1,
-                           &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege, &segt, &cellev, &bwords, &smask, &ssat,
+                           &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege, &segt, &cellev, &bwords, &smask, &ssat, &clist,
                            &segk0, &segk1, &segv0, &segv1, &work, &state, &wlist, &act0, &act1, &words,
                            &slist, &plist, &pmask, &whist};
     for (const DevBuf *b : all) key.push_back((uint64_t)(uintptr_t)b->p);
@@ -241,7 +241,7 @@ void Workspace::release()
     if (cap_stream) cudaStreamDestroy(cap_stream);
     cap_stream = nullptr;
     DevBuf *all[] = {&cells_lohi, &cells, &vN, &recs, &boxes, &keys, &counters, &evk0, &evk1, &evv0, &evv1,
-                     &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege, &segt, &cellev, &bwords, &smask, &ssat, &segk0,
+                     &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege, &segt, &cellev, &bwords, &smask, &ssat, &clist, &segk0,
                      &segk1, &segv0, &segv1, &work, &state, &wlist, &act0, &act1, &words, &slist, &plist, &pmask, &whist, &out_lo,
                      &out_hi, &part_lo, &part_hi, &lvl_lo, &lvl_hi, &wpart};
     for (DevBuf *b : all) b->release();
@@ -257,7 +257,7 @@ void Workspace::release()
 size_t Workspace::bytes() const
 {
     const DevBuf *all[] = {&cells_lohi, &cells, &vN, &recs, &boxes, &keys, &counters, &evk0, &evk1, &evv0, &evv1,
-                           &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege, &segt, &cellev, &bwords, &smask, &ssat,
+                           &ents0, &ents1, &ente0, &ente1, &ua, &ub, &uc, &ud, &hist, &scan, &segs, &sege, &segt, &cellev, &bwords, &smask, &ssat, &clist,
                            &segk0, &segk1, &segv0, &segv1, &work, &state, &wlist, &act0, &act1, &words,
                            &slist, &plist, &pmask, &whist, &out_lo, &out_hi, &part_lo, &part_hi, &lvl_lo, &lvl_hi, &wpart};
     size_t s = 0;
@@ -441,6 +441,14 @@ int ar_scene_set_blend(ar_scene *s, int32_t mode)
     if (!s) return fail(AR_EINVAL, "scene is null");
     if (mode != AR_BLEND_INTERVAL && mode != AR_BLEND_RELATIONAL) return fail(AR_EINVAL, "unknown blend mode %d", mode);
     s->blend = mode;
+    return AR_OK;
+}
+
+int ar_debug_set_cull(ar_scene *s, int32_t mode)
+{
+    if (!s) return fail(AR_EINVAL, "scene is null");
+    if (mode < -1 || mode > 1) return fail(AR_EINVAL, "mode must be -1, 0 or 1");
+    s->cull_force = mode;
     return AR_OK;
 }
 
@@ -651,6 +659,9 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
     NvtxRange batch_range("ar.cell_batch");
     if (profiling) CK(cudaEventRecord(ev[0], st));
     CK(cudaMemsetAsync(ws.counters.p, 0, sizeof(unsigned long long) * 8, st));
+    // the certain drops culled first where the last render found many
+    const bool cull = !plain && (s->cull_force >= 0 ? s->cull_force == 1 : ws.cull_on);
+    if (cull) RK(ws.clist.ensure(sizeof(uint32_t) * (n_pairs + 1)));
     NvtxRange prep_range("ar.prep: cells and (Gaussian, cell) decisions");
     if (launch_cell_prep(M, d_lo, d_hi, cc, ws.cells.p, st)) return fail(AR_EDEVICE, "cell_prep launch");
     const int rp = plain ? launch_record_prep64(M, ws.vN.as<double>(), s->gp, cc, ws.cells.p, TS,
@@ -658,7 +669,9 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
                                                 ws.counters.as<unsigned long long>(), st)
                          : launch_record_prep(M, ws.vN.as<double>(), s->gp, cc, ws.cells.p, TS,
                                               ws.recs.as<float>(), ws.boxes.as<PixBox>(), ws.keys.as<double>(),
-                                              ws.counters.as<unsigned long long>(), st);
+                                              ws.counters.as<unsigned long long>(), st,
+                                              cull ? ws.clist.as<uint32_t>() : nullptr,
+                                              cull ? ws.clist.as<uint32_t>() + n_pairs : nullptr);
     if (rp) return fail(AR_EDEVICE, "record_prep launch: %s", cudaGetErrorString(cudaGetLastError()));
     launches += 2;
     if (profiling) CK(cudaEventRecord(ev[1], st));
@@ -667,6 +680,8 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
     prep_range.end();
     const unsigned long long n_valid = ws.h_counters[2];
     const uint64_t ne = 2 * n_valid, nent = 2 * ws.h_counters[3];
+    // culling pays where many pairs reach no pixel: here fewer than 3/4 do
+    if (!plain) ws.cull_on = n_valid * 4 < n_pairs * 3;
     if (ws.whist_pending) {
         // the previous render's histograms arrived with this synchronisation
         ws.w0 = learned_window(ws.h_whist);
@@ -1543,8 +1558,11 @@ int ar_debug_records(ar_scene *s, const ar_intrinsics *in, const ar_nominal_pose
     const double *d_lo = ws.cells_lohi.as<double>(), *d_hi = d_lo + MAXV;
     if (launch_pose_prep(s->uw_lo, s->uw_hi, s->Mw, s->n, cc, ws.vN.as<double>(), st) ||
         launch_cell_prep(M, d_lo, d_hi, cc, ws.cells.p, st) ||
+        (s->cull_force != 0 && ws.clist.ensure(sizeof(uint32_t) * (cc.n_gauss + 1)) != AR_OK) ||
         launch_record_prep(M, ws.vN.as<double>(), s->gp, cc, ws.cells.p, 16, ws.recs.as<float>(),
-                           ws.boxes.as<PixBox>(), ws.keys.as<double>(), ws.counters.as<unsigned long long>(), st))
+                           ws.boxes.as<PixBox>(), ws.keys.as<double>(), ws.counters.as<unsigned long long>(), st,
+                           s->cull_force != 0 ? ws.clist.as<uint32_t>() : nullptr,
+                           s->cull_force != 0 ? ws.clist.as<uint32_t>() + cc.n_gauss : nullptr))
         return fail(AR_EDEVICE, "record prep launch: %s", cudaGetErrorString(cudaGetLastError()));
     if (!out) return AR_OK;  // (ar_debug_alpha: the device records are what it needs)
     const int w = rec_width(M);

@@ -44,6 +44,12 @@ template <int M> struct CellData {
     double dx[3][3];
     double dd_t[M], kd_t[M];
     int n_t, n_a;
+    // FP32 enclosures ([lo, hi]) of the depth chain's per-cell values, for
+    // the early certain drops of the decision part
+    float dx32[3][3][2];       // of dx[b][k]
+    float s32[3][M + 1][2];    // of s[b][j]
+    float rdd32[3][2][M + 1][2];  // of rd_lo[3 b + 2][j] (0) and rd_hi[3 b + 2][j] (1)
+    float ddt32[M][2];         // of dd_t[j]
     SB<M, double> rd64[9];  // the same forms widened by a relative 1e-14 (sound in FP64)
     SB<M, double> s64[3];
 };

@@ -37,6 +37,8 @@ struct Workspace {
     DevBuf cells_lohi, cells, vN, recs, boxes, keys, counters;
     DevBuf evk0, evk1, evv0, evv1, ents0, ents1, ente0, ente1;
     DevBuf ua, ub, uc, ud, hist, scan, segs, sege, segk0, segk1, segv0, segv1, work;
+    DevBuf clist;                              // pairs left by the cull (then their count)
+    bool cull_on = true;                       // the last render found culling worth it
     DevBuf segt, cellev, bwords, smask, ssat;  // two-phase binning: full-list lengths, cell event ranges,
                                                // counts, active mask and its summed-area tables
     DevBuf state, wlist, act0, act1, words, slist;  // windowed rounds: pair states, build list, active segments
@@ -137,6 +139,9 @@ struct ar_scene {
     // depth prefix of the first binning phase: -1 learned per workspace, else
     // the shift (0: one phase); set by ar_debug_set_prefix for tests
     int prefix_force = -1;
+    // culling of the certain drops before the FP64 decision chain: -1 chosen
+    // per workspace, 0 off, 1 on; set by ar_debug_set_cull for tests
+    int cull_force = -1;
     float fp64_dev = AR_FP64_ALPHA_DEFAULT;  // FP64 re-evaluation threshold (ar_scene_set_fp64_alpha)
     ar_render_stats stats;
     cudaStream_t stats_stream = nullptr;

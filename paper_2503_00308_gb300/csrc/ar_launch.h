@@ -54,9 +54,12 @@ struct RenderLaunch {
 size_t cell_data_bytes(int M);
 int rec_width(int M);
 int launch_cell_prep(int M, const double *lo, const double *hi, const CallConst &cc, void *cells, cudaStream_t st);
+// list, count (optional): cull the certain drops first and run the FP64
+// decision chain over the list of the other pairs (cull_kernel)
 int launch_record_prep(int M, const double *vN, const void *gp,
                        const CallConst &cc, const void *cells, int TS, float *recs, PixBox *boxes, double *keys,
-                       unsigned long long *counters, cudaStream_t st);
+                       unsigned long long *counters, cudaStream_t st, uint32_t *list = nullptr,
+                       uint32_t *count = nullptr);
 int launch_render(int M, int TS, const RenderLaunch &a, cudaStream_t st);
 int launch_record_prep64(int M, const double *vN, const void *gp,
                          const CallConst &cc, const void *cells, int TS, double *recs, PixBox *boxes, double *keys,

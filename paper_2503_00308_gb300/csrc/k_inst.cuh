@@ -24,13 +24,27 @@ int AR_CAT(launch_cell_prep_m, AR_M)(const double *lo, const double *hi, const C
 int AR_CAT(launch_record_prep_m, AR_M)(const double *vN, const void *gp,
                                        const CallConst &cc, const void *cells, int TS, float *recs,
                                        PixBox *boxes, double *keys, unsigned long long *counters,
-                                       cudaStream_t st)
+                                       cudaStream_t st, uint32_t *list, uint32_t *count)
 {
     const int T = 128;
     dim3 grid((unsigned)((cc.n_gauss + T - 1) / T), (unsigned)cc.n_cells);
+    const CellData<AR_M> *cd = (const CellData<AR_M> *)cells;
     // decision part only: the value parts are built by the renderer on demand
-    record_prep_kernel<AR_M, float, false><<<grid, T, 0, st>>>(vN, (const GParam *)gp, cc, (const CellData<AR_M> *)cells,
-                                                               TS, recs, boxes, keys, counters);
+    if (!list) {
+        record_prep_kernel<AR_M, float, false><<<grid, T, 0, st>>>(vN, (const GParam *)gp, cc, cd, TS, recs, boxes,
+                                                                   keys, counters);
+        return cudaGetLastError() == cudaSuccess ? 0 : 1;
+    }
+    if (cudaMemsetAsync(count, 0, sizeof(uint32_t), st) != cudaSuccess) return 1;
+    cull_kernel<AR_M><<<grid, T, 0, st>>>(vN, (const GParam *)gp, cc, cd, boxes, list, count);
+    const uint64_t pairs = (uint64_t)cc.n_gauss * (uint64_t)cc.n_cells;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    uint64_t lg = (pairs + T - 1) / T;
+    if (lg > (uint64_t)sms * 32u) lg = (uint64_t)sms * 32u;
+    record_prep_list_kernel<AR_M, float, false><<<(unsigned)(lg ? lg : 1), T, 0, st>>>(
+        vN, (const GParam *)gp, cc, cd, TS, recs, boxes, keys, counters, list, count);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 

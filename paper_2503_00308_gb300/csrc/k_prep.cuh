@@ -178,6 +178,19 @@ __global__ void cell_prep_kernel(const double *__restrict__ cells_lo, const doub
             }
         }
         for (int j = 0; j < M; ++j) cd.kd_t[j] = dsub(cd.dd_t[j], cd.g[j]);
+        auto enc = [](double x, float *o) {
+            o[0] = __double2float_rd(x);
+            o[1] = __double2float_ru(x);
+        };
+        for (int b = 0; b < 3; ++b) {
+            for (int k = 0; k < 3; ++k) enc(cd.dx[b][k], cd.dx32[b][k]);
+            for (int j = 0; j <= M; ++j) {
+                enc(cd.s[b][j], cd.s32[b][j]);
+                enc(cd.rd_lo[3 * b + 2][j], cd.rdd32[b][0][j]);
+                enc(cd.rd_hi[3 * b + 2][j], cd.rdd32[b][1][j]);
+            }
+        }
+        for (int j = 0; j < M; ++j) enc(cd.dd_t[j], cd.ddt32[j]);
     }
     // FP64 value-chain copies, widened to cover the rounding of sin, cos and
     // the Taylor terms (a relative 1e-14 is far above their few-ulp error);
@@ -349,6 +362,117 @@ static __device__ __noinline__ int screen_fp64(const double (*rd_int)[2], const 
     return SCREEN_KEEP;
 }
 
+// The enclosures screen_fp32 starts from: the concretised R_delta entries
+// and v - s (enc: the enclosures of v_lo, v_hi, N that pose_prep_kernel
+// stored)
+template <int M>
+__device__ __forceinline__ void screen_inputs_fp32(const CellData<M> &cd, const float *enc, EI *Ri, EI *vs, bool &ok)
+{
+    for (int e = 0; e < 9; ++e)
+        Ri[e] = EI{E32{cd.rd_int32[e][0][0], cd.rd_int32[e][0][1]}, E32{cd.rd_int32[e][1][0], cd.rd_int32[e][1][1]}};
+    for (int b = 0; b < 3; ++b)
+        vs[b] = EI{e_chk(e_sub(E32{enc[2 * b], enc[2 * b + 1]}, E32{cd.s_int32[b][1][0], cd.s_int32[b][1][1]}), ok),
+                   e_chk(e_sub(E32{enc[6 + 2 * b], enc[7 + 2 * b]}, E32{cd.s_int32[b][0][0], cd.s_int32[b][0][1]}),
+                         ok)};
+}
+
+// The first decisions of screen_fp32, from enclosures D of the depth ends
+// (max(d_lo, near), d_hi): the camera-frame x, y and the projected mean's
+// interval (ucx, ucy, mux, muy), then the frustum guard band: SCREEN_DROP,
+// SCREEN_KEEP inside the band, SCREEN_STRADDLE across it, or
+// SCREEN_UNDECIDED where the enclosures do not settle it.
+enum { SCREEN_STRADDLE = 3 };
+template <int M>
+__device__ __forceinline__ int screen_guard_fp32(const CellData<M> &cd, const EI *Ri, const EI *vs, const EI &D,
+                                                 const CallConst &cc, EI &ucx, EI &ucy, EI &mux, EI &muy, bool &ok)
+{
+    ucx = ei_add(ei_add(ei_mul(Ri[0], vs[0], ok), ei_mul(Ri[3], vs[1], ok), ok), ei_mul(Ri[6], vs[2], ok), ok);
+    ucy = ei_add(ei_add(ei_mul(Ri[1], vs[0], ok), ei_mul(Ri[4], vs[1], ok), ok), ei_mul(Ri[7], vs[2], ok), ok);
+    // the intrinsics are floats: exact
+    const E32 fx = {cc.fx, cc.fx}, fy = {cc.fy, cc.fy}, cx = {cc.cx, cc.cx}, cy = {cc.cy, cc.cy};
+    // u / D_hi or u / D_lo by the sign of u; where the sign is not settled,
+    // the enclosure of either quotient
+    auto qlo = [&](E32 u) {
+        const E32 a = e_div_pos(u, D.u), b = e_div_pos(u, D.l);
+        return u.lo >= 0.f ? a : (u.hi < 0.f ? b : e_hull(a, b));
+    };
+    auto qhi = [&](E32 u) {
+        const E32 a = e_div_pos(u, D.l), b = e_div_pos(u, D.u);
+        return u.lo >= 0.f ? a : (u.hi < 0.f ? b : e_hull(a, b));
+    };
+    mux = EI{e_chk(e_add(cx, e_mul(fx, qlo(ucx.l))), ok), e_chk(e_add(cx, e_mul(fx, qhi(ucx.u))), ok)};
+    muy = EI{e_chk(e_add(cy, e_mul(fy, qlo(ucy.l))), ok), e_chk(e_add(cy, e_mul(fy, qhi(ucy.u))), ok)};
+    if (!ok) return SCREEN_UNDECIDED;
+    const E32 one = {1.f, 1.f}, slack = {cd.slack32[0], cd.slack32[1]};
+    auto widen_dn = [&](E32 x) { return e_sub(x, e_mul(slack, e_add(one, e_abs(x)))); };
+    auto widen_up = [&](E32 x) { return e_add(x, e_mul(slack, e_add(one, e_abs(x)))); };
+    const E32 cxp = {cd.guard32[0][0], cd.guard32[0][1]}, cxm = {cd.guard32[1][0], cd.guard32[1][1]};
+    const E32 cyp = {cd.guard32[2][0], cd.guard32[2][1]}, cym = {cd.guard32[3][0], cd.guard32[3][1]};
+    const E32 ml = widen_dn(mux.l), mh = widen_up(mux.u), nl = widen_dn(muy.l), nh = widen_up(muy.u);
+    // drop: ml > cx + gx || mh < cx - gx || nl > cy + gy || nh < cy - gy
+    const int d0 = e_gt(ml, cxp), d1 = e_gt(cxm, mh), d2 = e_gt(nl, cyp), d3 = e_gt(cym, nh);
+    if (d0 == 1 || d1 == 1 || d2 == 1 || d3 == 1) return SCREEN_DROP;
+    if (d0 < 0 || d1 < 0 || d2 < 0 || d3 < 0) return SCREEN_UNDECIDED;
+    // inside: ml >= cx - gx && mh <= cx + gx && nl >= cy - gy && nh <= cy + gy
+    const int i0 = e_ge(ml, cxm), i1 = e_ge(cxp, mh), i2 = e_ge(nl, cym), i3 = e_ge(cyp, nh);
+    if (i0 < 0 || i1 < 0 || i2 < 0 || i3 < 0) return SCREEN_UNDECIDED;
+    return (i0 && i1 && i2 && i3) ? SCREEN_KEEP : SCREEN_STRADDLE;
+}
+
+// FP32 enclosures of the depth chain's ends dlo, dhi (record_decide), step
+// for step on enclosures of its operands; ok is cleared where a value leaves
+// the checked range or a sign the chain branches on is not settled.  Every
+// FP64 result of the chain, rounded to nearest, lies in these enclosures.
+template <int M>
+__device__ __forceinline__ void depth_fp32(const CellData<M> &cd, const float *enc, E32 &dlo, E32 &dhi, bool &ok)
+{
+    const int n_t = cd.n_t, n_a = cd.n_a;
+    const E32 half = {0.5f, 0.5f};
+    auto E = [](const float *p) { return E32{p[0], p[1]}; };
+    E32 ddr[M];
+    E32 dlk = {0.f, 0.f}, dhk = {0.f, 0.f};
+    for (int b = 0; b < 3; ++b) {
+        const E32 xl = E(cd.dx32[b][0]), xh = E(cd.dx32[b][1]), xm = E(cd.dx32[b][2]);
+        const E32 ylk = e_sub(E32{enc[2 * b], enc[2 * b + 1]}, E(cd.s32[b][M]));
+        const E32 yhk = e_sub(E32{enc[6 + 2 * b], enc[7 + 2 * b]}, E(cd.s32[b][M]));
+        E32 yl = ylk, yh = yhk;
+        for (int j = 0; j < n_t; ++j) {
+            yl = e_sub(yl, e_abs(E(cd.s32[b][j])));
+            yh = e_add(yh, e_abs(E(cd.s32[b][j])));
+        }
+        const E32 ym = e_mul(half, e_add(yl, yh));
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+            if (j < n_t || j >= n_a) continue;
+            const E32 t = e_mul(ym, E(cd.rdd32[b][0][j]));
+            ddr[j] = b == 0 ? t : e_add(ddr[j], t);
+        }
+        // the chain branches on ym >= 0 and xm >= 0 (xm: rounding down keeps the sign)
+        if (!(ym.lo >= 0.f) && !(ym.hi < 0.f)) {
+            ok = false;
+            return;
+        }
+        const bool yp = ym.lo >= 0.f, xp = xm.lo >= 0.f;
+        E32 lk = e_add(e_mul(ym, E(cd.rdd32[b][yp ? 0 : 1][M])), e_mul(xm, xp ? ylk : yhk));
+        lk = e_sub(lk, e_mul(half, e_add(e_mul(xl, yl), e_mul(xh, yh))));
+        E32 hk = e_add(e_mul(ym, E(cd.rdd32[b][yp ? 1 : 0][M])), e_mul(xm, xp ? yhk : ylk));
+        hk = e_sub(hk, e_mul(half, e_add(e_mul(xh, yl), e_mul(xl, yh))));
+        dlk = b == 0 ? lk : e_add(dlk, lk);
+        dhk = b == 0 ? hk : e_add(dhk, hk);
+    }
+    dlo = dlk;
+    dhi = dhk;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        if (j >= n_a) continue;
+        const E32 c = e_abs(j < n_t ? E(cd.ddt32[j]) : ddr[j]);
+        dlo = e_sub(dlo, c);
+        dhi = e_add(dhi, c);
+    }
+    e_chk(dlo, ok);
+    e_chk(dhi, ok);
+}
+
 // The same decisions from FP32 enclosures (E32) of every FP64 value above,
 // step for step: where each comparison, ceil and floor of screen_fp64 is
 // settled by the enclosures, it has the same outcome as in FP64; otherwise
@@ -363,51 +487,20 @@ __device__ __forceinline__ int screen_fp32(const CellData<M> &cd, const float *e
     bool ok = true;
     const double nearp = (double)cc.near_plane;
     EI Ri[9], vs[3];
-    for (int e = 0; e < 9; ++e)
-        Ri[e] = EI{E32{cd.rd_int32[e][0][0], cd.rd_int32[e][0][1]}, E32{cd.rd_int32[e][1][0], cd.rd_int32[e][1][1]}};
-    for (int b = 0; b < 3; ++b) {
-        // enc: the enclosures of v_lo, v_hi, N that pose_prep_kernel stored
-        vs[b] = EI{e_chk(e_sub(E32{enc[2 * b], enc[2 * b + 1]}, E32{cd.s_int32[b][1][0], cd.s_int32[b][1][1]}), ok),
-                   e_chk(e_sub(E32{enc[6 + 2 * b], enc[7 + 2 * b]}, E32{cd.s_int32[b][0][0], cd.s_int32[b][0][1]}),
-                         ok)};
-    }
+    screen_inputs_fp32(cd, enc, Ri, vs, ok);
     E32 Ne[9];
     for (int i = 0; i < 9; ++i) Ne[i] = E32{enc[12 + 2 * i], enc[13 + 2 * i]};
     const double dl = fmax(dlo, nearp);
     const EI D = {e_of(dl), e_of(dhi)};
-    const EI ucx = ei_add(ei_add(ei_mul(Ri[0], vs[0], ok), ei_mul(Ri[3], vs[1], ok), ok), ei_mul(Ri[6], vs[2], ok), ok);
-    const EI ucy = ei_add(ei_add(ei_mul(Ri[1], vs[0], ok), ei_mul(Ri[4], vs[1], ok), ok), ei_mul(Ri[7], vs[2], ok), ok);
-    // the intrinsics are floats: exact
-    const E32 fx = {cc.fx, cc.fx}, fy = {cc.fy, cc.fy}, cx = {cc.cx, cc.cx}, cy = {cc.cy, cc.cy};
-    // u / D_hi or u / D_lo by the sign of u; where the sign is not settled,
-    // the enclosure of either quotient
-    auto qlo = [&](E32 u) {
-        const E32 a = e_div_pos(u, D.u), b = e_div_pos(u, D.l);
-        return u.lo >= 0.f ? a : (u.hi < 0.f ? b : e_hull(a, b));
-    };
-    auto qhi = [&](E32 u) {
-        const E32 a = e_div_pos(u, D.l), b = e_div_pos(u, D.u);
-        return u.lo >= 0.f ? a : (u.hi < 0.f ? b : e_hull(a, b));
-    };
-    const EI mux = {e_chk(e_add(cx, e_mul(fx, qlo(ucx.l))), ok), e_chk(e_add(cx, e_mul(fx, qhi(ucx.u))), ok)};
-    const EI muy = {e_chk(e_add(cy, e_mul(fy, qlo(ucy.l))), ok), e_chk(e_add(cy, e_mul(fy, qhi(ucy.u))), ok)};
-    if (!ok) return SCREEN_UNDECIDED;
+    EI ucx, ucy, mux, muy;
+    const int g = screen_guard_fp32(cd, Ri, vs, D, cc, ucx, ucy, mux, muy, ok);
+    if (g == SCREEN_DROP) return SCREEN_DROP;
+    if (g == SCREEN_UNDECIDED) return SCREEN_UNDECIDED;
+    if (g == SCREEN_STRADDLE) straddle = true;
+    const E32 fx = {cc.fx, cc.fx}, fy = {cc.fy, cc.fy};
     const E32 one = {1.f, 1.f}, slack = {cd.slack32[0], cd.slack32[1]};
     auto widen_dn = [&](E32 x) { return e_sub(x, e_mul(slack, e_add(one, e_abs(x)))); };
     auto widen_up = [&](E32 x) { return e_add(x, e_mul(slack, e_add(one, e_abs(x)))); };
-    {
-        const E32 cxp = {cd.guard32[0][0], cd.guard32[0][1]}, cxm = {cd.guard32[1][0], cd.guard32[1][1]};
-        const E32 cyp = {cd.guard32[2][0], cd.guard32[2][1]}, cym = {cd.guard32[3][0], cd.guard32[3][1]};
-        const E32 ml = widen_dn(mux.l), mh = widen_up(mux.u), nl = widen_dn(muy.l), nh = widen_up(muy.u);
-        // drop: ml > cx + gx || mh < cx - gx || nl > cy + gy || nh < cy - gy
-        const int d0 = e_gt(ml, cxp), d1 = e_gt(cxm, mh), d2 = e_gt(nl, cyp), d3 = e_gt(cym, nh);
-        if (d0 == 1 || d1 == 1 || d2 == 1 || d3 == 1) return SCREEN_DROP;
-        if (d0 < 0 || d1 < 0 || d2 < 0 || d3 < 0) return SCREEN_UNDECIDED;
-        // inside: ml >= cx - gx && mh <= cx + gx && nl >= cy - gy && nh <= cy + gy
-        const int i0 = e_ge(ml, cxm), i1 = e_ge(cxp, mh), i2 = e_ge(nl, cym), i3 = e_ge(cyp, nh);
-        if (i0 < 0 || i1 < 0 || i2 < 0 || i3 < 0) return SCREEN_UNDECIDED;
-        if (!(i0 && i1 && i2 && i3)) straddle = true;
-    }
     E32 X00 = {0.f, 0.f}, X11 = {0.f, 0.f};
     for (int c = 0; c < 3; ++c) {
         EI m[3];
@@ -1057,6 +1150,92 @@ __global__ void __launch_bounds__(128) record_prep_kernel(
         if (v) atomicAdd(&counters[2], (unsigned long long)v);
         if (e) atomicAdd(&counters[3], (unsigned long long)e);
         if (sp) atomicAdd(&counters[4], (unsigned long long)sp);
+    }
+}
+
+// The certain drops of the decision part, from FP32 enclosures (depth_fp32,
+// screen_guard_fp32): a pair whose opacity stays below the cutoff, whose
+// depth lies behind the near plane, or whose projected mean lies outside the
+// frustum guard band over the whole cell gets an absent box and no record,
+// as the FP64 chain would decide; the other pairs are listed (in no
+// particular order) for record_prep_list_kernel, so that its warps run the
+// FP64 chain on full warps of pairs that need it.
+template <int M>
+__global__ void __launch_bounds__(128) cull_kernel(const double *__restrict__ vN, const GParam *__restrict__ gp,
+                                                   CallConst cc, const CellData<M> *__restrict__ cells,
+                                                   PixBox *__restrict__ boxes, uint32_t *__restrict__ list,
+                                                   uint32_t *__restrict__ count)
+{
+    const int cell = blockIdx.y;
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool keep = false;
+    const int64_t ri = (int64_t)cell * cc.n_gauss + g;
+    if (g < cc.n_gauss) {
+        boxes[ri] = PixBox{-1, -1, -1, -1};
+        keep = gp[g].tau_hi >= 0;  // else o < 1/255: never above the cutoff
+        if (keep) {
+            const CellData<M> &cd = cells[cell];
+            const float *enc = reinterpret_cast<const float *>(vN + VN_STRIDE * g + VN_ENC);
+            bool ok = true;
+            E32 el, eh;
+            depth_fp32<M>(cd, enc, el, eh, ok);
+            const float nearf = cc.near_plane;
+            if (ok && eh.hi <= nearf) keep = false;  // d_hi <= near: behind the near plane
+            if (ok && keep && eh.lo > nearf) {
+                EI Ri[9], vs[3], ucx, ucy, mux, muy;
+                screen_inputs_fp32(cd, enc, Ri, vs, ok);
+                const EI D = {E32{fmaxf(el.lo, nearf), fmaxf(el.hi, nearf)}, eh};
+                if (ok && screen_guard_fp32(cd, Ri, vs, D, cc, ucx, ucy, mux, muy, ok) == SCREEN_DROP) keep = false;
+            }
+        }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (m) {
+        const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+        uint32_t at = 0;
+        if (lane == leader) at = atomicAdd(count, (uint32_t)__popc(m));
+        at = __shfl_sync(0xffffffffu, at, leader);
+        if (keep) list[at + __popc(m & ((1u << lane) - 1u))] = (uint32_t)ri;
+    }
+}
+
+// record_prep_kernel over the pairs cull_kernel listed (grid-stride; the
+// count is read on the device)
+template <int M, class RO, bool VALUE>
+__global__ void __launch_bounds__(128) record_prep_list_kernel(
+    const double *__restrict__ vN, const GParam *__restrict__ gp, CallConst cc,
+    const CellData<M> *__restrict__ cells, int TS, RO *__restrict__ recs, PixBox *__restrict__ boxes,
+    double *__restrict__ keys, unsigned long long *__restrict__ counters, const uint32_t *__restrict__ list,
+    const uint32_t *__restrict__ count)
+{
+    const uint32_t n = *count;
+    unsigned long long acc[5] = {0, 0, 0, 0, 0};  // a thread takes several pairs: 64-bit sums
+    for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        if (i >= n) continue;
+        const int64_t ri = list[i];
+        const int cell = (int)(ri / cc.n_gauss);
+        const int64_t g = ri - (int64_t)cell * cc.n_gauss;
+        PrepCount pc = {0, 0, 0, 0, 0};
+        const int64_t fl = record_decide<M, RO>(vN, gp, cc, cells[cell], cell, g, TS, recs, boxes, keys, pc);
+        if (VALUE && fl >= 0) {
+            RO *rec = recs + ri * Rec<M>::WIDTH;
+            const uint32_t f = record_value<M, RO>(vN + VN_STRIDE * g, cc.fx, cc.fy, cc.cx, cc.cy, cells[cell],
+                                                   rec[Rec<M>::MU_X], rec[Rec<M>::MU_Y], (uint32_t)fl, rec);
+            pc.fallback = (f & F_FALLBACK) ? 1u : 0u;
+            pc.split = (f & F_SPLIT) ? 1u : 0u;
+        }
+        acc[0] += pc.triples;
+        acc[1] += pc.fallback;
+        acc[2] += pc.valid;
+        acc[3] += pc.tiles;
+        acc[4] += pc.split;
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+#pragma unroll
+        for (int d = 16; d; d >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], d);
+        if ((threadIdx.x & 31) == 0 && acc[k]) atomicAdd(&counters[k], acc[k]);
     }
 }
 

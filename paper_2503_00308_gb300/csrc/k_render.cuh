@@ -509,8 +509,33 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
         // each warp covers an 8 x 4 block of the tile, so that the pixel boxes
         // of small Gaussians cut fewer warps and warps finish together
         const int wb = tid >> 5, ln = tid & 31;
-        const int px = tx * TS + (wb % (TS / 8)) * 8 + (ln & 7);
-        const int py = ty * TS + (wb / (TS / 8)) * 4 + (ln >> 3);
+        // the pixel this thread sweeps, by its thread index in the FP32
+        // sweep's layout; the FP64 instance packs the listed pixels onto its
+        // first threads (the rank of tid among the mask's set bits), so that
+        // they share few warps
+        int pid = tid;
+        bool active = true;
+        if (F64) {
+            const uint32_t *pm = precise_mask + (size_t)wk * (NT / 32);
+            int rem = tid;
+            pid = -1;
+#pragma unroll
+            for (int w = 0; w < NT / 32; ++w) {
+                uint32_t m = pm[w];
+                const int c = __popc(m);
+                if (pid < 0 && rem < c) {
+                    for (int k = 0; k < rem; ++k) m &= m - 1u;
+                    pid = w * 32 + __ffs(m) - 1;
+                } else if (pid < 0) {
+                    rem -= c;
+                }
+            }
+            active = pid >= 0;
+            if (!active) pid = tid;  // a position of the tile; the thread sweeps nothing
+        }
+        const int pwb = pid >> 5, pln = pid & 31;
+        const int px = tx * TS + (pwb % (TS / 8)) * 8 + (pln & 7);
+        const int py = ty * TS + (pwb / (TS / 8)) * 4 + (pln >> 3);
         const bool inside = px < W && py < H;
         const float ux = px + 0.5f, uy = py + 0.5f;
         const uint32_t b0 = seg_start[seg], b1 = seg_end[seg];
@@ -545,8 +570,6 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
         for (int k = 0; k < RING; ++k) s_rid[k * NT + tid] = 0xffffffffu;
         uint32_t head = 0;
         // the FP64 instance sweeps only the pixels the FP32 sweep listed
-        const bool active = F64 ? ((precise_mask[(size_t)wk * (NT / 32) + (tid >> 5)] >> (tid & 31)) & 1u) != 0u
-                                : true;
         bool done = !inside || !active;
         float lo_adj = 0.f, hi_adj = 0.f;  // -1: decided 0 / 1; >= 0: widening for skipped events
         bool abandoned = false;

@@ -451,3 +451,31 @@ def test_depth_prefix_with_batches_and_scene_boxes(arlib):
         s.close()
     for r in res[1:]:
         assert np.array_equal(r[0], res[0][0]) and np.array_equal(r[1], res[0][1])
+
+
+def test_cull_before_decisions_is_bit_identical(arlib):
+    """The cull of certain drops before the FP64 decision chain changes no
+    record and no bound: a camera inside the scene (half the Gaussians behind
+    the near plane, many outside the guard band) rendered with the cull always
+    on, always off and chosen per workspace."""
+    ar = arlib
+    w = synth.unbounded750k(n=30_000, width=320, height=180, f=225.0, splits=(2, 1, 2, 1, 1, 1))
+    outs = []
+    for mode in (0, 1, -1):
+        s = ar.Scene(w.scene)
+        ar.ar_debug_set_cull(s.handle, mode)
+        ar.ar_set_profiling(s.handle, True)
+        out_lo = torch.full((w.n_cells, w.camera.height, w.camera.width, 3), -7.0, device="cuda")
+        out_hi = torch.full_like(out_lo, -7.0)
+        for _ in range(2):
+            s.render(w.camera, w.cells_lo, w.cells_hi, out_lo, out_hi, tile=16)
+        st = ar.ar_last_render_stats(s.handle)
+        torch.cuda.synchronize()
+        recs = s.debug_records(w.camera, w.cells_lo[0], w.cells_hi[0])
+        outs.append((out_lo.cpu().numpy(), out_hi.cpu().numpy(), st, recs))
+        s.close()
+    assert outs[0][2]["n_records"] < 0.5 * 30_000 * w.n_cells   # most pairs reach no pixel
+    for o in outs[1:]:
+        assert np.array_equal(o[0], outs[0][0]) and np.array_equal(o[1], outs[0][1])
+        assert o[2]["n_records"] == outs[0][2]["n_records"] and o[2]["n_entries"] == outs[0][2]["n_entries"]
+        assert np.array_equal(o[3], outs[0][3])
