@@ -52,13 +52,14 @@ BOOKKEEPING_FLOPS_PER_TRIPLE = 156
 
 
 # DRAM bytes of the render kernel per opacity evaluation, from an ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum) of the first 4 cells of the
-# 300k-Gaussian workload: 43.8 MB over 73.0M evaluations.  Valid only for the
-# kernel sources it was taken from (their SHA-256 below); otherwise the
-# roofline's traffic is reported as null.
-RENDER_TRAFFIC = {"bytes_per_evaluation": (30896896 + 12922112) / 73014342,
+# (dram__bytes_read.sum + dram__bytes_write.sum) of round 0 of the first 4
+# cells of the 300k-Gaussian workload, both instances (FP32 sweep 37.1 MB, FP64
+# re-sweep 13.7 MB) over 73.2M evaluations.  Valid only for the kernel
+# sources it was taken from (their SHA-256 below); otherwise the roofline's
+# traffic is reported as null.
+RENDER_TRAFFIC = {"bytes_per_evaluation": (28485632 + 8572672 + 13522176 + 141056) / 73160149,
                   "sources": ["k_render.cuh", "ar_num.cuh", "ar_common.cuh", "k_inst.cuh"],
-                  "sha256": "756d67ef4afa7d5f0c442fae7aaba8f751e2b434b7dae497b72e7dbb2d16afdf"}
+                  "sha256": "fb6de62c9629d4b87d439b32822a5b363cb3e0230c9d5b8236771632b5715d20"}
 
 
 def render_traffic(n_evaluated: int):
