@@ -32,8 +32,9 @@ struct BinArgs {
     // run_rebin bins the full lists of the segments that need them.
     int prefix_shift = 0;
     uint32_t *cell_ev = nullptr;    // [n_cells + 1] first sorted event of each cell
+    uint32_t *pref_start = nullptr; // [n_cells + 1] first index of each cell's prefix events (compacted)
     uint32_t *seg_total = nullptr;  // [n_segments]
-    uint32_t *words = nullptr;      // [2] entry counts known on the device only
+    uint32_t *words = nullptr;      // [4] counts known on the device only (entries of each phase, prefix events)
     uint32_t *mask = nullptr;       // [(n_segments + 31) / 32] active segments of the second phase
     uint32_t *sat = nullptr;        // [n_cells][(nty + 1) (ntx + 1)] their summed-area tables
 };

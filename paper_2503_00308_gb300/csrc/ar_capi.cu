@@ -564,7 +564,7 @@ static int bin_pairs(Workspace &ws, const PixBox *boxes, const double *keys, uin
     RK(ws.segv1.ensure(sizeof(uint32_t) * n_seg));
     RK(ws.work.ensure(256));
     if (ba_out) {
-        RK(ws.cellev.ensure(sizeof(uint32_t) * (n_cells + 1)));
+        RK(ws.cellev.ensure(sizeof(uint32_t) * 2 * (n_cells + 1)));
         RK(ws.bwords.ensure(sizeof(uint32_t) * 4));
     }
     if (shift > 0) {
@@ -597,6 +597,7 @@ static int bin_pairs(Workspace &ws, const PixBox *boxes, const double *keys, uin
     ba.seg_v[0] = ws.segv0.as<uint32_t>(); ba.seg_v[1] = ws.segv1.as<uint32_t>();
     if (ba_out) {
         ba.cell_ev = ws.cellev.as<uint32_t>();
+        ba.pref_start = ba.cell_ev + (n_cells + 1);
         ba.words = ws.bwords.as<uint32_t>();
     }
     if (shift > 0) {

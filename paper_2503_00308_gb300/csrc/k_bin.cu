@@ -55,10 +55,24 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s
     return excl;
 }
 
+// The length of a scanned array known on the device only: mul ceil(*p /
+// div) words, at most the host's bound (p null: the host's length).
+struct DevLen {
+    const uint32_t *p = nullptr;
+    uint32_t mul = 1, div = 1;
+};
+__device__ __forceinline__ uint32_t dev_len(DevLen d, uint32_t n)
+{
+    if (!d.p) return n;
+    const uint64_t w = (uint64_t)d.mul * (((uint64_t)*d.p + d.div - 1) / d.div);
+    return w < n ? (uint32_t)w : n;
+}
+
 __global__ void __launch_bounds__(SC_THREADS) scan_sums_kernel(const uint32_t *__restrict__ in, uint32_t n,
-                                                               uint32_t *__restrict__ sums)
+                                                               uint32_t *__restrict__ sums, DevLen dl)
 {
     __shared__ uint32_t s_warp[32];
+    n = dev_len(dl, n);
     const uint64_t base = (uint64_t)blockIdx.x * SC_TILE + (uint64_t)threadIdx.x * SC_IPT;
     uint32_t t = 0;
 #pragma unroll
@@ -71,9 +85,11 @@ __global__ void __launch_bounds__(SC_THREADS) scan_sums_kernel(const uint32_t *_
 
 __global__ void __launch_bounds__(SC_THREADS) scan_apply_kernel(const uint32_t *__restrict__ in, uint32_t n,
                                                                 const uint32_t *__restrict__ offs,
-                                                                uint32_t *__restrict__ out)
+                                                                uint32_t *__restrict__ out, DevLen dl)
 {
     __shared__ uint32_t s_warp[32];
+    n = dev_len(dl, n);
+    if ((uint64_t)blockIdx.x * SC_TILE >= n) return;  // uniform over the block
     const uint64_t base = (uint64_t)blockIdx.x * SC_TILE + (uint64_t)threadIdx.x * SC_IPT;
     uint32_t v[SC_IPT];
     uint32_t t = 0;
@@ -101,22 +117,30 @@ size_t scan_temp_words(uint64_t n)
     return w + 2;
 }
 
-// exclusive scan of n words (in may equal out); tmp from scan_temp_words
-void exclusive_scan(const uint32_t *in, uint32_t *out, uint64_t n, uint32_t *tmp, cudaStream_t st, int *launches)
+// exclusive scan of n words (in may equal out); tmp from scan_temp_words.
+// dl: the length on the device (n its bound); the words past it are neither
+// read nor written.
+static void exclusive_scan_dl(const uint32_t *in, uint32_t *out, uint64_t n, uint32_t *tmp, cudaStream_t st,
+                              int *launches, DevLen dl)
 {
     if (n == 0) return;
     const uint64_t nb = (n + SC_TILE - 1) / SC_TILE;
     if (nb == 1) {
-        scan_apply_kernel<<<1, SC_THREADS, 0, st>>>(in, (uint32_t)n, nullptr, out);
+        scan_apply_kernel<<<1, SC_THREADS, 0, st>>>(in, (uint32_t)n, nullptr, out, dl);
         ++*launches;
         return;
     }
     uint32_t *sums = tmp, *offs = tmp + nb;
-    scan_sums_kernel<<<(unsigned)nb, SC_THREADS, 0, st>>>(in, (uint32_t)n, sums);
+    scan_sums_kernel<<<(unsigned)nb, SC_THREADS, 0, st>>>(in, (uint32_t)n, sums, dl);
     ++*launches;
-    exclusive_scan(sums, offs, nb, tmp + 2 * nb, st, launches);
-    scan_apply_kernel<<<(unsigned)nb, SC_THREADS, 0, st>>>(in, (uint32_t)n, offs, out);
+    exclusive_scan_dl(sums, offs, nb, tmp + 2 * nb, st, launches, DevLen{});
+    scan_apply_kernel<<<(unsigned)nb, SC_THREADS, 0, st>>>(in, (uint32_t)n, offs, out, dl);
     ++*launches;
+}
+
+void exclusive_scan(const uint32_t *in, uint32_t *out, uint64_t n, uint32_t *tmp, cudaStream_t st, int *launches)
+{
+    exclusive_scan_dl(in, out, n, tmp, st, launches, DevLen{});
 }
 
 // ------------------------------------------------------------ radix sort
@@ -146,7 +170,11 @@ __global__ void __launch_bounds__(RS_THREADS) rs_hist_kernel(const K *__restrict
 {
     constexpr uint32_t NB = 1u << RB;
     __shared__ uint32_t h[NB];
-    if (n_dev) n = min(n, *n_dev);
+    // with a device count, the histogram's columns are its blocks alone
+    if (n_dev) {
+        n = min(n, *n_dev);
+        nblocks = (n + RS_TILE - 1) / RS_TILE;
+    }
     for (uint32_t blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
         if (threadIdx.x < NB) h[threadIdx.x] = 0;
         __syncthreads();
@@ -212,7 +240,10 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(const K *__restr
     __shared__ uint32_t s_warp[RS_WARPS];
     __shared__ K s_key[RS_TILE];
     __shared__ uint32_t s_val[RS_TILE];
-    if (n_dev) n = min(n, *n_dev);
+    if (n_dev) {
+        n = min(n, *n_dev);
+        nblocks = (n + RS_TILE - 1) / RS_TILE;
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t ltmask = (1u << lane) - 1u;
     for (uint32_t blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
@@ -320,7 +351,9 @@ static void radix_pass(const K *ka, const uint32_t *va, K *kb, uint32_t *vb, uin
     const uint32_t grid = n_dev ? (nb < kDevGrid ? nb : kDevGrid) : nb;
     rs_hist_kernel<K, RB, CELL><<<grid, RS_THREADS, 0, st>>>(ka, va, (uint32_t)n, shift, n_gauss, hist, nb, n_dev);
     ++*launches;
-    exclusive_scan(hist, hist, ((uint64_t)1 << RB) * nb, scan_tmp, st, launches);
+    DevLen dl;
+    if (n_dev) dl = DevLen{n_dev, 1u << RB, (uint32_t)RS_TILE};
+    exclusive_scan_dl(hist, hist, ((uint64_t)1 << RB) * nb, scan_tmp, st, launches, dl);
     rs_scatter_kernel<K, RB, CELL><<<grid, RS_THREADS, 0, st>>>(ka, va, kb, vb, (uint32_t)n, shift, n_gauss, hist, nb,
                                                                 n_dev);
     ++*launches;
@@ -447,9 +480,61 @@ __global__ void tile_counts_kernel(const uint32_t *__restrict__ ev_val, uint64_t
 
 // *word = cnt[n - 1] before an in-place exclusive scan of cnt, then (add)
 // the scan's last value: the total
-__global__ void scan_last_kernel(const uint32_t *__restrict__ v, uint64_t n, uint32_t *__restrict__ word, int add)
+__global__ void scan_last_kernel(const uint32_t *__restrict__ v, uint64_t n, uint32_t *__restrict__ word, int add,
+                                 DevLen dl)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) *word = (add ? *word : 0u) + (n ? v[n - 1] : 0u);
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const uint32_t m = dev_len(dl, (uint32_t)n);
+        *word = (add ? *word : 0u) + (m ? v[m - 1] : 0u);
+    }
+}
+
+// The first phase's events as one index range: the prefix events of cell c
+// are pref_start[c] .. pref_start[c + 1] - 1 (one block; *n_pre: their total)
+__global__ void __launch_bounds__(SC_THREADS) prefix_ranges_kernel(const uint32_t *__restrict__ cell_ev, int n_cells,
+                                                                   int shift, uint32_t *__restrict__ pref_start,
+                                                                   uint32_t *__restrict__ n_pre)
+{
+    __shared__ uint32_t s_warp[32];
+    uint32_t carry = 0;
+    for (int c0 = 0; c0 < n_cells; c0 += SC_THREADS) {
+        const int c = c0 + (int)threadIdx.x;
+        uint32_t p = 0;
+        if (c < n_cells) {
+            const uint32_t ec = cell_ev[c + 1] - cell_ev[c];
+            p = (uint32_t)(((uint64_t)ec + (1u << shift) - 1u) >> shift);
+        }
+        uint32_t total;
+        const uint32_t first = carry + block_exclusive_scan(p, s_warp, total);
+        if (c < n_cells) pref_start[c] = first;
+        carry += total;
+    }
+    if (threadIdx.x == 0) {
+        pref_start[n_cells] = carry;
+        *n_pre = carry;
+    }
+}
+
+// The prefix events' tile counts, in the compacted index i < *n_pre, and the
+// sorted event each index stands for (evmap)
+__global__ void prefix_counts_kernel(const uint32_t *__restrict__ ev_val, uint64_t ne,
+                                     const PixBox *__restrict__ boxes, int TS, const uint32_t *__restrict__ cell_ev,
+                                     const uint32_t *__restrict__ pref_start, int n_cells,
+                                     const uint32_t *__restrict__ n_pre, uint32_t *__restrict__ cnt,
+                                     uint32_t *__restrict__ evmap)
+{
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i >= ne || i >= *n_pre) return;
+    int lo = 0, hi = n_cells;  // the cell c with pref_start[c] <= i < pref_start[c + 1]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pref_start[mid] <= i) lo = mid; else hi = mid;
+    }
+    const uint32_t e = cell_ev[lo] + (uint32_t)(i - pref_start[lo]);
+    int tx0, tx1, ty0, ty1;
+    tile_rect(boxes[ev_val[e] >> 1], TS, tx0, tx1, ty0, ty1);
+    cnt[i] = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+    evmap[i] = e;
 }
 
 // Entry counts of the segments' full lists, as 2D difference marks per cell:
@@ -550,21 +635,23 @@ __device__ __forceinline__ uint32_t sat_rect(const uint32_t *__restrict__ s, int
     return s[(ty1 + 1) * w + tx1 + 1] - s[ty0 * w + tx1 + 1] - s[(ty1 + 1) * w + tx0] + s[ty0 * w + tx0];
 }
 
+__global__ void events_if_active_kernel(const uint32_t *__restrict__ n_active, uint32_t ne, uint32_t *__restrict__ out)
+{
+    if (threadIdx.x == 0) *out = *n_active ? ne : 0u;
+}
+
+// (no segment active: nothing is written, and the scan reads nothing)
 __global__ void masked_counts_kernel(const uint32_t *__restrict__ ev_val, uint64_t ne,
                                      const PixBox *__restrict__ boxes, int TS, int ntx, int nty, uint64_t n_gauss,
                                      const uint32_t *__restrict__ sat, const uint32_t *__restrict__ n_active,
                                      uint32_t *__restrict__ cnt)
 {
     const uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    if (e >= ne) return;
-    uint32_t n = 0;
-    if (*n_active) {
-        const uint32_t ri = ev_val[e] >> 1;
-        int tx0, tx1, ty0, ty1;
-        tile_rect(boxes[ri], TS, tx0, tx1, ty0, ty1);
-        n = sat_rect(sat + (ri / n_gauss) * (uint64_t)(ntx + 1) * (nty + 1), ntx + 1, tx0, tx1, ty0, ty1);
-    }
-    cnt[e] = n;
+    if (e >= ne || *n_active == 0) return;
+    const uint32_t ri = ev_val[e] >> 1;
+    int tx0, tx1, ty0, ty1;
+    tile_rect(boxes[ri], TS, tx0, tx1, ty0, ty1);
+    cnt[e] = sat_rect(sat + (ri / n_gauss) * (uint64_t)(ntx + 1) * (nty + 1), ntx + 1, tx0, tx1, ty0, ty1);
 }
 
 // Entry keys: (tile << cb) | cell when cb >= 0 (the entries of one cell are
@@ -585,29 +672,32 @@ __device__ __forceinline__ uint32_t entry_segment(uint32_t key, int cb, int n_ti
 // that range, so every store instruction writes 32 consecutive words; each
 // lane finds the event of its entry by a binary search over the warp's 32
 // offsets (shuffles).  Launch with a multiple of 32 threads per block.
-// Events outside their cell's depth prefix (cell_ev, shift: in_prefix) give
-// no entries.
+// With evmap, the items are the first phase's prefix events in their
+// compacted index (*n_map of them, evmap: the sorted event of each), else the
+// sorted events themselves.
 __global__ void emit_entries_kernel(const uint32_t *__restrict__ ev_val, uint64_t ne,
                                     const PixBox *__restrict__ boxes, int TS, int ntx, int n_tiles, int cb,
-                                    uint64_t n_gauss, const uint32_t *__restrict__ cell_ev, int shift,
-                                    const uint32_t *__restrict__ off, uint32_t *__restrict__ ent_seg,
-                                    uint32_t *__restrict__ ent_ev)
+                                    uint64_t n_gauss, const uint32_t *__restrict__ evmap,
+                                    const uint32_t *__restrict__ n_map, const uint32_t *__restrict__ off,
+                                    uint32_t *__restrict__ ent_seg, uint32_t *__restrict__ ent_ev)
 {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
+    if (evmap) ne = min(ne, (uint64_t)*n_map);
     const uint64_t e0 = ((blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5) * 32u;
     if (e0 >= ne) return;  // uniform across the warp
-    const uint64_t e = e0 + (uint64_t)lane;
-    uint32_t myoff = 0xffffffffu, myend = 0, cell = 0;
+    const uint64_t item = e0 + (uint64_t)lane;
+    uint32_t myoff = 0xffffffffu, myend = 0, cell = 0, myev = 0;
     int tx0 = 0, ty0 = 0, tw = 1;
-    if (e < ne) {
-        const uint32_t ri = ev_val[e] >> 1;
+    if (item < ne) {
+        myev = evmap ? evmap[item] : (uint32_t)item;
+        const uint32_t ri = ev_val[myev] >> 1;
         cell = (uint32_t)(ri / n_gauss);
         int tx1, ty1;
         tile_rect(boxes[ri], TS, tx0, tx1, ty0, ty1);
         tw = tx1 - tx0 + 1;
-        myoff = off[e];
-        myend = myoff + (in_prefix(e, cell, cell_ev, shift) ? (uint32_t)(tw * (ty1 - ty0 + 1)) : 0u);
+        myoff = off[item];
+        myend = myoff + (uint32_t)(tw * (ty1 - ty0 + 1));
     }
     const uint32_t start = __shfl_sync(full, myoff, 0);
     uint32_t end = myend;
@@ -625,11 +715,12 @@ __global__ void emit_entries_kernel(const uint32_t *__restrict__ ev_val, uint64_
         const uint32_t oj = __shfl_sync(full, myoff, j);
         const uint32_t cj = __shfl_sync(full, cell, j);
         const int x0 = __shfl_sync(full, tx0, j), y0 = __shfl_sync(full, ty0, j), w = __shfl_sync(full, tw, j);
+        const uint32_t evj = __shfl_sync(full, myev, j);
         if (o < end) {
             const uint32_t k = o - oj;
             const uint32_t ty = (uint32_t)y0 + k / (uint32_t)w, tx = (uint32_t)x0 + k % (uint32_t)w;
             ent_seg[o] = entry_key(cj, ty * (uint32_t)ntx + tx, cb, n_tiles);
-            ent_ev[o] = (uint32_t)(e0 + (uint64_t)j);
+            ent_ev[o] = evj;
         }
     }
 }
@@ -821,20 +912,26 @@ int run_binning(const BinArgs &a, BinOut &o, cudaStream_t st, int *launches)
         *launches += 3;
         o.seg_total = a.seg_total;
     }
-    // 4. entries per tile (of the prefix: their count is then known on the device only)
-    tile_counts_kernel<<<blocks_for(ne, T), T, 0, st>>>(evv, ne, a.boxes, a.TS, a.n_gauss, a.cell_ev,
-                                                         a.prefix_shift, a.u32_a);
-    ++*launches;
-    const uint32_t *n_dev = nullptr;
+    // 4. entries per tile.  The first phase counts its prefix events alone,
+    // in their compacted index (words[2] of them; evmap: the sorted event of
+    // each), and the count of its entries is then known on the device only.
+    const uint32_t *n_dev = nullptr, *evmap = nullptr;
     if (prefix) {
-        scan_last_kernel<<<1, 32, 0, st>>>(a.u32_a, ne, a.words, 0);
-        ++*launches;
-    }
-    exclusive_scan(a.u32_a, a.u32_a, ne, a.scan_tmp, st, launches);
-    if (prefix) {
-        scan_last_kernel<<<1, 32, 0, st>>>(a.u32_a, ne, a.words, 1);
-        ++*launches;
+        prefix_ranges_kernel<<<1, SC_THREADS, 0, st>>>(a.cell_ev, a.n_cells, a.prefix_shift, a.pref_start,
+                                                       a.words + 2);
+        prefix_counts_kernel<<<blocks_for(ne, T), T, 0, st>>>(evv, ne, a.boxes, a.TS, a.cell_ev, a.pref_start,
+                                                              a.n_cells, a.words + 2, a.u32_a, a.u32_b);
+        const DevLen dl{a.words + 2, 1, 1};
+        scan_last_kernel<<<1, 32, 0, st>>>(a.u32_a, ne, a.words, 0, dl);
+        exclusive_scan_dl(a.u32_a, a.u32_a, ne, a.scan_tmp, st, launches, dl);
+        scan_last_kernel<<<1, 32, 0, st>>>(a.u32_a, ne, a.words, 1, dl);
+        *launches += 4;
         n_dev = a.words;
+        evmap = a.u32_b;
+    } else {
+        tile_counts_kernel<<<blocks_for(ne, T), T, 0, st>>>(evv, ne, a.boxes, a.TS, a.n_gauss, a.cell_ev, 0, a.u32_a);
+        ++*launches;
+        exclusive_scan(a.u32_a, a.u32_a, ne, a.scan_tmp, st, launches);
     }
     // entry keys: tile bits above cell bits when both fit in 32 bits
     int cb = 0, tb = 0;
@@ -843,7 +940,8 @@ int run_binning(const BinArgs &a, BinOut &o, cudaStream_t st, int *launches)
     if (tb == 0) tb = 1;
     const bool packed = cb + tb <= 32;
     emit_entries_kernel<<<blocks_for(ne, T), T, 0, st>>>(evv, ne, a.boxes, a.TS, a.ntx, a.n_tiles, packed ? cb : -1,
-                                                          a.n_gauss, a.cell_ev, a.prefix_shift, a.u32_a, a.ent_seg[0],
+                                                          a.n_gauss, evmap, prefix ? a.words + 2 : nullptr, a.u32_a,
+                                                          a.ent_seg[0],
                                                           a.ent_ev[0]);
     ++*launches;
     // 5-6. stable sort by tile, segment bounds
@@ -890,12 +988,15 @@ int run_rebin(const BinArgs &a, const BinOut &first, const uint32_t *active, con
                                                                                     nty + 1, 0);
     seg_prefix_kernel<<<blocks_for((uint64_t)a.n_cells * (a.ntx + 1), T), T, 0, st>>>(a.sat, a.n_cells, a.ntx + 1,
                                                                                       nty + 1, 1);
+    // the events' count, or 0 when no segment is active (nothing is then read)
+    events_if_active_kernel<<<1, 32, 0, st>>>(n_active, (uint32_t)ne, a.words + 3);
+    const DevLen dl{a.words + 3, 1, 1};
     masked_counts_kernel<<<blocks_for(ne, T), T, 0, st>>>(first.ev_val, ne, a.boxes, a.TS, a.ntx, nty, a.n_gauss,
                                                            a.sat, n_active, a.u32_a);
-    scan_last_kernel<<<1, 32, 0, st>>>(a.u32_a, ne, a.words + 1, 0);
-    *launches += 6;
-    exclusive_scan(a.u32_a, a.u32_a, ne, a.scan_tmp, st, launches);
-    scan_last_kernel<<<1, 32, 0, st>>>(a.u32_a, ne, a.words + 1, 1);
+    scan_last_kernel<<<1, 32, 0, st>>>(a.u32_a, ne, a.words + 1, 0, dl);
+    *launches += 7;
+    exclusive_scan_dl(a.u32_a, a.u32_a, ne, a.scan_tmp, st, launches, dl);
+    scan_last_kernel<<<1, 32, 0, st>>>(a.u32_a, ne, a.words + 1, 1, dl);
     int cb = 0, tb = 0;
     while ((1ull << cb) < (uint64_t)a.n_cells) ++cb;
     while ((1ull << tb) < (uint64_t)a.n_tiles) ++tb;
