@@ -399,6 +399,9 @@ struct EvInfo {
 // fifth of the opacity evaluations against 5e-8.
 // A pixel stops when both sides have; a tile stops when all its pixels have.
 constexpr float EXIT_EPS = 1e-5f;
+// an incomplete list (a depth prefix) of a segment with at most this many
+// entries in full is not swept but deferred to the next round
+constexpr uint32_t SHORT_DEFER = 256;
 
 // a / (1 - a) rounded up, for 0 <= a < 1 (__fdividef is within 2 ulp here;
 // the factor 1 + 2^-21 covers that)
@@ -608,13 +611,18 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
             }
         };
         int buf = 0;
-        if (b0 < b1) stage(0, b0);
+        // a short list held only in part is deferred to the next round, which
+        // has it in full: the segments that outrun their depth prefix are
+        // mostly short (sparse tiles), and a sweep of their prefix would be
+        // done twice
+        if (incomplete && total <= SHORT_DEFER) abandoned = true;
+        if (b0 < b1 && !abandoned) stage(0, b0);
         // a complete list ends the sweep when it runs out; a prefix only when
         // every pixel has stopped, or by abandoning the segment at the first
         // chunk it does not hold in full (the next binning phase gives the
         // segment its full list, and the sweep starts again: the exit tests
         // fall at the same entries, so the bounds are those of one sweep)
-        for (uint32_t base = b0; base < b1 || incomplete; base += CH, buf ^= 1) {
+        for (uint32_t base = b0; !abandoned && (base < b1 || incomplete); base += CH, buf ^= 1) {
             if (!done) {
                 const float left = (float)(total - (base - b0));
                 // PA is rounded down; 1.01 covers its relative error for < 10^5 factors
