@@ -711,7 +711,7 @@ static int render_batch(ar_scene *s, Workspace &ws, const CallConst &cc, int M, 
         RK(ws.words.ensure(sizeof(uint32_t) * 8));
         RK(ws.slist.ensure(sizeof(uint32_t) * n_pairs));
         RK(ws.plist.ensure(sizeof(uint32_t) * n_seg));
-        RK(ws.pmask.ensure(sizeof(uint32_t) * n_seg * (TS * TS / 32)));
+        RK(ws.pmask.ensure(sizeof(uint32_t) * n_seg * (TS * TS / 32 + 1)));  // pixel mask + a flag per slot
     }
     // The rest of the batch (binning, then the windowed rounds of build and
     // render) depends on the host only through the sizes read above, so with

@@ -46,7 +46,7 @@ struct RenderLaunch {
     int interleave = 0, direct = 0;
     // precision: the FP32 sweep (f64 = 0) appends a segment that needs an FP64
     // evaluation to precise[*n_precise], with the mask of the pixels that do in
-    // precise_mask[slot * TS * TS / 32 ...]; the f64 = 1 instance sweeps them
+    // precise_mask[slot * (TS * TS / 32 + 1) ...] (then a flag word); the f64 = 1 instance sweeps them
     int f64 = 0;
     uint32_t *precise = nullptr, *n_precise = nullptr, *precise_mask = nullptr;
 };

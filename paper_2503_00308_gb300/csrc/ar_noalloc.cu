@@ -157,7 +157,7 @@ int ar_render_abstract_noalloc(ar_scene *s, const ar_intrinsics *in, const ar_no
     uint32_t *state = A.take<uint32_t>(n_pairs), *wlist = A.take<uint32_t>(n_pairs);
     uint32_t *slist = A.take<uint32_t>(n_pairs);
     uint32_t *act0 = A.take<uint32_t>(n_seg), *act1 = A.take<uint32_t>(n_seg), *words = A.take<uint32_t>(8);
-    uint32_t *plist = A.take<uint32_t>(n_seg), *pmask = A.take<uint32_t>(n_seg * (TS * TS / 32));
+    uint32_t *plist = A.take<uint32_t>(n_seg), *pmask = A.take<uint32_t>(n_seg * (TS * TS / 32 + 1));
     if (A.over) return too_big("the per-(Gaussian, cell) records", A.used);
 
     // pose cells: lo and hi rows straight from the caller's array (no staging copy)

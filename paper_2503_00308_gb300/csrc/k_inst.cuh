@@ -84,23 +84,26 @@ static int launch_render_ts(const RenderLaunch &a, cudaStream_t st)
     // barriers) and a ring of 4 (rings of 3-8 measured: 4 keeps the ring's
     // shared memory small)
     constexpr int RING = 4;
-    typedef RenderSmem<AR_M, TS, CH, RING> SM;
+    typedef RenderShape<TS, F64> SH;
+    typedef RenderSmem<AR_M, TS, CH, RING, SH::NTH> SM;
     auto kern = render_kernel<AR_M, TS, CH, RING, REL, F64>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::BYTES) != cudaSuccess)
         return 1;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TS * TS, SM::BYTES) != cudaSuccess || per_sm < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SH::NTH, SM::BYTES) != cudaSuccess || per_sm < 1)
         per_sm = 1;
     const uint32_t nseg = (uint32_t)a.n_cells * (uint32_t)a.n_tiles;
+    // work items: segments, or for the FP64 instance (segment, group of 32 pixels)
+    const uint64_t items = (uint64_t)nseg * (F64 ? (uint64_t)(TS * TS / 32) : 1u);
     uint32_t grid = (uint32_t)(sms * per_sm);
-    if (grid > nseg) grid = nseg;
+    if (grid > items) grid = (uint32_t)items;
     // direct launches (a.direct: the active list holds all nseg segments) take
     // one CTA per segment
     if (a.direct) grid = nseg;
     if (cudaMemsetAsync(a.work, 0, sizeof(unsigned int), st) != cudaSuccess) return 1;
-    kern<<<grid, TS * TS, SM::BYTES, st>>>(a.recs, a.boxes, a.seg_start, a.seg_end, a.seg_total, a.cell_ev,
+    kern<<<grid, SH::NTH, SM::BYTES, st>>>(a.recs, a.boxes, a.seg_start, a.seg_end, a.seg_total, a.cell_ev,
                                            a.active, a.n_active,
                                            a.window,
                                            a.next_active, a.n_next, a.precise, a.n_precise, a.precise_mask, a.sweep_hist,

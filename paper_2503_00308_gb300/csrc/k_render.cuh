@@ -421,8 +421,9 @@ __device__ __forceinline__ float open_ratio_up(float a)
 //   every access is bank-conflict free.  The ring lets the upper endpoint of
 //   a Gaussian reuse the evaluation made at its lower endpoint; an upper
 //   endpoint whose evaluation has left the ring evaluates again.
-template <int M, int TS, int CH, int RING> struct RenderSmem {
-    static constexpr int NT = TS * TS;
+// NTH: threads per CTA (the tile's pixels, or one warp for the FP64 instance)
+template <int M, int TS, int CH, int RING, int NTH = TS * TS> struct RenderSmem {
+    static constexpr int NT = NTH;
     static constexpr int PAY = M + 4;  // alo, ahi, rL, L.k, L.c[M]
     static constexpr size_t REC = 2 * sizeof(float) * CH * Rec<M>::WIDTH;  // two chunk buffers
     static constexpr size_t EV = 2 * sizeof(EvInfo) * CH;
@@ -446,6 +447,13 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <int TS> struct RenderOcc {
     static constexpr int MIN_BLOCKS = TS * TS >= 256 ? 2 : 1;
 };
+// The FP64 instance runs one warp per CTA, sixteen CTAs per SM (the same
+// registers per thread as two 256-thread CTAs)
+template <int TS, bool F64> struct RenderShape {
+    static constexpr int NTH = F64 ? 32 : TS * TS;
+    static constexpr int MIN_BLOCKS = F64 ? 16 : RenderOcc<TS>::MIN_BLOCKS;
+    static constexpr int MASKW = TS * TS / 32 + 1;  // words per listed segment: pixel mask, abandon flag
+};
 
 // Persistent grid: each CTA takes (cell, tile) segments from the active list
 // (longest first in the first round) through an atomic counter until none
@@ -468,9 +476,11 @@ template <int TS> struct RenderOcc {
 // F64 = true instance sweeps the listed segments again from their start for
 // the masked pixels alone (the others start as stopped and write nothing).
 // The decision is per pixel, taken from the pixel's own sweep, so every pixel
-// gets the bounds one FP64-capable sweep would give it.
+// gets the bounds one FP64-capable sweep would give it.  The FP64 instance
+// runs one warp per CTA: each work item is a listed segment and a group of up
+// to 32 of its listed pixels, so that many segments are in flight at once.
 template <int M, int TS, int CH, int RING, bool REL, bool F64>
-__global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kernel(
+__global__ void __launch_bounds__(RenderShape<TS, F64>::NTH, RenderShape<TS, F64>::MIN_BLOCKS) render_kernel(
     const float *__restrict__ recs, const PixBox *__restrict__ boxes, const uint32_t *__restrict__ seg_start,
     const uint32_t *__restrict__ seg_end, const uint32_t *__restrict__ seg_total,
     const uint32_t *__restrict__ cell_ev, const uint32_t *__restrict__ active, const uint32_t *__restrict__ n_active,
@@ -483,8 +493,11 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
     unsigned long long *__restrict__ counters, unsigned int *__restrict__ work, int direct)
 {
     using RL = Rec<M>;
-    using SM = RenderSmem<M, TS, CH, RING>;
-    constexpr int NT = TS * TS;
+    using SH = RenderShape<TS, F64>;
+    using SM = RenderSmem<M, TS, CH, RING, SH::NTH>;
+    constexpr int NT = SH::NTH;      // threads
+    constexpr int NPIX = TS * TS;    // pixels of a tile
+    constexpr int GROUPS = F64 ? NPIX / 32 : 1;  // work items per listed segment
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float(*s_rec2)[RL::WIDTH] = reinterpret_cast<float(*)[RL::WIDTH]>(smem_raw);        // [2 * CH]
     EvInfo *s_ev2 = reinterpret_cast<EvInfo *>(smem_raw + SM::REC);                    // [2 * CH]
@@ -502,8 +515,9 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
     for (uint32_t round = 0;; ++round) {
         if (tid == 0) *s_next = direct ? (round == 0 ? blockIdx.x : 0xffffffffu) : atomicAdd(work, 1u);
         __syncthreads();
-        const uint32_t wk = *s_next;
+        const uint32_t item = *s_next;
         __syncthreads();
+        const uint32_t wk = item / GROUPS, grp = item % GROUPS;
         if (wk >= n_seg) break;
         const uint32_t seg = active[wk];
         const int cell = (int)(seg / (uint32_t)n_tiles);
@@ -513,17 +527,16 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
         // of small Gaussians cut fewer warps and warps finish together
         const int wb = tid >> 5, ln = tid & 31;
         // the pixel this thread sweeps, by its thread index in the FP32
-        // sweep's layout; the FP64 instance packs the listed pixels onto its
-        // first threads (the rank of tid among the mask's set bits), so that
-        // they share few warps
+        // sweep's layout; the FP64 instance takes the listed pixels of rank
+        // 32 grp + tid among the mask's set bits
         int pid = tid;
         bool active = true;
         if (F64) {
-            const uint32_t *pm = precise_mask + (size_t)wk * (NT / 32);
-            int rem = tid;
+            const uint32_t *pm = precise_mask + (size_t)wk * SH::MASKW;
+            int rem = (int)grp * 32 + tid;
             pid = -1;
 #pragma unroll
-            for (int w = 0; w < NT / 32; ++w) {
+            for (int w = 0; w < NPIX / 32; ++w) {
                 uint32_t m = pm[w];
                 const int c = __popc(m);
                 if (pid < 0 && rem < c) {
@@ -534,7 +547,8 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
                 }
             }
             active = pid >= 0;
-            if (!active) pid = tid;  // a position of the tile; the thread sweeps nothing
+            if (!active) pid = 0;  // a position of the tile; the thread sweeps nothing
+            if (!__syncthreads_or(active)) continue;  // a group past the segment's listed pixels
         }
         const int pwb = pid >> 5, pln = pid & 31;
         const int px = tx * TS + (pwb % (TS / 8)) * 8 + (pln & 7);
@@ -779,7 +793,8 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
             }
         }
         if (abandoned) {
-            if (tid == 0) {
+            // (the FP64 instance's groups of one segment list it once)
+            if (tid == 0 && (!F64 || atomicOr(&precise_mask[(size_t)wk * SH::MASKW + NPIX / 32], 1u) == 0u)) {
                 next_active[atomicAdd(n_next, 1u)] = seg;
                 if (counters) atomicAdd(&counters[5], 1ull);
             }
@@ -792,12 +807,13 @@ __global__ void __launch_bounds__(TS *TS, RenderOcc<TS>::MIN_BLOCKS) render_kern
             if (tid == 0) {
                 const uint32_t slot = atomicAdd(n_precise, 1u);
                 precise_list[slot] = seg;
+                precise_mask[(size_t)slot * SH::MASKW + NPIX / 32] = 0u;  // the FP64 instance's abandon flag
                 s_next[1] = slot;
                 if (counters) atomicAdd(&counters[7], 1ull);
             }
             __syncthreads();
             const uint32_t m = __ballot_sync(0xffffffffu, wide_hit);
-            if ((tid & 31) == 0) precise_mask[(size_t)s_next[1] * (NT / 32) + (tid >> 5)] = m;
+            if ((tid & 31) == 0) precise_mask[(size_t)s_next[1] * SH::MASKW + (tid >> 5)] = m;
         }
         if (!F64 && sweep_hist && tid == 0) atomicAdd(&sweep_hist[min(swept / 32u, 255u)], 1u);
         // where in its cell's depth order the segment stopped (64 buckets of
