@@ -53,13 +53,13 @@ BOOKKEEPING_FLOPS_PER_TRIPLE = 156
 
 # DRAM bytes of the render kernel per opacity evaluation, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of round 0 of the first 4
-# cells of the 300k-Gaussian workload, both instances (FP32 sweep 37.1 MB, FP64
-# re-sweep 13.7 MB) over 73.2M evaluations.  Valid only for the kernel
-# sources it was taken from (their SHA-256 below); otherwise the roofline's
-# traffic is reported as null.
-RENDER_TRAFFIC = {"bytes_per_evaluation": (28485632 + 8572672 + 13522176 + 141056) / 73160149,
+# cells of the 300k-Gaussian workload, both instances (FP32 sweep 34.8 MB, FP64
+# re-sweep 15.3 MB), over the render's 73.2M evaluations.  Valid only for the
+# kernel sources it was taken from (their SHA-256 below); otherwise the
+# roofline's traffic is reported as null.
+RENDER_TRAFFIC = {"bytes_per_evaluation": (27405056 + 7374336 + 14476288 + 822272) / 73160149,
                   "sources": ["k_render.cuh", "ar_num.cuh", "ar_common.cuh", "k_inst.cuh"],
-                  "sha256": "fb6de62c9629d4b87d439b32822a5b363cb3e0230c9d5b8236771632b5715d20"}
+                  "sha256": "658915c911b0d7995ddf96cee00cb67026eca724022b23726dfcc6b1aefe5357"}
 
 
 def render_traffic(n_evaluated: int):
