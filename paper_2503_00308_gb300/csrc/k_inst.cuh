@@ -27,16 +27,20 @@ int AR_CAT(launch_record_prep_m, AR_M)(const double *vN, const void *gp,
                                        cudaStream_t st, uint32_t *list, uint32_t *count)
 {
     const int T = 128;
-    dim3 grid((unsigned)((cc.n_gauss + T - 1) / T), (unsigned)cc.n_cells);
     const CellData<AR_M> *cd = (const CellData<AR_M> *)cells;
+    const unsigned gb = (unsigned)((cc.n_gauss + T - 1) / T);
+    // all cells of a range of Gaussians together (their vN rows stay in L2),
+    // where the grid's y can hold the Gaussian blocks
+    const int cf = gb <= 65535u ? 1 : 0;
+    const dim3 grid = cf ? dim3((unsigned)cc.n_cells, gb) : dim3(gb, (unsigned)cc.n_cells);
     // decision part only: the value parts are built by the renderer on demand
     if (!list) {
         record_prep_kernel<AR_M, float, false><<<grid, T, 0, st>>>(vN, (const GParam *)gp, cc, cd, TS, recs, boxes,
-                                                                   keys, counters);
+                                                                   keys, counters, cf);
         return cudaGetLastError() == cudaSuccess ? 0 : 1;
     }
     if (cudaMemsetAsync(count, 0, sizeof(uint32_t), st) != cudaSuccess) return 1;
-    cull_kernel<AR_M><<<grid, T, 0, st>>>(vN, (const GParam *)gp, cc, cd, boxes, list, count);
+    cull_kernel<AR_M><<<grid, T, 0, st>>>(vN, (const GParam *)gp, cc, cd, boxes, list, count, cf);
     const uint64_t pairs = (uint64_t)cc.n_gauss * (uint64_t)cc.n_cells;
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
@@ -56,7 +60,7 @@ int AR_CAT(launch_record_prep64_m, AR_M)(const double *vN, const void *gp,
     const int T = 128;
     dim3 grid((unsigned)((cc.n_gauss + T - 1) / T), (unsigned)cc.n_cells);
     record_prep_kernel<AR_M, double><<<grid, T, 0, st>>>(vN, (const GParam *)gp, cc, (const CellData<AR_M> *)cells,
-                                                         TS, recs, boxes, keys, counters);
+                                                         TS, recs, boxes, keys, counters, 0);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 

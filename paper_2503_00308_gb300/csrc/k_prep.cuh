@@ -1127,10 +1127,13 @@ __global__ void __launch_bounds__(128, 5) record_prep_kernel(
     const double *__restrict__ vN, const GParam *__restrict__ gp, CallConst cc,
     const CellData<M> *__restrict__ cells, int TS,
     RO *__restrict__ recs, PixBox *__restrict__ boxes, double *__restrict__ keys,
-    unsigned long long *__restrict__ counters)
+    unsigned long long *__restrict__ counters, int cells_fast)
 {
-    const int cell = blockIdx.y;
-    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    // cells_fast: the grid's x is the cell, so that the blocks of all cells
+    // over one range of Gaussians run together and share that range's vN
+    // rows in L2 (a scene's rows can exceed L2: 240 B per Gaussian)
+    const int cell = cells_fast ? blockIdx.x : blockIdx.y;
+    const int64_t g = (cells_fast ? blockIdx.y : blockIdx.x) * (int64_t)blockDim.x + threadIdx.x;
     PrepCount pc = {0, 0, 0, 0, 0};
     if (g < cc.n_gauss) {
         const int64_t fl = record_decide<M, RO>(vN, gp, cc, cells[cell], cell, g, TS, recs, boxes, keys, pc);
@@ -1167,10 +1170,10 @@ template <int M>
 __global__ void __launch_bounds__(128) cull_kernel(const double *__restrict__ vN, const GParam *__restrict__ gp,
                                                    CallConst cc, const CellData<M> *__restrict__ cells,
                                                    PixBox *__restrict__ boxes, uint32_t *__restrict__ list,
-                                                   uint32_t *__restrict__ count)
+                                                   uint32_t *__restrict__ count, int cells_fast)
 {
-    const int cell = blockIdx.y;
-    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int cell = cells_fast ? blockIdx.x : blockIdx.y;  // (see record_prep_kernel)
+    const int64_t g = (cells_fast ? blockIdx.y : blockIdx.x) * (int64_t)blockDim.x + threadIdx.x;
     bool keep = false;
     const int64_t ri = (int64_t)cell * cc.n_gauss + g;
     if (g < cc.n_gauss) {
