@@ -479,3 +479,58 @@ def test_cull_before_decisions_is_bit_identical(arlib):
         assert np.array_equal(o[0], outs[0][0]) and np.array_equal(o[1], outs[0][1])
         assert o[2]["n_records"] == outs[0][2]["n_records"] and o[2]["n_entries"] == outs[0][2]["n_entries"]
         assert np.array_equal(o[3], outs[0][3])
+
+
+def test_depth_prefix_and_cull_with_empty_cells(arlib, orc):
+    """Cells that see nothing (the camera moved past the object) next to
+    cells that do: every depth prefix, with the cull on and off, gives the
+    bounds of one phase without the cull, the empty cells' bounds are 0, and
+    a seen cell matches the oracle."""
+    ar = arlib
+    sc = synth.object_scene(2000, 21)
+    cam = synth.look_camera(48, 40, 55.0, centre=(0, 0, -4))
+    base_lo, base_hi = synth.cell_grid([0.03, 0.0, 0.03, 0.0, 0.01, 0.0], [2, 1, 1, 1, 2, 1])
+    far = np.array([[0.0, 0.0, 8.0, 0.0, 0.0, 0.0]])     # 8 m forward: every Gaussian behind the camera
+    lo = np.concatenate([base_lo[:2], far - 0.01, base_lo[2:]])
+    hi = np.concatenate([base_hi[:2], far + 0.01, base_hi[2:]])
+    res = {}
+    for shift, cull in ((0, 0), (3, 0), (6, 1), (2, 1), (-1, -1)):
+        s = ar.Scene(sc)
+        ar.ar_debug_set_prefix(s.handle, shift)
+        ar.ar_debug_set_cull(s.handle, cull)
+        out_lo = torch.full((lo.shape[0], cam.height, cam.width, 3), -7.0, device="cuda")
+        out_hi = torch.full_like(out_lo, -7.0)
+        for _ in range(2):
+            s.render(cam, lo, hi, out_lo, out_hi, tile=16)
+        torch.cuda.synchronize()
+        res[(shift, cull)] = (out_lo.double().cpu().numpy(), out_hi.double().cpu().numpy())
+        s.close()
+    ref_lo, ref_hi = res[(0, 0)]
+    assert np.all(ref_lo[2] == 0) and np.all(ref_hi[2] == 0)
+    for key, (o_lo, o_hi) in res.items():
+        assert np.array_equal(o_lo, ref_lo) and np.array_equal(o_hi, ref_hi), key
+    compare(orc, sc, cam, lo[1], hi[1], ref_lo[1], ref_hi[1], label="seen cell beside an empty one")
+
+
+def test_cull_with_scene_boxes(arlib):
+    """The cull reads the enclosures of the mean's box, as the FP64 chain
+    reads the box: with scene-parameter boxes the records and bounds do not
+    depend on it."""
+    ar = arlib
+    w = synth.unbounded750k(n=20_000, width=256, height=144, f=180.0, splits=(2, 1, 1, 1, 1, 1))
+    boxes = synth.scene_boxes(w.scene, 4, frac=0.5, red_add=0.2, mean_d=(0.05, 0.02, 0.05), opacity_scale=0.9,
+                              opacity_add=0.05)
+    outs = []
+    for cull in (0, 1):
+        s = ar.Scene(w.scene)
+        s.set_boxes(boxes)
+        ar.ar_debug_set_cull(s.handle, cull)
+        out_lo = torch.empty((w.n_cells, w.camera.height, w.camera.width, 3), device="cuda")
+        out_hi = torch.empty_like(out_lo)
+        s.render(w.camera, w.cells_lo, w.cells_hi, out_lo, out_hi, tile=16)
+        torch.cuda.synchronize()
+        outs.append((out_lo.cpu().numpy(), out_hi.cpu().numpy(),
+                     s.debug_records(w.camera, w.cells_lo[0], w.cells_hi[0])))
+        s.close()
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    assert np.array_equal(outs[0][2], outs[1][2])
