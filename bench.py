@@ -59,7 +59,7 @@ BOOKKEEPING_FLOPS_PER_TRIPLE = 156
 # roofline's traffic is reported as null.
 RENDER_TRAFFIC = {"bytes_per_evaluation": (27405056 + 7374336 + 14476288 + 822272) / 73160149,
                   "sources": ["k_render.cuh", "ar_num.cuh", "ar_common.cuh", "k_inst.cuh"],
-                  "sha256": "658915c911b0d7995ddf96cee00cb67026eca724022b23726dfcc6b1aefe5357"}
+                  "sha256": "9b247f98615f8610da6e25ef7fac6c5446332002a7750c02396de9cce4d5c100"}
 
 
 def render_traffic(n_evaluated: int):
