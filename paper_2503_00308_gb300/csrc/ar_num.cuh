@@ -146,8 +146,31 @@ __device__ __forceinline__ void axpy_rn(float a, const float *x, float *c)
     if (M & 1) c[M - 1] = __fmaf_rn(a, x[M - 1], c[M - 1]);
 }
 
+// gamma_n = n u (1 + 2^-12), which covers (1 + u)^n - 1 for n < 2^10.  The
+// product is exact (n (1 + 2^-12) has at most 24 significant bits for
+// n < 2^11, and u is a power of two), so it is written in round-to-nearest:
+// the value is the directed product's, and it folds to a constant where n is
+// known at compile time.
+template <class R>
+__device__ __forceinline__ R gamma_n(int n)
+{
+    return (R)n * (Num<R>::U * (R)1.000244140625);
+}
+// 1 + gamma_n rounded up, exactly.  The numbers just above 1 are spaced 2u
+// apart, and gamma_n / (2u) = n/2 + n 2^-13 lies strictly between floor(n/2)
+// and floor(n/2) + 1 for 1 <= n < 2^12, so the rounded-up sum is
+// 1 + (floor(n/2) + 1) 2u, a sum without rounding.
+template <class R>
+__device__ __forceinline__ R one_plus_gamma_ru(int n)
+{
+    return n > 0 ? (R)1 + (R)(n / 2 + 1) * ((R)2 * Num<R>::U) : (R)1;
+}
+
 // Accumulator of a sound form  sum_t a_t F_t + b  (one side).  DN = true for
 // a lower form (constant rounded down, slack subtracted), false for upper.
+// The coefficient updates of term / term_ck can be left out (cf = false)
+// where only the constant and the radius of the result are used: they do not
+// depend on the coefficients.
 template <int M, class R, bool DN> struct Acc {
     LF<M, R> f;
     R rs;   // sum_t |a_t| r_t  (to be scaled by gamma_n)
@@ -168,19 +191,19 @@ template <int M, class R, bool DN> struct Acc {
     __device__ __forceinline__ void add_slack(R s) { ex = Num<R>::add_ru(ex, s); }
     // add a * (Fc . p + Fk) where the form has radius r (the caller has
     // chosen the side of the form)
-    __device__ __forceinline__ void term_ck(R a, const R *Fc, R Fk, R r)
+    __device__ __forceinline__ void term_ck(R a, const R *Fc, R Fk, R r, bool cf = true)
     {
         using N = Num<R>;
-        axpy_rn<M>(a, Fc, f.c);
+        if (cf) axpy_rn<M>(a, Fc, f.c);
         f.k = DN ? N::fma_rd(a, Fk, f.k) : N::fma_ru(a, Fk, f.k);
         rs = N::fma_ru(N::abs(a), r, rs);
         ++n;
     }
     // add a * F where F has radius r (the caller has chosen the side of F)
-    __device__ __forceinline__ void term(R a, const LF<M, R> &F, R r)
+    __device__ __forceinline__ void term(R a, const LF<M, R> &F, R r, bool cf = true)
     {
         using N = Num<R>;
-        axpy_rn<M>(a, F.c, f.c);
+        if (cf) axpy_rn<M>(a, F.c, f.c);
         f.k = DN ? N::fma_rd(a, F.k, f.k) : N::fma_ru(a, F.k, f.k);
         rs = N::fma_ru(N::abs(a), r, rs);
         ++n;
@@ -192,15 +215,12 @@ template <int M, class R, bool DN> struct Acc {
     __device__ __forceinline__ R radius_bound() const
     {
         using N = Num<R>;
-        const R g = N::mul_ru((R)n, N::mul_ru(N::U, (R)1.000244140625));
-        return N::fma_ru(rs, N::add_ru((R)1, g), N::TINY);
+        return N::fma_ru(rs, one_plus_gamma_ru<R>(n), N::TINY);
     }
     __device__ __forceinline__ LF<M, R> result() const
     {
         using N = Num<R>;
-        // gamma_n = n u (1 + 2^-12) covers (1 + u)^n for n < 2^10
-        R g = N::mul_ru((R)n, N::mul_ru(N::U, (R)1.000244140625));
-        R s = N::add_ru(N::fma_ru(g, rs, ex), N::TINY);
+        R s = N::add_ru(N::fma_ru(gamma_n<R>(n), rs, ex), N::TINY);
         LF<M, R> out = f;
         out.k = DN ? N::sub_rd(f.k, s) : N::add_ru(f.k, s);
         return out;
@@ -233,6 +253,14 @@ __device__ __forceinline__ void sb_finish(SB<M, R> &b)
     b.r = r;
     b.vlo = N::sub_rd(b.klo, r);
     b.vhi = N::add_ru(b.khi, r);
+}
+
+// midpoint of the concretisation, rounded to nearest: the slope a product
+// takes for the other factor
+template <int M, class R>
+__device__ __forceinline__ R sb_mid(const SB<M, R> &b)
+{
+    return Num<R>::mul_rn(b.vlo + b.vhi, (R)0.5);
 }
 
 template <int M, class R>
@@ -299,9 +327,14 @@ template <int M, class R> struct SAcc {
     // + x * y  (averaged McCormick planes)
     __device__ __forceinline__ void mul(const SB<M, R> &x, const SB<M, R> &y)
     {
+        mul_ym(x, y, sb_mid(y));
+    }
+    // the same with y's midpoint given (a value of sb_mid(y) computed before)
+    __device__ __forceinline__ void mul_ym(const SB<M, R> &x, const SB<M, R> &y, R ym)
+    {
         using N = Num<R>;
         const R xl = x.vlo, xh = x.vhi, yl = y.vlo, yh = y.vhi;
-        const R xm = N::mul_rn(xl + xh, (R)0.5), ym = N::mul_rn(yl + yh, (R)0.5);
+        const R xm = sb_mid(x);
         term(ym, x);
         term(xm, y);
         // constants: -(xl yl + xh yh)/2 below, -(xh yl + xl yh)/2 above
@@ -309,7 +342,7 @@ template <int M, class R> struct SAcc {
                   -N::mul_rd(N::fma_rd(xh, yl, N::mul_rd(xl, yh)), (R)0.5));
         // the slopes are the rounded midpoints: cover |ym - y_mid| max|x| + ...
         const R xa = N::max(N::abs(xl), N::abs(xh)), ya = N::max(N::abs(yl), N::abs(yh));
-        add_slack(N::mul_ru(N::fma_ru(N::abs(ym), xa, N::mul_ru(N::abs(xm), ya)), N::mul_ru(N::U, (R)1.001)));
+        add_slack(N::mul_ru(N::fma_ru(N::abs(ym), xa, N::mul_ru(N::abs(xm), ya)), N::U * (R)1.001));  // (an exact product)
     }
     // + x^2  (tangent at the midpoint c below, secant above; both have slope
     // x_lo + x_hi = 2c)
@@ -325,9 +358,7 @@ template <int M, class R> struct SAcc {
     __device__ __forceinline__ SB<M, R> result() const
     {
         using N = Num<R>;
-        // gamma_n = n u (1 + 2^-12) covers (1 + u)^n for n < 2^10
-        const R g = N::mul_ru((R)n, N::mul_ru(N::U, (R)1.000244140625));
-        const R sl = N::add_ru(N::fma_ru(g, rs, ex), N::TINY);
+        const R sl = N::add_ru(N::fma_ru(gamma_n<R>(n), rs, ex), N::TINY);
         SB<M, R> b;
 #pragma unroll
         for (int j = 0; j < M; ++j) b.c[j] = c[j];

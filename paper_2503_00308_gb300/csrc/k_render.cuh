@@ -62,9 +62,10 @@ __device__ __forceinline__ void load_sb(const RE *src, SB<M, R> &b)
     b.r = (R)v[M + 2];
 }
 
-// c[M], klo, khi, vlo, vhi, r (W entries)
+// c[M], klo, khi, vlo, vhi, r (W entries); returns sb_mid(b), read from the
+// record where it was computed in the same precision, else computed here
 template <int M, class R, class RE>
-__device__ __forceinline__ void load_sbw(const RE *src, SB<M, R> &b)
+__device__ __forceinline__ R load_sbw(const RE *src, SB<M, R> &b)
 {
     RE v[Rec<M>::WS];
     load_vec<Rec<M>::WS>(src, v);
@@ -75,6 +76,8 @@ __device__ __forceinline__ void load_sbw(const RE *src, SB<M, R> &b)
     b.vlo = (R)v[M + 2];
     b.vhi = (R)v[M + 3];
     b.r = (R)v[M + 4];
+    if constexpr (sizeof(R) == sizeof(RE)) return v[M + 5];
+    else return sb_mid(b);
 }
 
 __device__ __forceinline__ float clamp01(float x) { return fminf(1.f, fmaxf(0.f, x)); }
@@ -93,9 +96,13 @@ __device__ __forceinline__ uint32_t rec_flags(const double *r, int at) { return 
 // of that times a (a_hi only while m_lo > 0: below that the secant ends at
 // x = 0 and a_hi = o).  The FP32 renderer evaluates the pair again in FP64
 // where this estimate exceeds its threshold (pixel_alpha_fp64).
+//
+// upper_c = false leaves the upper form's coefficients out (they are zero in
+// out.U): its constant, radius and out.ahi do not depend on them, and a sweep
+// whose upper sums are final uses no more than those.
 template <int M, class R = float, class RE = R>
 __device__ __forceinline__ void pixel_alpha(const RE *__restrict__ r, R ux, R uy, AlphaOut<M, R> &out,
-                                            R *m_out = nullptr)
+                                            R *m_out = nullptr, bool upper_c = true)
 {
     using RL = Rec<M>;
     using N = Num<R>;
@@ -140,12 +147,12 @@ __device__ __forceinline__ void pixel_alpha(const RE *__restrict__ r, R ux, R uy
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         B w0, w1;
-        load_sbw<M, R, RE>(r + RL::W0 + c * RL::WS, w0);
-        load_sbw<M, R, RE>(r + RL::W0 + (3 + c) * RL::WS, w1);
+        const R m0 = load_sbw<M, R, RE>(r + RL::W0 + c * RL::WS, w0);
+        const R m1 = load_sbw<M, R, RE>(r + RL::W0 + (3 + c) * RL::WS, w1);
         SAcc<M, R> pq;
         pq.init(0, 0);
-        pq.mul(Dx, w0);
-        pq.mul(Dy, w1);
+        pq.mul_ym(Dx, w0, m0);
+        pq.mul_ym(Dy, w1, m1);
         const B q = pq.result();
         pm.sqr(q);
     }
@@ -173,7 +180,7 @@ __device__ __forceinline__ void pixel_alpha(const RE *__restrict__ r, R ux, R uy
     const R e2 = N::mul_ru(o, el_up), s2 = N::mul_ru(o, s);
     Acc<M, R, false> ua;
     ua.init(N::fma_ru(-s2, xl, e2));
-    ua.term_ck(R(-0.5) * s2, m.c, m.klo, m.r);
+    ua.term_ck(R(-0.5) * s2, m.c, m.klo, m.r, upper_c);
     LF<M, R> Ua = ua.result();
     const R rUa = ua.radius_bound();
     const R amax = N::add_ru(Ua.k, rUa);
@@ -192,7 +199,7 @@ __device__ __forceinline__ void pixel_alpha(const RE *__restrict__ r, R ux, R uy
         Acc<M, R, false> u1;
         const R keep = R(1) - psi2;
         u1.init(N::mul_ru(keep, N::mul_ru(N::sub_ru(R(1), lam), o)));
-        u1.term(keep * lam, Ua, rUa);
+        u1.term(keep * lam, Ua, rUa, upper_c);
         out.U = u1.result();
         out.rU = u1.radius_bound();
     }
@@ -589,6 +596,10 @@ __global__ void __launch_bounds__(RenderShape<TS, F64>::NTH, RenderShape<TS, F64
         // the FP64 instance sweeps only the pixels the FP32 sweep listed
         bool done = !inside || !active;
         float lo_adj = 0.f, hi_adj = 0.f;  // -1: decided 0 / 1; >= 0: widening for skipped events
+        // the upper sums' constants have reached 1 in every channel (interval
+        // blend): final, because they only grow, so the upper bounds are 1
+        // and the sweep stops adding to them
+        bool hi_fix = false;
         bool abandoned = false;
         uint32_t swept = b1 - b0;  // entries swept before the tile stopped
         uint32_t seg_evals = 0, seg_recomp = 0, seg_wide = 0;
@@ -649,6 +660,7 @@ __global__ void __launch_bounds__(RenderShape<TS, F64>::NTH, RenderShape<TS, F64
                     lo_zero = lo_zero && __fadd_ru(lo.upper_min(ch), elo2) <= 0.f;
                     hi_one = hi_one && (REL ? hk[ch] : hi.k[ch]) >= 1.f;
                 }
+                if (!REL) hi_fix = hi_one;
                 const bool lo_dec = lo_zero || elo2 <= EXIT_EPS;
                 const bool hi_dec = hi_one || ehi2 <= EXIT_EPS;
                 if (lo_dec && hi_dec) {
@@ -709,7 +721,7 @@ __global__ void __launch_bounds__(RenderShape<TS, F64>::NTH, RenderShape<TS, F64
                     }
                 }
                 if (!have) {
-                    pixel_alpha<M>(r, ux, uy, cache);
+                    pixel_alpha<M>(r, ux, uy, cache, (float *)nullptr, lower && !hi_fix);
                     // a wide m interval: the Exp stage's points in FP64 where
                     // the FP32 deviation, weighted by how much this pixel's
                     // bounds can still move with it, exceeds the threshold.
@@ -752,7 +764,7 @@ __global__ void __launch_bounds__(RenderShape<TS, F64>::NTH, RenderShape<TS, F64
                 const float col[3] = {r[RL::COL], r[RL::COL + 1], r[RL::COL + 2]};
                 const float colh[3] = {r[RL::COL_HI], r[RL::COL_HI + 1], r[RL::COL_HI + 2]};
                 if (lower) {
-                    hi.add(PB, colh, cache.U, cache.rU);
+                    if (!hi_fix) hi.add(PB, colh, cache.U, cache.rU);
                     if (REL) {
 #pragma unroll
                         for (int ch = 0; ch < 3; ++ch) hk[ch] = __fmaf_ru(__fmul_ru(PB, colh[ch]), cache.U.k, hk[ch]);
