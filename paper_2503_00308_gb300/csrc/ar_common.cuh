@@ -56,8 +56,11 @@ template <int M> struct CellData {
 
 // Per-(Gaussian, cell) record read by the per-pixel kernel, in elements of
 // the record precision (float for the batched renderer, double for the plain
-// one).  A bounded scalar with shared coefficients is stored as c[M], klo,
-// khi, r (SB), the W entries also with their concretisation vlo, vhi.
+// one).  A bounded scalar with shared coefficients is stored as c[M], -klo,
+// khi, r (SB), the W entries also with their concretisation -vlo, vhi and the
+// midpoint of [vlo, vhi].  The lower ends are stored negated: the FP32 pixel
+// stage holds each (lower, upper) pair as (-lo, hi) and updates both ends in
+// one packed operation rounded up.
 //
 // Delta = S u - P (Algorithm 1 line 9 with S = d^2, P = d up) is stored as
 //   Delta.lo = (u - mu) S.lo + R.lo,  R.lo = mu S.lo - P.hi,
@@ -71,9 +74,9 @@ template <int M> struct CellData {
 // Every entry starts on a multiple of 4 elements, so that the pixel stage reads
 // it with 16-byte vector loads.
 template <int M> struct Rec {
-    static constexpr int SBW = (M + 3 + 3) / 4 * 4;  // c[M], klo, khi, r (padded)
+    static constexpr int SBW = (M + 3 + 3) / 4 * 4;  // c[M], -klo, khi, r (padded)
     static constexpr int S = 0, RX = SBW, RY = 2 * SBW;
-    static constexpr int WS = (M + 5 + 3) / 4 * 4;   // c[M], klo, khi, vlo, vhi, r (padded)
+    static constexpr int WS = (M + 5 + 3) / 4 * 4;   // c[M], -klo, khi, -vlo, vhi, r, mid (padded)
     static constexpr int W0 = 3 * SBW;               // W_rc at W0 + (3 r + c) WS
     // scalars: o_hi, tau_dn, tau_up, c_lo[3], flags, mu_x, mu_y, gap_s, o_lo, c_hi[3]
     // (the opacity and colour boxes of the scene parameters; lo = hi without boxes)

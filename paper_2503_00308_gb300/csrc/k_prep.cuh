@@ -260,27 +260,28 @@ __device__ __forceinline__ void rec_put_flags(float *dst, uint32_t f) { *dst = _
 __device__ __forceinline__ void rec_put_flags(double *dst, uint32_t f) { *dst = (double)f; }
 
 // ------------------------------------------------------------- records
-// c[M], klo, khi, r (the S and R entries of a record)
+// c[M], -klo, khi, r (the S and R entries of a record; the lower end negated)
 template <int M, class R>
 __device__ __forceinline__ void store_sb(R *dst, const SB<M, R> &b)
 {
 #pragma unroll
     for (int j = 0; j < M; ++j) dst[j] = b.c[j];
-    dst[M] = b.klo;
+    dst[M] = -b.klo;
     dst[M + 1] = b.khi;
     dst[M + 2] = b.r;
 }
-// c[M], klo, khi, vlo, vhi, r, mid (the W entries; mid = sb_mid(b), the slope
-// the pixel stage's product Delta W takes for Delta, kept in the padding)
+// c[M], -klo, khi, -vlo, vhi, r, mid (the W entries, the lower ends negated;
+// mid = sb_mid(b), the slope the pixel stage's product Delta W takes for
+// Delta, kept in the padding)
 template <int M, class R>
 __device__ __forceinline__ void store_sbw(R *dst, const SB<M, R> &b)
 {
     static_assert(M + 5 < Rec<M>::WS, "the W entry has no room for its midpoint");
 #pragma unroll
     for (int j = 0; j < M; ++j) dst[j] = b.c[j];
-    dst[M] = b.klo;
+    dst[M] = -b.klo;
     dst[M + 1] = b.khi;
-    dst[M + 2] = b.vlo;
+    dst[M + 2] = -b.vlo;
     dst[M + 3] = b.vhi;
     dst[M + 4] = b.r;
     dst[M + 5] = sb_mid(b);

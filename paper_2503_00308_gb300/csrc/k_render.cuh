@@ -47,7 +47,7 @@ __device__ __forceinline__ void load_vec(const double *src, double *dst)
     for (int q = 0; q < n / 2; ++q) reinterpret_cast<double2 *>(dst)[q] = reinterpret_cast<const double2 *>(src)[q];
 }
 
-// c[M], klo, khi, r (S and R entries; vlo, vhi are not needed).  The record
+// c[M], -klo, khi, r (S and R entries; vlo, vhi are not needed).  The record
 // element type RE may be narrower than the arithmetic type R (an FP32 record
 // evaluated in FP64): the conversion is exact.
 template <int M, class R, class RE>
@@ -57,13 +57,13 @@ __device__ __forceinline__ void load_sb(const RE *src, SB<M, R> &b)
     load_vec<Rec<M>::SBW>(src, v);
 #pragma unroll
     for (int j = 0; j < M; ++j) b.c[j] = (R)v[j];
-    b.klo = (R)v[M];
+    b.klo = -(R)v[M];
     b.khi = (R)v[M + 1];
     b.r = (R)v[M + 2];
 }
 
-// c[M], klo, khi, vlo, vhi, r (W entries); returns sb_mid(b), read from the
-// record where it was computed in the same precision, else computed here
+// c[M], -klo, khi, -vlo, vhi, r, mid (W entries); returns sb_mid(b), read
+// from the record where it was computed in the same precision, else computed
 template <int M, class R, class RE>
 __device__ __forceinline__ R load_sbw(const RE *src, SB<M, R> &b)
 {
@@ -71,9 +71,9 @@ __device__ __forceinline__ R load_sbw(const RE *src, SB<M, R> &b)
     load_vec<Rec<M>::WS>(src, v);
 #pragma unroll
     for (int j = 0; j < M; ++j) b.c[j] = (R)v[j];
-    b.klo = (R)v[M];
+    b.klo = -(R)v[M];
     b.khi = (R)v[M + 1];
-    b.vlo = (R)v[M + 2];
+    b.vlo = -(R)v[M + 2];
     b.vhi = (R)v[M + 3];
     b.r = (R)v[M + 4];
     if constexpr (sizeof(R) == sizeof(RE)) return v[M + 5];
@@ -87,39 +87,16 @@ __device__ __forceinline__ double clamp01(double x) { return fmin(1.0, fmax(0.0,
 __device__ __forceinline__ uint32_t rec_flags(const float *r, int at) { return __float_as_uint(r[at]); }
 __device__ __forceinline__ uint32_t rec_flags(const double *r, int at) { return (uint32_t)r[at]; }
 
-// Effective-opacity bounds of one (Gaussian, cell) record at pixel (ux, uy),
-// in the arithmetic of R from a record of element type RE.
-//
-// out.dev estimates how far evaluating in R's precision moves alo and ahi: m
-// is a small difference of terms of magnitude about |m_lo| + |m_hi|, so its
-// ends move by about 32 u (|m_lo| + |m_hi|), and a = o e^(-m/2) moves by half
-// of that times a (a_hi only while m_lo > 0: below that the secant ends at
-// x = 0 and a_hi = o).  The FP32 renderer evaluates the pair again in FP64
-// where this estimate exceeds its threshold (pixel_alpha_fp64).
-//
-// upper_c = false leaves the upper form's coefficients out (they are zero in
-// out.U): its constant, radius and out.ahi do not depend on them, and a sweep
-// whose upper sums are final uses no more than those.
-template <int M, class R = float, class RE = R>
-__device__ __forceinline__ void pixel_alpha(const RE *__restrict__ r, R ux, R uy, AlphaOut<M, R> &out,
-                                            R *m_out = nullptr, bool upper_c = true)
+// The bounded m of a record at pixel (ux, uy) (Algorithm 1 line 10 relaxed):
+// Delta = S u - P, held as (u - mu) S + R (see Rec): the lower form takes
+// S.lo and R.lo whatever the sign of u - mu (the pair is u S.lo - P.hi
+// exactly); where u - mu < 0 the conversion gap of S is covered.  Then
+// q = Delta^T W by McCormick products and m = sum_c q_c^2.
+template <int M, class R, class RE>
+__device__ __forceinline__ SB<M, R> m_form(const RE *__restrict__ r, R ux, R uy)
 {
     using RL = Rec<M>;
     using N = Num<R>;
-    // opacity box [o_lo, o]: o_lo scales the lower forms, o the upper ones
-    const R o = r[RL::O], o_lo = r[RL::O_LO];
-    const uint32_t flags = rec_flags(r, RL::FLAGS);
-    out.dev = 0;
-    if (flags & F_FALLBACK) {
-#pragma unroll
-        for (int j = 0; j < M; ++j) { out.L.c[j] = 0; out.U.c[j] = 0; }
-        out.L.k = 0; out.U.k = o; out.rL = 0; out.rU = 0;
-        out.alo = 0; out.ahi = o;
-        return;
-    }
-    // Delta = S u - P, held as (u - mu) S + R (see Rec): the lower form takes
-    // S.lo and R.lo whatever the sign of u - mu (the pair is u S.lo - P.hi
-    // exactly); where u - mu < 0 the conversion gap of S is covered
     typedef SB<M, R> B;
     B Dx, Dy;
     {
@@ -156,7 +133,209 @@ __device__ __forceinline__ void pixel_alpha(const RE *__restrict__ r, R ux, R uy
         const B q = pq.result();
         pm.sqr(q);
     }
-    const B m = pm.result();
+    return pm.result();
+}
+
+// ---------------------------------------------------------------------------
+// The same chain in FP32 with the lower and upper constants of every pair
+// held together as the float2 (-lo, hi).  Directed rounding is symmetric
+// under negation, RD(x) = -RU(-x) for every operation (signed zeros
+// included), so both ends move in one packed operation rounded up
+// (__ffma2_ru, __fadd2_ru, __fmul2_ru), and each end gets the bits of the
+// scalar SAcc operation it stands for; m_form_packed returns m_form's value.
+template <int M> struct PSB {
+    float c[M];
+    float2 k;  // (-klo, khi)
+    float r;
+    float2 v;  // (-vlo, vhi)
+};
+
+// S and R entries: c[M], -klo, khi, r
+template <int M>
+__device__ __forceinline__ void load_psb(const float *src, PSB<M> &b)
+{
+    float v[Rec<M>::SBW];
+    load_vec<Rec<M>::SBW>(src, v);
+#pragma unroll
+    for (int j = 0; j < M; ++j) b.c[j] = v[j];
+    b.k = make_float2(v[M], v[M + 1]);
+    b.r = v[M + 2];
+}
+// W entries: c[M], -klo, khi, -vlo, vhi, r; returns the stored midpoint
+template <int M>
+__device__ __forceinline__ float load_psbw(const float *src, PSB<M> &b)
+{
+    float v[Rec<M>::WS];
+    load_vec<Rec<M>::WS>(src, v);
+#pragma unroll
+    for (int j = 0; j < M; ++j) b.c[j] = v[j];
+    b.k = make_float2(v[M], v[M + 1]);
+    b.v = make_float2(v[M + 2], v[M + 3]);
+    b.r = v[M + 4];
+    return v[M + 5];
+}
+
+// SAcc<M, float> with packed constants
+template <int M> struct PSAcc {
+    float c[M];
+    float2 k;  // (-klo, khi)
+    float rs, ex;
+    int n;
+
+    __device__ __forceinline__ void init()
+    {
+#pragma unroll
+        for (int j = 0; j < M; ++j) c[j] = 0.f;
+        k = make_float2(-0.f, 0.f);  // the negation of +0, and +0
+        rs = 0.f;
+        ex = 0.f;
+        n = 0;
+    }
+    // SAcc::term_same_side
+    __device__ __forceinline__ void term_same_side(float a, const PSB<M> &x)
+    {
+        axpy_rn<M>(a, x.c, c);
+        k = __ffma2_ru(make_float2(a, a), x.k, k);
+        rs = __fmaf_ru(fabsf(a), x.r, rs);
+        ++n;
+    }
+    // SAcc::term: for a < 0 the lower end takes (-a) x.hi, the upper one
+    // (-a) (-x.lo)
+    __device__ __forceinline__ void term(float a, const PSB<M> &x)
+    {
+        axpy_rn<M>(a, x.c, c);
+        const bool pos = a >= 0.f;
+        const float b = pos ? a : -a;
+        const float2 p = pos ? x.k : make_float2(x.k.y, x.k.x);
+        k = __ffma2_ru(make_float2(b, b), p, k);
+        rs = __fmaf_ru(fabsf(a), x.r, rs);
+        ++n;
+    }
+    // SAcc::mul_ym.  The constants (-dlo, dhi) are
+    //   (RU(RU(xl yl + RU(xh yh)) / 2), RU(RU(xh (-yl) + RU((-xl) yh)) / 2)),
+    // the second being -RD(RD(xh yl + RD(xl yh)) / 2).
+    __device__ __forceinline__ void mul_ym(const PSB<M> &x, const PSB<M> &y, float ym)
+    {
+        const float nxl = x.v.x, xh = x.v.y, nyl = y.v.x, yh = y.v.y;
+        const float xm = __fmul_rn(xh - nxl, 0.5f);  // sb_mid(x)
+        term(ym, x);
+        term(xm, y);
+        const float2 q = __ffma2_ru(x.v, make_float2(nyl, nyl), make_float2(__fmul_ru(xh, yh), __fmul_ru(nxl, yh)));
+        k = __fadd2_ru(k, __fmul2_ru(q, make_float2(0.5f, 0.5f)));
+        const float xa = fmaxf(fabsf(nxl), fabsf(xh)), ya = fmaxf(fabsf(nyl), fabsf(yh));
+        ex = __fadd_ru(ex, __fmul_ru(__fmaf_ru(fabsf(ym), xa, __fmul_ru(fabsf(xm), ya)), Num<float>::U * 1.001f));
+    }
+    // SAcc::sqr: the constants (-dlo, dhi) are
+    //   (RU(cm cm), max(RU(xl xl + RU(-s xl)), RU(xh xh + RU(-s xh))))
+    __device__ __forceinline__ void sqr(const PSB<M> &x)
+    {
+        const float nxl = x.v.x, xh = x.v.y;
+        const float s = xh - nxl;
+        const float cm = __fmul_rn(s, 0.5f);
+        term(s, x);
+        const float2 e = __ffma2_ru(x.v, x.v, __fmul2_ru(make_float2(s, -s), x.v));
+        k = __fadd2_ru(k, make_float2(__fmul_ru(cm, cm), fmaxf(e.x, e.y)));
+    }
+    // SAcc::result with sb_finish
+    __device__ __forceinline__ PSB<M> result() const
+    {
+        const float sl = __fadd_ru(__fmaf_ru(gamma_n<float>(n), rs, ex), Num<float>::TINY);
+        PSB<M> b;
+#pragma unroll
+        for (int j = 0; j < M; ++j) b.c[j] = c[j];
+        b.k = __fadd2_ru(k, make_float2(sl, sl));
+        float r = 0.f;
+#pragma unroll
+        for (int j = 0; j < M; ++j) r = __fadd_ru(r, fabsf(c[j]));
+        b.r = r;
+        b.v = __fadd2_ru(b.k, make_float2(r, r));
+        return b;
+    }
+};
+
+template <int M>
+__device__ __forceinline__ SB<M, float> m_form_packed(const float *__restrict__ r, float ux, float uy)
+{
+    using RL = Rec<M>;
+    PSB<M> Dx, Dy;
+    {
+        PSB<M> S, Rr;
+        load_psb<M>(r + RL::S, S);
+        const float dx = ux - r[RL::MU_X], dy = uy - r[RL::MU_Y];
+        const float gap = r[RL::GAP_S];
+        PSAcc<M> a;
+        load_psb<M>(r + RL::RX, Rr);
+        a.init();
+        a.term_same_side(dx, S);
+        a.term(1.f, Rr);
+        if (dx < 0.f) a.ex = __fadd_ru(a.ex, __fmul_ru(-dx, gap));
+        Dx = a.result();
+        load_psb<M>(r + RL::RY, Rr);
+        a.init();
+        a.term_same_side(dy, S);
+        a.term(1.f, Rr);
+        if (dy < 0.f) a.ex = __fadd_ru(a.ex, __fmul_ru(-dy, gap));
+        Dy = a.result();
+    }
+    PSAcc<M> pm;
+    pm.init();
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        PSB<M> w0, w1;
+        const float m0 = load_psbw<M>(r + RL::W0 + c * RL::WS, w0);
+        const float m1 = load_psbw<M>(r + RL::W0 + (3 + c) * RL::WS, w1);
+        PSAcc<M> pq;
+        pq.init();
+        pq.mul_ym(Dx, w0, m0);
+        pq.mul_ym(Dy, w1, m1);
+        pm.sqr(pq.result());
+    }
+    const PSB<M> p = pm.result();
+    SB<M, float> m;
+#pragma unroll
+    for (int j = 0; j < M; ++j) m.c[j] = p.c[j];
+    m.klo = -p.k.x;
+    m.khi = p.k.y;
+    m.r = p.r;
+    m.vlo = -p.v.x;
+    m.vhi = p.v.y;
+    return m;
+}
+
+// Effective-opacity bounds of one (Gaussian, cell) record at pixel (ux, uy),
+// in the arithmetic of R from a record of element type RE.
+//
+// out.dev estimates how far evaluating in R's precision moves alo and ahi: m
+// is a small difference of terms of magnitude about |m_lo| + |m_hi|, so its
+// ends move by about 32 u (|m_lo| + |m_hi|), and a = o e^(-m/2) moves by half
+// of that times a (a_hi only while m_lo > 0: below that the secant ends at
+// x = 0 and a_hi = o).  The FP32 renderer evaluates the pair again in FP64
+// where this estimate exceeds its threshold (pixel_alpha_fp64).
+//
+// upper_c = false leaves the upper form's coefficients out (they are zero in
+// out.U): its constant, radius and out.ahi do not depend on them, and a sweep
+// whose upper sums are final uses no more than those.
+template <int M, class R = float, class RE = R>
+__device__ __forceinline__ void pixel_alpha(const RE *__restrict__ r, R ux, R uy, AlphaOut<M, R> &out,
+                                            R *m_out = nullptr, bool upper_c = true)
+{
+    using RL = Rec<M>;
+    using N = Num<R>;
+    // opacity box [o_lo, o]: o_lo scales the lower forms, o the upper ones
+    const R o = r[RL::O], o_lo = r[RL::O_LO];
+    const uint32_t flags = rec_flags(r, RL::FLAGS);
+    out.dev = 0;
+    if (flags & F_FALLBACK) {
+#pragma unroll
+        for (int j = 0; j < M; ++j) { out.L.c[j] = 0; out.U.c[j] = 0; }
+        out.L.k = 0; out.U.k = o; out.rL = 0; out.rU = 0;
+        out.alo = 0; out.ahi = o;
+        return;
+    }
+    typedef SB<M, R> B;
+    B m;
+    if constexpr (sizeof(R) == sizeof(float) && sizeof(RE) == sizeof(float)) m = m_form_packed<M>(r, ux, uy);
+    else m = m_form<M, R, RE>(r, ux, uy);
     const R mlo = m.vlo, mhi = m.vhi;
     if (m_out) {
         m_out[0] = mlo;
@@ -424,21 +603,30 @@ __device__ __forceinline__ float open_ratio_up(float a)
 //   event info and pixel boxes (the next chunk is copied in while the current
 //   one is swept),
 //   and a per-thread ring of the last RING opacity evaluations made at lower
-//   endpoints (record id + alo, ahi, rL, L), stored column-per-thread so that
-//   every access is bank-conflict free.  The ring lets the upper endpoint of
+//   endpoints (record id + alo, ahi, rL, L, the latter as 16-byte vectors),
+//   stored column-per-thread so that every access is bank-conflict free.  The ring lets the upper endpoint of
 //   a Gaussian reuse the evaluation made at its lower endpoint; an upper
 //   endpoint whose evaluation has left the ring evaluates again.
 // NTH: threads per CTA (the tile's pixels, or one warp for the FP64 instance)
 template <int M, int TS, int CH, int RING, int NTH = TS * TS> struct RenderSmem {
     static constexpr int NT = NTH;
     static constexpr int PAY = M + 4;  // alo, ahi, rL, L.k, L.c[M]
+    static constexpr int PV = (PAY + 3) / 4;  // ... as 16-byte vectors (the last one padded)
     static constexpr size_t REC = 2 * sizeof(float) * CH * Rec<M>::WIDTH;  // two chunk buffers
     static constexpr size_t EV = 2 * sizeof(EvInfo) * CH;
     static constexpr size_t BOX = 2 * sizeof(PixBox) * CH;
     static constexpr size_t RID = sizeof(uint32_t) * RING * NT;
-    static constexpr size_t RPAY = sizeof(float) * RING * PAY * NT;
+    static constexpr size_t RPAY = sizeof(float4) * RING * PV * NT;
     static constexpr size_t BYTES = REC + EV + BOX + RID + RPAY + 16;
 };
+
+// element i of an array of float4 (i a compile-time constant after unrolling)
+template <int N>
+__device__ __forceinline__ float f4_at(const float4 (&v)[N], int i)
+{
+    const float4 &t = v[i >> 2];
+    return (i & 3) == 0 ? t.x : (i & 3) == 1 ? t.y : (i & 3) == 2 ? t.z : t.w;
+}
 
 // 16-byte asynchronous global -> shared copies (completed by cp_async_wait_all)
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
@@ -510,7 +698,7 @@ __global__ void __launch_bounds__(RenderShape<TS, F64>::NTH, RenderShape<TS, F64
     EvInfo *s_ev2 = reinterpret_cast<EvInfo *>(smem_raw + SM::REC);                    // [2 * CH]
     PixBox *s_box2 = reinterpret_cast<PixBox *>(smem_raw + SM::REC + SM::EV);          // [2 * CH]
     uint32_t *s_rid = reinterpret_cast<uint32_t *>(smem_raw + SM::REC + SM::EV + SM::BOX);
-    float *s_pay = reinterpret_cast<float *>(smem_raw + SM::REC + SM::EV + SM::BOX + SM::RID);
+    float4 *s_pay = reinterpret_cast<float4 *>(smem_raw + SM::REC + SM::EV + SM::BOX + SM::RID);
     uint32_t *s_next = reinterpret_cast<uint32_t *>(smem_raw + SM::REC + SM::EV + SM::BOX + SM::RID + SM::RPAY);
     const int tid = threadIdx.x;
     uint32_t evals = 0, recomp = 0, wide = 0;
@@ -706,18 +894,22 @@ __global__ void __launch_bounds__(RenderShape<TS, F64>::NTH, RenderShape<TS, F64
                 n_open += lower ? 1 : -1;
                 bool have = !lower && c_rec == ev.rec;
                 if (!lower && !have) {
+                    int hit = -1;
 #pragma unroll
-                    for (int k = 0; k < RING; ++k) {
-                        if (s_rid[k * NT + tid] == ev.rec) {
-                            const float *pp = s_pay + (size_t)k * SM::PAY * NT + tid;
-                            cache.alo = pp[0];
-                            cache.ahi = pp[NT];
-                            cache.rL = pp[2 * NT];
-                            cache.L.k = pp[3 * NT];
+                    for (int k = 0; k < RING; ++k)
+                        if (s_rid[k * NT + tid] == ev.rec) hit = k;
+                    if (hit >= 0) {
+                        const float4 *pp = s_pay + (size_t)hit * SM::PV * NT + tid;
+                        float4 v[SM::PV];
 #pragma unroll
-                            for (int j = 0; j < M; ++j) cache.L.c[j] = pp[(4 + j) * NT];
-                            have = true;
-                        }
+                        for (int q = 0; q < SM::PV; ++q) v[q] = pp[q * NT];
+                        cache.alo = v[0].x;
+                        cache.ahi = v[0].y;
+                        cache.rL = v[0].z;
+                        cache.L.k = v[0].w;
+#pragma unroll
+                        for (int j = 0; j < M; ++j) cache.L.c[j] = f4_at(v, 4 + j);
+                        have = true;
                     }
                 }
                 if (!have) {
@@ -780,13 +972,11 @@ __global__ void __launch_bounds__(RenderShape<TS, F64>::NTH, RenderShape<TS, F64
                     const int k = (int)(head % RING);
                     ++head;
                     s_rid[k * NT + tid] = ev.rec;
-                    float *pp = s_pay + (size_t)k * SM::PAY * NT + tid;
-                    pp[0] = cache.alo;
-                    pp[NT] = cache.ahi;
-                    pp[2 * NT] = cache.rL;
-                    pp[3 * NT] = cache.L.k;
+                    float4 *pp = s_pay + (size_t)k * SM::PV * NT + tid;
+                    auto pay = [&](int i) { return i < 4 ? (i == 0 ? cache.alo : i == 1 ? cache.ahi : i == 2 ? cache.rL : cache.L.k)
+                                                         : (i < 4 + M ? cache.L.c[i < 4 + M ? i - 4 : 0] : 0.f); };
 #pragma unroll
-                    for (int j = 0; j < M; ++j) pp[(4 + j) * NT] = cache.L.c[j];
+                    for (int q = 0; q < SM::PV; ++q) pp[q * NT] = make_float4(pay(4 * q), pay(4 * q + 1), pay(4 * q + 2), pay(4 * q + 3));
                 } else {
                     open_w = fmaxf(0.f, __fsub_ru(open_w, open_ratio_up(cache.ahi)));
                     const uint32_t flags = __float_as_uint(r[RL::FLAGS]);
@@ -998,12 +1188,12 @@ __global__ void debug_alpha_kernel(const float *__restrict__ recs, int n, const 
     o[6] = a.L.k; o[13] = a.U.k;
     o[14] = a.rL; o[15] = a.rU; o[16] = a.alo; o[17] = a.ahi; o[18] = a.dev; o[19] = mlo; o[20] = mhi;
     for (int e = 0; e < 6; ++e) {
-        o[21 + 2 * e] = r[RL::W0 + e * RL::WS + M + 2];
+        o[21 + 2 * e] = -r[RL::W0 + e * RL::WS + M + 2];
         o[22 + 2 * e] = r[RL::W0 + e * RL::WS + M + 3];
     }
     const int sb[3] = {RL::S, RL::RX, RL::RY};
     for (int q = 0; q < 3; ++q) {
-        o[33 + 2 * q] = (double)r[sb[q] + M] - (double)r[sb[q] + M + 2];
+        o[33 + 2 * q] = -(double)r[sb[q] + M] - (double)r[sb[q] + M + 2];
         o[34 + 2 * q] = (double)r[sb[q] + M + 1] + (double)r[sb[q] + M + 2];
     }
     o[39] = (double)__float_as_uint(r[RL::FLAGS]);
