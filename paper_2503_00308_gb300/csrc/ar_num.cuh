@@ -247,9 +247,9 @@ template <int M, class R>
 __device__ __forceinline__ void sb_finish(SB<M, R> &b)
 {
     using N = Num<R>;
-    R r = 0;
+    R r = N::abs(b.c[0]);  // = RU(0 + |c_0|)
 #pragma unroll
-    for (int j = 0; j < M; ++j) r = N::add_ru(r, N::abs(b.c[j]));
+    for (int j = 1; j < M; ++j) r = N::add_ru(r, N::abs(b.c[j]));
     b.r = r;
     b.vlo = N::sub_rd(b.klo, r);
     b.vhi = N::add_ru(b.khi, r);
