@@ -53,13 +53,13 @@ BOOKKEEPING_FLOPS_PER_TRIPLE = 156
 
 # DRAM bytes of the render kernel per opacity evaluation, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of round 0 of the first 4
-# cells of the 300k-Gaussian workload, both instances (FP32 sweep 34.8 MB, FP64
-# re-sweep 15.3 MB), over the render's 73.2M evaluations.  Valid only for the
+# cells of the 300k-Gaussian workload, both instances (FP32 sweep 35.8 MB, FP64
+# re-sweep 15.2 MB), over the render's 73.2M evaluations.  Valid only for the
 # kernel sources it was taken from (their SHA-256 below); otherwise the
 # roofline's traffic is reported as null.
-RENDER_TRAFFIC = {"bytes_per_evaluation": (27405056 + 7374336 + 14476288 + 822272) / 73160149,
+RENDER_TRAFFIC = {"bytes_per_evaluation": (27406080 + 8434944 + 14498816 + 726784) / 73160149,
                   "sources": ["k_render.cuh", "ar_num.cuh", "ar_common.cuh", "k_inst.cuh"],
-                  "sha256": "9b247f98615f8610da6e25ef7fac6c5446332002a7750c02396de9cce4d5c100"}
+                  "sha256": "b67ddf18717487802c5e3997236170be770f07c50c36d4eb8088f2fc927ef2d1"}
 
 
 def render_traffic(n_evaluated: int):
