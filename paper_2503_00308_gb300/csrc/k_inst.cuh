@@ -89,7 +89,7 @@ static int launch_render_ts(const RenderLaunch &a, cudaStream_t st)
     // shared memory small)
     constexpr int RING = 4;
     typedef RenderShape<TS, F64> SH;
-    typedef RenderSmem<AR_M, TS, CH, RING, SH::NTH> SM;
+    typedef RenderSmem<AR_M, TS, CH, RING, SH::NTH, SH::NBUF> SM;
     auto kern = render_kernel<AR_M, TS, CH, RING, REL, F64>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::BYTES) != cudaSuccess)
         return 1;

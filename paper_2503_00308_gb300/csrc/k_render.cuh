@@ -597,24 +597,26 @@ __device__ __forceinline__ float open_ratio_up(float a)
     return den > 0.f ? __fmul_ru(__fdividef(a, den), 1.000000477f) : 3.0e38f;
 }
 
-// Shared-memory layout of the render kernel (dynamic; about 60 KB at six
+// Shared-memory layout of the render kernel (dynamic; about 70 KB at six
 // pose variables, tile 16, chunks of 16 and a ring of 4, so two CTAs fit on an SM):
-//   two buffers, each with the records staged for a chunk of CH events, their
-//   event info and pixel boxes (the next chunk is copied in while the current
-//   one is swept),
+//   two buffers (one in the FP64 instance), each with the records staged for
+//   a chunk of CH events, their event info and pixel boxes (the next chunk is
+//   copied in while the current one is swept),
 //   and a per-thread ring of the last RING opacity evaluations made at lower
 //   endpoints (record id + alo, ahi, rL, L, the latter as 16-byte vectors),
 //   stored column-per-thread so that every access is bank-conflict free.  The ring lets the upper endpoint of
 //   a Gaussian reuse the evaluation made at its lower endpoint; an upper
 //   endpoint whose evaluation has left the ring evaluates again.
-// NTH: threads per CTA (the tile's pixels, or one warp for the FP64 instance)
-template <int M, int TS, int CH, int RING, int NTH = TS * TS> struct RenderSmem {
+// NTH: threads per CTA (the tile's pixels, or one warp for the FP64 instance);
+// NBUF: chunk buffers (two, or one for the FP64 instance, whose one-warp CTAs
+// then fit fourteen to an SM instead of nine)
+template <int M, int TS, int CH, int RING, int NTH = TS * TS, int NBUF = 2> struct RenderSmem {
     static constexpr int NT = NTH;
     static constexpr int PAY = M + 4;  // alo, ahi, rL, L.k, L.c[M]
     static constexpr int PV = (PAY + 3) / 4;  // ... as 16-byte vectors (the last one padded)
-    static constexpr size_t REC = 2 * sizeof(float) * CH * Rec<M>::WIDTH;  // two chunk buffers
-    static constexpr size_t EV = 2 * sizeof(EvInfo) * CH;
-    static constexpr size_t BOX = 2 * sizeof(PixBox) * CH;
+    static constexpr size_t REC = NBUF * sizeof(float) * CH * Rec<M>::WIDTH;  // chunk buffers
+    static constexpr size_t EV = NBUF * sizeof(EvInfo) * CH;
+    static constexpr size_t BOX = NBUF * sizeof(PixBox) * CH;
     static constexpr size_t RID = sizeof(uint32_t) * RING * NT;
     static constexpr size_t RPAY = sizeof(float4) * RING * PV * NT;
     static constexpr size_t BYTES = REC + EV + BOX + RID + RPAY + 16;
@@ -646,6 +648,7 @@ template <int TS> struct RenderOcc {
 // registers per thread as two 256-thread CTAs)
 template <int TS, bool F64> struct RenderShape {
     static constexpr int NTH = F64 ? 32 : TS * TS;
+    static constexpr int NBUF = F64 ? 1 : 2;  // chunk buffers (see RenderSmem)
     static constexpr int MIN_BLOCKS = F64 ? 16 : RenderOcc<TS>::MIN_BLOCKS;
     static constexpr int MASKW = TS * TS / 32 + 1;  // words per listed segment: pixel mask, abandon flag
 };
@@ -689,7 +692,7 @@ __global__ void __launch_bounds__(RenderShape<TS, F64>::NTH, RenderShape<TS, F64
 {
     using RL = Rec<M>;
     using SH = RenderShape<TS, F64>;
-    using SM = RenderSmem<M, TS, CH, RING, SH::NTH>;
+    using SM = RenderSmem<M, TS, CH, RING, SH::NTH, SH::NBUF>;
     constexpr int NT = SH::NTH;      // threads
     constexpr int NPIX = TS * TS;    // pixels of a tile
     constexpr int GROUPS = F64 ? NPIX / 32 : 1;  // work items per listed segment
@@ -835,7 +838,7 @@ __global__ void __launch_bounds__(RenderShape<TS, F64>::NTH, RenderShape<TS, F64
         // chunk it does not hold in full (the next binning phase gives the
         // segment its full list, and the sweep starts again: the exit tests
         // fall at the same entries, so the bounds are those of one sweep)
-        for (uint32_t base = b0; !abandoned && (base < b1 || incomplete); base += CH, buf ^= 1) {
+        for (uint32_t base = b0; !abandoned && (base < b1 || incomplete); base += CH, buf = (buf + 1) % SH::NBUF) {
             if (!done) {
                 const float left = (float)(total - (base - b0));
                 // PA is rounded down; 1.01 covers its relative error for < 10^5 factors
@@ -857,6 +860,12 @@ __global__ void __launch_bounds__(RenderShape<TS, F64>::NTH, RenderShape<TS, F64
                     hi_adj = hi_one ? -1.f : ehi2;
                 }
             }
+            // one buffer: the chunk is copied in once every thread has swept
+            // the previous one
+            if (SH::NBUF == 1 && base != b0) {
+                __syncthreads();
+                stage(0, base);
+            }
             cp_async_wait_all();  // this thread's copies of the current chunk
             if (__syncthreads_and(done)) {  // ... and everyone's, now visible
                 swept = base - b0;
@@ -873,7 +882,7 @@ __global__ void __launch_bounds__(RenderShape<TS, F64>::NTH, RenderShape<TS, F64
             }
             // the next chunk streams in while this one is swept; the buffer it
             // overwrites was swept by every thread before the barrier above
-            if (base + CH < b1) stage(buf ^ 1, base + CH);
+            if (SH::NBUF == 2 && base + CH < b1) stage(buf ^ 1, base + CH);
             const EvInfo *s_ev = s_ev2 + buf * CH;
             const PixBox *s_box = s_box2 + buf * CH;
             float(*s_rec)[RL::WIDTH] = s_rec2 + buf * CH;
