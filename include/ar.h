@@ -318,6 +318,9 @@ int ar_debug_records(ar_scene *scene, const ar_intrinsics *intr, const ar_nomina
  * in FP64 where the FP32 deviation estimate alone exceeds the scene's
  * ar_scene_set_fp64_alpha threshold (precision 1; the renderer also weights it
  * by the pixel's transmittance), or always in FP64 as well (precision 2).
+ * Precision 3 is precision 0 with the chain to the Mahalanobis term taken by
+ * scalar directed-rounding steps in place of the renderer's packed (-lo, hi)
+ * pairs: the outputs are the same bit for bit, which a test checks.
  * out: host, [n][40] doubles per pair: the lower opacity form (coefficients of
  * the 6 pose dimensions tx..rz over the cell normalised to [-1, 1], then the
  * constant), the upper form (7), the radii bounding the sums of the

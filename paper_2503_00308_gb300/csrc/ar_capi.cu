@@ -1600,7 +1600,7 @@ int ar_debug_alpha(ar_scene *s, const ar_intrinsics *in, const ar_nominal_pose *
     constexpr int OW = 42, W_OUT = 40;
     if (!s || !out || (n > 0 && (!gi || !px || !py))) return fail(AR_EINVAL, "null argument");
     if (n < 0 || n > (1 << 20)) return fail(AR_EINVAL, "n must be in [0, 2^20]");
-    if (precision < 0 || precision > 2) return fail(AR_EINVAL, "precision must be 0, 1 or 2");
+    if (precision < 0 || precision > 3) return fail(AR_EINVAL, "precision must be 0, 1, 2 or 3");
     for (int32_t t = 0; t < n; ++t)
         if (gi[t] < 0 || gi[t] >= s->n || px[t] < 0 || py[t] < 0 || px[t] >= in->width || py[t] >= in->height)
             return fail(AR_EINVAL, "triple %d out of range", t);

@@ -314,8 +314,10 @@ __device__ __forceinline__ SB<M, float> m_form_packed(const float *__restrict__ 
 //
 // upper_c = false leaves the upper form's coefficients out (they are zero in
 // out.U): its constant, radius and out.ahi do not depend on them, and a sweep
-// whose upper sums are final uses no more than those.
-template <int M, class R = float, class RE = R>
+// whose upper sums are final uses no more than those.  SCALAR = true takes the
+// FP32 chain to m with the scalar SAcc steps in place of the packed ones (the
+// same bits; a test hook checks that they are).
+template <int M, class R = float, class RE = R, bool SCALAR = false>
 __device__ __forceinline__ void pixel_alpha(const RE *__restrict__ r, R ux, R uy, AlphaOut<M, R> &out,
                                             R *m_out = nullptr, bool upper_c = true)
 {
@@ -334,7 +336,7 @@ __device__ __forceinline__ void pixel_alpha(const RE *__restrict__ r, R ux, R uy
     }
     typedef SB<M, R> B;
     B m;
-    if constexpr (sizeof(R) == sizeof(float) && sizeof(RE) == sizeof(float)) m = m_form_packed<M>(r, ux, uy);
+    if constexpr (!SCALAR && sizeof(R) == sizeof(float) && sizeof(RE) == sizeof(float)) m = m_form_packed<M>(r, ux, uy);
     else m = m_form<M, R, RE>(r, ux, uy);
     const R mlo = m.vlo, mhi = m.vhi;
     if (m_out) {
@@ -1180,7 +1182,8 @@ __global__ void debug_alpha_kernel(const float *__restrict__ recs, int n, const 
     AlphaOut<M, float> a;
     float m32[2] = {0.f, 0.f};
     double m64[2] = {0.0, 0.0};
-    pixel_alpha<M>(r, ux, uy, a, m32);
+    if (precision == 3) pixel_alpha<M, float, float, true>(r, ux, uy, a, m32);
+    else pixel_alpha<M>(r, ux, uy, a, m32);
     double mlo = m32[0], mhi = m32[1];
     int took = 0;
     if (precision == 2 || (precision == 1 && a.dev > fp64_dev)) {
