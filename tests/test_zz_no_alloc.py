@@ -59,10 +59,13 @@ def test_noalloc_matches_allocating_entry_point_twice():
 
 
 def test_noalloc_allocates_nothing():
-    """After warm-up calls, a new and larger request changes neither the
-    device's free memory nor the bytes torch's caching allocator holds.  (The
+    """After warm-up calls, a new and larger request takes no device memory
+    and leaves the bytes torch's caching allocator holds unchanged.  (The
     allocating entry point renders the larger request first, so that every
-    kernel both requests launch is already loaded on the device.)"""
+    kernel both requests launch is already loaded on the device.)  Free memory
+    is compared from below only: an allocation can only lower it, while the
+    driver may hand back, at any later launch, local memory it reserved for an
+    earlier kernel with a larger stack frame."""
     from paper_2503_00308_gb300 import _build, ar
     _build.build()
     sc = synth.object_scene(2500, 5)
@@ -82,7 +85,7 @@ def test_noalloc_allocates_nothing():
     ar.ar_render_abstract_noalloc(s.handle, intr, pose, cl, len(cl), 16, out_lo, out_hi, 0)
     torch.cuda.synchronize()
     free1, _ = torch.cuda.mem_get_info()
-    assert free1 == free0 and torch.cuda.memory_reserved() == reserved0
+    assert free1 >= free0 and torch.cuda.memory_reserved() == reserved0, (free0, free1)
     assert np.array_equal(out_lo.cpu().numpy(), ref_lo) and np.array_equal(out_hi.cpu().numpy(), ref_hi)
     s.close()
 
