@@ -53,13 +53,13 @@ BOOKKEEPING_FLOPS_PER_TRIPLE = 156
 
 # DRAM bytes of the render kernel per opacity evaluation, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of round 0 of the first 4
-# cells of the 300k-Gaussian workload, both instances (FP32 sweep 35.8 MB, FP64
-# re-sweep 15.2 MB), over the render's 73.2M evaluations.  Valid only for the
+# cells of the 300k-Gaussian workload, both instances (FP32 sweep 35.6 MB, FP64
+# re-sweep 15.0 MB), over the render's 73.2M evaluations.  Valid only for the
 # kernel sources it was taken from (their SHA-256 below); otherwise the
 # roofline's traffic is reported as null.
-RENDER_TRAFFIC = {"bytes_per_evaluation": (27406080 + 8434944 + 14498816 + 726784) / 73160149,
+RENDER_TRAFFIC = {"bytes_per_evaluation": (27421952 + 8210688 + 14208256 + 770304) / 73160149,
                   "sources": ["k_render.cuh", "ar_num.cuh", "ar_common.cuh", "k_inst.cuh"],
-                  "sha256": "b67ddf18717487802c5e3997236170be770f07c50c36d4eb8088f2fc927ef2d1"}
+                  "sha256": "8c9745917e963b6bda2abd316fbede1feb72bca27086a702d94f1fa9fdf3beea"}
 
 
 def render_traffic(n_evaluated: int):
