@@ -58,17 +58,24 @@ BOOKKEEPING_FLOPS_PER_TRIPLE = 156
 # kernel sources it was taken from (their SHA-256 below); otherwise the
 # roofline's traffic is reported as null.
 RENDER_TRAFFIC = {"bytes_per_evaluation": (27421952 + 8210688 + 14208256 + 770304) / 73160149,
+                  # the same capture's smsp__issue_active of the FP32 sweep (the bound of
+                  # this issue-limited kernel: one warp instruction per scheduler per cycle)
+                  "issue_active_fp32_sweep": 0.6353,
                   "sources": ["k_render.cuh", "ar_num.cuh", "ar_common.cuh", "k_inst.cuh"],
                   "sha256": "8c9745917e963b6bda2abd316fbede1feb72bca27086a702d94f1fa9fdf3beea"}
 
 
-def render_traffic(n_evaluated: int):
+def render_capture_valid() -> bool:
     import hashlib
     h = hashlib.sha256()
     for f in RENDER_TRAFFIC["sources"]:
         with open(os.path.join(ROOT, "paper_2503_00308_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    if h.hexdigest() != RENDER_TRAFFIC["sha256"]:
+    return h.hexdigest() == RENDER_TRAFFIC["sha256"]
+
+
+def render_traffic(n_evaluated: int):
+    if not render_capture_valid():
         return None
     return RENDER_TRAFFIC["bytes_per_evaluation"] * n_evaluated
 
@@ -659,7 +666,12 @@ def run_ours(args, rank, world, local, pg):
                      "triples_evaluated": stats["n_evaluated"],
                      "triples_in_boxes": stats["n_triples"],
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal: MEASURED_PEAKS.json has no FP32 figure)",
-                     "fp32_fma_probe_tflops": fma_probe(sp)},
+                     "fp32_fma_probe_tflops": fma_probe(sp),
+                     "issue_active_fp32_sweep": (RENDER_TRAFFIC["issue_active_fp32_sweep"]
+                                                 if render_capture_valid() else None),
+                     "issue_note": "ncu smsp__issue_active of the FP32 sweep on the first 4 cells, from the "
+                                   "capture the traffic figure comes from: the kernel is bound by instruction "
+                                   "issue (directed-rounding bookkeeping), not by FP32 FLOPs"},
         "stages_ms": {"prep": stats["ms_prep"], "bin": stats["ms_bin"], "build": stats["ms_build"],
                       "render": stats["ms_render"], "total": stats["ms_total"]},
         "counts": count_dict(stats),
