@@ -1298,7 +1298,9 @@ __global__ void __launch_bounds__(128) record_build_kernel(
 // Finishes the records of the pairs record_build_kernel deferred (list[0,
 // *count)): one warp per pair, every lane running the value chain of the pair
 // (the same values), the warp splitting its cell (SPLIT_WARP).  Grid-stride
-// over the list by warps.  counters as in record_build_kernel ([0] fallbacks,
+// over the list by warps, pair i on block i mod gridDim.x first, so that a
+// short list puts one pair on each SM instead of four on a few SMs sharing
+// their FP64 pipes.  counters as in record_build_kernel ([0] fallbacks,
 // [2] splits; the pairs were counted as built there).
 template <int M>
 __global__ void __launch_bounds__(128) split_build_kernel(
@@ -1311,7 +1313,7 @@ __global__ void __launch_bounds__(128) split_build_kernel(
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t n = *count;
     uint32_t fb = 0, sp = 0;
-    for (uint32_t i = blockIdx.x * 4 + w; i < n; i += gridDim.x * 4) {
+    for (uint32_t i = (uint32_t)w * gridDim.x + blockIdx.x; i < n; i += gridDim.x * 4) {
         const uint32_t p = list[i];
         const int cell = (int)(p / (uint64_t)n_gauss);
         const int64_t g = (int64_t)p - (int64_t)cell * n_gauss;
@@ -1343,7 +1345,8 @@ __global__ void __launch_bounds__(128) khigh_build_kernel(
     using RL = Rec<M>;
     const uint32_t n = *count;
     uint32_t fb = 0, sp = 0;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    // pair i on block i mod gridDim.x first (a short list spreads over the SMs)
+    for (uint32_t i = threadIdx.x * gridDim.x + blockIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const uint32_t p = list[list_cap - 1u - i];
         const int cell = (int)(p / (uint64_t)n_gauss);
         const int64_t g = (int64_t)p - (int64_t)cell * n_gauss;
