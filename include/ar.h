@@ -368,6 +368,28 @@ int ar_debug_set_prefix(ar_scene *scene, int32_t shift);
  * or another mode. */
 int ar_debug_set_cull(ar_scene *scene, int32_t mode);
 
+/* Test hooks, host only (no CUDA call): the two sizes a scene's next render
+ * learns from the sweep statistics of its previous one.
+ * ar_debug_learned_prefix: the depth prefix of the first binning phase (each
+ * cell's first 2^-shift of its sorted events; 0 = one phase).  weights[64]
+ * and counts[64]: over 64 equal buckets of each cell's depth order, the
+ * summed full-list lengths and the number of the segments whose sweep
+ * stopped in the bucket; n_entries, n_events: the tile entries and the depth
+ * events of the render to come.  The shift minimises, over 0..6, the entries
+ * the first phase sorts (n_entries 2^-shift), plus the full lists of the
+ * segments that stopped past the prefix (scaled from the previous render),
+ * the events of a second phase if there is one, and 12000 entries per
+ * restarted segment; empty statistics give 3.  Result in *shift.
+ * ar_debug_learned_window: the first round's record window (entries of a
+ * segment whose records are built before its first sweep) from hist[256],
+ * the segments by the entries they swept, in buckets of 32: the end of the
+ * bucket that holds the 99.5th percentile plus one bucket, clamped to
+ * [128, 4096]; an empty histogram gives 512.  Result in *window.
+ * AR_EINVAL for null pointers. */
+int ar_debug_learned_prefix(const uint64_t *weights, const uint32_t *counts, uint64_t n_entries, uint64_t n_events,
+                            int32_t *shift);
+int ar_debug_learned_window(const uint32_t *hist, uint32_t *window);
+
 /* Device-memory limit (bytes, >= 1 MiB) for the scene's render workspace.
  * ar_render_abstract splits the cells of a call into batches whose
  * per-(Gaussian, cell) records take about a third of this limit, and runs the

@@ -82,6 +82,8 @@ def lib():
             "ar_debug_set_entry_cap": ([P, c_int64], ctypes.c_int),
             "ar_debug_set_prefix": ([P, c_int32], ctypes.c_int),
             "ar_debug_set_cull": ([P, c_int32], ctypes.c_int),
+            "ar_debug_learned_prefix": ([P, P, ctypes.c_uint64, ctypes.c_uint64, P], ctypes.c_int),
+            "ar_debug_learned_window": ([P, P], ctypes.c_int),
             "ar_bounds_union": ([P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P], ctypes.c_int),
             "ar_partition_piece": ([P, P, c_int64, P], ctypes.c_int),
             "ar_render_abstract_refined": ([P, P, P, P, ctypes.c_int32, ctypes.c_int32, P, P, P, ctypes.c_int32, P, P],
@@ -291,6 +293,27 @@ def ar_debug_set_prefix(scene, shift: int):
 
 def ar_debug_set_cull(scene, mode: int):
     return check(lib().ar_debug_set_cull(scene, int(mode)))
+
+
+def ar_debug_learned_prefix(weights, counts, n_entries: int, n_events: int) -> int:
+    """The depth-prefix shift learned from 64-bucket stop statistics (host only)."""
+    w = np.ascontiguousarray(weights, dtype=np.uint64)
+    c = np.ascontiguousarray(counts, dtype=np.uint32)
+    if w.shape != (64,) or c.shape != (64,):
+        raise ValueError("weights and counts must have 64 entries")
+    out = c_int32()
+    check(lib().ar_debug_learned_prefix(_ptr(w), _ptr(c), int(n_entries), int(n_events), ctypes.byref(out)))
+    return out.value
+
+
+def ar_debug_learned_window(hist) -> int:
+    """The first round's record window learned from a 256-bucket sweep histogram (host only)."""
+    h = np.ascontiguousarray(hist, dtype=np.uint32)
+    if h.shape != (256,):
+        raise ValueError("hist must have 256 entries")
+    out = ctypes.c_uint32()
+    check(lib().ar_debug_learned_window(_ptr(h), ctypes.byref(out)))
+    return out.value
 
 
 def ar_last_render_stats(scene) -> dict:

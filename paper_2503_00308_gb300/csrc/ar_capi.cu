@@ -452,6 +452,22 @@ int ar_debug_set_cull(ar_scene *s, int32_t mode)
     return AR_OK;
 }
 
+int ar_debug_learned_prefix(const uint64_t *weights, const uint32_t *counts, uint64_t n_entries, uint64_t n_events,
+                            int32_t *shift)
+{
+    if (!weights || !counts || !shift) return fail(AR_EINVAL, "null argument");
+    static_assert(sizeof(unsigned long long) == sizeof(uint64_t), "64-bit histogram words");
+    *shift = learned_prefix_shift(reinterpret_cast<const unsigned long long *>(weights), counts, n_entries, n_events);
+    return AR_OK;
+}
+
+int ar_debug_learned_window(const uint32_t *hist, uint32_t *window)
+{
+    if (!hist || !window) return fail(AR_EINVAL, "null argument");
+    *window = learned_window(hist);
+    return AR_OK;
+}
+
 int ar_debug_set_prefix(ar_scene *s, int32_t shift)
 {
     if (!s) return fail(AR_EINVAL, "scene is null");
